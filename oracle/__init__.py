@@ -1,0 +1,217 @@
+"""ctypes binding of the plain FP64 CPU oracle (`sb_oracle.c`).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by `__graft_entry__.smoke()`
+and by the benchmark's CPU-baseline leg; the product path never touches it.
+It shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "libsb_oracle.so")
+_SRC = os.path.join(_HERE, "sb_oracle.c")
+
+RUNNING, CONVERGED, STALLED, MAXITER, NONFINITE = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP contraction off so x86 and Arm agree)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "sb_oracle.h"))
+    ):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [("d", C.c_int), ("K", C.c_int), ("log_w", C.c_void_p), ("mu", C.c_void_p),
+                ("L", C.c_void_p), ("lo", C.c_void_p), ("hi", C.c_void_p)]
+
+
+class _Config(C.Structure):
+    _fields_ = [("n_rays", C.c_int), ("n_steps", C.c_int), ("n_starts", C.c_int), ("m", C.c_int),
+                ("max_iter", C.c_int), ("max_backtracks", C.c_int), ("newton_steps", C.c_int),
+                ("cand_cap", C.c_int), ("gtol", C.c_double), ("armijo_c1", C.c_double),
+                ("backtrack", C.c_double), ("dedup_coarse", C.c_double), ("dedup_tol", C.c_double),
+                ("eps_grad", C.c_double), ("seed", C.c_uint64), ("n_threads", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _lib.orc_loglik.restype = C.c_double
+        for name in ("orc_select_starts", "orc_discover", "orc_cholesky", "orc_laplace", "orc_evidence"):
+            getattr(_lib, name).restype = C.c_int
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class OracleProblem:
+    """Keeps the numpy arrays alive while the C struct points at them."""
+
+    def __init__(self, inst):
+        self.d, self.K = int(inst.d), int(inst.K)
+        self.arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (inst.log_w, inst.mu, inst.L, inst.lo, inst.hi)]
+        self.s = _Problem(self.d, self.K, *[_ptr(a) for a in self.arrs])
+
+
+def _cfg(cfg, n_threads: int = 1) -> _Config:
+    return _Config(cfg.n_rays, cfg.n_steps, cfg.n_starts, cfg.m, cfg.max_iter, cfg.max_backtracks,
+                   cfg.newton_steps, cfg.cand_cap, cfg.gtol, cfg.armijo_c1, cfg.backtrack,
+                   cfg.dedup_coarse, cfg.dedup_tol, cfg.eps_grad, int(cfg.seed) & ((1 << 64) - 1),
+                   int(n_threads))
+
+
+def philox4x32_10(ctr, key):
+    c = (C.c_uint32 * 4)(*ctr)
+    k = (C.c_uint32 * 2)(*key)
+    o = (C.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def ray_directions(d: int, n_rays: int, seed: int) -> np.ndarray:
+    u = np.empty((n_rays, d))
+    lib().orc_ray_directions(C.c_int(d), C.c_int(n_rays), C.c_uint64(seed), _ptr(u))
+    return u
+
+
+def loglik(inst, x, want_grad=False, want_hess=False):
+    """l(x) for one point; optionally grad l and -hess l."""
+    P = OracleProblem(inst)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    g = np.empty(P.d) if want_grad else None
+    h = np.empty((P.d, P.d)) if want_hess else None
+    val = lib().orc_loglik(C.byref(P.s), _ptr(x), _ptr(g) if g is not None else None,
+                           _ptr(h) if h is not None else None)
+    out = [val]
+    if want_grad:
+        out.append(g)
+    if want_hess:
+        out.append(h)
+    return out[0] if len(out) == 1 else tuple(out)
+
+
+def ray_loglik(inst, cfg, n_threads=1):
+    P = OracleProblem(inst)
+    c = _cfg(cfg, n_threads)
+    u = np.empty((cfg.n_rays, P.d))
+    te = np.empty(cfg.n_rays)
+    ell = np.empty((cfg.n_rays, cfg.n_steps))
+    lib().orc_ray_loglik(C.byref(P.s), C.byref(c), _ptr(u), _ptr(te), _ptr(ell))
+    return u, te, ell
+
+
+def select_starts(cfg, ell):
+    ell = np.ascontiguousarray(ell, dtype=np.float64)
+    c = _cfg(cfg)
+    idx = np.empty(max(cfg.n_starts, 1), dtype=np.int64)
+    n = lib().orc_select_starts(C.byref(c), _ptr(ell), _ptr(idx))
+    return idx[:n]
+
+
+def discover(inst, cfg, n_threads=1):
+    P = OracleProblem(inst)
+    c = _cfg(cfg, n_threads)
+    starts = np.empty((max(cfg.n_starts, 1), P.d))
+    ls = np.empty(max(cfg.n_starts, 1))
+    n = lib().orc_discover(C.byref(P.s), C.byref(c), _ptr(starts), _ptr(ls))
+    return starts[:n], ls[:n]
+
+
+def two_loop(S, Y, rho, q):
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    count, d = (S.shape[0], S.shape[1]) if S.ndim == 2 and S.shape[0] > 0 else (0, q.shape[0])
+    r = np.empty(d)
+    lib().orc_two_loop(C.c_int(d), C.c_int(count), _ptr(S), _ptr(Y), _ptr(rho), _ptr(q), _ptr(r))
+    return r
+
+
+@dataclass
+class RefineResult:
+    x: np.ndarray
+    ell: np.ndarray
+    status: np.ndarray
+    iters: np.ndarray
+    evals: int
+
+
+def lbfgs(inst, cfg, x0, n_threads=1) -> RefineResult:
+    P = OracleProblem(inst)
+    c = _cfg(cfg, n_threads)
+    x0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(-1, P.d)
+    n = x0.shape[0]
+    xo = np.empty_like(x0)
+    lo = np.empty(n)
+    st = np.empty(n, dtype=np.int8)
+    it = np.empty(n, dtype=np.int32)
+    ev = C.c_int64(0)
+    lib().orc_lbfgs(C.byref(P.s), C.byref(c), _ptr(x0), C.c_int(n), _ptr(xo), _ptr(lo), _ptr(st), _ptr(it),
+                    C.byref(ev))
+    return RefineResult(xo, lo, st, it, int(ev.value))
+
+
+def cholesky(A):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    d = A.shape[0]
+    Cm = np.empty_like(A)
+    rc = lib().orc_cholesky(C.c_int(d), _ptr(A), _ptr(Cm))
+    return Cm if rc == 0 else None
+
+
+@dataclass
+class LaplaceResult:
+    logZ: float
+    modes: np.ndarray
+    logZk: np.ndarray
+    ell: np.ndarray
+    n_modes: int
+
+
+def laplace(inst, cfg, x, ell, status=None, cap=None, n_threads=1) -> LaplaceResult:
+    P = OracleProblem(inst)
+    c = _cfg(cfg, n_threads)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, P.d)
+    ell = np.ascontiguousarray(ell, dtype=np.float64)
+    n = x.shape[0]
+    cap = cap if cap is not None else max(cfg.cand_cap, 1)
+    modes = np.empty((cap, P.d))
+    zk = np.empty(cap)
+    lm = np.empty(cap)
+    nm = C.c_int(0)
+    lz = C.c_double(0.0)
+    st = None if status is None else np.ascontiguousarray(status, dtype=np.int8)
+    lib().orc_laplace(C.byref(P.s), C.byref(c), _ptr(x), _ptr(ell), _ptr(st) if st is not None else None,
+                      C.c_int(n), _ptr(modes), _ptr(zk), _ptr(lm), C.c_int(cap), C.byref(nm), C.byref(lz))
+    k = min(nm.value, cap)
+    return LaplaceResult(lz.value, modes[:k], zk[:k], lm[:k], nm.value)
+
+
+def evidence(inst, cfg, n_threads=1) -> LaplaceResult:
+    """discover + refine + laplace, exactly as the three functions above chain them."""
+    starts, _ = discover(inst, cfg, n_threads)
+    ref = lbfgs(inst, cfg, starts, n_threads)
+    return laplace(inst, cfg, ref.x, ref.ell, ref.status, n_threads=n_threads)
