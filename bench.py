@@ -1,0 +1,388 @@
+"""Benchmark of the evidence hot path (one step = one full evidence solve:
+discover + refine + laplace) on the seeded synthetic d=1024, K=8 mixture.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sb|reference]
+                    [--workload 4] [--prec bf16|tf32|fp64]
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on
+the host cores (the reference arm of this build) on a bounded sample of the
+same workload. Under torchrun each rank solves its own replica (no data-path
+collective); value = evaluations of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "logL+grad evals/sec and evidence solves/sec at d=1024 K=8 vs plain FP64 GPU; |ΔlogZ|"
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sb", choices=["sb", "reference"])
+    ap.add_argument("--workload", type=int, default=4)
+    ap.add_argument("--prec", default="bf16", choices=list(PREC))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_cfg(wid, prec):
+    from paper_2601_19957_gb300.instances import workload
+
+    insts, cfg = workload(wid)
+    cfg.prec = PREC[prec]
+    if wid == 4:
+        cfg.cand_cap = 64  # Hessians of 64 candidates at d=1024 = 512 MB of scratch
+    return insts[0], cfg
+
+
+def workload_name(wid, inst, cfg):
+    return (f"seeded synthetic Gaussian mixture d={inst.d} K={inst.K}, uniform prior [-10,10]^d, "
+            f"{cfg.n_rays} sunburst rays x {cfg.n_steps} steps, {cfg.n_starts} L-BFGS starts, m={cfg.m}")
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.lines = []
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ----------------------------------------------------------------------------- cpu baseline
+def cpu_baseline(inst, cfg, seconds):
+    """The FP64 oracle as it stands, on the host cores: L-BFGS walkers from the
+    oracle's own ray starts is too slow at d=1024 for a bounded sample, so the
+    sample is l+grad evaluations of oracle L-BFGS on walkers started at seeded
+    points of the workload, a few iterations each."""
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(7)
+    # time one walker-iteration first to size the sample to ~`seconds`
+    probe = inst.mu[rng.integers(0, inst.K, 1)] + rng.normal(0, 0.2, (1, inst.d))
+    c = type(cfg)(**{**cfg.__dict__, "max_iter": 1})
+    t0 = time.perf_counter()
+    r = oracle.lbfgs(inst, c, probe, n_threads=1)
+    t_one = (time.perf_counter() - t0) / max(r.evals, 1)
+    n_walk = max(cores, 1)
+    iters = max(1, int(seconds * cores / (t_one * n_walk * 2.0)))
+    c = type(cfg)(**{**cfg.__dict__, "max_iter": iters})
+    x0 = inst.mu[rng.integers(0, inst.K, n_walk)] + rng.normal(0, 0.2, (n_walk, inst.d))
+    t0 = time.perf_counter()
+    r = oracle.lbfgs(inst, c, x0, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": r.evals / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{r.evals} l+grad evaluations of FP64 oracle L-BFGS ({n_walk} walkers x <= {iters} iterations, "
+                      f"d={inst.d}, K={inst.K}) in {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- dist helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    import torch
+
+    import paper_2601_19957_gb300 as sb
+    from paper_2601_19957_gb300 import build as sbbuild
+
+    sbbuild.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    inst, cfg = workload_cfg(args.workload, args.prec)
+    prob = sb.Problem(inst)
+    c = sb.make_config(cfg)
+    wsp = sb.workspace(prob, c)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 512 MB > L2
+    L = sb.lib()
+    logV = float(np.log(inst.hi - inst.lo).sum())
+    closed = float(np.log(np.exp(inst.log_w).sum())) - logV
+
+    def one_step():
+        out = sb.evidence(prob, c, ws=wsp, sync_check=False)
+        return out
+
+    for _ in range(args.warmup):
+        out = one_step()
+    st = (sb.C.c_int64 * 4)()
+    L.sb_evidence_stats(sb.C.byref(prob.s), sb.C.byref(c), wsp.ptr, sb.C.c_size_t(wsp.nbytes), st,
+                        sb._stream())
+    evals_per_step = int(st[0]) + int(st[1])
+    n_cand, n_modes = int(st[2]), int(st[3])
+
+    clk = ClockSampler(local)
+    clk.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    L.sb_profile_enable(1)
+    launches0 = L.sb_launch_count()
+    times = []
+    ev_total = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = one_step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        L.sb_evidence_stats(sb.C.byref(prob.s), sb.C.byref(c), wsp.ptr, sb.C.c_size_t(wsp.nbytes), st, sb._stream())
+        ev_total += int(st[0]) + int(st[1])
+    torch.cuda.synchronize()
+    launches = L.sb_launch_count() - launches0
+    L.sb_profile_enable(0)
+    prof_ms = (sb.C.c_double * 8)()
+    prof_n = (sb.C.c_int64 * 8)()
+    L.sb_profile_read(prof_ms, prof_n)
+    clocks = clk.stop()
+    t_total = sum(times) / 1e3
+    if dist:
+        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+        ev = torch.tensor([ev_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(ev)
+        ev_total = int(ev.item())
+    value = ev_total / t_total
+    ms_per_step = 1e3 * t_total / args.steps
+    dlogZ = abs(out.logZ - closed)
+
+    # roofline of the dominant kernel class, measured live in the timed region
+    d, K = inst.d, inst.K
+    flop_per_eval = K * d * (d + 1)  # one triangular contraction L_k^T (x - mu_k) over all k
+    names = ["tc_z_walkers", "tc_z_rays", "tc_grad", "lbfgs_step", "f64_z", "f64_grad", "cholesky", "other"]
+    share = {names[i]: {"ms": prof_ms[i], "launches": int(prof_n[i])} for i in range(8)}
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except Exception:
+        pass
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "of measured" if peaks else "of fallback"
+    refine_evals = ev_total - args.steps * int(st[0])
+    ray_evals = args.steps * int(st[0])
+    gemm_ms = prof_ms[0] + prof_ms[1] + prof_ms[2]
+    gemm_flop = (refine_evals * 2 + ray_evals) * flop_per_eval
+    lb_ms = prof_ms[3]
+    # two-loop traffic per walker-iteration: 4 m d history reads + ~8 d vector reads/writes (FP32)
+    lb_bytes = refine_evals * (4 * cfg.m * d + 8 * d) * 4
+    if cfg.prec == 0:
+        peak = 1.25e3  # GFLOP/s-scale FP64 (2 FMA/clk/SM x 152 SMs x 2.07 GHz x 2)
+        gemm_tf = gemm_flop / max(prof_ms[4] + prof_ms[5], 1e-9) / 1e9
+        roof = {"bound": "alu", "achieved": gemm_tf, "peak": peak, "unit": "GFLOP/s", "frac": gemm_tf / peak,
+                "traffic": None, "kernel": "f64_z+f64_grad", "peak_source": "FP64 units x clock (nominal)"}
+    elif gemm_ms >= lb_ms:
+        achieved = gemm_flop / (gemm_ms / 1e3) / 1e12
+        tflops_peak = bf16_peak if cfg.prec == 2 else bf16_peak / 2.0
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tflops_peak, "unit": "TFLOP/s",
+                "frac": achieved / tflops_peak, "traffic": None, "kernel": "k_tc_gemm (z + grad)",
+                "peak_source": peak_src + (" bf16 burst" if cfg.prec == 2 else " bf16 burst / 2 (tf32 nominal ratio)")}
+    else:
+        achieved = lb_bytes / (lb_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": None, "kernel": "k_lbfgs_step", "peak_source": peak_src}
+
+    res = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "evals/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {0: "f64", 1: "tf32", 2: "bf16"}[cfg.prec],
+        "data": "synthetic",
+        "config": {"workload": workload_name(args.workload, inst, cfg), "d": d, "K": K, "n_rays": cfg.n_rays,
+                   "n_steps": cfg.n_steps, "n_starts": cfg.n_starts, "m": cfg.m, "prec": args.prec,
+                   "laplace": "fp64", "parallelism": f"replicas x{ws}",
+                   "l2": "512 MB buffer zeroed between timed steps; per-step working set > L2",
+                   "evals_counted": "ray-sample l evaluations + L-BFGS l+grad evaluations per solve"},
+        "solves_per_sec": ws * args.steps / t_total,
+        "evals_per_step": evals_per_step,
+        "n_candidates": n_cand,
+        "n_modes": n_modes,
+        "logZ": out.logZ,
+        "abs_dlogZ_vs_closed_form": dlogZ,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "roofline": roof,
+        "kernel_ms": share,
+    }
+    if rank == 0 and not args.no_e2e:
+        res["e2e"] = e2e_measure(sb, inst, cfg, c, args, evals_per_step)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(inst, cfg, args.cpu_seconds)
+    if rank == 0:
+        res["fp64_gpu"] = fp64_comparator(sb, inst, prob)
+        print(json.dumps(res))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def e2e_measure(sb, inst, cfg, c, args, evals_per_step):
+    """Same metric through sb_evidence_host: host arrays in, log Z and modes out."""
+    import torch
+
+    wsh = sb.evidence_host_workspace(inst, c)
+    sb.evidence_host(inst, c, wsh)  # warm
+    t0 = time.perf_counter()
+    n = max(1, min(args.steps, 3))
+    for _ in range(n):
+        logZ, modes, zk, nm = sb.evidence_host(inst, c, wsh)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / n
+    h2d = 8 * (inst.K + inst.K * inst.d + inst.K * inst.d * inst.d + 2 * inst.d)
+    d2h = 8 + 4 + 8 * min(nm, cfg.cand_cap) * (inst.d + 1)
+    return {"value": evals_per_step / dt, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": dt * 1e3}
+
+
+def fp64_comparator(sb, inst, prob):
+    """Plain FP64 GPU path: l+grad evals/s of the FP64 CUDA-core kernels on a batch."""
+    import torch
+
+    rng = np.random.default_rng(11)
+    n = 2048
+    X = torch.as_tensor(inst.mu[rng.integers(0, inst.K, n)] + rng.normal(0, 0.3, (n, inst.d)), device="cuda")
+    wsl = sb.Workspace(sb.lib().sb_loglik_workspace_bytes(sb.C.byref(prob.s), 0, n))
+    sb.loglik(prob, X, prec=0, ws=wsl)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    reps = 2
+    for _ in range(reps):
+        sb.loglik(prob, X, prec=0, ws=wsl)
+    e1.record()
+    e1.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3 / reps
+    flop = n * 2 * inst.K * inst.d * (inst.d + 1)
+    out = {"evals_per_sec": n / dt, "gflops": flop / dt / 1e9, "batch": n}
+    # the tensor-core kernels on the same batch
+    for name, p in (("bf16", 2), ("tf32", 1)):
+        wst = sb.Workspace(sb.lib().sb_loglik_workspace_bytes(sb.C.byref(prob.s), p, n))
+        sb.loglik(prob, X, prec=p, ws=wst)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            sb.loglik(prob, X, prec=p, ws=wst)
+        e1.record()
+        e1.synchronize()
+        dtp = e0.elapsed_time(e1) / 1e3 / 5
+        out[f"{name}_evals_per_sec"] = n / dtp
+        out[f"{name}_speedup_vs_fp64"] = dt / dtp
+    return out
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 oracle on the host cores, same metric and config."""
+    if rank != 0:
+        return 0
+    inst, cfg = workload_cfg(args.workload, args.prec)
+    per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        cpu_baseline(inst, cfg, min(per_step, 3.0))
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(inst, cfg, per_step))
+    dt = time.perf_counter() - t0
+    v = float(np.mean([r["value"] for r in vals]))
+    res = {"metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": workload_name(args.workload, inst, cfg), "d": inst.d, "K": inst.K},
+           "cpu_baseline": {"value": v, "unit": "evals/s", "cores": vals[0]["cores"], "kind": "oracle",
+                            "sample": vals[0]["sample"]},
+           "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main() or 0)

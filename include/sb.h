@@ -1,0 +1,194 @@
+/*
+ * sb.h -- C ABI of the GB300 (sm_103a) evidence library `libsb.so`.
+ *
+ * The library computes Bayesian evidence log Z for a Gaussian-mixture
+ * log-likelihood under a uniform box prior by the mode-centric method of
+ * SunBURST (arXiv 2601.19957): sunburst rays from the prior centre (Sec. 3.5),
+ * batched L-BFGS refinement (Sec. 3.6, App. A.5), and a Laplace term per
+ * distinct mode combined by log-sum-exp (Sec. 3.7, App. A.3, A.8, A.10).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named in `sb_problem`, and every array argument, are DEVICE
+ *    pointers unless the comment says "host". The caller owns all memory.
+ *  - Arrays are dense, row-major, float64 unless stated: a point set is
+ *    [n][d]; the precision Cholesky factors are [K][d][d] (lower triangle used).
+ *  - `ws` is caller-owned device scratch of at least the size the matching
+ *    *_workspace_bytes query returns (256-byte aligned base). The library
+ *    allocates no device memory of its own.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued on it. Entry points that must observe device state
+ *    (noted per function) synchronise that stream before returning.
+ *  - Argument errors are detected on the host and returned before any launch.
+ *    Problems only visible on the device (non-finite parameters, lo >= hi,
+ *    non-positive Cholesky diagonal, zero modes) are recorded in a status word
+ *    inside `ws`; `sb_check` reads it.
+ *  - No C++ exception crosses this boundary.
+ */
+#ifndef SB_H
+#define SB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sb_status {
+    SB_OK = 0,
+    SB_ERR_INVALID_ARG = 1, /* bad sizes, null pointers, lo >= hi, L_kk <= 0 */
+    SB_ERR_CUDA = 2,        /* a CUDA runtime call failed                      */
+    SB_ERR_WORKSPACE = 3,   /* ws smaller than the query says                  */
+    SB_ERR_NONFINITE = 4,   /* NaN/Inf in parameters or in a required result   */
+    SB_ERR_NO_MODES = 5,    /* no candidate survived the Laplace filters       */
+    SB_ERR_TIMEOUT = 6,     /* a bounded device loop ran out of iterations     */
+    SB_ERR_UNSUPPORTED = 7  /* size outside what this build handles (d > 1024) */
+} sb_status;
+
+/* Arithmetic of the log-likelihood / gradient contractions (discover, refine).
+ * The Laplace stage (Newton polish, Hessian, Cholesky, log-sum-exp) is always FP64. */
+typedef enum sb_precision {
+    SB_PREC_FP64 = 0, /* FP64 on CUDA cores, FP64 L-BFGS state               */
+    SB_PREC_TF32 = 1, /* tcgen05 kind::tf32, FP32 accumulate, FP32 state      */
+    SB_PREC_BF16 = 2  /* tcgen05 kind::f16 (bf16), FP32 accumulate, FP32 state */
+} sb_precision;
+
+/* One evidence problem (Sec. 3.2): l(x) = log sum_k w_k N(x; mu_k, P_k^{-1}),
+ * P_k = L_k L_k^T, uniform prior on prod_i [lo_i, hi_i]. */
+typedef struct sb_problem {
+    int32_t d;            /* dimension, 1 <= d <= 1024                      */
+    int32_t K;            /* components, 1 <= K <= 64                       */
+    const double *log_w;  /* [K]      log mixture weights                   */
+    const double *mu;     /* [K][d]   component means                       */
+    const double *L;      /* [K][d][d] lower Cholesky factors of precisions */
+    const double *lo;     /* [d]      prior box lower edges                 */
+    const double *hi;     /* [d]      prior box upper edges (hi > lo)       */
+} sb_problem;
+
+/* Knobs of one solve. Defaults used by the tests are in parentheses. */
+typedef struct sb_config {
+    int32_t n_rays;         /* sunburst rays from the prior centre (Sec. 3.5.1)           */
+    int32_t n_steps;        /* coarse samples per ray, t_j = (j+1)/n_steps (Sec. 3.5.2)    */
+    int32_t n_starts;       /* L-BFGS walkers, <= n_rays * n_steps                         */
+    int32_t m;              /* L-BFGS history pairs, 1..64 (App. A.5)                      */
+    int32_t max_iter;       /* accepted L-BFGS steps per walker (1000)                     */
+    int32_t max_backtracks; /* Armijo halvings per line search (40)                        */
+    int32_t newton_steps;   /* FP64 Newton polish steps per candidate (3)                  */
+    int32_t cand_cap;       /* most candidates entering the Laplace stage (256)            */
+    double gtol;            /* stop when |grad l|_inf <= gtol (1 + |l|) (1e-12)            */
+    double armijo_c1;       /* sufficient-decrease constant (1e-4)                         */
+    double backtrack;       /* step factor per backtrack (0.5)                             */
+    double dedup_coarse;    /* coarse L-inf dedup radius / max_i (hi_i - lo_i) (1e-3)      */
+    double dedup_tol;       /* final L-inf dedup radius / max_i (hi_i - lo_i) (1e-6)       */
+    double eps_grad;        /* gradient filter |grad l|_inf <= eps_grad (1 + |l|) (1e-6)   */
+    uint64_t seed;          /* Philox4x32-10 key for the ray directions                    */
+    int32_t prec;           /* sb_precision of discover/refine                             */
+    int32_t reserved;       /* must be 0                                                   */
+} sb_config;
+
+/* Walker terminal states written by sb_refine (int8 per walker). */
+enum { SB_WALKER_RUNNING = 0, SB_WALKER_CONVERGED = 1, SB_WALKER_STALLED = 2,
+       SB_WALKER_MAXITER = 3, SB_WALKER_NONFINITE = 4 };
+
+/* Human-readable name of a status code (static storage). */
+const char *sb_status_string(sb_status s);
+
+/* Bytes of device scratch the solve stages need for this problem and config
+ * (the maximum over sb_discover, sb_refine, sb_laplace and sb_evidence).
+ * Host-only call: no allocation, no CUDA call. Returns 0 if the arguments are invalid. */
+size_t sb_workspace_bytes(const sb_problem *prob, const sb_config *cfg);
+
+/* Bytes of scratch sb_loglik needs for n points at precision prec. */
+size_t sb_loglik_workspace_bytes(const sb_problem *prob, int32_t prec, int32_t n);
+
+/*
+ * Batched log-likelihood (and gradient) of the mixture at n points:
+ *   ell[p] = l(x_p) = LSE_k [log w_k - (d/2) log 2pi + sum_i log L_k,ii - |L_k^T (x_p - mu_k)|^2 / 2]
+ *   grad[p*d + i] = d l / d x_i = -sum_k r_k (L_k L_k^T (x_p - mu_k))_i,  r = softmax_k
+ * (Sec. 3.2 likelihood; the gradient replaces the finite differences of App. A.4.1).
+ * x: [n][d]; ell: [n]; grad: [n][d] or NULL for values only. Asynchronous.
+ */
+sb_status sb_loglik(const sb_problem *prob, int32_t prec, const double *x, int32_t n, double *ell,
+                    double *grad, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Mode discovery (Sec. 3.5.1-3.5.2): n_rays unit directions u_r (Philox4x32-10
+ * normals, key = seed, normalised), samples x_rj = c + ((j+1)/n_steps) t_exit,r u_r
+ * with c the box centre and t_exit,r the distance to the box surface, l at every
+ * sample, then the n_starts samples first in the order (tier: local maximum
+ * along the ray first; rank of l inside the ray; -l; flat index r*n_steps+j),
+ * written in ascending flat index.
+ * starts: [n_starts][d]; ell: [n_starts] (l at each start). Asynchronous.
+ */
+sb_status sb_discover(const sb_problem *prob, const sb_config *cfg, double *starts, double *ell, void *ws,
+                      size_t ws_bytes, void *stream);
+
+/*
+ * Batched L-BFGS refinement (Sec. 3.6.2, App. A.5) of n walkers maximising l:
+ * two-loop recursion with history m, Armijo backtracking, terminal states in
+ * status_out (SB_WALKER_*). starts: [n][d]; x_out: [n][d]; ell_out: [n];
+ * status_out: int8 [n]; iters_out: int32 [n] accepted steps (may be NULL);
+ * n_evals: int64 device scalar, total l+grad evaluations (may be NULL).
+ * Synchronises `stream` (the host polls the active-walker count).
+ */
+sb_status sb_refine(const sb_problem *prob, const sb_config *cfg, const double *starts, int32_t n, double *x_out,
+                    double *ell_out, int8_t *status_out, int32_t *iters_out, int64_t *n_evals, void *ws,
+                    size_t ws_bytes, void *stream);
+
+/*
+ * Laplace stage in FP64 (Sec. 3.6.4 filters, Sec. 3.7.1 Laplace, App. A.8, A.10):
+ * coarse L-inf dedup of the walkers (x, ell, status), FP64 Newton polish with
+ * the analytic Hessian H = -hess l and its Cholesky factor, positive-definite /
+ * gradient / in-box filters, final dedup, log Z_k = l(x*) + (d/2) log 2pi -
+ * sum_i log C_ii (H = C C^T), log Z = LSE_k log Z_k - log V.
+ * status may be NULL (all walkers eligible). modes: [cap][d]; logZk, ell_modes:
+ * [cap] (ell_modes may be NULL); n_modes: int32 device scalar; logZ: device scalar.
+ * Modes are ordered by decreasing l. Asynchronous; zero modes give logZ = -inf
+ * and set SB_ERR_NO_MODES in the status word.
+ */
+sb_status sb_laplace(const sb_problem *prob, const sb_config *cfg, const double *x, const double *ell,
+                     const int8_t *status, int32_t n, double *modes, double *logZk, double *ell_modes, int32_t cap,
+                     int32_t *n_modes, double *logZ, void *ws, size_t ws_bytes, void *stream);
+
+/* discover + refine + laplace on device buffers (the whole hot path).
+ * logZ, n_modes: device scalars; modes [cap][d]; logZk [cap]. Synchronises `stream`. */
+sb_status sb_evidence(const sb_problem *prob, const sb_config *cfg, double *logZ, double *modes, double *logZk,
+                      int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes, void *stream);
+
+/* sb_evidence with HOST inputs and outputs: copies the problem arrays (host
+ * pointers in `host_prob`) into `ws`, solves, and copies log Z, the modes and
+ * their log Z_k back (host pointers; modes/logZk may be NULL). ws must hold
+ * sb_evidence_host_workspace_bytes. Synchronises `stream`. */
+size_t sb_evidence_host_workspace_bytes(const sb_problem *host_prob, const sb_config *cfg);
+sb_status sb_evidence_host(const sb_problem *host_prob, const sb_config *cfg, double *logZ, double *modes,
+                           double *logZk, int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes, void *stream);
+
+/* Synchronise `stream` and return the status word the device recorded in ws
+ * (SB_OK if nothing went wrong); clears the word. */
+sb_status sb_check(void *ws, size_t ws_bytes, void *stream);
+
+/* Counters of the last sb_evidence call that used this workspace (synchronises
+ * `stream`): out[0] ray samples evaluated (l only), out[1] l + grad evaluations
+ * of the L-BFGS stage, out[2] coarse candidates polished, out[3] modes kept.
+ * out: host int64[4]. */
+sb_status sb_evidence_stats(const sb_problem *prob, const sb_config *cfg, void *ws, size_t ws_bytes, int64_t *out,
+                            void *stream);
+
+/* Number of kernel launches this process has issued through the library so far
+ * (host counter, diagnostics only). */
+int64_t sb_launch_count(void);
+
+/* Device-time profiling of the main kernel classes (diagnostics). While enabled,
+ * each launch of a class is bracketed by CUDA events on its stream.
+ * sb_profile_read synchronises those events, writes per-class total
+ * milliseconds and launch counts (host arrays of 8: 0 tensor-core z GEMM at
+ * walkers, 1 tensor-core z GEMM at ray samples, 2 tensor-core gradient GEMM,
+ * 3 L-BFGS step, 4 FP64 z GEMM, 5 FP64 gradient GEMM, 6 FP64 Cholesky,
+ * 7 other), clears the record and returns the number of unreadable events. */
+void sb_profile_enable(int on);
+int32_t sb_profile_read(double *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SB_H */

@@ -1,0 +1,282 @@
+"""Python binding of libsb, the GB300 (sm_103a) evidence library.
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels behind the C ABI of include/sb.h. PyTorch supplies device memory and
+streams. The library must be built (``build.build()``); importing a function
+that needs it fails loudly if ``_lib/libsb.so`` is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from .instances import Instance, SolveConfig
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsb.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "sb.h")
+
+SB_OK, SB_ERR_INVALID_ARG, SB_ERR_CUDA, SB_ERR_WORKSPACE, SB_ERR_NONFINITE, SB_ERR_NO_MODES, SB_ERR_TIMEOUT, \
+    SB_ERR_UNSUPPORTED = range(8)
+PREC_FP64, PREC_TF32, PREC_BF16 = 0, 1, 2
+RUNNING, CONVERGED, STALLED, MAXITER, NONFINITE = range(5)
+
+
+class SbError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)}")
+
+
+class _Problem(C.Structure):
+    _fields_ = [("d", C.c_int32), ("K", C.c_int32), ("log_w", C.c_void_p), ("mu", C.c_void_p),
+                ("L", C.c_void_p), ("lo", C.c_void_p), ("hi", C.c_void_p)]
+
+
+class _Config(C.Structure):
+    _fields_ = [("n_rays", C.c_int32), ("n_steps", C.c_int32), ("n_starts", C.c_int32), ("m", C.c_int32),
+                ("max_iter", C.c_int32), ("max_backtracks", C.c_int32), ("newton_steps", C.c_int32),
+                ("cand_cap", C.c_int32), ("gtol", C.c_double), ("armijo_c1", C.c_double),
+                ("backtrack", C.c_double), ("dedup_coarse", C.c_double), ("dedup_tol", C.c_double),
+                ("eps_grad", C.c_double), ("seed", C.c_uint64), ("prec", C.c_int32), ("reserved", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libsb.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libsb.so not built ({LIB_PATH}); run paper_2601_19957_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        L.sb_status_string.restype = C.c_char_p
+        L.sb_workspace_bytes.restype = C.c_size_t
+        L.sb_loglik_workspace_bytes.restype = C.c_size_t
+        L.sb_evidence_host_workspace_bytes.restype = C.c_size_t
+        for name in ("sb_loglik", "sb_discover", "sb_refine", "sb_laplace", "sb_evidence", "sb_evidence_host",
+                     "sb_check"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    """Function names declared in include/sb.h."""
+    with open(HEADER_PATH) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sb_[a-z0-9_]+)\s*\(", text)))
+
+
+def status_string(code: int) -> str:
+    try:
+        return lib().sb_status_string(int(code)).decode()
+    except Exception:
+        return f"status {code}"
+
+
+def _check(code: int, where: str):
+    if code != SB_OK:
+        raise SbError(code, where)
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Problem:
+    """Device copy of one Instance plus the C struct that points at it."""
+
+    def __init__(self, inst: Instance, device="cuda"):
+        torch = _torch()
+        self.inst = inst
+        self.d, self.K = int(inst.d), int(inst.K)
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=device)
+        self.log_w, self.mu, self.L, self.lo, self.hi = (f(inst.log_w), f(inst.mu), f(inst.L), f(inst.lo),
+                                                         f(inst.hi))
+        self.s = _Problem(self.d, self.K, self.log_w.data_ptr(), self.mu.data_ptr(), self.L.data_ptr(),
+                          self.lo.data_ptr(), self.hi.data_ptr())
+
+
+def host_problem(inst: Instance):
+    """C struct pointing at host numpy arrays (for sb_evidence_host); keeps them alive."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (inst.log_w, inst.mu, inst.L, inst.lo, inst.hi)]
+    s = _Problem(int(inst.d), int(inst.K), *[a.ctypes.data for a in arrs])
+    return s, arrs
+
+
+def make_config(cfg: SolveConfig, **over) -> _Config:
+    v = dict(cfg.__dict__)
+    v.update(over)
+    return _Config(v["n_rays"], v["n_steps"], v["n_starts"], v["m"], v["max_iter"], v["max_backtracks"],
+                   v["newton_steps"], v["cand_cap"], v["gtol"], v["armijo_c1"], v["backtrack"], v["dedup_coarse"],
+                   v["dedup_tol"], v["eps_grad"], int(v["seed"]) & ((1 << 64) - 1), int(v["prec"]), 0)
+
+
+def workspace_bytes(prob: Problem, cfg: _Config) -> int:
+    return int(lib().sb_workspace_bytes(C.byref(prob.s), C.byref(cfg)))
+
+
+class Workspace:
+    """Caller-owned device scratch sized by the library's query."""
+
+    def __init__(self, nbytes: int, device="cuda"):
+        torch = _torch()
+        if nbytes <= 0:
+            raise SbError(SB_ERR_INVALID_ARG, "workspace query")
+        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+        self.nbytes = int(nbytes)
+
+    @property
+    def ptr(self):
+        return C.c_void_p(self.buf.data_ptr())
+
+
+def workspace(prob: Problem, cfg: _Config) -> Workspace:
+    return Workspace(workspace_bytes(prob, cfg))
+
+
+def check(ws: Workspace, stream=None):
+    """Synchronise and raise on the device status word (non-finite input, no modes, ...)."""
+    _check(lib().sb_check(ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)), "sb_check")
+
+
+def loglik(prob: Problem, x, prec: int = PREC_FP64, want_grad: bool = True, ws: Workspace = None, stream=None):
+    torch = _torch()
+    x = x.to(dtype=torch.float64).contiguous()
+    n = x.shape[0]
+    ell = torch.empty(n, dtype=torch.float64, device=x.device)
+    grad = torch.empty_like(x) if want_grad else None
+    if ws is None:
+        ws = Workspace(lib().sb_loglik_workspace_bytes(C.byref(prob.s), int(prec), int(n)))
+    _check(lib().sb_loglik(C.byref(prob.s), C.c_int32(prec), _ptr(x), C.c_int32(n), _ptr(ell), _ptr(grad), ws.ptr,
+                           C.c_size_t(ws.nbytes), _stream(stream)), "sb_loglik")
+    return (ell, grad) if want_grad else ell
+
+
+def discover(prob: Problem, cfg: _Config, ws: Workspace = None, stream=None):
+    torch = _torch()
+    ws = ws or workspace(prob, cfg)
+    starts = torch.empty((cfg.n_starts, prob.d), dtype=torch.float64, device="cuda")
+    ell = torch.empty(cfg.n_starts, dtype=torch.float64, device="cuda")
+    _check(lib().sb_discover(C.byref(prob.s), C.byref(cfg), _ptr(starts), _ptr(ell), ws.ptr, C.c_size_t(ws.nbytes),
+                             _stream(stream)), "sb_discover")
+    return starts, ell
+
+
+@dataclass
+class RefineOut:
+    x: object
+    ell: object
+    status: object
+    iters: object
+    n_evals: int
+
+
+def refine(prob: Problem, cfg: _Config, starts, ws: Workspace = None, stream=None) -> RefineOut:
+    torch = _torch()
+    ws = ws or workspace(prob, cfg)
+    starts = starts.to(dtype=torch.float64).contiguous()
+    n = starts.shape[0]
+    x = torch.empty_like(starts)
+    ell = torch.empty(n, dtype=torch.float64, device=starts.device)
+    st = torch.empty(n, dtype=torch.int8, device=starts.device)
+    it = torch.empty(n, dtype=torch.int32, device=starts.device)
+    ev = torch.zeros(1, dtype=torch.int64, device=starts.device)
+    _check(lib().sb_refine(C.byref(prob.s), C.byref(cfg), _ptr(starts), C.c_int32(n), _ptr(x), _ptr(ell), _ptr(st),
+                           _ptr(it), _ptr(ev), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)), "sb_refine")
+    return RefineOut(x, ell, st, it, int(ev.item()))
+
+
+@dataclass
+class LaplaceOut:
+    logZ: float
+    modes: object
+    logZk: object
+    ell: object
+    n_modes: int
+
+
+def laplace(prob: Problem, cfg: _Config, x, ell, status=None, cap: Optional[int] = None, ws: Workspace = None,
+            stream=None, raise_no_modes: bool = False) -> LaplaceOut:
+    torch = _torch()
+    ws = ws or workspace(prob, cfg)
+    x = x.to(dtype=torch.float64).contiguous()
+    ell = ell.to(dtype=torch.float64).contiguous()
+    n = x.shape[0]
+    cap = cap or cfg.cand_cap
+    modes = torch.empty((cap, prob.d), dtype=torch.float64, device=x.device)
+    zk = torch.empty(cap, dtype=torch.float64, device=x.device)
+    lm = torch.empty(cap, dtype=torch.float64, device=x.device)
+    nm = torch.zeros(1, dtype=torch.int32, device=x.device)
+    lz = torch.zeros(1, dtype=torch.float64, device=x.device)
+    st = None if status is None else status.to(dtype=torch.int8).contiguous()
+    _check(lib().sb_laplace(C.byref(prob.s), C.byref(cfg), _ptr(x), _ptr(ell), _ptr(st), C.c_int32(n), _ptr(modes),
+                            _ptr(zk), _ptr(lm), C.c_int32(cap), _ptr(nm), _ptr(lz), ws.ptr, C.c_size_t(ws.nbytes),
+                            _stream(stream)), "sb_laplace")
+    code = lib().sb_check(ws.ptr, C.c_size_t(ws.nbytes), _stream(stream))
+    if code != SB_OK and (code != SB_ERR_NO_MODES or raise_no_modes):
+        raise SbError(code, "sb_laplace")
+    k = min(int(nm.item()), cap)
+    return LaplaceOut(float(lz.item()), modes[:k], zk[:k], lm[:k], int(nm.item()))
+
+
+def evidence(prob: Problem, cfg: _Config, cap: Optional[int] = None, ws: Workspace = None, stream=None,
+             sync_check: bool = True) -> LaplaceOut:
+    torch = _torch()
+    ws = ws or workspace(prob, cfg)
+    cap = cap or cfg.cand_cap
+    modes = torch.empty((cap, prob.d), dtype=torch.float64, device="cuda")
+    zk = torch.empty(cap, dtype=torch.float64, device="cuda")
+    nm = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lz = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _check(lib().sb_evidence(C.byref(prob.s), C.byref(cfg), _ptr(lz), _ptr(modes), _ptr(zk), C.c_int32(cap),
+                             _ptr(nm), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)), "sb_evidence")
+    if sync_check:
+        code = lib().sb_check(ws.ptr, C.c_size_t(ws.nbytes), _stream(stream))
+        if code not in (SB_OK, SB_ERR_NO_MODES):
+            raise SbError(code, "sb_evidence")
+    k = min(int(nm.item()), cap)
+    return LaplaceOut(float(lz.item()), modes[:k], zk[:k], None, int(nm.item()))
+
+
+def evidence_host_workspace(inst: Instance, cfg: _Config) -> Workspace:
+    s, _keep = host_problem(inst)
+    return Workspace(lib().sb_evidence_host_workspace_bytes(C.byref(s), C.byref(cfg)))
+
+
+def evidence_host(inst: Instance, cfg: _Config, ws: Workspace, stream=None):
+    """The whole path on HOST arrays: copies in, solves, copies log Z and the modes out."""
+    s, keep = host_problem(inst)
+    cap = cfg.cand_cap
+    lz = np.zeros(1)
+    nm = np.zeros(1, dtype=np.int32)
+    modes = np.zeros((cap, inst.d))
+    zk = np.zeros(cap)
+    code = lib().sb_evidence_host(C.byref(s), C.byref(cfg), lz.ctypes.data_as(C.c_void_p),
+                                  modes.ctypes.data_as(C.c_void_p), zk.ctypes.data_as(C.c_void_p), C.c_int32(cap),
+                                  nm.ctypes.data_as(C.c_void_p), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream))
+    if code not in (SB_OK, SB_ERR_NO_MODES):
+        raise SbError(code, "sb_evidence_host")
+    del keep
+    k = min(int(nm[0]), cap)
+    return float(lz[0]), modes[:k], zk[:k], int(nm[0])

@@ -1,0 +1,600 @@
+// laplace.cu -- FP64 Laplace stage: dedup, Newton polish, filters, log Z.
+//
+//  * coarse / final deduplication: greedy L-infinity merging in order of
+//    decreasing l, ties to the lower index (Sec. 3.5.4, App. A.7); one CTA,
+//    each round an argmax over the unassigned points and an early-exit
+//    L-infinity test of every unassigned point against the new representative;
+//  * Hessian H = -hess l = sum_k r_k P_k - sum_k r_k g_k g_k^T + gbar gbar^T,
+//    with P_k = L_k L_k^T precomputed once and g_k = -L_k z_k (the analytic
+//    form of the finite-difference Hessian of Sec. 3.7.2 / App. A.4.3);
+//    components with r_k == 0 contribute exactly nothing and are skipped;
+//  * batched blocked Cholesky H = C C^T (right-looking, 32x32 blocks:
+//    diagonal factor, panel triangular solve, trailing update), which also
+//    serves as the positive-definiteness (saddle) filter of Sec. 3.6.4;
+//  * Newton polish x <- x + t H^{-1} grad l, t halved until l does not drop;
+//  * log Z_k = l(x*) + (d/2) log 2pi - sum_i log C_ii (Sec. 3.7.1 with the
+//    whitening identity of App. A.8) and log Z = LSE_k log Z_k - log V
+//    (Sec. 3.7.3, App. A.10, Sec. 3.2).
+#include "sb_laplace.cuh"
+
+namespace sb {
+
+namespace {
+
+constexpr int NB = 32;  // Cholesky block
+
+// ------------------------------------------------------------------ dedup
+// Greedy rounds in one CTA of 1024 threads. `elig` marks points that take part.
+__global__ void __launch_bounds__(1024) k_dedup(int n, int d, const double *X, const double *ell,
+                                                const int8_t *status, const uint8_t *keep_in, double tau_scale,
+                                                const double *wmax, int cap, int32_t *reps, int32_t *n_reps,
+                                                uint8_t *assigned) {
+    __shared__ double s_l[32];
+    __shared__ int s_i[32];
+    __shared__ int s_best;
+    const double tau = tau_scale * wmax[0];
+    for (int w = threadIdx.x; w < n; w += blockDim.x) {
+        bool el = isfinite(ell[w]);
+        if (status && status[w] == SB_WALKER_NONFINITE) el = false;
+        if (keep_in && !keep_in[w]) el = false;
+        assigned[w] = el ? 0 : 1;
+    }
+    __syncthreads();
+    int count = 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    while (true) {
+        double bl = -INFINITY;
+        int bi = -1;
+        for (int w = threadIdx.x; w < n; w += blockDim.x) {
+            if (assigned[w]) continue;
+            const double l = ell[w];
+            if (bi < 0 || l > bl) {  // strided ascending: first seen has the lower index
+                bl = l;
+                bi = w;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ol = __shfl_xor_sync(0xffffffffu, bl, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (oi >= 0 && (bi < 0 || ol > bl || (ol == bl && oi < bi))) {
+                bl = ol;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            s_l[wid] = bl;
+            s_i[wid] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = -INFINITY;
+            int ib = -1;
+            for (int q = 0; q < 32; ++q) {
+                const int oi = s_i[q];
+                const double ol = s_l[q];
+                if (oi >= 0 && (ib < 0 || ol > b || (ol == b && oi < ib))) {
+                    b = ol;
+                    ib = oi;
+                }
+            }
+            s_best = ib;
+            if (ib >= 0) {
+                assigned[ib] = 1;
+                if (count < cap) reps[count] = ib;
+            }
+        }
+        __syncthreads();
+        const int best = s_best;
+        if (best < 0) break;
+        ++count;
+        if (count >= cap) break;
+        const double *xb = X + (size_t)best * d;
+        for (int w = threadIdx.x; w < n; w += blockDim.x) {
+            if (assigned[w]) continue;
+            const double *xw = X + (size_t)w * d;
+            bool within = true;
+            for (int i = 0; i < d; ++i)
+                if (fabs(xw[i] - xb[i]) > tau) {
+                    within = false;
+                    break;
+                }
+            if (within) assigned[w] = 1;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_reps = count < cap ? count : cap;
+}
+
+__global__ void __launch_bounds__(256) k_gather_rows(int d, const double *X, const int32_t *idx, const int32_t *n_idx,
+                                                     double *out, const double *ell, double *ell_out) {
+    const int c = blockIdx.x;
+    if (c >= *n_idx) return;
+    const int w = idx[c];
+    for (int i = threadIdx.x; i < d; i += blockDim.x) out[(size_t)c * d + i] = X[(size_t)w * d + i];
+    if (threadIdx.x == 0 && ell_out) ell_out[c] = ell[w];
+}
+
+// ------------------------------------------------------------------ P_k = L_k L_k^T
+__global__ void __launch_bounds__(256) k_precision(int d, const double *L, double *P) {
+    const int k = blockIdx.z, i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+    if (j0 > i0) return;  // lower blocks only, mirrored on store
+    const double *Lk = L + (size_t)k * d * d;
+    __shared__ double As[16][65], Bs[16][65];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double acc[4][4] = {};
+    const int jmax = min(d, j0 + 64);  // P_ij = sum_{l <= min(i,j)} L_il L_jl
+    for (int l0 = 0; l0 < jmax; l0 += 16) {
+        for (int e = tid; e < 16 * 64; e += 256) {
+            const int r = e >> 4, kk = e & 15, l = l0 + kk;
+            const int i = i0 + r, j = j0 + r;
+            As[kk][r] = (i < d && l < d && l <= i) ? Lk[(size_t)i * d + l] : 0.0;
+            Bs[kk][r] = (j < d && l < d && l <= j) ? Lk[(size_t)j * d + l] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+    double *Pk = P + (size_t)k * d * d;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
+            if (i < d && j < d) {
+                Pk[(size_t)i * d + j] = acc[r][c];
+                Pk[(size_t)j * d + i] = acc[r][c];
+            }
+        }
+}
+
+// ------------------------------------------------------------------ per-component gradients
+// GK[c][k][i] = -sum_{j<=i} L_k[i][j] z_ck[j]  (zero when r_ck == 0)
+__global__ void __launch_bounds__(256) k_comp_grads(int d, int K, const double *L, const double *Z, const double *R,
+                                                    const int32_t *n_c, double *GK) {
+    const int c = blockIdx.x, k = blockIdx.y;
+    if (c >= *n_c) return;
+    const double r = R[(size_t)c * K + k];
+    double *g = GK + ((size_t)c * K + k) * d;
+    if (r == 0.0) {
+        for (int i = threadIdx.x; i < d; i += blockDim.x) g[i] = 0.0;
+        return;
+    }
+    extern __shared__ double zs[];
+    const double *z = Z + ((size_t)c * K + k) * d;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) zs[i] = z[i];
+    __syncthreads();
+    const double *Lk = L + (size_t)k * d * d;
+    // one warp per output row: coalesced reads of L_k rows
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < d; i += nw) {
+        double s = 0.0;
+        for (int j = lane; j <= i; j += 32) s += Lk[(size_t)i * d + j] * zs[j];
+        s = warp_sum(s);
+        if (lane == 0) g[i] = -s;
+    }
+}
+
+// H[c][i][i2] = gbar_i gbar_i2 + sum_k r_k (P_k[i][i2] - g_ki g_ki2)
+__global__ void __launch_bounds__(256) k_hessian(int d, int K, const double *P, const double *GK, const double *R,
+                                                 const double *gbar, const int32_t *n_c, double *H) {
+    const int c = blockIdx.y;
+    if (c >= *n_c) return;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)d * d) return;
+    const int i = (int)(e / d), i2 = (int)(e % d);
+    const double *gb = gbar + (size_t)c * d;
+    double h = gb[i] * gb[i2];
+    for (int k = 0; k < K; ++k) {
+        const double r = R[(size_t)c * K + k];
+        if (r == 0.0) continue;
+        const double *gk = GK + ((size_t)c * K + k) * d;
+        h += r * (P[(size_t)k * d * d + e] - gk[i] * gk[i2]);
+    }
+    H[(size_t)c * d * d + e] = h;
+}
+
+// ------------------------------------------------------------------ blocked Cholesky
+__global__ void __launch_bounds__(NB *NB) k_potrf_diag(int d, int kb, double *H, const int32_t *n_c, int32_t *info) {
+    const int c = blockIdx.x;
+    if (c >= *n_c || info[c]) return;
+    double *A = H + (size_t)c * d * d;
+    __shared__ double a[NB][NB + 1];
+    __shared__ int bad;
+    const int tx = threadIdx.x % NB, ty = threadIdx.x / NB;
+    const int o = kb * NB;
+    {
+        const int i = o + ty, j = o + tx;
+        double v;
+        if (i < d && j < d)
+            v = A[(size_t)i * d + j];
+        else
+            v = (ty == tx) ? 1.0 : 0.0;  // identity padding of the ragged last block
+        a[ty][tx] = v;
+    }
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < NB; ++j) {
+        if (threadIdx.x == 0) {
+            const double p = a[j][j];
+            if (!(p > 0.0))
+                bad = 1;
+            else
+                a[j][j] = sqrt(p);
+        }
+        __syncthreads();
+        if (bad) break;
+        if (ty == 0 && tx > j) a[tx][j] = a[tx][j] / a[j][j];
+        __syncthreads();
+        if (tx > j && ty > j && tx >= ty) a[tx][ty] -= a[tx][j] * a[ty][j];
+        __syncthreads();
+    }
+    if (bad) {
+        if (threadIdx.x == 0) info[c] = 1;
+        return;
+    }
+    const int i = o + ty, j = o + tx;
+    if (i < d && j < d && j <= i) A[(size_t)i * d + j] = a[ty][tx];
+}
+
+// Panel: A[ib][kb] <- A[ib][kb] L_kk^{-T}, one thread per panel row.
+__global__ void __launch_bounds__(NB) k_trsm_panel(int d, int kb, double *H, const int32_t *n_c,
+                                                   const int32_t *info) {
+    const int c = blockIdx.y, ib = kb + 1 + blockIdx.x;
+    if (c >= *n_c || info[c]) return;
+    const int nblk = (d + NB - 1) / NB;
+    if (ib >= nblk) return;
+    double *A = H + (size_t)c * d * d;
+    __shared__ double l[NB][NB + 1];
+    const int o = kb * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += NB) {
+        const int i = e / NB, j = e % NB;
+        l[i][j] = (o + i < d && o + j < d) ? A[(size_t)(o + i) * d + o + j] : (i == j ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    const int row = ib * NB + threadIdx.x;
+    if (row >= d) return;
+    double x[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) x[j] = (o + j < d) ? A[(size_t)row * d + o + j] : 0.0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        double s = x[j];
+#pragma unroll
+        for (int q = 0; q < j; ++q) s -= x[q] * l[j][q];
+        x[j] = s / l[j][j];
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (o + j < d) A[(size_t)row * d + o + j] = x[j];
+}
+
+// Trailing update A[ib][jb] -= A[ib][kb] A[jb][kb]^T for kb < jb <= ib.
+__global__ void __launch_bounds__(256) k_syrk_update(int d, int kb, double *H, const int32_t *n_c,
+                                                     const int32_t *info) {
+    const int c = blockIdx.z;
+    if (c >= *n_c || info[c]) return;
+    const int ib = kb + 1 + blockIdx.y, jb = kb + 1 + blockIdx.x;
+    if (jb > ib) return;
+    const int nblk = (d + NB - 1) / NB;
+    if (ib >= nblk) return;
+    double *A = H + (size_t)c * d * d;
+    __shared__ double pa[NB][NB + 1], pb[NB][NB + 1];
+    const int o = kb * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += 256) {
+        const int r = e / NB, q = e % NB;
+        const int ia = ib * NB + r, ja = jb * NB + r, col = o + q;
+        pa[r][q] = (ia < d && col < d) ? A[(size_t)ia * d + col] : 0.0;
+        pb[r][q] = (ja < d && col < d) ? A[(size_t)ja * d + col] : 0.0;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % NB, ty = threadIdx.x / NB;  // ty 0..7
+#pragma unroll
+    for (int rr = 0; rr < NB / 8; ++rr) {
+        const int r = ty + 8 * rr;
+        const int i = ib * NB + r, j = jb * NB + tx;
+        if (i >= d || j >= d || j > i) continue;
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) s += pa[r][q] * pb[tx][q];
+        A[(size_t)i * d + j] -= s;
+    }
+}
+
+// Solve (C C^T) delta = g for each candidate still polishing.
+__global__ void __launch_bounds__(256) k_chol_solve(int d, const double *H, const double *g, const int32_t *n_c,
+                                                    const int32_t *info, const uint8_t *active, double *delta) {
+    const int c = blockIdx.x;
+    if (c >= *n_c || info[c] || !active[c]) return;
+    extern __shared__ double y[];
+    const double *C = H + (size_t)c * d * d;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) y[i] = g[(size_t)c * d + i];
+    __syncthreads();
+    for (int i = 0; i < d; ++i) {  // forward: C y = g
+        if (threadIdx.x == 0) y[i] = y[i] / C[(size_t)i * d + i];
+        __syncthreads();
+        const double yi = y[i];
+        for (int k = i + 1 + threadIdx.x; k < d; k += blockDim.x) y[k] -= C[(size_t)k * d + i] * yi;
+        __syncthreads();
+    }
+    for (int i = d - 1; i >= 0; --i) {  // backward: C^T delta = y
+        if (threadIdx.x == 0) y[i] = y[i] / C[(size_t)i * d + i];
+        __syncthreads();
+        const double yi = y[i];
+        for (int k = threadIdx.x; k < i; k += blockDim.x) y[k] -= C[(size_t)i * d + k] * yi;
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < d; i += blockDim.x) delta[(size_t)c * d + i] = y[i];
+}
+
+// ------------------------------------------------------------------ Newton line search
+// mode 0: start (t = 1, trial = x + delta, searching = active & Cholesky ok)
+// mode 1: decide on the evaluated trial (accept if l_t >= l, else halve)
+__global__ void __launch_bounds__(256) k_newton_ls(int d, int mode, const int32_t *n_c, const int32_t *info,
+                                                   uint8_t *active, uint8_t *searching, int32_t *halvings, double *t,
+                                                   double *XC, double *LC, const double *delta, double *XN,
+                                                   const double *LN) {
+    const int c = blockIdx.x;
+    if (c >= *n_c) return;
+    __shared__ int s_act;
+    if (threadIdx.x == 0) {
+        int act = 0;
+        if (mode == 0) {
+            const int s = active[c] && !info[c];
+            if (!s) active[c] = 0;
+            searching[c] = (uint8_t)s;
+            halvings[c] = 0;
+            t[c] = 1.0;
+            act = s ? 2 : 0;  // 2: write the trial
+        } else if (searching[c]) {
+            if (LN[c] >= LC[c]) {
+                searching[c] = 0;
+                LC[c] = LN[c];
+                act = 1;  // 1: accept
+            } else if (halvings[c] + 1 >= 30) {
+                searching[c] = 0;
+                active[c] = 0;  // no acceptable step: stop polishing this candidate
+            } else {
+                ++halvings[c];
+                t[c] *= 0.5;
+                act = 2;
+            }
+        }
+        s_act = act;
+    }
+    __syncthreads();
+    const int act = s_act;
+    if (act == 1) {
+        for (int i = threadIdx.x; i < d; i += blockDim.x) XC[(size_t)c * d + i] = XN[(size_t)c * d + i];
+    } else if (act == 2) {
+        const double tc = t[c];
+        for (int i = threadIdx.x; i < d; i += blockDim.x)
+            XN[(size_t)c * d + i] = add_rn(XC[(size_t)c * d + i], mul_rn(tc, delta[(size_t)c * d + i]));
+    }
+}
+
+// Halvings 1..kHalvings-1 evaluated as one batch: the first acceptable
+// halving is the one a sequential search would stop at.
+__global__ void __launch_bounds__(256) k_ls_batch_setup(int d, const int32_t *n_c, const uint8_t *searching,
+                                                        const double *XC, const double *delta, double *XN2,
+                                                        int32_t *rows2, int32_t *n_rows2) {
+    const int c = blockIdx.x;
+    if (c >= *n_c || !searching[c]) return;
+    __shared__ int base;
+    if (threadIdx.x == 0) base = atomicAdd(n_rows2, kHalvings - 1);
+    __syncthreads();
+    double t = 1.0;
+    for (int h = 1; h < kHalvings; ++h) {
+        t *= 0.5;
+        const size_t row = (size_t)c * (kHalvings - 1) + (h - 1);
+        for (int i = threadIdx.x; i < d; i += blockDim.x)
+            XN2[row * d + i] = add_rn(XC[(size_t)c * d + i], mul_rn(t, delta[(size_t)c * d + i]));
+        if (threadIdx.x == 0) rows2[base + h - 1] = (int32_t)row;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ls_batch_decide(int d, const int32_t *n_c, uint8_t *searching,
+                                                         uint8_t *active, double *XC, double *LC, const double *XN2,
+                                                         const double *LN2) {
+    const int c = blockIdx.x;
+    if (c >= *n_c || !searching[c]) return;
+    __shared__ int hsel;
+    if (threadIdx.x == 0) {
+        int hs = -1;
+        for (int h = 1; h < kHalvings; ++h)
+            if (LN2[(size_t)c * (kHalvings - 1) + h - 1] >= LC[c]) {
+                hs = h;
+                break;
+            }
+        hsel = hs;
+    }
+    __syncthreads();
+    const int h = hsel;
+    if (h < 0) {
+        if (threadIdx.x == 0) {
+            searching[c] = 0;
+            active[c] = 0;
+        }
+        return;
+    }
+    const size_t row = (size_t)c * (kHalvings - 1) + (h - 1);
+    for (int i = threadIdx.x; i < d; i += blockDim.x) XC[(size_t)c * d + i] = XN2[row * d + i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        LC[c] = LN2[row];
+        searching[c] = 0;
+    }
+}
+
+// ------------------------------------------------------------------ filters and log Z_k
+__global__ void __launch_bounds__(256) k_cand_stats(int d, const double *XC, const double *LC, const double *GC,
+                                                    const double *H, const int32_t *info, const double *lo,
+                                                    const double *hi, double eps_grad, const int32_t *n_c,
+                                                    uint8_t *keep, double *logZk) {
+    const int c = blockIdx.x;
+    if (c >= *n_c) return;
+    __shared__ double s_gm[32], s_ld[32];
+    __shared__ int s_in[32];
+    double gm = 0.0, ld = 0.0;
+    int inside = 1;
+    const bool ok = info[c] == 0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        gm = fmax(gm, fabs(GC[(size_t)c * d + i]));
+        const double x = XC[(size_t)c * d + i];
+        if (!(x >= lo[i] && x <= hi[i])) inside = 0;
+        if (ok) ld += log(H[(size_t)c * d * d + (size_t)i * d + i]);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    gm = warp_max(gm);
+    ld = warp_sum(ld);
+    inside = __all_sync(0xffffffffu, inside);
+    if (lane == 0) {
+        s_gm[wid] = gm;
+        s_ld[wid] = ld;
+        s_in[wid] = inside;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double g = 0.0, l = 0.0;
+        int in = 1;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            g = fmax(g, s_gm[q]);
+            l += s_ld[q];
+            in &= s_in[q];
+        }
+        const double ell = LC[c];
+        keep[c] = (uint8_t)(ok && isfinite(ell) && g <= eps_grad * (1.0 + fabs(ell)) && in);
+        logZk[c] = ok ? (ell + 0.5 * (double)d * SB_LOG_2PI) - l : NAN;
+    }
+}
+
+// Final dedup of the kept candidates, outputs in order of decreasing l, LSE - log V.
+__global__ void __launch_bounds__(1024) k_laplace_final(int d, const double *XC, const double *LC,
+                                                        const double *logZk_c, const int32_t *n_c,
+                                                        const int32_t *reps, const int32_t *n_reps, const double *logV,
+                                                        int cap, double *modes, double *logZk, double *ell_modes,
+                                                        int32_t *n_modes, double *logZ, int32_t *dev_status) {
+    const int nm = *n_reps;
+    for (int t = 0; t < nm && t < cap; ++t) {
+        const int c = reps[t];
+        for (int i = threadIdx.x; i < d; i += blockDim.x) modes[(size_t)t * d + i] = XC[(size_t)c * d + i];
+        if (threadIdx.x == 0) {
+            logZk[t] = logZk_c[c];
+            if (ell_modes) ell_modes[t] = LC[c];
+        }
+    }
+    if (threadIdx.x == 0) {
+        double zmax = -INFINITY;
+        for (int t = 0; t < nm; ++t) zmax = fmax(zmax, logZk_c[reps[t]]);
+        double lz = -INFINITY;
+        if (nm > 0) {
+            double s = 0.0;
+            for (int t = 0; t < nm; ++t) s += exp(logZk_c[reps[t]] - zmax);
+            lz = zmax + log(s) - logV[0];
+        } else {
+            atomicOr(dev_status, SB_DEV_NO_MODES);
+        }
+        *logZ = lz;
+        *n_modes = nm;
+    }
+}
+
+}  // namespace
+
+void launch_dedup(int n, int d, const double *X, const double *ell, const int8_t *status, const uint8_t *keep,
+                  double tau_scale, const double *wmax, int cap, int32_t *reps, int32_t *n_reps, uint8_t *assigned,
+                  cudaStream_t s) {
+    note_launch();
+    k_dedup<<<1, 1024, 0, s>>>(n, d, X, ell, status, keep, tau_scale, wmax, cap, reps, n_reps, assigned);
+}
+
+void launch_gather_rows(int d, int cap, const double *X, const int32_t *idx, const int32_t *n_idx, double *out,
+                        const double *ell, double *ell_out, cudaStream_t s) {
+    note_launch();
+    k_gather_rows<<<cap, 256, 0, s>>>(d, X, idx, n_idx, out, ell, ell_out);
+}
+
+void launch_precision(int d, int K, const double *L, double *P, cudaStream_t s) {
+    dim3 g((d + 63) / 64, (d + 63) / 64, K);
+    note_launch();
+    k_precision<<<g, 256, 0, s>>>(d, L, P);
+}
+
+void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P, const double *Z, const double *R,
+                         const double *gbar, const int32_t *n_c, double *GK, double *H, int32_t *info,
+                         cudaStream_t s) {
+    note_launch();
+    k_comp_grads<<<dim3(cap, K), 256, sizeof(double) * d, s>>>(d, K, L, Z, R, n_c, GK);
+    const int64_t dd = (int64_t)d * d;
+    note_launch();
+    k_hessian<<<dim3((unsigned)((dd + 255) / 256), cap), 256, 0, s>>>(d, K, P, GK, R, gbar, n_c, H);
+    cudaMemsetAsync(info, 0, sizeof(int32_t) * cap, s);
+    const int nblk = (d + NB - 1) / NB;
+    ProfScope prof(PROF_CHOLESKY, s);
+    for (int kb = 0; kb < nblk; ++kb) {
+        note_launch();
+        k_potrf_diag<<<cap, NB * NB, 0, s>>>(d, kb, H, n_c, info);
+        const int rest = nblk - kb - 1;
+        if (rest > 0) {
+            note_launch();
+            k_trsm_panel<<<dim3(rest, cap), NB, 0, s>>>(d, kb, H, n_c, info);
+            note_launch();
+            k_syrk_update<<<dim3(rest, rest, cap), 256, 0, s>>>(d, kb, H, n_c, info);
+        }
+    }
+}
+
+void launch_chol_solve(int d, int cap, const double *H, const double *g, const int32_t *n_c, const int32_t *info,
+                       const uint8_t *active, double *delta, cudaStream_t s) {
+    note_launch();
+    k_chol_solve<<<cap, 256, sizeof(double) * d, s>>>(d, H, g, n_c, info, active, delta);
+}
+
+void launch_newton_ls(int d, int cap, int mode, const int32_t *n_c, const int32_t *info, uint8_t *active,
+                      uint8_t *searching, int32_t *halvings, double *t, double *XC, double *LC, const double *delta,
+                      double *XN, const double *LN, cudaStream_t s) {
+    note_launch();
+    k_newton_ls<<<cap, 256, 0, s>>>(d, mode, n_c, info, active, searching, halvings, t, XC, LC, delta, XN, LN);
+}
+
+void launch_ls_batch_setup(int d, int cap, const int32_t *n_c, const uint8_t *searching, const double *XC,
+                           const double *delta, double *XN2, int32_t *rows2, int32_t *n_rows2, cudaStream_t s) {
+    cudaMemsetAsync(n_rows2, 0, sizeof(int32_t), s);
+    note_launch();
+    k_ls_batch_setup<<<cap, 256, 0, s>>>(d, n_c, searching, XC, delta, XN2, rows2, n_rows2);
+}
+
+void launch_ls_batch_decide(int d, int cap, const int32_t *n_c, uint8_t *searching, uint8_t *active, double *XC,
+                            double *LC, const double *XN2, const double *LN2, cudaStream_t s) {
+    note_launch();
+    k_ls_batch_decide<<<cap, 256, 0, s>>>(d, n_c, searching, active, XC, LC, XN2, LN2);
+}
+
+void launch_cand_stats(int d, int cap, const double *XC, const double *LC, const double *GC, const double *H,
+                       const int32_t *info, const double *lo, const double *hi, double eps_grad, const int32_t *n_c,
+                       uint8_t *keep, double *logZk, cudaStream_t s) {
+    note_launch();
+    k_cand_stats<<<cap, 256, 0, s>>>(d, XC, LC, GC, H, info, lo, hi, eps_grad, n_c, keep, logZk);
+}
+
+void launch_laplace_final(int d, const double *XC, const double *LC, const double *logZk_c, const int32_t *n_c,
+                          const int32_t *reps, const int32_t *n_reps, const double *logV, int cap, double *modes,
+                          double *logZk, double *ell_modes, int32_t *n_modes, double *logZ, int32_t *dev_status,
+                          cudaStream_t s) {
+    note_launch();
+    k_laplace_final<<<1, 1024, 0, s>>>(d, XC, LC, logZk_c, n_c, reps, n_reps, logV, cap, modes, logZk, ell_modes,
+                                       n_modes, logZ, dev_status);
+}
+
+}  // namespace sb

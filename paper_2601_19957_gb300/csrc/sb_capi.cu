@@ -1,0 +1,731 @@
+// sb_capi.cu -- the C ABI of libsb (declared in include/sb.h): argument
+// validation, workspace carving and the host-side orchestration of the
+// discover -> refine -> laplace stages.
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "sb_internal.cuh"
+#include "sb_laplace.cuh"
+#include "sb_lbfgs.cuh"
+#include "sb_tc.cuh"
+
+using namespace sb;
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_prof_on{0};
+std::mutex g_prof_mu;
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+};
+std::vector<ProfRec> g_prof;
+}  // namespace
+void sb::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+sb::ProfScope::ProfScope(int c, cudaStream_t st) : cls(c), s(st), a(nullptr), b(nullptr) {
+    if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        a = b = nullptr;
+        return;
+    }
+    cudaEventRecord(a, s);
+}
+sb::ProfScope::~ProfScope() {
+    if (!a) return;
+    cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.push_back({cls, a, b});
+}
+
+extern "C" void sb_profile_enable(int on) { g_prof_on.store(on ? 1 : 0); }
+
+extern "C" int32_t sb_profile_read(double *ms, int64_t *launches) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (int c = 0; c < PROF_NCLASS; ++c) {
+        if (ms) ms[c] = 0.0;
+        if (launches) launches[c] = 0;
+    }
+    int32_t bad = 0;
+    for (auto &r : g_prof) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            if (ms) ms[r.cls] += t;
+            if (launches) launches[r.cls] += 1;
+        } else {
+            ++bad;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_prof.clear();
+    return bad;
+}
+
+extern "C" int64_t sb_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+extern "C" const char *sb_status_string(sb_status s) {
+    switch (s) {
+        case SB_OK: return "SB_OK";
+        case SB_ERR_INVALID_ARG: return "SB_ERR_INVALID_ARG";
+        case SB_ERR_CUDA: return "SB_ERR_CUDA";
+        case SB_ERR_WORKSPACE: return "SB_ERR_WORKSPACE";
+        case SB_ERR_NONFINITE: return "SB_ERR_NONFINITE";
+        case SB_ERR_NO_MODES: return "SB_ERR_NO_MODES";
+        case SB_ERR_TIMEOUT: return "SB_ERR_TIMEOUT";
+        case SB_ERR_UNSUPPORTED: return "SB_ERR_UNSUPPORTED";
+    }
+    return "SB_ERR_UNKNOWN";
+}
+
+namespace {
+
+constexpr int kRoundsPerPoll = 8;  // L-BFGS rounds between host reads of the active count
+
+inline int njt(int d) { return (d + 63) / 64; }
+
+sb_status check_problem(const sb_problem *p) {
+    if (!p || !p->log_w || !p->mu || !p->L || !p->lo || !p->hi) return SB_ERR_INVALID_ARG;
+    if (p->d < 1 || p->K < 1) return SB_ERR_INVALID_ARG;
+    if (p->d > kMaxD || p->K > kMaxK) return SB_ERR_UNSUPPORTED;
+    return SB_OK;
+}
+
+sb_status check_config(const sb_config *c) {
+    if (!c) return SB_ERR_INVALID_ARG;
+    if (c->n_rays < 1 || c->n_steps < 1 || c->n_steps > 1024 || c->n_starts < 1) return SB_ERR_INVALID_ARG;
+    const int64_t total = (int64_t)c->n_rays * c->n_steps;
+    if (total > 0x7fffffffLL || c->n_starts > total) return SB_ERR_INVALID_ARG;
+    if (c->m < 1 || c->m > kMaxM || c->max_iter < 0 || c->max_backtracks < 0 || c->max_backtracks > 10000)
+        return SB_ERR_INVALID_ARG;
+    if (c->newton_steps < 0 || c->newton_steps > 64 || c->cand_cap < 1 || c->cand_cap > 4096)
+        return SB_ERR_INVALID_ARG;
+    if (!(c->gtol >= 0) || !(c->armijo_c1 > 0 && c->armijo_c1 < 1) || !(c->backtrack > 0 && c->backtrack < 1))
+        return SB_ERR_INVALID_ARG;
+    if (!(c->dedup_coarse >= 0) || !(c->dedup_tol >= 0) || !(c->eps_grad >= 0)) return SB_ERR_INVALID_ARG;
+    if (c->prec < SB_PREC_FP64 || c->prec > SB_PREC_BF16 || c->reserved != 0) return SB_ERR_INVALID_ARG;
+    return SB_OK;
+}
+
+// ------------------------------------------------------------------ workspace layout
+struct SetupWs {
+    WsHeader *hdr;
+    double *a, *c, *half, *logV, *wmax;
+};
+
+struct DiscoverWs {
+    double *u, *texit, *ell_all, *qpart;
+    int chunk;
+    SelectWs sel;
+    TcWs tc;  // tensor-core scratch (mixed precision)
+};
+
+template <typename T>
+struct RefineWs {
+    LbfgsArgs<T> lb;
+    int64_t *n_evals;
+    double *qpart, *Z, *R;  // FP64 evaluation
+    TcWs tc;                // mixed-precision evaluation
+};
+
+struct LaplaceWs {
+    double *P, *XC, *LC, *GC, *Z, *R, *qpart, *GK, *H, *delta, *XN, *LN, *XN2, *LN2, *qpart2, *logZk_c, *t;
+    int32_t *reps, *n_reps, *info, *halvings, *rows2, *n_rows2, *reps2, *n_reps2;
+    uint8_t *assigned, *active, *searching, *keep;
+};
+
+struct EvidenceWs {
+    double *starts, *ell_starts, *x_out, *ell_out;
+    int8_t *status;
+};
+
+struct Layout {
+    SetupWs su;
+    DiscoverWs di;
+    RefineWs<double> r64;
+    RefineWs<float> r32;
+    LaplaceWs la;
+    EvidenceWs ev;
+    size_t bytes;
+};
+
+int discover_chunk(int d, int K, int64_t total) {
+    const int64_t per = (int64_t)K * njt(d);
+    int64_t b = ((int64_t)8 << 20) / per;  // qpart <= 64 MB
+    if (b < 64) b = 64;
+    if (b > total) b = total;
+    return (int)b;
+}
+
+template <typename T>
+void carve_refine(Carver &cv, RefineWs<T> &r, int n, int d, int K, int m, bool fp64_eval, int prec) {
+    auto &a = r.lb;
+    a.X = cv.take<T>((size_t)n * d);
+    a.G = cv.take<T>((size_t)n * d);
+    a.P = cv.take<T>((size_t)n * d);
+    a.XT = cv.take<T>((size_t)n * d);
+    a.GT = cv.take<T>((size_t)n * d);
+    a.FT = cv.take<T>((size_t)n);
+    a.S = cv.take<T>((size_t)n * m * d);
+    a.Y = cv.take<T>((size_t)n * m * d);
+    a.rho = cv.take<T>((size_t)n * m);
+    a.st = cv.take<WalkerState<T>>((size_t)n);
+    a.act = cv.take<int32_t>((size_t)n);
+    a.n_act = cv.take<int32_t>(1);
+    r.n_evals = cv.take<int64_t>(1);
+    if (fp64_eval) {
+        r.qpart = cv.take<double>(lik_f64_qpart_elems(d, K, n));
+        r.Z = cv.take<double>((size_t)n * K * d);
+        r.R = cv.take<double>((size_t)n * K);
+    } else {
+        carve_tc(cv, r.tc, n, d, K, prec);
+    }
+}
+
+// One layout serves every entry point: the stages' regions never overlap.
+Layout layout(void *base, const sb_problem *p, const sb_config *c) {
+    Layout L{};
+    Carver cv(base);
+    const int d = p->d, K = p->K;
+    L.su.hdr = cv.take<WsHeader>(1);
+    L.su.a = cv.take<double>(K);
+    L.su.c = cv.take<double>(d);
+    L.su.half = cv.take<double>(d);
+    L.su.logV = cv.take<double>(1);
+    L.su.wmax = cv.take<double>(1);
+
+    const int64_t total = (int64_t)c->n_rays * c->n_steps;
+    const bool fp64 = c->prec == SB_PREC_FP64;
+    L.di.u = cv.take<double>((size_t)c->n_rays * d);
+    L.di.texit = cv.take<double>(c->n_rays);
+    L.di.ell_all = cv.take<double>(total);
+    L.di.chunk = discover_chunk(d, K, total);
+    if (fp64)
+        L.di.qpart = cv.take<double>(lik_f64_qpart_elems(d, K, L.di.chunk));
+    else
+        carve_tc(cv, L.di.tc, tc_ray_chunk(d, K, total), d, K, c->prec);
+    L.di.sel.bucket = cv.take<int32_t>(total);
+    L.di.sel.hist = cv.take<uint32_t>(c->n_steps * 2 > 256 ? c->n_steps * 2 : 256);
+    L.di.sel.state = cv.take<uint64_t>(8);
+    L.di.sel.blockcnt = cv.take<int32_t>(select_blocks(total));
+    L.di.sel.idx = cv.take<int64_t>(c->n_starts);
+
+    const int n = c->n_starts;
+    if (fp64)
+        carve_refine(cv, L.r64, n, d, K, c->m, true, c->prec);
+    else
+        carve_refine(cv, L.r32, n, d, K, c->m, false, c->prec);
+
+    const int cap = c->cand_cap;
+    const int nJT = njt(d);
+    const int H2 = kHalvings - 1;
+    auto &la = L.la;
+    la.P = cv.take<double>((size_t)K * d * d);
+    la.reps = cv.take<int32_t>(cap);
+    la.n_reps = cv.take<int32_t>(1);
+    la.assigned = cv.take<uint8_t>(n > cap ? n : cap);
+    la.XC = cv.take<double>((size_t)cap * d);
+    la.LC = cv.take<double>(cap);
+    la.GC = cv.take<double>((size_t)cap * d);
+    la.Z = cv.take<double>((size_t)cap * K * d);
+    la.R = cv.take<double>((size_t)cap * K);
+    la.qpart = cv.take<double>((size_t)cap * K * nJT);
+    la.GK = cv.take<double>((size_t)cap * K * d);
+    la.H = cv.take<double>((size_t)cap * d * d);
+    la.info = cv.take<int32_t>(cap);
+    la.active = cv.take<uint8_t>(cap);
+    la.searching = cv.take<uint8_t>(cap);
+    la.halvings = cv.take<int32_t>(cap);
+    la.t = cv.take<double>(cap);
+    la.delta = cv.take<double>((size_t)cap * d);
+    la.XN = cv.take<double>((size_t)cap * d);
+    la.LN = cv.take<double>(cap);
+    la.XN2 = cv.take<double>((size_t)cap * H2 * d);
+    la.LN2 = cv.take<double>((size_t)cap * H2);
+    la.qpart2 = cv.take<double>((size_t)cap * H2 * K * nJT);
+    la.rows2 = cv.take<int32_t>((size_t)cap * H2);
+    la.n_rows2 = cv.take<int32_t>(1);
+    la.keep = cv.take<uint8_t>(cap);
+    la.logZk_c = cv.take<double>(cap);
+    la.reps2 = cv.take<int32_t>(cap);
+    la.n_reps2 = cv.take<int32_t>(1);
+
+    L.ev.starts = cv.take<double>((size_t)n * d);
+    L.ev.ell_starts = cv.take<double>(n);
+    L.ev.x_out = cv.take<double>((size_t)n * d);
+    L.ev.ell_out = cv.take<double>(n);
+    L.ev.status = cv.take<int8_t>(n);
+    L.bytes = cv.bytes();
+    return L;
+}
+
+ProbView make_view(const sb_problem *p, const Layout &L) {
+    ProbView v;
+    v.d = p->d;
+    v.K = p->K;
+    v.log_w = p->log_w;
+    v.mu = p->mu;
+    v.L = p->L;
+    v.lo = p->lo;
+    v.hi = p->hi;
+    v.a = L.su.a;
+    v.c = L.su.c;
+    v.half = L.su.half;
+    v.logV = L.su.logV;
+    v.wmax = L.su.wmax;
+    v.status = &L.su.hdr->status;
+    return v;
+}
+
+// ------------------------------------------------------------------ FP64 evaluation helpers
+LikF64Args f64_args(const ProbView &pv) {
+    LikF64Args a{};
+    a.d = pv.d;
+    a.K = pv.K;
+    a.mu = pv.mu;
+    a.L = pv.L;
+    a.a = pv.a;
+    a.c = pv.c;
+    a.ell_sign = 1.0;
+    a.grad_sign = -1.0;
+    return a;
+}
+
+// ------------------------------------------------------------------ stages
+sb_status run_discover(const ProbView &pv, const sb_config *c, const Layout &L, double *starts, double *ell,
+                       cudaStream_t s) {
+    const int d = pv.d;
+    const int64_t total = (int64_t)c->n_rays * c->n_steps;
+    launch_ray_dirs(d, c->n_rays, c->seed, pv, L.di.u, L.di.texit, s);
+    if (c->prec == SB_PREC_FP64) {
+        for (int64_t f0 = 0; f0 < total; f0 += L.di.chunk) {
+            const int rows = (int)((total - f0) < L.di.chunk ? (total - f0) : L.di.chunk);
+            LikF64Args a = f64_args(pv);
+            a.u = L.di.u;
+            a.texit = L.di.texit;
+            a.n_steps = c->n_steps;
+            a.flat0 = f0;
+            a.n_rows = rows;
+            a.qpart = L.di.qpart;
+            a.ell = L.di.ell_all + f0;
+            a.out_by_walker = 0;
+            launch_lik_f64_rays(a, s);
+        }
+    } else {
+        const sb_status st = tc_ray_loglik(pv, c, L.di.tc, L.di.u, L.di.texit, L.di.ell_all, s);
+        if (st != SB_OK) return st;
+    }
+    launch_select_starts(L.di.ell_all, c->n_rays, c->n_steps, c->n_starts, L.di.sel, s);
+    launch_gather_starts(pv, L.di.u, L.di.texit, c->n_steps, L.di.sel.idx, L.di.ell_all, c->n_starts, starts, ell, s);
+    SB_CUDA_TRY(cudaGetLastError());
+    return SB_OK;
+}
+
+template <typename T>
+void eval_round(const ProbView &pv, const sb_config *c, const RefineWs<T> &r, int n, cudaStream_t s);
+
+template <>
+void eval_round<double>(const ProbView &pv, const sb_config *c, const RefineWs<double> &r, int n, cudaStream_t s) {
+    (void)c;
+    LikF64Args a = f64_args(pv);
+    a.X = r.lb.XT;
+    a.rows = r.lb.act;
+    a.n_rows_dev = r.lb.n_act;
+    a.n_rows = n;
+    a.qpart = r.qpart;
+    a.Z = r.Z;
+    a.R = r.R;
+    a.ell = r.lb.FT;
+    a.ell_sign = -1.0;  // f = -l
+    a.G = r.lb.GT;
+    a.grad_sign = 1.0;  // grad f = -grad l
+    a.out_by_walker = 1;
+    launch_lik_f64_points(a, true, s);
+}
+
+template <>
+void eval_round<float>(const ProbView &pv, const sb_config *c, const RefineWs<float> &r, int n, cudaStream_t s) {
+    tc_eval_walkers(pv, c, r.tc, r.lb.XT, r.lb.act, r.lb.n_act, n, r.lb.FT, r.lb.GT, s);
+}
+
+template <typename T>
+sb_status run_refine(const ProbView &pv, const sb_config *c, const RefineWs<T> &r, const double *starts, int n,
+                     double *x_out, double *ell_out, int8_t *status_out, int32_t *iters_out, int64_t *n_evals,
+                     cudaStream_t s) {
+    LbfgsArgs<T> a = r.lb;
+    a.d = pv.d;
+    a.m = c->m;
+    a.max_iter = c->max_iter;
+    a.max_backtracks = c->max_backtracks;
+    a.c1 = (T)c->armijo_c1;
+    a.backtrack = (T)c->backtrack;
+    a.gtol = (T)c->gtol;
+    RefineWs<T> rr = r;
+    rr.lb = a;
+    int64_t *ev = n_evals ? n_evals : r.n_evals;
+    launch_lbfgs_init<T>(n, pv.d, starts, a, ev, s);
+    // every accepted step takes at most 2 (max_backtracks + 1) rounds
+    const int64_t cap_rounds = 2 + (int64_t)(c->max_iter + 1) * 2 * (c->max_backtracks + 2);
+    int64_t round = 0;
+    while (true) {
+        for (int b = 0; b < kRoundsPerPoll; ++b) {
+            eval_round<T>(pv, c, rr, n, s);
+            launch_lbfgs_step<T>(a, n, s);
+            launch_lbfgs_compact<T>(a, ev, s);
+        }
+        round += kRoundsPerPoll;
+        int32_t h_act = 0;
+        SB_CUDA_TRY(cudaMemcpyAsync(&h_act, a.n_act, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SB_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h_act == 0 || round >= cap_rounds) break;
+    }
+    launch_lbfgs_finish<T>(n, pv.d, a, x_out, ell_out, status_out, iters_out, pv.status, s);
+    SB_CUDA_TRY(cudaGetLastError());
+    return SB_OK;
+}
+
+// l and grad l (FP64) at the rows of X listed in rows[0..*n_rows) (or 0..n), outputs by row id.
+void f64_points(const ProbView &pv, const double *X, const int32_t *rows, const int32_t *n_rows_dev, int n_rows,
+                double *qpart, double *Z, double *R, double *ell, double *G, cudaStream_t s) {
+    LikF64Args a = f64_args(pv);
+    a.X = X;
+    a.rows = rows;
+    a.n_rows_dev = n_rows_dev;
+    a.n_rows = n_rows;
+    a.qpart = qpart;
+    a.Z = Z;
+    a.R = R;
+    a.ell = ell;
+    a.G = G;
+    a.out_by_walker = 1;
+    launch_lik_f64_points(a, G != nullptr, s);
+}
+
+sb_status run_laplace(const ProbView &pv, const sb_config *c, const Layout &L, const double *x, const double *ell,
+                      const int8_t *status, int n, double *modes, double *logZk, double *ell_modes, int cap_out,
+                      int32_t *n_modes, double *logZ, cudaStream_t s) {
+    const int d = pv.d, K = pv.K, cap = c->cand_cap;
+    const auto &la = L.la;
+    launch_precision(d, K, pv.L, la.P, s);
+    launch_dedup(n, d, x, ell, status, nullptr, c->dedup_coarse, pv.wmax, cap, la.reps, la.n_reps, la.assigned, s);
+    launch_gather_rows(d, cap, x, la.reps, la.n_reps, la.XC, ell, la.LC, s);
+    SB_CUDA_TRY(cudaMemsetAsync(la.active, 1, cap, s));
+    // l, grad l, H and its Cholesky factor at every candidate
+    auto eval_full = [&]() {
+        f64_points(pv, la.XC, nullptr, la.n_reps, cap, la.qpart, la.Z, la.R, la.LC, la.GC, s);
+        launch_hessian_chol(d, K, cap, pv.L, la.P, la.Z, la.R, la.GC, la.n_reps, la.GK, la.H, la.info, s);
+    };
+    eval_full();
+    for (int step = 0; step < c->newton_steps; ++step) {
+        launch_chol_solve(d, cap, la.H, la.GC, la.n_reps, la.info, la.active, la.delta, s);
+        launch_newton_ls(d, cap, 0, la.n_reps, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
+                         la.delta, la.XN, la.LN, s);
+        f64_points(pv, la.XN, nullptr, la.n_reps, cap, la.qpart, nullptr, nullptr, la.LN, nullptr, s);
+        launch_newton_ls(d, cap, 1, la.n_reps, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
+                         la.delta, la.XN, la.LN, s);
+        launch_ls_batch_setup(d, cap, la.n_reps, la.searching, la.XC, la.delta, la.XN2, la.rows2, la.n_rows2, s);
+        f64_points(pv, la.XN2, la.rows2, la.n_rows2, cap * (kHalvings - 1), la.qpart2, nullptr, nullptr, la.LN2,
+                   nullptr, s);
+        launch_ls_batch_decide(d, cap, la.n_reps, la.searching, la.active, la.XC, la.LC, la.XN2, la.LN2, s);
+        eval_full();
+    }
+    SB_CUDA_TRY(cudaMemsetAsync(la.keep, 0, cap, s));
+    launch_cand_stats(d, cap, la.XC, la.LC, la.GC, la.H, la.info, pv.lo, pv.hi, c->eps_grad, la.n_reps, la.keep,
+                      la.logZk_c, s);
+    launch_dedup(cap, d, la.XC, la.LC, nullptr, la.keep, c->dedup_tol, pv.wmax, cap, la.reps2, la.n_reps2,
+                 la.assigned, s);
+    launch_laplace_final(d, la.XC, la.LC, la.logZk_c, la.n_reps, la.reps2, la.n_reps2, pv.logV, cap_out, modes, logZk,
+                         ell_modes, n_modes, logZ, pv.status, s);
+    SB_CUDA_TRY(cudaGetLastError());
+    return SB_OK;
+}
+
+struct Prelude {
+    Layout L;
+    ProbView pv;
+    cudaStream_t s;
+};
+
+sb_status prelude(const sb_problem *p, const sb_config *c, void *ws, size_t ws_bytes, void *stream, Prelude &out) {
+    sb_status st = check_problem(p);
+    if (st != SB_OK) return st;
+    st = check_config(c);
+    if (st != SB_OK) return st;
+    if (!ws) return SB_ERR_INVALID_ARG;
+    if (c->prec != SB_PREC_FP64 && !tc_available(c->prec)) return SB_ERR_UNSUPPORTED;
+    Layout L = layout(ws, p, c);
+    if (ws_bytes < L.bytes) return SB_ERR_WORKSPACE;
+    out.L = L;
+    out.pv = make_view(p, L);
+    out.s = static_cast<cudaStream_t>(stream);
+    SB_CUDA_TRY(cudaMemsetAsync(L.su.hdr, 0, sizeof(WsHeader), out.s));
+    launch_setup(out.pv, out.s);
+    if (c->prec != SB_PREC_FP64) {
+        // one converted copy of L_k, mu, c serves discover and refine
+        st = tc_prepare(out.pv, out.L.di.tc, out.s);
+        if (st != SB_OK) return st;
+        for (int i = 0; i < 4; ++i) out.L.r32.tc.p[i] = out.L.di.tc.p[i];
+        out.L.r32.tc.mapT = out.L.di.tc.mapT;
+        out.L.r32.tc.mapB = out.L.di.tc.mapB;
+    }
+    SB_CUDA_TRY(cudaGetLastError());
+    return SB_OK;
+}
+
+}  // namespace
+
+extern "C" size_t sb_workspace_bytes(const sb_problem *p, const sb_config *c) {
+    if (check_problem(p) != SB_OK || check_config(c) != SB_OK) return 0;
+    return layout(nullptr, p, c).bytes;
+}
+
+extern "C" sb_status sb_discover(const sb_problem *p, const sb_config *c, double *starts, double *ell, void *ws,
+                                 size_t ws_bytes, void *stream) {
+    if (!starts || !ell) return SB_ERR_INVALID_ARG;
+    Prelude P;
+    sb_status st = prelude(p, c, ws, ws_bytes, stream, P);
+    if (st != SB_OK) return st;
+    return run_discover(P.pv, c, P.L, starts, ell, P.s);
+}
+
+extern "C" sb_status sb_refine(const sb_problem *p, const sb_config *c, const double *starts, int32_t n,
+                               double *x_out, double *ell_out, int8_t *status_out, int32_t *iters_out,
+                               int64_t *n_evals, void *ws, size_t ws_bytes, void *stream) {
+    if (!starts || !x_out || !ell_out || !status_out) return SB_ERR_INVALID_ARG;
+    if (!c || n < 1 || n > c->n_starts) return SB_ERR_INVALID_ARG;
+    Prelude P;
+    sb_status st = prelude(p, c, ws, ws_bytes, stream, P);
+    if (st != SB_OK) return st;
+    if (c->prec == SB_PREC_FP64)
+        return run_refine<double>(P.pv, c, P.L.r64, starts, n, x_out, ell_out, status_out, iters_out, n_evals, P.s);
+    return run_refine<float>(P.pv, c, P.L.r32, starts, n, x_out, ell_out, status_out, iters_out, n_evals, P.s);
+}
+
+extern "C" sb_status sb_laplace(const sb_problem *p, const sb_config *c, const double *x, const double *ell,
+                                const int8_t *status, int32_t n, double *modes, double *logZk, double *ell_modes,
+                                int32_t cap, int32_t *n_modes, double *logZ, void *ws, size_t ws_bytes,
+                                void *stream) {
+    if (!x || !ell || !modes || !logZk || !n_modes || !logZ || cap < 1) return SB_ERR_INVALID_ARG;
+    if (!c || n < 1 || n > (c->n_starts > c->cand_cap ? c->n_starts : c->cand_cap)) return SB_ERR_INVALID_ARG;
+    Prelude P;
+    sb_status st = prelude(p, c, ws, ws_bytes, stream, P);
+    if (st != SB_OK) return st;
+    return run_laplace(P.pv, c, P.L, x, ell, status, n, modes, logZk, ell_modes, cap, n_modes, logZ, P.s);
+}
+
+extern "C" sb_status sb_evidence(const sb_problem *p, const sb_config *c, double *logZ, double *modes,
+                                 double *logZk, int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes,
+                                 void *stream) {
+    if (!logZ || !modes || !logZk || !n_modes || cap < 1) return SB_ERR_INVALID_ARG;
+    Prelude P;
+    sb_status st = prelude(p, c, ws, ws_bytes, stream, P);
+    if (st != SB_OK) return st;
+    const auto &ev = P.L.ev;
+    st = run_discover(P.pv, c, P.L, ev.starts, ev.ell_starts, P.s);
+    if (st != SB_OK) return st;
+    if (c->prec == SB_PREC_FP64)
+        st = run_refine<double>(P.pv, c, P.L.r64, ev.starts, c->n_starts, ev.x_out, ev.ell_out, ev.status, nullptr,
+                                nullptr, P.s);
+    else
+        st = run_refine<float>(P.pv, c, P.L.r32, ev.starts, c->n_starts, ev.x_out, ev.ell_out, ev.status, nullptr,
+                               nullptr, P.s);
+    if (st != SB_OK) return st;
+    return run_laplace(P.pv, c, P.L, ev.x_out, ev.ell_out, ev.status, c->n_starts, modes, logZk, nullptr, cap,
+                       n_modes, logZ, P.s);
+}
+
+extern "C" sb_status sb_check(void *ws, size_t ws_bytes, void *stream) {
+    if (!ws || ws_bytes < sizeof(WsHeader)) return SB_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t word = 0;
+    SB_CUDA_TRY(cudaMemcpyAsync(&word, ws, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SB_CUDA_TRY(cudaStreamSynchronize(s));
+    SB_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(int32_t), s));
+    if (word & SB_DEV_NONFINITE) return SB_ERR_NONFINITE;
+    if (word & SB_DEV_INVALID) return SB_ERR_INVALID_ARG;
+    if (word & SB_DEV_TIMEOUT) return SB_ERR_TIMEOUT;
+    if (word & SB_DEV_NO_MODES) return SB_ERR_NO_MODES;
+    return SB_OK;
+}
+
+// ------------------------------------------------------------------ host-buffer entry point
+namespace {
+struct HostLayout {
+    double *log_w, *mu, *L, *lo, *hi, *logZ, *modes, *logZk;
+    int32_t *n_modes;
+    void *inner;
+    size_t inner_bytes, bytes;
+};
+
+HostLayout host_layout(void *base, const sb_problem *p, const sb_config *c, int cap) {
+    HostLayout h{};
+    Carver cv(base);
+    const int d = p->d, K = p->K;
+    h.log_w = cv.take<double>(K);
+    h.mu = cv.take<double>((size_t)K * d);
+    h.L = cv.take<double>((size_t)K * d * d);
+    h.lo = cv.take<double>(d);
+    h.hi = cv.take<double>(d);
+    h.logZ = cv.take<double>(1);
+    h.n_modes = cv.take<int32_t>(1);
+    h.modes = cv.take<double>((size_t)cap * d);
+    h.logZk = cv.take<double>(cap);
+    sb_problem tmp = *p;
+    h.inner_bytes = layout(nullptr, &tmp, c).bytes;
+    h.inner = cv.take<char>(h.inner_bytes);
+    h.bytes = cv.bytes();
+    return h;
+}
+}  // namespace
+
+extern "C" size_t sb_evidence_host_workspace_bytes(const sb_problem *hp, const sb_config *c) {
+    if (check_problem(hp) != SB_OK || check_config(c) != SB_OK) return 0;
+    return host_layout(nullptr, hp, c, c->cand_cap).bytes;
+}
+
+extern "C" sb_status sb_evidence_host(const sb_problem *hp, const sb_config *c, double *logZ, double *modes,
+                                      double *logZk, int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes,
+                                      void *stream) {
+    sb_status st = check_problem(hp);
+    if (st != SB_OK) return st;
+    st = check_config(c);
+    if (st != SB_OK) return st;
+    if (!logZ || !n_modes || !ws || cap < 1) return SB_ERR_INVALID_ARG;
+    const int ccap = c->cand_cap;
+    HostLayout h = host_layout(ws, hp, c, ccap);
+    if (ws_bytes < h.bytes) return SB_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int d = hp->d, K = hp->K;
+    SB_CUDA_TRY(cudaMemcpyAsync(h.log_w, hp->log_w, sizeof(double) * K, cudaMemcpyHostToDevice, s));
+    SB_CUDA_TRY(cudaMemcpyAsync(h.mu, hp->mu, sizeof(double) * K * d, cudaMemcpyHostToDevice, s));
+    SB_CUDA_TRY(cudaMemcpyAsync(h.L, hp->L, sizeof(double) * (size_t)K * d * d, cudaMemcpyHostToDevice, s));
+    SB_CUDA_TRY(cudaMemcpyAsync(h.lo, hp->lo, sizeof(double) * d, cudaMemcpyHostToDevice, s));
+    SB_CUDA_TRY(cudaMemcpyAsync(h.hi, hp->hi, sizeof(double) * d, cudaMemcpyHostToDevice, s));
+    sb_problem dp{d, K, h.log_w, h.mu, h.L, h.lo, h.hi};
+    st = sb_evidence(&dp, c, h.logZ, h.modes, h.logZk, ccap, h.n_modes, h.inner, h.inner_bytes, stream);
+    if (st != SB_OK) return st;
+    SB_CUDA_TRY(cudaMemcpyAsync(logZ, h.logZ, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SB_CUDA_TRY(cudaMemcpyAsync(n_modes, h.n_modes, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SB_CUDA_TRY(cudaStreamSynchronize(s));
+    const int nm = *n_modes < cap ? *n_modes : cap;
+    const int nc = nm < ccap ? nm : ccap;
+    if (modes && nc > 0)
+        SB_CUDA_TRY(cudaMemcpyAsync(modes, h.modes, sizeof(double) * (size_t)nc * d, cudaMemcpyDeviceToHost, s));
+    if (logZk && nc > 0) SB_CUDA_TRY(cudaMemcpyAsync(logZk, h.logZk, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    SB_CUDA_TRY(cudaStreamSynchronize(s));
+    return sb_check(h.inner, h.inner_bytes, stream);
+}
+
+// ------------------------------------------------------------------ batched log-likelihood
+extern "C" size_t sb_loglik_workspace_bytes(const sb_problem *p, int32_t prec, int32_t n) {
+    if (check_problem(p) != SB_OK || n < 1) return 0;
+    Carver cv(nullptr);
+    cv.take<WsHeader>(1);
+    cv.take<double>(p->K);
+    if (prec == SB_PREC_FP64) {
+        cv.take<double>(lik_f64_qpart_elems(p->d, p->K, n));
+        cv.take<double>((size_t)n * p->K * p->d);
+        cv.take<double>((size_t)n * p->K);
+    } else if (prec == SB_PREC_TF32 || prec == SB_PREC_BF16) {
+        TcWs t;
+        carve_tc(cv, t, n, p->d, p->K, prec);
+        cv.take<float>((size_t)n);
+        cv.take<float>((size_t)n * p->d);
+        cv.take<double>(2 * (size_t)p->d + 3);
+    } else {
+        return 0;
+    }
+    return cv.bytes();
+}
+
+extern "C" sb_status sb_loglik(const sb_problem *p, int32_t prec, const double *x, int32_t n, double *ell,
+                               double *grad, void *ws, size_t ws_bytes, void *stream) {
+    sb_status st = check_problem(p);
+    if (st != SB_OK) return st;
+    if (!x || !ell || !ws || n < 1) return SB_ERR_INVALID_ARG;
+    if (prec < SB_PREC_FP64 || prec > SB_PREC_BF16) return SB_ERR_INVALID_ARG;
+    if (prec != SB_PREC_FP64 && !tc_available(prec)) return SB_ERR_UNSUPPORTED;
+    if (ws_bytes < sb_loglik_workspace_bytes(p, prec, n)) return SB_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Carver cv(ws);
+    WsHeader *hdr = cv.take<WsHeader>(1);
+    double *a = cv.take<double>(p->K);
+    SB_CUDA_TRY(cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s));
+    ProbView pv{};
+    pv.d = p->d;
+    pv.K = p->K;
+    pv.log_w = p->log_w;
+    pv.mu = p->mu;
+    pv.L = p->L;
+    pv.lo = p->lo;
+    pv.hi = p->hi;
+    pv.a = a;
+    pv.status = &hdr->status;
+    if (prec == SB_PREC_FP64) {
+        double *qpart = cv.take<double>(lik_f64_qpart_elems(p->d, p->K, n));
+        double *Z = cv.take<double>((size_t)n * p->K * p->d);
+        double *R = cv.take<double>((size_t)n * p->K);
+        // setup needs c/half/logV/wmax only for box work; give it scratch inside Z (overwritten later)
+        pv.c = Z;
+        pv.half = Z + p->d;
+        pv.logV = Z + 2 * p->d;
+        pv.wmax = Z + 2 * p->d + 1;
+        launch_setup(pv, s);
+        LikF64Args la = f64_args(pv);
+        la.X = x;
+        la.n_rows = n;
+        la.qpart = qpart;
+        la.Z = Z;
+        la.R = R;
+        la.ell = ell;
+        la.G = grad;
+        la.out_by_walker = 0;
+        launch_lik_f64_points(la, grad != nullptr, s);
+    } else {
+        TcWs t;
+        carve_tc(cv, t, n, p->d, p->K, prec);
+        float *f = cv.take<float>((size_t)n);
+        float *g = cv.take<float>((size_t)n * p->d);
+        double *box = cv.take<double>(2 * (size_t)p->d + 3);
+        pv.c = box;
+        pv.half = box + p->d;
+        pv.logV = box + 2 * p->d;
+        pv.wmax = box + 2 * p->d + 1;
+        launch_setup(pv, s);
+        sb_config c{};
+        c.prec = prec;
+        st = tc_prepare(pv, t, s);
+        if (st != SB_OK) return st;
+        st = tc_loglik_points(pv, &c, t, x, n, f, grad ? g : nullptr, ell, grad, s);
+        if (st != SB_OK) return st;
+    }
+    SB_CUDA_TRY(cudaGetLastError());
+    return SB_OK;
+}
+
+extern "C" sb_status sb_evidence_stats(const sb_problem *p, const sb_config *c, void *ws, size_t ws_bytes,
+                                       int64_t *out, void *stream) {
+    sb_status st = check_problem(p);
+    if (st != SB_OK) return st;
+    st = check_config(c);
+    if (st != SB_OK) return st;
+    if (!ws || !out) return SB_ERR_INVALID_ARG;
+    const Layout L = layout(ws, p, c);
+    if (ws_bytes < L.bytes) return SB_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int64_t ev = 0;
+    int32_t nc = 0, nm = 0;
+    const int64_t *evp = c->prec == SB_PREC_FP64 ? L.r64.n_evals : L.r32.n_evals;
+    SB_CUDA_TRY(cudaMemcpyAsync(&ev, evp, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SB_CUDA_TRY(cudaMemcpyAsync(&nc, L.la.n_reps, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SB_CUDA_TRY(cudaMemcpyAsync(&nm, L.la.n_reps2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SB_CUDA_TRY(cudaStreamSynchronize(s));
+    out[0] = (int64_t)c->n_rays * c->n_steps;
+    out[1] = ev;
+    out[2] = nc;
+    out[3] = nm;
+    return SB_OK;
+}

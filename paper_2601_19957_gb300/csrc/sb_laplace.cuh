@@ -1,0 +1,36 @@
+// sb_laplace.cuh -- launch interface of the FP64 Laplace-stage kernels.
+#pragma once
+#include "sb_internal.cuh"
+
+namespace sb {
+
+constexpr int kHalvings = 30;  // Newton step halvings (t = 1, 1/2, ..., 2^-29)
+
+void launch_dedup(int n, int d, const double *X, const double *ell, const int8_t *status, const uint8_t *keep,
+                  double tau_scale, const double *wmax, int cap, int32_t *reps, int32_t *n_reps, uint8_t *assigned,
+                  cudaStream_t s);
+void launch_gather_rows(int d, int cap, const double *X, const int32_t *idx, const int32_t *n_idx, double *out,
+                        const double *ell, double *ell_out, cudaStream_t s);
+void launch_precision(int d, int K, const double *L, double *P, cudaStream_t s);
+void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P, const double *Z, const double *R,
+                         const double *gbar, const int32_t *n_c, double *GK, double *H, int32_t *info,
+                         cudaStream_t s);
+void launch_chol_solve(int d, int cap, const double *H, const double *g, const int32_t *n_c, const int32_t *info,
+                       const uint8_t *active, double *delta, cudaStream_t s);
+void launch_newton_ls(int d, int cap, int mode, const int32_t *n_c, const int32_t *info, uint8_t *active,
+                      uint8_t *searching, int32_t *halvings, double *t, double *XC, double *LC, const double *delta,
+                      double *XN, const double *LN, cudaStream_t s);
+// Batched halvings h = 1..kHalvings-1 for the candidates still searching after t = 1.
+void launch_ls_batch_setup(int d, int cap, const int32_t *n_c, const uint8_t *searching, const double *XC,
+                           const double *delta, double *XN2, int32_t *rows2, int32_t *n_rows2, cudaStream_t s);
+void launch_ls_batch_decide(int d, int cap, const int32_t *n_c, uint8_t *searching, uint8_t *active, double *XC,
+                            double *LC, const double *XN2, const double *LN2, cudaStream_t s);
+void launch_cand_stats(int d, int cap, const double *XC, const double *LC, const double *GC, const double *H,
+                       const int32_t *info, const double *lo, const double *hi, double eps_grad, const int32_t *n_c,
+                       uint8_t *keep, double *logZk, cudaStream_t s);
+void launch_laplace_final(int d, const double *XC, const double *LC, const double *logZk_c, const int32_t *n_c,
+                          const int32_t *reps, const int32_t *n_reps, const double *logV, int cap, double *modes,
+                          double *logZk, double *ell_modes, int32_t *n_modes, double *logZ, int32_t *dev_status,
+                          cudaStream_t s);
+
+}  // namespace sb

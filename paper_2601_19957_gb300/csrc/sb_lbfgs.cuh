@@ -1,0 +1,44 @@
+// sb_lbfgs.cuh -- walker state and launch interface of the batched L-BFGS kernels.
+#pragma once
+#include "sb_internal.cuh"
+
+namespace sb {
+
+template <typename T>
+struct WalkerState {
+    T f;        // f = -l at the accepted point
+    T alpha;    // step of the pending trial
+    T dphi;     // grad f . p of the current direction
+    int32_t it;     // accepted steps
+    int32_t count;  // stored pairs
+    int32_t head;   // ring slot of the oldest pair
+    int16_t bt;     // backtracks in the current line search
+    int8_t status;  // SB_WALKER_*
+    int8_t phase;   // 0: start point pending evaluation, 1: trial pending
+    int8_t attempt; // 0 first line search of the iteration, 1 retry without history
+    int8_t flat;    // consecutive accepted steps without a decrease of f
+    int8_t pad[2];
+};
+
+template <typename T>
+struct LbfgsArgs {
+    int d, m, max_iter, max_backtracks;
+    T c1, backtrack, gtol;
+    T *X, *G, *P, *XT, *GT, *FT;  // [N][d] (FT: [N])
+    T *S, *Y, *rho;               // [N][m][d], [N][m][d], [N][m]
+    WalkerState<T> *st;           // [N]
+    int32_t *act;                 // [N] active walker ids
+    int32_t *n_act;               // device scalar
+};
+
+template <typename T>
+void launch_lbfgs_init(int n, int d, const double *starts, const LbfgsArgs<T> &a, int64_t *n_evals, cudaStream_t s);
+template <typename T>
+void launch_lbfgs_step(const LbfgsArgs<T> &a, int n, cudaStream_t s);
+template <typename T>
+void launch_lbfgs_compact(const LbfgsArgs<T> &a, int64_t *n_evals, cudaStream_t s);
+template <typename T>
+void launch_lbfgs_finish(int n, int d, const LbfgsArgs<T> &a, double *x_out, double *ell_out, int8_t *status_out,
+                         int32_t *iters_out, int32_t *dev_status, cudaStream_t s);
+
+}  // namespace sb

@@ -1,0 +1,31 @@
+// sb_tc.cuh -- mixed-precision (tcgen05 tensor-core) log-likelihood and gradient.
+#pragma once
+#include <cuda.h>
+
+#include "sb_internal.cuh"
+
+namespace sb {
+
+// Scratch of the tensor-core path: converted L_k copies (GEMM1 / GEMM2 layouts),
+// FP32 means and box centre, z rows, |z|^2 partials, responsibilities, and the
+// TMA descriptors of the two L_k copies (host-side, rebuilt per call).
+struct TcWs {
+    void *p[16];
+    size_t rows;
+    int prec, bn;
+    CUtensorMap mapT, mapB;
+};
+
+bool tc_available(int prec);
+void carve_tc(Carver &cv, TcWs &t, int rows, int d, int K, int prec);
+int tc_ray_chunk(int d, int K, int64_t total);
+// Converts L_k / mu / c into the tensor-core copies and encodes the tensor maps.
+sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s);
+sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const double *u, const double *texit,
+                        double *ell_all, cudaStream_t s);
+void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, const float *XT, const int32_t *act,
+                     const int32_t *n_act, int n, float *FT, float *GT, cudaStream_t s);
+sb_status tc_loglik_points(const ProbView &pv, const sb_config *c, const TcWs &t, const double *x, int n, float *f,
+                           float *g, double *ell, double *grad, cudaStream_t s);
+
+}  // namespace sb

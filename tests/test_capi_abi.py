@@ -1,0 +1,59 @@
+"""The C-ABI library loads on a machine without a GPU and exports every
+function include/sb.h declares; host-side argument checks need no device."""
+import ctypes as C
+
+import pytest
+
+import paper_2601_19957_gb300 as sb
+from paper_2601_19957_gb300 import build as sbbuild
+from paper_2601_19957_gb300.instances import SolveConfig, workload
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    sbbuild.build()
+
+
+def test_every_declared_symbol_is_exported():
+    names = sb.declared_symbols()
+    assert {"sb_discover", "sb_refine", "sb_laplace", "sb_evidence", "sb_loglik"} <= set(names)
+    L = sb.lib()
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_status_strings():
+    assert sb.status_string(0) == "SB_OK"
+    assert sb.status_string(5) == "SB_ERR_NO_MODES"
+
+
+def _fake_problem(d, K):
+    # non-null dummy device pointers: the size query never dereferences them
+    return sb._Problem(d, K, 0x1000, 0x1000, 0x1000, 0x1000, 0x1000)
+
+
+def test_workspace_query_grows_with_walkers_and_rejects_bad_args():
+    _, cfg = workload(1, scale=0.125)
+    p = _fake_problem(64, 4)
+    small = sb.lib().sb_workspace_bytes(C.byref(p), C.byref(sb.make_config(cfg)))
+    big = sb.lib().sb_workspace_bytes(C.byref(p), C.byref(sb.make_config(cfg, n_starts=cfg.n_starts * 2)))
+    assert 0 < small < big
+    assert sb.lib().sb_workspace_bytes(C.byref(p), C.byref(sb.make_config(cfg, m=0))) == 0
+    assert sb.lib().sb_workspace_bytes(C.byref(_fake_problem(0, 1)), C.byref(sb.make_config(cfg))) == 0
+    too_many = sb.make_config(cfg, n_starts=cfg.n_rays * cfg.n_steps + 1)
+    assert sb.lib().sb_workspace_bytes(C.byref(p), C.byref(too_many)) == 0
+
+
+def test_entry_points_reject_invalid_arguments_before_any_launch():
+    cfg = sb.make_config(SolveConfig())
+    p = _fake_problem(8, 1)
+    L = sb.lib()
+    # null outputs / null workspace are refused on the host
+    assert L.sb_discover(C.byref(p), C.byref(cfg), None, None, None, C.c_size_t(0), None) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_evidence(C.byref(p), C.byref(cfg), None, None, None, 1, None, None, C.c_size_t(0), None) == \
+        sb.SB_ERR_INVALID_ARG
+    d2000 = _fake_problem(2000, 1)
+    assert L.sb_workspace_bytes(C.byref(d2000), C.byref(cfg)) == 0
+    buf = (C.c_char * 16)()
+    assert L.sb_evidence(C.byref(p), C.byref(cfg), buf, buf, buf, 1, buf, buf, C.c_size_t(16), None) == \
+        sb.SB_ERR_WORKSPACE
