@@ -225,6 +225,11 @@ def main():
     value = ev_total / t_total
     ms_per_step = 1e3 * t_total / args.steps
     dlogZ = abs(out.logZ - closed)
+    # accuracy given the discovered mode set: each mode is matched to its component
+    modes = out.modes.cpu().numpy()
+    found = sorted({int(np.argmin(np.abs(inst.mu - m).max(1))) for m in modes})
+    closed_found = float(np.log(np.exp(inst.log_w[found]).sum())) - logV if found else -math.inf
+    dlogZ_found = abs(out.logZ - closed_found) if found else None
 
     # roofline of the dominant kernel class, measured live in the timed region
     d, K = inst.d, inst.K
@@ -287,6 +292,8 @@ def main():
         "n_modes": n_modes,
         "logZ": out.logZ,
         "abs_dlogZ_vs_closed_form": dlogZ,
+        "abs_dlogZ_given_found_modes": dlogZ_found,
+        "components_found": f"{len(found)}/{inst.K}",
         "gpu_launches": int(launches),
         "clocks": clocks,
         "roofline": roof,

@@ -1,0 +1,88 @@
+"""Whole evidence path with tensor-core discovery/refinement (BF16 or TF32,
+FP32 L-BFGS) and the FP64 Laplace stage, through the C ABI.
+
+After the FP64 Newton polish the modes and their Laplace terms are FP64
+quantities again, so log Z must agree with the FP64 oracle (same mode set) to
+1e-10 relative, and with the closed form log sum w - log V."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import paper_2601_19957_gb300 as sb
+from paper_2601_19957_gb300.instances import workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2601_19957_gb300 import build as sbbuild
+
+    sbbuild.build()
+    oracle.build()
+
+
+def _closed(inst):
+    return float(np.log(np.exp(inst.log_w).sum()) - np.log(inst.hi - inst.lo).sum())
+
+
+def _check_modes_against_components(inst, out):
+    """Each mode is a component mean (to 1e-9) with Laplace term log w_k (to 1e-9), no
+    component twice; log Z = LSE of the found components' log w_k - log V (1e-10 rel)."""
+    modes = out.modes.cpu().numpy()
+    zk = out.logZk.cpu().numpy()
+    seen = set()
+    for t in range(out.n_modes):
+        k = int(np.argmin(np.abs(inst.mu - modes[t]).max(1)))
+        assert k not in seen
+        seen.add(k)
+        assert np.abs(inst.mu[k] - modes[t]).max() < 1e-9
+        assert abs(zk[t] - inst.log_w[k]) < 1e-9
+    found = np.array(sorted(seen))
+    expect = float(np.log(np.exp(inst.log_w[found]).sum()) - np.log(inst.hi - inst.lo).sum())
+    assert abs(out.logZ - expect) <= 1e-10 * abs(expect)
+    return found
+
+
+@pytest.mark.parametrize("prec", [sb.PREC_BF16, sb.PREC_TF32])
+def test_mixed_evidence_workload1(prec):
+    """Mixed-precision discovery may pick other starts than the FP64 oracle (several
+    start sets are correct), so the check is on the mode set: every mode found is a
+    true component with its exact Laplace term, and the FP64 oracle's modes (same
+    workload) are all found too."""
+    insts, c = workload(1, scale=0.25)
+    inst = insts[0]
+    c.prec = prec
+    out = sb.evidence(sb.Problem(inst), sb.make_config(c))
+    found = _check_modes_against_components(inst, out)
+    c64 = type(c)(**{**c.__dict__, "prec": 0})
+    ref = oracle.evidence(inst, c64, n_threads=8)
+    ref_k = {int(np.argmin(np.abs(inst.mu - m).max(1))) for m in ref.modes}
+    assert ref_k <= set(found.tolist())
+
+
+@pytest.mark.parametrize("prec", [sb.PREC_BF16, sb.PREC_TF32])
+def test_mixed_evidence_ill_conditioned_gaussian_workload2(prec):
+    """d=256, condition number up to 1e4: polish + Cholesky in FP64 recover log Z = -log V."""
+    insts, c = workload(2, scale=1.0 / 16)
+    inst = insts[0]
+    c.prec = prec
+    out = sb.evidence(sb.Problem(inst), sb.make_config(c))
+    assert out.n_modes == 1
+    assert abs(out.logZ - _closed(inst)) <= 1e-10 * abs(_closed(inst))
+    assert np.abs(out.modes[0].cpu().numpy() - inst.mu[0]).max() < 1e-9
+
+
+@pytest.mark.parametrize("prec", [sb.PREC_BF16, sb.PREC_TF32])
+def test_mixed_evidence_d1024_k8_scaled(prec):
+    insts, c = workload(4, scale=1.0 / 32)
+    inst = insts[0]
+    c.prec = prec
+    c.cand_cap = 64
+    out = sb.evidence(sb.Problem(inst), sb.make_config(c))
+    assert out.n_modes >= 1
+    _check_modes_against_components(inst, out)
