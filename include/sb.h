@@ -98,6 +98,22 @@ const char *sb_status_string(sb_status s);
  * Host-only call: no allocation, no CUDA call. Returns 0 if the arguments are invalid. */
 size_t sb_workspace_bytes(const sb_problem *prob, const sb_config *cfg);
 
+/*
+ * sb_loglik without a workspace, for callers that cannot allocate device
+ * memory (for example code inside a host application that owns every device
+ * allocation, or a plugin that may not call cudaMalloc). There is no
+ * counterpart in the paper. Same arguments and results as sb_loglik minus
+ * ws/ws_bytes: the scratch is a 32 MiB array inside this library, held by
+ * every GPU that loads it until the process exits. Requests whose
+ * sb_loglik_workspace_bytes exceed 32 MiB return SB_ERR_WORKSPACE before any
+ * launch. The first call on a device looks up that device's address of the
+ * array (make it before any stream capture). Calls that overlap on the GPU
+ * (concurrent streams, or several host threads) share the array and race;
+ * serialise them. It allocates nothing: no cudaMalloc, no cudaFree.
+ */
+sb_status sb_loglik_noalloc(const sb_problem *prob, int32_t prec, const double *x, int32_t n, double *ell,
+                            double *grad, void *stream);
+
 /* Bytes of scratch sb_loglik needs for n points at precision prec. */
 size_t sb_loglik_workspace_bytes(const sb_problem *prob, int32_t prec, int32_t n);
 

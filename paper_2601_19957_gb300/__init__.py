@@ -60,7 +60,7 @@ def lib():
         L.sb_workspace_bytes.restype = C.c_size_t
         L.sb_loglik_workspace_bytes.restype = C.c_size_t
         L.sb_evidence_host_workspace_bytes.restype = C.c_size_t
-        for name in ("sb_loglik", "sb_discover", "sb_refine", "sb_laplace", "sb_evidence", "sb_evidence_host",
+        for name in ("sb_loglik", "sb_loglik_noalloc", "sb_discover", "sb_refine", "sb_laplace", "sb_evidence", "sb_evidence_host",
                      "sb_check"):
             getattr(L, name).restype = C.c_int
         _lib = L
