@@ -578,8 +578,9 @@ static int greedy_dedup(int d, const double *X, const orc_rank *order, int n, do
  *    coarse dedup with tau_c = dedup_coarse * max_i (hi_i - lo_i); at most
  *    cand_cap representatives (highest l first) go on;
  *  - FP64 Newton polish: up to newton_steps steps x <- x + t H^{-1} grad l
- *    with H = -hess l via Cholesky, t = 1, halved (<= 30 times) until l does
- *    not decrease;
+ *    with H = -hess l via Cholesky; t = 1 is taken at once when the model
+ *    increase g.delta/2 <= 1e-10 (1 + |l|) (the descent test is rounding noise
+ *    there), otherwise t is halved (<= 30 times) until l does not decrease;
  *  - filters (Sec. 3.6.4, strengthened): keep if Cholesky of H succeeds at the
  *    final point (positive definite), |grad l|_inf <= eps_grad (1 + |l|), and
  *    lo <= x <= hi (the prior contains the mode, Sec. 3.2);
@@ -631,7 +632,13 @@ int orc_laplace(const orc_problem *p, const orc_config *c, const double *x, cons
             chol_solve(d, C, g, delta);
             double t = 1.0;
             int acc = 0;
-            for (int h = 0; h < 30; ++h) {
+            /* inside the quadratic-convergence regime (model increase g.delta/2 at
+               the rounding level of l) the descent test is noise: take the full step */
+            if (0.5 * dot(d, g, delta) <= 1e-10 * (1.0 + fabs(l))) {
+                for (int i = 0; i < d; ++i) xn[i] = xc[i] + t * delta[i];
+                acc = 1;
+            }
+            for (int h = 0; h < 30 && !acc; ++h) {
                 for (int i = 0; i < d; ++i) xn[i] = xc[i] + t * delta[i];
                 double ln = orc_loglik(p, xn, NULL, NULL);
                 if (ln >= l) {
