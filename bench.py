@@ -40,13 +40,18 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    # profiling cases (small, for ncu captures; not bench lines)
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="time only the tensor-core l+grad contraction on --n-points points")
+    ap.add_argument("--n-points", type=int, default=16384)
+    ap.add_argument("--scale", type=float, default=None, help="scale ray/start counts (profiling only)")
     return ap.parse_args()
 
 
-def workload_cfg(wid, prec):
+def workload_cfg(wid, prec, scale=None):
     from paper_2601_19957_gb300.instances import workload
 
-    insts, cfg = workload(wid)
+    insts, cfg = workload(wid, scale=scale)
     cfg.prec = PREC[prec]
     if wid == 4:
         cfg.cand_cap = 64  # Hessians of 64 candidates at d=1024 = 512 MB of scratch
@@ -148,6 +153,17 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_over_ranks(t_seconds, evals, dist, device):
+    """Replicas: whole-job time is the slowest rank's, work is the sum over ranks."""
+    import torch
+
+    tt = torch.tensor([float(t_seconds)], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ev = torch.tensor([float(evals)], device=device, dtype=torch.float64)
+    dist.all_reduce(ev, op=dist.ReduceOp.SUM)
+    return float(tt.item()), int(ev.item())
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -165,9 +181,11 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    inst, cfg = workload_cfg(args.workload, args.prec)
+    inst, cfg = workload_cfg(args.workload, args.prec, args.scale)
     prob = sb.Problem(inst)
     c = sb.make_config(cfg)
+    if args.kernel_only:
+        return kernel_only(sb, inst, prob, cfg, args)
     wsp = sb.workspace(prob, c)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 512 MB > L2
@@ -216,12 +234,7 @@ def main():
     clocks = clk.stop()
     t_total = sum(times) / 1e3
     if dist:
-        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-        ev = torch.tensor([ev_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(ev)
-        ev_total = int(ev.item())
+        t_total, ev_total = reduce_over_ranks(t_total, ev_total, dist, "cuda")
     value = ev_total / t_total
     ms_per_step = 1e3 * t_total / args.steps
     dlogZ = abs(out.logZ - closed)
@@ -309,6 +322,31 @@ def main():
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def kernel_only(sb, inst, prob, cfg, args):
+    """The tensor-core l+grad contraction alone (profiling case)."""
+    import torch
+
+    rng = np.random.default_rng(3)
+    n = args.n_points
+    X = torch.as_tensor(inst.mu[rng.integers(0, inst.K, n)] + rng.normal(0, 0.3, (n, inst.d)), device="cuda")
+    wsl = sb.Workspace(sb.lib().sb_loglik_workspace_bytes(sb.C.byref(prob.s), cfg.prec, n))
+    for _ in range(args.warmup):
+        sb.loglik(prob, X, prec=cfg.prec, ws=wsl)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sb.loglik(prob, X, prec=cfg.prec, ws=wsl)
+    e1.record()
+    e1.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3 / max(args.steps, 1)
+    flop = n * 2 * inst.K * inst.d * (inst.d + 1)
+    print(json.dumps({"case": "kernel-only", "n": n, "d": inst.d, "K": inst.K, "prec": args.prec,
+                      "ms": dt * 1e3, "evals_per_sec": n / dt, "algorithmic_tflops": flop / dt / 1e12}))
+    return 0
 
 
 def e2e_measure(sb, inst, cfg, c, args, evals_per_step):

@@ -179,6 +179,37 @@ size_t sb_evidence_host_workspace_bytes(const sb_problem *host_prob, const sb_co
 sb_status sb_evidence_host(const sb_problem *host_prob, const sb_config *cfg, double *logZ, double *modes,
                            double *logZk, int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes, void *stream);
 
+/*
+ * Adjoint of log Z with respect to the component means and precision Cholesky
+ * factors, at the modes of a forward solve (FP64; not in the paper, which has
+ * no gradient of log Z). For log Z = LSE_m log Z_m - log V and
+ * pi = softmax_m log Z_m, writes
+ *   dmu[k][i]    = grad_logZ * d log Z / d mu_k,i
+ *   dL[k][i][j]  = grad_logZ * d log Z / d L_k,ij   (lower triangle; upper = 0)
+ * including the implicit shift of each mode (its Hessian is recomputed, never
+ * stored): d log Z_m/dphi = d/dphi [l - 1/2 log det H - 1/2 v^T grad l] at the
+ * mode with v = H^-1 grad_x log det H. modes: [n_modes][d]; logZk: [n_modes]
+ * (device, as written by sb_evidence); dmu: [K][d]; dL: [K][d][d] (device).
+ * ws: sb_evidence_backward_workspace_bytes. Synchronises `stream`.
+ */
+size_t sb_evidence_backward_workspace_bytes(const sb_problem *prob);
+sb_status sb_evidence_backward(const sb_problem *prob, const double *modes, const double *logZk, int32_t n_modes,
+                               double grad_logZ, double *dmu, double *dL, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Many independent evidence problems (uneven d and K) in one call: problem i
+ * is solved by sb_evidence on worker stream i % n_workers, each worker with
+ * its own host thread and workspace slice, so the problems' kernels overlap on
+ * the GPU. probs: HOST array of P problems (their arrays are device pointers);
+ * logZ: device [P]; n_modes: device int32 [P]. The work starts after what is
+ * already queued on `stream`; the call returns when every problem is solved.
+ * Device-side conditions (e.g. zero modes) are per problem: logZ = -inf.
+ */
+size_t sb_evidence_batched_workspace_bytes(const sb_problem *probs, int32_t P, const sb_config *cfg,
+                                           int32_t n_workers);
+sb_status sb_evidence_batched(const sb_problem *probs, int32_t P, const sb_config *cfg, double *logZ,
+                              int32_t *n_modes, int32_t n_workers, void *ws, size_t ws_bytes, void *stream);
+
 /* Synchronise `stream` and return the status word the device recorded in ws
  * (SB_OK if nothing went wrong); clears the word. */
 sb_status sb_check(void *ws, size_t ws_bytes, void *stream);

@@ -60,6 +60,12 @@ def lib():
         L.sb_workspace_bytes.restype = C.c_size_t
         L.sb_loglik_workspace_bytes.restype = C.c_size_t
         L.sb_evidence_host_workspace_bytes.restype = C.c_size_t
+        L.sb_evidence_backward_workspace_bytes.restype = C.c_size_t
+        L.sb_evidence_batched_workspace_bytes.restype = C.c_size_t
+        L.sb_evidence_batched.restype = C.c_int
+        L.sb_evidence_backward.restype = C.c_int
+        L.sb_evidence_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         for name in ("sb_loglik", "sb_loglik_noalloc", "sb_discover", "sb_refine", "sb_laplace", "sb_evidence", "sb_evidence_host",
                      "sb_check"):
             getattr(L, name).restype = C.c_int
@@ -115,6 +121,16 @@ class Problem:
                                                          f(inst.hi))
         self.s = _Problem(self.d, self.K, self.log_w.data_ptr(), self.mu.data_ptr(), self.L.data_ptr(),
                           self.lo.data_ptr(), self.hi.data_ptr())
+
+
+class TensorProblem:
+    """C struct over caller-owned CUDA float64 tensors (log_w, mu, L, lo, hi)."""
+
+    def __init__(self, log_w, mu, L, lo, hi):
+        self.tensors = [t.contiguous() for t in (log_w, mu, L, lo, hi)]
+        self.log_w, self.mu, self.L, self.lo, self.hi = self.tensors
+        self.K, self.d = int(mu.shape[0]), int(mu.shape[1])
+        self.s = _Problem(self.d, self.K, *[t.data_ptr() for t in self.tensors])
 
 
 def host_problem(inst: Instance):
@@ -280,3 +296,65 @@ def evidence_host(inst: Instance, cfg: _Config, ws: Workspace, stream=None):
     del keep
     k = min(int(nm[0]), cap)
     return float(lz[0]), modes[:k], zk[:k], int(nm[0])
+
+
+def evidence_backward(prob, modes, logZk, n_modes: int, grad_logZ: float = 1.0, stream=None):
+    """d log Z / d mu_k and d log Z / d L_k (lower) at the modes of a forward solve."""
+    torch = _torch()
+    dmu = torch.zeros((prob.K, prob.d), dtype=torch.float64, device="cuda")
+    dL = torch.zeros((prob.K, prob.d, prob.d), dtype=torch.float64, device="cuda")
+    ws = Workspace(lib().sb_evidence_backward_workspace_bytes(C.byref(prob.s)))
+    modes = modes.contiguous()
+    logZk = logZk.contiguous()
+    _check(lib().sb_evidence_backward(C.byref(prob.s), _ptr(modes), _ptr(logZk), int(n_modes), float(grad_logZ),
+                                      _ptr(dmu), _ptr(dL), ws.ptr, ws.nbytes, _stream(stream)),
+           "sb_evidence_backward")
+    return dmu, dL
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class EvidenceFunction(torch.autograd.Function):
+        """log Z as a differentiable function of the component means and
+        precision Cholesky factors (log_w and the box are treated as constants)."""
+
+        @staticmethod
+        def forward(ctx, mu, L, log_w, lo, hi, cfg):
+            prob = TensorProblem(log_w.detach(), mu.detach(), L.detach(), lo.detach(), hi.detach())
+            out = evidence(prob, cfg)
+            ctx.prob = prob
+            ctx.save_for_backward(out.modes.clone(), out.logZk.clone())
+            ctx.n_modes = out.n_modes
+            return torch.tensor(out.logZ, dtype=torch.float64, device=mu.device)
+
+        @staticmethod
+        def backward(ctx, grad):
+            modes, logZk = ctx.saved_tensors
+            if ctx.n_modes == 0:
+                return None, None, None, None, None, None
+            dmu, dL = evidence_backward(ctx.prob, modes, logZk, min(ctx.n_modes, modes.shape[0]),
+                                        float(grad.item()))
+            return dmu, dL, None, None, None, None
+
+    return EvidenceFunction
+
+
+def evidence_autograd(mu, L, log_w, lo, hi, cfg: _Config):
+    """log Z with autograd support for mu and L (see EvidenceFunction)."""
+    return _autograd_function().apply(mu, L, log_w, lo, hi, cfg)
+
+
+def evidence_batched(problems, cfg: _Config, n_workers: int = 8, stream=None):
+    """Solve many independent problems (list of Problem) in one library call.
+    Returns (logZ, n_modes) as CUDA tensors of length P."""
+    torch = _torch()
+    P = len(problems)
+    arr = (_Problem * P)(*[p.s for p in problems])
+    nbytes = lib().sb_evidence_batched_workspace_bytes(arr, P, C.byref(cfg), int(n_workers))
+    ws = Workspace(nbytes)
+    logZ = torch.empty(P, dtype=torch.float64, device="cuda")
+    nm = torch.empty(P, dtype=torch.int32, device="cuda")
+    _check(lib().sb_evidence_batched(arr, P, C.byref(cfg), _ptr(logZ), _ptr(nm), int(n_workers), ws.ptr,
+                                     C.c_size_t(ws.nbytes), _stream(stream)), "sb_evidence_batched")
+    return logZ, nm

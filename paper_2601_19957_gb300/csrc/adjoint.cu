@@ -1,0 +1,408 @@
+// adjoint.cu -- FP64 adjoint of log Z with respect to the component means and
+// precision Cholesky factors (mu_k, L_k), for torch.autograd.
+//
+// log Z = LSE_m log Z_m - log V with log Z_m = l(x*_m) + (d/2) log 2pi - 1/2 log det H_m
+// (Sec. 3.7.1, App. A.3, A.8) and x*_m a stationary point of l. With
+// pi_m = softmax_m log Z_m and W = H^-1 at x*:
+//
+//   d log Z_m / d phi = d/dphi [ l - 1/2 log det H - 1/2 v^T grad l ]   (x = x*, v held fixed)
+//   v = W t,  t = grad_x log det H = (tr(W dH/dx_i))_i
+//
+// The last term is the implicit shift of the mode, dx*/dphi = W d(grad l)/dphi,
+// which moves log det H (l itself is stationary). Reverse-mode through the
+// mixture pieces at x (delta_k = x - mu_k, z_k = L_k^T delta_k, r = softmax(e),
+// g_k = -L_k z_k, gbar = sum r_k g_k, H = sum_k r_k (P_k - g_k g_k^T) + gbar gbar^T):
+//
+//   c       = -W gbar - v/2
+//   beta_k  = -1/2 [tr(W P_k) - g_k^T W g_k] + c^T g_k
+//   eps_k   = r_k + r_k (beta_k - sum_j r_j beta_j)                       (adjoint of e_k)
+//   gam_k   = r_k (W g_k + c)                                             (adjoint of g_k)
+//   dmu_k   = -eps_k g_k + P_k gam_k
+//   dL_k    = lower[ eps_k (diag(1/L_ii) - delta_k z_k^T) - gam_k z_k^T - delta_k (L_k^T gam_k)^T - r_k W L_k ]
+//
+// and t from the same reverse pass applied to log det H alone:
+//   beta'_k = tr(W P_k) - g_k^T W g_k + 2 gbar^T W g_k,  eps'_k = r_k (beta'_k - sum_j r_j beta'_j)
+//   gam'_k  = 2 r_k W (gbar - g_k),  t = sum_k (eps'_k g_k - P_k gam'_k).
+// tr(W P_k) = <W L_k, L_k>_F. Components with r_k == 0 contribute exactly zero
+// and are skipped. H is recomputed at every mode (not stored by the forward),
+// factored H = C C^T, and W is applied through triangular solves: W B =
+// C^-T (C^-1 B) for the d right-hand sides of L_k and for vectors.
+#include "sb_adjoint.cuh"
+
+namespace sb {
+
+namespace {
+
+constexpr int TB = 32;  // triangular-solve row block
+
+// ------------------------------------------------------------------ blocked TRSM, row-major B [d][n]
+// Lower: X = C^-1 B.  Update of row block I: B_I -= C[I][0:I] X[0:I] (all columns).
+__global__ void __launch_bounds__(256) k_trsm_update(int d, int n, int I, bool upper, const double *C, double *B) {
+    // tile: 32 rows of block I x 64 columns
+    const int c0 = blockIdx.x * 64;
+    const int r0 = I * TB;
+    __shared__ double Cs[TB][TB + 1];
+    __shared__ double Xs[TB][64 + 1];
+    const int tid = threadIdx.x, tc = tid & 63, tr = tid >> 6;  // 4 row groups x 64 cols
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int nb = (d + TB - 1) / TB;
+    const int kb_lo = upper ? I + 1 : 0, kb_hi = upper ? nb : I;
+    for (int kb = kb_lo; kb < kb_hi; ++kb) {
+        const int k0 = kb * TB;
+        for (int e = tid; e < TB * TB; e += 256) {
+            const int i = e / TB, k = e % TB;
+            const int gi = r0 + i, gk = k0 + k;
+            double v = 0.0;
+            if (gi < d && gk < d) v = upper ? C[(size_t)gk * d + gi] : C[(size_t)gi * d + gk];  // (C^T)_ik = C_ki
+            Cs[i][k] = v;
+        }
+        for (int e = tid; e < TB * 64; e += 256) {
+            const int k = e / 64, c = e % 64;
+            const int gk = k0 + k, gc = c0 + c;
+            Xs[k][c] = (gk < d && gc < n) ? B[(size_t)gk * n + gc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < TB; ++k) {
+            const double x = Xs[k][tc];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = fma(Cs[tr + 4 * q][k], x, acc[q]);
+        }
+        __syncthreads();
+    }
+    const int gc = c0 + tc;
+    if (gc < n)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int gi = r0 + tr + 4 * q;
+            if (gi < d) B[(size_t)gi * n + gc] -= acc[q];
+        }
+}
+
+// Diagonal block solve for all columns: thread per column.
+__global__ void __launch_bounds__(256) k_trsm_diag(int d, int n, int I, bool upper, const double *C, double *B) {
+    __shared__ double Cs[TB][TB + 1];
+    const int r0 = I * TB;
+    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+        const int i = e / TB, k = e % TB;
+        const int gi = r0 + i, gk = r0 + k;
+        double v = (i == k) ? 1.0 : 0.0;
+        if (gi < d && gk < d) v = upper ? C[(size_t)gk * d + gi] : C[(size_t)gi * d + gk];
+        Cs[i][k] = v;
+    }
+    __syncthreads();
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= n) return;
+    const int rows = min(TB, d - r0);
+    double x[TB];
+#pragma unroll
+    for (int i = 0; i < TB; ++i) x[i] = i < rows ? B[(size_t)(r0 + i) * n + col] : 0.0;
+    if (!upper) {
+#pragma unroll
+        for (int i = 0; i < TB; ++i) {
+            double s = x[i];
+#pragma unroll
+            for (int k = 0; k < i; ++k) s -= Cs[i][k] * x[k];
+            x[i] = s / Cs[i][i];
+        }
+    } else {
+#pragma unroll
+        for (int i = TB - 1; i >= 0; --i) {
+            double s = x[i];
+#pragma unroll
+            for (int k = i + 1; k < TB; ++k) s -= Cs[i][k] * x[k];
+            x[i] = s / Cs[i][i];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < TB; ++i)
+        if (i < rows) B[(size_t)(r0 + i) * n + col] = x[i];
+}
+
+// W B = C^-T C^-1 B in place (B row-major [d][n]).
+void apply_W(int d, int n, const double *C, double *B, cudaStream_t s) {
+    const int nb = (d + TB - 1) / TB;
+    const int gu = (n + 63) / 64, gd = (n + 255) / 256;
+    for (int I = 0; I < nb; ++I) {
+        if (I > 0) {
+            note_launch();
+            k_trsm_update<<<gu, 256, 0, s>>>(d, n, I, false, C, B);
+        }
+        note_launch();
+        k_trsm_diag<<<gd, 256, 0, s>>>(d, n, I, false, C, B);
+    }
+    for (int I = nb - 1; I >= 0; --I) {
+        if (I < nb - 1) {
+            note_launch();
+            k_trsm_update<<<gu, 256, 0, s>>>(d, n, I, true, C, B);
+        }
+        note_launch();
+        k_trsm_diag<<<gd, 256, 0, s>>>(d, n, I, true, C, B);
+    }
+}
+
+// ------------------------------------------------------------------ per-mode vector algebra
+// Column vectors for the right-hand-side block V [d][nv] (row-major, so W acts on columns):
+// columns 0..K-1 = g_k (active only, else 0), K = gbar.
+__global__ void k_pack_rhs(int d, int K, const double *GK, const double *gbar, const double *R, double *V) {
+    const int nv = K + 1;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d * nv; e += gridDim.x * blockDim.x) {
+        const int i = e / nv, c = e % nv;
+        double v;
+        if (c < K)
+            v = R[c] != 0.0 ? GK[(size_t)c * d + i] : 0.0;
+        else
+            v = gbar[i];
+        V[e] = v;
+    }
+}
+
+// copy L_k (lower, zero above) into M [d][d]
+__global__ void k_copy_lower(int d, const double *Lk, double *M) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)d * d;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / d), j = (int)(e % d);
+        M[e] = j <= i ? Lk[e] : 0.0;
+    }
+}
+
+template <typename T>
+__device__ T block_sum256(T v, T *sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    T t = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+    __syncthreads();
+    return t;
+}
+
+// tr(W P_k) = <W L_k, L_k>_F over the lower triangle (W L_k in M).
+__global__ void __launch_bounds__(256) k_trace_WP(int d, const double *M, const double *Lk, double *out) {
+    __shared__ double sh[8];
+    double s = 0.0;
+    for (size_t e = threadIdx.x; e < (size_t)d * d; e += blockDim.x) {
+        const int i = (int)(e / d), j = (int)(e % d);
+        if (j <= i) s += M[e] * Lk[e];
+    }
+    s = block_sum256(s, sh);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// One CTA: given WV (W applied to [g_0..g_{K-1}, gbar]) and tr(W P_k), form t (stage 0),
+// or with Wt known form c, eps, gam (stage 1). Vectors of length d in global scratch.
+__global__ void __launch_bounds__(256) k_adj_stage(int stage, int d, int K, const double *R, const double *GK,
+                                                   const double *gbar, const double *WV, const double *trWP,
+                                                   const double *P, const double *Wt, double *t_out, double *eps,
+                                                   double *gam, double *cvec) {
+    __shared__ double sh[8];
+    __shared__ double s_beta[kMaxK];
+    const int nv = K + 1;
+    // per active component: dot products g_k^T W g_k, gbar^T W g_k, c^T g_k
+    for (int k = 0; k < K; ++k) {
+        const double r = R[k];
+        if (r == 0.0) {
+            if (threadIdx.x == 0) s_beta[k] = 0.0;
+            continue;
+        }
+        double a1 = 0.0, a2 = 0.0;
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            const double gk = GK[(size_t)k * d + i];
+            const double wgk = WV[(size_t)i * nv + k];
+            a1 += gk * wgk;                     // g_k^T W g_k
+            if (stage == 0)
+                a2 += gbar[i] * wgk;            // gbar^T W g_k
+            else
+                a2 += (-WV[(size_t)i * nv + K] - 0.5 * Wt[i]) * gk;  // c^T g_k
+        }
+        a1 = block_sum256(a1, sh);
+        a2 = block_sum256(a2, sh);
+        if (threadIdx.x == 0)
+            s_beta[k] = stage == 0 ? (trWP[k] - a1 + 2.0 * a2) : (-0.5 * (trWP[k] - a1) + a2);
+    }
+    __syncthreads();
+    double sb = 0.0;
+    for (int k = 0; k < K; ++k) sb += R[k] * s_beta[k];
+    if (stage == 0) {
+        // t = sum_k eps'_k g_k - P_k gam'_k,  gam'_k = 2 r_k W (gbar - g_k)
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            double ti = 0.0;
+            for (int k = 0; k < K; ++k) {
+                const double r = R[k];
+                if (r == 0.0) continue;
+                const double e1 = r * (s_beta[k] - sb);
+                ti += e1 * GK[(size_t)k * d + i];
+                // (P_k gam'_k)_i = 2 r sum_j P_k[i][j] (W gbar - W g_k)_j
+                const double *Pk = P + (size_t)k * d * d + (size_t)i * d;
+                double pg = 0.0;
+                for (int j = 0; j < d; ++j) pg += Pk[j] * (WV[(size_t)j * nv + K] - WV[(size_t)j * nv + k]);
+                ti -= 2.0 * r * pg;
+            }
+            t_out[i] = ti;
+        }
+    } else {
+        if (threadIdx.x < K) {
+            const int k = threadIdx.x;
+            eps[k] = R[k] == 0.0 ? 0.0 : R[k] + R[k] * (s_beta[k] - sb);
+        }
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            const double c = -WV[(size_t)i * nv + K] - 0.5 * Wt[i];
+            cvec[i] = c;
+            for (int k = 0; k < K; ++k) gam[(size_t)k * d + i] = R[k] == 0.0 ? 0.0 : R[k] * (WV[(size_t)i * nv + k] + c);
+        }
+    }
+}
+
+// dmu_k += pi (-eps_k g_k + P_k gam_k): one CTA per component, thread per row.
+__global__ void __launch_bounds__(256) k_adj_dmu(int d, int K, double pi, const double *R, const double *eps,
+                                                 const double *GK, const double *P, const double *gam, double *dmu) {
+    const int k = blockIdx.y;
+    if (R[k] == 0.0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d) return;
+    const double *Pk = P + (size_t)k * d * d + (size_t)i * d;
+    const double *gk = gam + (size_t)k * d;
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) s += Pk[j] * gk[j];
+    dmu[(size_t)k * d + i] += pi * (-eps[k] * GK[(size_t)k * d + i] + s);
+}
+
+// L^T gam for component k (u[j] = sum_i L[i][j] gam[i]).
+__global__ void __launch_bounds__(256) k_adj_Ltg(int d, const double *Lk, const double *g, double *u) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= d) return;
+    double s = 0.0;
+    for (int i = j; i < d; ++i) s += Lk[(size_t)i * d + j] * g[i];
+    u[j] = s;
+}
+
+// dL_k += pi lower[ eps (diag(1/L) - delta z^T) - gam z^T - delta u^T - r M ],  M = W L_k, u = L^T gam.
+__global__ void __launch_bounds__(256) k_adj_dL(int d, double pi, double r, double eps, const double *Lk,
+                                                const double *x, const double *mu, const double *z, const double *gam,
+                                                const double *u, const double *M, double *dL) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)d * d;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / d), j = (int)(e % d);
+        if (j > i) continue;
+        const double di = x[i] - mu[i];
+        double v = -eps * di * z[j] - gam[i] * z[j] - di * u[j] - r * M[e];
+        if (i == j) v += eps / Lk[e];
+        dL[e] += pi * v;
+    }
+}
+
+__global__ void k_softmax_pi(int n, const double *logZk, double g, double *pi) {
+    if (threadIdx.x != 0) return;
+    double mx = -INFINITY;
+    for (int i = 0; i < n; ++i) mx = fmax(mx, logZk[i]);
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += exp(logZk[i] - mx);
+    for (int i = 0; i < n; ++i) pi[i] = g * exp(logZk[i] - mx) / s;
+}
+
+}  // namespace
+
+void adjoint_carve(Carver &cv, AdjWs &w, int d, int K) {
+    const int nJT = (d + 63) / 64;
+    w.P = cv.take<double>((size_t)K * d * d);
+    w.H = cv.take<double>((size_t)d * d);
+    w.M = cv.take<double>((size_t)K * d * d);
+    w.Z = cv.take<double>((size_t)K * d);
+    w.R = cv.take<double>((size_t)K);
+    w.qpart = cv.take<double>((size_t)K * nJT);
+    w.gbar = cv.take<double>(d);
+    w.ell = cv.take<double>(1);
+    w.GK = cv.take<double>((size_t)K * d);
+    w.V = cv.take<double>((size_t)d * (K + 1));
+    w.T = cv.take<double>(d);
+    w.cvec = cv.take<double>(d);
+    w.eps = cv.take<double>(K);
+    w.gam = cv.take<double>((size_t)K * d);
+    w.u = cv.take<double>(d);
+    w.trWP = cv.take<double>(K);
+    w.pi = cv.take<double>(kMaxAdjModes);
+    w.info = cv.take<int32_t>(1);
+    w.one = cv.take<int32_t>(1);
+}
+
+sb_status adjoint_run(const ProbView &pv, const AdjWs &w, const double *modes, const double *logZk, int n_modes,
+                      double grad_logZ, double *dmu, double *dL, cudaStream_t s) {
+    const int d = pv.d, K = pv.K;
+    if (n_modes < 1 || n_modes > kMaxAdjModes) return SB_ERR_INVALID_ARG;
+    SB_CUDA_TRY(cudaMemsetAsync(dmu, 0, sizeof(double) * K * d, s));
+    SB_CUDA_TRY(cudaMemsetAsync(dL, 0, sizeof(double) * (size_t)K * d * d, s));
+    const int32_t one = 1;
+    SB_CUDA_TRY(cudaMemcpyAsync(w.one, &one, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    note_launch();
+    k_softmax_pi<<<1, 32, 0, s>>>(n_modes, logZk, grad_logZ, w.pi);
+    launch_precision(d, K, pv.L, w.P, s);
+    std::vector<double> pis(n_modes), Rh(K), epsh(K);
+    SB_CUDA_TRY(cudaMemcpyAsync(pis.data(), w.pi, sizeof(double) * n_modes, cudaMemcpyDeviceToHost, s));
+    SB_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int mo = 0; mo < n_modes; ++mo) {
+        const double *x = modes + (size_t)mo * d;
+        // l, grad l, z_k, r_k at x (FP64 likelihood kernels), then g_k, H and H = C C^T
+        LikF64Args la{};
+        la.d = d;
+        la.K = K;
+        la.mu = pv.mu;
+        la.L = pv.L;
+        la.a = pv.a;
+        la.X = x;
+        la.n_rows = 1;
+        la.qpart = w.qpart;
+        la.Z = w.Z;
+        la.R = w.R;
+        la.ell = w.ell;
+        la.ell_sign = 1.0;
+        la.G = w.gbar;
+        la.grad_sign = -1.0;
+        la.out_by_walker = 0;
+        launch_lik_f64_points(la, true, s);
+        launch_hessian_chol(d, K, 1, pv.L, w.P, w.Z, w.R, w.gbar, w.one, w.GK, w.H, w.info, s);
+        // W [g_0 .. g_{K-1}, gbar]
+        note_launch();
+        k_pack_rhs<<<(d * (K + 1) + 255) / 256, 256, 0, s>>>(d, K, w.GK, w.gbar, w.R, w.V);
+        apply_W(d, K + 1, w.H, w.V, s);
+        SB_CUDA_TRY(cudaMemcpyAsync(Rh.data(), w.R, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+        SB_CUDA_TRY(cudaStreamSynchronize(s));
+        // W L_k and tr(W P_k) = <W L_k, L_k>_F for the components with r_k > 0
+        for (int k = 0; k < K; ++k) {
+            if (Rh[k] == 0.0) continue;
+            double *Mk = w.M + (size_t)k * d * d;
+            note_launch();
+            k_copy_lower<<<1184, 256, 0, s>>>(d, pv.L + (size_t)k * d * d, Mk);
+            apply_W(d, d, w.H, Mk, s);
+            note_launch();
+            k_trace_WP<<<1, 256, 0, s>>>(d, Mk, pv.L + (size_t)k * d * d, w.trWP + k);
+        }
+        // t = grad_x log det H, then v = W t (in place)
+        note_launch();
+        k_adj_stage<<<1, 256, 0, s>>>(0, d, K, w.R, w.GK, w.gbar, w.V, w.trWP, w.P, nullptr, w.T, nullptr, nullptr,
+                                      nullptr);
+        apply_W(d, 1, w.H, w.T, s);
+        // c, eps_k, gam_k
+        note_launch();
+        k_adj_stage<<<1, 256, 0, s>>>(1, d, K, w.R, w.GK, w.gbar, w.V, w.trWP, w.P, w.T, nullptr, w.eps, w.gam,
+                                      w.cvec);
+        note_launch();
+        k_adj_dmu<<<dim3((d + 255) / 256, K), 256, 0, s>>>(d, K, pis[mo], w.R, w.eps, w.GK, w.P, w.gam, dmu);
+        SB_CUDA_TRY(cudaMemcpyAsync(epsh.data(), w.eps, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+        SB_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int k = 0; k < K; ++k) {
+            if (Rh[k] == 0.0) continue;
+            const double *Lk = pv.L + (size_t)k * d * d;
+            note_launch();
+            k_adj_Ltg<<<(d + 255) / 256, 256, 0, s>>>(d, Lk, w.gam + (size_t)k * d, w.u);
+            note_launch();
+            k_adj_dL<<<1184, 256, 0, s>>>(d, pis[mo], Rh[k], epsh[k], Lk, x, pv.mu + (size_t)k * d,
+                                          w.Z + (size_t)k * d, w.gam + (size_t)k * d, w.u, w.M + (size_t)k * d * d,
+                                          dL + (size_t)k * d * d);
+        }
+    }
+    SB_CUDA_TRY(cudaGetLastError());
+    return SB_OK;
+}
+
+}  // namespace sb

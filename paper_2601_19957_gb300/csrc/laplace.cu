@@ -11,7 +11,9 @@
 //  * batched blocked Cholesky H = C C^T (right-looking, 32x32 blocks:
 //    diagonal factor, panel triangular solve, trailing update), which also
 //    serves as the positive-definiteness (saddle) filter of Sec. 3.6.4;
-//  * Newton polish x <- x + t H^{-1} grad l, t halved until l does not drop;
+//  * Newton polish x <- x + t H^{-1} grad l: t = 1 at once when the model
+//    increase g^T delta / 2 <= 1e-10 (1 + |l|) (there the descent test is
+//    rounding noise), otherwise t halved until l does not drop;
 //  * log Z_k = l(x*) + (d/2) log 2pi - sum_i log C_ii (Sec. 3.7.1 with the
 //    whitening identity of App. A.8) and log Z = LSE_k log Z_k - log V
 //    (Sec. 3.7.3, App. A.10, Sec. 3.2).
@@ -314,7 +316,8 @@ __global__ void __launch_bounds__(256) k_syrk_update(int d, int kb, double *H, c
 
 // Solve (C C^T) delta = g for each candidate still polishing.
 __global__ void __launch_bounds__(256) k_chol_solve(int d, const double *H, const double *g, const int32_t *n_c,
-                                                    const int32_t *info, const uint8_t *active, double *delta) {
+                                                    const int32_t *info, const uint8_t *active, double *delta,
+                                                    double *pred) {
     const int c = blockIdx.x;
     if (c >= *n_c || info[c] || !active[c]) return;
     extern __shared__ double y[];
@@ -335,7 +338,21 @@ __global__ void __launch_bounds__(256) k_chol_solve(int d, const double *H, cons
         for (int k = threadIdx.x; k < i; k += blockDim.x) y[k] -= C[(size_t)i * d + k] * yi;
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < d; i += blockDim.x) delta[(size_t)c * d + i] = y[i];
+    // model increase of l along the Newton step: g^T delta / 2
+    __shared__ double s_part[8];
+    double gd = 0.0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        delta[(size_t)c * d + i] = y[i];
+        gd += g[(size_t)c * d + i] * y[i];
+    }
+    gd = warp_sum(gd);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = gd;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s_part[q];
+        pred[c] = 0.5 * t;
+    }
 }
 
 // ------------------------------------------------------------------ Newton line search
@@ -344,7 +361,7 @@ __global__ void __launch_bounds__(256) k_chol_solve(int d, const double *H, cons
 __global__ void __launch_bounds__(256) k_newton_ls(int d, int mode, const int32_t *n_c, const int32_t *info,
                                                    uint8_t *active, uint8_t *searching, int32_t *halvings, double *t,
                                                    double *XC, double *LC, const double *delta, double *XN,
-                                                   const double *LN) {
+                                                   const double *LN, const double *pred) {
     const int c = blockIdx.x;
     if (c >= *n_c) return;
     __shared__ int s_act;
@@ -353,10 +370,16 @@ __global__ void __launch_bounds__(256) k_newton_ls(int d, int mode, const int32_
         if (mode == 0) {
             const int s = active[c] && !info[c];
             if (!s) active[c] = 0;
-            searching[c] = (uint8_t)s;
             halvings[c] = 0;
             t[c] = 1.0;
-            act = s ? 2 : 0;  // 2: write the trial
+            if (s && pred[c] <= 1e-10 * (1.0 + fabs(LC[c]))) {
+                // quadratic-convergence regime: the descent test is rounding noise, take t = 1
+                searching[c] = 0;
+                act = 3;
+            } else {
+                searching[c] = (uint8_t)s;
+                act = s ? 2 : 0;  // 2: write the trial
+            }
         } else if (searching[c]) {
             if (LN[c] >= LC[c]) {
                 searching[c] = 0;
@@ -377,6 +400,9 @@ __global__ void __launch_bounds__(256) k_newton_ls(int d, int mode, const int32_
     const int act = s_act;
     if (act == 1) {
         for (int i = threadIdx.x; i < d; i += blockDim.x) XC[(size_t)c * d + i] = XN[(size_t)c * d + i];
+    } else if (act == 3) {
+        for (int i = threadIdx.x; i < d; i += blockDim.x)
+            XC[(size_t)c * d + i] = add_rn(XC[(size_t)c * d + i], mul_rn(1.0, delta[(size_t)c * d + i]));
     } else if (act == 2) {
         const double tc = t[c];
         for (int i = threadIdx.x; i < d; i += blockDim.x)
@@ -556,16 +582,17 @@ void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P
 }
 
 void launch_chol_solve(int d, int cap, const double *H, const double *g, const int32_t *n_c, const int32_t *info,
-                       const uint8_t *active, double *delta, cudaStream_t s) {
+                       const uint8_t *active, double *delta, double *pred, cudaStream_t s) {
     note_launch();
-    k_chol_solve<<<cap, 256, sizeof(double) * d, s>>>(d, H, g, n_c, info, active, delta);
+    k_chol_solve<<<cap, 256, sizeof(double) * d, s>>>(d, H, g, n_c, info, active, delta, pred);
 }
 
 void launch_newton_ls(int d, int cap, int mode, const int32_t *n_c, const int32_t *info, uint8_t *active,
                       uint8_t *searching, int32_t *halvings, double *t, double *XC, double *LC, const double *delta,
-                      double *XN, const double *LN, cudaStream_t s) {
+                      double *XN, const double *LN, const double *pred, cudaStream_t s) {
     note_launch();
-    k_newton_ls<<<cap, 256, 0, s>>>(d, mode, n_c, info, active, searching, halvings, t, XC, LC, delta, XN, LN);
+    k_newton_ls<<<cap, 256, 0, s>>>(d, mode, n_c, info, active, searching, halvings, t, XC, LC, delta, XN, LN,
+                                    pred);
 }
 
 void launch_ls_batch_setup(int d, int cap, const int32_t *n_c, const uint8_t *searching, const double *XC,

@@ -5,8 +5,10 @@
 
 #include <atomic>
 #include <mutex>
+#include <thread>
 #include <vector>
 
+#include "sb_adjoint.cuh"
 #include "sb_internal.cuh"
 #include "sb_laplace.cuh"
 #include "sb_lbfgs.cuh"
@@ -118,6 +120,7 @@ struct SetupWs {
 
 struct DiscoverWs {
     double *u, *texit, *ell_all, *qpart;
+    float *u32;  // FP32 copy of the directions (tensor-core path)
     int chunk;
     SelectWs sel;
     TcWs tc;  // tensor-core scratch (mixed precision)
@@ -126,13 +129,14 @@ struct DiscoverWs {
 template <typename T>
 struct RefineWs {
     LbfgsArgs<T> lb;
+    float *MSY, *MYY;  // [N][m][m] S^T Y and Y^T Y (FP32 compact-form step)
     int64_t *n_evals;
     double *qpart, *Z, *R;  // FP64 evaluation
     TcWs tc;                // mixed-precision evaluation
 };
 
 struct LaplaceWs {
-    double *P, *XC, *LC, *GC, *Z, *R, *qpart, *GK, *H, *delta, *XN, *LN, *XN2, *LN2, *qpart2, *logZk_c, *t;
+    double *P, *XC, *LC, *GC, *Z, *R, *qpart, *GK, *H, *delta, *XN, *LN, *XN2, *LN2, *qpart2, *logZk_c, *t, *pred;
     int32_t *reps, *n_reps, *info, *halvings, *rows2, *n_rows2, *reps2, *n_reps2;
     uint8_t *assigned, *active, *searching, *keep;
 };
@@ -182,6 +186,8 @@ void carve_refine(Carver &cv, RefineWs<T> &r, int n, int d, int K, int m, bool f
         r.R = cv.take<double>((size_t)n * K);
     } else {
         carve_tc(cv, r.tc, n, d, K, prec);
+        r.MSY = cv.take<float>((size_t)n * m * m);
+        r.MYY = cv.take<float>((size_t)n * m * m);
     }
 }
 
@@ -205,8 +211,10 @@ Layout layout(void *base, const sb_problem *p, const sb_config *c) {
     L.di.chunk = discover_chunk(d, K, total);
     if (fp64)
         L.di.qpart = cv.take<double>(lik_f64_qpart_elems(d, K, L.di.chunk));
-    else
+    else {
         carve_tc(cv, L.di.tc, tc_ray_chunk(d, K, total), d, K, c->prec);
+        L.di.u32 = cv.take<float>((size_t)c->n_rays * d);
+    }
     L.di.sel.bucket = cv.take<int32_t>(total);
     L.di.sel.hist = cv.take<uint32_t>(c->n_steps * 2 > 256 ? c->n_steps * 2 : 256);
     L.di.sel.state = cv.take<uint64_t>(8);
@@ -240,6 +248,7 @@ Layout layout(void *base, const sb_problem *p, const sb_config *c) {
     la.searching = cv.take<uint8_t>(cap);
     la.halvings = cv.take<int32_t>(cap);
     la.t = cv.take<double>(cap);
+    la.pred = cv.take<double>(cap);
     la.delta = cv.take<double>((size_t)cap * d);
     la.XN = cv.take<double>((size_t)cap * d);
     la.LN = cv.take<double>(cap);
@@ -315,7 +324,7 @@ sb_status run_discover(const ProbView &pv, const sb_config *c, const Layout &L, 
             launch_lik_f64_rays(a, s);
         }
     } else {
-        const sb_status st = tc_ray_loglik(pv, c, L.di.tc, L.di.u, L.di.texit, L.di.ell_all, s);
+        const sb_status st = tc_ray_loglik(pv, c, L.di.tc, L.di.u, L.di.u32, L.di.texit, L.di.ell_all, s);
         if (st != SB_OK) return st;
     }
     launch_select_starts(L.di.ell_all, c->n_rays, c->n_steps, c->n_starts, L.di.sel, s);
@@ -351,6 +360,28 @@ void eval_round<float>(const ProbView &pv, const sb_config *c, const RefineWs<fl
     tc_eval_walkers(pv, c, r.tc, r.lb.XT, r.lb.act, r.lb.n_act, n, r.lb.FT, r.lb.GT, s);
 }
 
+int device_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <typename T>
+void step_round(const RefineWs<T> &r, const LbfgsArgs<T> &a, int n, cudaStream_t s);
+template <>
+void step_round<double>(const RefineWs<double> &, const LbfgsArgs<double> &a, int n, cudaStream_t s) {
+    launch_lbfgs_step<double>(a, n, s);  // two-loop recursion, warp per walker
+}
+template <>
+void step_round<float>(const RefineWs<float> &r, const LbfgsArgs<float> &a, int n, cudaStream_t s) {
+    launch_lbfgs_step_cta(a, n, r.MSY, r.MYY, device_sms(), s);  // compact form, CTA per walker
+}
+
 template <typename T>
 sb_status run_refine(const ProbView &pv, const sb_config *c, const RefineWs<T> &r, const double *starts, int n,
                      double *x_out, double *ell_out, int8_t *status_out, int32_t *iters_out, int64_t *n_evals,
@@ -373,7 +404,7 @@ sb_status run_refine(const ProbView &pv, const sb_config *c, const RefineWs<T> &
     while (true) {
         for (int b = 0; b < kRoundsPerPoll; ++b) {
             eval_round<T>(pv, c, rr, n, s);
-            launch_lbfgs_step<T>(a, n, s);
+            step_round<T>(rr, a, n, s);
             launch_lbfgs_compact<T>(a, ev, s);
         }
         round += kRoundsPerPoll;
@@ -420,12 +451,12 @@ sb_status run_laplace(const ProbView &pv, const sb_config *c, const Layout &L, c
     };
     eval_full();
     for (int step = 0; step < c->newton_steps; ++step) {
-        launch_chol_solve(d, cap, la.H, la.GC, la.n_reps, la.info, la.active, la.delta, s);
+        launch_chol_solve(d, cap, la.H, la.GC, la.n_reps, la.info, la.active, la.delta, la.pred, s);
         launch_newton_ls(d, cap, 0, la.n_reps, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
-                         la.delta, la.XN, la.LN, s);
+                         la.delta, la.XN, la.LN, la.pred, s);
         f64_points(pv, la.XN, nullptr, la.n_reps, cap, la.qpart, nullptr, nullptr, la.LN, nullptr, s);
         launch_newton_ls(d, cap, 1, la.n_reps, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
-                         la.delta, la.XN, la.LN, s);
+                         la.delta, la.XN, la.LN, la.pred, s);
         launch_ls_batch_setup(d, cap, la.n_reps, la.searching, la.XC, la.delta, la.XN2, la.rows2, la.n_rows2, s);
         f64_points(pv, la.XN2, la.rows2, la.n_rows2, cap * (kHalvings - 1), la.qpart2, nullptr, nullptr, la.LN2,
                    nullptr, s);
@@ -470,6 +501,7 @@ sb_status prelude(const sb_problem *p, const sb_config *c, void *ws, size_t ws_b
         for (int i = 0; i < 4; ++i) out.L.r32.tc.p[i] = out.L.di.tc.p[i];
         out.L.r32.tc.mapT = out.L.di.tc.mapT;
         out.L.r32.tc.mapB = out.L.di.tc.mapB;
+        if (!tc_maps_for_rows(out.L.r32.tc)) return SB_ERR_CUDA;
     }
     SB_CUDA_TRY(cudaGetLastError());
     return SB_OK;
@@ -727,5 +759,147 @@ extern "C" sb_status sb_evidence_stats(const sb_problem *p, const sb_config *c, 
     out[1] = ev;
     out[2] = nc;
     out[3] = nm;
+    return SB_OK;
+}
+
+// ------------------------------------------------------------------ adjoint
+namespace {
+struct BwdLayout {
+    WsHeader *hdr;
+    double *a, *c, *half, *logV, *wmax;
+    AdjWs adj;
+    size_t bytes;
+};
+BwdLayout bwd_layout(void *base, const sb_problem *p) {
+    BwdLayout B{};
+    Carver cv(base);
+    B.hdr = cv.take<WsHeader>(1);
+    B.a = cv.take<double>(p->K);
+    B.c = cv.take<double>(p->d);
+    B.half = cv.take<double>(p->d);
+    B.logV = cv.take<double>(1);
+    B.wmax = cv.take<double>(1);
+    adjoint_carve(cv, B.adj, p->d, p->K);
+    B.bytes = cv.bytes();
+    return B;
+}
+}  // namespace
+
+extern "C" size_t sb_evidence_backward_workspace_bytes(const sb_problem *p) {
+    if (check_problem(p) != SB_OK) return 0;
+    return bwd_layout(nullptr, p).bytes;
+}
+
+extern "C" sb_status sb_evidence_backward(const sb_problem *p, const double *modes, const double *logZk,
+                                          int32_t n_modes, double grad_logZ, double *dmu, double *dL, void *ws,
+                                          size_t ws_bytes, void *stream) {
+    sb_status st = check_problem(p);
+    if (st != SB_OK) return st;
+    if (!modes || !logZk || !dmu || !dL || !ws || n_modes < 1 || n_modes > kMaxAdjModes) return SB_ERR_INVALID_ARG;
+    const BwdLayout B = bwd_layout(ws, p);
+    if (ws_bytes < B.bytes) return SB_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SB_CUDA_TRY(cudaMemsetAsync(B.hdr, 0, sizeof(WsHeader), s));
+    ProbView pv{};
+    pv.d = p->d;
+    pv.K = p->K;
+    pv.log_w = p->log_w;
+    pv.mu = p->mu;
+    pv.L = p->L;
+    pv.lo = p->lo;
+    pv.hi = p->hi;
+    pv.a = B.a;
+    pv.c = B.c;
+    pv.half = B.half;
+    pv.logV = B.logV;
+    pv.wmax = B.wmax;
+    pv.status = &B.hdr->status;
+    launch_setup(pv, s);
+    return adjoint_run(pv, B.adj, modes, logZk, n_modes, grad_logZ, dmu, dL, s);
+}
+
+// ------------------------------------------------------------------ batched problems
+// Independent problems of uneven d and K run on `n_workers` worker streams,
+// each with its own host thread (the refine stage polls its stream) and its own
+// slice of the workspace; problem i goes to worker i % n_workers.
+namespace {
+size_t batched_slice_bytes(const sb_problem *probs, int32_t P, const sb_config *c) {
+    size_t mx = 0;
+    for (int32_t i = 0; i < P; ++i) {
+        const size_t b = layout(nullptr, &probs[i], c).bytes;
+        if (b > mx) mx = b;
+    }
+    // per-problem modes buffer [cand_cap][d_max] and logZk [cand_cap]
+    int dmax = 1;
+    for (int32_t i = 0; i < P; ++i) dmax = probs[i].d > dmax ? probs[i].d : dmax;
+    const size_t extra = ((size_t)c->cand_cap * dmax * sizeof(double) + 255) / 256 * 256 +
+                         ((size_t)c->cand_cap * sizeof(double) + 255) / 256 * 256;
+    return (mx + extra + 255) / 256 * 256;
+}
+}  // namespace
+
+extern "C" size_t sb_evidence_batched_workspace_bytes(const sb_problem *probs, int32_t P, const sb_config *c,
+                                                      int32_t n_workers) {
+    if (!probs || P < 1 || n_workers < 1 || check_config(c) != SB_OK) return 0;
+    for (int32_t i = 0; i < P; ++i)
+        if (check_problem(&probs[i]) != SB_OK) return 0;
+    const int32_t w = n_workers < P ? n_workers : P;
+    return (size_t)w * batched_slice_bytes(probs, P, c);
+}
+
+extern "C" sb_status sb_evidence_batched(const sb_problem *probs, int32_t P, const sb_config *c, double *logZ,
+                                         int32_t *n_modes, int32_t n_workers, void *ws, size_t ws_bytes,
+                                         void *stream) {
+    if (!probs || P < 1 || n_workers < 1 || !logZ || !n_modes || !ws) return SB_ERR_INVALID_ARG;
+    sb_status st = check_config(c);
+    if (st != SB_OK) return st;
+    for (int32_t i = 0; i < P; ++i) {
+        st = check_problem(&probs[i]);
+        if (st != SB_OK) return st;
+    }
+    const int32_t W = n_workers < P ? n_workers : P;
+    const size_t slice = batched_slice_bytes(probs, P, c);
+    if (ws_bytes < (size_t)W * slice) return SB_ERR_WORKSPACE;
+    cudaStream_t caller = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    SB_CUDA_TRY(cudaGetDevice(&dev));
+    cudaEvent_t ready;
+    SB_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    SB_CUDA_TRY(cudaEventRecord(ready, caller));
+    std::vector<sb_status> res(W, SB_OK);
+    std::vector<std::thread> pool;
+    for (int32_t w = 0; w < W; ++w) {
+        pool.emplace_back([&, w]() {
+            cudaSetDevice(dev);
+            cudaStream_t s;
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+                res[w] = SB_ERR_CUDA;
+                return;
+            }
+            cudaStreamWaitEvent(s, ready, 0);
+            char *base = static_cast<char *>(ws) + (size_t)w * slice;
+            Carver cv(base);
+            int dmax = 1;
+            for (int32_t i = 0; i < P; ++i) dmax = probs[i].d > dmax ? probs[i].d : dmax;
+            double *modes = cv.take<double>((size_t)c->cand_cap * dmax);
+            double *zk = cv.take<double>((size_t)c->cand_cap);
+            void *inner = base + cv.bytes();
+            const size_t inner_bytes = slice - cv.bytes();
+            for (int32_t i = w; i < P; i += W) {
+                const sb_status r = sb_evidence(&probs[i], c, logZ + i, modes, zk, c->cand_cap, n_modes + i, inner,
+                                                inner_bytes, s);
+                if (r != SB_OK) {
+                    res[w] = r;
+                    break;
+                }
+            }
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        });
+    }
+    for (auto &t : pool) t.join();
+    cudaEventDestroy(ready);
+    for (auto r : res)
+        if (r != SB_OK) return r;
     return SB_OK;
 }

@@ -16,10 +16,10 @@ void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P
                          const double *gbar, const int32_t *n_c, double *GK, double *H, int32_t *info,
                          cudaStream_t s);
 void launch_chol_solve(int d, int cap, const double *H, const double *g, const int32_t *n_c, const int32_t *info,
-                       const uint8_t *active, double *delta, cudaStream_t s);
+                       const uint8_t *active, double *delta, double *pred, cudaStream_t s);
 void launch_newton_ls(int d, int cap, int mode, const int32_t *n_c, const int32_t *info, uint8_t *active,
                       uint8_t *searching, int32_t *halvings, double *t, double *XC, double *LC, const double *delta,
-                      double *XN, const double *LN, cudaStream_t s);
+                      double *XN, const double *LN, const double *pred, cudaStream_t s);
 // Batched halvings h = 1..kHalvings-1 for the candidates still searching after t = 1.
 void launch_ls_batch_setup(int d, int cap, const int32_t *n_c, const uint8_t *searching, const double *XC,
                            const double *delta, double *XN2, int32_t *rows2, int32_t *n_rows2, cudaStream_t s);

@@ -37,6 +37,9 @@ template <typename T>
 void launch_lbfgs_step(const LbfgsArgs<T> &a, int n, cudaStream_t s);
 template <typename T>
 void launch_lbfgs_compact(const LbfgsArgs<T> &a, int64_t *n_evals, cudaStream_t s);
+// FP32 step, one CTA per walker, compact-representation direction (lbfgs_cta.cu).
+void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *MYY, int num_sms, cudaStream_t s);
+
 template <typename T>
 void launch_lbfgs_finish(int n, int d, const LbfgsArgs<T> &a, double *x_out, double *ell_out, int8_t *status_out,
                          int32_t *iters_out, int32_t *dev_status, cudaStream_t s);

@@ -12,17 +12,20 @@ namespace sb {
 struct TcWs {
     void *p[16];
     size_t rows;
-    int prec, bn;
-    CUtensorMap mapT, mapB;
+    int prec, bn, d, K, ldz;
+    CUtensorMap mapT, mapB;    // B operands: L_k^T (GEMM1) and L_k (GEMM2)
+    CUtensorMap mapA1, mapZ;   // A operands: centred points (GEMM1) and scaled z (GEMM2)
 };
 
 bool tc_available(int prec);
 void carve_tc(Carver &cv, TcWs &t, int rows, int d, int K, int prec);
 int tc_ray_chunk(int d, int K, int64_t total);
+// Encodes the A-operand tensor maps of this scratch (depends on its row capacity).
+bool tc_maps_for_rows(TcWs &t);
 // Converts L_k / mu / c into the tensor-core copies and encodes the tensor maps.
 sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s);
-sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const double *u, const double *texit,
-                        double *ell_all, cudaStream_t s);
+sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const double *u, float *u32,
+                        const double *texit, double *ell_all, cudaStream_t s);
 void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, const float *XT, const int32_t *act,
                      const int32_t *n_act, int n, float *FT, float *GT, cudaStream_t s);
 sb_status tc_loglik_points(const ProbView &pv, const sb_config *c, const TcWs &t, const double *x, int n, float *f,

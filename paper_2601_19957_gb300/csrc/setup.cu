@@ -36,6 +36,19 @@ struct OrOp {
     __device__ int operator()(int a, int b) const { return a | b; }
 };
 
+// Finiteness of the lower triangles of all L_k, spread over many blocks.
+__global__ void __launch_bounds__(256) k_check_L(ProbView pv) {
+    const int d = pv.d;
+    const size_t tot = (size_t)pv.K * d * d;
+    int bad = 0;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = e % ((size_t)d * d);
+        const int i = (int)(r / d), j = (int)(r % d);
+        if (j <= i && !isfinite(pv.L[e])) bad = 1;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(pv.status, SB_DEV_NONFINITE);
+}
+
 __global__ void __launch_bounds__(256) k_setup(ProbView pv) {
     __shared__ double shd[32];
     __shared__ int shi[32];
@@ -72,11 +85,6 @@ __global__ void __launch_bounds__(256) k_setup(ProbView pv) {
             s += log(l);
             if (!isfinite(pv.mu[(size_t)k * d + i])) bad |= SB_DEV_NONFINITE;
         }
-        // lower triangle finite
-        for (size_t e = threadIdx.x; e < (size_t)d * d; e += blockDim.x) {
-            const int i = (int)(e / d), j = (int)(e % d);
-            if (j <= i && !isfinite(Lk[e])) bad |= SB_DEV_NONFINITE;
-        }
         s = block_reduce(s, AddOp(), shd, 0.0);
         bad = block_reduce(bad, OrOp(), shi, 0);
         if (threadIdx.x == 0) {
@@ -91,6 +99,11 @@ __global__ void __launch_bounds__(256) k_setup(ProbView pv) {
 void launch_setup(const ProbView &pv, cudaStream_t s) {
     note_launch();
     k_setup<<<pv.K + 1, 256, 0, s>>>(pv);
+    const size_t tot = (size_t)pv.K * pv.d * pv.d;
+    size_t blocks = (tot + 1023) / 1024;
+    if (blocks > 1184) blocks = 1184;
+    note_launch();
+    k_check_L<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(pv);
 }
 
 }  // namespace sb

@@ -7,21 +7,27 @@
 //   GEMM2  g_n[i]   = sum_k sum_{j<=i} (r_nk z_nk[j]) L_k[i][j] M = points, N = i, K = (k, j)
 // g_n is grad f for f = -l (Sec. 3.2 likelihood, analytic gradient for App. A.5).
 //
-// Kernel anatomy (one persistent CTA per SM, 10 warps):
-//   warps 0-3  build the A tile of each K chunk in shared memory: GEMM1 gathers
-//              x rows (walkers through the active list, or ray samples
-//              c + t u generated on the fly), subtracts mu_k in FP32 and rounds
-//              to bf16 / tf32; GEMM2 scales the stored z rows by r_nk. The tile
-//              is written in the 128-byte-swizzled K-major layout the MMA reads.
-//   warp 4     TMA loads of the L_k tile (3-D tensor map, OOB rows zero-filled).
-//   warp 5     allocates TMEM and issues tcgen05.mma (M=128, N=BN, 4 per chunk).
-//   warps 6-9  drain the FP32 accumulator from TMEM (tcgen05.ld) into the
-//              epilogue: |z|^2 partials and z (GEMM1), or grad f rows (GEMM2).
-// Two TMEM accumulator buffers let the epilogue of one tile overlap the MMAs
-// of the next. Only the triangle occupied by L_k is visited (K chunks i >= j0
-// for GEMM1, j < i0 + BN for GEMM2). Every mbarrier wait is bounded: on
-// timeout the CTA raises SB_DEV_TIMEOUT, drains its TMA loads and MMAs, frees
-// TMEM and exits.
+// Data flow per evaluation round:
+//   k_tc_center   A1[k][n][:] = round(x_n - mu_k), formed in FP32 (walkers gathered
+//                 through the active list, or ray samples c + t u), bf16 or tf32
+//   k_tc_gemm Z   z = A1 L_k (GEMM1): |z|^2 partials, z rows stored [k][n][:]
+//   k_tc_lse      l, r (FP64 reduction)
+//   k_tc_scale    z[k][n][:] *= r_nk in place -> A2 of GEMM2
+//   k_tc_gemm G   grad f = sum_k A2_k L_k^T rows (GEMM2)
+// Both operands of both GEMMs reach shared memory by TMA (3-D tensor maps,
+// 128-byte swizzle, out-of-range rows/columns zero-filled), so the MMA
+// pipeline never waits on a gathered load. Centring before rounding keeps the
+// stationary point: at x = mu_k the A operand is exactly zero.
+//
+// Kernel anatomy (one persistent CTA per SM, 6 warps): warp 0 issues the TMA
+// loads of A and B for each 128-byte K chunk; warp 1 allocates TMEM and issues
+// tcgen05.mma (M=128, N=BN<=256, four per chunk) with tcgen05.commit to the
+// stage's empty barrier; warps 2-5 drain the FP32 accumulator with
+// tcgen05.ld (one thread per row). Two TMEM accumulators let the epilogue of
+// one tile overlap the MMAs of the next. Only the triangle occupied by L_k is
+// visited (K chunks i >= j0 for GEMM1, j < i0 + BN for GEMM2). Every mbarrier
+// wait is bounded: on timeout the CTA raises SB_DEV_TIMEOUT, lets its issued
+// TMA loads and MMAs land, frees TMEM and exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -36,9 +42,10 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int ROWB = 128;  // bytes of one K chunk per row (one swizzle atom row)
-constexpr int THREADS = 320;
+constexpr int THREADS = 192;
 constexpr long long kSpinLimit = 1ll << 24;
 
+// MODE_ZW: GEMM1 storing z (walkers/points); MODE_ZR: GEMM1 values only (ray samples); MODE_G: GEMM2
 enum { MODE_ZW = 0, MODE_ZR = 1, MODE_G = 2 };
 
 struct TcArgs {
@@ -49,12 +56,13 @@ struct TcArgs {
     const float *X;         // walker points (FP32)
     const float *mu32;      // [K][d]
     const float *c32;       // [d] box centre
-    const double *u;        // [n_rays][d] ray directions
+    const double *u;        // [n_rays][d] ray directions (FP64)
+    const float *u32;       // [n_rays][d] ray directions (FP32 copy read by the producers)
     const double *texit;    // [n_rays]
     int n_steps;
     long long flat0;
-    void *Z;                // [rows][K][ldz] (bf16 or fp32)
-    int ldz;
+    void *Z;                // [K][z_rows][ldz] z rows, component-major (bf16 or fp32)
+    int ldz, z_rows;
     float *qpart;           // [rows][K][n_ntile]
     const float *R;         // [rows][K]
     float *G;               // [walkers][d] grad f
@@ -195,8 +203,10 @@ __device__ __forceinline__ TileInfo decode_tile(int t, int d, int K) {
         ti.c_hi = (jmax + KC - 1) / KC;
         ti.nchunks = K * ti.c_hi;
     } else {
-        ti.k = t % K;
-        ti.nt = (t / K) % nct;
+        // column tiles of one (row block, component) are adjacent in the schedule, so
+        // CTAs that run together gather the same x rows (served from L2)
+        ti.nt = t % nct;
+        ti.k = (t / nct) % K;
         ti.mb = t / (K * nct);
         ti.c_lo = (ti.nt * BN) / KC;
         ti.c_hi = (d + KC - 1) / KC;
@@ -207,7 +217,8 @@ __device__ __forceinline__ TileInfo decode_tile(int t, int d, int K) {
 
 // ------------------------------------------------------------------ the kernel
 template <int BN, int PREC, int MODE>
-__global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmapB, TcArgs a) {
+__global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmapA,
+                                                        const __grid_constant__ CUtensorMap tmapB, TcArgs a) {
     constexpr int KC = (PREC == SB_PREC_BF16) ? 64 : 32;  // elements per 128-byte chunk row
     constexpr int STAGES = (BN >= 256) ? 4 : 6;
     constexpr int A_BYTES = BM * ROWB;
@@ -219,16 +230,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * A_BYTES;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sB + STAGES * B_BYTES);
-    uint64_t *full_a = bars;
-    uint64_t *full_b = bars + STAGES;
-    uint64_t *empty = bars + 2 * STAGES;
-    uint64_t *tfull = bars + 3 * STAGES;
+    uint64_t *full = bars;
+    uint64_t *empty = bars + STAGES;
+    uint64_t *tfull = bars + 2 * STAGES;
     uint64_t *tempty = tfull + 2;
     uint64_t *drain = tempty + 2;
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(drain + 1);
     volatile int *s_abort = reinterpret_cast<volatile int *>(s_tmem + 1);
-    int *s_row = const_cast<int *>(reinterpret_cast<volatile int *>(s_abort + 1));  // [BM] per-row source
-    float *s_scale = reinterpret_cast<float *>(s_row + BM);                          // [BM] ray t * t_exit
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int d = a.d, K = a.K;
@@ -239,8 +247,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full_a[s], 4);
-            mbar_init(&full_b[s], 1);
+            mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         for (int s = 0; s < 2; ++s) {
@@ -251,7 +258,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
                      "r"(2 * BN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -261,181 +268,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
 
-    if (warp < 4) {
-        // ---------------------------------------------------------- A producers
-        int stage = 0;
-        uint32_t phase = 0;
-        const int sub = lane >> 4;          // bf16: lanes 0-15 row r, 16-31 row r+1
-        const int l16 = lane & 15;
-        for (int t = blockIdx.x; t < n_tiles && !warp_aborted(s_abort); t += gridDim.x) {
-            const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K);
-            // per-row sources of this warp's 32 rows
-            {
-                const int r = warp * 32 + lane;
-                const int n = ti.mb * BM + r;
-                int src = -1;
-                float sc = 0.f;
-                if (n < n_rows) {
-                    if (MODE == MODE_ZW) {
-                        src = a.act ? a.act[n] : n;
-                    } else if (MODE == MODE_ZR) {
-                        const long long flat = a.flat0 + n;
-                        const int ray = (int)(flat / a.n_steps), j = (int)(flat % a.n_steps);
-                        src = ray;
-                        sc = (float)(((double)(j + 1) / (double)a.n_steps) * a.texit[ray]);
-                    } else {
-                        src = n;
-                    }
-                }
-                s_row[r] = src;
-                s_scale[r] = sc;
-            }
-            __syncwarp();
-            for (int q = 0; q < ti.nchunks; ++q) {
-                int kk, c0;
-                if (MODE == MODE_G) {
-                    kk = q / ti.c_hi;
-                    c0 = (q % ti.c_hi) * KC;
-                } else {
-                    kk = ti.k;
-                    c0 = (ti.c_lo + q) * KC;
-                }
-                if (!warp_bwait(&empty[stage], phase ^ 1, s_abort)) break;
-                uint8_t *tile = sA + stage * A_BYTES;
-                if (PREC == SB_PREC_BF16) {
-                    // each lane: 4 consecutive columns (8 bytes of the swizzled row)
-                    const int col = c0 + 4 * l16;
-                    float m4[4] = {0.f, 0.f, 0.f, 0.f}, c4[4] = {0.f, 0.f, 0.f, 0.f};
-                    if (MODE != MODE_G) {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (col + e < d) {
-                                m4[e] = a.mu32[(size_t)kk * d + col + e];
-                                if (MODE == MODE_ZR) c4[e] = a.c32[col + e];
-                            }
-                    }
-#pragma unroll 4
-                    for (int rr = 0; rr < 16; ++rr) {
-                        const int r = warp * 32 + 2 * rr + sub;
-                        const int src = s_row[r];
-                        float v[4] = {0.f, 0.f, 0.f, 0.f};
-                        if (src >= 0) {
-                            if (MODE == MODE_ZW) {
-                                const float *xr = a.X + (size_t)src * a.ld;
-                                if (((a.ld & 3) == 0) && col + 3 < d) {
-                                    const float4 x4 = *reinterpret_cast<const float4 *>(xr + col);
-                                    v[0] = x4.x - m4[0];
-                                    v[1] = x4.y - m4[1];
-                                    v[2] = x4.z - m4[2];
-                                    v[3] = x4.w - m4[3];
-                                } else {
-#pragma unroll
-                                    for (int e = 0; e < 4; ++e)
-                                        if (col + e < d) v[e] = xr[col + e] - m4[e];
-                                }
-                            } else if (MODE == MODE_ZR) {
-                                const double *ur = a.u + (size_t)src * d;
-                                const float sc = s_scale[r];
-#pragma unroll
-                                for (int e = 0; e < 4; ++e)
-                                    if (col + e < d) v[e] = (c4[e] + sc * (float)ur[col + e]) - m4[e];
-                            } else {
-                                const float rk = a.R[(size_t)src * K + kk];
-                                if (rk != 0.f) {
-                                    const __nv_bfloat16 *zr = reinterpret_cast<const __nv_bfloat16 *>(a.Z) +
-                                                              ((size_t)src * K + kk) * a.ldz;
-                                    if (col + 3 < a.ldz) {
-                                        const uint2 z2 = *reinterpret_cast<const uint2 *>(zr + col);
-                                        const __nv_bfloat162 p0 = *reinterpret_cast<const __nv_bfloat162 *>(&z2.x);
-                                        const __nv_bfloat162 p1 = *reinterpret_cast<const __nv_bfloat162 *>(&z2.y);
-                                        v[0] = __low2float(p0) * rk;
-                                        v[1] = __high2float(p0) * rk;
-                                        v[2] = __low2float(p1) * rk;
-                                        v[3] = __high2float(p1) * rk;
-                                    }
-                                    if (col + 3 >= d) {
-#pragma unroll
-                                        for (int e = 0; e < 4; ++e)
-                                            if (col + e >= d) v[e] = 0.f;
-                                    }
-                                }
-                            }
-                        }
-                        uint2 packed;
-                        packed.x = pack_bf16x2(v[0], v[1]);
-                        packed.y = pack_bf16x2(v[2], v[3]);
-                        const int chunk = (l16 >> 1) ^ (r & 7);
-                        *reinterpret_cast<uint2 *>(tile + r * ROWB + chunk * 16 + (l16 & 1) * 8) = packed;
-                    }
-                } else {
-                    // TF32: each lane 4 columns = one 16-byte chunk; 4 rows per warp step
-                    const int l8 = lane & 7, sub4 = lane >> 3;
-                    const int col = c0 + 4 * l8;
-                    float m4[4] = {0.f, 0.f, 0.f, 0.f}, c4[4] = {0.f, 0.f, 0.f, 0.f};
-                    if (MODE != MODE_G) {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (col + e < d) {
-                                m4[e] = a.mu32[(size_t)kk * d + col + e];
-                                if (MODE == MODE_ZR) c4[e] = a.c32[col + e];
-                            }
-                    }
-#pragma unroll 2
-                    for (int rr = 0; rr < 8; ++rr) {
-                        const int r = warp * 32 + 4 * rr + sub4;
-                        const int src = s_row[r];
-                        float v[4] = {0.f, 0.f, 0.f, 0.f};
-                        if (src >= 0) {
-                            if (MODE == MODE_ZW) {
-                                const float *xr = a.X + (size_t)src * a.ld;
-                                if (((a.ld & 3) == 0) && col + 3 < d) {
-                                    const float4 x4 = *reinterpret_cast<const float4 *>(xr + col);
-                                    v[0] = x4.x - m4[0];
-                                    v[1] = x4.y - m4[1];
-                                    v[2] = x4.z - m4[2];
-                                    v[3] = x4.w - m4[3];
-                                } else {
-#pragma unroll
-                                    for (int e = 0; e < 4; ++e)
-                                        if (col + e < d) v[e] = xr[col + e] - m4[e];
-                                }
-                            } else if (MODE == MODE_ZR) {
-                                const double *ur = a.u + (size_t)src * d;
-                                const float sc = s_scale[r];
-#pragma unroll
-                                for (int e = 0; e < 4; ++e)
-                                    if (col + e < d) v[e] = (c4[e] + sc * (float)ur[col + e]) - m4[e];
-                            } else {
-                                const float rk = a.R[(size_t)src * K + kk];
-                                if (rk != 0.f) {
-                                    const float *zr =
-                                        reinterpret_cast<const float *>(a.Z) + ((size_t)src * K + kk) * a.ldz;
-#pragma unroll
-                                    for (int e = 0; e < 4; ++e)
-                                        if (col + e < d) v[e] = zr[col + e] * rk;
-                                }
-                            }
-                        }
-                        float4 o;
-                        o.x = to_tf32(v[0]);
-                        o.y = to_tf32(v[1]);
-                        o.z = to_tf32(v[2]);
-                        o.w = to_tf32(v[3]);
-                        const int chunk = l8 ^ (r & 7);
-                        *reinterpret_cast<float4 *>(tile + r * ROWB + chunk * 16) = o;
-                    }
-                }
-                fence_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&full_a[stage]);
-                if (++stage == STAGES) {
-                    stage = 0;
-                    phase ^= 1;
-                }
-            }
-        }
-    } else if (warp == 4) {
-        // ---------------------------------------------------------- TMA loads of L_k tiles
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA loads of A and B
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
@@ -450,14 +284,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                         ok = false;
                         break;
                     }
-                    mbar_arrive_tx(&full_b[stage], B_BYTES);
+                    mbar_arrive_tx(&full[stage], A_BYTES + B_BYTES);
+                    int kk, c0;
                     if (MODE == MODE_G) {
-                        const int kk = q / ti.c_hi, j0 = (q % ti.c_hi) * KC;
-                        tma_load_3d(sB + stage * B_BYTES, &tmapB, &full_b[stage], j0, ti.nt * BN, kk);
+                        kk = q / ti.c_hi;
+                        c0 = (q % ti.c_hi) * KC;
                     } else {
-                        tma_load_3d(sB + stage * B_BYTES, &tmapB, &full_b[stage], (ti.c_lo + q) * KC, ti.nt * BN,
-                                    ti.k);
+                        kk = ti.k;
+                        c0 = (ti.c_lo + q) * KC;
                     }
+                    tma_load_3d(sA + stage * A_BYTES, &tmapA, &full[stage], c0, ti.mb * BM, kk);
+                    tma_load_3d(sB + stage * B_BYTES, &tmapB, &full[stage], c0, ti.nt * BN, kk);
                     inflight_stage[n_inflight % 8] = stage;
                     inflight_phase[n_inflight % 8] = phase;
                     ++n_inflight;
@@ -473,11 +310,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                 const int first = n_inflight > STAGES ? n_inflight - STAGES : 0;
                 for (int q = first; q < n_inflight; ++q) {
                     volatile int never = 0;
-                    bwait(&full_b[inflight_stage[q % 8]], inflight_phase[q % 8], &never);
+                    bwait(&full[inflight_stage[q % 8]], inflight_phase[q % 8], &never);
                 }
             }
         }
-    } else if (warp == 5) {
+        __syncwarp();
+    } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issue
         if (lane == 0) {
             int stage = 0;
@@ -492,7 +330,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                 const uint32_t dt = tmem + (uint32_t)(acc * BN);
                 bool ok = true;
                 for (int q = 0; q < ti.nchunks; ++q) {
-                    if (!bwait(&full_a[stage], phase, s_abort) || !bwait(&full_b[stage], phase, s_abort)) {
+                    if (!bwait(&full[stage], phase, s_abort)) {
                         ok = false;
                         break;
                     }
@@ -526,7 +364,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         }
         __syncwarp();
     } else {
-        // ---------------------------------------------------------- epilogue
+        // ---------------------------------------------------------- epilogue (warps 2-5)
         const int quad = warp & 3;
         const int r = quad * 32 + lane;
         int acc = 0;
@@ -567,9 +405,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                         q2 = fmaf(z, z, q2);
                     }
                     if (MODE == MODE_ZW && valid && col < a.ldz) {
+                        const size_t zrow = ((size_t)ti.k * a.z_rows + n) * a.ldz + col;
                         if (PREC == SB_PREC_BF16) {
-                            __nv_bfloat16 *zr =
-                                reinterpret_cast<__nv_bfloat16 *>(a.Z) + ((size_t)n * K + ti.k) * a.ldz + col;
+                            __nv_bfloat16 *zr = reinterpret_cast<__nv_bfloat16 *>(a.Z) + zrow;
 #pragma unroll
                             for (int e = 0; e < 32; e += 8) {
                                 if (col + e + 8 <= a.ldz) {
@@ -582,7 +420,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                                 }
                             }
                         } else {
-                            float *zr = reinterpret_cast<float *>(a.Z) + ((size_t)n * K + ti.k) * a.ldz + col;
+                            float *zr = reinterpret_cast<float *>(a.Z) + zrow;
 #pragma unroll
                             for (int e = 0; e < 32; e += 4)
                                 if (col + e + 4 <= a.ldz)
@@ -607,7 +445,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
     tc_fence_before();
     __syncthreads();
     if (*s_abort && threadIdx.x == 0) atomicOr(a.err, SB_DEV_TIMEOUT);
-    if (warp == 5) {
+    if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
     }
@@ -644,6 +482,123 @@ __global__ void __launch_bounds__(256) k_tc_lse(int mode, int K, int n_ntile, co
         FT[act ? act[n] : n] = (float)(-l);
     else
         ell[n] = l;
+}
+
+// A operand of GEMM1: A1[k][n][i] = round(x_n[i] - mu_k[i]) formed in FP32; x_n is a
+// walker row (through the active list) or the ray sample c + t_j t_exit u_r.
+// Rows from n_rows up to the next multiple of 128 and columns >= d are zeroed.
+template <int PREC>
+__global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int K, int rows_cap, int ldp,
+                                                   const int32_t *n_rows_dev, int n_rows_max, const int32_t *act,
+                                                   const float *X, int ld, const float *u32, const double *texit,
+                                                   int n_steps, long long flat0, const float *mu32, const float *c32,
+                                                   void *A1) {
+    constexpr int VE = (PREC == SB_PREC_BF16) ? 8 : 4;  // elements per 16-byte store
+    const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
+    int rows_pad = (n_rows + BM - 1) / BM * BM;
+    if (rows_pad > rows_cap) rows_pad = rows_cap;
+    const int ncg = ldp / VE;
+    const long long total = (long long)K * rows_pad * ncg;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int cg = (int)(e % ncg);
+        const long long kn = e / ncg;
+        const int n = (int)(kn % rows_pad);
+        const int k = (int)(kn / rows_pad);
+        const int i0 = cg * VE;
+        float v[VE];
+#pragma unroll
+        for (int q = 0; q < VE; ++q) v[q] = 0.f;
+        if (n < n_rows) {
+            if (!ray_mode) {
+                const float *xr = X + (size_t)(act ? act[n] : n) * ld;
+                if ((ld & 3) == 0 && i0 + VE <= d) {
+#pragma unroll
+                    for (int q = 0; q < VE; q += 4) {
+                        const float4 x4 = *reinterpret_cast<const float4 *>(xr + i0 + q);
+                        v[q] = x4.x;
+                        v[q + 1] = x4.y;
+                        v[q + 2] = x4.z;
+                        v[q + 3] = x4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < VE; ++q)
+                        if (i0 + q < d) v[q] = xr[i0 + q];
+                }
+            } else {
+                const long long flat = flat0 + n;
+                const int ray = (int)(flat / n_steps), j = (int)(flat % n_steps);
+                const float sc = (float)(((double)(j + 1) / (double)n_steps) * texit[ray]);
+                const float *ur = u32 + (size_t)ray * d;
+#pragma unroll
+                for (int q = 0; q < VE; ++q)
+                    if (i0 + q < d) v[q] = fmaf(sc, ur[i0 + q], c32[i0 + q]);
+            }
+            const float *mk = mu32 + (size_t)k * d;
+#pragma unroll
+            for (int q = 0; q < VE; ++q)
+                if (i0 + q < d)
+                    v[q] -= mk[i0 + q];
+                else
+                    v[q] = 0.f;
+        }
+        const size_t o = ((size_t)k * rows_cap + n) * ldp + i0;
+        if (PREC == SB_PREC_BF16) {
+            uint4 p;
+            p.x = pack_bf16x2(v[0], v[1]);
+            p.y = pack_bf16x2(v[2], v[3]);
+            p.z = pack_bf16x2(v[4], v[5]);
+            p.w = pack_bf16x2(v[6], v[7]);
+            *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(A1) + o) = p;
+        } else {
+            *reinterpret_cast<float4 *>(reinterpret_cast<float *>(A1) + o) =
+                make_float4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
+        }
+    }
+}
+
+// A operand of GEMM2 in place: z[k][n][:] *= r_nk (rows up to the next multiple of 128 zeroed).
+template <int PREC>
+__global__ void __launch_bounds__(256) k_tc_scale(int K, int rows_cap, int ldz, const int32_t *n_rows_dev,
+                                                  int n_rows_max, const float *R, void *Z) {
+    constexpr int VE = (PREC == SB_PREC_BF16) ? 8 : 4;
+    const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
+    int rows_pad = (n_rows + BM - 1) / BM * BM;
+    if (rows_pad > rows_cap) rows_pad = rows_cap;
+    const int ncg = ldz / VE;
+    const long long total = (long long)K * rows_pad * ncg;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int cg = (int)(e % ncg);
+        const long long kn = e / ncg;
+        const int n = (int)(kn % rows_pad);
+        const int k = (int)(kn / rows_pad);
+        const size_t o = ((size_t)k * rows_cap + n) * ldz + (size_t)cg * VE;
+        if (n >= n_rows) {  // padding rows hold stale values (possibly NaN): overwrite, never scale
+            if (PREC == SB_PREC_BF16)
+                *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(Z) + o) = make_uint4(0u, 0u, 0u, 0u);
+            else
+                *reinterpret_cast<float4 *>(reinterpret_cast<float *>(Z) + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        const float r = R[(size_t)n * K + k];
+        if (PREC == SB_PREC_BF16) {
+            uint4 *pz = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(Z) + o);
+            uint4 p = *pz;
+            uint32_t w[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[q]);
+                w[q] = pack_bf16x2(__low2float(h) * r, __high2float(h) * r);
+            }
+            *pz = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+            float4 *pz = reinterpret_cast<float4 *>(reinterpret_cast<float *>(Z) + o);
+            const float4 v = *pz;
+            *pz = make_float4(to_tf32(v.x * r), to_tf32(v.y * r), to_tf32(v.z * r), to_tf32(v.w * r));
+        }
+    }
 }
 
 template <typename E>
@@ -719,16 +674,16 @@ inline int esz(int prec) { return prec == SB_PREC_BF16 ? 2 : 4; }
 inline int ldp_of(int d, int prec) { return prec == SB_PREC_BF16 ? (d + 7) / 8 * 8 : (d + 3) / 4 * 4; }
 inline int bn_of(int d) { return d > 128 ? 256 : (d > 64 ? 128 : 64); }
 inline int ldz_of(int d) { return (d + 63) / 64 * 64; }
+inline int ldz_of_t(const TcWs &t) { return t.ldz; }
 
-// 3-D map over [K][d rows][ldp] with box (128 bytes of K, BN rows, 1).
-bool make_map(CUtensorMap *m, void *base, int d, int K, int prec, int bn) {
+// 3-D map over [dim2][dim1][stride1] elements with box (128 bytes of dim0, box1 rows, 1).
+bool make_map(CUtensorMap *m, void *base, int dim0, int dim1, int dim2, int stride1, int prec, int box1) {
     auto fn = encode_fn();
     if (!fn) return false;
     const int e = esz(prec);
-    const int ldp = ldp_of(d, prec);
-    cuuint64_t dims[3] = {(cuuint64_t)d, (cuuint64_t)d, (cuuint64_t)K};
-    cuuint64_t strides[2] = {(cuuint64_t)ldp * e, (cuuint64_t)ldp * e * d};
-    cuuint32_t box[3] = {(cuuint32_t)(128 / e), (cuuint32_t)bn, 1};
+    cuuint64_t dims[3] = {(cuuint64_t)dim0, (cuuint64_t)dim1, (cuuint64_t)dim2};
+    cuuint64_t strides[2] = {(cuuint64_t)stride1 * e, (cuuint64_t)stride1 * e * dim1};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / e), (cuuint32_t)box1, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt =
         prec == SB_PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -739,11 +694,11 @@ bool make_map(CUtensorMap *m, void *base, int d, int K, int prec, int bn) {
 template <int BN, int PREC, int MODE>
 constexpr int smem_bytes() {
     constexpr int STAGES = (BN >= 256) ? 4 : 6;
-    return 1024 + STAGES * (BM * ROWB + BN * ROWB) + (3 * STAGES + 5) * 8 + 16 + BM * 8 + 64;
+    return 1024 + STAGES * (BM * ROWB + BN * ROWB) + (2 * STAGES + 5) * 8 + 64;
 }
 
 template <int BN, int PREC, int MODE>
-void launch_gemm(const CUtensorMap &map, const TcArgs &a, cudaStream_t s) {
+void launch_gemm(const CUtensorMap &mapA, const CUtensorMap &map, const TcArgs &a, cudaStream_t s) {
     constexpr int SM = smem_bytes<BN, PREC, MODE>();
     static std::once_flag once;
     std::call_once(once, [] {
@@ -756,29 +711,67 @@ void launch_gemm(const CUtensorMap &map, const TcArgs &a, cudaStream_t s) {
     if (tiles < grid) grid = (int)(tiles > 0 ? tiles : 1);
     ProfScope prof(MODE == MODE_ZW ? PROF_TC_Z_WALKERS : (MODE == MODE_ZR ? PROF_TC_Z_RAYS : PROF_TC_GRAD), s);
     note_launch();
-    k_tc_gemm<BN, PREC, MODE><<<grid, THREADS, SM, s>>>(map, a);
+    k_tc_gemm<BN, PREC, MODE><<<grid, THREADS, SM, s>>>(mapA, map, a);
 }
 
 template <int PREC, int MODE>
-void launch_gemm_bn(int bn, const CUtensorMap &map, const TcArgs &a, cudaStream_t s) {
+void launch_gemm_bn(int bn, const CUtensorMap &mapA, const CUtensorMap &map, const TcArgs &a, cudaStream_t s) {
     if (bn == 256)
-        launch_gemm<256, PREC, MODE>(map, a, s);
+        launch_gemm<256, PREC, MODE>(mapA, map, a, s);
     else if (bn == 128)
-        launch_gemm<128, PREC, MODE>(map, a, s);
+        launch_gemm<128, PREC, MODE>(mapA, map, a, s);
     else
-        launch_gemm<64, PREC, MODE>(map, a, s);
+        launch_gemm<64, PREC, MODE>(mapA, map, a, s);
 }
 
-void launch_gemm_any(int prec, int mode, int bn, const CUtensorMap &map, const TcArgs &a, cudaStream_t s) {
+void launch_gemm_any(int prec, int mode, int bn, const CUtensorMap &mapA, const CUtensorMap &map, const TcArgs &a,
+                     cudaStream_t s) {
     if (prec == SB_PREC_BF16) {
-        if (mode == MODE_ZW) launch_gemm_bn<SB_PREC_BF16, MODE_ZW>(bn, map, a, s);
-        else if (mode == MODE_ZR) launch_gemm_bn<SB_PREC_BF16, MODE_ZR>(bn, map, a, s);
-        else launch_gemm_bn<SB_PREC_BF16, MODE_G>(bn, map, a, s);
+        if (mode == MODE_ZW) launch_gemm_bn<SB_PREC_BF16, MODE_ZW>(bn, mapA, map, a, s);
+        else if (mode == MODE_ZR) launch_gemm_bn<SB_PREC_BF16, MODE_ZR>(bn, mapA, map, a, s);
+        else launch_gemm_bn<SB_PREC_BF16, MODE_G>(bn, mapA, map, a, s);
     } else {
-        if (mode == MODE_ZW) launch_gemm_bn<SB_PREC_TF32, MODE_ZW>(bn, map, a, s);
-        else if (mode == MODE_ZR) launch_gemm_bn<SB_PREC_TF32, MODE_ZR>(bn, map, a, s);
-        else launch_gemm_bn<SB_PREC_TF32, MODE_G>(bn, map, a, s);
+        if (mode == MODE_ZW) launch_gemm_bn<SB_PREC_TF32, MODE_ZW>(bn, mapA, map, a, s);
+        else if (mode == MODE_ZR) launch_gemm_bn<SB_PREC_TF32, MODE_ZR>(bn, mapA, map, a, s);
+        else launch_gemm_bn<SB_PREC_TF32, MODE_G>(bn, mapA, map, a, s);
     }
+}
+
+unsigned grid_for(long long items) {
+    long long g = (items + 255) / 256;
+    const long long cap = (long long)num_sms() * 8;
+    if (g > cap) g = cap;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+void launch_center(const TcWs &t, int ray_mode, int d, int K, const int32_t *n_rows_dev, int n_rows_max,
+                   const int32_t *act, const float *X, const float *u32, const double *texit, int n_steps,
+                   long long flat0, cudaStream_t s) {
+    const int ldp = ldp_of(d, t.prec);
+    const long long items = (long long)K * t.rows * (ldp / (t.prec == SB_PREC_BF16 ? 8 : 4));
+    note_launch();
+    if (t.prec == SB_PREC_BF16)
+        k_tc_center<SB_PREC_BF16><<<grid_for(items), 256, 0, s>>>(ray_mode, d, K, (int)t.rows, ldp, n_rows_dev,
+                                                                 n_rows_max, act, X, d, u32, texit, n_steps, flat0,
+                                                                 (const float *)t.p[2], (const float *)t.p[3],
+                                                                 t.p[9]);
+    else
+        k_tc_center<SB_PREC_TF32><<<grid_for(items), 256, 0, s>>>(ray_mode, d, K, (int)t.rows, ldp, n_rows_dev,
+                                                                 n_rows_max, act, X, d, u32, texit, n_steps, flat0,
+                                                                 (const float *)t.p[2], (const float *)t.p[3],
+                                                                 t.p[9]);
+}
+
+void launch_scale(const TcWs &t, int K, const int32_t *n_rows_dev, int n_rows_max, cudaStream_t s) {
+    const int ldz = ldz_of_t(t);
+    const long long items = (long long)K * t.rows * (ldz / (t.prec == SB_PREC_BF16 ? 8 : 4));
+    note_launch();
+    if (t.prec == SB_PREC_BF16)
+        k_tc_scale<SB_PREC_BF16><<<grid_for(items), 256, 0, s>>>(K, (int)t.rows, ldz, n_rows_dev, n_rows_max,
+                                                                (const float *)t.p[6], t.p[4]);
+    else
+        k_tc_scale<SB_PREC_TF32><<<grid_for(items), 256, 0, s>>>(K, (int)t.rows, ldz, n_rows_dev, n_rows_max,
+                                                                (const float *)t.p[6], t.p[4]);
 }
 
 TcArgs base_args(const ProbView &pv, const TcWs &t) {
@@ -789,6 +782,7 @@ TcArgs base_args(const ProbView &pv, const TcWs &t) {
     a.c32 = (const float *)t.p[3];
     a.Z = t.p[4];
     a.ldz = ldz_of(pv.d);
+    a.z_rows = (int)t.rows;
     a.qpart = (float *)t.p[5];
     a.R = (const float *)t.p[6];
     a.n_ntile = (pv.d + t.bn - 1) / t.bn;
@@ -800,29 +794,41 @@ TcArgs base_args(const ProbView &pv, const TcWs &t) {
 
 bool tc_available(int prec) { return (prec == SB_PREC_BF16 || prec == SB_PREC_TF32) && encode_fn() != nullptr; }
 
-// Layout: [0] LT, [1] LB, [2] mu32, [3] c32, [4] Z, [5] qpart, [6] R, [7] X32 (points), [8] G32 (points)
+// Layout: [0] LT, [1] LB, [2] mu32, [3] c32, [4] Z [K][rows][ldz], [5] qpart, [6] R,
+// [7] X32 (points), [8] G32 (points), [9] A1 [K][rows][ldp] (centred GEMM1 operand)
 void carve_tc(Carver &cv, TcWs &t, int rows, int d, int K, int prec) {
     const int e = esz(prec), ldp = ldp_of(d, prec), bn = bn_of(d);
     const int nct = (d + bn - 1) / bn;
+    rows = (rows + BM - 1) / BM * BM;
     t.rows = rows;
     t.prec = prec;
     t.bn = bn;
+    t.d = d;
+    t.K = K;
+    t.ldz = ldz_of(d);
     t.p[0] = cv.take<uint8_t>((size_t)K * d * ldp * e);
     t.p[1] = cv.take<uint8_t>((size_t)K * d * ldp * e);
     t.p[2] = cv.take<float>((size_t)K * d);
     t.p[3] = cv.take<float>((size_t)d);
-    t.p[4] = cv.take<uint8_t>((size_t)rows * K * ldz_of(d) * e);
+    t.p[4] = cv.take<uint8_t>((size_t)rows * K * t.ldz * e);
     t.p[5] = cv.take<float>((size_t)rows * K * nct);
     t.p[6] = cv.take<float>((size_t)rows * K);
     t.p[7] = cv.take<float>((size_t)rows * d);
     t.p[8] = cv.take<float>((size_t)rows * d);
+    t.p[9] = cv.take<uint8_t>((size_t)K * rows * ldp * e);
 }
 
 int tc_ray_chunk(int d, int K, int64_t total) {
     (void)d;
     (void)K;
-    const int64_t b = 65536;
+    const int64_t b = 32768;  // centred operand of a chunk: K x 32768 x d elements
     return (int)(total < b ? total : b);
+}
+
+bool tc_maps_for_rows(TcWs &t) {
+    const int ldp = ldp_of(t.d, t.prec);
+    return make_map(&t.mapA1, t.p[9], t.d, (int)t.rows, t.K, ldp, t.prec, BM) &&
+           make_map(&t.mapZ, t.p[4], t.d, (int)t.rows, t.K, t.ldz, t.prec, BM);
 }
 
 sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s) {
@@ -835,23 +841,27 @@ sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s) {
         k_tc_convert_L<float><<<1184, 256, 0, s>>>(d, K, ldp, pv.L, (float *)t.p[0], (float *)t.p[1]);
     note_launch();
     k_tc_convert_vec<<<(K * d + 255) / 256, 256, 0, s>>>(d, K, pv.mu, pv.c, (float *)t.p[2], (float *)t.p[3]);
-    if (!make_map(&t.mapT, t.p[0], d, K, t.prec, t.bn) || !make_map(&t.mapB, t.p[1], d, K, t.prec, t.bn))
+    if (!make_map(&t.mapT, t.p[0], d, d, K, ldp, t.prec, t.bn) || !make_map(&t.mapB, t.p[1], d, d, K, ldp, t.prec, t.bn))
         return SB_ERR_CUDA;
+    if (!tc_maps_for_rows(t)) return SB_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
 }
 
-sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const double *u, const double *texit,
-                        double *ell_all, cudaStream_t s) {
+sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const double *u, float *u32,
+                        const double *texit, double *ell_all, cudaStream_t s) {
     const int64_t total = (int64_t)c->n_rays * c->n_steps;
+    {
+        const size_t nel = (size_t)c->n_rays * pv.d;
+        note_launch();
+        k_tc_points_in<<<(unsigned)((nel + 255) / 256 < 4096 ? (nel + 255) / 256 : 4096), 256, 0, s>>>(
+            c->n_rays, pv.d, u, u32);
+    }
     for (int64_t f0 = 0; f0 < total; f0 += (int64_t)t.rows) {
         const int rows = (int)((total - f0) < (int64_t)t.rows ? (total - f0) : (int64_t)t.rows);
         TcArgs a = base_args(pv, t);
         a.n_rows_max = rows;
-        a.u = u;
-        a.texit = texit;
-        a.n_steps = c->n_steps;
-        a.flat0 = f0;
-        launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapT, a, s);
+        launch_center(t, 1, pv.d, pv.K, nullptr, rows, nullptr, nullptr, u32, texit, c->n_steps, f0, s);
+        launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
         note_launch();
         k_tc_lse<<<(rows + 255) / 256, 256, 0, s>>>(1, pv.K, a.n_ntile, nullptr, rows, nullptr, a.qpart, pv.a,
                                                     nullptr, nullptr, ell_all + f0);
@@ -863,17 +873,17 @@ void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, cons
                      const int32_t *n_act, int n, float *FT, float *GT, cudaStream_t s) {
     (void)c;
     TcArgs a = base_args(pv, t);
-    a.X = XT;
-    a.ld = pv.d;
     a.act = act;
     a.n_rows_dev = n_act;
     a.n_rows_max = n;
-    launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapT, a, s);
+    launch_center(t, 0, pv.d, pv.K, n_act, n, act, XT, nullptr, nullptr, 1, 0, s);
+    launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
     note_launch();
     k_tc_lse<<<(n + 255) / 256, 256, 0, s>>>(0, pv.K, a.n_ntile, n_act, n, act, a.qpart, pv.a, (float *)t.p[6], FT,
                                              nullptr);
+    launch_scale(t, pv.K, n_act, n, s);
     a.G = GT;
-    launch_gemm_any(t.prec, MODE_G, t.bn, t.mapB, a, s);
+    launch_gemm_any(t.prec, MODE_G, t.bn, t.mapZ, t.mapB, a, s);
 }
 
 sb_status tc_loglik_points(const ProbView &pv, const sb_config *c, const TcWs &t, const double *x, int n, float *f,
@@ -886,16 +896,16 @@ sb_status tc_loglik_points(const ProbView &pv, const sb_config *c, const TcWs &t
     k_tc_points_in<<<(unsigned)(((size_t)n * pv.d + 255) / 256 < 4096 ? ((size_t)n * pv.d + 255) / 256 : 4096), 256,
                      0, s>>>(n, pv.d, x, X);
     TcArgs a = base_args(pv, t);
-    a.X = X;
-    a.ld = pv.d;
     a.n_rows_max = n;
-    launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapT, a, s);
+    launch_center(t, 0, pv.d, pv.K, nullptr, n, nullptr, X, nullptr, nullptr, 1, 0, s);
+    launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
     note_launch();
     k_tc_lse<<<(n + 255) / 256, 256, 0, s>>>(2, pv.K, a.n_ntile, nullptr, n, nullptr, a.qpart, pv.a,
                                              (float *)t.p[6], nullptr, ell);
     if (grad) {
+        launch_scale(t, pv.K, nullptr, n, s);
         a.G = G;
-        launch_gemm_any(t.prec, MODE_G, t.bn, t.mapB, a, s);
+        launch_gemm_any(t.prec, MODE_G, t.bn, t.mapZ, t.mapB, a, s);
         note_launch();
         k_tc_points_out<<<(unsigned)(((size_t)n * pv.d + 255) / 256 < 4096 ? ((size_t)n * pv.d + 255) / 256 : 4096),
                           256, 0, s>>>(n, pv.d, G, grad);
