@@ -210,6 +210,13 @@ size_t sb_evidence_batched_workspace_bytes(const sb_problem *probs, int32_t P, c
 sb_status sb_evidence_batched(const sb_problem *probs, int32_t P, const sb_config *cfg, double *logZ,
                               int32_t *n_modes, int32_t n_workers, void *ws, size_t ws_bytes, void *stream);
 
+/* Output tile width (64, 128 or 256 columns) the tensor-core GEMMs use for
+ * (d, K, prec) in this process, as chosen by the library's autotuner on the
+ * first mixed-precision call with that shape (which synchronises its stream);
+ * 0 if that shape has not been tuned yet. SB_TUNE=0 in the environment skips
+ * the timing (heuristic width); SB_TUNE_CACHE=<file> persists the choices. */
+int32_t sb_tuned_tile(int32_t d, int32_t K, int32_t prec);
+
 /* Synchronise `stream` and return the status word the device recorded in ws
  * (SB_OK if nothing went wrong); clears the word. */
 sb_status sb_check(void *ws, size_t ws_bytes, void *stream);
@@ -234,6 +241,16 @@ int64_t sb_launch_count(void);
  * 7 other), clears the record and returns the number of unreadable events. */
 void sb_profile_enable(int on);
 int32_t sb_profile_read(double *ms, int64_t *launches);
+
+/* Algorithmic bytes moved by the launches of profiling class `cls` while
+ * profiling was enabled, then clears that count. Only class 3 (the FP32 L-BFGS
+ * step) counts bytes: per walker visited, the vectors it reads and writes
+ * (x, grad, trial point and gradient, direction, state) and, for a new
+ * direction, every stored pair read in both passes of the two-loop recursion
+ * (4 m d history elements at a full history, the figure of the limited-memory
+ * update of Nocedal & Wright, Alg. 7.4). Other classes return 0. Synchronises
+ * the device; returns -1 on a CUDA error. */
+double sb_profile_bytes(int32_t cls);
 
 #ifdef __cplusplus
 }

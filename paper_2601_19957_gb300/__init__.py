@@ -63,6 +63,8 @@ def lib():
         L.sb_evidence_backward_workspace_bytes.restype = C.c_size_t
         L.sb_evidence_batched_workspace_bytes.restype = C.c_size_t
         L.sb_evidence_batched.restype = C.c_int
+        L.sb_profile_bytes.restype = C.c_double
+        L.sb_profile_bytes.argtypes = [C.c_int32]
         L.sb_evidence_backward.restype = C.c_int
         L.sb_evidence_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]

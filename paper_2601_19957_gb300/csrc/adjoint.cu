@@ -359,7 +359,7 @@ sb_status adjoint_run(const ProbView &pv, const AdjWs &w, const double *modes, c
         la.G = w.gbar;
         la.grad_sign = -1.0;
         la.out_by_walker = 0;
-        launch_lik_f64_points(la, true, s);
+        launch_lik_f64_few(la, true, s);
         launch_hessian_chol(d, K, 1, pv.L, w.P, w.Z, w.R, w.gbar, w.one, w.GK, w.H, w.info, s);
         // W [g_0 .. g_{K-1}, gbar]
         note_launch();

@@ -314,43 +314,93 @@ __global__ void __launch_bounds__(256) k_syrk_update(int d, int kb, double *H, c
     }
 }
 
-// Solve (C C^T) delta = g for each candidate still polishing.
+// Solve (C C^T) delta = g for each candidate still polishing: one CTA per
+// candidate, blocked by 32 rows. Forward: y_I = C_II^-1 (g_I - C_I,<I y_<I);
+// backward: delta_I = C_II^-T (y_I - sum_{J>I} C_JI^T delta_J). The off-diagonal
+// products read whole rows of C (coalesced); the 32 x 32 diagonal solves run on
+// one warp with shuffles.
 __global__ void __launch_bounds__(256) k_chol_solve(int d, const double *H, const double *g, const int32_t *n_c,
                                                     const int32_t *info, const uint8_t *active, double *delta,
                                                     double *pred) {
     const int c = blockIdx.x;
     if (c >= *n_c || info[c] || !active[c]) return;
-    extern __shared__ double y[];
+    extern __shared__ double y[];  // [d]
+    __shared__ double part[8][33];
+    __shared__ double Dg[32][33];
     const double *C = H + (size_t)c * d * d;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < d; i += blockDim.x) y[i] = g[(size_t)c * d + i];
     __syncthreads();
-    for (int i = 0; i < d; ++i) {  // forward: C y = g
-        if (threadIdx.x == 0) y[i] = y[i] / C[(size_t)i * d + i];
+    const int nb = (d + 31) / 32;
+    // forward substitution
+    for (int I = 0; I < nb; ++I) {
+        const int r0 = I * 32, rows = min(32, d - r0);
+        // rhs of block I minus C[I][0:r0] y[0:r0]: warp w handles rows r0 + w, r0 + w + 8, ...
+        for (int rr = wid; rr < rows; rr += 8) {
+            const double *Crow = C + (size_t)(r0 + rr) * d;
+            double sacc = 0.0;
+            for (int j = lane; j < r0; j += 32) sacc += Crow[j] * y[j];
+            sacc = warp_sum(sacc);
+            if (lane == 0) part[0][rr] = sacc;
+        }
+        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+            const int i = e / 32, j = e % 32;
+            Dg[i][j] = (i < rows && j < rows) ? C[(size_t)(r0 + i) * d + r0 + j] : (i == j ? 1.0 : 0.0);
+        }
         __syncthreads();
-        const double yi = y[i];
-        for (int k = i + 1 + threadIdx.x; k < d; k += blockDim.x) y[k] -= C[(size_t)k * d + i] * yi;
+        if (wid == 0) {
+            double v = lane < rows ? y[r0 + lane] - part[0][lane] : 0.0;
+            for (int i = 0; i < 32; ++i) {
+                const double yi = __shfl_sync(0xffffffffu, v, i) / Dg[i][i];
+                if (lane == i) v = yi;
+                if (lane > i) v -= Dg[lane][i] * yi;
+            }
+            if (lane < rows) y[r0 + lane] = v;
+        }
         __syncthreads();
     }
-    for (int i = d - 1; i >= 0; --i) {  // backward: C^T delta = y
-        if (threadIdx.x == 0) y[i] = y[i] / C[(size_t)i * d + i];
+    // backward substitution with C^T
+    for (int I = nb - 1; I >= 0; --I) {
+        const int r0 = I * 32, rows = min(32, d - r0);
+        // sum_{J > I} C[j][r0 + i] delta[j]: threads over (i, j-slices); column block of C rows below
+        {
+            const int i = lane;  // column r0 + i
+            double sacc = 0.0;
+            if (i < rows)
+                for (int j = r0 + 32 + wid; j < d; j += 8) sacc += C[(size_t)j * d + r0 + i] * y[j];
+            part[wid][i] = sacc;
+        }
+        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+            const int i = e / 32, j = e % 32;
+            Dg[i][j] = (i < rows && j < rows) ? C[(size_t)(r0 + i) * d + r0 + j] : (i == j ? 1.0 : 0.0);
+        }
         __syncthreads();
-        const double yi = y[i];
-        for (int k = threadIdx.x; k < i; k += blockDim.x) y[k] -= C[(size_t)i * d + k] * yi;
+        if (wid == 0) {
+            double sacc = 0.0;
+            for (int q = 0; q < 8; ++q) sacc += part[q][lane];
+            double v = lane < rows ? y[r0 + lane] - sacc : 0.0;
+            // C_II^T x = v: upper-triangular (C^T)_{ij} = C_{ji}; back substitution
+            for (int i = 31; i >= 0; --i) {
+                const double xi = __shfl_sync(0xffffffffu, v, i) / Dg[i][i];
+                if (lane == i) v = xi;
+                if (lane < i) v -= Dg[i][lane] * xi;
+            }
+            if (lane < rows) y[r0 + lane] = v;
+        }
         __syncthreads();
     }
     // model increase of l along the Newton step: g^T delta / 2
-    __shared__ double s_part[8];
     double gd = 0.0;
     for (int i = threadIdx.x; i < d; i += blockDim.x) {
         delta[(size_t)c * d + i] = y[i];
         gd += g[(size_t)c * d + i] * y[i];
     }
     gd = warp_sum(gd);
-    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = gd;
+    if (lane == 0) part[0][wid] = gd;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s_part[q];
+        for (int q = 0; q < 8; ++q) t += part[0][q];
         pred[c] = 0.5 * t;
     }
 }

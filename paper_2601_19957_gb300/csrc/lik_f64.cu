@@ -230,6 +230,105 @@ __global__ void __launch_bounds__(256) k_ggemm_f64(LikF64Args a) {
         }
     }
 }
+// ------------------------------------------------------------------ few points (GEMV shape)
+// For a handful of points (the Laplace stage's candidates) a 64-row GEMM tile
+// does 64 rows of FP64 work for each real row. These kernels spread the work
+// over (column block, component, point block) instead, with the same outputs,
+// layouts and a fixed summation order.
+constexpr int FEW_CB = 8;  // points per CTA
+
+// z_k[j] for 64 columns j of one component and FEW_CB points; thread per column.
+__global__ void __launch_bounds__(64) k_few_z(LikF64Args a) {
+    const int n_rows = rows_of(a);
+    const int jt = blockIdx.x, j0 = jt * 64, k = blockIdx.y, c0 = blockIdx.z * FEW_CB;
+    if (c0 >= n_rows) return;
+    const int d = a.d, K = a.K, nJT = (d + 63) / 64;
+    const int nc = min(FEW_CB, n_rows - c0);
+    __shared__ double dl[FEW_CB][64];  // delta = x - mu_k for 64 rows i of the current chunk
+    __shared__ int s_src[FEW_CB], s_out[FEW_CB];
+    if (threadIdx.x < FEW_CB) {
+        const int n = c0 + threadIdx.x;
+        const int w = (threadIdx.x < nc) ? (a.rows ? a.rows[n] : n) : 0;
+        s_src[threadIdx.x] = w;
+        s_out[threadIdx.x] = (threadIdx.x < nc) ? (a.out_by_walker ? w : n) : -1;
+    }
+    __syncthreads();
+    const double *Lk = a.L + (size_t)k * d * d;
+    const double *mk = a.mu + (size_t)k * d;
+    const int j = j0 + threadIdx.x;
+    double acc[FEW_CB];
+#pragma unroll
+    for (int c = 0; c < FEW_CB; ++c) acc[c] = 0.0;
+    for (int i0 = j0; i0 < d; i0 += 64) {
+        const int i = i0 + threadIdx.x;
+#pragma unroll
+        for (int c = 0; c < FEW_CB; ++c)
+            dl[c][threadIdx.x] = (c < nc && i < d) ? sub_rn(a.X[(size_t)s_src[c] * d + i], mk[i]) : 0.0;
+        __syncthreads();
+        const int imax = min(64, d - i0);
+        for (int ii = 0; ii < imax; ++ii) {
+            const int ig = i0 + ii;
+            const double l = (j < d && j <= ig) ? Lk[(size_t)ig * d + j] : 0.0;
+#pragma unroll
+            for (int c = 0; c < FEW_CB; ++c) acc[c] = fma(dl[c][ii], l, acc[c]);
+        }
+        __syncthreads();
+    }
+    // |z|^2 over the 64 columns: warp shuffles then two warps through shared memory
+    __shared__ double red[FEW_CB][2];
+#pragma unroll
+    for (int c = 0; c < FEW_CB; ++c) {
+        double q = (j < d) ? acc[c] * acc[c] : 0.0;
+        q = warp_sum(q);
+        if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = q;
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+        const int c = threadIdx.x;
+        a.qpart[((size_t)s_out[c] * K + k) * nJT + jt] = red[c][0] + red[c][1];
+    }
+    if (a.Z && j < d)
+        for (int c = 0; c < nc; ++c) a.Z[((size_t)s_out[c] * K + k) * d + j] = acc[c];
+}
+
+// grad: out[n][i] = sign * sum_k sum_{j<=i} r_nk z_nk[j] L_k[i][j]; warp per row i, FEW_CB points.
+__global__ void __launch_bounds__(256) k_few_g(LikF64Args a) {
+    const int n_rows = rows_of(a);
+    const int c0 = blockIdx.y * FEW_CB;
+    if (c0 >= n_rows) return;
+    const int d = a.d, K = a.K;
+    const int nc = min(FEW_CB, n_rows - c0);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int i = blockIdx.x * 8 + wid;
+    __shared__ int s_out[FEW_CB];
+    if (threadIdx.x < FEW_CB) {
+        const int n = c0 + threadIdx.x;
+        s_out[threadIdx.x] = (threadIdx.x < nc) ? (a.out_by_walker ? (a.rows ? a.rows[n] : n) : n) : -1;
+    }
+    __syncthreads();
+    if (i >= d) return;
+    double acc[FEW_CB];
+#pragma unroll
+    for (int c = 0; c < FEW_CB; ++c) acc[c] = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double *Lrow = a.L + (size_t)k * d * d + (size_t)i * d;
+        for (int j = lane; j <= i; j += 32) {
+            const double l = Lrow[j];
+#pragma unroll
+            for (int c = 0; c < FEW_CB; ++c)
+                if (c < nc) {
+                    const int o = s_out[c];
+                    acc[c] = fma(a.R[(size_t)o * K + k] * a.Z[((size_t)o * K + k) * d + j], l, acc[c]);
+                }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < FEW_CB; ++c) {
+        const double v = warp_sum(acc[c]);
+        if (lane == 0 && c < nc) a.G[(size_t)s_out[c] * d + i] = a.grad_sign * v;
+    }
+}
+
 }  // namespace
 
 size_t lik_f64_qpart_elems(int d, int K, int rows) { return (size_t)rows * K * ((d + BN - 1) / BN); }
@@ -274,4 +373,24 @@ void launch_lik_f64_points(const LikF64Args &a, bool want_grad, cudaStream_t s) 
     }
 }
 
+}  // namespace sb
+
+namespace sb {
+void launch_lik_f64_few(const LikF64Args &a, bool want_grad, cudaStream_t s) {
+    if (a.n_rows <= 0) return;
+    const int nJT = (a.d + 63) / 64;
+    const int cb = (a.n_rows + 7) / 8;
+    {
+        ProfScope prof(PROF_F64_Z, s);
+        note_launch();
+        k_few_z<<<dim3(nJT, a.K, cb), 64, 0, s>>>(a);
+    }
+    note_launch();
+    k_lse_f64<<<(a.n_rows + 255) / 256, 256, 0, s>>>(a);
+    if (want_grad) {
+        ProfScope prof(PROF_F64_GRAD, s);
+        note_launch();
+        k_few_g<<<dim3((a.d + 7) / 8, cb), 256, 0, s>>>(a);
+    }
+}
 }  // namespace sb

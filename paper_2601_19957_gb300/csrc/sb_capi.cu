@@ -1,6 +1,7 @@
 // sb_capi.cu -- the C ABI of libsb (declared in include/sb.h): argument
 // validation, workspace carving and the host-side orchestration of the
 // discover -> refine -> laplace stages.
+#include <stdlib.h>
 #include <string.h>
 
 #include <atomic>
@@ -26,10 +27,12 @@ struct ProfRec {
 };
 std::vector<ProfRec> g_prof;
 }  // namespace
-void sb::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void sb::note_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 sb::ProfScope::ProfScope(int c, cudaStream_t st) : cls(c), s(st), a(nullptr), b(nullptr) {
     if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
         a = b = nullptr;
         return;
@@ -43,7 +46,14 @@ sb::ProfScope::~ProfScope() {
     g_prof.push_back({cls, a, b});
 }
 
+bool sb::prof_enabled() { return g_prof_on.load(std::memory_order_relaxed) != 0; }
+
 extern "C" void sb_profile_enable(int on) { g_prof_on.store(on ? 1 : 0); }
+
+extern "C" double sb_profile_bytes(int32_t cls) {
+    if (cls == PROF_LBFGS_STEP) return lbfgs_bytes_take();
+    return 0.0;
+}
 
 extern "C" int32_t sb_profile_read(double *ms, int64_t *launches) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -379,7 +389,10 @@ void step_round<double>(const RefineWs<double> &, const LbfgsArgs<double> &a, in
 }
 template <>
 void step_round<float>(const RefineWs<float> &r, const LbfgsArgs<float> &a, int n, cudaStream_t s) {
-    launch_lbfgs_step_cta(a, n, r.MSY, r.MYY, device_sms(), s);  // compact form, CTA per walker
+    // compact form, CTA per walker, FP32 history (bf16 history measured slower: the
+    // step is latency-bound, not bandwidth-bound)
+    static const bool bf16h = getenv("SB_LBFGS_BF16") != nullptr;
+    launch_lbfgs_step_cta(a, n, r.MSY, r.MYY, device_sms(), bf16h, s);
 }
 
 template <typename T>
@@ -401,24 +414,68 @@ sb_status run_refine(const ProbView &pv, const sb_config *c, const RefineWs<T> &
     // every accepted step takes at most 2 (max_backtracks + 1) rounds
     const int64_t cap_rounds = 2 + (int64_t)(c->max_iter + 1) * 2 * (c->max_backtracks + 2);
     int64_t round = 0;
+    // Small problems are launch-bound: capture one batch of rounds into a CUDA
+    // graph and replay it. Large ones keep direct launches (their kernels take
+    // far longer than a launch, and the per-kernel profiling stays available).
+    const bool use_graph = (int64_t)pv.d * n <= ((int64_t)1 << 20);
+    cudaGraphExec_t ge = nullptr;
+    int64_t per_batch = 0;
+    if (use_graph) {
+        // The caller's stream may be the legacy default stream, which cannot be
+        // captured: record on a private stream and replay the graph on the caller's.
+        cudaStream_t cs = nullptr;
+        SB_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        const int64_t before = sb_launch_count();
+        cudaError_t ec = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (ec == cudaSuccess) {
+            for (int b = 0; b < kRoundsPerPoll; ++b) {
+                eval_round<T>(pv, c, rr, n, cs);
+                step_round<T>(rr, a, n, cs);
+                launch_lbfgs_compact<T>(a, ev, cs);
+            }
+            ec = cudaStreamEndCapture(cs, &g);
+        }
+        per_batch = sb_launch_count() - before;
+        note_launch(-per_batch);  // counted per replay below
+        cudaStreamDestroy(cs);
+        if (ec != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return SB_ERR_CUDA;
+        }
+        cudaGraphDestroy(g);
+    }
     while (true) {
-        for (int b = 0; b < kRoundsPerPoll; ++b) {
-            eval_round<T>(pv, c, rr, n, s);
-            step_round<T>(rr, a, n, s);
-            launch_lbfgs_compact<T>(a, ev, s);
+        if (ge) {
+            if (cudaGraphLaunch(ge, s) != cudaSuccess) {
+                cudaGraphExecDestroy(ge);
+                return SB_ERR_CUDA;
+            }
+            note_launch(per_batch);
+        } else {
+            for (int b = 0; b < kRoundsPerPoll; ++b) {
+                eval_round<T>(pv, c, rr, n, s);
+                step_round<T>(rr, a, n, s);
+                launch_lbfgs_compact<T>(a, ev, s);
+            }
         }
         round += kRoundsPerPoll;
         int32_t h_act = 0;
-        SB_CUDA_TRY(cudaMemcpyAsync(&h_act, a.n_act, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        SB_CUDA_TRY(cudaStreamSynchronize(s));
+        if (cudaMemcpyAsync(&h_act, a.n_act, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            if (ge) cudaGraphExecDestroy(ge);
+            return SB_ERR_CUDA;
+        }
         if (h_act == 0 || round >= cap_rounds) break;
     }
+    if (ge) cudaGraphExecDestroy(ge);
     launch_lbfgs_finish<T>(n, pv.d, a, x_out, ell_out, status_out, iters_out, pv.status, s);
     SB_CUDA_TRY(cudaGetLastError());
     return SB_OK;
 }
 
-// l and grad l (FP64) at the rows of X listed in rows[0..*n_rows) (or 0..n), outputs by row id.
+// l and grad l (FP64) at the Laplace stage's candidates (few points): rows of X listed in
+// rows[0..*n_rows) (or 0..n), outputs by row id.
 void f64_points(const ProbView &pv, const double *X, const int32_t *rows, const int32_t *n_rows_dev, int n_rows,
                 double *qpart, double *Z, double *R, double *ell, double *G, cudaStream_t s) {
     LikF64Args a = f64_args(pv);
@@ -432,7 +489,7 @@ void f64_points(const ProbView &pv, const double *X, const int32_t *rows, const 
     a.ell = ell;
     a.G = G;
     a.out_by_walker = 1;
-    launch_lik_f64_points(a, G != nullptr, s);
+    launch_lik_f64_few(a, G != nullptr, s);
 }
 
 sb_status run_laplace(const ProbView &pv, const sb_config *c, const Layout &L, const double *x, const double *ell,
@@ -501,6 +558,7 @@ sb_status prelude(const sb_problem *p, const sb_config *c, void *ws, size_t ws_b
         for (int i = 0; i < 4; ++i) out.L.r32.tc.p[i] = out.L.di.tc.p[i];
         out.L.r32.tc.mapT = out.L.di.tc.mapT;
         out.L.r32.tc.mapB = out.L.di.tc.mapB;
+        out.L.r32.tc.bn = out.L.di.tc.bn;
         if (!tc_maps_for_rows(out.L.r32.tc)) return SB_ERR_CUDA;
     }
     SB_CUDA_TRY(cudaGetLastError());
@@ -903,3 +961,5 @@ extern "C" sb_status sb_evidence_batched(const sb_problem *probs, int32_t P, con
         if (r != SB_OK) return r;
     return SB_OK;
 }
+
+extern "C" int32_t sb_tuned_tile(int32_t d, int32_t K, int32_t prec) { return tc_tuned_tile(d, K, prec); }

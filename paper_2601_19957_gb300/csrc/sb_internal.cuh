@@ -141,7 +141,7 @@ struct ProbView {
 };
 
 // Host-side count of kernel launches issued by the library (diagnostics).
-void note_launch();
+void note_launch(int64_t n = 1);
 
 // Optional per-class device timing of launches (CUDA events on the launching
 // stream, recorded only while profiling is enabled through the C ABI).
@@ -156,6 +156,7 @@ enum ProfClass {
     PROF_OTHER = 7,
     PROF_NCLASS = 8
 };
+bool prof_enabled();
 struct ProfScope {
     int cls;
     cudaStream_t s;
@@ -196,6 +197,8 @@ struct LikF64Args {
 void launch_lik_f64_rays(const LikF64Args &a, cudaStream_t s);                 // values at ray samples
 void launch_lik_f64_points(const LikF64Args &a, bool want_grad, cudaStream_t s);// values (+grads) at points
 size_t lik_f64_qpart_elems(int d, int K, int rows);
+// Same outputs for a handful of points (GEMV-shaped work split; n_rows is the capacity).
+void launch_lik_f64_few(const LikF64Args &a, bool want_grad, cudaStream_t s);
 
 // rays.cu
 void launch_ray_dirs(int d, int n_rays, uint64_t seed, const ProbView &pv, double *u, double *texit, cudaStream_t s);

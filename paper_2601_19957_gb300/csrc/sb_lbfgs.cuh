@@ -38,7 +38,11 @@ void launch_lbfgs_step(const LbfgsArgs<T> &a, int n, cudaStream_t s);
 template <typename T>
 void launch_lbfgs_compact(const LbfgsArgs<T> &a, int64_t *n_evals, cudaStream_t s);
 // FP32 step, one CTA per walker, compact-representation direction (lbfgs_cta.cu).
-void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *MYY, int num_sms, cudaStream_t s);
+void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *MYY, int num_sms, bool bf16_history,
+                           cudaStream_t s);
+// Algorithmic bytes moved by the FP32 step launches while profiling was on
+// (synchronises the device, then clears the counter); -1 on a CUDA error.
+double lbfgs_bytes_take();
 
 template <typename T>
 void launch_lbfgs_finish(int n, int d, const LbfgsArgs<T> &a, double *x_out, double *ell_out, int8_t *status_out,

@@ -22,7 +22,11 @@ void carve_tc(Carver &cv, TcWs &t, int rows, int d, int K, int prec);
 int tc_ray_chunk(int d, int K, int64_t total);
 // Encodes the A-operand tensor maps of this scratch (depends on its row capacity).
 bool tc_maps_for_rows(TcWs &t);
-// Converts L_k / mu / c into the tensor-core copies and encodes the tensor maps.
+// Tile width the autotuner chose for (d, K, prec) in this process (0: not tuned yet).
+int tc_tuned_tile(int d, int K, int prec);
+// Converts L_k / mu / c into the tensor-core copies, picks the tile width
+// (autotuned once per shape; that first call synchronises the stream) and
+// encodes the tensor maps.
 sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s);
 sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const double *u, float *u32,
                         const double *texit, double *ell_all, cudaStream_t s);

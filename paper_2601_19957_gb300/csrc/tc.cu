@@ -32,7 +32,11 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <cstdio>
+#include <cstdlib>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "sb_tc.cuh"
 
@@ -111,7 +115,6 @@ __device__ __forceinline__ bool warp_bwait(uint64_t *bar, uint32_t parity, volat
 __device__ __forceinline__ bool warp_aborted(volatile int *abort_flag) {
     return __any_sync(0xffffffffu, *abort_flag != 0) != 0;
 }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -215,6 +218,16 @@ __device__ __forceinline__ TileInfo decode_tile(int t, int d, int K) {
     return ti;
 }
 
+// Tile sequence of one CTA: whole groups (every column tile of one row block,
+// and component for GEMM1), groups dealt round-robin. Column tiles differ in
+// their number of K chunks (the triangle), so dealing single tiles round-robin
+// with a grid that is a multiple of the tile count per group would give each
+// CTA the same column tile over and over; whole groups carry equal work and
+// reuse their A rows inside the CTA.
+__device__ __forceinline__ int tile_of(int i, int nct) {
+    return (blockIdx.x + (i / nct) * gridDim.x) * nct + (i % nct);
+}
+
 // ------------------------------------------------------------------ the kernel
 template <int BN, int PREC, int MODE>
 __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ CUtensorMap tmapA,
@@ -276,7 +289,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             int inflight_stage[8];
             uint32_t inflight_phase[8];
             int n_inflight = 0;
-            for (int t = blockIdx.x; t < n_tiles && !*s_abort; t += gridDim.x) {
+            for (int it = 0, t = tile_of(0, nct); t < n_tiles && !*s_abort; t = tile_of(++it, nct)) {
                 const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K);
                 bool ok = true;
                 for (int q = 0; q < ti.nchunks; ++q) {
@@ -323,7 +336,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             int acc = 0;
             uint32_t acc_phase = 0;
             bool issued = false;
-            for (int t = blockIdx.x; t < n_tiles && !*s_abort; t += gridDim.x) {
+            for (int it = 0, t = tile_of(0, nct); t < n_tiles && !*s_abort; t = tile_of(++it, nct)) {
                 const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K);
                 if (!bwait(&tempty[acc], acc_phase ^ 1, s_abort)) break;
                 tc_fence_after();
@@ -369,12 +382,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         const int r = quad * 32 + lane;
         int acc = 0;
         uint32_t acc_phase = 0;
-        for (int t = blockIdx.x; t < n_tiles && !warp_aborted(s_abort); t += gridDim.x) {
+        for (int it = 0, t = tile_of(0, nct); t < n_tiles && !warp_aborted(s_abort); t = tile_of(++it, nct)) {
             const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K);
             if (!warp_bwait(&tfull[acc], acc_phase, s_abort)) break;
             tc_fence_after();
             const int n = ti.mb * BM + r;
             const bool valid = n < n_rows;
+            const int w_out = (MODE == MODE_G && valid) ? (a.act ? a.act[n] : n) : 0;
             const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * BN);
             float q2 = 0.f;
 #pragma unroll 1
@@ -384,8 +398,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                 const int col = ti.nt * BN + c0;
                 if (MODE == MODE_G) {
                     if (valid && col < d) {
-                        const int w = a.act ? a.act[n] : n;
-                        float *g = a.G + (size_t)w * d + col;
+                        float *g = a.G + (size_t)w_out * d + col;
                         if ((d & 3) == 0 && col + 32 <= d) {
 #pragma unroll
                             for (int e = 0; e < 32; e += 4)
@@ -487,8 +500,9 @@ __global__ void __launch_bounds__(256) k_tc_lse(int mode, int K, int n_ntile, co
 // A operand of GEMM1: A1[k][n][i] = round(x_n[i] - mu_k[i]) formed in FP32; x_n is a
 // walker row (through the active list) or the ray sample c + t_j t_exit u_r.
 // Rows from n_rows up to the next multiple of 128 and columns >= d are zeroed.
+// Grid: x over (row, 16-byte column group), y = component.
 template <int PREC>
-__global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int K, int rows_cap, int ldp,
+__global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int rows_cap, int ldp,
                                                    const int32_t *n_rows_dev, int n_rows_max, const int32_t *act,
                                                    const float *X, int ld, const float *u32, const double *texit,
                                                    int n_steps, long long flat0, const float *mu32, const float *c32,
@@ -498,63 +512,70 @@ __global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int K, i
     int rows_pad = (n_rows + BM - 1) / BM * BM;
     if (rows_pad > rows_cap) rows_pad = rows_cap;
     const int ncg = ldp / VE;
-    const long long total = (long long)K * rows_pad * ncg;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int cg = (int)(e % ncg);
-        const long long kn = e / ncg;
-        const int n = (int)(kn % rows_pad);
-        const int k = (int)(kn / rows_pad);
-        const int i0 = cg * VE;
-        float v[VE];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = e / ncg, cg = e - n * ncg;
+    if (n >= rows_pad) return;
+    const int k = blockIdx.y;
+    const int i0 = cg * VE;
+    float v[VE];
 #pragma unroll
-        for (int q = 0; q < VE; ++q) v[q] = 0.f;
-        if (n < n_rows) {
-            if (!ray_mode) {
-                const float *xr = X + (size_t)(act ? act[n] : n) * ld;
-                if ((ld & 3) == 0 && i0 + VE <= d) {
+    for (int q = 0; q < VE; ++q) v[q] = 0.f;
+    if (n < n_rows) {
+        const float *mk = mu32 + (size_t)k * d;
+        const bool vec = ((d & 3) == 0) && i0 + VE <= d;
+        float m[VE];
+        if (vec) {
 #pragma unroll
-                    for (int q = 0; q < VE; q += 4) {
-                        const float4 x4 = *reinterpret_cast<const float4 *>(xr + i0 + q);
-                        v[q] = x4.x;
-                        v[q + 1] = x4.y;
-                        v[q + 2] = x4.z;
-                        v[q + 3] = x4.w;
-                    }
-                } else {
+            for (int q = 0; q < VE; q += 4) {
+                const float4 t = *reinterpret_cast<const float4 *>(mk + i0 + q);
+                m[q] = t.x;
+                m[q + 1] = t.y;
+                m[q + 2] = t.z;
+                m[q + 3] = t.w;
+            }
+        } else {
 #pragma unroll
-                    for (int q = 0; q < VE; ++q)
-                        if (i0 + q < d) v[q] = xr[i0 + q];
+            for (int q = 0; q < VE; ++q) m[q] = i0 + q < d ? mk[i0 + q] : 0.f;
+        }
+        if (!ray_mode) {
+            const float *xr = X + (size_t)(act ? act[n] : n) * ld;
+            if (vec && (ld & 3) == 0) {
+#pragma unroll
+                for (int q = 0; q < VE; q += 4) {
+                    const float4 x4 = *reinterpret_cast<const float4 *>(xr + i0 + q);
+                    v[q] = x4.x;
+                    v[q + 1] = x4.y;
+                    v[q + 2] = x4.z;
+                    v[q + 3] = x4.w;
                 }
             } else {
-                const long long flat = flat0 + n;
-                const int ray = (int)(flat / n_steps), j = (int)(flat % n_steps);
-                const float sc = (float)(((double)(j + 1) / (double)n_steps) * texit[ray]);
-                const float *ur = u32 + (size_t)ray * d;
 #pragma unroll
                 for (int q = 0; q < VE; ++q)
-                    if (i0 + q < d) v[q] = fmaf(sc, ur[i0 + q], c32[i0 + q]);
+                    if (i0 + q < d) v[q] = xr[i0 + q];
             }
-            const float *mk = mu32 + (size_t)k * d;
+        } else {
+            const long long flat = flat0 + n;
+            const int ray = (int)(flat / n_steps), j = (int)(flat - (long long)ray * n_steps);
+            const float sc = (float)(((double)(j + 1) / (double)n_steps) * texit[ray]);
+            const float *ur = u32 + (size_t)ray * d;
 #pragma unroll
             for (int q = 0; q < VE; ++q)
-                if (i0 + q < d)
-                    v[q] -= mk[i0 + q];
-                else
-                    v[q] = 0.f;
+                if (i0 + q < d) v[q] = fmaf(sc, ur[i0 + q], c32[i0 + q]);
         }
-        const size_t o = ((size_t)k * rows_cap + n) * ldp + i0;
-        if (PREC == SB_PREC_BF16) {
-            uint4 p;
-            p.x = pack_bf16x2(v[0], v[1]);
-            p.y = pack_bf16x2(v[2], v[3]);
-            p.z = pack_bf16x2(v[4], v[5]);
-            p.w = pack_bf16x2(v[6], v[7]);
-            *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(A1) + o) = p;
-        } else {
-            *reinterpret_cast<float4 *>(reinterpret_cast<float *>(A1) + o) =
-                make_float4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
-        }
+#pragma unroll
+        for (int q = 0; q < VE; ++q) v[q] = (i0 + q < d) ? v[q] - m[q] : 0.f;
+    }
+    const size_t o = ((size_t)k * rows_cap + n) * ldp + i0;
+    if (PREC == SB_PREC_BF16) {
+        uint4 p;
+        p.x = pack_bf16x2(v[0], v[1]);
+        p.y = pack_bf16x2(v[2], v[3]);
+        p.z = pack_bf16x2(v[4], v[5]);
+        p.w = pack_bf16x2(v[6], v[7]);
+        *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(A1) + o) = p;
+    } else {
+        *reinterpret_cast<float4 *>(reinterpret_cast<float *>(A1) + o) =
+            make_float4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
     }
 }
 
@@ -567,37 +588,33 @@ __global__ void __launch_bounds__(256) k_tc_scale(int K, int rows_cap, int ldz, 
     int rows_pad = (n_rows + BM - 1) / BM * BM;
     if (rows_pad > rows_cap) rows_pad = rows_cap;
     const int ncg = ldz / VE;
-    const long long total = (long long)K * rows_pad * ncg;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int cg = (int)(e % ncg);
-        const long long kn = e / ncg;
-        const int n = (int)(kn % rows_pad);
-        const int k = (int)(kn / rows_pad);
-        const size_t o = ((size_t)k * rows_cap + n) * ldz + (size_t)cg * VE;
-        if (n >= n_rows) {  // padding rows hold stale values (possibly NaN): overwrite, never scale
-            if (PREC == SB_PREC_BF16)
-                *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(Z) + o) = make_uint4(0u, 0u, 0u, 0u);
-            else
-                *reinterpret_cast<float4 *>(reinterpret_cast<float *>(Z) + o) = make_float4(0.f, 0.f, 0.f, 0.f);
-            continue;
-        }
-        const float r = R[(size_t)n * K + k];
-        if (PREC == SB_PREC_BF16) {
-            uint4 *pz = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(Z) + o);
-            uint4 p = *pz;
-            uint32_t w[4] = {p.x, p.y, p.z, p.w};
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = e / ncg, cg = e - n * ncg;
+    if (n >= rows_pad) return;
+    const int k = blockIdx.y;
+    const size_t o = ((size_t)k * rows_cap + n) * ldz + (size_t)cg * VE;
+    if (n >= n_rows) {  // padding rows hold stale values (possibly NaN): overwrite, never scale
+        if (PREC == SB_PREC_BF16)
+            *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(Z) + o) = make_uint4(0u, 0u, 0u, 0u);
+        else
+            *reinterpret_cast<float4 *>(reinterpret_cast<float *>(Z) + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const float r = R[(size_t)n * K + k];
+    if (PREC == SB_PREC_BF16) {
+        uint4 *pz = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(Z) + o);
+        uint4 p = *pz;
+        uint32_t w[4] = {p.x, p.y, p.z, p.w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[q]);
-                w[q] = pack_bf16x2(__low2float(h) * r, __high2float(h) * r);
-            }
-            *pz = make_uint4(w[0], w[1], w[2], w[3]);
-        } else {
-            float4 *pz = reinterpret_cast<float4 *>(reinterpret_cast<float *>(Z) + o);
-            const float4 v = *pz;
-            *pz = make_float4(to_tf32(v.x * r), to_tf32(v.y * r), to_tf32(v.z * r), to_tf32(v.w * r));
+        for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[q]);
+            w[q] = pack_bf16x2(__low2float(h) * r, __high2float(h) * r);
         }
+        *pz = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+        float4 *pz = reinterpret_cast<float4 *>(reinterpret_cast<float *>(Z) + o);
+        const float4 v = *pz;
+        *pz = make_float4(to_tf32(v.x * r), to_tf32(v.y * r), to_tf32(v.z * r), to_tf32(v.w * r));
     }
 }
 
@@ -704,11 +721,10 @@ void launch_gemm(const CUtensorMap &mapA, const CUtensorMap &map, const TcArgs &
     std::call_once(once, [] {
         cudaFuncSetAttribute(k_tc_gemm<BN, PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
     });
-    const int nct = (a.d + BN - 1) / BN;
     const int mb = (a.n_rows_max + BM - 1) / BM;
-    long long tiles = (long long)mb * nct * (MODE == MODE_G ? 1 : a.K);
+    const long long groups = (long long)mb * (MODE == MODE_G ? 1 : a.K);
     int grid = num_sms();
-    if (tiles < grid) grid = (int)(tiles > 0 ? tiles : 1);
+    if (groups < grid) grid = (int)(groups > 0 ? groups : 1);
     ProfScope prof(MODE == MODE_ZW ? PROF_TC_Z_WALKERS : (MODE == MODE_ZR ? PROF_TC_Z_RAYS : PROF_TC_GRAD), s);
     note_launch();
     k_tc_gemm<BN, PREC, MODE><<<grid, THREADS, SM, s>>>(mapA, map, a);
@@ -737,41 +753,38 @@ void launch_gemm_any(int prec, int mode, int bn, const CUtensorMap &mapA, const 
     }
 }
 
-unsigned grid_for(long long items) {
-    long long g = (items + 255) / 256;
-    const long long cap = (long long)num_sms() * 8;
-    if (g > cap) g = cap;
-    return (unsigned)(g > 0 ? g : 1);
-}
-
 void launch_center(const TcWs &t, int ray_mode, int d, int K, const int32_t *n_rows_dev, int n_rows_max,
                    const int32_t *act, const float *X, const float *u32, const double *texit, int n_steps,
                    long long flat0, cudaStream_t s) {
     const int ldp = ldp_of(d, t.prec);
-    const long long items = (long long)K * t.rows * (ldp / (t.prec == SB_PREC_BF16 ? 8 : 4));
+    const int ncg = ldp / (t.prec == SB_PREC_BF16 ? 8 : 4);
+    int rows = (n_rows_max + BM - 1) / BM * BM;
+    if (rows > (int)t.rows) rows = (int)t.rows;
+    const dim3 grid((unsigned)(((long long)rows * ncg + 255) / 256), (unsigned)K);
     note_launch();
     if (t.prec == SB_PREC_BF16)
-        k_tc_center<SB_PREC_BF16><<<grid_for(items), 256, 0, s>>>(ray_mode, d, K, (int)t.rows, ldp, n_rows_dev,
-                                                                 n_rows_max, act, X, d, u32, texit, n_steps, flat0,
-                                                                 (const float *)t.p[2], (const float *)t.p[3],
-                                                                 t.p[9]);
+        k_tc_center<SB_PREC_BF16><<<grid, 256, 0, s>>>(ray_mode, d, (int)t.rows, ldp, n_rows_dev, n_rows_max, act, X,
+                                                      d, u32, texit, n_steps, flat0, (const float *)t.p[2],
+                                                      (const float *)t.p[3], t.p[9]);
     else
-        k_tc_center<SB_PREC_TF32><<<grid_for(items), 256, 0, s>>>(ray_mode, d, K, (int)t.rows, ldp, n_rows_dev,
-                                                                 n_rows_max, act, X, d, u32, texit, n_steps, flat0,
-                                                                 (const float *)t.p[2], (const float *)t.p[3],
-                                                                 t.p[9]);
+        k_tc_center<SB_PREC_TF32><<<grid, 256, 0, s>>>(ray_mode, d, (int)t.rows, ldp, n_rows_dev, n_rows_max, act, X,
+                                                      d, u32, texit, n_steps, flat0, (const float *)t.p[2],
+                                                      (const float *)t.p[3], t.p[9]);
 }
 
 void launch_scale(const TcWs &t, int K, const int32_t *n_rows_dev, int n_rows_max, cudaStream_t s) {
     const int ldz = ldz_of_t(t);
-    const long long items = (long long)K * t.rows * (ldz / (t.prec == SB_PREC_BF16 ? 8 : 4));
+    const int ncg = ldz / (t.prec == SB_PREC_BF16 ? 8 : 4);
+    int rows = (n_rows_max + BM - 1) / BM * BM;
+    if (rows > (int)t.rows) rows = (int)t.rows;
+    const dim3 grid((unsigned)(((long long)rows * ncg + 255) / 256), (unsigned)K);
     note_launch();
     if (t.prec == SB_PREC_BF16)
-        k_tc_scale<SB_PREC_BF16><<<grid_for(items), 256, 0, s>>>(K, (int)t.rows, ldz, n_rows_dev, n_rows_max,
-                                                                (const float *)t.p[6], t.p[4]);
+        k_tc_scale<SB_PREC_BF16><<<grid, 256, 0, s>>>(K, (int)t.rows, ldz, n_rows_dev, n_rows_max,
+                                                     (const float *)t.p[6], t.p[4]);
     else
-        k_tc_scale<SB_PREC_TF32><<<grid_for(items), 256, 0, s>>>(K, (int)t.rows, ldz, n_rows_dev, n_rows_max,
-                                                                (const float *)t.p[6], t.p[4]);
+        k_tc_scale<SB_PREC_TF32><<<grid, 256, 0, s>>>(K, (int)t.rows, ldz, n_rows_dev, n_rows_max,
+                                                     (const float *)t.p[6], t.p[4]);
 }
 
 TcArgs base_args(const ProbView &pv, const TcWs &t) {
@@ -798,7 +811,7 @@ bool tc_available(int prec) { return (prec == SB_PREC_BF16 || prec == SB_PREC_TF
 // [7] X32 (points), [8] G32 (points), [9] A1 [K][rows][ldp] (centred GEMM1 operand)
 void carve_tc(Carver &cv, TcWs &t, int rows, int d, int K, int prec) {
     const int e = esz(prec), ldp = ldp_of(d, prec), bn = bn_of(d);
-    const int nct = (d + bn - 1) / bn;
+    const int nct = (d + 63) / 64;  // partials sized for the narrowest tile the tuner may pick
     rows = (rows + BM - 1) / BM * BM;
     t.rows = rows;
     t.prec = prec;
@@ -831,6 +844,98 @@ bool tc_maps_for_rows(TcWs &t) {
            make_map(&t.mapZ, t.p[4], t.d, (int)t.rows, t.K, t.ldz, t.prec, BM);
 }
 
+// ------------------------------------------------------------------ tile autotuner
+// The output tile width BN of both GEMMs is picked per (d, K, precision) by
+// timing GEMM1 + GEMM2 for every candidate on this call's scratch (MMA timing
+// does not depend on the values), once per process; SB_TUNE=0 uses the
+// heuristic instead, SB_TUNE_CACHE=<file> keeps the choices across processes.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = std::getenv("SB_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    int d, K, p, bn;
+    while (std::fscanf(f, " {\"d\": %d, \"K\": %d, \"prec\": %d, \"bn\": %d}", &d, &K, &p, &bn) == 4)
+        g_tune[std::make_tuple(d, K, p)] = bn;
+    std::fclose(f);
+}
+
+void tune_store_locked() {
+    const char *path = std::getenv("SB_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "w");
+    if (!f) return;
+    for (auto &kv : g_tune)
+        std::fprintf(f, "{\"d\": %d, \"K\": %d, \"prec\": %d, \"bn\": %d}\n", std::get<0>(kv.first),
+                     std::get<1>(kv.first), std::get<2>(kv.first), kv.second);
+    std::fclose(f);
+}
+
+float time_tile(const ProbView &pv, TcWs &t, int bn, cudaStream_t s) {
+    const int d = pv.d, K = pv.K, ldp = ldp_of(d, t.prec);
+    TcWs u = t;
+    u.bn = bn;
+    if (!make_map(&u.mapT, u.p[0], d, d, K, ldp, u.prec, bn) || !make_map(&u.mapB, u.p[1], d, d, K, ldp, u.prec, bn))
+        return -1.f;
+    TcArgs a = base_args(pv, u);
+    a.n_rows_max = (int)(u.rows < 2048 ? u.rows : 2048);
+    a.G = (float *)u.p[8];
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.f;
+    float best = -1.f;
+    for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, s);
+        launch_gemm_any(u.prec, MODE_ZW, bn, u.mapA1, u.mapT, a, s);
+        launch_gemm_any(u.prec, MODE_G, bn, u.mapZ, u.mapB, a, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && (best < 0.f || ms < best)) best = ms;  // first repetition warms up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+int pick_tile(const ProbView &pv, TcWs &t, cudaStream_t s) {
+    const auto key = std::make_tuple(pv.d, pv.K, t.prec);
+    const char *off = std::getenv("SB_TUNE");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+    int bn = bn_of(pv.d);
+    if (!(off && off[0] == '0')) {
+        float best = -1.f;
+        for (int cand : {64, 128, 256}) {
+            if (cand > 64 && (pv.d + 63) / 64 * 64 <= cand / 2) continue;  // tile mostly padding
+            const float ms = time_tile(pv, t, cand, s);
+            if (ms > 0.f && (best < 0.f || ms < best)) {
+                best = ms;
+                bn = cand;
+            }
+        }
+    }
+    g_tune[key] = bn;
+    tune_store_locked();
+    return bn;
+}
+}  // namespace
+
+int tc_tuned_tile(int d, int K, int prec) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(d, K, prec));
+    return it == g_tune.end() ? 0 : it->second;
+}
+
 sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s) {
     const int d = pv.d, K = pv.K;
     const int ldp = ldp_of(d, t.prec);
@@ -841,9 +946,10 @@ sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s) {
         k_tc_convert_L<float><<<1184, 256, 0, s>>>(d, K, ldp, pv.L, (float *)t.p[0], (float *)t.p[1]);
     note_launch();
     k_tc_convert_vec<<<(K * d + 255) / 256, 256, 0, s>>>(d, K, pv.mu, pv.c, (float *)t.p[2], (float *)t.p[3]);
+    if (!tc_maps_for_rows(t)) return SB_ERR_CUDA;
+    t.bn = pick_tile(pv, t, s);
     if (!make_map(&t.mapT, t.p[0], d, d, K, ldp, t.prec, t.bn) || !make_map(&t.mapB, t.p[1], d, d, K, ldp, t.prec, t.bn))
         return SB_ERR_CUDA;
-    if (!tc_maps_for_rows(t)) return SB_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
 }
 
