@@ -316,6 +316,7 @@ def main():
         "clocks": clocks,
         "roofline": roof,
         "kernel_ms": share,
+        "step_ms": [round(t, 3) for t in times],
     }
     if rank == 0 and not args.no_e2e:
         res["e2e"] = e2e_measure(sb, inst, cfg, c, args, evals_per_step)

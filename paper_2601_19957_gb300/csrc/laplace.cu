@@ -26,16 +26,74 @@ namespace {
 constexpr int NB = 32;  // Cholesky block
 
 // ------------------------------------------------------------------ dedup
-// Greedy rounds in one CTA of 1024 threads. `elig` marks points that take part.
-__global__ void __launch_bounds__(1024) k_dedup(int n, int d, const double *X, const double *ell,
-                                                const int8_t *status, const uint8_t *keep_in, double tau_scale,
-                                                const double *wmax, int cap, int32_t *reps, int32_t *n_reps,
-                                                uint8_t *assigned) {
-    __shared__ double s_l[32];
-    __shared__ int s_i[32];
+// Greedy rounds over a grid of co-resident CTAs (cooperative launch). CTA b
+// owns points [b*per, (b+1)*per) and their `assigned` flags. Each round:
+//   1. every CTA reduces its unassigned points to (max l, lowest index) and
+//      publishes it in the round's partial slot (two slots, alternating);
+//   2. one grid barrier;
+//   3. every CTA reduces the partials itself (same order, same result), so
+//      all know the representative without a second barrier; the owner marks
+//      it, CTA 0 records it;
+//   4. every CTA tests its unassigned points against the representative,
+//      one warp per point: coalesced 32-coordinate slices, leaving at the
+//      first coordinate farther than tau (a warp vote).
+// A slot is rewritten two rounds later, after every CTA has passed the
+// barrier of the round in between, so it is never overwritten while read.
+// The barrier wait is bounded: on timeout the CTA flags SB_DEV_TIMEOUT and
+// leaves; every other CTA then times out at its next barrier.
+constexpr int DD_THREADS = 256;
+constexpr long long kBarrierSpins = 1ll << 22;
+
+__device__ bool grid_barrier(uint32_t *bar, uint32_t n_blocks, int32_t *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t *gen = bar + 1;
+        const uint32_t g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) == n_blocks - 1) {
+            bar[0] = 0;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g) {
+                if (++it > kBarrierSpins) {
+                    ok = 0;
+                    atomicOr(err, SB_DEV_TIMEOUT);
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// (l, index) order of the greedy: larger l first, ties to the lower index; index < 0 is "none".
+__device__ __forceinline__ bool dd_better(double l, int i, double bl, int bi) {
+    return i >= 0 && (bi < 0 || l > bl || (l == bl && i < bi));
+}
+
+__global__ void __launch_bounds__(DD_THREADS) k_dedup(int n, int d, const double *X, const double *ell,
+                                                      const int8_t *status, const uint8_t *keep_in, double tau_scale,
+                                                      const double *wmax, int cap, int32_t *reps, int32_t *n_reps,
+                                                      uint8_t *assigned, double *part_l, int32_t *part_i,
+                                                      uint32_t *bar, int32_t *err) {
+    extern __shared__ double s_xb[];  // [d] the round's representative
+    __shared__ double s_l[DD_THREADS / 32];
+    __shared__ int s_i[DD_THREADS / 32];
     __shared__ int s_best;
+    const int G = gridDim.x;
+    const int per = (n + G - 1) / G;
+    const int w0 = blockIdx.x * per, w1 = min(n, w0 + per);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const double tau = tau_scale * wmax[0];
-    for (int w = threadIdx.x; w < n; w += blockDim.x) {
+    for (int w = w0 + threadIdx.x; w < w1; w += DD_THREADS) {
         bool el = isfinite(ell[w]);
         if (status && status[w] == SB_WALKER_NONFINITE) el = false;
         if (keep_in && !keep_in[w]) el = false;
@@ -43,14 +101,14 @@ __global__ void __launch_bounds__(1024) k_dedup(int n, int d, const double *X, c
     }
     __syncthreads();
     int count = 0;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    while (true) {
+    for (int round = 0;; ++round) {
+        // 1. this CTA's best unassigned point
         double bl = -INFINITY;
         int bi = -1;
-        for (int w = threadIdx.x; w < n; w += blockDim.x) {
+        for (int w = w0 + threadIdx.x; w < w1; w += DD_THREADS) {
             if (assigned[w]) continue;
             const double l = ell[w];
-            if (bi < 0 || l > bl) {  // strided ascending: first seen has the lower index
+            if (bi < 0 || l > bl) {  // strided ascending: the first seen has the lower index
                 bl = l;
                 bi = w;
             }
@@ -59,7 +117,7 @@ __global__ void __launch_bounds__(1024) k_dedup(int n, int d, const double *X, c
         for (int o = 16; o > 0; o >>= 1) {
             const double ol = __shfl_xor_sync(0xffffffffu, bl, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (oi >= 0 && (bi < 0 || ol > bl || (ol == bl && oi < bi))) {
+            if (dd_better(ol, oi, bl, bi)) {
                 bl = ol;
                 bi = oi;
             }
@@ -69,21 +127,58 @@ __global__ void __launch_bounds__(1024) k_dedup(int n, int d, const double *X, c
             s_i[wid] = bi;
         }
         __syncthreads();
+        const int slot = (round & 1) * G;
         if (threadIdx.x == 0) {
             double b = -INFINITY;
             int ib = -1;
-            for (int q = 0; q < 32; ++q) {
-                const int oi = s_i[q];
-                const double ol = s_l[q];
-                if (oi >= 0 && (ib < 0 || ol > b || (ol == b && oi < ib))) {
-                    b = ol;
-                    ib = oi;
+            for (int q = 0; q < DD_THREADS / 32; ++q)
+                if (dd_better(s_l[q], s_i[q], b, ib)) {
+                    b = s_l[q];
+                    ib = s_i[q];
                 }
+            part_l[slot + blockIdx.x] = b;
+            part_i[slot + blockIdx.x] = ib;
+        }
+        // 2.
+        if (!grid_barrier(bar, (uint32_t)G, err)) break;
+        // 3. the global best from the partials (read past L1: written by other CTAs)
+        bl = -INFINITY;
+        bi = -1;
+        for (int q = threadIdx.x; q < G; q += DD_THREADS) {
+            const double l = __ldcg(part_l + slot + q);
+            const int i = __ldcg(part_i + slot + q);
+            if (dd_better(l, i, bl, bi)) {
+                bl = l;
+                bi = i;
             }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ol = __shfl_xor_sync(0xffffffffu, bl, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (dd_better(ol, oi, bl, bi)) {
+                bl = ol;
+                bi = oi;
+            }
+        }
+        __syncthreads();  // s_l / s_i of step 1 fully consumed
+        if (lane == 0) {
+            s_l[wid] = bl;
+            s_i[wid] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = -INFINITY;
+            int ib = -1;
+            for (int q = 0; q < DD_THREADS / 32; ++q)
+                if (dd_better(s_l[q], s_i[q], b, ib)) {
+                    b = s_l[q];
+                    ib = s_i[q];
+                }
             s_best = ib;
             if (ib >= 0) {
-                assigned[ib] = 1;
-                if (count < cap) reps[count] = ib;
+                if (ib >= w0 && ib < w1) assigned[ib] = 1;
+                if (blockIdx.x == 0 && count < cap) reps[count] = ib;
             }
         }
         __syncthreads();
@@ -91,21 +186,27 @@ __global__ void __launch_bounds__(1024) k_dedup(int n, int d, const double *X, c
         if (best < 0) break;
         ++count;
         if (count >= cap) break;
+        // 4. L-infinity test of this CTA's unassigned points against the representative
         const double *xb = X + (size_t)best * d;
-        for (int w = threadIdx.x; w < n; w += blockDim.x) {
+        for (int i = threadIdx.x; i < d; i += DD_THREADS) s_xb[i] = xb[i];
+        __syncthreads();
+        for (int w = w0 + wid; w < w1; w += DD_THREADS / 32) {
             if (assigned[w]) continue;
             const double *xw = X + (size_t)w * d;
             bool within = true;
-            for (int i = 0; i < d; ++i)
-                if (fabs(xw[i] - xb[i]) > tau) {
+            for (int i0 = 0; i0 < d; i0 += 32) {
+                const int i = i0 + lane;
+                const bool far = i < d && fabs(xw[i] - s_xb[i]) > tau;
+                if (__any_sync(0xffffffffu, far)) {
                     within = false;
                     break;
                 }
-            if (within) assigned[w] = 1;
+            }
+            if (within && lane == 0) assigned[w] = 1;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) *n_reps = count < cap ? count : cap;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_reps = count < cap ? count : cap;
 }
 
 __global__ void __launch_bounds__(256) k_gather_rows(int d, const double *X, const int32_t *idx, const int32_t *n_idx,
@@ -590,9 +691,26 @@ __global__ void __launch_bounds__(1024) k_laplace_final(int d, const double *XC,
 
 void launch_dedup(int n, int d, const double *X, const double *ell, const int8_t *status, const uint8_t *keep,
                   double tau_scale, const double *wmax, int cap, int32_t *reps, int32_t *n_reps, uint8_t *assigned,
-                  cudaStream_t s) {
+                  const DedupScratch &sc, cudaStream_t s) {
+    // one CTA per 128 points up to one per SM (kept small so that concurrent
+    // solves on other streams can still be co-resident)
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    int G = (n + 127) / 128;
+    if (G > sms) G = sms;
+    if (G > kDedupMaxGrid) G = kDedupMaxGrid;
+    if (G < 1) G = 1;
+    cudaMemsetAsync(sc.bar, 0, 2 * sizeof(uint32_t), s);
+    void *args[] = {&n, &d, &X, &ell, &status, &keep, &tau_scale, &wmax, &cap, &reps, &n_reps, &assigned,
+                    const_cast<double **>(&sc.part_l), const_cast<int32_t **>(&sc.part_i),
+                    const_cast<uint32_t **>(&sc.bar), const_cast<int32_t **>(&sc.err)};
     note_launch();
-    k_dedup<<<1, 1024, 0, s>>>(n, d, X, ell, status, keep, tau_scale, wmax, cap, reps, n_reps, assigned);
+    cudaLaunchCooperativeKernel((const void *)k_dedup, dim3(G), dim3(DD_THREADS), args, sizeof(double) * d, s);
 }
 
 void launch_gather_rows(int d, int cap, const double *X, const int32_t *idx, const int32_t *n_idx, double *out,

@@ -14,52 +14,35 @@
 // same matrix the two-loop recursion applies (App. A.5), so the direction is
 // identical in exact arithmetic; what changes is the data flow. The two-loop
 // walks the pairs with a serial dependency (each alpha_i needs the q left by
-// the previous pair), so a walker waits on one memory latency per pair. Here
-// one pass computes all inner products S^T g, Y^T g and the new pair's row and
-// column of S^T Y and Y^T Y at once (all loads independent), an m x m
-// triangular solve gives the coefficients, and a second pass forms
-// p = -gamma g - S a + gamma Y w. The m x m matrices S^T Y and Y^T Y live per
-// walker in HBM and are updated incrementally, so the history S, Y is read
-// twice per iteration (the second read mostly from L2) and never re-walked.
+// the previous pair). Here one pass computes all inner products S^T g, Y^T g
+// and the new pair's row and column of S^T Y and Y^T Y at once (independent
+// loads, several pairs in flight), an m x m triangular solve gives the
+// coefficients, and a second pass forms p = -gamma g - S a + gamma Y w. The
+// m x m matrices S^T Y and Y^T Y live per walker in HBM and are updated
+// incrementally, so the history S, Y is read twice per iteration (the second
+// read mostly from L2) and never re-walked.
 //
-// History storage is FP32 or bf16 (the BF16-likelihood path stores bf16 pairs:
-// half the bytes of the stream that bounds this kernel).
-//
-// Layout: thread t of the CTA owns coordinates 4t..4t+3 (float4, d <= 1024).
-#include <cuda_bf16.h>
-#include <stdlib.h>
-
+// A walker's step is a chain of dependent phases (reductions, the m x m
+// solve), so the SM is kept busy by several walkers at once: CT threads per
+// walker, each thread owning the float4 groups at coordinates 4 (t + q CT),
+// q < 1024 / (4 CT).
 #include "sb_lbfgs.cuh"
 
 namespace sb {
 
 namespace {
 
-constexpr int CTA = 256;
-constexpr int NW = CTA / 32;
-
-// Sum of NV per-thread values over the CTA (sh holds NW * NV floats); every thread gets the totals.
-// One barrier: callers alternate between two scratch buffers, so a buffer is
-// never rewritten before every thread has read it (the next call's barrier
-// orders it).
-template <int NV>
-__device__ __forceinline__ void block_sum(float (&v)[NV], float *sh) {
-    static_assert(NV <= 20, "block_sum scratch holds 20 values per warp");
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
-    if (lane == 0)
-#pragma unroll
-        for (int j = 0; j < NV; ++j) sh[wid * NV + j] = v[j];
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        float t = 0.f;
-#pragma unroll
-        for (int q = 0; q < NW; ++q) t += sh[q * NV + j];
-        v[j] = t;
-    }
-}
+template <int CT>
+struct Cfg {
+    static constexpr int NW = CT / 32;            // warps per walker
+    static constexpr int VPT = kMaxD / (4 * CT);  // float4 groups per thread
+    static constexpr int PG = CT >= 256 ? 4 : 2;  // pairs per pass-1 reduction
+    static constexpr int MINB = CT >= 256 ? 2 : 4; // CTAs per SM
+    static constexpr int DEPTH = CT >= 256 ? 2 : 3; // pair groups in flight (cp.async ring)
+    // ring bytes: DEPTH groups x PG pairs x (s, y) x VPT float4 per thread
+    static constexpr int RING_F4 = DEPTH * PG * 2 * VPT * CT;
+};
+constexpr int kCT = 128;  // threads per walker used by the solver
 
 // Vector accesses need 16-byte aligned rows: d % 4 == 0 (rows start at multiples of d).
 __device__ __forceinline__ float4 ld4(const float *p, int i0, int d) {
@@ -85,58 +68,112 @@ __device__ __forceinline__ float dot4(float4 a, float4 b) { return a.x * b.x + a
 __device__ __forceinline__ float4 axpy4(float a, float4 x, float4 y) {
     return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
 }
+__device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
-// History storage: FP32, or bf16 (half the bytes of the dominant stream). Inner
-// products and S^T Y / Y^T Y are formed from the stored (rounded) vectors, so the
-// step applies the exact L-BFGS matrix of the stored pairs.
-__device__ __forceinline__ float4 ldh4(const float *p, int i0, int d) { return ld4(p, i0, d); }
-__device__ __forceinline__ float4 ldh4(const __nv_bfloat16 *p, int i0, int d) {
-    if (((d & 3) == 0) && i0 + 3 < d) {
-        const uint2 u = *reinterpret_cast<const uint2 *>(p + i0);
-        const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&u.x);
-        const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&u.y);
-        return make_float4(__low2float(a), __high2float(a), __low2float(b), __high2float(b));
+// Per-thread asynchronous copies global -> shared (16 bytes, L2 only). A thread
+// only ever reads back the chunks it copied itself, so completing its own
+// groups (cp.async.wait_group) is all the synchronisation the ring needs.
+__device__ __forceinline__ void cp_async16(float4 *dst, const float *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// A vector of d coordinates as this thread's VPT float4 groups.
+template <int CT>
+struct Vec {
+    float4 v[Cfg<CT>::VPT];
+    __device__ __forceinline__ static int i0(int q) { return 4 * ((int)threadIdx.x + q * CT); }
+    __device__ __forceinline__ void load(const float *p, int d) {
+#pragma unroll
+        for (int q = 0; q < Cfg<CT>::VPT; ++q) v[q] = ld4(p, i0(q), d);
     }
-    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i0 + 0 < d) r.x = __bfloat162float(p[i0 + 0]);
-    if (i0 + 1 < d) r.y = __bfloat162float(p[i0 + 1]);
-    if (i0 + 2 < d) r.z = __bfloat162float(p[i0 + 2]);
-    if (i0 + 3 < d) r.w = __bfloat162float(p[i0 + 3]);
+    __device__ __forceinline__ void store(float *p, int d) const {
+#pragma unroll
+        for (int q = 0; q < Cfg<CT>::VPT; ++q) st4(p, i0(q), d, v[q]);
+    }
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int q = 0; q < Cfg<CT>::VPT; ++q) v[q] = zero4();
+    }
+};
+template <int CT>
+__device__ __forceinline__ float dotv(const Vec<CT> &a, const Vec<CT> &b) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < Cfg<CT>::VPT; ++q) s += dot4(a.v[q], b.v[q]);
+    return s;
+}
+// y += c x
+template <int CT>
+__device__ __forceinline__ void axpyv(float c, const Vec<CT> &x, Vec<CT> &y) {
+#pragma unroll
+    for (int q = 0; q < Cfg<CT>::VPT; ++q) y.v[q] = axpy4(c, x.v[q], y.v[q]);
+}
+// a + c b
+template <int CT>
+__device__ __forceinline__ Vec<CT> lincomb(const Vec<CT> &a, float c, const Vec<CT> &b) {
+    Vec<CT> r;
+#pragma unroll
+    for (int q = 0; q < Cfg<CT>::VPT; ++q) r.v[q] = axpy4(c, b.v[q], a.v[q]);
     return r;
 }
-__device__ __forceinline__ void sth4(float *p, int i0, int d, float4 v) { st4(p, i0, d, v); }
-__device__ __forceinline__ void sth4(__nv_bfloat16 *p, int i0, int d, float4 v) {
-    if (((d & 3) == 0) && i0 + 3 < d) {
-        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
-        uint2 u;
-        u.x = *reinterpret_cast<uint32_t *>(&a);
-        u.y = *reinterpret_cast<uint32_t *>(&b);
-        *reinterpret_cast<uint2 *>(p + i0) = u;
-        return;
+template <int CT>
+__device__ __forceinline__ Vec<CT> subv(const Vec<CT> &a, const Vec<CT> &b) {
+    Vec<CT> r;
+#pragma unroll
+    for (int q = 0; q < Cfg<CT>::VPT; ++q)
+        r.v[q] = make_float4(a.v[q].x - b.v[q].x, a.v[q].y - b.v[q].y, a.v[q].z - b.v[q].z, a.v[q].w - b.v[q].w);
+    return r;
+}
+template <int CT>
+__device__ __forceinline__ bool finitev(const Vec<CT> &a) {
+    bool f = true;
+#pragma unroll
+    for (int q = 0; q < Cfg<CT>::VPT; ++q)
+        f = f && isfinite(a.v[q].x) && isfinite(a.v[q].y) && isfinite(a.v[q].z) && isfinite(a.v[q].w);
+    return f;
+}
+template <int CT>
+__device__ __forceinline__ float absmaxv(const Vec<CT> &a) {
+    float m = 0.f;
+#pragma unroll
+    for (int q = 0; q < Cfg<CT>::VPT; ++q)
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(a.v[q].x), fabsf(a.v[q].y)), fmaxf(fabsf(a.v[q].z), fabsf(a.v[q].w))));
+    return m;
+}
+
+// Sum of NV per-thread values over the CTA; every thread gets the totals.
+// One barrier: callers alternate between two scratch buffers, so a buffer is
+// never rewritten before every thread has read it (the next call's barrier
+// orders it).
+template <int CT, int NV>
+__device__ __forceinline__ void block_sum(float (&v)[NV], float *sh) {
+    static_assert(NV <= 32, "block_sum scratch holds 32 values per warp");
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) sh[wid * NV + j] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < Cfg<CT>::NW; ++q) t += sh[q * NV + j];
+        v[j] = t;
     }
-    if (i0 + 0 < d) p[i0 + 0] = __float2bfloat16_rn(v.x);
-    if (i0 + 1 < d) p[i0 + 1] = __float2bfloat16_rn(v.y);
-    if (i0 + 2 < d) p[i0 + 2] = __float2bfloat16_rn(v.z);
-    if (i0 + 3 < d) p[i0 + 3] = __float2bfloat16_rn(v.w);
 }
-// The value a stored vector reads back as.
-__device__ __forceinline__ float4 stored(float4 v, const float *) { return v; }
-__device__ __forceinline__ float4 stored(float4 v, const __nv_bfloat16 *) {
-    return make_float4(__bfloat162float(__float2bfloat16_rn(v.x)), __bfloat162float(__float2bfloat16_rn(v.y)),
-                       __bfloat162float(__float2bfloat16_rn(v.z)), __bfloat162float(__float2bfloat16_rn(v.w)));
-}
-
-constexpr int LD = kMaxM + 1;  // padded row stride of the m x m matrices: rows and columns both conflict-free
-
-struct Shared {
-    float red2[2][NW * 32];  // reduction scratch, used alternately (see block_sum)
-    float u1[kMaxM], u2[kMaxM], nsy[kMaxM], nys[kMaxM], nyy[kMaxM];
-    float ca[kMaxM], cw[kMaxM], dinv[kMaxM];
-    float R[kMaxM * LD];   // S^T Y in logical (oldest-first) order
-    float YY[kMaxM * LD];  // Y^T Y in logical order
-    float gamma;
-    int slot_of[kMaxM];
-};
 
 // Reduce 32 per-lane values over the warp with 31 shuffles (recursive halving:
 // at each level a lane keeps one half of its values and adds its partner's
@@ -156,25 +193,50 @@ __device__ __forceinline__ float warp_transpose_sum(float (&v)[32]) {
     return v[0];
 }
 
-// Sums over the CTA of NV <= 32 per-thread values; thread t < NV returns total
-// t (the others return garbage). One barrier, alternating scratch as block_sum.
-template <int NV>
-__device__ __forceinline__ float block_sum_scatter(const float (&in)[NV], float *sh) {
-    float v[32];
+// The same over 16 values with 16 shuffles: halving within each half-warp,
+// then one exchange between the halves. Lanes j and j + 16 return value j.
+__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16]) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = j < NV ? in[j] : 0.f;
+    for (int o = 8; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < o; ++j) {
+            const float send = up ? v[j] : v[j + o];
+            const float keep = up ? v[j + o] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
+// Sums over the CTA of NV <= 32 per-thread values; thread t < NV returns
+// total t (the others return garbage). One barrier, alternating scratch as block_sum.
+template <int CT, int NV>
+__device__ __forceinline__ float block_sum_scatter(const float (&in)[NV], float *sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    sh[wid * 32 + lane] = warp_transpose_sum(v);
+    if (NV <= 16) {
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = j < NV ? in[j] : 0.f;
+        const float t = warp_transpose_sum16(v);
+        if (lane < 16) sh[wid * 32 + lane] = t;
+    } else {
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = j < NV ? in[j] : 0.f;
+        sh[wid * 32 + lane] = warp_transpose_sum(v);
+    }
     __syncthreads();
     float t = 0.f;
     if (threadIdx.x < NV)
 #pragma unroll
-        for (int q = 0; q < NW; ++q) t += sh[q * 32 + threadIdx.x];
+        for (int q = 0; q < Cfg<CT>::NW; ++q) t += sh[q * 32 + threadIdx.x];
     return t;
 }
 
 // NV sums and one maximum over the CTA with a single barrier; every thread gets all.
-template <int NV>
+template <int CT, int NV>
 __device__ __forceinline__ void block_sum_max(float (&v)[NV], float &mx, float *sh) {
     static_assert(NV + 1 <= 32, "scratch holds 32 values per warp");
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -191,202 +253,284 @@ __device__ __forceinline__ void block_sum_max(float (&v)[NV], float &mx, float *
     for (int j = 0; j < NV; ++j) {
         float t = 0.f;
 #pragma unroll
-        for (int q = 0; q < NW; ++q) t += sh[q * 32 + j];
+        for (int q = 0; q < Cfg<CT>::NW; ++q) t += sh[q * 32 + j];
         v[j] = t;
     }
     float m = sh[NV];
 #pragma unroll
-    for (int q = 1; q < NW; ++q) m = fmaxf(m, sh[q * 32 + NV]);
+    for (int q = 1; q < Cfg<CT>::NW; ++q) m = fmaxf(m, sh[q * 32 + NV]);
     mx = m;
 }
 
+// Odd row stride of the m x m matrices: their rows and their columns are both
+// free of shared-memory bank conflicts.
+__host__ __device__ __forceinline__ int mm_ld(int m) { return (m & 1) ? m + 2 : m + 1; }
+
+template <int CT>
+struct Shared {
+    float red2[2][Cfg<CT>::NW * 32];  // reduction scratch, used alternately (see block_sum)
+    float u1[kMaxM], u2[kMaxM], nsy[kMaxM], nys[kMaxM], nyy[kMaxM];
+    float ca[kMaxM], cw[kMaxM], dinv[kMaxM];
+    float gamma;
+    int slot_of[kMaxM];
+    // dynamic shared memory: the pair ring, then S^T Y and Y^T Y (logical order, stride ld)
+    float4 *ring;
+    float *R, *YY;
+    int ld;
+};
+
+// S^T Y and Y^T Y of the walker in logical order: the new pair's row and column
+// (logical cn, or -1) from pass 1, the rest from the per-walker slot-indexed
+// copies, which receive the new row and column at the same time. Returns bytes moved.
+template <int CT>
+__device__ __forceinline__ uint64_t stage_mm(Shared<CT> &sh, float *msy, float *myy, int count, int m, int cn) {
+    for (int e = threadIdx.x; e < count * count; e += CT) {
+        const int i = e / count, j = e % count;
+        const int si = sh.slot_of[i], sj = sh.slot_of[j];
+        float r, yy;
+        if (j == cn) {
+            r = sh.nsy[i];
+            yy = sh.nyy[i];
+        } else if (i == cn) {
+            r = sh.nys[j];
+            yy = sh.nyy[j];
+        } else {
+            r = msy[(size_t)si * m + sj];
+            yy = myy[(size_t)si * m + sj];
+        }
+        if (i == cn || j == cn) {
+            msy[(size_t)si * m + sj] = r;
+            myy[(size_t)si * m + sj] = yy;
+        }
+        sh.R[i * sh.ld + j] = r;
+        sh.YY[i * sh.ld + j] = yy;
+    }
+    return (uint64_t)count * count * 8 + (cn >= 0 ? (uint64_t)(2 * count - 1) * 8 : 0);
+}
+
+// Warp that runs the m x m solve: CTAs are dealt to SMs round-robin, so the
+// CTAs co-resident on one SM have consecutive values of blockIdx / (grid / MINB).
+template <int CT>
+__device__ __forceinline__ int solver_warp() {
+    const int per = max(1, (int)gridDim.x / Cfg<CT>::MINB);
+    return (int)(blockIdx.x / per) % Cfg<CT>::NW;
+}
+
+// The m x m part (one warp): w = R^-1 u1, gamma, tv = D w + gamma Y^T Y w -
+// gamma Y^T g, a = R^-T tv. Column-oriented substitutions: lane j holds the
+// running right-hand side of rows j and j + 32; each step broadcasts one
+// solved unknown. Results in sh.cw, sh.ca, sh.gamma.
+template <int CT>
+__device__ __forceinline__ void solve_mm(Shared<CT> &sh, int c) {
+    const int lane = threadIdx.x & 31;
+    const int LD = sh.ld;
+    const float *R = sh.R, *YY = sh.YY;
+    for (int i = lane; i < c; i += 32) sh.dinv[i] = 1.f / R[i * LD + i];
+    __syncwarp();
+    float acc0 = lane < c ? sh.u1[lane] : 0.f, acc1 = lane + 32 < c ? sh.u1[lane + 32] : 0.f;
+    for (int i = c - 1; i >= 0; --i) {
+        const float wi = __shfl_sync(0xffffffffu, i < 32 ? acc0 : acc1, i & 31) * sh.dinv[i];
+        if (lane == 0) sh.cw[i] = wi;
+        if (lane < i) acc0 -= R[lane * LD + i] * wi;
+        if (lane + 32 < i) acc1 -= R[(lane + 32) * LD + i] * wi;
+    }
+    __syncwarp();
+    const float gam = R[(c - 1) * LD + (c - 1)] / YY[(c - 1) * LD + (c - 1)];
+    if (lane == 0) sh.gamma = gam;
+    float tv0 = 0.f, tv1 = 0.f;
+    if (lane < c) {
+        float yyw = 0.f;
+        for (int j = 0; j < c; ++j) yyw += YY[lane * LD + j] * sh.cw[j];
+        tv0 = R[lane * LD + lane] * sh.cw[lane] + gam * yyw - gam * sh.u2[lane];
+    }
+    if (lane + 32 < c) {
+        const int i = lane + 32;
+        float yyw = 0.f;
+        for (int j = 0; j < c; ++j) yyw += YY[i * sh.ld + j] * sh.cw[j];
+        tv1 = R[i * LD + i] * sh.cw[i] + gam * yyw - gam * sh.u2[i];
+    }
+    for (int i = 0; i < c; ++i) {
+        const float ai = __shfl_sync(0xffffffffu, i < 32 ? tv0 : tv1, i & 31) * sh.dinv[i];
+        if (lane == 0) sh.ca[i] = ai;
+        if (lane > i && lane < c) tv0 -= R[i * LD + lane] * ai;
+        if (lane + 32 > i && lane + 32 < c) tv1 -= R[i * LD + lane + 32] * ai;
+    }
+}
+
 // Direction for walker state st (count pairs from ring slot head). When
-// new_slot >= 0 the pair in that slot was stored this iteration (it is the
-// newest, logical index count - 1) and the new row/column of S^T Y, Y^T Y is
-// computed in the same pass. Writes P and the unit trial X + P; updates
-// st.dphi / alpha / bt and possibly resets history. Returns the algorithmic
-// bytes it moved.
-template <typename HT>
-__device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<float> &st, int new_slot, float4 g4,
-                              float4 x4, float4 s_new, float4 y_new, float *MSY, float *MYY, Shared &sh, int &par) {
-    const int d = a.d, m = a.m, i0 = 4 * threadIdx.x;
+// new_slot >= 0 the pair in that slot was stored this visit (it is the newest,
+// logical index count - 1) and its row and column of S^T Y, Y^T Y come from the
+// same pass. Writes P and the unit trial X + P; updates st.dphi / alpha / bt
+// and possibly resets the history (steepest descent when p is not a descent
+// direction). Returns the algorithmic bytes moved.
+template <int CT>
+__device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<float> &st, int new_slot,
+                              const Vec<CT> &g, const Vec<CT> &x, const Vec<CT> &s_new, const Vec<CT> &y_new,
+                              float *MSY, float *MYY, Shared<CT> &sh, int &par) {
+    constexpr int PG = Cfg<CT>::PG;
+    const int d = a.d, m = a.m;
     const int count = st.count;
     uint64_t bytes = 0;
-    float4 p4;
+    Vec<CT> p;
+    p.zero();
     if (count > 0) {
-        const HT *S = reinterpret_cast<const HT *>(a.S) + (size_t)w * m * d;
-        const HT *Y = reinterpret_cast<const HT *>(a.Y) + (size_t)w * m * d;
+        const float *S = a.S + (size_t)w * m * d;
+        const float *Y = a.Y + (size_t)w * m * d;
         if (threadIdx.x < count) sh.slot_of[threadIdx.x] = (st.head + threadIdx.x) % m;
         __syncthreads();
-        // pass 1: inner products, four pairs per reduction; the loads of the next
-        // group are issued before the current group is reduced
-        float4 s4[4], y4[4];
-        auto load_group = [&](int i) {
+        // Both passes stream the pairs through the shared-memory ring, DEPTH groups
+        // of PG pairs in flight per thread (cp.async); pass 2's first groups are
+        // issued before the m x m solve, which does not need them.
+        constexpr int D = Cfg<CT>::DEPTH, VPT = Cfg<CT>::VPT;
+        const int ngroups = (count + PG - 1) / PG;
+        const bool vec_ok = (d & 3) == 0;
+        auto rp = [&](int grp, int q, int v, int j) -> float4 * {
+            return sh.ring + ((((size_t)(grp % D) * PG + q) * 2 + v) * VPT + j) * CT + threadIdx.x;
+        };
+        auto issue = [&](int grp) {  // always commits one group (possibly empty)
+            if (grp < ngroups) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                s4[q] = y4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (i + q < count) {
-                    const int slot = sh.slot_of[i + q];
-                    s4[q] = ldh4(S + (size_t)slot * d, i0, d);
-                    y4[q] = ldh4(Y + (size_t)slot * d, i0, d);
+                for (int q = 0; q < PG; ++q) {
+                    const int i = grp * PG + q;
+                    if (i >= count) break;
+                    const size_t row = (size_t)sh.slot_of[i] * d;
+#pragma unroll
+                    for (int j = 0; j < VPT; ++j) {
+                        const int i0 = Vec<CT>::i0(j);
+                        if (vec_ok && i0 + 3 < d) {
+                            cp_async16(rp(grp, q, 0, j), S + row + i0);
+                            cp_async16(rp(grp, q, 1, j), Y + row + i0);
+                        } else {
+                            for (int e = 0; e < 4 && i0 + e < d; ++e) {
+                                cp_async4(reinterpret_cast<float *>(rp(grp, q, 0, j)) + e, S + row + i0 + e);
+                                cp_async4(reinterpret_cast<float *>(rp(grp, q, 1, j)) + e, Y + row + i0 + e);
+                            }
+                        }
+                    }
                 }
             }
+            cp_async_commit();
         };
-        load_group(0);
-        for (int i = 0; i < count; i += 4) {
-            float v[20];
+        auto fetch = [&](int grp, int q, Vec<CT> &sv, Vec<CT> &yv) {  // this thread's chunks of one pair
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                v[q] = dot4(s4[q], g4);            // u1 = S^T g
-                v[4 + q] = dot4(y4[q], g4);        // u2 = Y^T g
-                v[8 + q] = dot4(s4[q], y_new);     // s_i . y_new
-                v[12 + q] = dot4(s_new, y4[q]);    // s_new . y_i
-                v[16 + q] = dot4(y4[q], y_new);    // y_i . y_new
+            for (int j = 0; j < VPT; ++j) {
+                const int i0 = Vec<CT>::i0(j);
+                float4 a4 = *rp(grp, q, 0, j), b4 = *rp(grp, q, 1, j);
+                if (!(i0 + 3 < d)) {  // ragged tail: lanes past d hold stale data
+                    if (i0 + 0 >= d) a4.x = b4.x = 0.f;
+                    if (i0 + 1 >= d) a4.y = b4.y = 0.f;
+                    if (i0 + 2 >= d) a4.z = b4.z = 0.f;
+                    if (i0 + 3 >= d) a4.w = b4.w = 0.f;
+                }
+                sv.v[j] = a4;
+                yv.v[j] = b4;
             }
-            if (i + 4 < count) load_group(i + 4);
-            const float t = block_sum_scatter<20>(v, sh.red2[par++ & 1]);
-            if (threadIdx.x < 20) {
-                const int q = threadIdx.x & 3, k = threadIdx.x >> 2;
+        };
+        // pass 1: inner products, PG pairs per reduction
+#pragma unroll 1
+        for (int g0 = 0; g0 < D; ++g0) issue(g0);
+        for (int grp = 0; grp < ngroups; ++grp) {
+            cp_async_wait<D - 1>();
+            const int i = grp * PG;
+            float v[5 * PG];
+#pragma unroll
+            for (int q = 0; q < PG; ++q) {
+                Vec<CT> s4, y4;
+                if (i + q < count) {
+                    fetch(grp, q, s4, y4);
+                } else {
+                    s4.zero();
+                    y4.zero();
+                }
+                v[q] = dotv(s4, g);               // u1 = S^T g
+                v[PG + q] = dotv(y4, g);          // u2 = Y^T g
+                v[2 * PG + q] = dotv(s4, y_new);  // s_i . y_new
+                v[3 * PG + q] = dotv(s_new, y4);  // s_new . y_i
+                v[4 * PG + q] = dotv(y4, y_new);  // y_i . y_new
+            }
+            issue(grp + D);  // into the slot just read (this thread's reads are done)
+            const float t = block_sum_scatter<CT, 5 * PG>(v, sh.red2[par++ & 1]);
+            if (threadIdx.x < 5 * PG) {
+                const int q = threadIdx.x % PG, k = threadIdx.x / PG;
                 if (i + q < count) {
                     float *dst = k == 0 ? sh.u1 : k == 1 ? sh.u2 : k == 2 ? sh.nsy : k == 3 ? sh.nys : sh.nyy;
                     dst[i + q] = t;
                 }
             }
         }
+#pragma unroll 1
+        for (int g0 = 0; g0 < D; ++g0) issue(g0);  // pass 2's first groups
         __syncthreads();
-        // S^T Y and Y^T Y in logical order: the new pair's row and column from
-        // this pass, the rest from the per-walker copies (slot-indexed, m x m),
-        // which receive the new row and column at the same time
-        float *msy = MSY + (size_t)w * m * m;
-        float *myy = MYY + (size_t)w * m * m;
-        const int cn = new_slot >= 0 ? count - 1 : -1;  // logical index of the new pair
-        for (int e = threadIdx.x; e < count * count; e += CTA) {
-            const int i = e / count, j = e % count;
-            const int si = sh.slot_of[i], sj = sh.slot_of[j];
-            float r, yy;
-            if (j == cn) {
-                r = sh.nsy[i];
-                yy = sh.nyy[i];
-            } else if (i == cn) {
-                r = sh.nys[j];
-                yy = sh.nyy[j];
-            } else {
-                r = msy[(size_t)si * m + sj];
-                yy = myy[(size_t)si * m + sj];
-            }
-            if (i == cn || j == cn) {
-                msy[(size_t)si * m + sj] = r;
-                myy[(size_t)si * m + sj] = yy;
-            }
-            sh.R[i * LD + j] = r;
-            sh.YY[i * LD + j] = yy;
-        }
-        bytes += (uint64_t)count * count * 8 + (cn >= 0 ? (uint64_t)(2 * count - 1) * 8 : 0);
-        // pass 2's first two pairs are fetched before the solve (they do not depend on it)
-        float4 cs[2], cy[2], ns[2], ny[2];
-        auto load_pair2 = [&](int i, float4(&ps)[2], float4(&py)[2]) {
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                ps[q] = py[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (i + q < count) {
-                    const int slot = sh.slot_of[i + q];
-                    ps[q] = ldh4(S + (size_t)slot * d, i0, d);
-                    py[q] = ldh4(Y + (size_t)slot * d, i0, d);
-                }
-            }
-        };
-        load_pair2(0, cs, cy);
+        bytes += stage_mm<CT>(sh, MSY + (size_t)w * m * m, MYY + (size_t)w * m * m, count, m,
+                              new_slot >= 0 ? count - 1 : -1);
         __syncthreads();
-        const int c = count;
-        const int lane = threadIdx.x & 31;
-        if (threadIdx.x < 32) {
-            // Column-oriented substitutions: lane j holds the running right-hand
-            // side of rows j and j + 32; each step broadcasts one solved unknown.
-            for (int i = lane; i < c; i += 32) sh.dinv[i] = 1.f / sh.R[i * LD + i];
-            __syncwarp();
-            // w = R^-1 u1, R upper (R_ij = s_i . y_j for i <= j)
-            float acc0 = lane < c ? sh.u1[lane] : 0.f, acc1 = lane + 32 < c ? sh.u1[lane + 32] : 0.f;
-            for (int i = c - 1; i >= 0; --i) {
-                const float wi = __shfl_sync(0xffffffffu, i < 32 ? acc0 : acc1, i & 31) * sh.dinv[i];
-                if (lane == 0) sh.cw[i] = wi;
-                if (lane < i) acc0 -= sh.R[lane * LD + i] * wi;
-                if (lane + 32 < i) acc1 -= sh.R[(lane + 32) * LD + i] * wi;
-            }
-            __syncwarp();
-            const float gam = sh.R[(c - 1) * LD + (c - 1)] / sh.YY[(c - 1) * LD + (c - 1)];
-            if (lane == 0) sh.gamma = gam;
-            // tv = D w + gamma Y^T Y w - gamma Y^T g   (lane i: rows i, i + 32)
-            float tv0 = 0.f, tv1 = 0.f;
-            if (lane < c) {
-                float yyw = 0.f;
-                for (int j = 0; j < c; ++j) yyw += sh.YY[lane * LD + j] * sh.cw[j];
-                tv0 = sh.R[lane * LD + lane] * sh.cw[lane] + gam * yyw - gam * sh.u2[lane];
-            }
-            if (lane + 32 < c) {
-                const int i = lane + 32;
-                float yyw = 0.f;
-                for (int j = 0; j < c; ++j) yyw += sh.YY[i * LD + j] * sh.cw[j];
-                tv1 = sh.R[i * LD + i] * sh.cw[i] + gam * yyw - gam * sh.u2[i];
-            }
-            // a = R^-T tv (R^T lower)
-            for (int i = 0; i < c; ++i) {
-                const float ai = __shfl_sync(0xffffffffu, i < 32 ? tv0 : tv1, i & 31) * sh.dinv[i];
-                if (lane == 0) sh.ca[i] = ai;
-                if (lane > i && lane < c) tv0 -= sh.R[i * LD + lane] * ai;
-                if (lane + 32 > i && lane + 32 < c) tv1 -= sh.R[i * LD + lane + 32] * ai;
-            }
-        }
+        // the solving warp differs between the CTAs that share an SM (their warp w
+        // would otherwise all sit on the same scheduler)
+        if ((int)(threadIdx.x >> 5) == solver_warp<CT>()) solve_mm<CT>(sh, count);
         __syncthreads();
-        // pass 2: p = -gamma g - S a + gamma Y w, two pairs consumed while the next two load
+        // pass 2: p = -gamma g - S a + gamma Y w
         const float gam = sh.gamma;
-        p4 = make_float4(-gam * g4.x, -gam * g4.y, -gam * g4.z, -gam * g4.w);
-        for (int i = 0; i < count; i += 2) {
-            if (i + 2 < count) load_pair2(i + 2, ns, ny);
+        p.zero();
+        axpyv(-gam, g, p);
+        for (int grp = 0; grp < ngroups; ++grp) {
+            cp_async_wait<D - 1>();
 #pragma unroll
-            for (int q = 0; q < 2; ++q)
-                if (i + q < count) {
-                    p4 = axpy4(-sh.ca[i + q], cs[q], p4);
-                    p4 = axpy4(gam * sh.cw[i + q], cy[q], p4);
+            for (int q = 0; q < PG; ++q) {
+                const int i = grp * PG + q;
+                if (i < count) {
+                    Vec<CT> s4, y4;
+                    fetch(grp, q, s4, y4);
+                    axpyv(-sh.ca[i], s4, p);
+                    axpyv(gam * sh.cw[i], y4, p);
                 }
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                cs[q] = ns[q];
-                cy[q] = ny[q];
             }
+            issue(grp + D);
         }
+        cp_async_wait<0>();  // (only empty groups remain) the ring is free for the next walker
         // the two-loop recursion's history traffic: each pair read in both passes
-        bytes += (uint64_t)4 * count * d * sizeof(HT);
+        bytes += (uint64_t)16 * count * d;
     }
     float dp[1];
     if (count > 0) {
-        dp[0] = dot4(g4, p4);
-        block_sum<1>(dp, sh.red2[par++ & 1]);
+        dp[0] = dotv(g, p);
+        block_sum<CT, 1>(dp, sh.red2[par++ & 1]);
     }
     if (count == 0 || !(dp[0] < 0.f)) {
         st.count = 0;
         st.head = 0;
-        float gg[1] = {dot4(g4, g4)};
-        block_sum<1>(gg, sh.red2[par++ & 1]);
+        float gg[1] = {dotv(g, g)};
+        block_sum<CT, 1>(gg, sh.red2[par++ & 1]);
         const float gn = sqrtf(gg[0]);
-        p4 = make_float4(-g4.x / gn, -g4.y / gn, -g4.z / gn, -g4.w / gn);
-        dp[0] = dot4(g4, p4);
-        block_sum<1>(dp, sh.red2[par++ & 1]);
+#pragma unroll
+        for (int q = 0; q < Cfg<CT>::VPT; ++q)
+            p.v[q] = make_float4(-g.v[q].x / gn, -g.v[q].y / gn, -g.v[q].z / gn, -g.v[q].w / gn);
+        dp[0] = dotv(g, p);
+        block_sum<CT, 1>(dp, sh.red2[par++ & 1]);
     }
     st.dphi = dp[0];
     st.alpha = 1.f;
     st.bt = 0;
-    st4(a.P + (size_t)w * d, i0, d, p4);
-    st4(a.XT + (size_t)w * d, i0, d, make_float4(x4.x + p4.x, x4.y + p4.y, x4.z + p4.z, x4.w + p4.w));
+    p.store(a.P + (size_t)w * d, d);
+    lincomb(x, 1.f, p).store(a.XT + (size_t)w * d, d);
     return bytes + (uint64_t)8 * d;
 }
 
 // Algorithmic bytes of the L-BFGS step launches (added only while counting is on).
 __device__ unsigned long long g_lbfgs_bytes;
 
-template <typename HT, int MINB>
-__global__ void __launch_bounds__(CTA, MINB) k_lbfgs_cta(LbfgsArgs<float> a, float *MSY, float *MYY, int count_bytes) {
-    __shared__ Shared sh;
-    const int d = a.d, m = a.m, i0 = 4 * threadIdx.x;
+template <int CT>
+__global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float> a, float *MSY, float *MYY,
+                                                                int count_bytes) {
+    __shared__ Shared<CT> sh;
+    extern __shared__ __align__(16) float4 dyn[];  // [RING_F4] ring, then R, YY [m][ld]
+    const int d = a.d, m = a.m;
+    if (threadIdx.x == 0) {
+        sh.ring = dyn;
+        sh.ld = mm_ld(m);
+        sh.R = reinterpret_cast<float *>(dyn + Cfg<CT>::RING_F4);
+        sh.YY = sh.R + (size_t)m * sh.ld;
+    }
+    __syncthreads();
     const int n_act = *a.n_act;
     int par = 0;  // alternation of the reduction scratch (identical in every thread)
     uint64_t bytes = 0;
@@ -396,29 +540,29 @@ __global__ void __launch_bounds__(CTA, MINB) k_lbfgs_cta(LbfgsArgs<float> a, flo
         const float ft = a.FT[w];
         float *X = a.X + (size_t)w * d;
         float *G = a.G + (size_t)w * d;
-        const float *XT = a.XT + (size_t)w * d;
-        const float *GT = a.GT + (size_t)w * d;
-        float4 x4 = ld4(X, i0, d), g4 = ld4(G, i0, d);
-        const float4 xt4 = ld4(XT, i0, d), gt4 = ld4(GT, i0, d);
+        Vec<CT> x, g, xt, gt;
+        x.load(X, d);
+        g.load(G, d);
+        xt.load(a.XT + (size_t)w * d, d);
+        gt.load(a.GT + (size_t)w * d, d);
         bytes += (uint64_t)16 * d + 4 + 2 * sizeof(WalkerState<float>);
         // finiteness of the trial gradient, the candidate pair's inner products and
         // max |grad| at the trial, all in one reduction
-        const HT *tag = nullptr;
-        const float4 s4 = stored(make_float4(xt4.x - x4.x, xt4.y - x4.y, xt4.z - x4.z, xt4.w - x4.w), tag);
-        const float4 y4 = stored(make_float4(gt4.x - g4.x, gt4.y - g4.y, gt4.z - g4.z, gt4.w - g4.w), tag);
-        float r4[4] = {(isfinite(gt4.x) && isfinite(gt4.y) && isfinite(gt4.z) && isfinite(gt4.w)) ? 0.f : 1.f,
-                       dot4(s4, s4), dot4(y4, y4), dot4(s4, y4)};
-        float gm = fmaxf(fmaxf(fabsf(gt4.x), fabsf(gt4.y)), fmaxf(fabsf(gt4.z), fabsf(gt4.w)));
-        block_sum_max<4>(r4, gm, sh.red2[par++ & 1]);
+        const Vec<CT> s4 = subv(xt, x), y4 = subv(gt, g);
+        float r4[4] = {finitev(gt) ? 0.f : 1.f, dotv(s4, s4), dotv(y4, y4), dotv(s4, y4)};
+        float gm = absmaxv(gt);
+        block_sum_max<CT, 4>(r4, gm, sh.red2[par++ & 1]);
         const bool finite = isfinite(ft) && r4[0] == 0.f;
         bool newiter = false;
         int new_slot = -1;
-        float4 s_new = make_float4(0.f, 0.f, 0.f, 0.f), y_new = s_new;
+        Vec<CT> s_new, y_new;
+        s_new.zero();
+        y_new.zero();
         if (st.phase == 0) {
-            x4 = xt4;
-            g4 = gt4;
-            st4(X, i0, d, x4);
-            st4(G, i0, d, g4);
+            x = xt;
+            g = gt;
+            x.store(X, d);
+            g.store(G, d);
             bytes += (uint64_t)8 * d;
             st.f = ft;
             st.phase = 1;
@@ -436,19 +580,19 @@ __global__ void __launch_bounds__(CTA, MINB) k_lbfgs_cta(LbfgsArgs<float> a, flo
                     slot = st.head;
                     st.head = (st.head + 1) % m;
                 }
-                sth4(reinterpret_cast<HT *>(a.S) + ((size_t)w * m + slot) * d, i0, d, s4);
-                sth4(reinterpret_cast<HT *>(a.Y) + ((size_t)w * m + slot) * d, i0, d, y4);
+                s4.store(a.S + ((size_t)w * m + slot) * d, d);
+                y4.store(a.Y + ((size_t)w * m + slot) * d, d);
                 if (threadIdx.x == 0) a.rho[(size_t)w * m + slot] = 1.f / r4[3];
-                bytes += (uint64_t)2 * d * sizeof(HT) + 4;
+                bytes += (uint64_t)8 * d + 4;
                 new_slot = slot;
                 s_new = s4;
                 y_new = y4;
             }
             st.flat = (ft >= st.f) ? st.flat + 1 : 0;
-            x4 = xt4;
-            g4 = gt4;
-            st4(X, i0, d, x4);
-            st4(G, i0, d, g4);
+            x = xt;
+            g = gt;
+            x.store(X, d);
+            g.store(G, d);
             bytes += (uint64_t)8 * d;
             st.f = ft;
             ++st.it;
@@ -457,16 +601,15 @@ __global__ void __launch_bounds__(CTA, MINB) k_lbfgs_cta(LbfgsArgs<float> a, flo
             ++st.bt;
             if (st.bt <= a.max_backtracks) {
                 st.alpha *= a.backtrack;
-                const float4 p4 = ld4(a.P + (size_t)w * d, i0, d);
-                st4(a.XT + (size_t)w * d, i0, d,
-                    make_float4(fmaf(st.alpha, p4.x, x4.x), fmaf(st.alpha, p4.y, x4.y), fmaf(st.alpha, p4.z, x4.z),
-                                fmaf(st.alpha, p4.w, x4.w)));
+                Vec<CT> p;
+                p.load(a.P + (size_t)w * d, d);
+                lincomb(x, st.alpha, p).store(a.XT + (size_t)w * d, d);
                 bytes += (uint64_t)8 * d;
             } else if (st.count > 0 && st.attempt == 0) {
                 st.count = 0;
                 st.head = 0;
                 st.attempt = 1;
-                bytes += direction<HT>(a, w, st, -1, g4, x4, s_new, y_new, MSY, MYY, sh, par);
+                bytes += direction<CT>(a, w, st, -1, g, x, s_new, y_new, MSY, MYY, sh, par);
             } else {
                 st.status = SB_WALKER_STALLED;
             }
@@ -480,7 +623,7 @@ __global__ void __launch_bounds__(CTA, MINB) k_lbfgs_cta(LbfgsArgs<float> a, flo
                 st.status = SB_WALKER_MAXITER;
             } else {
                 st.attempt = 0;
-                bytes += direction<HT>(a, w, st, new_slot, g4, x4, s_new, y_new, MSY, MYY, sh, par);
+                bytes += direction<CT>(a, w, st, new_slot, g, x, s_new, y_new, MSY, MYY, sh, par);
             }
         }
         if (threadIdx.x == 0) a.st[w] = st;
@@ -491,28 +634,20 @@ __global__ void __launch_bounds__(CTA, MINB) k_lbfgs_cta(LbfgsArgs<float> a, flo
 
 }  // namespace
 
-void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *MYY, int num_sms, bool bf16_history,
-                           cudaStream_t s) {
+void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *MYY, int num_sms, cudaStream_t s) {
     ProfScope prof(PROF_LBFGS_STEP, s);
     const int count_bytes = prof_enabled() ? 1 : 0;
-    static const int minb = [] {
-        const char *e = getenv("SB_LBFGS_MINB");
-        return (e && atoi(e) == 3) ? 3 : 2;
-    }();
-    int grid = num_sms * minb;
+    int grid = num_sms * Cfg<kCT>::MINB;
     if (grid > n) grid = n > 0 ? n : 1;
-    note_launch();
-    if (minb == 3) {
-        if (bf16_history)
-            k_lbfgs_cta<__nv_bfloat16, 3><<<grid, CTA, 0, s>>>(a, MSY, MYY, count_bytes);
-        else
-            k_lbfgs_cta<float, 3><<<grid, CTA, 0, s>>>(a, MSY, MYY, count_bytes);
-    } else {
-        if (bf16_history)
-            k_lbfgs_cta<__nv_bfloat16, 2><<<grid, CTA, 0, s>>>(a, MSY, MYY, count_bytes);
-        else
-            k_lbfgs_cta<float, 2><<<grid, CTA, 0, s>>>(a, MSY, MYY, count_bytes);
+    const size_t dyn = (size_t)Cfg<kCT>::RING_F4 * sizeof(float4) + 2 * sizeof(float) * a.m * mm_ld(a.m);
+    static bool attr = false;
+    if (!attr) {
+        const size_t most = (size_t)Cfg<kCT>::RING_F4 * sizeof(float4) + 2 * sizeof(float) * kMaxM * mm_ld(kMaxM);
+        cudaFuncSetAttribute(k_lbfgs_cta<kCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+        attr = true;
     }
+    note_launch();
+    k_lbfgs_cta<kCT><<<grid, kCT, dyn, s>>>(a, MSY, MYY, count_bytes);
 }
 
 double lbfgs_bytes_take() {

@@ -149,6 +149,9 @@ struct LaplaceWs {
     double *P, *XC, *LC, *GC, *Z, *R, *qpart, *GK, *H, *delta, *XN, *LN, *XN2, *LN2, *qpart2, *logZk_c, *t, *pred;
     int32_t *reps, *n_reps, *info, *halvings, *rows2, *n_rows2, *reps2, *n_reps2;
     uint8_t *assigned, *active, *searching, *keep;
+    double *dd_l;
+    int32_t *dd_i;
+    uint32_t *dd_bar;
 };
 
 struct EvidenceWs {
@@ -245,6 +248,9 @@ Layout layout(void *base, const sb_problem *p, const sb_config *c) {
     la.reps = cv.take<int32_t>(cap);
     la.n_reps = cv.take<int32_t>(1);
     la.assigned = cv.take<uint8_t>(n > cap ? n : cap);
+    la.dd_l = cv.take<double>(2 * kDedupMaxGrid);
+    la.dd_i = cv.take<int32_t>(2 * kDedupMaxGrid);
+    la.dd_bar = cv.take<uint32_t>(2);
     la.XC = cv.take<double>((size_t)cap * d);
     la.LC = cv.take<double>(cap);
     la.GC = cv.take<double>((size_t)cap * d);
@@ -389,10 +395,8 @@ void step_round<double>(const RefineWs<double> &, const LbfgsArgs<double> &a, in
 }
 template <>
 void step_round<float>(const RefineWs<float> &r, const LbfgsArgs<float> &a, int n, cudaStream_t s) {
-    // compact form, CTA per walker, FP32 history (bf16 history measured slower: the
-    // step is latency-bound, not bandwidth-bound)
-    static const bool bf16h = getenv("SB_LBFGS_BF16") != nullptr;
-    launch_lbfgs_step_cta(a, n, r.MSY, r.MYY, device_sms(), bf16h, s);
+    // compact form, CTA per walker, FP32 history (bf16 history measured slower)
+    launch_lbfgs_step_cta(a, n, r.MSY, r.MYY, device_sms(), s);
 }
 
 template <typename T>
@@ -407,6 +411,7 @@ sb_status run_refine(const ProbView &pv, const sb_config *c, const RefineWs<T> &
     a.c1 = (T)c->armijo_c1;
     a.backtrack = (T)c->backtrack;
     a.gtol = (T)c->gtol;
+    a.err = pv.status;
     RefineWs<T> rr = r;
     rr.lb = a;
     int64_t *ev = n_evals ? n_evals : r.n_evals;
@@ -498,7 +503,9 @@ sb_status run_laplace(const ProbView &pv, const sb_config *c, const Layout &L, c
     const int d = pv.d, K = pv.K, cap = c->cand_cap;
     const auto &la = L.la;
     launch_precision(d, K, pv.L, la.P, s);
-    launch_dedup(n, d, x, ell, status, nullptr, c->dedup_coarse, pv.wmax, cap, la.reps, la.n_reps, la.assigned, s);
+    const DedupScratch dds{la.dd_l, la.dd_i, la.dd_bar, pv.status};
+    launch_dedup(n, d, x, ell, status, nullptr, c->dedup_coarse, pv.wmax, cap, la.reps, la.n_reps, la.assigned, dds,
+                 s);
     launch_gather_rows(d, cap, x, la.reps, la.n_reps, la.XC, ell, la.LC, s);
     SB_CUDA_TRY(cudaMemsetAsync(la.active, 1, cap, s));
     // l, grad l, H and its Cholesky factor at every candidate
@@ -524,7 +531,7 @@ sb_status run_laplace(const ProbView &pv, const sb_config *c, const Layout &L, c
     launch_cand_stats(d, cap, la.XC, la.LC, la.GC, la.H, la.info, pv.lo, pv.hi, c->eps_grad, la.n_reps, la.keep,
                       la.logZk_c, s);
     launch_dedup(cap, d, la.XC, la.LC, nullptr, la.keep, c->dedup_tol, pv.wmax, cap, la.reps2, la.n_reps2,
-                 la.assigned, s);
+                 la.assigned, dds, s);
     launch_laplace_final(d, la.XC, la.LC, la.logZk_c, la.n_reps, la.reps2, la.n_reps2, pv.logV, cap_out, modes, logZk,
                          ell_modes, n_modes, logZ, pv.status, s);
     SB_CUDA_TRY(cudaGetLastError());

@@ -6,9 +6,17 @@ namespace sb {
 
 constexpr int kHalvings = 30;  // Newton step halvings (t = 1, 1/2, ..., 2^-29)
 
+// Scratch of the grid-wide greedy dedup: per-CTA partials (two rounds) and the grid barrier.
+constexpr int kDedupMaxGrid = 1024;
+struct DedupScratch {
+    double *part_l;   // [2 * kDedupMaxGrid]
+    int32_t *part_i;  // [2 * kDedupMaxGrid]
+    uint32_t *bar;    // [2] arrival count, generation
+    int32_t *err;     // device status word (SB_DEV_TIMEOUT)
+};
 void launch_dedup(int n, int d, const double *X, const double *ell, const int8_t *status, const uint8_t *keep,
                   double tau_scale, const double *wmax, int cap, int32_t *reps, int32_t *n_reps, uint8_t *assigned,
-                  cudaStream_t s);
+                  const DedupScratch &sc, cudaStream_t s);
 void launch_gather_rows(int d, int cap, const double *X, const int32_t *idx, const int32_t *n_idx, double *out,
                         const double *ell, double *ell_out, cudaStream_t s);
 void launch_precision(int d, int K, const double *L, double *P, cudaStream_t s);

@@ -29,6 +29,7 @@ struct LbfgsArgs {
     WalkerState<T> *st;           // [N]
     int32_t *act;                 // [N] active walker ids
     int32_t *n_act;               // device scalar
+    int32_t *err;                 // device status word (SB_DEV_TIMEOUT from bounded waits), may be null
 };
 
 template <typename T>
@@ -38,8 +39,8 @@ void launch_lbfgs_step(const LbfgsArgs<T> &a, int n, cudaStream_t s);
 template <typename T>
 void launch_lbfgs_compact(const LbfgsArgs<T> &a, int64_t *n_evals, cudaStream_t s);
 // FP32 step, one CTA per walker, compact-representation direction (lbfgs_cta.cu).
-void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *MYY, int num_sms, bool bf16_history,
-                           cudaStream_t s);
+// With d % 4 == 0 and a.err set, the stored pairs are streamed by bulk copies.
+void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *MYY, int num_sms, cudaStream_t s);
 // Algorithmic bytes moved by the FP32 step launches while profiling was on
 // (synchronises the device, then clears the counter); -1 on a CUDA error.
 double lbfgs_bytes_take();

@@ -38,6 +38,7 @@
 #include <mutex>
 #include <tuple>
 
+#include "sb_ptx.cuh"
 #include "sb_tc.cuh"
 
 namespace sb {
@@ -47,7 +48,6 @@ namespace {
 constexpr int BM = 128;
 constexpr int ROWB = 128;  // bytes of one K chunk per row (one swizzle atom row)
 constexpr int THREADS = 192;
-constexpr long long kSpinLimit = 1ll << 24;
 
 // MODE_ZW: GEMM1 storing z (walkers/points); MODE_ZR: GEMM1 values only (ray samples); MODE_G: GEMM2
 enum { MODE_ZW = 0, MODE_ZR = 1, MODE_G = 2 };
@@ -75,39 +75,6 @@ struct TcArgs {
 };
 
 // ------------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-// Bounded wait: false on timeout or when another role aborted.
-__device__ __forceinline__ bool bwait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    for (long long it = 0;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63) == 63) {
-            if (*abort_flag) return false;
-            if (it > kSpinLimit) {
-                *abort_flag = 1;
-                return false;
-            }
-        }
-    }
-}
 // Warp-uniform variants for roles where all 32 lanes take part.
 __device__ __forceinline__ bool warp_bwait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
     return __all_sync(0xffffffffu, bwait(bar, parity, abort_flag) ? 1 : 0) != 0;
@@ -269,7 +236,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         }
         mbar_init(drain, 1);
         *s_abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_fence_init();
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
@@ -465,10 +432,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
 }
 
 // ------------------------------------------------------------------ small kernels
-// LSE over components from the FP32 |z|^2 partials, in FP64.
+// LSE over components from the FP32 |z|^2 partials: e_k and the maximum in
+// FP64, exp/log of the shifted values (in [0, 1] and [1, K]) in FP32, whose
+// absolute error stays below the FP32 resolution of the outputs.
 // mode 0: walkers (FT[act[n]] = -l, R); mode 1: ray samples (ell[flat0 + n] = l);
 // mode 2: points (ell[n] = l, R).
-__global__ void __launch_bounds__(256) k_tc_lse(int mode, int K, int n_ntile, const int32_t *n_rows_dev,
+__global__ void __launch_bounds__(128) k_tc_lse(int mode, int K, int n_ntile, const int32_t *n_rows_dev,
                                                 int n_rows_max, const int32_t *act, const float *qpart,
                                                 const double *a_k, float *R, float *FT, double *ell) {
     const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
@@ -483,14 +452,15 @@ __global__ void __launch_bounds__(256) k_tc_lse(int mode, int K, int n_ntile, co
         e[k] = a_k[k] - 0.5 * q;
         emax = fmax(emax, e[k]);
     }
-    double s = 0.0;
-    for (int k = 0; k < K; ++k) s += exp(e[k] - emax);
-    const double l = emax + log(s);
+    float s = 0.f;
+    for (int k = 0; k < K; ++k) s += __expf((float)(e[k] - emax));
+    const double l = emax + (double)__logf(s);
     if (mode == 1) {
         ell[n] = l;
         return;
     }
-    for (int k = 0; k < K; ++k) R[(size_t)n * K + k] = (float)(exp(e[k] - emax) / s);
+    const float inv = 1.f / s;
+    for (int k = 0; k < K; ++k) R[(size_t)n * K + k] = __expf((float)(e[k] - emax)) * inv;
     if (mode == 0)
         FT[act ? act[n] : n] = (float)(-l);
     else
@@ -500,9 +470,10 @@ __global__ void __launch_bounds__(256) k_tc_lse(int mode, int K, int n_ntile, co
 // A operand of GEMM1: A1[k][n][i] = round(x_n[i] - mu_k[i]) formed in FP32; x_n is a
 // walker row (through the active list) or the ray sample c + t_j t_exit u_r.
 // Rows from n_rows up to the next multiple of 128 and columns >= d are zeroed.
-// Grid: x over (row, 16-byte column group), y = component.
+// One thread per (row, 16-byte column group): x is formed once and the thread
+// writes that column group for every component.
 template <int PREC>
-__global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int rows_cap, int ldp,
+__global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int K, int rows_cap, int ldp,
                                                    const int32_t *n_rows_dev, int n_rows_max, const int32_t *act,
                                                    const float *X, int ld, const float *u32, const double *texit,
                                                    int n_steps, long long flat0, const float *mu32, const float *c32,
@@ -515,67 +486,84 @@ __global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int rows
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = e / ncg, cg = e - n * ncg;
     if (n >= rows_pad) return;
-    const int k = blockIdx.y;
     const int i0 = cg * VE;
-    float v[VE];
+    const bool live = n < n_rows;
+    const bool vec = ((d & 3) == 0) && i0 + VE <= d;
+    float x[VE];
 #pragma unroll
-    for (int q = 0; q < VE; ++q) v[q] = 0.f;
-    if (n < n_rows) {
-        const float *mk = mu32 + (size_t)k * d;
-        const bool vec = ((d & 3) == 0) && i0 + VE <= d;
-        float m[VE];
-        if (vec) {
-#pragma unroll
-            for (int q = 0; q < VE; q += 4) {
-                const float4 t = *reinterpret_cast<const float4 *>(mk + i0 + q);
-                m[q] = t.x;
-                m[q + 1] = t.y;
-                m[q + 2] = t.z;
-                m[q + 3] = t.w;
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < VE; ++q) m[q] = i0 + q < d ? mk[i0 + q] : 0.f;
-        }
+    for (int q = 0; q < VE; ++q) x[q] = 0.f;
+    if (live) {
         if (!ray_mode) {
             const float *xr = X + (size_t)(act ? act[n] : n) * ld;
             if (vec && (ld & 3) == 0) {
 #pragma unroll
                 for (int q = 0; q < VE; q += 4) {
-                    const float4 x4 = *reinterpret_cast<const float4 *>(xr + i0 + q);
-                    v[q] = x4.x;
-                    v[q + 1] = x4.y;
-                    v[q + 2] = x4.z;
-                    v[q + 3] = x4.w;
+                    const float4 t = *reinterpret_cast<const float4 *>(xr + i0 + q);
+                    x[q] = t.x;
+                    x[q + 1] = t.y;
+                    x[q + 2] = t.z;
+                    x[q + 3] = t.w;
                 }
             } else {
 #pragma unroll
                 for (int q = 0; q < VE; ++q)
-                    if (i0 + q < d) v[q] = xr[i0 + q];
+                    if (i0 + q < d) x[q] = xr[i0 + q];
             }
         } else {
+            // FP32 position on the ray: the operand is rounded to bf16 / tf32 below anyway
             const long long flat = flat0 + n;
             const int ray = (int)(flat / n_steps), j = (int)(flat - (long long)ray * n_steps);
-            const float sc = (float)(((double)(j + 1) / (double)n_steps) * texit[ray]);
+            const float sc = ((float)(j + 1) / (float)n_steps) * (float)texit[ray];
             const float *ur = u32 + (size_t)ray * d;
+            if (vec) {
 #pragma unroll
-            for (int q = 0; q < VE; ++q)
-                if (i0 + q < d) v[q] = fmaf(sc, ur[i0 + q], c32[i0 + q]);
+                for (int q = 0; q < VE; q += 4) {
+                    const float4 u4 = *reinterpret_cast<const float4 *>(ur + i0 + q);
+                    const float4 c4 = *reinterpret_cast<const float4 *>(c32 + i0 + q);
+                    x[q] = fmaf(sc, u4.x, c4.x);
+                    x[q + 1] = fmaf(sc, u4.y, c4.y);
+                    x[q + 2] = fmaf(sc, u4.z, c4.z);
+                    x[q + 3] = fmaf(sc, u4.w, c4.w);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < VE; ++q)
+                    if (i0 + q < d) x[q] = fmaf(sc, ur[i0 + q], c32[i0 + q]);
+            }
         }
-#pragma unroll
-        for (int q = 0; q < VE; ++q) v[q] = (i0 + q < d) ? v[q] - m[q] : 0.f;
     }
-    const size_t o = ((size_t)k * rows_cap + n) * ldp + i0;
-    if (PREC == SB_PREC_BF16) {
-        uint4 p;
-        p.x = pack_bf16x2(v[0], v[1]);
-        p.y = pack_bf16x2(v[2], v[3]);
-        p.z = pack_bf16x2(v[4], v[5]);
-        p.w = pack_bf16x2(v[6], v[7]);
-        *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(A1) + o) = p;
-    } else {
-        *reinterpret_cast<float4 *>(reinterpret_cast<float *>(A1) + o) =
-            make_float4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
+    for (int k = 0; k < K; ++k) {
+        float v[VE];
+#pragma unroll
+        for (int q = 0; q < VE; ++q) v[q] = 0.f;
+        if (live) {
+            const float *mk = mu32 + (size_t)k * d;
+            if (vec) {
+#pragma unroll
+                for (int q = 0; q < VE; q += 4) {
+                    const float4 m4 = *reinterpret_cast<const float4 *>(mk + i0 + q);
+                    v[q] = x[q] - m4.x;
+                    v[q + 1] = x[q + 1] - m4.y;
+                    v[q + 2] = x[q + 2] - m4.z;
+                    v[q + 3] = x[q + 3] - m4.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < VE; ++q) v[q] = (i0 + q < d) ? x[q] - mk[i0 + q] : 0.f;
+            }
+        }
+        const size_t o = ((size_t)k * rows_cap + n) * ldp + i0;
+        if (PREC == SB_PREC_BF16) {
+            uint4 p;
+            p.x = pack_bf16x2(v[0], v[1]);
+            p.y = pack_bf16x2(v[2], v[3]);
+            p.z = pack_bf16x2(v[4], v[5]);
+            p.w = pack_bf16x2(v[6], v[7]);
+            *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(A1) + o) = p;
+        } else {
+            *reinterpret_cast<float4 *>(reinterpret_cast<float *>(A1) + o) =
+                make_float4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
+        }
     }
 }
 
@@ -760,15 +748,15 @@ void launch_center(const TcWs &t, int ray_mode, int d, int K, const int32_t *n_r
     const int ncg = ldp / (t.prec == SB_PREC_BF16 ? 8 : 4);
     int rows = (n_rows_max + BM - 1) / BM * BM;
     if (rows > (int)t.rows) rows = (int)t.rows;
-    const dim3 grid((unsigned)(((long long)rows * ncg + 255) / 256), (unsigned)K);
+    const dim3 grid((unsigned)(((long long)rows * ncg + 255) / 256));
     note_launch();
     if (t.prec == SB_PREC_BF16)
-        k_tc_center<SB_PREC_BF16><<<grid, 256, 0, s>>>(ray_mode, d, (int)t.rows, ldp, n_rows_dev, n_rows_max, act, X,
-                                                      d, u32, texit, n_steps, flat0, (const float *)t.p[2],
+        k_tc_center<SB_PREC_BF16><<<grid, 256, 0, s>>>(ray_mode, d, K, (int)t.rows, ldp, n_rows_dev, n_rows_max, act,
+                                                      X, d, u32, texit, n_steps, flat0, (const float *)t.p[2],
                                                       (const float *)t.p[3], t.p[9]);
     else
-        k_tc_center<SB_PREC_TF32><<<grid, 256, 0, s>>>(ray_mode, d, (int)t.rows, ldp, n_rows_dev, n_rows_max, act, X,
-                                                      d, u32, texit, n_steps, flat0, (const float *)t.p[2],
+        k_tc_center<SB_PREC_TF32><<<grid, 256, 0, s>>>(ray_mode, d, K, (int)t.rows, ldp, n_rows_dev, n_rows_max, act,
+                                                      X, d, u32, texit, n_steps, flat0, (const float *)t.p[2],
                                                       (const float *)t.p[3], t.p[9]);
 }
 
@@ -969,7 +957,7 @@ sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, c
         launch_center(t, 1, pv.d, pv.K, nullptr, rows, nullptr, nullptr, u32, texit, c->n_steps, f0, s);
         launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
         note_launch();
-        k_tc_lse<<<(rows + 255) / 256, 256, 0, s>>>(1, pv.K, a.n_ntile, nullptr, rows, nullptr, a.qpart, pv.a,
+        k_tc_lse<<<(rows + 127) / 128, 128, 0, s>>>(1, pv.K, a.n_ntile, nullptr, rows, nullptr, a.qpart, pv.a,
                                                     nullptr, nullptr, ell_all + f0);
     }
     return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
@@ -985,7 +973,7 @@ void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, cons
     launch_center(t, 0, pv.d, pv.K, n_act, n, act, XT, nullptr, nullptr, 1, 0, s);
     launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
     note_launch();
-    k_tc_lse<<<(n + 255) / 256, 256, 0, s>>>(0, pv.K, a.n_ntile, n_act, n, act, a.qpart, pv.a, (float *)t.p[6], FT,
+    k_tc_lse<<<(n + 127) / 128, 128, 0, s>>>(0, pv.K, a.n_ntile, n_act, n, act, a.qpart, pv.a, (float *)t.p[6], FT,
                                              nullptr);
     launch_scale(t, pv.K, n_act, n, s);
     a.G = GT;
@@ -1006,7 +994,7 @@ sb_status tc_loglik_points(const ProbView &pv, const sb_config *c, const TcWs &t
     launch_center(t, 0, pv.d, pv.K, nullptr, n, nullptr, X, nullptr, nullptr, 1, 0, s);
     launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
     note_launch();
-    k_tc_lse<<<(n + 255) / 256, 256, 0, s>>>(2, pv.K, a.n_ntile, nullptr, n, nullptr, a.qpart, pv.a,
+    k_tc_lse<<<(n + 127) / 128, 128, 0, s>>>(2, pv.K, a.n_ntile, nullptr, n, nullptr, a.qpart, pv.a,
                                              (float *)t.p[6], nullptr, ell);
     if (grad) {
         launch_scale(t, pv.K, nullptr, n, s);
