@@ -263,25 +263,29 @@ __global__ void __launch_bounds__(256) k_precision(int d, const double *L, doubl
 }
 
 // ------------------------------------------------------------------ per-component gradients
-// GK[c][k][i] = -sum_{j<=i} L_k[i][j] z_ck[j]  (zero when r_ck == 0)
+// GK[c][k][i] = -sum_{j<=i} L_k[i][j] z_ck[j]  (zero when r_ck == 0). Grid (candidate,
+// component, row slice): the rows of one product are spread over kGradSlices CTAs.
+constexpr int kGradSlices = 16;
 __global__ void __launch_bounds__(256) k_comp_grads(int d, int K, const double *L, const double *Z, const double *R,
                                                     const int32_t *n_c, double *GK) {
     const int c = blockIdx.x, k = blockIdx.y;
     if (c >= *n_c) return;
+    const int per = (d + kGradSlices - 1) / kGradSlices;
+    const int i_lo = blockIdx.z * per, i_hi = min(d, i_lo + per);
     const double r = R[(size_t)c * K + k];
     double *g = GK + ((size_t)c * K + k) * d;
     if (r == 0.0) {
-        for (int i = threadIdx.x; i < d; i += blockDim.x) g[i] = 0.0;
+        for (int i = i_lo + threadIdx.x; i < i_hi; i += blockDim.x) g[i] = 0.0;
         return;
     }
     extern __shared__ double zs[];
     const double *z = Z + ((size_t)c * K + k) * d;
-    for (int i = threadIdx.x; i < d; i += blockDim.x) zs[i] = z[i];
+    for (int i = threadIdx.x; i < i_hi; i += blockDim.x) zs[i] = z[i];
     __syncthreads();
     const double *Lk = L + (size_t)k * d * d;
     // one warp per output row: coalesced reads of L_k rows
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = wid; i < d; i += nw) {
+    for (int i = i_lo + wid; i < i_hi; i += nw) {
         double s = 0.0;
         for (int j = lane; j <= i; j += 32) s += Lk[(size_t)i * d + j] * zs[j];
         s = warp_sum(s);
@@ -425,12 +429,18 @@ __global__ void __launch_bounds__(256) k_chol_solve(int d, const double *H, cons
                                                     double *pred) {
     const int c = blockIdx.x;
     if (c >= *n_c || info[c] || !active[c]) return;
-    extern __shared__ double y[];  // [d]
+    extern __shared__ double y[];  // [d] right-hand side / solution, then [d] 1 / C_ii
+    double *dinv = y + d;
     __shared__ double part[8][33];
     __shared__ double Dg[32][33];
     const double *C = H + (size_t)c * d * d;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < d; i += blockDim.x) y[i] = g[(size_t)c * d + i];
+    // the reciprocals of the diagonal, all at once: the substitutions below then
+    // have multiplications, not divisions, on their sequential path
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        y[i] = g[(size_t)c * d + i];
+        dinv[i] = 1.0 / C[(size_t)i * d + i];
+    }
     __syncthreads();
     const int nb = (d + 31) / 32;
     // forward substitution
@@ -452,7 +462,7 @@ __global__ void __launch_bounds__(256) k_chol_solve(int d, const double *H, cons
         if (wid == 0) {
             double v = lane < rows ? y[r0 + lane] - part[0][lane] : 0.0;
             for (int i = 0; i < 32; ++i) {
-                const double yi = __shfl_sync(0xffffffffu, v, i) / Dg[i][i];
+                const double yi = __shfl_sync(0xffffffffu, v, i) * (i < rows ? dinv[r0 + i] : 1.0);
                 if (lane == i) v = yi;
                 if (lane > i) v -= Dg[lane][i] * yi;
             }
@@ -482,7 +492,7 @@ __global__ void __launch_bounds__(256) k_chol_solve(int d, const double *H, cons
             double v = lane < rows ? y[r0 + lane] - sacc : 0.0;
             // C_II^T x = v: upper-triangular (C^T)_{ij} = C_{ji}; back substitution
             for (int i = 31; i >= 0; --i) {
-                const double xi = __shfl_sync(0xffffffffu, v, i) / Dg[i][i];
+                const double xi = __shfl_sync(0xffffffffu, v, i) * (i < rows ? dinv[r0 + i] : 1.0);
                 if (lane == i) v = xi;
                 if (lane < i) v -= Dg[i][lane] * xi;
             }
@@ -729,7 +739,7 @@ void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P
                          const double *gbar, const int32_t *n_c, double *GK, double *H, int32_t *info,
                          cudaStream_t s) {
     note_launch();
-    k_comp_grads<<<dim3(cap, K), 256, sizeof(double) * d, s>>>(d, K, L, Z, R, n_c, GK);
+    k_comp_grads<<<dim3(cap, K, kGradSlices), 256, sizeof(double) * d, s>>>(d, K, L, Z, R, n_c, GK);
     const int64_t dd = (int64_t)d * d;
     note_launch();
     k_hessian<<<dim3((unsigned)((dd + 255) / 256), cap), 256, 0, s>>>(d, K, P, GK, R, gbar, n_c, H);
@@ -752,7 +762,7 @@ void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P
 void launch_chol_solve(int d, int cap, const double *H, const double *g, const int32_t *n_c, const int32_t *info,
                        const uint8_t *active, double *delta, double *pred, cudaStream_t s) {
     note_launch();
-    k_chol_solve<<<cap, 256, sizeof(double) * d, s>>>(d, H, g, n_c, info, active, delta, pred);
+    k_chol_solve<<<cap, 256, 2 * sizeof(double) * d, s>>>(d, H, g, n_c, info, active, delta, pred);
 }
 
 void launch_newton_ls(int d, int cap, int mode, const int32_t *n_c, const int32_t *info, uint8_t *active,

@@ -237,95 +237,148 @@ __global__ void __launch_bounds__(256) k_ggemm_f64(LikF64Args a) {
 // layouts and a fixed summation order.
 constexpr int FEW_CB = 8;  // points per CTA
 
-// z_k[j] for 64 columns j of one component and FEW_CB points; thread per column.
-__global__ void __launch_bounds__(64) k_few_z(LikF64Args a) {
-    const int n_rows = rows_of(a);
-    const int jt = blockIdx.x, j0 = jt * 64, k = blockIdx.y, c0 = blockIdx.z * FEW_CB;
-    if (c0 >= n_rows) return;
-    const int d = a.d, K = a.K, nJT = (d + 63) / 64;
-    const int nc = min(FEW_CB, n_rows - c0);
-    __shared__ double dl[FEW_CB][64];  // delta = x - mu_k for 64 rows i of the current chunk
-    __shared__ int s_src[FEW_CB], s_out[FEW_CB];
-    if (threadIdx.x < FEW_CB) {
+// z_k[j] for the 64 columns j of one tile, one component and CB points: thread
+// (column, row group of 4) accumulates rows i = i0 + rg, i0 + rg + 4, ... of
+// L_k (coalesced row segments), then the four row groups are summed in a
+// fixed order.
+struct FewZShared {
+    double dl[FEW_CB][64];  // delta = x - mu_k for 64 rows i of the current chunk
+    double part[4][FEW_CB][64];
+    double red[FEW_CB][2];
+    int s_src[FEW_CB], s_out[FEW_CB];
+};
+
+template <int CB>
+__device__ __forceinline__ void few_z_body(const LikF64Args &a, int jt, int k, int c0, FewZShared &sm) {
+    const int d = a.d, K = a.K, nJT = (d + 63) / 64, j0 = jt * 64;
+    const int tx = threadIdx.x & 63, rg = threadIdx.x >> 6;
+    auto &dl = sm.dl;
+    auto &part = sm.part;
+    auto &red = sm.red;
+    auto &s_src = sm.s_src;
+    auto &s_out = sm.s_out;
+    if (threadIdx.x < CB) {
         const int n = c0 + threadIdx.x;
-        const int w = (threadIdx.x < nc) ? (a.rows ? a.rows[n] : n) : 0;
+        const int w = a.rows ? a.rows[n] : n;
         s_src[threadIdx.x] = w;
-        s_out[threadIdx.x] = (threadIdx.x < nc) ? (a.out_by_walker ? w : n) : -1;
+        s_out[threadIdx.x] = a.out_by_walker ? w : n;
     }
     __syncthreads();
     const double *Lk = a.L + (size_t)k * d * d;
     const double *mk = a.mu + (size_t)k * d;
-    const int j = j0 + threadIdx.x;
-    double acc[FEW_CB];
+    const int j = j0 + tx;
+    double acc[CB];
 #pragma unroll
-    for (int c = 0; c < FEW_CB; ++c) acc[c] = 0.0;
+    for (int c = 0; c < CB; ++c) acc[c] = 0.0;
     for (int i0 = j0; i0 < d; i0 += 64) {
-        const int i = i0 + threadIdx.x;
-#pragma unroll
-        for (int c = 0; c < FEW_CB; ++c)
-            dl[c][threadIdx.x] = (c < nc && i < d) ? sub_rn(a.X[(size_t)s_src[c] * d + i], mk[i]) : 0.0;
+        for (int e = threadIdx.x; e < CB * 64; e += 256) {
+            const int c = e >> 6, ii = e & 63, i = i0 + ii;
+            dl[c][ii] = i < d ? sub_rn(a.X[(size_t)s_src[c] * d + i], mk[i]) : 0.0;
+        }
         __syncthreads();
         const int imax = min(64, d - i0);
-        for (int ii = 0; ii < imax; ++ii) {
+        for (int ii = rg; ii < imax; ii += 4) {
             const int ig = i0 + ii;
             const double l = (j < d && j <= ig) ? Lk[(size_t)ig * d + j] : 0.0;
 #pragma unroll
-            for (int c = 0; c < FEW_CB; ++c) acc[c] = fma(dl[c][ii], l, acc[c]);
+            for (int c = 0; c < CB; ++c) acc[c] = fma(dl[c][ii], l, acc[c]);
         }
         __syncthreads();
     }
-    // |z|^2 over the 64 columns: warp shuffles then two warps through shared memory
-    __shared__ double red[FEW_CB][2];
 #pragma unroll
-    for (int c = 0; c < FEW_CB; ++c) {
-        double q = (j < d) ? acc[c] * acc[c] : 0.0;
-        q = warp_sum(q);
-        if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = q;
-    }
+    for (int c = 0; c < CB; ++c) part[rg][c][tx] = acc[c];
     __syncthreads();
-    if (threadIdx.x < nc) {
-        const int c = threadIdx.x;
-        a.qpart[((size_t)s_out[c] * K + k) * nJT + jt] = red[c][0] + red[c][1];
+    if (rg == 0) {
+        // |z|^2 over the 64 columns: warp shuffles, then the two warps through shared memory
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            const double z = ((part[0][c][tx] + part[1][c][tx]) + part[2][c][tx]) + part[3][c][tx];
+            acc[c] = z;
+            double q = (j < d) ? z * z : 0.0;
+            q = warp_sum(q);
+            if ((tx & 31) == 0) red[c][tx >> 5] = q;
+        }
+        asm volatile("bar.sync 1, 64;" ::: "memory");  // the two warps of row group 0
+        if (tx < CB) a.qpart[((size_t)s_out[tx] * K + k) * nJT + jt] = red[tx][0] + red[tx][1];
+        if (a.Z && j < d)
+#pragma unroll
+            for (int c = 0; c < CB; ++c) a.Z[((size_t)s_out[c] * K + k) * d + j] = acc[c];
     }
-    if (a.Z && j < d)
-        for (int c = 0; c < nc; ++c) a.Z[((size_t)s_out[c] * K + k) * d + j] = acc[c];
 }
 
-// grad: out[n][i] = sign * sum_k sum_{j<=i} r_nk z_nk[j] L_k[i][j]; warp per row i, FEW_CB points.
-__global__ void __launch_bounds__(256) k_few_g(LikF64Args a) {
+__global__ void __launch_bounds__(256) k_few_z(LikF64Args a) {
+    __shared__ FewZShared sm;
     const int n_rows = rows_of(a);
-    const int c0 = blockIdx.y * FEW_CB;
+    const int c0 = blockIdx.z * FEW_CB;
     if (c0 >= n_rows) return;
+    switch (min(FEW_CB, n_rows - c0)) {  // the live point count of this CTA (device-side)
+        case 1: few_z_body<1>(a, blockIdx.x, blockIdx.y, c0, sm); break;
+        case 2: few_z_body<2>(a, blockIdx.x, blockIdx.y, c0, sm); break;
+        case 3: few_z_body<3>(a, blockIdx.x, blockIdx.y, c0, sm); break;
+        case 4: few_z_body<4>(a, blockIdx.x, blockIdx.y, c0, sm); break;
+        case 5: few_z_body<5>(a, blockIdx.x, blockIdx.y, c0, sm); break;
+        case 6: few_z_body<6>(a, blockIdx.x, blockIdx.y, c0, sm); break;
+        case 7: few_z_body<7>(a, blockIdx.x, blockIdx.y, c0, sm); break;
+        default: few_z_body<8>(a, blockIdx.x, blockIdx.y, c0, sm); break;
+    }
+}
+
+// grad: out[n][i] = sign * sum_k sum_{j<=i} r_nk z_nk[j] L_k[i][j]; warp per row i,
+// CB points; components with r == 0 at every point of the CTA are skipped.
+template <int CB>
+__device__ __forceinline__ void few_g_body(const LikF64Args &a, int c0, int *s_out) {
     const int d = a.d, K = a.K;
-    const int nc = min(FEW_CB, n_rows - c0);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int i = blockIdx.x * 8 + wid;
-    __shared__ int s_out[FEW_CB];
-    if (threadIdx.x < FEW_CB) {
+    if (threadIdx.x < CB) {
         const int n = c0 + threadIdx.x;
-        s_out[threadIdx.x] = (threadIdx.x < nc) ? (a.out_by_walker ? (a.rows ? a.rows[n] : n) : n) : -1;
+        s_out[threadIdx.x] = a.out_by_walker ? (a.rows ? a.rows[n] : n) : n;
     }
     __syncthreads();
     if (i >= d) return;
-    double acc[FEW_CB];
+    double acc[CB];
 #pragma unroll
-    for (int c = 0; c < FEW_CB; ++c) acc[c] = 0.0;
+    for (int c = 0; c < CB; ++c) acc[c] = 0.0;
     for (int k = 0; k < K; ++k) {
+        double rk[CB];
+        const double *zk[CB];
+        bool any = false;
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            const int o = s_out[c];
+            rk[c] = a.R[(size_t)o * K + k];
+            zk[c] = a.Z + ((size_t)o * K + k) * d;
+            any = any || rk[c] != 0.0;
+        }
+        if (!any) continue;
         const double *Lrow = a.L + (size_t)k * d * d + (size_t)i * d;
         for (int j = lane; j <= i; j += 32) {
             const double l = Lrow[j];
 #pragma unroll
-            for (int c = 0; c < FEW_CB; ++c)
-                if (c < nc) {
-                    const int o = s_out[c];
-                    acc[c] = fma(a.R[(size_t)o * K + k] * a.Z[((size_t)o * K + k) * d + j], l, acc[c]);
-                }
+            for (int c = 0; c < CB; ++c) acc[c] = fma(rk[c] * zk[c][j], l, acc[c]);
         }
     }
 #pragma unroll
-    for (int c = 0; c < FEW_CB; ++c) {
+    for (int c = 0; c < CB; ++c) {
         const double v = warp_sum(acc[c]);
-        if (lane == 0 && c < nc) a.G[(size_t)s_out[c] * d + i] = a.grad_sign * v;
+        if (lane == 0) a.G[(size_t)s_out[c] * d + i] = a.grad_sign * v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_few_g(LikF64Args a) {
+    __shared__ int s_out[FEW_CB];
+    const int n_rows = rows_of(a);
+    const int c0 = blockIdx.y * FEW_CB;
+    if (c0 >= n_rows) return;
+    switch (min(FEW_CB, n_rows - c0)) {
+        case 1: few_g_body<1>(a, c0, s_out); break;
+        case 2: few_g_body<2>(a, c0, s_out); break;
+        case 3: few_g_body<3>(a, c0, s_out); break;
+        case 4: few_g_body<4>(a, c0, s_out); break;
+        case 5: few_g_body<5>(a, c0, s_out); break;
+        case 6: few_g_body<6>(a, c0, s_out); break;
+        case 7: few_g_body<7>(a, c0, s_out); break;
+        default: few_g_body<8>(a, c0, s_out); break;
     }
 }
 
@@ -383,7 +436,7 @@ void launch_lik_f64_few(const LikF64Args &a, bool want_grad, cudaStream_t s) {
     {
         ProfScope prof(PROF_F64_Z, s);
         note_launch();
-        k_few_z<<<dim3(nJT, a.K, cb), 64, 0, s>>>(a);
+        k_few_z<<<dim3(nJT, a.K, cb), 256, 0, s>>>(a);
     }
     note_launch();
     k_lse_f64<<<(a.n_rows + 255) / 256, 256, 0, s>>>(a);
