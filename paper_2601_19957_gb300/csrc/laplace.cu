@@ -313,78 +313,112 @@ __global__ void __launch_bounds__(256) k_hessian(int d, int K, const double *P, 
 }
 
 // ------------------------------------------------------------------ blocked Cholesky
-__global__ void __launch_bounds__(NB *NB) k_potrf_diag(int d, int kb, double *H, const int32_t *n_c, int32_t *info) {
+// Diagonal block factor, 256 threads. Per column j one thread takes
+// r = 1/sqrt(a_jj) (the only serial FP64 work of the step), the column below is
+// multiplied by r, and the trailing lower triangle (m (m + 1) / 2 entries,
+// m = 31 - j) is updated with each thread taking at most two entries.
+constexpr int DIAG_THREADS = 256;
+__global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(int d, int kb, double *H, const int32_t *n_c,
+                                                             int32_t *info) {
     const int c = blockIdx.x;
     if (c >= *n_c || info[c]) return;
     double *A = H + (size_t)c * d * d;
     __shared__ double a[NB][NB + 1];
+    __shared__ double s_r;
     __shared__ int bad;
-    const int tx = threadIdx.x % NB, ty = threadIdx.x / NB;
     const int o = kb * NB;
-    {
-        const int i = o + ty, j = o + tx;
-        double v;
-        if (i < d && j < d)
-            v = A[(size_t)i * d + j];
-        else
-            v = (ty == tx) ? 1.0 : 0.0;  // identity padding of the ragged last block
-        a[ty][tx] = v;
+    for (int e = threadIdx.x; e < NB * NB; e += DIAG_THREADS) {
+        const int i = e / NB, j = e % NB;
+        a[i][j] = (o + i < d && o + j < d) ? A[(size_t)(o + i) * d + o + j] : (i == j ? 1.0 : 0.0);  // identity padding
     }
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
     for (int j = 0; j < NB; ++j) {
         if (threadIdx.x == 0) {
             const double p = a[j][j];
-            if (!(p > 0.0))
+            if (!(p > 0.0)) {
                 bad = 1;
-            else
-                a[j][j] = sqrt(p);
+            } else {
+                const double r = rsqrt(p);
+                s_r = r;
+                a[j][j] = p * r;
+            }
         }
         __syncthreads();
         if (bad) break;
-        if (ty == 0 && tx > j) a[tx][j] = a[tx][j] / a[j][j];
+        if (threadIdx.x > j && threadIdx.x < NB) a[threadIdx.x][j] *= s_r;
         __syncthreads();
-        if (tx > j && ty > j && tx >= ty) a[tx][ty] -= a[tx][j] * a[ty][j];
+        const int m = NB - 1 - j;
+        for (int e = threadIdx.x; e < m * (m + 1) / 2; e += DIAG_THREADS) {
+            // e -> (ii >= kk) in the packed lower triangle of the trailing block
+            int ii = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+            while (ii * (ii + 1) / 2 > e) --ii;
+            while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+            const int kk = e - ii * (ii + 1) / 2;
+            const int i = j + 1 + ii, k = j + 1 + kk;
+            a[i][k] -= a[i][j] * a[k][j];
+        }
         __syncthreads();
     }
     if (bad) {
         if (threadIdx.x == 0) info[c] = 1;
         return;
     }
-    const int i = o + ty, j = o + tx;
-    if (i < d && j < d && j <= i) A[(size_t)i * d + j] = a[ty][tx];
+    for (int e = threadIdx.x; e < NB * NB; e += DIAG_THREADS) {
+        const int i = e / NB, j = e % NB;
+        if (o + i < d && o + j < d && j <= i) A[(size_t)(o + i) * d + o + j] = a[i][j];
+    }
 }
 
-// Panel: A[ib][kb] <- A[ib][kb] L_kk^{-T}, one thread per panel row.
-__global__ void __launch_bounds__(NB) k_trsm_panel(int d, int kb, double *H, const int32_t *n_c,
-                                                   const int32_t *info) {
+// Panel: A[ib][kb] <- A[ib][kb] L_kk^{-T}. 128 threads: thread (r, part) holds row r's
+// columns part, part + 4, ... in registers; per column j the owner scales by
+// 1 / L_jj (reciprocals taken once, in parallel) and publishes it, then every
+// thread updates its later columns. One barrier per column; the FP64 updates
+// are spread over four warps (four schedulers).
+constexpr int TRSM_THREADS = 128;
+__global__ void __launch_bounds__(TRSM_THREADS) k_trsm_panel(int d, int kb, double *H, const int32_t *n_c,
+                                                             const int32_t *info) {
     const int c = blockIdx.y, ib = kb + 1 + blockIdx.x;
     if (c >= *n_c || info[c]) return;
     const int nblk = (d + NB - 1) / NB;
     if (ib >= nblk) return;
     double *A = H + (size_t)c * d * d;
     __shared__ double l[NB][NB + 1];
+    __shared__ double xs[NB][NB + 1];
+    __shared__ double inv[NB];
     const int o = kb * NB;
-    for (int e = threadIdx.x; e < NB * NB; e += NB) {
+    for (int e = threadIdx.x; e < NB * NB; e += TRSM_THREADS) {
         const int i = e / NB, j = e % NB;
         l[i][j] = (o + i < d && o + j < d) ? A[(size_t)(o + i) * d + o + j] : (i == j ? 1.0 : 0.0);
     }
     __syncthreads();
-    const int row = ib * NB + threadIdx.x;
-    if (row >= d) return;
-    double x[NB];
+    if (threadIdx.x < NB) inv[threadIdx.x] = 1.0 / l[threadIdx.x][threadIdx.x];
+    const int r = threadIdx.x & (NB - 1), part = threadIdx.x >> 5;
+    const int row = ib * NB + r;
+    double x[NB / 4];
 #pragma unroll
-    for (int j = 0; j < NB; ++j) x[j] = (o + j < d) ? A[(size_t)row * d + o + j] : 0.0;
+    for (int q = 0; q < NB / 4; ++q) {
+        const int j = part + 4 * q;
+        x[q] = (row < d && o + j < d) ? A[(size_t)row * d + o + j] : 0.0;
+    }
+    __syncthreads();
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-        double s = x[j];
+        if (part == (j & 3)) {
+            x[j >> 2] *= inv[j];
+            xs[r][j] = x[j >> 2];
+        }
+        __syncthreads();
+        const double xj = xs[r][j];
 #pragma unroll
-        for (int q = 0; q < j; ++q) s -= x[q] * l[j][q];
-        x[j] = s / l[j][j];
+        for (int q = 0; q < NB / 4; ++q)
+            if (part + 4 * q > j) x[q] -= xj * l[part + 4 * q][j];
     }
 #pragma unroll
-    for (int j = 0; j < NB; ++j)
-        if (o + j < d) A[(size_t)row * d + o + j] = x[j];
+    for (int q = 0; q < NB / 4; ++q) {
+        const int j = part + 4 * q;
+        if (row < d && o + j < d) A[(size_t)row * d + o + j] = x[q];
+    }
 }
 
 // Trailing update A[ib][jb] -= A[ib][kb] A[jb][kb]^T for kb < jb <= ib.
@@ -748,11 +782,11 @@ void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P
     ProfScope prof(PROF_CHOLESKY, s);
     for (int kb = 0; kb < nblk; ++kb) {
         note_launch();
-        k_potrf_diag<<<cap, NB * NB, 0, s>>>(d, kb, H, n_c, info);
+        k_potrf_diag<<<cap, DIAG_THREADS, 0, s>>>(d, kb, H, n_c, info);
         const int rest = nblk - kb - 1;
         if (rest > 0) {
             note_launch();
-            k_trsm_panel<<<dim3(rest, cap), NB, 0, s>>>(d, kb, H, n_c, info);
+            k_trsm_panel<<<dim3(rest, cap), TRSM_THREADS, 0, s>>>(d, kb, H, n_c, info);
             note_launch();
             k_syrk_update<<<dim3(rest, rest, cap), 256, 0, s>>>(d, kb, H, n_c, info);
         }

@@ -28,7 +28,9 @@ int tc_tuned_tile(int d, int K, int prec);
 // (autotuned once per shape; that first call synchronises the stream) and
 // encodes the tensor maps.
 sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s);
-sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const double *u, float *u32,
+// l at every ray sample x_rj = c + t_j t_exit,r u_r from the FP32 directions
+// u32 [n_rays][d]; chunks of the scratch row capacity.
+sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const float *u32,
                         const double *texit, double *ell_all, cudaStream_t s);
 void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, const float *XT, const int32_t *act,
                      const int32_t *n_act, int n, float *FT, float *GT, cudaStream_t s);

@@ -873,7 +873,9 @@ float time_tile(const ProbView &pv, TcWs &t, int bn, cudaStream_t s) {
     if (!make_map(&u.mapT, u.p[0], d, d, K, ldp, u.prec, bn) || !make_map(&u.mapB, u.p[1], d, d, K, ldp, u.prec, bn))
         return -1.f;
     TcArgs a = base_args(pv, u);
-    a.n_rows_max = (int)(u.rows < 2048 ? u.rows : 2048);
+    // as many rows as the scratch holds, up to 16384: enough row blocks to fill
+    // every SM, so the timing ranks the tiles as a full-size launch would
+    a.n_rows_max = (int)(u.rows < 16384 ? u.rows : 16384);
     a.G = (float *)u.p[8];
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.f;
@@ -902,11 +904,13 @@ int pick_tile(const ProbView &pv, TcWs &t, cudaStream_t s) {
     if (it != g_tune.end()) return it->second;
     int bn = bn_of(pv.d);
     if (!(off && off[0] == '0')) {
+        // widest tile first; a narrower one must be at least 3 % faster to win,
+        // so timing noise between near-equal tiles does not flip the choice
         float best = -1.f;
-        for (int cand : {64, 128, 256}) {
+        for (int cand : {256, 128, 64}) {
             if (cand > 64 && (pv.d + 63) / 64 * 64 <= cand / 2) continue;  // tile mostly padding
             const float ms = time_tile(pv, t, cand, s);
-            if (ms > 0.f && (best < 0.f || ms < best)) {
+            if (ms > 0.f && (best < 0.f || ms < 0.97f * best)) {
                 best = ms;
                 bn = cand;
             }
@@ -941,15 +945,9 @@ sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s) {
     return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
 }
 
-sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const double *u, float *u32,
+sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const float *u32,
                         const double *texit, double *ell_all, cudaStream_t s) {
     const int64_t total = (int64_t)c->n_rays * c->n_steps;
-    {
-        const size_t nel = (size_t)c->n_rays * pv.d;
-        note_launch();
-        k_tc_points_in<<<(unsigned)((nel + 255) / 256 < 4096 ? (nel + 255) / 256 : 4096), 256, 0, s>>>(
-            c->n_rays, pv.d, u, u32);
-    }
     for (int64_t f0 = 0; f0 < total; f0 += (int64_t)t.rows) {
         const int rows = (int)((total - f0) < (int64_t)t.rows ? (total - f0) : (int64_t)t.rows);
         TcArgs a = base_args(pv, t);
