@@ -69,6 +69,7 @@ struct TcArgs {
     int ldz, z_rows;
     float *qpart;           // [rows][K][n_ntile]
     const float *R;         // [rows][K]
+    const uint32_t *rflag;  // [row blocks][K]: some row of the block has r_nk > 0
     float *G;               // [walkers][d] grad f
     int n_ntile;
     int32_t *err;
@@ -158,12 +159,22 @@ struct TileInfo {
     int mb, nt, k;     // row block, output column tile, component (GEMM1)
     int c_lo, c_hi;    // K-chunk range (GEMM1) or chunk count per component (GEMM2: c_hi)
     int nchunks;
+    uint32_t kmask;    // GEMM2: components with r_nk > 0 somewhere in the row block
 };
 
+// Component of GEMM2 chunk q: the (q / c_hi)-th set bit of the tile's mask.
+__device__ __forceinline__ int chunk_component(const TileInfo &ti, int q) {
+    int idx = q / ti.c_hi;
+    uint32_t m = ti.kmask;
+    while (idx-- > 0) m &= m - 1;
+    return __ffs(m) - 1;
+}
+
 template <int MODE, int BN, int KC>
-__device__ __forceinline__ TileInfo decode_tile(int t, int d, int K) {
+__device__ __forceinline__ TileInfo decode_tile(int t, int d, int K, const uint32_t *rflag) {
     TileInfo ti;
     const int nct = (d + BN - 1) / BN;
+    ti.kmask = 0;
     if (MODE == MODE_G) {
         ti.nt = t % nct;
         ti.mb = t / nct;
@@ -171,7 +182,13 @@ __device__ __forceinline__ TileInfo decode_tile(int t, int d, int K) {
         const int jmax = min(d, (ti.nt + 1) * BN);
         ti.c_lo = 0;
         ti.c_hi = (jmax + KC - 1) / KC;
-        ti.nchunks = K * ti.c_hi;
+        // components whose responsibility is zero at every row of the block add
+        // exactly nothing to the gradient: their chunks are not visited (every
+        // role reads the same flags, so the three agree on the chunk list)
+        for (int k = 0; k < K; ++k)
+            if (!rflag || rflag[(size_t)ti.mb * K + k]) ti.kmask |= 1u << k;
+        if (ti.kmask == 0) ti.kmask = 1u;  // keep one (all-zero or non-finite rows)
+        ti.nchunks = __popc(ti.kmask) * ti.c_hi;
     } else {
         // column tiles of one (row block, component) are adjacent in the schedule, so
         // CTAs that run together gather the same x rows (served from L2)
@@ -257,7 +274,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             uint32_t inflight_phase[8];
             int n_inflight = 0;
             for (int it = 0, t = tile_of(0, nct); t < n_tiles && !*s_abort; t = tile_of(++it, nct)) {
-                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K);
+                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag);
                 bool ok = true;
                 for (int q = 0; q < ti.nchunks; ++q) {
                     if (!bwait(&empty[stage], phase ^ 1, s_abort)) {
@@ -267,7 +284,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                     mbar_arrive_tx(&full[stage], A_BYTES + B_BYTES);
                     int kk, c0;
                     if (MODE == MODE_G) {
-                        kk = q / ti.c_hi;
+                        kk = chunk_component(ti, q);
                         c0 = (q % ti.c_hi) * KC;
                     } else {
                         kk = ti.k;
@@ -304,7 +321,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             uint32_t acc_phase = 0;
             bool issued = false;
             for (int it = 0, t = tile_of(0, nct); t < n_tiles && !*s_abort; t = tile_of(++it, nct)) {
-                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K);
+                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag);
                 if (!bwait(&tempty[acc], acc_phase ^ 1, s_abort)) break;
                 tc_fence_after();
                 const uint32_t dt = tmem + (uint32_t)(acc * BN);
@@ -350,7 +367,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int it = 0, t = tile_of(0, nct); t < n_tiles && !warp_aborted(s_abort); t = tile_of(++it, nct)) {
-            const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K);
+            const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag);
             if (!warp_bwait(&tfull[acc], acc_phase, s_abort)) break;
             tc_fence_after();
             const int n = ti.mb * BM + r;
@@ -436,31 +453,43 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
 // FP64, exp/log of the shifted values (in [0, 1] and [1, K]) in FP32, whose
 // absolute error stays below the FP32 resolution of the outputs.
 // mode 0: walkers (FT[act[n]] = -l, R); mode 1: ray samples (ell[flat0 + n] = l);
-// mode 2: points (ell[n] = l, R).
+// mode 2: points (ell[n] = l, R). Modes 0 and 2 also raise rflag[block][k] when
+// some row of the 128-row block has r_nk > 0 (GEMM2 and the scaling pass skip
+// the other (block, component) pairs, whose terms are exactly zero).
 __global__ void __launch_bounds__(128) k_tc_lse(int mode, int K, int n_ntile, const int32_t *n_rows_dev,
                                                 int n_rows_max, const int32_t *act, const float *qpart,
-                                                const double *a_k, float *R, float *FT, double *ell) {
+                                                const double *a_k, float *R, float *FT, double *ell,
+                                                uint32_t *rflag) {
     const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= n_rows) return;
+    const bool valid = n < n_rows;
     double e[kMaxK];
     double emax = -INFINITY;
-    for (int k = 0; k < K; ++k) {
-        const float *qp = qpart + ((size_t)n * K + k) * n_ntile;
-        double q = 0.0;
-        for (int t = 0; t < n_ntile; ++t) q += (double)qp[t];
-        e[k] = a_k[k] - 0.5 * q;
-        emax = fmax(emax, e[k]);
-    }
     float s = 0.f;
-    for (int k = 0; k < K; ++k) s += __expf((float)(e[k] - emax));
+    if (valid) {
+        for (int k = 0; k < K; ++k) {
+            const float *qp = qpart + ((size_t)n * K + k) * n_ntile;
+            double q = 0.0;
+            for (int t = 0; t < n_ntile; ++t) q += (double)qp[t];
+            e[k] = a_k[k] - 0.5 * q;
+            emax = fmax(emax, e[k]);
+        }
+        for (int k = 0; k < K; ++k) s += __expf((float)(e[k] - emax));
+    }
     const double l = emax + (double)__logf(s);
     if (mode == 1) {
-        ell[n] = l;
+        if (valid) ell[n] = l;
         return;
     }
     const float inv = 1.f / s;
-    for (int k = 0; k < K; ++k) R[(size_t)n * K + k] = __expf((float)(e[k] - emax)) * inv;
+    for (int k = 0; k < K; ++k) {
+        const float r = valid ? __expf((float)(e[k] - emax)) * inv : 0.f;
+        if (valid) R[(size_t)n * K + k] = r;
+        // row block of 128 rows = four whole warps: one flag per (block, component)
+        const unsigned any = __ballot_sync(0xffffffffu, r > 0.f);
+        if (rflag && any && (threadIdx.x & 31) == 0) atomicOr(&rflag[(size_t)(n / 128) * K + k], 1u);
+    }
+    if (!valid) return;
     if (mode == 0)
         FT[act ? act[n] : n] = (float)(-l);
     else
@@ -570,7 +599,7 @@ __global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int K, i
 // A operand of GEMM2 in place: z[k][n][:] *= r_nk (rows up to the next multiple of 128 zeroed).
 template <int PREC>
 __global__ void __launch_bounds__(256) k_tc_scale(int K, int rows_cap, int ldz, const int32_t *n_rows_dev,
-                                                  int n_rows_max, const float *R, void *Z) {
+                                                  int n_rows_max, const float *R, const uint32_t *rflag, void *Z) {
     constexpr int VE = (PREC == SB_PREC_BF16) ? 8 : 4;
     const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
     int rows_pad = (n_rows + BM - 1) / BM * BM;
@@ -580,6 +609,7 @@ __global__ void __launch_bounds__(256) k_tc_scale(int K, int rows_cap, int ldz, 
     const int n = e / ncg, cg = e - n * ncg;
     if (n >= rows_pad) return;
     const int k = blockIdx.y;
+    if (!rflag[(size_t)(n / BM) * K + k]) return;  // GEMM2 does not read this (block, component)
     const size_t o = ((size_t)k * rows_cap + n) * ldz + (size_t)cg * VE;
     if (n >= n_rows) {  // padding rows hold stale values (possibly NaN): overwrite, never scale
         if (PREC == SB_PREC_BF16)
@@ -769,10 +799,10 @@ void launch_scale(const TcWs &t, int K, const int32_t *n_rows_dev, int n_rows_ma
     note_launch();
     if (t.prec == SB_PREC_BF16)
         k_tc_scale<SB_PREC_BF16><<<grid, 256, 0, s>>>(K, (int)t.rows, ldz, n_rows_dev, n_rows_max,
-                                                     (const float *)t.p[6], t.p[4]);
+                                                     (const float *)t.p[6], (const uint32_t *)t.p[10], t.p[4]);
     else
         k_tc_scale<SB_PREC_TF32><<<grid, 256, 0, s>>>(K, (int)t.rows, ldz, n_rows_dev, n_rows_max,
-                                                     (const float *)t.p[6], t.p[4]);
+                                                     (const float *)t.p[6], (const uint32_t *)t.p[10], t.p[4]);
 }
 
 TcArgs base_args(const ProbView &pv, const TcWs &t) {
@@ -786,6 +816,7 @@ TcArgs base_args(const ProbView &pv, const TcWs &t) {
     a.z_rows = (int)t.rows;
     a.qpart = (float *)t.p[5];
     a.R = (const float *)t.p[6];
+    a.rflag = (const uint32_t *)t.p[10];
     a.n_ntile = (pv.d + t.bn - 1) / t.bn;
     a.err = pv.status;
     return a;
@@ -817,6 +848,7 @@ void carve_tc(Carver &cv, TcWs &t, int rows, int d, int K, int prec) {
     t.p[7] = cv.take<float>((size_t)rows * d);
     t.p[8] = cv.take<float>((size_t)rows * d);
     t.p[9] = cv.take<uint8_t>((size_t)K * rows * ldp * e);
+    t.p[10] = cv.take<uint32_t>((size_t)(rows / BM) * K);
 }
 
 int tc_ray_chunk(int d, int K, int64_t total) {
@@ -876,6 +908,7 @@ float time_tile(const ProbView &pv, TcWs &t, int bn, cudaStream_t s) {
     // as many rows as the scratch holds, up to 16384: enough row blocks to fill
     // every SM, so the timing ranks the tiles as a full-size launch would
     a.n_rows_max = (int)(u.rows < 16384 ? u.rows : 16384);
+    a.rflag = nullptr;  // time the dense case: every component visited
     a.G = (float *)u.p[8];
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.f;
@@ -956,7 +989,7 @@ sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, c
         launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
         note_launch();
         k_tc_lse<<<(rows + 127) / 128, 128, 0, s>>>(1, pv.K, a.n_ntile, nullptr, rows, nullptr, a.qpart, pv.a,
-                                                    nullptr, nullptr, ell_all + f0);
+                                                    nullptr, nullptr, ell_all + f0, nullptr);
     }
     return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
 }
@@ -971,8 +1004,9 @@ void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, cons
     launch_center(t, 0, pv.d, pv.K, n_act, n, act, XT, nullptr, nullptr, 1, 0, s);
     launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
     note_launch();
+    cudaMemsetAsync(t.p[10], 0, sizeof(uint32_t) * ((n + BM - 1) / BM) * pv.K, s);
     k_tc_lse<<<(n + 127) / 128, 128, 0, s>>>(0, pv.K, a.n_ntile, n_act, n, act, a.qpart, pv.a, (float *)t.p[6], FT,
-                                             nullptr);
+                                             nullptr, (uint32_t *)t.p[10]);
     launch_scale(t, pv.K, n_act, n, s);
     a.G = GT;
     launch_gemm_any(t.prec, MODE_G, t.bn, t.mapZ, t.mapB, a, s);
@@ -992,8 +1026,9 @@ sb_status tc_loglik_points(const ProbView &pv, const sb_config *c, const TcWs &t
     launch_center(t, 0, pv.d, pv.K, nullptr, n, nullptr, X, nullptr, nullptr, 1, 0, s);
     launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
     note_launch();
+    cudaMemsetAsync(t.p[10], 0, sizeof(uint32_t) * ((n + BM - 1) / BM) * pv.K, s);
     k_tc_lse<<<(n + 127) / 128, 128, 0, s>>>(2, pv.K, a.n_ntile, nullptr, n, nullptr, a.qpart, pv.a,
-                                             (float *)t.p[6], nullptr, ell);
+                                             (float *)t.p[6], nullptr, ell, (uint32_t *)t.p[10]);
     if (grad) {
         launch_scale(t, pv.K, nullptr, n, s);
         a.G = G;
