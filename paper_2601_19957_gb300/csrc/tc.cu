@@ -10,10 +10,14 @@
 // Data flow per evaluation round:
 //   k_tc_center   A1[k][n][:] = round(x_n - mu_k), formed in FP32 (walkers gathered
 //                 through the active list, or ray samples c + t u), bf16 or tf32
-//   k_tc_gemm Z   z = A1 L_k (GEMM1): |z|^2 partials, z rows stored [k][n][:]
-//   k_tc_lse      l, r (FP64 reduction)
-//   k_tc_scale    z[k][n][:] *= r_nk in place -> A2 of GEMM2
-//   k_tc_gemm G   grad f = sum_k A2_k L_k^T rows (GEMM2)
+//   k_tc_gemm ZR  z = A1 L_k (GEMM1): |z|^2 partials only
+//   k_tc_lse      l, r; flags of the (128-row block, component) pairs with r > 0
+//   k_tc_gemm ZW  GEMM1 again for the flagged pairs only, z stored as
+//                 A2[k][n][:] = r_nk z_nk (the A operand of GEMM2)
+//   k_tc_gemm G   grad f = sum_k A2_k L_k^T rows over the flagged components (GEMM2)
+// With separated modes most responsibilities are exactly 0 in FP32 (the
+// exponent underflows), so the store pass and GEMM2 visit a fraction of the
+// K components; the terms they skip are exactly zero.
 // Both operands of both GEMMs reach shared memory by TMA (3-D tensor maps,
 // 128-byte swizzle, out-of-range rows/columns zero-filled), so the MMA
 // pipeline never waits on a gathered load. Centring before rounding keeps the
@@ -48,6 +52,7 @@ namespace {
 constexpr int BM = 128;
 constexpr int ROWB = 128;  // bytes of one K chunk per row (one swizzle atom row)
 constexpr int THREADS = 192;
+constexpr int kMaxGroupList = 4096;  // store-pass groups compacted in shared memory
 
 // MODE_ZW: GEMM1 storing z (walkers/points); MODE_ZR: GEMM1 values only (ray samples); MODE_G: GEMM2
 enum { MODE_ZW = 0, MODE_ZR = 1, MODE_G = 2 };
@@ -70,6 +75,7 @@ struct TcArgs {
     float *qpart;           // [rows][K][n_ntile]
     const float *R;         // [rows][K]
     const uint32_t *rflag;  // [row blocks][K]: some row of the block has r_nk > 0
+    int prof;               // profiling class of the launch (-1: by mode)
     float *G;               // [walkers][d] grad f
     int n_ntile;
     int32_t *err;
@@ -160,7 +166,17 @@ struct TileInfo {
     int c_lo, c_hi;    // K-chunk range (GEMM1) or chunk count per component (GEMM2: c_hi)
     int nchunks;
     uint32_t kmask;    // GEMM2: components with r_nk > 0 somewhere in the row block
+    bool skip;         // GEMM1 store pass: this (row block, component) is not needed
 };
+
+// Components with r_nk > 0 at some row of row block mb (all when no flags are
+// given); a block with none keeps component 0 (non-finite or empty rows).
+__device__ __forceinline__ uint32_t block_kmask(const uint32_t *rflag, int mb, int K) {
+    uint32_t m = 0;
+    for (int k = 0; k < K; ++k)
+        if (!rflag || rflag[(size_t)mb * K + k]) m |= 1u << k;
+    return m ? m : 1u;
+}
 
 // Component of GEMM2 chunk q: the (q / c_hi)-th set bit of the tile's mask.
 __device__ __forceinline__ int chunk_component(const TileInfo &ti, int q) {
@@ -171,10 +187,12 @@ __device__ __forceinline__ int chunk_component(const TileInfo &ti, int q) {
 }
 
 template <int MODE, int BN, int KC>
-__device__ __forceinline__ TileInfo decode_tile(int t, int d, int K, const uint32_t *rflag) {
+__device__ __forceinline__ TileInfo decode_tile(int t, int d, int K, const uint32_t *rflag, const int *glist) {
     TileInfo ti;
     const int nct = (d + BN - 1) / BN;
+    if (glist) t = glist[t / nct] * nct + t % nct;  // compacted store-pass schedule
     ti.kmask = 0;
+    ti.skip = false;
     if (MODE == MODE_G) {
         ti.nt = t % nct;
         ti.mb = t / nct;
@@ -185,9 +203,7 @@ __device__ __forceinline__ TileInfo decode_tile(int t, int d, int K, const uint3
         // components whose responsibility is zero at every row of the block add
         // exactly nothing to the gradient: their chunks are not visited (every
         // role reads the same flags, so the three agree on the chunk list)
-        for (int k = 0; k < K; ++k)
-            if (!rflag || rflag[(size_t)ti.mb * K + k]) ti.kmask |= 1u << k;
-        if (ti.kmask == 0) ti.kmask = 1u;  // keep one (all-zero or non-finite rows)
+        ti.kmask = block_kmask(rflag, ti.mb, K);
         ti.nchunks = __popc(ti.kmask) * ti.c_hi;
     } else {
         // column tiles of one (row block, component) are adjacent in the schedule, so
@@ -198,6 +214,9 @@ __device__ __forceinline__ TileInfo decode_tile(int t, int d, int K, const uint3
         ti.c_lo = (ti.nt * BN) / KC;
         ti.c_hi = (d + KC - 1) / KC;
         ti.nchunks = ti.c_hi - ti.c_lo;
+        // store pass (flags given): only the (block, component) pairs GEMM2 reads
+        // (already the case for a compacted schedule)
+        if (MODE == MODE_ZW && rflag && !glist) ti.skip = !((block_kmask(rflag, ti.mb, K) >> ti.k) & 1u);
     }
     return ti;
 }
@@ -234,13 +253,44 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
     uint64_t *drain = tempty + 2;
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(drain + 1);
     volatile int *s_abort = reinterpret_cast<volatile int *>(s_tmem + 1);
+    int *s_wcnt = const_cast<int *>(s_abort) + 1;  // [8] per-warp counts (group compaction)
+    int *s_gcount = s_wcnt + 8;
+    int *s_glist = s_gcount + 1;                  // [kMaxGroupList] GEMM1 store pass: groups to visit
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int d = a.d, K = a.K;
     const int n_rows = a.n_rows_dev ? *a.n_rows_dev : a.n_rows_max;
     const int n_mblk = (n_rows + BM - 1) / BM;
     const int nct = (d + BN - 1) / BN;
-    const int n_tiles = (MODE == MODE_G) ? n_mblk * nct : n_mblk * nct * K;
+    int n_tiles = (MODE == MODE_G) ? n_mblk * nct : n_mblk * nct * K;
+    // Store pass: the (row block, component) groups GEMM2 reads, compacted in
+    // order, so that the round-robin deal spreads the work that remains (a
+    // fixed stride over all groups would hand every CTA the same component).
+    const int n_groups = n_mblk * K;
+    const bool compact = MODE == MODE_ZW && a.rflag != nullptr && n_groups <= kMaxGroupList;
+    if (compact) {
+        if (threadIdx.x == 0) *s_gcount = 0;
+        __syncthreads();
+        for (int g0 = 0; g0 < n_groups; g0 += (int)blockDim.x) {
+            const int g = g0 + (int)threadIdx.x;
+            const bool act = g < n_groups && ((block_kmask(a.rflag, g / K, K) >> (g % K)) & 1u);
+            const unsigned bal = __ballot_sync(0xffffffffu, act);
+            if (lane == 0) s_wcnt[warp] = __popc(bal);
+            __syncthreads();
+            int off = *s_gcount;
+            for (int w = 0; w < warp; ++w) off += s_wcnt[w];
+            if (act) s_glist[off + __popc(bal & ((1u << lane) - 1u))] = g;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int tot = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_wcnt[w];
+                *s_gcount += tot;
+            }
+            __syncthreads();
+        }
+        n_tiles = *s_gcount * nct;
+    }
+    const int *glist = compact ? s_glist : nullptr;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -274,7 +324,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             uint32_t inflight_phase[8];
             int n_inflight = 0;
             for (int it = 0, t = tile_of(0, nct); t < n_tiles && !*s_abort; t = tile_of(++it, nct)) {
-                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag);
+                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag, glist);
+                if (ti.skip) continue;
                 bool ok = true;
                 for (int q = 0; q < ti.nchunks; ++q) {
                     if (!bwait(&empty[stage], phase ^ 1, s_abort)) {
@@ -321,7 +372,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             uint32_t acc_phase = 0;
             bool issued = false;
             for (int it = 0, t = tile_of(0, nct); t < n_tiles && !*s_abort; t = tile_of(++it, nct)) {
-                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag);
+                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag, glist);
+                if (ti.skip) continue;
                 if (!bwait(&tempty[acc], acc_phase ^ 1, s_abort)) break;
                 tc_fence_after();
                 const uint32_t dt = tmem + (uint32_t)(acc * BN);
@@ -367,12 +419,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int it = 0, t = tile_of(0, nct); t < n_tiles && !warp_aborted(s_abort); t = tile_of(++it, nct)) {
-            const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag);
+            const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag, glist);
+            if (ti.skip) continue;
             if (!warp_bwait(&tfull[acc], acc_phase, s_abort)) break;
             tc_fence_after();
             const int n = ti.mb * BM + r;
             const bool valid = n < n_rows;
             const int w_out = (MODE == MODE_G && valid) ? (a.act ? a.act[n] : n) : 0;
+            // store pass: z is written as r_nk z_nk (GEMM2's A operand); rows past the
+            // live count are written as zeros (their z rows would be stale)
+            const bool scaled = MODE == MODE_ZW && a.rflag != nullptr;
+            const float sc = scaled ? (valid ? a.R[(size_t)n * K + ti.k] : 0.f) : 1.f;
+            const bool store_row = MODE == MODE_ZW && (valid || (scaled && n < a.z_rows));
             const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * BN);
             float q2 = 0.f;
 #pragma unroll 1
@@ -401,7 +459,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                         const float z = __uint_as_float(v[e]);
                         q2 = fmaf(z, z, q2);
                     }
-                    if (MODE == MODE_ZW && valid && col < a.ldz) {
+                    if (store_row && col < a.ldz) {
+                        if (scaled)
+#pragma unroll
+                            for (int e = 0; e < 32; ++e) {
+                                const float y = __uint_as_float(v[e]) * sc;
+                                v[e] = __float_as_uint(PREC == SB_PREC_BF16 ? y : to_tf32(y));
+                            }
                         const size_t zrow = ((size_t)ti.k * a.z_rows + n) * a.ldz + col;
                         if (PREC == SB_PREC_BF16) {
                             __nv_bfloat16 *zr = reinterpret_cast<__nv_bfloat16 *>(a.Z) + zrow;
@@ -428,7 +492,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                     }
                 }
             }
-            if (MODE != MODE_G && valid) a.qpart[((size_t)n * K + ti.k) * a.n_ntile + ti.nt] = q2;
+            if (MODE != MODE_G && !scaled && valid) a.qpart[((size_t)n * K + ti.k) * a.n_ntile + ti.nt] = q2;
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
@@ -596,46 +660,6 @@ __global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int K, i
     }
 }
 
-// A operand of GEMM2 in place: z[k][n][:] *= r_nk (rows up to the next multiple of 128 zeroed).
-template <int PREC>
-__global__ void __launch_bounds__(256) k_tc_scale(int K, int rows_cap, int ldz, const int32_t *n_rows_dev,
-                                                  int n_rows_max, const float *R, const uint32_t *rflag, void *Z) {
-    constexpr int VE = (PREC == SB_PREC_BF16) ? 8 : 4;
-    const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
-    int rows_pad = (n_rows + BM - 1) / BM * BM;
-    if (rows_pad > rows_cap) rows_pad = rows_cap;
-    const int ncg = ldz / VE;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = e / ncg, cg = e - n * ncg;
-    if (n >= rows_pad) return;
-    const int k = blockIdx.y;
-    if (!rflag[(size_t)(n / BM) * K + k]) return;  // GEMM2 does not read this (block, component)
-    const size_t o = ((size_t)k * rows_cap + n) * ldz + (size_t)cg * VE;
-    if (n >= n_rows) {  // padding rows hold stale values (possibly NaN): overwrite, never scale
-        if (PREC == SB_PREC_BF16)
-            *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(Z) + o) = make_uint4(0u, 0u, 0u, 0u);
-        else
-            *reinterpret_cast<float4 *>(reinterpret_cast<float *>(Z) + o) = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
-    const float r = R[(size_t)n * K + k];
-    if (PREC == SB_PREC_BF16) {
-        uint4 *pz = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(Z) + o);
-        uint4 p = *pz;
-        uint32_t w[4] = {p.x, p.y, p.z, p.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[q]);
-            w[q] = pack_bf16x2(__low2float(h) * r, __high2float(h) * r);
-        }
-        *pz = make_uint4(w[0], w[1], w[2], w[3]);
-    } else {
-        float4 *pz = reinterpret_cast<float4 *>(reinterpret_cast<float *>(Z) + o);
-        const float4 v = *pz;
-        *pz = make_float4(to_tf32(v.x * r), to_tf32(v.y * r), to_tf32(v.z * r), to_tf32(v.w * r));
-    }
-}
-
 template <typename E>
 __global__ void k_tc_convert_L(int d, int K, int ldp, const double *L, E *LT, E *LB) {
     const size_t tot = (size_t)K * d * ldp;
@@ -709,7 +733,6 @@ inline int esz(int prec) { return prec == SB_PREC_BF16 ? 2 : 4; }
 inline int ldp_of(int d, int prec) { return prec == SB_PREC_BF16 ? (d + 7) / 8 * 8 : (d + 3) / 4 * 4; }
 inline int bn_of(int d) { return d > 128 ? 256 : (d > 64 ? 128 : 64); }
 inline int ldz_of(int d) { return (d + 63) / 64 * 64; }
-inline int ldz_of_t(const TcWs &t) { return t.ldz; }
 
 // 3-D map over [dim2][dim1][stride1] elements with box (128 bytes of dim0, box1 rows, 1).
 bool make_map(CUtensorMap *m, void *base, int dim0, int dim1, int dim2, int stride1, int prec, int box1) {
@@ -729,7 +752,8 @@ bool make_map(CUtensorMap *m, void *base, int dim0, int dim1, int dim2, int stri
 template <int BN, int PREC, int MODE>
 constexpr int smem_bytes() {
     constexpr int STAGES = (BN >= 256) ? 4 : 6;
-    return 1024 + STAGES * (BM * ROWB + BN * ROWB) + (2 * STAGES + 5) * 8 + 64;
+    return 1024 + STAGES * (BM * ROWB + BN * ROWB) + (2 * STAGES + 5) * 8 + 64 +
+           (MODE == MODE_ZW ? (9 + kMaxGroupList) * 4 : 0);
 }
 
 template <int BN, int PREC, int MODE>
@@ -743,7 +767,9 @@ void launch_gemm(const CUtensorMap &mapA, const CUtensorMap &map, const TcArgs &
     const long long groups = (long long)mb * (MODE == MODE_G ? 1 : a.K);
     int grid = num_sms();
     if (groups < grid) grid = (int)(groups > 0 ? groups : 1);
-    ProfScope prof(MODE == MODE_ZW ? PROF_TC_Z_WALKERS : (MODE == MODE_ZR ? PROF_TC_Z_RAYS : PROF_TC_GRAD), s);
+    ProfScope prof(a.prof >= 0 ? a.prof
+                               : (MODE == MODE_ZW ? PROF_TC_Z_WALKERS : (MODE == MODE_ZR ? PROF_TC_Z_RAYS : PROF_TC_GRAD)),
+                   s);
     note_launch();
     k_tc_gemm<BN, PREC, MODE><<<grid, THREADS, SM, s>>>(mapA, map, a);
 }
@@ -790,21 +816,6 @@ void launch_center(const TcWs &t, int ray_mode, int d, int K, const int32_t *n_r
                                                       (const float *)t.p[3], t.p[9]);
 }
 
-void launch_scale(const TcWs &t, int K, const int32_t *n_rows_dev, int n_rows_max, cudaStream_t s) {
-    const int ldz = ldz_of_t(t);
-    const int ncg = ldz / (t.prec == SB_PREC_BF16 ? 8 : 4);
-    int rows = (n_rows_max + BM - 1) / BM * BM;
-    if (rows > (int)t.rows) rows = (int)t.rows;
-    const dim3 grid((unsigned)(((long long)rows * ncg + 255) / 256), (unsigned)K);
-    note_launch();
-    if (t.prec == SB_PREC_BF16)
-        k_tc_scale<SB_PREC_BF16><<<grid, 256, 0, s>>>(K, (int)t.rows, ldz, n_rows_dev, n_rows_max,
-                                                     (const float *)t.p[6], (const uint32_t *)t.p[10], t.p[4]);
-    else
-        k_tc_scale<SB_PREC_TF32><<<grid, 256, 0, s>>>(K, (int)t.rows, ldz, n_rows_dev, n_rows_max,
-                                                     (const float *)t.p[6], (const uint32_t *)t.p[10], t.p[4]);
-}
-
 TcArgs base_args(const ProbView &pv, const TcWs &t) {
     TcArgs a{};
     a.d = pv.d;
@@ -817,6 +828,7 @@ TcArgs base_args(const ProbView &pv, const TcWs &t) {
     a.qpart = (float *)t.p[5];
     a.R = (const float *)t.p[6];
     a.rflag = (const uint32_t *)t.p[10];
+    a.prof = -1;
     a.n_ntile = (pv.d + t.bn - 1) / t.bn;
     a.err = pv.status;
     return a;
@@ -1001,13 +1013,18 @@ void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, cons
     a.act = act;
     a.n_rows_dev = n_act;
     a.n_rows_max = n;
+    a.prof = PROF_TC_Z_WALKERS;
     launch_center(t, 0, pv.d, pv.K, n_act, n, act, XT, nullptr, nullptr, 1, 0, s);
-    launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
-    note_launch();
+    // |z|^2 for every component (no z stored), then l, r and the flags of the
+    // (row block, component) pairs with r > 0, then z again for those pairs only,
+    // stored as r z (GEMM2's A operand), then the gradient
+    launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
     cudaMemsetAsync(t.p[10], 0, sizeof(uint32_t) * ((n + BM - 1) / BM) * pv.K, s);
+    note_launch();
     k_tc_lse<<<(n + 127) / 128, 128, 0, s>>>(0, pv.K, a.n_ntile, n_act, n, act, a.qpart, pv.a, (float *)t.p[6], FT,
                                              nullptr, (uint32_t *)t.p[10]);
-    launch_scale(t, pv.K, n_act, n, s);
+    launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
+    a.prof = -1;
     a.G = GT;
     launch_gemm_any(t.prec, MODE_G, t.bn, t.mapZ, t.mapB, a, s);
 }
@@ -1023,14 +1040,16 @@ sb_status tc_loglik_points(const ProbView &pv, const sb_config *c, const TcWs &t
                      0, s>>>(n, pv.d, x, X);
     TcArgs a = base_args(pv, t);
     a.n_rows_max = n;
+    a.prof = PROF_TC_Z_WALKERS;
     launch_center(t, 0, pv.d, pv.K, nullptr, n, nullptr, X, nullptr, nullptr, 1, 0, s);
-    launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
-    note_launch();
+    launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
     cudaMemsetAsync(t.p[10], 0, sizeof(uint32_t) * ((n + BM - 1) / BM) * pv.K, s);
+    note_launch();
     k_tc_lse<<<(n + 127) / 128, 128, 0, s>>>(2, pv.K, a.n_ntile, nullptr, n, nullptr, a.qpart, pv.a,
                                              (float *)t.p[6], nullptr, ell, (uint32_t *)t.p[10]);
     if (grad) {
-        launch_scale(t, pv.K, nullptr, n, s);
+        launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
+        a.prof = -1;
         a.G = G;
         launch_gemm_any(t.prec, MODE_G, t.bn, t.mapZ, t.mapB, a, s);
         note_launch();
