@@ -219,16 +219,21 @@ __global__ void __launch_bounds__(256) k_gather_rows(int d, const double *X, con
 }
 
 // ------------------------------------------------------------------ P_k = L_k L_k^T
-__global__ void __launch_bounds__(256) k_precision(int d, const double *L, double *P) {
-    const int k = blockIdx.z, i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
-    if (j0 > i0) return;  // lower blocks only, mirrored on store
+// 32 x 32 output tiles (lower ones, mirrored on store), 256 threads with 2 x 2
+// outputs each: small tiles keep the deep tiles near the diagonal short, which
+// bounds the FP64 critical path when only a few components are formed.
+constexpr int PT = 32;
+__global__ void __launch_bounds__(256) k_precision(int d, const double *L, double *P, const int32_t *need) {
+    const int k = blockIdx.z, i0 = blockIdx.y * PT, j0 = blockIdx.x * PT;
+    if (j0 > i0) return;
+    if (need && !need[k]) return;
     const double *Lk = L + (size_t)k * d * d;
-    __shared__ double As[16][65], Bs[16][65];
+    __shared__ double As[16][PT + 1], Bs[16][PT + 1];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    double acc[4][4] = {};
-    const int jmax = min(d, j0 + 64);  // P_ij = sum_{l <= min(i,j)} L_il L_jl
+    double acc[2][2] = {};
+    const int jmax = min(d, j0 + PT);  // P_ij = sum_{l <= min(i,j)} L_il L_jl
     for (int l0 = 0; l0 < jmax; l0 += 16) {
-        for (int e = tid; e < 16 * 64; e += 256) {
+        for (int e = tid; e < 16 * PT; e += 256) {
             const int r = e >> 4, kk = e & 15, l = l0 + kk;
             const int i = i0 + r, j = j0 + r;
             As[kk][r] = (i < d && l < d && l <= i) ? Lk[(size_t)i * d + l] : 0.0;
@@ -237,29 +242,39 @@ __global__ void __launch_bounds__(256) k_precision(int d, const double *L, doubl
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
-            double av[4], bv[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tx + 16 * c];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+            const double a0 = As[kk][ty], a1 = As[kk][ty + 16];
+            const double b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+            acc[0][0] = fma(a0, b0, acc[0][0]);
+            acc[0][1] = fma(a0, b1, acc[0][1]);
+            acc[1][0] = fma(a1, b0, acc[1][0]);
+            acc[1][1] = fma(a1, b1, acc[1][1]);
         }
         __syncthreads();
     }
     double *Pk = P + (size_t)k * d * d;
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 2; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < 2; ++c) {
             const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
             if (i < d && j < d) {
                 Pk[(size_t)i * d + j] = acc[r][c];
                 Pk[(size_t)j * d + i] = acc[r][c];
             }
         }
+}
+
+// Components whose P_k the Hessians are about to read: r_ck != 0 at some live
+// candidate and P_k not formed yet (the Hessian skips r == 0 terms, so the
+// other P_k are never read). Marks them formed.
+__global__ void k_precision_need(int K, const double *R, const int32_t *n_c, int32_t *done, int32_t *need) {
+    const int k = threadIdx.x;
+    if (k >= K) return;
+    bool any = false;
+    for (int c = 0; c < *n_c; ++c) any = any || R[(size_t)c * K + k] != 0.0;
+    const bool nk = any && !done[k];
+    need[k] = nk ? 1 : 0;
+    if (nk) done[k] = 1;
 }
 
 // ------------------------------------------------------------------ per-component gradients
@@ -764,9 +779,18 @@ void launch_gather_rows(int d, int cap, const double *X, const int32_t *idx, con
 }
 
 void launch_precision(int d, int K, const double *L, double *P, cudaStream_t s) {
-    dim3 g((d + 63) / 64, (d + 63) / 64, K);
+    dim3 g((d + PT - 1) / PT, (d + PT - 1) / PT, K);
     note_launch();
-    k_precision<<<g, 256, 0, s>>>(d, L, P);
+    k_precision<<<g, 256, 0, s>>>(d, L, P, nullptr);
+}
+
+void launch_precision_needed(int d, int K, const double *L, const double *R, const int32_t *n_c, int32_t *done,
+                             int32_t *need, double *P, cudaStream_t s) {
+    note_launch();
+    k_precision_need<<<1, kMaxK, 0, s>>>(K, R, n_c, done, need);
+    dim3 g((d + PT - 1) / PT, (d + PT - 1) / PT, K);
+    note_launch();
+    k_precision<<<g, 256, 0, s>>>(d, L, P, need);
 }
 
 void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P, const double *Z, const double *R,

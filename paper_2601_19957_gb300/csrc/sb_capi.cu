@@ -152,6 +152,7 @@ struct LaplaceWs {
     double *dd_l;
     int32_t *dd_i;
     uint32_t *dd_bar;
+    int32_t *p_done, *p_need;  // [K] P_k formed / to form now
 };
 
 struct EvidenceWs {
@@ -251,6 +252,8 @@ Layout layout(void *base, const sb_problem *p, const sb_config *c) {
     la.dd_l = cv.take<double>(2 * kDedupMaxGrid);
     la.dd_i = cv.take<int32_t>(2 * kDedupMaxGrid);
     la.dd_bar = cv.take<uint32_t>(2);
+    la.p_done = cv.take<int32_t>(kMaxK);
+    la.p_need = cv.take<int32_t>(kMaxK);
     la.XC = cv.take<double>((size_t)cap * d);
     la.LC = cv.take<double>(cap);
     la.GC = cv.take<double>((size_t)cap * d);
@@ -502,7 +505,7 @@ sb_status run_laplace(const ProbView &pv, const sb_config *c, const Layout &L, c
                       int32_t *n_modes, double *logZ, cudaStream_t s) {
     const int d = pv.d, K = pv.K, cap = c->cand_cap;
     const auto &la = L.la;
-    launch_precision(d, K, pv.L, la.P, s);
+    SB_CUDA_TRY(cudaMemsetAsync(la.p_done, 0, sizeof(int32_t) * kMaxK, s));
     const DedupScratch dds{la.dd_l, la.dd_i, la.dd_bar, pv.status};
     launch_dedup(n, d, x, ell, status, nullptr, c->dedup_coarse, pv.wmax, cap, la.reps, la.n_reps, la.assigned, dds,
                  s);
@@ -511,6 +514,7 @@ sb_status run_laplace(const ProbView &pv, const sb_config *c, const Layout &L, c
     // l, grad l, H and its Cholesky factor at every candidate
     auto eval_full = [&]() {
         f64_points(pv, la.XC, nullptr, la.n_reps, cap, la.qpart, la.Z, la.R, la.LC, la.GC, s);
+        launch_precision_needed(d, K, pv.L, la.R, la.n_reps, la.p_done, la.p_need, la.P, s);
         launch_hessian_chol(d, K, cap, pv.L, la.P, la.Z, la.R, la.GC, la.n_reps, la.GK, la.H, la.info, s);
     };
     eval_full();

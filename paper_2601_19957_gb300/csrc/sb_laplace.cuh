@@ -20,6 +20,10 @@ void launch_dedup(int n, int d, const double *X, const double *ell, const int8_t
 void launch_gather_rows(int d, int cap, const double *X, const int32_t *idx, const int32_t *n_idx, double *out,
                         const double *ell, double *ell_out, cudaStream_t s);
 void launch_precision(int d, int K, const double *L, double *P, cudaStream_t s);
+// P_k only for the components with r != 0 at some live candidate that are not
+// formed yet (done[K] is cleared by the caller before the first call).
+void launch_precision_needed(int d, int K, const double *L, const double *R, const int32_t *n_c, int32_t *done,
+                             int32_t *need, double *P, cudaStream_t s);
 void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P, const double *Z, const double *R,
                          const double *gbar, const int32_t *n_c, double *GK, double *H, int32_t *info,
                          cudaStream_t s);
