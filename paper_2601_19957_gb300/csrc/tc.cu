@@ -187,15 +187,20 @@ __device__ __forceinline__ int chunk_component(const TileInfo &ti, int q) {
 }
 
 template <int MODE, int BN, int KC>
-__device__ __forceinline__ TileInfo decode_tile(int t, int d, int K, const uint32_t *rflag, const int *glist) {
+__device__ __forceinline__ TileInfo decode_tile(int t, int d, int K, const uint32_t *rflag, const int *glist,
+                                                int n_mblk) {
     TileInfo ti;
     const int nct = (d + BN - 1) / BN;
     if (glist) t = glist[t / nct] * nct + t % nct;  // compacted store-pass schedule
     ti.kmask = 0;
     ti.skip = false;
     if (MODE == MODE_G) {
-        ti.nt = t % nct;
-        ti.mb = t / nct;
+        // single tiles, widest K range first (column tile nct - 1 of every row
+        // block, then nct - 2, ...), dealt round-robin: the costly tiles start
+        // first and the short ones fill in, and small row counts still spread
+        // over every SM
+        ti.nt = nct - 1 - t / n_mblk;
+        ti.mb = t % n_mblk;
         ti.k = 0;
         const int jmax = min(d, (ti.nt + 1) * BN);
         ti.c_lo = 0;
@@ -221,12 +226,13 @@ __device__ __forceinline__ TileInfo decode_tile(int t, int d, int K, const uint3
     return ti;
 }
 
-// Tile sequence of one CTA: whole groups (every column tile of one row block,
-// and component for GEMM1), groups dealt round-robin. Column tiles differ in
-// their number of K chunks (the triangle), so dealing single tiles round-robin
-// with a grid that is a multiple of the tile count per group would give each
-// CTA the same column tile over and over; whole groups carry equal work and
-// reuse their A rows inside the CTA.
+// Tile sequence of one CTA: groups of gsz consecutive tile indices dealt
+// round-robin. GEMM1 groups are whole (row block, component) pairs — every
+// column tile, whose K ranges differ (the triangle), so single tiles dealt with
+// a grid that is a multiple of the tile count per group would give each CTA the
+// same column tile over and over; whole groups carry equal work and reuse their
+// A rows inside the CTA. GEMM2 deals single tiles in decreasing cost order
+// (see decode_tile).
 __device__ __forceinline__ int tile_of(int i, int nct) {
     return (blockIdx.x + (i / nct) * gridDim.x) * nct + (i % nct);
 }
@@ -291,6 +297,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         n_tiles = *s_gcount * nct;
     }
     const int *glist = compact ? s_glist : nullptr;
+    const int gsz = (MODE == MODE_G) ? 1 : nct;  // tiles per scheduling group
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -323,8 +330,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             int inflight_stage[8];
             uint32_t inflight_phase[8];
             int n_inflight = 0;
-            for (int it = 0, t = tile_of(0, nct); t < n_tiles && !*s_abort; t = tile_of(++it, nct)) {
-                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag, glist);
+            for (int it = 0, t = tile_of(0, gsz); t < n_tiles && !*s_abort; t = tile_of(++it, gsz)) {
+                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag, glist, n_mblk);
                 if (ti.skip) continue;
                 bool ok = true;
                 for (int q = 0; q < ti.nchunks; ++q) {
@@ -371,8 +378,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             int acc = 0;
             uint32_t acc_phase = 0;
             bool issued = false;
-            for (int it = 0, t = tile_of(0, nct); t < n_tiles && !*s_abort; t = tile_of(++it, nct)) {
-                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag, glist);
+            for (int it = 0, t = tile_of(0, gsz); t < n_tiles && !*s_abort; t = tile_of(++it, gsz)) {
+                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag, glist, n_mblk);
                 if (ti.skip) continue;
                 if (!bwait(&tempty[acc], acc_phase ^ 1, s_abort)) break;
                 tc_fence_after();
@@ -418,8 +425,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         const int r = quad * 32 + lane;
         int acc = 0;
         uint32_t acc_phase = 0;
-        for (int it = 0, t = tile_of(0, nct); t < n_tiles && !warp_aborted(s_abort); t = tile_of(++it, nct)) {
-            const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag, glist);
+        for (int it = 0, t = tile_of(0, gsz); t < n_tiles && !warp_aborted(s_abort); t = tile_of(++it, gsz)) {
+            const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag, glist, n_mblk);
             if (ti.skip) continue;
             if (!warp_bwait(&tfull[acc], acc_phase, s_abort)) break;
             tc_fence_after();
@@ -764,7 +771,7 @@ void launch_gemm(const CUtensorMap &mapA, const CUtensorMap &map, const TcArgs &
         cudaFuncSetAttribute(k_tc_gemm<BN, PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM);
     });
     const int mb = (a.n_rows_max + BM - 1) / BM;
-    const long long groups = (long long)mb * (MODE == MODE_G ? 1 : a.K);
+    const long long groups = (long long)mb * (MODE == MODE_G ? (a.d + BN - 1) / BN : a.K);
     int grid = num_sms();
     if (groups < grid) grid = (int)(groups > 0 ? groups : 1);
     ProfScope prof(a.prof >= 0 ? a.prof
