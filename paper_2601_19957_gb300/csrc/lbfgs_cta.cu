@@ -24,8 +24,10 @@
 //
 // A walker's step is a chain of dependent phases (reductions, the m x m
 // solve), so the SM is kept busy by several walkers at once: CT threads per
-// walker, each thread owning the float4 groups at coordinates 4 (t + q CT),
-// q < 1024 / (4 CT).
+// walker, thread t owning the float4 groups at coordinates 4 (t + q CT),
+// q < VPT = 1024 / (4 CT).
+#include <cuda_bf16.h>
+
 #include "sb_lbfgs.cuh"
 
 namespace sb {
@@ -73,7 +75,7 @@ __device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.
 // Per-thread asynchronous copies global -> shared (16 bytes, L2 only). A thread
 // only ever reads back the chunks it copied itself, so completing its own
 // groups (cp.async.wait_group) is all the synchronisation the ring needs.
-__device__ __forceinline__ void cp_async16(float4 *dst, const float *src) {
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
                  "l"(src)
                  : "memory");
@@ -83,16 +85,41 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                  : "memory");
 }
+// History storage of the stored pairs: FP32, or bf16 (half the bytes of the
+// stream that bounds the step). Inner products and S^T Y / Y^T Y are formed
+// from the stored (rounded) vectors, so the direction applies the exact
+// L-BFGS matrix of the pairs as stored.
+__device__ __forceinline__ float4 round_bf16(float4 v) {
+    return make_float4(__bfloat162float(__float2bfloat16_rn(v.x)), __bfloat162float(__float2bfloat16_rn(v.y)),
+                       __bfloat162float(__float2bfloat16_rn(v.z)), __bfloat162float(__float2bfloat16_rn(v.w)));
+}
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+__device__ __forceinline__ float4 unpack4(uint32_t lo, uint32_t hi) {
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&lo);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&hi);
+    return make_float4(__low2float(a), __high2float(a), __low2float(b), __high2float(b));
+}
+
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// A vector of d coordinates as this thread's VPT float4 groups.
-template <int CT>
+// A vector of d coordinates as this thread's VPT float4 groups. Mapping M = 0
+// (FP32 pairs): group q of thread t holds coordinates 4 (t + q CT) .. +3, so one
+// 16-byte access instruction of a warp covers a contiguous 512-byte stretch.
+// M = 1 (bf16 pairs): thread t holds the 4 VPT consecutive coordinates from
+// 4 VPT t, so its share of a bf16 row is one 16-byte chunk and a warp's copy
+// instruction covers 512 contiguous bytes.
+template <int CT, int M>
 struct Vec {
     float4 v[Cfg<CT>::VPT];
-    __device__ __forceinline__ static int i0(int q) { return 4 * ((int)threadIdx.x + q * CT); }
+    __device__ __forceinline__ static int i0(int q) {
+        return M ? 4 * (Cfg<CT>::VPT * (int)threadIdx.x + q) : 4 * ((int)threadIdx.x + q * CT);
+    }
     __device__ __forceinline__ void load(const float *p, int d) {
 #pragma unroll
         for (int q = 0; q < Cfg<CT>::VPT; ++q) v[q] = ld4(p, i0(q), d);
@@ -106,45 +133,45 @@ struct Vec {
         for (int q = 0; q < Cfg<CT>::VPT; ++q) v[q] = zero4();
     }
 };
-template <int CT>
-__device__ __forceinline__ float dotv(const Vec<CT> &a, const Vec<CT> &b) {
+template <int CT, int M>
+__device__ __forceinline__ float dotv(const Vec<CT, M> &a, const Vec<CT, M> &b) {
     float s = 0.f;
 #pragma unroll
     for (int q = 0; q < Cfg<CT>::VPT; ++q) s += dot4(a.v[q], b.v[q]);
     return s;
 }
 // y += c x
-template <int CT>
-__device__ __forceinline__ void axpyv(float c, const Vec<CT> &x, Vec<CT> &y) {
+template <int CT, int M>
+__device__ __forceinline__ void axpyv(float c, const Vec<CT, M> &x, Vec<CT, M> &y) {
 #pragma unroll
     for (int q = 0; q < Cfg<CT>::VPT; ++q) y.v[q] = axpy4(c, x.v[q], y.v[q]);
 }
 // a + c b
-template <int CT>
-__device__ __forceinline__ Vec<CT> lincomb(const Vec<CT> &a, float c, const Vec<CT> &b) {
-    Vec<CT> r;
+template <int CT, int M>
+__device__ __forceinline__ Vec<CT, M> lincomb(const Vec<CT, M> &a, float c, const Vec<CT, M> &b) {
+    Vec<CT, M> r;
 #pragma unroll
     for (int q = 0; q < Cfg<CT>::VPT; ++q) r.v[q] = axpy4(c, b.v[q], a.v[q]);
     return r;
 }
-template <int CT>
-__device__ __forceinline__ Vec<CT> subv(const Vec<CT> &a, const Vec<CT> &b) {
-    Vec<CT> r;
+template <int CT, int M>
+__device__ __forceinline__ Vec<CT, M> subv(const Vec<CT, M> &a, const Vec<CT, M> &b) {
+    Vec<CT, M> r;
 #pragma unroll
     for (int q = 0; q < Cfg<CT>::VPT; ++q)
         r.v[q] = make_float4(a.v[q].x - b.v[q].x, a.v[q].y - b.v[q].y, a.v[q].z - b.v[q].z, a.v[q].w - b.v[q].w);
     return r;
 }
-template <int CT>
-__device__ __forceinline__ bool finitev(const Vec<CT> &a) {
+template <int CT, int M>
+__device__ __forceinline__ bool finitev(const Vec<CT, M> &a) {
     bool f = true;
 #pragma unroll
     for (int q = 0; q < Cfg<CT>::VPT; ++q)
         f = f && isfinite(a.v[q].x) && isfinite(a.v[q].y) && isfinite(a.v[q].z) && isfinite(a.v[q].w);
     return f;
 }
-template <int CT>
-__device__ __forceinline__ float absmaxv(const Vec<CT> &a) {
+template <int CT, int M>
+__device__ __forceinline__ float absmaxv(const Vec<CT, M> &a) {
     float m = 0.f;
 #pragma unroll
     for (int q = 0; q < Cfg<CT>::VPT; ++q)
@@ -357,35 +384,84 @@ __device__ __forceinline__ void solve_mm(Shared<CT> &sh, int c) {
     }
 }
 
+// Stores this thread's coordinates of a history vector (already rounded to HT).
+template <int CT, int M, typename HT>
+__device__ __forceinline__ void store_hist(const Vec<CT, M> &v, HT *row, int d) {
+    if (sizeof(HT) == 4) {
+        v.store(reinterpret_cast<float *>(row), d);
+    } else {  // mapping 1: 8 consecutive coordinates, one 16-byte chunk
+        const int e0 = Vec<CT, M>::i0(0);
+        if ((d & 7) == 0 && e0 + 7 < d) {
+            *reinterpret_cast<uint4 *>(row + e0) = make_uint4(pack2(v.v[0].x, v.v[0].y), pack2(v.v[0].z, v.v[0].w),
+                                                              pack2(v.v[1].x, v.v[1].y), pack2(v.v[1].z, v.v[1].w));
+        } else {
+            const float f[8] = {v.v[0].x, v.v[0].y, v.v[0].z, v.v[0].w, v.v[1].x, v.v[1].y, v.v[1].z, v.v[1].w};
+            __nv_bfloat16 *r = reinterpret_cast<__nv_bfloat16 *>(row);
+            for (int e = 0; e < 8 && e0 + e < d; ++e) r[e0 + e] = __float2bfloat16_rn(f[e]);
+        }
+    }
+}
+
 // Direction for walker state st (count pairs from ring slot head). When
 // new_slot >= 0 the pair in that slot was stored this visit (it is the newest,
 // logical index count - 1) and its row and column of S^T Y, Y^T Y come from the
 // same pass. Writes P and the unit trial X + P; updates st.dphi / alpha / bt
 // and possibly resets the history (steepest descent when p is not a descent
 // direction). Returns the algorithmic bytes moved.
-template <int CT>
+template <int CT, typename HT, int MAP = (sizeof(HT) == 2)>
 __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<float> &st, int new_slot,
-                              const Vec<CT> &g, const Vec<CT> &x, const Vec<CT> &s_new, const Vec<CT> &y_new,
+                              const Vec<CT, MAP> &g, const Vec<CT, MAP> &x, const Vec<CT, MAP> &s_new, const Vec<CT, MAP> &y_new,
                               float *MSY, float *MYY, Shared<CT> &sh, int &par) {
     constexpr int PG = Cfg<CT>::PG;
     const int d = a.d, m = a.m;
     const int count = st.count;
     uint64_t bytes = 0;
-    Vec<CT> p;
+    Vec<CT, MAP> p;
     p.zero();
     if (count > 0) {
-        const float *S = a.S + (size_t)w * m * d;
-        const float *Y = a.Y + (size_t)w * m * d;
+        const HT *S = reinterpret_cast<const HT *>(a.S) + (size_t)w * m * d;
+        const HT *Y = reinterpret_cast<const HT *>(a.Y) + (size_t)w * m * d;
         if (threadIdx.x < count) sh.slot_of[threadIdx.x] = (st.head + threadIdx.x) % m;
         __syncthreads();
         // Both passes stream the pairs through the shared-memory ring, DEPTH groups
         // of PG pairs in flight per thread (cp.async); pass 2's first groups are
         // issued before the m x m solve, which does not need them.
-        constexpr int D = Cfg<CT>::DEPTH, VPT = Cfg<CT>::VPT;
+        constexpr int VPT = Cfg<CT>::VPT;
+        // bf16 chunks are half the size: twice the groups in flight in the same ring
+        constexpr int D = sizeof(HT) == 2 ? 2 * Cfg<CT>::DEPTH : Cfg<CT>::DEPTH;
         const int ngroups = (count + PG - 1) / PG;
         const bool vec_ok = (d & 3) == 0;
-        auto rp = [&](int grp, int q, int v, int j) -> float4 * {
-            return sh.ring + ((((size_t)(grp % D) * PG + q) * 2 + v) * VPT + j) * CT + threadIdx.x;
+        constexpr bool BF = sizeof(HT) == 2;
+        static_assert(!BF || VPT == 2, "bf16 history: two groups of 4 (8 bytes each) per thread");
+        constexpr int U4 = BF ? VPT / 2 : VPT;  // 16-byte ring chunks per stored vector per thread
+        auto rp = [&](int grp, int q, int v, int j) -> uint4 * {
+            return reinterpret_cast<uint4 *>(sh.ring) + ((((size_t)(grp % D) * PG + q) * 2 + v) * U4 + j) * CT +
+                   threadIdx.x;
+        };
+        // this thread's chunks of one stored vector into the ring (cp.async, or
+        // plain copies for a ragged end of the row)
+        auto issue_vec = [&](int grp, int q, int v, const HT *row) {
+#pragma unroll
+            for (int j = 0; j < U4; ++j) {
+                if (BF) {
+                    const int e0 = Vec<CT, MAP>::i0(0);  // 8 consecutive elements
+                    if ((d & 7) == 0 && e0 + 7 < d) {
+                        cp_async16(rp(grp, q, v, j), row + e0);
+                    } else {
+                        HT *dst = reinterpret_cast<HT *>(rp(grp, q, v, j));
+                        for (int e = 0; e < 8 && e0 + e < d; ++e) dst[e] = row[e0 + e];
+                    }
+                } else {
+                    const int i0 = Vec<CT, MAP>::i0(j);
+                    if (vec_ok && i0 + 3 < d) {
+                        cp_async16(rp(grp, q, v, j), row + i0);
+                    } else {
+                        for (int e = 0; e < 4 && i0 + e < d; ++e)
+                            cp_async4(reinterpret_cast<float *>(rp(grp, q, v, j)) + e,
+                                      reinterpret_cast<const float *>(row) + i0 + e);
+                    }
+                }
+            }
         };
         auto issue = [&](int grp) {  // always commits one group (possibly empty)
             if (grp < ngroups) {
@@ -394,36 +470,38 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
                     const int i = grp * PG + q;
                     if (i >= count) break;
                     const size_t row = (size_t)sh.slot_of[i] * d;
-#pragma unroll
-                    for (int j = 0; j < VPT; ++j) {
-                        const int i0 = Vec<CT>::i0(j);
-                        if (vec_ok && i0 + 3 < d) {
-                            cp_async16(rp(grp, q, 0, j), S + row + i0);
-                            cp_async16(rp(grp, q, 1, j), Y + row + i0);
-                        } else {
-                            for (int e = 0; e < 4 && i0 + e < d; ++e) {
-                                cp_async4(reinterpret_cast<float *>(rp(grp, q, 0, j)) + e, S + row + i0 + e);
-                                cp_async4(reinterpret_cast<float *>(rp(grp, q, 1, j)) + e, Y + row + i0 + e);
-                            }
-                        }
-                    }
+                    issue_vec(grp, q, 0, S + row);
+                    issue_vec(grp, q, 1, Y + row);
                 }
             }
             cp_async_commit();
         };
-        auto fetch = [&](int grp, int q, Vec<CT> &sv, Vec<CT> &yv) {  // this thread's chunks of one pair
+        auto fetch = [&](int grp, int q, Vec<CT, MAP> &sv, Vec<CT, MAP> &yv) {  // this thread's chunks of one pair
+            if (BF) {
+                const uint4 a4 = *rp(grp, q, 0, 0), b4 = *rp(grp, q, 1, 0);
+                sv.v[0] = unpack4(a4.x, a4.y);
+                sv.v[1] = unpack4(a4.z, a4.w);
+                yv.v[0] = unpack4(b4.x, b4.y);
+                yv.v[1] = unpack4(b4.z, b4.w);
+            } else {
+#pragma unroll
+                for (int j = 0; j < VPT; ++j) {
+                    const uint4 a4 = *rp(grp, q, 0, j), b4 = *rp(grp, q, 1, j);
+                    sv.v[j] = make_float4(__uint_as_float(a4.x), __uint_as_float(a4.y), __uint_as_float(a4.z),
+                                          __uint_as_float(a4.w));
+                    yv.v[j] = make_float4(__uint_as_float(b4.x), __uint_as_float(b4.y), __uint_as_float(b4.z),
+                                          __uint_as_float(b4.w));
+                }
+            }
 #pragma unroll
             for (int j = 0; j < VPT; ++j) {
-                const int i0 = Vec<CT>::i0(j);
-                float4 a4 = *rp(grp, q, 0, j), b4 = *rp(grp, q, 1, j);
+                const int i0 = Vec<CT, MAP>::i0(j);
                 if (!(i0 + 3 < d)) {  // ragged tail: lanes past d hold stale data
-                    if (i0 + 0 >= d) a4.x = b4.x = 0.f;
-                    if (i0 + 1 >= d) a4.y = b4.y = 0.f;
-                    if (i0 + 2 >= d) a4.z = b4.z = 0.f;
-                    if (i0 + 3 >= d) a4.w = b4.w = 0.f;
+                    if (i0 + 0 >= d) sv.v[j].x = yv.v[j].x = 0.f;
+                    if (i0 + 1 >= d) sv.v[j].y = yv.v[j].y = 0.f;
+                    if (i0 + 2 >= d) sv.v[j].z = yv.v[j].z = 0.f;
+                    if (i0 + 3 >= d) sv.v[j].w = yv.v[j].w = 0.f;
                 }
-                sv.v[j] = a4;
-                yv.v[j] = b4;
             }
         };
         // pass 1: inner products, PG pairs per reduction
@@ -435,7 +513,7 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
             float v[5 * PG];
 #pragma unroll
             for (int q = 0; q < PG; ++q) {
-                Vec<CT> s4, y4;
+                Vec<CT, MAP> s4, y4;
                 if (i + q < count) {
                     fetch(grp, q, s4, y4);
                 } else {
@@ -478,7 +556,7 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
             for (int q = 0; q < PG; ++q) {
                 const int i = grp * PG + q;
                 if (i < count) {
-                    Vec<CT> s4, y4;
+                    Vec<CT, MAP> s4, y4;
                     fetch(grp, q, s4, y4);
                     axpyv(-sh.ca[i], s4, p);
                     axpyv(gam * sh.cw[i], y4, p);
@@ -488,7 +566,7 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
         }
         cp_async_wait<0>();  // (only empty groups remain) the ring is free for the next walker
         // the two-loop recursion's history traffic: each pair read in both passes
-        bytes += (uint64_t)16 * count * d;
+        bytes += (uint64_t)4 * count * d * sizeof(HT);
     }
     float dp[1];
     if (count > 0) {
@@ -518,9 +596,10 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
 // Algorithmic bytes of the L-BFGS step launches (added only while counting is on).
 __device__ unsigned long long g_lbfgs_bytes;
 
-template <int CT>
+template <int CT, typename HT>
 __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float> a, float *MSY, float *MYY,
                                                                 int count_bytes) {
+    constexpr int MAP = sizeof(HT) == 2;  // coordinate mapping (see Vec)
     __shared__ Shared<CT> sh;
     extern __shared__ __align__(16) float4 dyn[];  // [RING_F4] ring, then R, YY [m][ld]
     const int d = a.d, m = a.m;
@@ -540,7 +619,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
         const float ft = a.FT[w];
         float *X = a.X + (size_t)w * d;
         float *G = a.G + (size_t)w * d;
-        Vec<CT> x, g, xt, gt;
+        Vec<CT, MAP> x, g, xt, gt;
         x.load(X, d);
         g.load(G, d);
         xt.load(a.XT + (size_t)w * d, d);
@@ -548,14 +627,21 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
         bytes += (uint64_t)16 * d + 4 + 2 * sizeof(WalkerState<float>);
         // finiteness of the trial gradient, the candidate pair's inner products and
         // max |grad| at the trial, all in one reduction
-        const Vec<CT> s4 = subv(xt, x), y4 = subv(gt, g);
+        Vec<CT, MAP> s4 = subv(xt, x), y4 = subv(gt, g);
+        if (sizeof(HT) == 2) {  // the pair as it will be stored
+#pragma unroll
+            for (int q = 0; q < Cfg<CT>::VPT; ++q) {
+                s4.v[q] = round_bf16(s4.v[q]);
+                y4.v[q] = round_bf16(y4.v[q]);
+            }
+        }
         float r4[4] = {finitev(gt) ? 0.f : 1.f, dotv(s4, s4), dotv(y4, y4), dotv(s4, y4)};
         float gm = absmaxv(gt);
         block_sum_max<CT, 4>(r4, gm, sh.red2[par++ & 1]);
         const bool finite = isfinite(ft) && r4[0] == 0.f;
         bool newiter = false;
         int new_slot = -1;
-        Vec<CT> s_new, y_new;
+        Vec<CT, MAP> s_new, y_new;
         s_new.zero();
         y_new.zero();
         if (st.phase == 0) {
@@ -580,10 +666,10 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                     slot = st.head;
                     st.head = (st.head + 1) % m;
                 }
-                s4.store(a.S + ((size_t)w * m + slot) * d, d);
-                y4.store(a.Y + ((size_t)w * m + slot) * d, d);
+                store_hist<CT, MAP, HT>(s4, reinterpret_cast<HT *>(a.S) + ((size_t)w * m + slot) * d, d);
+                store_hist<CT, MAP, HT>(y4, reinterpret_cast<HT *>(a.Y) + ((size_t)w * m + slot) * d, d);
                 if (threadIdx.x == 0) a.rho[(size_t)w * m + slot] = 1.f / r4[3];
-                bytes += (uint64_t)8 * d + 4;
+                bytes += (uint64_t)2 * d * sizeof(HT) + 4;
                 new_slot = slot;
                 s_new = s4;
                 y_new = y4;
@@ -601,7 +687,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
             ++st.bt;
             if (st.bt <= a.max_backtracks) {
                 st.alpha *= a.backtrack;
-                Vec<CT> p;
+                Vec<CT, MAP> p;
                 p.load(a.P + (size_t)w * d, d);
                 lincomb(x, st.alpha, p).store(a.XT + (size_t)w * d, d);
                 bytes += (uint64_t)8 * d;
@@ -609,7 +695,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                 st.count = 0;
                 st.head = 0;
                 st.attempt = 1;
-                bytes += direction<CT>(a, w, st, -1, g, x, s_new, y_new, MSY, MYY, sh, par);
+                bytes += direction<CT, HT>(a, w, st, -1, g, x, s_new, y_new, MSY, MYY, sh, par);
             } else {
                 st.status = SB_WALKER_STALLED;
             }
@@ -623,7 +709,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                 st.status = SB_WALKER_MAXITER;
             } else {
                 st.attempt = 0;
-                bytes += direction<CT>(a, w, st, new_slot, g, x, s_new, y_new, MSY, MYY, sh, par);
+                bytes += direction<CT, HT>(a, w, st, new_slot, g, x, s_new, y_new, MSY, MYY, sh, par);
             }
         }
         if (threadIdx.x == 0) a.st[w] = st;
@@ -634,7 +720,8 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
 
 }  // namespace
 
-void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *MYY, int num_sms, cudaStream_t s) {
+void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *MYY, int num_sms, bool bf16_history,
+                           cudaStream_t s) {
     ProfScope prof(PROF_LBFGS_STEP, s);
     const int count_bytes = prof_enabled() ? 1 : 0;
     int grid = num_sms * Cfg<kCT>::MINB;
@@ -643,11 +730,16 @@ void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *
     static bool attr = false;
     if (!attr) {
         const size_t most = (size_t)Cfg<kCT>::RING_F4 * sizeof(float4) + 2 * sizeof(float) * kMaxM * mm_ld(kMaxM);
-        cudaFuncSetAttribute(k_lbfgs_cta<kCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+        cudaFuncSetAttribute(k_lbfgs_cta<kCT, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+        cudaFuncSetAttribute(k_lbfgs_cta<kCT, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)most);
         attr = true;
     }
     note_launch();
-    k_lbfgs_cta<kCT><<<grid, kCT, dyn, s>>>(a, MSY, MYY, count_bytes);
+    if (bf16_history)
+        k_lbfgs_cta<kCT, __nv_bfloat16><<<grid, kCT, dyn, s>>>(a, MSY, MYY, count_bytes);
+    else
+        k_lbfgs_cta<kCT, float><<<grid, kCT, dyn, s>>>(a, MSY, MYY, count_bytes);
 }
 
 double lbfgs_bytes_take() {

@@ -390,6 +390,10 @@ int device_sms() {
     return n;
 }
 
+// Storage of the mixed path's L-BFGS pairs: bf16 (the step is bound by the
+// history stream; the FP64 Newton polish fixes the final accuracy).
+constexpr bool kBf16History = true;
+
 template <typename T>
 void step_round(const RefineWs<T> &r, const LbfgsArgs<T> &a, int n, cudaStream_t s);
 template <>
@@ -398,8 +402,8 @@ void step_round<double>(const RefineWs<double> &, const LbfgsArgs<double> &a, in
 }
 template <>
 void step_round<float>(const RefineWs<float> &r, const LbfgsArgs<float> &a, int n, cudaStream_t s) {
-    // compact form, CTA per walker, FP32 history (bf16 history measured slower)
-    launch_lbfgs_step_cta(a, n, r.MSY, r.MYY, device_sms(), s);
+    // compact form, CTA per walker
+    launch_lbfgs_step_cta(a, n, r.MSY, r.MYY, device_sms(), kBf16History, s);
 }
 
 template <typename T>

@@ -40,7 +40,8 @@ template <typename T>
 void launch_lbfgs_compact(const LbfgsArgs<T> &a, int64_t *n_evals, cudaStream_t s);
 // FP32 step, one CTA per walker, compact-representation direction (lbfgs_cta.cu).
 // With d % 4 == 0 and a.err set, the stored pairs are streamed by bulk copies.
-void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *MYY, int num_sms, cudaStream_t s);
+void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *MYY, int num_sms, bool bf16_history,
+                           cudaStream_t s);
 // Algorithmic bytes moved by the FP32 step launches while profiling was on
 // (synchronises the device, then clears the counter); -1 on a CUDA error.
 double lbfgs_bytes_take();
