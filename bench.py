@@ -25,6 +25,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes per algorithmic byte of the L-BFGS step with bf16 pairs, measured
+# with ncu over all step launches of one solve at d=1024, K=8, 8192 walkers
+# (9.20 + 41.24 GB DRAM for 72 x 1.205 GB algorithmic): the second pass of the
+# two-loop recursion is mostly served by L2.
+LBFGS_DRAM_PER_ALGORITHMIC_BYTE = 0.581
+
 METRIC = "logL+grad evals/sec and evidence solves/sec at d=1024 K=8 vs plain FP64 GPU; |ΔlogZ|"
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
 
@@ -281,10 +287,13 @@ def main():
                 "peak_source": peak_src + (" bf16 burst" if cfg.prec == 2 else " bf16 burst / 2 (tf32 nominal ratio)")}
     else:
         achieved = lb_bytes / (lb_ms / 1e3) / 1e9
+        per_launch = lb_bytes / max(int(prof_n[3]), 1)
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": None, "kernel": "k_lbfgs_cta (FP32 L-BFGS step)", "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": lb_bytes / max(int(prof_n[3]), 1),
-                "ms_per_launch": lb_ms / max(int(prof_n[3]), 1)}
+                "traffic": per_launch * LBFGS_DRAM_PER_ALGORITHMIC_BYTE if cfg.prec == 2 else None,
+                "traffic_source": "DRAM bytes of all 72 step launches of one 8192-walker solve (ncu), as a "
+                                  "fraction of their algorithmic bytes, times this run's algorithmic bytes",
+                "kernel": "k_lbfgs_cta (FP32 L-BFGS step, bf16 pairs)", "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": per_launch, "ms_per_launch": lb_ms / max(int(prof_n[3]), 1)}
 
     res = {
         "metric": METRIC,
