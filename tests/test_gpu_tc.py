@@ -78,3 +78,22 @@ def test_tc_far_points_values(prec):
     X = np.random.default_rng(3).uniform(-10, 10, (200, 64))
     wl, _ = _check(inst, X, prec)
     assert wl < 16.0
+
+
+@pytest.mark.parametrize("prec", [sb.PREC_BF16, sb.PREC_TF32])
+def test_tc_gradient_overlapping_and_mixed_blocks(prec):
+    """Overlapping components put several non-zero responsibilities in one row,
+    so the store pass and the gradient GEMM visit several components of a row
+    block; rows near a single mode are interleaved with them, so one 128-row
+    block mixes shared and exactly-zero responsibilities, and a block of rows
+    near one mode only (rows 256..383) leaves the other components unvisited."""
+    inst = make_instance(96, 3, 77, s_range=(0.4, 0.6), mean_box=(-0.5, 0.5), sep=0.5)
+    rng = np.random.default_rng(5)
+    n = 400
+    between = (inst.mu[0] + inst.mu[1] + inst.mu[2]) / 3.0 + rng.normal(0, 0.2, (n, inst.d))
+    near = inst.mu[rng.integers(0, 3, n)] + rng.normal(0, 0.05, (n, inst.d))
+    X = np.where((np.arange(n) % 2 == 0)[:, None], between, near)
+    X[256:384] = inst.mu[1] + rng.normal(0, 0.05, (128, inst.d))
+    wl, wg = _check(inst, X, prec)
+    assert wl < 16.0, wl
+    assert wg < 16.0, wg
