@@ -340,42 +340,50 @@ __global__ void k_lbfgs_init(int n, int d, const double *starts, T *XT, WalkerSt
 // Ordered in-place compaction of the active list; counts the evaluations of the round.
 // Chunk b0 writes positions < b0 + 1024 only after all of its reads, and later
 // chunks read positions >= b0 + 1024, so the compaction can run in place.
+// Stable in-place compaction of the active list, one CTA of 1024 threads over
+// chunks of 1024 entries: a ballot per warp, one warp scans the 32 warp counts
+// with shuffles, two barriers per chunk. Writes never pass the chunk being
+// read (output position <= input position).
 template <typename T>
 __global__ void __launch_bounds__(1024) k_lbfgs_compact(const WalkerState<T> *st, int32_t *act, int32_t *n_act,
                                                         int64_t *n_evals) {
     __shared__ int warp_off[32];
-    __shared__ int s_base, s_tot;
+    __shared__ int s_base[2];
     const int prev = *n_act;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
-        s_base = 0;
+        s_base[0] = 0;
         if (n_evals) *n_evals += prev;
     }
     __syncthreads();
-    for (int b0 = 0; b0 < prev; b0 += 1024) {
+    int par = 0;
+    for (int b0 = 0; b0 < prev; b0 += 1024, par ^= 1) {
         const int nidx = b0 + threadIdx.x;
         const int w = nidx < prev ? act[nidx] : -1;
         const int keep = (w >= 0) && st[w].status == SB_WALKER_RUNNING;
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (lane == 0) warp_off[wid] = __popc(bal);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int s = 0;
-            for (int q = 0; q < 32; ++q) {
-                const int t = warp_off[q];
-                warp_off[q] = s;
-                s += t;
+        const int base = s_base[par];
+        if (wid == 0) {
+            const int c = warp_off[lane];
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
-            s_tot = s;
+            warp_off[lane] = incl - c;  // exclusive offsets of the warps
+            if (lane == 31) s_base[par ^ 1] = base + incl;
         }
         __syncthreads();
-        const int pos = s_base + warp_off[wid] + __popc(bal & ((1u << lane) - 1u));
+        const int pos = base + warp_off[wid] + __popc(bal & ((1u << lane) - 1u));
         if (keep) act[pos] = w;
-        __syncthreads();
-        if (threadIdx.x == 0) s_base += s_tot;
-        __syncthreads();
+        // warp_off is rewritten only after the next chunk's first barrier, which
+        // every thread reaches after this read; s_base alternates between two slots
     }
-    if (threadIdx.x == 0) *n_act = s_base;
+    __syncthreads();
+    if (threadIdx.x == 0) *n_act = s_base[par];
 }
 
 template <typename T>
