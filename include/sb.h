@@ -159,8 +159,9 @@ sb_status sb_refine(const sb_problem *prob, const sb_config *cfg, const double *
  * sum_i log C_ii (H = C C^T), log Z = LSE_k log Z_k - log V.
  * status may be NULL (all walkers eligible). modes: [cap][d]; logZk, ell_modes:
  * [cap] (ell_modes may be NULL); n_modes: int32 device scalar; logZ: device scalar.
- * Modes are ordered by decreasing l. Asynchronous; zero modes give logZ = -inf
- * and set SB_ERR_NO_MODES in the status word.
+ * Modes are ordered by decreasing l. Synchronises `stream` once (the host reads
+ * the number of coarse candidates to size the candidate kernels' grids); zero
+ * modes give logZ = -inf and set SB_ERR_NO_MODES in the status word.
  */
 sb_status sb_laplace(const sb_problem *prob, const sb_config *cfg, const double *x, const double *ell,
                      const int8_t *status, int32_t n, double *modes, double *logZk, double *ell_modes, int32_t cap,

@@ -514,31 +514,39 @@ sb_status run_laplace(const ProbView &pv, const sb_config *c, const Layout &L, c
     launch_dedup(n, d, x, ell, status, nullptr, c->dedup_coarse, pv.wmax, cap, la.reps, la.n_reps, la.assigned, dds,
                  s);
     launch_gather_rows(d, cap, x, la.reps, la.n_reps, la.XC, ell, la.LC, s);
-    SB_CUDA_TRY(cudaMemsetAsync(la.active, 1, cap, s));
+    // The candidate kernels below take one CTA (or a grid slice) per candidate;
+    // sizing their grids by the live count instead of cand_cap spares launching
+    // and retiring the idle blocks (most of a launch when two candidates of 256
+    // remain). The kernels still read the count on the device.
+    int32_t h_reps = 0;
+    SB_CUDA_TRY(cudaMemcpyAsync(&h_reps, la.n_reps, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SB_CUDA_TRY(cudaStreamSynchronize(s));
+    const int nc = h_reps < 1 ? 1 : (h_reps > cap ? cap : h_reps);
+    SB_CUDA_TRY(cudaMemsetAsync(la.active, 1, nc, s));
     // l, grad l, H and its Cholesky factor at every candidate
     auto eval_full = [&]() {
-        f64_points(pv, la.XC, nullptr, la.n_reps, cap, la.qpart, la.Z, la.R, la.LC, la.GC, s);
+        f64_points(pv, la.XC, nullptr, la.n_reps, nc, la.qpart, la.Z, la.R, la.LC, la.GC, s);
         launch_precision_needed(d, K, pv.L, la.R, la.n_reps, la.p_done, la.p_need, la.P, s);
-        launch_hessian_chol(d, K, cap, pv.L, la.P, la.Z, la.R, la.GC, la.n_reps, la.GK, la.H, la.info, s);
+        launch_hessian_chol(d, K, nc, pv.L, la.P, la.Z, la.R, la.GC, la.n_reps, la.GK, la.H, la.info, s);
     };
     eval_full();
     for (int step = 0; step < c->newton_steps; ++step) {
-        launch_chol_solve(d, cap, la.H, la.GC, la.n_reps, la.info, la.active, la.delta, la.pred, s);
-        launch_newton_ls(d, cap, 0, la.n_reps, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
+        launch_chol_solve(d, nc, la.H, la.GC, la.n_reps, la.info, la.active, la.delta, la.pred, s);
+        launch_newton_ls(d, nc, 0, la.n_reps, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
                          la.delta, la.XN, la.LN, la.pred, s);
-        f64_points(pv, la.XN, nullptr, la.n_reps, cap, la.qpart, nullptr, nullptr, la.LN, nullptr, s);
-        launch_newton_ls(d, cap, 1, la.n_reps, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
+        f64_points(pv, la.XN, nullptr, la.n_reps, nc, la.qpart, nullptr, nullptr, la.LN, nullptr, s);
+        launch_newton_ls(d, nc, 1, la.n_reps, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
                          la.delta, la.XN, la.LN, la.pred, s);
-        launch_ls_batch_setup(d, cap, la.n_reps, la.searching, la.XC, la.delta, la.XN2, la.rows2, la.n_rows2, s);
-        f64_points(pv, la.XN2, la.rows2, la.n_rows2, cap * (kHalvings - 1), la.qpart2, nullptr, nullptr, la.LN2,
+        launch_ls_batch_setup(d, nc, la.n_reps, la.searching, la.XC, la.delta, la.XN2, la.rows2, la.n_rows2, s);
+        f64_points(pv, la.XN2, la.rows2, la.n_rows2, nc * (kHalvings - 1), la.qpart2, nullptr, nullptr, la.LN2,
                    nullptr, s);
-        launch_ls_batch_decide(d, cap, la.n_reps, la.searching, la.active, la.XC, la.LC, la.XN2, la.LN2, s);
+        launch_ls_batch_decide(d, nc, la.n_reps, la.searching, la.active, la.XC, la.LC, la.XN2, la.LN2, s);
         eval_full();
     }
     SB_CUDA_TRY(cudaMemsetAsync(la.keep, 0, cap, s));
-    launch_cand_stats(d, cap, la.XC, la.LC, la.GC, la.H, la.info, pv.lo, pv.hi, c->eps_grad, la.n_reps, la.keep,
+    launch_cand_stats(d, nc, la.XC, la.LC, la.GC, la.H, la.info, pv.lo, pv.hi, c->eps_grad, la.n_reps, la.keep,
                       la.logZk_c, s);
-    launch_dedup(cap, d, la.XC, la.LC, nullptr, la.keep, c->dedup_tol, pv.wmax, cap, la.reps2, la.n_reps2,
+    launch_dedup(nc, d, la.XC, la.LC, nullptr, la.keep, c->dedup_tol, pv.wmax, cap, la.reps2, la.n_reps2,
                  la.assigned, dds, s);
     launch_laplace_final(d, la.XC, la.LC, la.logZk_c, la.n_reps, la.reps2, la.n_reps2, pv.logV, cap_out, modes, logZk,
                          ell_modes, n_modes, logZ, pv.status, s);
