@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sb", choices=["sb", "reference"])
     ap.add_argument("--workload", type=int, default=4)
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the forward solve and the d log Z / d (mu, L) adjoint (one JSON line)")
     ap.add_argument("--prec", default="bf16", choices=list(PREC))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -191,6 +193,8 @@ def main():
         return run_batched(sb, args)
     if args.workload == 2:
         return run_precision(sb, args)
+    if args.adjoint:
+        return run_adjoint(sb, args)
     inst, cfg = workload_cfg(args.workload, args.prec, args.scale)
     prob = sb.Problem(inst)
     c = sb.make_config(cfg)
@@ -337,6 +341,38 @@ def main():
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_adjoint(sb, args):
+    """Forward log Z and the hand-written adjoint d log Z / d mu_k, d log Z / d L_k
+    (FP64, H recomputed at each mode) on the d=1024, K=8 workload."""
+    import torch
+
+    inst, cfg = workload_cfg(args.workload, args.prec, args.scale)
+    prob = sb.Problem(inst)
+    c = sb.make_config(cfg)
+    wsp = sb.workspace(prob, c)
+    out = sb.evidence(prob, c, ws=wsp)
+    for _ in range(max(args.warmup, 1)):
+        sb.evidence_backward(prob, out.modes, out.logZk, out.n_modes)
+    torch.cuda.synchronize()
+    reps = max(args.steps, 1)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        dmu, dL = sb.evidence_backward(prob, out.modes, out.logZk, out.n_modes)
+    torch.cuda.synchronize()
+    dt_b = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        out = sb.evidence(prob, c, ws=wsp)
+    torch.cuda.synchronize()
+    dt_f = (time.perf_counter() - t0) / reps
+    d, K, nm = inst.d, inst.K, out.n_modes
+    print(json.dumps({"case": "adjoint", "workload": f"d={d} K={K}, {cfg.n_starts} starts, m={cfg.m}",
+                      "n_modes": nm, "ms_forward": dt_f * 1e3, "ms_backward": dt_b * 1e3,
+                      "backward_fp64_flop_model": 2.0 * nm * d ** 3,
+                      "max_abs_dmu": float(dmu.abs().max()), "max_abs_dL": float(dL.abs().max())}))
+    return 0
 
 
 def run_precision(sb, args):
