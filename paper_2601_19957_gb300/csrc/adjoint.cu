@@ -36,108 +36,110 @@ namespace {
 constexpr int TB = 32;  // triangular-solve row block
 
 // ------------------------------------------------------------------ blocked TRSM, row-major B [d][n]
-// Lower: X = C^-1 B.  Update of row block I: B_I -= C[I][0:I] X[0:I] (all columns).
-__global__ void __launch_bounds__(256) k_trsm_update(int d, int n, int I, bool upper, const double *C, double *B) {
-    // tile: 32 rows of block I x 64 columns
+// Right-looking: once row block I of X is solved, every later row block J takes
+// its update B_J -= A_JI X_I in one launch over (J, 64-column tile), so a launch
+// has up to (row blocks left) x n / 64 CTAs. Lower (X = C^-1 B): A_JI = C_JI for
+// J > I. Upper (X = C^-T B, row blocks in reverse): A_JI = (C_IJ)^T for J < I.
+__global__ void __launch_bounds__(256) k_trsm_right(int d, int n, int I, bool upper, const double *C, double *B) {
     const int c0 = blockIdx.x * 64;
-    const int r0 = I * TB;
-    __shared__ double Cs[TB][TB + 1];
+    const int J = upper ? (int)blockIdx.y : I + 1 + (int)blockIdx.y;
+    const int rJ = J * TB, rI = I * TB;
+    __shared__ double As[TB][TB + 1];
     __shared__ double Xs[TB][64 + 1];
-    const int tid = threadIdx.x, tc = tid & 63, tr = tid >> 6;  // 4 row groups x 64 cols
+    const int tid = threadIdx.x, tc = tid & 63, tr = tid >> 6;  // 4 row groups x 64 columns
+    for (int e = tid; e < TB * TB; e += 256) {
+        const int i = e / TB, k = e % TB;
+        const int gi = rJ + i, gk = rI + k;
+        double v = 0.0;
+        if (gi < d && gk < d) v = upper ? C[(size_t)gk * d + gi] : C[(size_t)gi * d + gk];
+        As[i][k] = v;
+    }
+    for (int e = tid; e < TB * 64; e += 256) {
+        const int k = e / 64, c = e % 64;
+        const int gk = rI + k, gc = c0 + c;
+        Xs[k][c] = (gk < d && gc < n) ? B[(size_t)gk * n + gc] : 0.0;
+    }
+    __syncthreads();
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const int nb = (d + TB - 1) / TB;
-    const int kb_lo = upper ? I + 1 : 0, kb_hi = upper ? nb : I;
-    for (int kb = kb_lo; kb < kb_hi; ++kb) {
-        const int k0 = kb * TB;
-        for (int e = tid; e < TB * TB; e += 256) {
-            const int i = e / TB, k = e % TB;
-            const int gi = r0 + i, gk = k0 + k;
-            double v = 0.0;
-            if (gi < d && gk < d) v = upper ? C[(size_t)gk * d + gi] : C[(size_t)gi * d + gk];  // (C^T)_ik = C_ki
-            Cs[i][k] = v;
-        }
-        for (int e = tid; e < TB * 64; e += 256) {
-            const int k = e / 64, c = e % 64;
-            const int gk = k0 + k, gc = c0 + c;
-            Xs[k][c] = (gk < d && gc < n) ? B[(size_t)gk * n + gc] : 0.0;
-        }
-        __syncthreads();
 #pragma unroll
-        for (int k = 0; k < TB; ++k) {
-            const double x = Xs[k][tc];
+    for (int k = 0; k < TB; ++k) {
+        const double x = Xs[k][tc];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) acc[q] = fma(Cs[tr + 4 * q][k], x, acc[q]);
-        }
-        __syncthreads();
+        for (int q = 0; q < 8; ++q) acc[q] = fma(As[tr + 4 * q][k], x, acc[q]);
     }
     const int gc = c0 + tc;
     if (gc < n)
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int gi = r0 + tr + 4 * q;
+            const int gi = rJ + tr + 4 * q;
             if (gi < d) B[(size_t)gi * n + gc] -= acc[q];
         }
 }
 
-// Diagonal block solve for all columns: thread per column.
+// Diagonal block solve for 32 columns per CTA: the 32 x 32 block of B is staged
+// in shared memory, each warp solves four columns with lanes over rows (one
+// shuffle per unknown, multiplication by the diagonal's reciprocals).
 __global__ void __launch_bounds__(256) k_trsm_diag(int d, int n, int I, bool upper, const double *C, double *B) {
     __shared__ double Cs[TB][TB + 1];
-    const int r0 = I * TB;
+    __shared__ double Bs[TB][TB + 1];
+    __shared__ double inv[TB];
+    const int r0 = I * TB, c0 = blockIdx.x * TB;
+    const int rows = min(TB, d - r0);
     for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
         const int i = e / TB, k = e % TB;
         const int gi = r0 + i, gk = r0 + k;
         double v = (i == k) ? 1.0 : 0.0;
         if (gi < d && gk < d) v = upper ? C[(size_t)gk * d + gi] : C[(size_t)gi * d + gk];
         Cs[i][k] = v;
+        Bs[i][k] = (i < rows && c0 + k < n) ? B[(size_t)(r0 + i) * n + c0 + k] : 0.0;
     }
     __syncthreads();
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= n) return;
-    const int rows = min(TB, d - r0);
-    double x[TB];
-#pragma unroll
-    for (int i = 0; i < TB; ++i) x[i] = i < rows ? B[(size_t)(r0 + i) * n + col] : 0.0;
-    if (!upper) {
-#pragma unroll
-        for (int i = 0; i < TB; ++i) {
-            double s = x[i];
-#pragma unroll
-            for (int k = 0; k < i; ++k) s -= Cs[i][k] * x[k];
-            x[i] = s / Cs[i][i];
+    if (threadIdx.x < TB) inv[threadIdx.x] = 1.0 / Cs[threadIdx.x][threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int col = wid; col < TB; col += (int)(blockDim.x >> 5)) {
+        double b = Bs[lane][col];
+        if (!upper) {
+            for (int i = 0; i < TB; ++i) {
+                const double xi = __shfl_sync(0xffffffffu, b, i) * inv[i];
+                if (lane == i) b = xi;
+                else if (lane > i) b -= Cs[lane][i] * xi;
+            }
+        } else {
+            for (int i = TB - 1; i >= 0; --i) {
+                const double xi = __shfl_sync(0xffffffffu, b, i) * inv[i];
+                if (lane == i) b = xi;
+                else if (lane < i) b -= Cs[lane][i] * xi;
+            }
         }
-    } else {
-#pragma unroll
-        for (int i = TB - 1; i >= 0; --i) {
-            double s = x[i];
-#pragma unroll
-            for (int k = i + 1; k < TB; ++k) s -= Cs[i][k] * x[k];
-            x[i] = s / Cs[i][i];
-        }
+        Bs[lane][col] = b;
     }
-#pragma unroll
-    for (int i = 0; i < TB; ++i)
-        if (i < rows) B[(size_t)(r0 + i) * n + col] = x[i];
+    __syncthreads();
+    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+        const int i = e / TB, k = e % TB;
+        if (i < rows && c0 + k < n) B[(size_t)(r0 + i) * n + c0 + k] = Bs[i][k];
+    }
 }
 
 // W B = C^-T C^-1 B in place (B row-major [d][n]).
 void apply_W(int d, int n, const double *C, double *B, cudaStream_t s) {
     const int nb = (d + TB - 1) / TB;
-    const int gu = (n + 63) / 64, gd = (n + 255) / 256;
+    const int gc = (n + 63) / 64, gd = (n + TB - 1) / TB;
     for (int I = 0; I < nb; ++I) {
-        if (I > 0) {
-            note_launch();
-            k_trsm_update<<<gu, 256, 0, s>>>(d, n, I, false, C, B);
-        }
         note_launch();
         k_trsm_diag<<<gd, 256, 0, s>>>(d, n, I, false, C, B);
-    }
-    for (int I = nb - 1; I >= 0; --I) {
         if (I < nb - 1) {
             note_launch();
-            k_trsm_update<<<gu, 256, 0, s>>>(d, n, I, true, C, B);
+            k_trsm_right<<<dim3(gc, nb - 1 - I), 256, 0, s>>>(d, n, I, false, C, B);
         }
+    }
+    for (int I = nb - 1; I >= 0; --I) {
         note_launch();
         k_trsm_diag<<<gd, 256, 0, s>>>(d, n, I, true, C, B);
+        if (I > 0) {
+            note_launch();
+            k_trsm_right<<<dim3(gc, I), 256, 0, s>>>(d, n, I, true, C, B);
+        }
     }
 }
 
