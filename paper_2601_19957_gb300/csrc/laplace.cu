@@ -64,7 +64,7 @@ __device__ bool grid_barrier(uint32_t *bar, uint32_t n_blocks, int32_t *err) {
                     atomicOr(err, SB_DEV_TIMEOUT);
                     break;
                 }
-                __nanosleep(256);
+                if (it > 4096) __nanosleep(128);  // spin first: most waits are a few microseconds
             }
         }
         __threadfence();
@@ -468,99 +468,122 @@ __global__ void __launch_bounds__(256) k_syrk_update(int d, int kb, double *H, c
     }
 }
 
-// Solve (C C^T) delta = g for each candidate still polishing: one CTA per
-// candidate, blocked by 32 rows. Forward: y_I = C_II^-1 (g_I - C_I,<I y_<I);
-// backward: delta_I = C_II^-T (y_I - sum_{J>I} C_JI^T delta_J). The off-diagonal
-// products read whole rows of C (coalesced); the 32 x 32 diagonal solves run on
-// one warp with shuffles.
-__global__ void __launch_bounds__(256) k_chol_solve(int d, const double *H, const double *g, const int32_t *n_c,
-                                                    const int32_t *info, const uint8_t *active, double *delta,
-                                                    double *pred) {
-    const int c = blockIdx.x;
-    if (c >= *n_c || info[c] || !active[c]) return;
-    extern __shared__ double y[];  // [d] right-hand side / solution, then [d] 1 / C_ii
-    double *dinv = y + d;
-    __shared__ double part[8][33];
+// Solve (C C^T) delta = g for each candidate still polishing and the model
+// increase g^T delta / 2: Gc CTAs per candidate (cooperative launch,
+// one bounded grid barrier per 32-row block and direction). CTA (c, q) owns the
+// row blocks J with J % Gc == q. Forward (C y = g): in step I the owner of block
+// I (already updated by every earlier step, by itself) solves the diagonal block
+// and publishes y_I; after the barrier every owner subtracts C_JI y_I from its
+// blocks J > I. The owner of block I + 1 has then finished block I + 1's last
+// update before it solves it in step I + 1, so one barrier per step suffices.
+// Backward (C^T delta = y) mirrors it with (C^T)_JI = (C_IJ)^T for J < I.
+// The right-hand side lives in delta[c] (global, read past L1 after barriers).
+constexpr int CS_THREADS = 256;
+__global__ void __launch_bounds__(CS_THREADS) k_chol_solve_coop(int d, int Gc, const double *H, const double *g,
+                                                                const int32_t *n_c, const int32_t *info,
+                                                                const uint8_t *active, double *delta, double *pred,
+                                                                uint32_t *bar, int32_t *err) {
     __shared__ double Dg[32][33];
-    const double *C = H + (size_t)c * d * d;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // the reciprocals of the diagonal, all at once: the substitutions below then
-    // have multiplications, not divisions, on their sequential path
-    for (int i = threadIdx.x; i < d; i += blockDim.x) {
-        y[i] = g[(size_t)c * d + i];
-        dinv[i] = 1.0 / C[(size_t)i * d + i];
-    }
-    __syncthreads();
+    __shared__ double dinv[32];
+    __shared__ double xs[32];
+    __shared__ double part[8];
+    const int c = blockIdx.x / Gc, q = blockIdx.x % Gc;
+    const bool live = c < *n_c && !info[c] && active[c];
     const int nb = (d + 31) / 32;
-    // forward substitution
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const double *C = H + (size_t)c * d * d;
+    double *y = delta + (size_t)c * d;
+    if (live)
+        for (int J = q; J < nb; J += Gc)
+            for (int i = J * 32 + (int)threadIdx.x; i < min(d, J * 32 + 32); i += CS_THREADS) y[i] = g[(size_t)c * d + i];
+    __syncthreads();
+    // the owner's diagonal solve of block I (lower: forward; upper: with C^T)
+    auto diag = [&](int I, bool upper) {
+        const int r0 = I * 32, rows = min(32, d - r0);
+        for (int e = threadIdx.x; e < 32 * 32; e += CS_THREADS) {
+            const int i = e / 32, j = e % 32;
+            Dg[i][j] = (i < rows && j < rows) ? C[(size_t)(r0 + i) * d + r0 + j] : (i == j ? 1.0 : 0.0);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) dinv[threadIdx.x] = 1.0 / Dg[threadIdx.x][threadIdx.x];
+        __syncthreads();
+        if (wid == 0) {
+            double v = lane < rows ? __ldcg(y + r0 + lane) : 0.0;
+            if (!upper) {
+                for (int i = 0; i < 32; ++i) {
+                    const double yi = __shfl_sync(0xffffffffu, v, i) * dinv[i];
+                    if (lane == i) v = yi;
+                    if (lane > i) v -= Dg[lane][i] * yi;
+                }
+            } else {
+                for (int i = 31; i >= 0; --i) {
+                    const double xi = __shfl_sync(0xffffffffu, v, i) * dinv[i];
+                    if (lane == i) v = xi;
+                    if (lane < i) v -= Dg[i][lane] * xi;
+                }
+            }
+            if (lane < rows) y[r0 + lane] = v;
+        }
+        __threadfence();
+        __syncthreads();
+    };
+    // forward
     for (int I = 0; I < nb; ++I) {
+        if (live && I % Gc == q) diag(I, false);
+        if (!grid_barrier(bar, gridDim.x, err)) return;
+        if (!live) continue;
         const int r0 = I * 32, rows = min(32, d - r0);
-        // rhs of block I minus C[I][0:r0] y[0:r0]: warp w handles rows r0 + w, r0 + w + 8, ...
-        for (int rr = wid; rr < rows; rr += 8) {
-            const double *Crow = C + (size_t)(r0 + rr) * d;
-            double sacc = 0.0;
-            for (int j = lane; j < r0; j += 32) sacc += Crow[j] * y[j];
-            sacc = warp_sum(sacc);
-            if (lane == 0) part[0][rr] = sacc;
-        }
-        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-            const int i = e / 32, j = e % 32;
-            Dg[i][j] = (i < rows && j < rows) ? C[(size_t)(r0 + i) * d + r0 + j] : (i == j ? 1.0 : 0.0);
-        }
+        if (threadIdx.x < 32) xs[threadIdx.x] = threadIdx.x < rows ? __ldcg(y + r0 + threadIdx.x) : 0.0;
         __syncthreads();
-        if (wid == 0) {
-            double v = lane < rows ? y[r0 + lane] - part[0][lane] : 0.0;
-            for (int i = 0; i < 32; ++i) {
-                const double yi = __shfl_sync(0xffffffffu, v, i) * (i < rows ? dinv[r0 + i] : 1.0);
-                if (lane == i) v = yi;
-                if (lane > i) v -= Dg[lane][i] * yi;
+        // y_J -= C_JI y_I for owned J > I: warp per output row
+        for (int J = I + 1; J < nb; ++J) {
+            if (J % Gc != q) continue;
+            const int j0 = J * 32, jr = min(32, d - j0);
+            for (int rr = wid; rr < jr; rr += CS_THREADS / 32) {
+                const double a = lane < rows ? C[(size_t)(j0 + rr) * d + r0 + lane] * xs[lane] : 0.0;
+                const double sum = warp_sum(a);
+                if (lane == 0) y[j0 + rr] -= sum;
             }
-            if (lane < rows) y[r0 + lane] = v;
         }
         __syncthreads();
     }
-    // backward substitution with C^T
+    // backward
     for (int I = nb - 1; I >= 0; --I) {
+        if (live && I % Gc == q) diag(I, true);
+        if (!grid_barrier(bar, gridDim.x, err)) return;
+        if (!live) continue;
         const int r0 = I * 32, rows = min(32, d - r0);
-        // sum_{J > I} C[j][r0 + i] delta[j]: threads over (i, j-slices); column block of C rows below
-        {
-            const int i = lane;  // column r0 + i
-            double sacc = 0.0;
-            if (i < rows)
-                for (int j = r0 + 32 + wid; j < d; j += 8) sacc += C[(size_t)j * d + r0 + i] * y[j];
-            part[wid][i] = sacc;
-        }
-        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-            const int i = e / 32, j = e % 32;
-            Dg[i][j] = (i < rows && j < rows) ? C[(size_t)(r0 + i) * d + r0 + j] : (i == j ? 1.0 : 0.0);
-        }
+        if (threadIdx.x < 32) xs[threadIdx.x] = threadIdx.x < rows ? __ldcg(y + r0 + threadIdx.x) : 0.0;
         __syncthreads();
-        if (wid == 0) {
-            double sacc = 0.0;
-            for (int q = 0; q < 8; ++q) sacc += part[q][lane];
-            double v = lane < rows ? y[r0 + lane] - sacc : 0.0;
-            // C_II^T x = v: upper-triangular (C^T)_{ij} = C_{ji}; back substitution
-            for (int i = 31; i >= 0; --i) {
-                const double xi = __shfl_sync(0xffffffffu, v, i) * (i < rows ? dinv[r0 + i] : 1.0);
-                if (lane == i) v = xi;
-                if (lane < i) v -= Dg[i][lane] * xi;
+        // y_J -= (C_IJ)^T x_I for owned J < I: thread per output column j (coalesced rows of C)
+        for (int J = 0; J < I; ++J) {
+            if (J % Gc != q) continue;
+            const int j0 = J * 32;
+            // 8 warps split the 32 rows of block I; lane = column j
+            double a = 0.0;
+            for (int i = wid; i < rows; i += CS_THREADS / 32) a += C[(size_t)(r0 + i) * d + j0 + lane] * xs[i];
+            __shared__ double red[8][33];
+            red[wid][lane] = a;
+            __syncthreads();
+            if (wid == 0) {
+                double t = 0.0;
+                for (int w = 0; w < CS_THREADS / 32; ++w) t += red[w][lane];
+                y[j0 + lane] -= t;
             }
-            if (lane < rows) y[r0 + lane] = v;
+            __syncthreads();
         }
-        __syncthreads();
     }
-    // model increase of l along the Newton step: g^T delta / 2
+    if (!grid_barrier(bar, gridDim.x, err)) return;
+    // model increase of l along the Newton step: g^T delta / 2 (first CTA of the candidate)
+    if (!live || q != 0) return;
     double gd = 0.0;
-    for (int i = threadIdx.x; i < d; i += blockDim.x) {
-        delta[(size_t)c * d + i] = y[i];
-        gd += g[(size_t)c * d + i] * y[i];
-    }
+    for (int i = threadIdx.x; i < d; i += CS_THREADS) gd += g[(size_t)c * d + i] * __ldcg(y + i);
     gd = warp_sum(gd);
-    if (lane == 0) part[0][wid] = gd;
+    if (lane == 0) part[wid] = gd;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int q = 0; q < 8; ++q) t += part[0][q];
+        for (int w = 0; w < CS_THREADS / 32; ++w) t += part[w];
         pred[c] = 0.5 * t;
     }
 }
@@ -817,10 +840,18 @@ void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P
     }
 }
 
-void launch_chol_solve(int d, int cap, const double *H, const double *g, const int32_t *n_c, const int32_t *info,
-                       const uint8_t *active, double *delta, double *pred, cudaStream_t s) {
+void launch_chol_solve_coop(int d, int nc, const double *H, const double *g, const int32_t *n_c, const int32_t *info,
+                            const uint8_t *active, double *delta, double *pred, uint32_t *bar, int32_t *err,
+                            cudaStream_t s) {
+    // CTAs per candidate: enough to spread the updates, few enough for one wave
+    int Gc = 144 / (nc > 0 ? nc : 1);
+    if (Gc > 16) Gc = 16;
+    if (Gc < 1) Gc = 1;
+    int G = nc * Gc;
+    cudaMemsetAsync(bar, 0, 2 * sizeof(uint32_t), s);
+    void *args[] = {&d, &Gc, &H, &g, &n_c, &info, &active, &delta, &pred, &bar, &err};
     note_launch();
-    k_chol_solve<<<cap, 256, 2 * sizeof(double) * d, s>>>(d, H, g, n_c, info, active, delta, pred);
+    cudaLaunchCooperativeKernel((const void *)k_chol_solve_coop, dim3(G), dim3(CS_THREADS), args, 0, s);
 }
 
 void launch_newton_ls(int d, int cap, int mode, const int32_t *n_c, const int32_t *info, uint8_t *active,

@@ -531,7 +531,8 @@ sb_status run_laplace(const ProbView &pv, const sb_config *c, const Layout &L, c
     };
     eval_full();
     for (int step = 0; step < c->newton_steps; ++step) {
-        launch_chol_solve(d, nc, la.H, la.GC, la.n_reps, la.info, la.active, la.delta, la.pred, s);
+        launch_chol_solve_coop(d, nc, la.H, la.GC, la.n_reps, la.info, la.active, la.delta, la.pred, la.dd_bar,
+                               pv.status, s);
         launch_newton_ls(d, nc, 0, la.n_reps, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
                          la.delta, la.XN, la.LN, la.pred, s);
         f64_points(pv, la.XN, nullptr, la.n_reps, nc, la.qpart, nullptr, nullptr, la.LN, nullptr, s);

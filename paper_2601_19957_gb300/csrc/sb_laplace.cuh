@@ -27,8 +27,12 @@ void launch_precision_needed(int d, int K, const double *L, const double *R, con
 void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P, const double *Z, const double *R,
                          const double *gbar, const int32_t *n_c, double *GK, double *H, int32_t *info,
                          cudaStream_t s);
-void launch_chol_solve(int d, int cap, const double *H, const double *g, const int32_t *n_c, const int32_t *info,
-                       const uint8_t *active, double *delta, double *pred, cudaStream_t s);
+// Newton step (C C^T) delta = g and g^T delta / 2 for the live candidates, over
+// nc * Gc co-resident CTAs (cooperative launch, one bounded grid barrier per
+// 32-row block and direction); nc = live candidates (host).
+void launch_chol_solve_coop(int d, int nc, const double *H, const double *g, const int32_t *n_c, const int32_t *info,
+                            const uint8_t *active, double *delta, double *pred, uint32_t *bar, int32_t *err,
+                            cudaStream_t s);
 void launch_newton_ls(int d, int cap, int mode, const int32_t *n_c, const int32_t *info, uint8_t *active,
                       uint8_t *searching, int32_t *halvings, double *t, double *XC, double *LC, const double *delta,
                       double *XN, const double *LN, const double *pred, cudaStream_t s);
