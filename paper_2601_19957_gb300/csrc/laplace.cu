@@ -328,10 +328,12 @@ __global__ void __launch_bounds__(256) k_hessian(int d, int K, const double *P, 
 }
 
 // ------------------------------------------------------------------ blocked Cholesky
-// Diagonal block factor, 256 threads. Per column j one thread takes
-// r = 1/sqrt(a_jj) (the only serial FP64 work of the step), the column below is
-// multiplied by r, and the trailing lower triangle (m (m + 1) / 2 entries,
-// m = 31 - j) is updated with each thread taking at most two entries.
+// Diagonal block factor, 256 threads, one barrier per column. Step j updates the
+// trailing lower triangle with the unscaled pivot column, a_ik -= a_ij a_kj / a_jj
+// (= L_ij L_kj), every thread taking 1 / a_jj itself; column j is final after
+// step j (later steps touch only columns > j), so the columns are scaled by
+// 1 / sqrt(a_jj) once at the end. A pivot <= 0 (not positive definite) stops
+// every thread at the same step.
 constexpr int DIAG_THREADS = 256;
 __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(int d, int kb, double *H, const int32_t *n_c,
                                                              int32_t *info) {
@@ -339,30 +341,20 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(int d, int kb, doub
     if (c >= *n_c || info[c]) return;
     double *A = H + (size_t)c * d * d;
     __shared__ double a[NB][NB + 1];
-    __shared__ double s_r;
-    __shared__ int bad;
     const int o = kb * NB;
     for (int e = threadIdx.x; e < NB * NB; e += DIAG_THREADS) {
         const int i = e / NB, j = e % NB;
         a[i][j] = (o + i < d && o + j < d) ? A[(size_t)(o + i) * d + o + j] : (i == j ? 1.0 : 0.0);  // identity padding
     }
-    if (threadIdx.x == 0) bad = 0;
     __syncthreads();
+    bool bad = false;
     for (int j = 0; j < NB; ++j) {
-        if (threadIdx.x == 0) {
-            const double p = a[j][j];
-            if (!(p > 0.0)) {
-                bad = 1;
-            } else {
-                const double r = rsqrt(p);
-                s_r = r;
-                a[j][j] = p * r;
-            }
+        const double p = a[j][j];
+        if (!(p > 0.0)) {
+            bad = true;
+            break;
         }
-        __syncthreads();
-        if (bad) break;
-        if (threadIdx.x > j && threadIdx.x < NB) a[threadIdx.x][j] *= s_r;
-        __syncthreads();
+        const double ip = 1.0 / p;
         const int m = NB - 1 - j;
         for (int e = threadIdx.x; e < m * (m + 1) / 2; e += DIAG_THREADS) {
             // e -> (ii >= kk) in the packed lower triangle of the trailing block
@@ -371,7 +363,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(int d, int kb, doub
             while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
             const int kk = e - ii * (ii + 1) / 2;
             const int i = j + 1 + ii, k = j + 1 + kk;
-            a[i][k] -= a[i][j] * a[k][j];
+            a[i][k] -= a[i][j] * a[k][j] * ip;
         }
         __syncthreads();
     }
@@ -381,7 +373,10 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(int d, int kb, doub
     }
     for (int e = threadIdx.x; e < NB * NB; e += DIAG_THREADS) {
         const int i = e / NB, j = e % NB;
-        if (o + i < d && o + j < d && j <= i) A[(size_t)(o + i) * d + o + j] = a[i][j];
+        if (o + i < d && o + j < d && j <= i) {
+            const double r = rsqrt(a[j][j]);
+            A[(size_t)(o + i) * d + o + j] = i == j ? a[j][j] * r : a[i][j] * r;
+        }
     }
 }
 
