@@ -202,26 +202,10 @@ __device__ __forceinline__ void block_sum(float (&v)[NV], float *sh) {
     }
 }
 
-// Reduce 32 per-lane values over the warp with 31 shuffles (recursive halving:
-// at each level a lane keeps one half of its values and adds its partner's
-// copy of that half). Lane j returns the warp total of value j.
-__device__ __forceinline__ float warp_transpose_sum(float (&v)[32]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int j = 0; j < o; ++j) {
-            const float send = up ? v[j] : v[j + o];
-            const float keep = up ? v[j + o] : v[j];
-            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-    }
-    return v[0];
-}
-
-// The same over 16 values with 16 shuffles: halving within each half-warp,
-// then one exchange between the halves. Lanes j and j + 16 return value j.
+// Reduce 16 per-lane values over the warp with 16 shuffles (recursive halving
+// within each half-warp: at each level a lane keeps one half of its values and
+// adds its partner's copy of that half; then one exchange between the halves).
+// Lanes j and j + 16 return the warp total of value j.
 __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -235,31 +219,6 @@ __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16]) {
         }
     }
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
-}
-
-// Sums over the CTA of NV <= 32 per-thread values; thread t < NV returns
-// total t (the others return garbage). One barrier, alternating scratch as block_sum.
-template <int CT, int NV>
-__device__ __forceinline__ float block_sum_scatter(const float (&in)[NV], float *sh) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (NV <= 16) {
-        float v[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = j < NV ? in[j] : 0.f;
-        const float t = warp_transpose_sum16(v);
-        if (lane < 16) sh[wid * 32 + lane] = t;
-    } else {
-        float v[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = j < NV ? in[j] : 0.f;
-        sh[wid * 32 + lane] = warp_transpose_sum(v);
-    }
-    __syncthreads();
-    float t = 0.f;
-    if (threadIdx.x < NV)
-#pragma unroll
-        for (int q = 0; q < Cfg<CT>::NW; ++q) t += sh[q * 32 + threadIdx.x];
-    return t;
 }
 
 // NV sums and one maximum over the CTA with a single barrier; every thread gets all.
@@ -292,6 +251,14 @@ __device__ __forceinline__ void block_sum_max(float (&v)[NV], float &mx, float *
 // Odd row stride of the m x m matrices: their rows and their columns are both
 // free of shared-memory bank conflicts.
 __host__ __device__ __forceinline__ int mm_ld(int m) { return (m & 1) ? m + 2 : m + 1; }
+// Floats of the dynamic area after the ring: S^T Y and Y^T Y, which also hold
+// pass 1's per-warp partial sums before they are staged.
+template <int CT>
+__host__ __device__ __forceinline__ int mm_floats(int m) {
+    const int mats = 2 * m * mm_ld(m);
+    const int p1 = (m + Cfg<CT>::PG - 1) / Cfg<CT>::PG * Cfg<CT>::NW * 5 * Cfg<CT>::PG;
+    return mats > p1 ? mats : p1;
+}
 
 template <int CT>
 struct Shared {
@@ -504,7 +471,14 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
                 }
             }
         };
-        // pass 1: inner products, PG pairs per reduction
+        // pass 1: inner products. Each warp reduces its share of a group's 5 PG
+        // products over its lanes and parks the totals in shared scratch (the
+        // m x m area, not staged yet); the warps' totals are summed once after the
+        // pass, so the pass itself runs without CTA barriers.
+        constexpr int NV = 5 * PG;
+        static_assert(NV <= 16, "one half-warp transpose per group");
+        float *p1 = sh.R;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll 1
         for (int g0 = 0; g0 < D; ++g0) issue(g0);
         for (int grp = 0; grp < ngroups; ++grp) {
@@ -527,14 +501,22 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
                 v[4 * PG + q] = dotv(y4, y_new);  // y_i . y_new
             }
             issue(grp + D);  // into the slot just read (this thread's reads are done)
-            const float t = block_sum_scatter<CT, 5 * PG>(v, sh.red2[par++ & 1]);
-            if (threadIdx.x < 5 * PG) {
-                const int q = threadIdx.x % PG, k = threadIdx.x / PG;
-                if (i + q < count) {
-                    float *dst = k == 0 ? sh.u1 : k == 1 ? sh.u2 : k == 2 ? sh.nsy : k == 3 ? sh.nys : sh.nyy;
-                    dst[i + q] = t;
-                }
-            }
+            float v16[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v16[j] = j < NV ? v[j] : 0.f;
+            const float t = warp_transpose_sum16(v16);
+            if (lane < NV) p1[(grp * Cfg<CT>::NW + wid) * NV + lane] = t;
+        }
+        __syncthreads();
+        // warp totals -> the 5 count inner products (warps summed in order)
+        for (int e = threadIdx.x; e < 5 * count; e += CT) {
+            const int k = e / count, i = e % count;
+            const float *src = p1 + (i / PG) * Cfg<CT>::NW * NV + k * PG + i % PG;
+            float t = 0.f;
+#pragma unroll
+            for (int q = 0; q < Cfg<CT>::NW; ++q) t += src[q * NV];
+            float *dst = k == 0 ? sh.u1 : k == 1 ? sh.u2 : k == 2 ? sh.nsy : k == 3 ? sh.nys : sh.nyy;
+            dst[i] = t;
         }
 #pragma unroll 1
         for (int g0 = 0; g0 < D; ++g0) issue(g0);  // pass 2's first groups
@@ -726,10 +708,10 @@ void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *
     const int count_bytes = prof_enabled() ? 1 : 0;
     int grid = num_sms * Cfg<kCT>::MINB;
     if (grid > n) grid = n > 0 ? n : 1;
-    const size_t dyn = (size_t)Cfg<kCT>::RING_F4 * sizeof(float4) + 2 * sizeof(float) * a.m * mm_ld(a.m);
+    const size_t dyn = (size_t)Cfg<kCT>::RING_F4 * sizeof(float4) + sizeof(float) * mm_floats<kCT>(a.m);
     static bool attr = false;
     if (!attr) {
-        const size_t most = (size_t)Cfg<kCT>::RING_F4 * sizeof(float4) + 2 * sizeof(float) * kMaxM * mm_ld(kMaxM);
+        const size_t most = (size_t)Cfg<kCT>::RING_F4 * sizeof(float4) + sizeof(float) * mm_floats<kCT>(kMaxM);
         cudaFuncSetAttribute(k_lbfgs_cta<kCT, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
         cudaFuncSetAttribute(k_lbfgs_cta<kCT, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)most);
