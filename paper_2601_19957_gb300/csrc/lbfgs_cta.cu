@@ -15,12 +15,14 @@
 // identical in exact arithmetic; what changes is the data flow. The two-loop
 // walks the pairs with a serial dependency (each alpha_i needs the q left by
 // the previous pair). Here one pass computes all inner products S^T g, Y^T g
-// and the new pair's row and column of S^T Y and Y^T Y at once (independent
-// loads, several pairs in flight), an m x m triangular solve gives the
-// coefficients, and a second pass forms p = -gamma g - S a + gamma Y w. The
-// m x m matrices S^T Y and Y^T Y live per walker in HBM and are updated
-// incrementally, so the history S, Y is read twice per iteration (the second
-// read mostly from L2) and never re-walked.
+// and the new pair's column of R and row and column of Y^T Y at once
+// (independent loads, several pairs in flight), m x m matrix-vector products
+// with R^-1 (kept per walker, one new column per appended pair) give the
+// coefficients, and a second pass forms p = -gamma g - S a + gamma Y w. R^-1,
+// Y^T Y and D live per walker in HBM and are updated incrementally, so the
+// history S, Y is read twice per iteration (the second read mostly from L2)
+// and never re-walked. With bf16 pairs the first pass runs on the tensor
+// cores (mma.sync, the pairs as the B operand; g split into three bf16 terms).
 //
 // A walker's step is a chain of dependent phases (reductions, the m x m
 // solve), so the SM is kept busy by several walkers at once: CT threads per
@@ -38,11 +40,15 @@ template <int CT>
 struct Cfg {
     static constexpr int NW = CT / 32;            // warps per walker
     static constexpr int VPT = kMaxD / (4 * CT);  // float4 groups per thread
-    static constexpr int PG = CT >= 256 ? 4 : 2;  // pairs per pass-1 reduction
+    static constexpr int PG = CT >= 256 ? 3 : 2;  // pairs per pass-1 ring group (5 PG products per warp transpose)
     static constexpr int MINB = CT >= 256 ? 2 : 4; // CTAs per SM
     static constexpr int DEPTH = CT >= 256 ? 2 : 3; // pair groups in flight (cp.async ring)
     // ring bytes: DEPTH groups x PG pairs x (s, y) x VPT float4 per thread
     static constexpr int RING_F4 = DEPTH * PG * 2 * VPT * CT;
+    // bf16 pairs: groups of PGB pairs (one 8-column tensor-core tile of s, y
+    // vectors), DB groups in the same ring (one 16-byte chunk per vector and thread)
+    static constexpr int PGB = 4;
+    static constexpr int DB = RING_F4 / (PGB * 2 * CT);
 };
 constexpr int kCT = 128;  // threads per walker used by the solver
 
@@ -86,7 +92,7 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
                  : "memory");
 }
 // History storage of the stored pairs: FP32, or bf16 (half the bytes of the
-// stream that bounds the step). Inner products and S^T Y / Y^T Y are formed
+// stream that bounds the step). Inner products, R and Y^T Y are formed
 // from the stored (rounded) vectors, so the direction applies the exact
 // L-BFGS matrix of the pairs as stored.
 __device__ __forceinline__ float4 round_bf16(float4 v) {
@@ -106,6 +112,35 @@ __device__ __forceinline__ float4 unpack4(uint32_t lo, uint32_t hi) {
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Four 8 x 8 bf16 matrices from shared memory; lane l gives the address of row
+// l % 8 of matrix l / 8 (16 bytes) and receives row l / 4, columns 2 (l % 4),
+// 2 (l % 4) + 1 of each matrix.
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *row) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"((uint32_t)__cvta_generic_to_shared(row))
+                 : "memory");
+}
+// D += A B for a 16 x 16 bf16 A whose rows 8..15 are zero (a0: row l / 4,
+// k = 2 (l % 4) + {0, 1}; a2: the same row, k + 8), a 16 x 8 bf16 B (b0: k =
+// 2 (l % 4) + {0, 1}, column l / 4; b1: k + 8) and FP32 accumulation; d0, d1
+// are row l / 4, columns 2 (l % 4) + {0, 1}.
+__device__ __forceinline__ void mma_rows8(float (&d)[4], uint32_t a0, uint32_t a2, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(0u), "r"(a2), "r"(0u), "r"(b0), "r"(b1));
+}
+// v = hi + mid + lo with each term a bf16 (the remainders are exact in FP32), so
+// products with bf16 vectors accumulate to FP32 accuracy on the tensor cores.
+__device__ __forceinline__ void split3_bf16(float v, float &hi, float &mid, float &lo) {
+    hi = __bfloat162float(__float2bfloat16_rn(v));
+    const float r = v - hi;
+    mid = __bfloat162float(__float2bfloat16_rn(r));
+    lo = r - mid;
 }
 
 // A vector of d coordinates as this thread's VPT float4 groups. Mapping M = 0
@@ -251,55 +286,93 @@ __device__ __forceinline__ void block_sum_max(float (&v)[NV], float &mx, float *
 // Odd row stride of the m x m matrices: their rows and their columns are both
 // free of shared-memory bank conflicts.
 __host__ __device__ __forceinline__ int mm_ld(int m) { return (m & 1) ? m + 2 : m + 1; }
-// Floats of the dynamic area after the ring: S^T Y and Y^T Y, which also hold
-// pass 1's per-warp partial sums before they are staged.
+// Pass 1's partial sums per ring group and warp: FP32 pairs, the 5 PG products
+// of the group; bf16 pairs, three rows (g, y_new, s_new) x the group's 2 PGB vectors.
+template <int CT>
+__host__ __device__ __forceinline__ int p1_floats(int m) {
+    const int f = (m + Cfg<CT>::PG - 1) / Cfg<CT>::PG * Cfg<CT>::NW * 5 * Cfg<CT>::PG;
+    const int b = (m + Cfg<CT>::PGB - 1) / Cfg<CT>::PGB * Cfg<CT>::NW * 3 * 2 * Cfg<CT>::PGB;
+    return f > b ? f : b;
+}
+// Floats of the dynamic area after the ring: R^-1, Y^T Y, pass 1's sums and the
+// six m-vectors (u1, u2, ca, cw, dg, nr).
 template <int CT>
 __host__ __device__ __forceinline__ int mm_floats(int m) {
-    const int mats = 2 * m * mm_ld(m);
-    const int p1 = (m + Cfg<CT>::PG - 1) / Cfg<CT>::PG * Cfg<CT>::NW * 5 * Cfg<CT>::PG;
-    return mats > p1 ? mats : p1;
+    return 2 * m * mm_ld(m) + p1_floats<CT>(m) + 6 * m;
 }
 
 template <int CT>
 struct Shared {
     float red2[2][Cfg<CT>::NW * 32];  // reduction scratch, used alternately (see block_sum)
-    float u1[kMaxM], u2[kMaxM], nsy[kMaxM], nys[kMaxM], nyy[kMaxM];
-    float ca[kMaxM], cw[kMaxM], dinv[kMaxM];
+    // m-vectors (dynamic): S^T g, Y^T g; the direction's coefficients a, w;
+    // D = diag(S^T Y); the new pair's column of R
+    float *u1, *u2, *ca, *cw, *dg, *nr;
     float gamma;
-    int slot_of[kMaxM];
-    // dynamic shared memory: the pair ring, then S^T Y and Y^T Y (logical order, stride ld)
+    // dynamic shared memory: the pair ring, R^-1 and Y^T Y (logical order,
+    // stride ld), then pass 1's per-warp partial sums
     float4 *ring;
-    float *R, *YY;
+    float *RI, *YY, *p1;
     int ld;
+    uint4 zero16;  // a zero row for the unused rows of the tensor-core operand
 };
 
-// S^T Y and Y^T Y of the walker in logical order: the new pair's row and column
-// (logical cn, or -1) from pass 1, the rest from the per-walker slot-indexed
-// copies, which receive the new row and column at the same time. Returns bytes moved.
+// The m x m state of a walker, slot-indexed in HBM (logical pair i sits in slot
+// (head + i) mod m): R^-1, the inverse of R = upper(S^T Y) (entries i <= j), Y^T Y,
+// and D_i = s_i . y_i (in rho). R^-1 is kept instead of R because the history
+// changes only by appending a pair (one new column of R^-1, a triangular
+// matvec) and dropping the oldest (the inverse of R's trailing block is the
+// trailing block of R^-1), so the direction needs matvecs, not substitutions.
+//
+// Copies the walker's R^-1, Y^T Y and D into shared memory in logical order as
+// 4-byte asynchronous copies that complete with the first ring group; the new
+// pair's row and column (logical cn, or -1) are skipped: pass 1 supplies them.
 template <int CT>
-__device__ __forceinline__ uint64_t stage_mm(Shared<CT> &sh, float *msy, float *myy, int count, int m, int cn) {
-    for (int e = threadIdx.x; e < count * count; e += CT) {
-        const int i = e / count, j = e % count;
-        const int si = sh.slot_of[i], sj = sh.slot_of[j];
-        float r, yy;
-        if (j == cn) {
-            r = sh.nsy[i];
-            yy = sh.nyy[i];
-        } else if (i == cn) {
-            r = sh.nys[j];
-            yy = sh.nyy[j];
-        } else {
-            r = msy[(size_t)si * m + sj];
-            yy = myy[(size_t)si * m + sj];
+__device__ __forceinline__ void fetch_mm(Shared<CT> &sh, const float *mri, const float *myy, const float *dw,
+                                         int count, int m, int head, int cn) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = wid; i < count; i += Cfg<CT>::NW) {
+        if (i == cn) continue;
+        int si = head + i;
+        if (si >= m) si -= m;
+        for (int j = lane; j < count; j += 32) {
+            if (j == cn) continue;
+            int sj = head + j;
+            if (sj >= m) sj -= m;
+            if (j >= i) cp_async4(sh.RI + i * sh.ld + j, mri + (size_t)si * m + sj);
+            cp_async4(sh.YY + i * sh.ld + j, myy + (size_t)si * m + sj);
         }
-        if (i == cn || j == cn) {
-            msy[(size_t)si * m + sj] = r;
-            myy[(size_t)si * m + sj] = yy;
-        }
-        sh.R[i * sh.ld + j] = r;
-        sh.YY[i * sh.ld + j] = yy;
+        if (lane == 0) cp_async4(sh.dg + i, dw + si);
     }
-    return (uint64_t)count * count * 8 + (cn >= 0 ? (uint64_t)(2 * count - 1) * 8 : 0);
+}
+// The new pair's part of the state from pass 1: Y^T Y's row and column (y_i .
+// y_new) into shared memory and HBM, R's new column (s_i . y_new, the last entry
+// being D_new) into sh.nr and D_new into sh.dg and HBM. R^-1's new column is
+// formed by the solver. Returns the bytes of m x m state moved this visit.
+template <int CT, typename P1>
+__device__ __forceinline__ uint64_t new_mm(Shared<CT> &sh, float *myy, float *dw, int count, int m, int head, int cn,
+                                           P1 p1sum) {
+    if (cn >= 0) {
+        for (int e = threadIdx.x; e < 2 * count - 1; e += CT) {
+            // e < count: column cn, row e; else row cn, column e - count
+            const int i = e < count ? e : cn, j = e < count ? cn : e - count;
+            const float yy = p1sum(4, e < count ? i : j);
+            int si = head + i, sj = head + j;
+            if (si >= m) si -= m;
+            if (sj >= m) sj -= m;
+            myy[(size_t)si * m + sj] = yy;
+            sh.YY[i * sh.ld + j] = yy;
+            if (e < count) {
+                const float r = p1sum(2, i);
+                sh.nr[i] = r;
+                if (i == cn) {
+                    sh.dg[cn] = r;
+                    dw[si] = r;
+                }
+            }
+        }
+    }
+    const uint64_t c = count;
+    return (c * (c + 1) / 2 + c * c + c) * 4 + (cn >= 0 ? (uint64_t)(3 * c) * 4 : 0);
 }
 
 // Warp that runs the m x m solve: CTAs are dealt to SMs round-robin, so the
@@ -310,44 +383,57 @@ __device__ __forceinline__ int solver_warp() {
     return (int)(blockIdx.x / per) % Cfg<CT>::NW;
 }
 
-// The m x m part (one warp): w = R^-1 u1, gamma, tv = D w + gamma Y^T Y w -
-// gamma Y^T g, a = R^-T tv. Column-oriented substitutions: lane j holds the
-// running right-hand side of rows j and j + 32; each step broadcasts one
-// solved unknown. Results in sh.cw, sh.ca, sh.gamma.
+// The m x m part (one warp), with R^-1 in shared memory: the new column of R^-1
+// when a pair was appended (logical cn; RI_i,cn = -(sum_{i<=k<cn} RI_ik R_k,cn) / D_cn,
+// RI_cn,cn = 1 / D_cn, also written to HBM), then w = R^-1 u1, gamma = D_c-1 /
+// (y^T y)_c-1, tv = D w + gamma Y^T Y w - gamma u2 and a = R^-T tv. Each lane
+// forms whole entries (rows lane and lane + 32) with sums in ascending index
+// order. Results in sh.cw, sh.ca, sh.gamma.
 template <int CT>
-__device__ __forceinline__ void solve_mm(Shared<CT> &sh, int c) {
+__device__ __forceinline__ void solve_mm(Shared<CT> &sh, int c, int cn, float *mri, int m, int head) {
     const int lane = threadIdx.x & 31;
     const int LD = sh.ld;
-    const float *R = sh.R, *YY = sh.YY;
-    for (int i = lane; i < c; i += 32) sh.dinv[i] = 1.f / R[i * LD + i];
-    __syncwarp();
-    float acc0 = lane < c ? sh.u1[lane] : 0.f, acc1 = lane + 32 < c ? sh.u1[lane + 32] : 0.f;
-    for (int i = c - 1; i >= 0; --i) {
-        const float wi = __shfl_sync(0xffffffffu, i < 32 ? acc0 : acc1, i & 31) * sh.dinv[i];
-        if (lane == 0) sh.cw[i] = wi;
-        if (lane < i) acc0 -= R[lane * LD + i] * wi;
-        if (lane + 32 < i) acc1 -= R[(lane + 32) * LD + i] * wi;
+    float *RI = sh.RI;
+    const float *YY = sh.YY;
+    float *tv = sh.p1;  // pass 1's partial sums are consumed before the solve
+    if (cn >= 0) {
+        const float dn = sh.nr[cn];
+        int sc = head + cn;
+        if (sc >= m) sc -= m;
+        for (int i = lane; i <= cn; i += 32) {
+            float v;
+            if (i == cn) {
+                v = 1.f / dn;
+            } else {
+                float t = 0.f;
+                for (int k = i; k < cn; ++k) t += RI[i * LD + k] * sh.nr[k];
+                v = -t / dn;
+            }
+            RI[i * LD + cn] = v;
+            int si = head + i;
+            if (si >= m) si -= m;
+            mri[(size_t)si * m + sc] = v;
+        }
+        __syncwarp();
+    }
+    for (int i = lane; i < c; i += 32) {
+        float t = 0.f;
+        for (int k = i; k < c; ++k) t += RI[i * LD + k] * sh.u1[k];
+        sh.cw[i] = t;
     }
     __syncwarp();
-    const float gam = R[(c - 1) * LD + (c - 1)] / YY[(c - 1) * LD + (c - 1)];
+    const float gam = sh.dg[c - 1] / YY[(c - 1) * LD + (c - 1)];
     if (lane == 0) sh.gamma = gam;
-    float tv0 = 0.f, tv1 = 0.f;
-    if (lane < c) {
+    for (int i = lane; i < c; i += 32) {
         float yyw = 0.f;
-        for (int j = 0; j < c; ++j) yyw += YY[lane * LD + j] * sh.cw[j];
-        tv0 = R[lane * LD + lane] * sh.cw[lane] + gam * yyw - gam * sh.u2[lane];
+        for (int j = 0; j < c; ++j) yyw += YY[i * LD + j] * sh.cw[j];
+        tv[i] = sh.dg[i] * sh.cw[i] + gam * yyw - gam * sh.u2[i];
     }
-    if (lane + 32 < c) {
-        const int i = lane + 32;
-        float yyw = 0.f;
-        for (int j = 0; j < c; ++j) yyw += YY[i * sh.ld + j] * sh.cw[j];
-        tv1 = R[i * LD + i] * sh.cw[i] + gam * yyw - gam * sh.u2[i];
-    }
-    for (int i = 0; i < c; ++i) {
-        const float ai = __shfl_sync(0xffffffffu, i < 32 ? tv0 : tv1, i & 31) * sh.dinv[i];
-        if (lane == 0) sh.ca[i] = ai;
-        if (lane > i && lane < c) tv0 -= R[i * LD + lane] * ai;
-        if (lane + 32 > i && lane + 32 < c) tv1 -= R[i * LD + lane + 32] * ai;
+    __syncwarp();
+    for (int j = lane; j < c; j += 32) {
+        float t = 0.f;
+        for (int i = 0; i <= j; ++i) t += RI[i * LD + j] * tv[i];
+        sh.ca[j] = t;
     }
 }
 
@@ -369,182 +455,321 @@ __device__ __forceinline__ void store_hist(const Vec<CT, M> &v, HT *row, int d) 
     }
 }
 
+// The shared-memory ring the stored pairs stream through: D slots of PG pairs,
+// blocks of CT 16-byte chunks (chunk j of vector v of pair q of slot sl; U4
+// chunks per vector and thread). Within a block the chunk of thread t sits at
+// t ^ (block % 8), so the same chunk of 8 consecutive blocks (the rows of one
+// ldmatrix) falls in 8 different bank groups.
+template <int CT, typename HT>
+struct Ring {
+    static constexpr bool BF = sizeof(HT) == 2;
+    static constexpr int MAP = BF;
+    static constexpr int PG = BF ? Cfg<CT>::PGB : Cfg<CT>::PG;
+    static constexpr int D = BF ? Cfg<CT>::DB : Cfg<CT>::DEPTH;
+    static constexpr int U4 = BF ? Cfg<CT>::VPT / 2 : Cfg<CT>::VPT;
+    uint4 *base;
+    int d;
+    __device__ __forceinline__ uint4 *at(int sl, int q, int v, int j, int t) const {
+        const int b = ((sl * PG + q) * 2 + v) * U4 + j;
+        return base + (size_t)b * CT + (t ^ (b & 7));
+    }
+    // this thread's chunks of a stored row (cp.async, or plain copies zero-padded
+    // past d for a ragged end of the row)
+    __device__ __forceinline__ void copy_in(int sl, int q, int v, const HT *row) const {
+#pragma unroll
+        for (int j = 0; j < U4; ++j) {
+            uint4 *dst = at(sl, q, v, j, threadIdx.x);
+            if (BF) {
+                const int e0 = Vec<CT, MAP>::i0(0);  // 8 consecutive elements
+                if ((d & 7) == 0 && e0 + 7 < d) {
+                    cp_async16(dst, row + e0);
+                } else {
+                    uint16_t h[8];
+                    const uint16_t *src = reinterpret_cast<const uint16_t *>(row);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) h[e] = e0 + e < d ? src[e0 + e] : (uint16_t)0;
+                    *dst = make_uint4(h[0] | (uint32_t)h[1] << 16, h[2] | (uint32_t)h[3] << 16,
+                                      h[4] | (uint32_t)h[5] << 16, h[6] | (uint32_t)h[7] << 16);
+                }
+            } else {
+                const int i0 = Vec<CT, MAP>::i0(j);
+                if ((d & 3) == 0 && i0 + 3 < d) {
+                    cp_async16(dst, row + i0);
+                } else {
+                    for (int e = 0; e < 4 && i0 + e < d; ++e)
+                        cp_async4(reinterpret_cast<float *>(dst) + e, reinterpret_cast<const float *>(row) + i0 + e);
+                }
+            }
+        }
+    }
+    // this thread's coordinates of pair q of slot sl
+    __device__ __forceinline__ void fetch(int sl, int q, Vec<CT, MAP> &sv, Vec<CT, MAP> &yv) const {
+        if (BF) {
+            const uint4 a4 = *at(sl, q, 0, 0, threadIdx.x), b4 = *at(sl, q, 1, 0, threadIdx.x);
+            sv.v[0] = unpack4(a4.x, a4.y);
+            sv.v[1] = unpack4(a4.z, a4.w);
+            yv.v[0] = unpack4(b4.x, b4.y);
+            yv.v[1] = unpack4(b4.z, b4.w);
+        } else {
+#pragma unroll
+            for (int j = 0; j < Cfg<CT>::VPT; ++j) {
+                const uint4 a4 = *at(sl, q, 0, j, threadIdx.x), b4 = *at(sl, q, 1, j, threadIdx.x);
+                sv.v[j] = make_float4(__uint_as_float(a4.x), __uint_as_float(a4.y), __uint_as_float(a4.z),
+                                      __uint_as_float(a4.w));
+                yv.v[j] = make_float4(__uint_as_float(b4.x), __uint_as_float(b4.y), __uint_as_float(b4.z),
+                                      __uint_as_float(b4.w));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < Cfg<CT>::VPT; ++j) {
+            const int i0 = Vec<CT, MAP>::i0(j);
+            if (!(i0 + 3 < d)) {  // ragged tail: lanes past d hold stale data
+                if (i0 + 0 >= d) sv.v[j].x = yv.v[j].x = 0.f;
+                if (i0 + 1 >= d) sv.v[j].y = yv.v[j].y = 0.f;
+                if (i0 + 2 >= d) sv.v[j].z = yv.v[j].z = 0.f;
+                if (i0 + 3 >= d) sv.v[j].w = yv.v[j].w = 0.f;
+            }
+        }
+    }
+    // Issues pass-1 group k (logical pairs k PG .. k PG + PG - 1 of the J stored
+    // from slot head) into slot k % D. Always commits.
+    __device__ __forceinline__ void issue1(int k, int J, int head, int m, const HT *S, const HT *Y) const {
+        const int sl = k % D;
+#pragma unroll
+        for (int q = 0; q < PG; ++q) {
+            const int j = k * PG + q;
+            if (j >= J) break;
+            int slot = head + j;
+            if (slot >= m) slot -= m;
+            copy_in(sl, q, 0, S + (size_t)slot * d);
+            copy_in(sl, q, 1, Y + (size_t)slot * d);
+        }
+        cp_async_commit();
+    }
+    // Issues pass-2 group k (logical pairs k PG .., slot k % D). Always commits.
+    __device__ __forceinline__ void issue2(int k, int count, int head, int m, const HT *S, const HT *Y) const {
+#pragma unroll
+        for (int q = 0; q < PG; ++q) {
+            const int i = k * PG + q;
+            if (i >= count) break;
+            int slot = head + i;
+            if (slot >= m) slot -= m;
+            copy_in(k % D, q, 0, S + (size_t)slot * d);
+            copy_in(k % D, q, 1, Y + (size_t)slot * d);
+        }
+        cp_async_commit();
+    }
+};
+
 // Direction for walker state st (count pairs from ring slot head). When
-// new_slot >= 0 the pair in that slot was stored this visit (it is the newest,
-// logical index count - 1) and its row and column of S^T Y, Y^T Y come from the
-// same pass. Writes P and the unit trial X + P; updates st.dphi / alpha / bt
-// and possibly resets the history (steepest descent when p is not a descent
-// direction). Returns the algorithmic bytes moved.
+// new_slot >= 0 the pair in that slot was stored this visit (the newest, logical
+// index count - 1; s_new, y_new) and its column of R, row and column of Y^T Y
+// come from the same pass. Writes P and
+// the unit trial X + P; updates st.dphi / alpha / bt and possibly resets the
+// history (steepest descent when p is not a descent direction). Returns the
+// algorithmic bytes moved.
 template <int CT, typename HT, int MAP = (sizeof(HT) == 2)>
 __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<float> &st, int new_slot,
-                              const Vec<CT, MAP> &g, const Vec<CT, MAP> &x, const Vec<CT, MAP> &s_new, const Vec<CT, MAP> &y_new,
-                              float *MSY, float *MYY, Shared<CT> &sh, int &par) {
-    constexpr int PG = Cfg<CT>::PG;
+                              const Vec<CT, MAP> &g_in, const Vec<CT, MAP> &x_in,
+                              const Vec<CT, MAP> &s_new, const Vec<CT, MAP> &y_new, float *MRI, float *MYY,
+                              Shared<CT> &sh, int &par) {
+    using RG = Ring<CT, HT>;
+    constexpr bool BF = RG::BF;
+    static_assert(!BF || Cfg<CT>::VPT == 2, "bf16 history: two groups of 4 (8 bytes each) per thread");
+    constexpr int PG = RG::PG, D = RG::D, NW = Cfg<CT>::NW;
     const int d = a.d, m = a.m;
     const int count = st.count;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t bytes = 0;
     Vec<CT, MAP> p;
     p.zero();
+    // x and g are stored at X, G by the caller; the bf16 path reads them back
+    // after pass 1 instead of holding them through it
+    Vec<CT, MAP> g = g_in, x = x_in;
     if (count > 0) {
         const HT *S = reinterpret_cast<const HT *>(a.S) + (size_t)w * m * d;
         const HT *Y = reinterpret_cast<const HT *>(a.Y) + (size_t)w * m * d;
-        if (threadIdx.x < count) sh.slot_of[threadIdx.x] = (st.head + threadIdx.x) % m;
-        __syncthreads();
-        // Both passes stream the pairs through the shared-memory ring, DEPTH groups
-        // of PG pairs in flight per thread (cp.async); pass 2's first groups are
-        // issued before the m x m solve, which does not need them.
-        constexpr int VPT = Cfg<CT>::VPT;
-        // bf16 chunks are half the size: twice the groups in flight in the same ring
-        constexpr int D = sizeof(HT) == 2 ? 2 * Cfg<CT>::DEPTH : Cfg<CT>::DEPTH;
-        const int ngroups = (count + PG - 1) / PG;
-        const bool vec_ok = (d & 3) == 0;
-        constexpr bool BF = sizeof(HT) == 2;
-        static_assert(!BF || VPT == 2, "bf16 history: two groups of 4 (8 bytes each) per thread");
-        constexpr int U4 = BF ? VPT / 2 : VPT;  // 16-byte ring chunks per stored vector per thread
-        auto rp = [&](int grp, int q, int v, int j) -> uint4 * {
-            return reinterpret_cast<uint4 *>(sh.ring) + ((((size_t)(grp % D) * PG + q) * 2 + v) * U4 + j) * CT +
-                   threadIdx.x;
-        };
-        // this thread's chunks of one stored vector into the ring (cp.async, or
-        // plain copies for a ragged end of the row)
-        auto issue_vec = [&](int grp, int q, int v, const HT *row) {
-#pragma unroll
-            for (int j = 0; j < U4; ++j) {
-                if (BF) {
-                    const int e0 = Vec<CT, MAP>::i0(0);  // 8 consecutive elements
-                    if ((d & 7) == 0 && e0 + 7 < d) {
-                        cp_async16(rp(grp, q, v, j), row + e0);
-                    } else {
-                        HT *dst = reinterpret_cast<HT *>(rp(grp, q, v, j));
-                        for (int e = 0; e < 8 && e0 + e < d; ++e) dst[e] = row[e0 + e];
-                    }
-                } else {
-                    const int i0 = Vec<CT, MAP>::i0(j);
-                    if (vec_ok && i0 + 3 < d) {
-                        cp_async16(rp(grp, q, v, j), row + i0);
-                    } else {
-                        for (int e = 0; e < 4 && i0 + e < d; ++e)
-                            cp_async4(reinterpret_cast<float *>(rp(grp, q, v, j)) + e,
-                                      reinterpret_cast<const float *>(row) + i0 + e);
-                    }
-                }
-            }
-        };
-        auto issue = [&](int grp) {  // always commits one group (possibly empty)
-            if (grp < ngroups) {
-#pragma unroll
-                for (int q = 0; q < PG; ++q) {
-                    const int i = grp * PG + q;
-                    if (i >= count) break;
-                    const size_t row = (size_t)sh.slot_of[i] * d;
-                    issue_vec(grp, q, 0, S + row);
-                    issue_vec(grp, q, 1, Y + row);
-                }
-            }
-            cp_async_commit();
-        };
-        auto fetch = [&](int grp, int q, Vec<CT, MAP> &sv, Vec<CT, MAP> &yv) {  // this thread's chunks of one pair
-            if (BF) {
-                const uint4 a4 = *rp(grp, q, 0, 0), b4 = *rp(grp, q, 1, 0);
-                sv.v[0] = unpack4(a4.x, a4.y);
-                sv.v[1] = unpack4(a4.z, a4.w);
-                yv.v[0] = unpack4(b4.x, b4.y);
-                yv.v[1] = unpack4(b4.z, b4.w);
-            } else {
-#pragma unroll
-                for (int j = 0; j < VPT; ++j) {
-                    const uint4 a4 = *rp(grp, q, 0, j), b4 = *rp(grp, q, 1, j);
-                    sv.v[j] = make_float4(__uint_as_float(a4.x), __uint_as_float(a4.y), __uint_as_float(a4.z),
-                                          __uint_as_float(a4.w));
-                    yv.v[j] = make_float4(__uint_as_float(b4.x), __uint_as_float(b4.y), __uint_as_float(b4.z),
-                                          __uint_as_float(b4.w));
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < VPT; ++j) {
-                const int i0 = Vec<CT, MAP>::i0(j);
-                if (!(i0 + 3 < d)) {  // ragged tail: lanes past d hold stale data
-                    if (i0 + 0 >= d) sv.v[j].x = yv.v[j].x = 0.f;
-                    if (i0 + 1 >= d) sv.v[j].y = yv.v[j].y = 0.f;
-                    if (i0 + 2 >= d) sv.v[j].z = yv.v[j].z = 0.f;
-                    if (i0 + 3 >= d) sv.v[j].w = yv.v[j].w = 0.f;
-                }
-            }
-        };
-        // pass 1: inner products. Each warp reduces its share of a group's 5 PG
-        // products over its lanes and parks the totals in shared scratch (the
-        // m x m area, not staged yet); the warps' totals are summed once after the
-        // pass, so the pass itself runs without CTA barriers.
-        constexpr int NV = 5 * PG;
-        static_assert(NV <= 16, "one half-warp transpose per group");
-        float *p1 = sh.R;
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const RG ring{reinterpret_cast<uint4 *>(sh.ring), d};
+        // pass 1 streams the logical pairs (the new one included: it is stored)
+        const bool added = new_slot >= 0;
+        const int J = count, head = st.head;
+        const int ng1 = (J + PG - 1) / PG;
+        const int K1 = ng1;
+        const int cn = added ? count - 1 : -1;
+        float *mri_w = MRI + (size_t)w * m * m, *myy_w = MYY + (size_t)w * m * m, *dw = a.rho + (size_t)w * m;
+        fetch_mm<CT>(sh, mri_w, myy_w, dw, count, m, st.head, cn);  // committed with ring group 0
 #pragma unroll 1
-        for (int g0 = 0; g0 < D; ++g0) issue(g0);
-        for (int grp = 0; grp < ngroups; ++grp) {
-            cp_async_wait<D - 1>();
-            const int i = grp * PG;
-            float v[5 * PG];
+        for (int k = 0; k < D - 1; ++k) ring.issue1(k, J, head, m, S, Y);
+        float *p1 = sh.p1;
+        if constexpr (BF) {
+            // Pass 1 on the tensor cores: per warp (its 256 coordinates, 16 k-steps of
+            // 16) and ring group (8 stored vectors s_0 y_0 .. s_3 y_3 as the columns of
+            // B), D = A B with the rows of A = (g_hi, g_mid, g_lo, y_new, s_new, 0 ..)
+            // at the same coordinates. The A fragments are staged once through this
+            // warp's own chunks of ring slot D - 1 (free until group D - 1 is issued into it).
+            uint4 *ring4 = reinterpret_cast<uint4 *>(sh.ring);
+            constexpr int SB = (D - 1) * PG * 2 * RG::U4;  // first block of slot D - 1
+            static_assert(2 * PG * RG::U4 >= 5, "slot D - 1 holds the five staged rows");
+            auto stage = [&](int r, int u) { return ring4 + (SB + r) * CT + (u ^ ((SB + r) & 7)); };
+            {
+                float hi[8], mi[8], lo[8];
+                const float gv[8] = {g.v[0].x, g.v[0].y, g.v[0].z, g.v[0].w, g.v[1].x, g.v[1].y, g.v[1].z, g.v[1].w};
 #pragma unroll
-            for (int q = 0; q < PG; ++q) {
-                Vec<CT, MAP> s4, y4;
-                if (i + q < count) {
-                    fetch(grp, q, s4, y4);
-                } else {
-                    s4.zero();
-                    y4.zero();
-                }
-                v[q] = dotv(s4, g);               // u1 = S^T g
-                v[PG + q] = dotv(y4, g);          // u2 = Y^T g
-                v[2 * PG + q] = dotv(s4, y_new);  // s_i . y_new
-                v[3 * PG + q] = dotv(s_new, y4);  // s_new . y_i
-                v[4 * PG + q] = dotv(y4, y_new);  // y_i . y_new
+                for (int e = 0; e < 8; ++e) split3_bf16(gv[e], hi[e], mi[e], lo[e]);
+                const int t = threadIdx.x;  // row r in block SB + r, this thread's chunk
+                *stage(0, t) = make_uint4(pack2(hi[0], hi[1]), pack2(hi[2], hi[3]), pack2(hi[4], hi[5]), pack2(hi[6], hi[7]));
+                *stage(1, t) = make_uint4(pack2(mi[0], mi[1]), pack2(mi[2], mi[3]), pack2(mi[4], mi[5]), pack2(mi[6], mi[7]));
+                *stage(2, t) = make_uint4(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]), pack2(lo[4], lo[5]), pack2(lo[6], lo[7]));
+                // s_new, y_new are bf16 values already (the pair as stored): exact
+                *stage(3, t) = make_uint4(pack2(y_new.v[0].x, y_new.v[0].y), pack2(y_new.v[0].z, y_new.v[0].w),
+                                          pack2(y_new.v[1].x, y_new.v[1].y), pack2(y_new.v[1].z, y_new.v[1].w));
+                *stage(4, t) = make_uint4(pack2(s_new.v[0].x, s_new.v[0].y), pack2(s_new.v[0].z, s_new.v[0].w),
+                                          pack2(s_new.v[1].x, s_new.v[1].y), pack2(s_new.v[1].z, s_new.v[1].w));
             }
-            issue(grp + D);  // into the slot just read (this thread's reads are done)
-            float v16[16];
+            __syncwarp();
+            const int mi8 = lane >> 3, ri8 = lane & 7;  // ldmatrix: matrix and row this lane addresses
+            uint32_t af[16][2];                         // A fragments (a0, a2) per k-step
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v16[j] = j < NV ? v[j] : 0.f;
-            const float t = warp_transpose_sum16(v16);
-            if (lane < NV) p1[(grp * Cfg<CT>::NW + wid) * NV + lane] = t;
+            for (int c = 0; c < 16; c += 2) {
+                const int u = 32 * wid + 2 * (c + (mi8 >> 1)) + (mi8 & 1);  // chunk (thread) index
+                const void *row = ri8 < 5 ? (const void *)stage(ri8, u) : (const void *)&sh.zero16;
+                uint32_t r[4];
+                ldsm_x4(r, row);
+                af[c][0] = r[0];
+                af[c][1] = r[1];
+                af[c + 1][0] = r[2];
+                af[c + 1][1] = r[3];
+            }
+            __syncwarp();  // the staging chunks are read before slot D - 1 is refilled
+            int nk = (d - 256 * wid + 15) / 16;  // k-steps of this warp inside d (warp-uniform)
+            nk = nk < 0 ? 0 : (nk > 16 ? 16 : nk);
+            const int gid = lane >> 2, tig = lane & 3;
+            ring.issue1(D - 1, J, head, m, S, Y);  // its slot held the staged operand
+            for (int k = 0; k < K1; ++k) {
+                cp_async_wait<D - 1>();
+                __syncwarp();  // every lane's copies of the group are visible to the warp
+                const int gi = k, sl = k % D;
+                if (gi < ng1) {
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                    // B rows: vector n = ri8 mod 2 PG of the group (pair n / 2, s or y); with
+                    // 2 PG < 8 the remaining columns repeat it and are not read back
+                    const int n = ri8 % (2 * PG);
+#pragma unroll
+                    for (int c = 0; c < 16; c += 2) {
+                        if (c < nk) {
+                            uint32_t b[4];
+                            ldsm_x4(b, ring.at(sl, n >> 1, n & 1, 0, 32 * wid + 2 * (c + (mi8 >> 1)) + (mi8 & 1)));
+                            mma_rows8(acc, af[c][0], af[c][1], b[0], b[1]);
+                            if (c + 1 < nk) mma_rows8(acc, af[c + 1][0], af[c + 1][1], b[2], b[3]);
+                        }
+                    }
+                    // g . v = (g_hi + g_mid) . v + g_lo . v from rows 0, 1, 2
+                    const float h0 = __shfl_down_sync(0xffffffffu, acc[0], 4);
+                    const float l0 = __shfl_down_sync(0xffffffffu, acc[0], 8);
+                    const float h1 = __shfl_down_sync(0xffffffffu, acc[1], 4);
+                    const float l1 = __shfl_down_sync(0xffffffffu, acc[1], 8);
+                    const int r = gid == 0 ? 0 : gid == 3 ? 1 : gid == 4 ? 2 : -1;
+                    if (r >= 0 && tig < PG) {
+                        const float2 o = gid == 0 ? make_float2((acc[0] + h0) + l0, (acc[1] + h1) + l1)
+                                                  : make_float2(acc[0], acc[1]);
+                        *reinterpret_cast<float2 *>(p1 + ((gi * NW + wid) * 3 + r) * (2 * PG) + 2 * tig) = o;
+                    }
+                }
+                __syncwarp();  // the warp has read the group before its slot is refilled
+                ring.issue1(k + D, J, head, m, S, Y);
+            }
+        } else {
+            // pass 1: inner products. Each warp reduces its share of a group's 5 PG
+            // products over its lanes and parks the totals in shared scratch; the
+            // warps' totals are summed once after the pass.
+            constexpr int NV = 5 * PG;
+            static_assert(NV <= 16, "one half-warp transpose per group");
+            ring.issue1(D - 1, J, head, m, S, Y);
+            for (int k = 0; k < K1; ++k) {
+                cp_async_wait<D - 1>();
+                const int gi = k, sl = k % D;
+                if (gi < ng1) {
+                    float v[NV];
+#pragma unroll
+                    for (int q = 0; q < PG; ++q) {
+                        Vec<CT, MAP> s4, y4;
+                        if (gi * PG + q < J) {
+                            ring.fetch(sl, q, s4, y4);
+                        } else {
+                            s4.zero();
+                            y4.zero();
+                        }
+                        v[q] = dotv(s4, g);               // u1 = S^T g
+                        v[PG + q] = dotv(y4, g);          // u2 = Y^T g
+                        v[2 * PG + q] = dotv(s4, y_new);  // s_i . y_new
+                        v[3 * PG + q] = dotv(s_new, y4);  // s_new . y_i
+                        v[4 * PG + q] = dotv(y4, y_new);  // y_i . y_new
+                    }
+                    float v16[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v16[j] = j < NV ? v[j] : 0.f;
+                    const float t = warp_transpose_sum16(v16);
+                    if (lane < NV) p1[(gi * NW + wid) * NV + lane] = t;
+                }
+                ring.issue1(k + D, J, head, m, S, Y);  // into the slot just read (own chunks)
+            }
         }
         __syncthreads();
-        // warp totals -> the 5 count inner products (warps summed in order)
-        for (int e = threadIdx.x; e < 5 * count; e += CT) {
-            const int k = e / count, i = e % count;
-            const float *src = p1 + (i / PG) * Cfg<CT>::NW * NV + k * PG + i % PG;
+        // product k of logical pair i (k: 0 s.g, 1 y.g, 2 s.y_new, 3 s_new.y, 4 y.y_new):
+        // the warps' totals summed in warp order
+        auto p1sum = [&](int k, int i) {
+            const int j = i;
+            const float *src;
+            int stride;
+            if constexpr (BF) {
+                constexpr int rk[5] = {0, 0, 1, 2, 1}, ck[5] = {0, 1, 0, 1, 1};
+                src = p1 + ((j / PG) * NW * 3 + rk[k]) * (2 * PG) + 2 * (j % PG) + ck[k];
+                stride = 3 * 2 * PG;
+            } else {
+                src = p1 + (j / PG) * NW * (5 * PG) + k * PG + j % PG;
+                stride = 5 * PG;
+            }
             float t = 0.f;
 #pragma unroll
-            for (int q = 0; q < Cfg<CT>::NW; ++q) t += src[q * NV];
-            float *dst = k == 0 ? sh.u1 : k == 1 ? sh.u2 : k == 2 ? sh.nsy : k == 3 ? sh.nys : sh.nyy;
-            dst[i] = t;
+            for (int q = 0; q < NW; ++q) t += src[q * stride];
+            return t;
+        };
+        for (int e = threadIdx.x; e < 2 * count; e += CT) {
+            if (e < count)
+                sh.u1[e] = p1sum(0, e);
+            else
+                sh.u2[e - count] = p1sum(1, e - count);
         }
+        bytes += new_mm<CT>(sh, myy_w, dw, count, m, st.head, cn, p1sum);
+        const int ng2 = (count + PG - 1) / PG;
 #pragma unroll 1
-        for (int g0 = 0; g0 < D; ++g0) issue(g0);  // pass 2's first groups
-        __syncthreads();
-        bytes += stage_mm<CT>(sh, MSY + (size_t)w * m * m, MYY + (size_t)w * m * m, count, m,
-                              new_slot >= 0 ? count - 1 : -1);
+        for (int k = 0; k < D; ++k) ring.issue2(k, count, st.head, m, S, Y);  // pass 2's first groups
+        if constexpr (BF) {
+            g.load(a.G + (size_t)w * d, d);
+            x.load(a.X + (size_t)w * d, d);
+        }
         __syncthreads();
         // the solving warp differs between the CTAs that share an SM (their warp w
         // would otherwise all sit on the same scheduler)
-        if ((int)(threadIdx.x >> 5) == solver_warp<CT>()) solve_mm<CT>(sh, count);
+        if (wid == solver_warp<CT>()) solve_mm<CT>(sh, count, cn, mri_w, m, st.head);
         __syncthreads();
         // pass 2: p = -gamma g - S a + gamma Y w
         const float gam = sh.gamma;
         p.zero();
         axpyv(-gam, g, p);
-        for (int grp = 0; grp < ngroups; ++grp) {
+        for (int k = 0; k < ng2; ++k) {
             cp_async_wait<D - 1>();
 #pragma unroll
             for (int q = 0; q < PG; ++q) {
-                const int i = grp * PG + q;
+                const int i = k * PG + q;
                 if (i < count) {
                     Vec<CT, MAP> s4, y4;
-                    fetch(grp, q, s4, y4);
+                    ring.fetch(k % D, q, s4, y4);
                     axpyv(-sh.ca[i], s4, p);
                     axpyv(gam * sh.cw[i], y4, p);
                 }
             }
-            issue(grp + D);
+            ring.issue2(k + D, count, st.head, m, S, Y);  // this thread's own chunks, just read
         }
         cp_async_wait<0>();  // (only empty groups remain) the ring is free for the next walker
         // the two-loop recursion's history traffic: each pair read in both passes
@@ -579,7 +804,7 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
 __device__ unsigned long long g_lbfgs_bytes;
 
 template <int CT, typename HT>
-__global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float> a, float *MSY, float *MYY,
+__global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float> a, float *MRI, float *MYY,
                                                                 int count_bytes) {
     constexpr int MAP = sizeof(HT) == 2;  // coordinate mapping (see Vec)
     __shared__ Shared<CT> sh;
@@ -588,8 +813,16 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
     if (threadIdx.x == 0) {
         sh.ring = dyn;
         sh.ld = mm_ld(m);
-        sh.R = reinterpret_cast<float *>(dyn + Cfg<CT>::RING_F4);
-        sh.YY = sh.R + (size_t)m * sh.ld;
+        sh.RI = reinterpret_cast<float *>(dyn + Cfg<CT>::RING_F4);
+        sh.YY = sh.RI + (size_t)m * sh.ld;
+        sh.p1 = sh.YY + (size_t)m * sh.ld;
+        sh.u1 = sh.p1 + p1_floats<CT>(m);
+        sh.u2 = sh.u1 + m;
+        sh.ca = sh.u2 + m;
+        sh.cw = sh.ca + m;
+        sh.dg = sh.cw + m;
+        sh.nr = sh.dg + m;
+        sh.zero16 = make_uint4(0u, 0u, 0u, 0u);
     }
     __syncthreads();
     const int n_act = *a.n_act;
@@ -650,8 +883,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                 }
                 store_hist<CT, MAP, HT>(s4, reinterpret_cast<HT *>(a.S) + ((size_t)w * m + slot) * d, d);
                 store_hist<CT, MAP, HT>(y4, reinterpret_cast<HT *>(a.Y) + ((size_t)w * m + slot) * d, d);
-                if (threadIdx.x == 0) a.rho[(size_t)w * m + slot] = 1.f / r4[3];
-                bytes += (uint64_t)2 * d * sizeof(HT) + 4;
+                bytes += (uint64_t)2 * d * sizeof(HT);
                 new_slot = slot;
                 s_new = s4;
                 y_new = y4;
@@ -677,7 +909,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                 st.count = 0;
                 st.head = 0;
                 st.attempt = 1;
-                bytes += direction<CT, HT>(a, w, st, -1, g, x, s_new, y_new, MSY, MYY, sh, par);
+                bytes += direction<CT, HT>(a, w, st, -1, g, x, s_new, y_new, MRI, MYY, sh, par);
             } else {
                 st.status = SB_WALKER_STALLED;
             }
@@ -691,18 +923,21 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                 st.status = SB_WALKER_MAXITER;
             } else {
                 st.attempt = 0;
-                bytes += direction<CT, HT>(a, w, st, new_slot, g, x, s_new, y_new, MSY, MYY, sh, par);
+                bytes += direction<CT, HT>(a, w, st, new_slot, g, x, s_new, y_new, MRI, MYY, sh, par);
             }
         }
         if (threadIdx.x == 0) a.st[w] = st;
-        __syncthreads();  // shared scratch (slot_of, m x m matrices) is reused by the next walker
+        // No barrier before the next walker: a thread's ring chunks are read by
+        // other lanes only in pass 1, which ends with a CTA barrier. The reduction
+        // scratch alternates, and every other shared array is rewritten only
+        // after the next walker's first reduction barrier.
     }
     if (count_bytes && threadIdx.x == 0 && bytes) atomicAdd(&g_lbfgs_bytes, (unsigned long long)bytes);
 }
 
 }  // namespace
 
-void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *MYY, int num_sms, bool bf16_history,
+void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *MYY, int num_sms, bool bf16_history,
                            cudaStream_t s) {
     ProfScope prof(PROF_LBFGS_STEP, s);
     const int count_bytes = prof_enabled() ? 1 : 0;
@@ -719,9 +954,9 @@ void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *
     }
     note_launch();
     if (bf16_history)
-        k_lbfgs_cta<kCT, __nv_bfloat16><<<grid, kCT, dyn, s>>>(a, MSY, MYY, count_bytes);
+        k_lbfgs_cta<kCT, __nv_bfloat16><<<grid, kCT, dyn, s>>>(a, MRI, MYY, count_bytes);
     else
-        k_lbfgs_cta<kCT, float><<<grid, kCT, dyn, s>>>(a, MSY, MYY, count_bytes);
+        k_lbfgs_cta<kCT, float><<<grid, kCT, dyn, s>>>(a, MRI, MYY, count_bytes);
 }
 
 double lbfgs_bytes_take() {

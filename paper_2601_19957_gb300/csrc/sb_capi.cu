@@ -139,7 +139,7 @@ struct DiscoverWs {
 template <typename T>
 struct RefineWs {
     LbfgsArgs<T> lb;
-    float *MSY, *MYY;  // [N][m][m] S^T Y and Y^T Y (FP32 compact-form step)
+    float *MRI, *MYY;  // [N][m][m] R^-1 (R = upper(S^T Y)) and Y^T Y, slot-indexed (FP32 compact-form step)
     int64_t *n_evals;
     double *qpart, *Z, *R;  // FP64 evaluation
     TcWs tc;                // mixed-precision evaluation
@@ -200,7 +200,7 @@ void carve_refine(Carver &cv, RefineWs<T> &r, int n, int d, int K, int m, bool f
         r.R = cv.take<double>((size_t)n * K);
     } else {
         carve_tc(cv, r.tc, n, d, K, prec);
-        r.MSY = cv.take<float>((size_t)n * m * m);
+        r.MRI = cv.take<float>((size_t)n * m * m);
         r.MYY = cv.take<float>((size_t)n * m * m);
     }
 }
@@ -403,7 +403,7 @@ void step_round<double>(const RefineWs<double> &, const LbfgsArgs<double> &a, in
 template <>
 void step_round<float>(const RefineWs<float> &r, const LbfgsArgs<float> &a, int n, cudaStream_t s) {
     // compact form, CTA per walker
-    launch_lbfgs_step_cta(a, n, r.MSY, r.MYY, device_sms(), kBf16History, s);
+    launch_lbfgs_step_cta(a, n, r.MRI, r.MYY, device_sms(), kBf16History, s);
 }
 
 template <typename T>

@@ -25,7 +25,7 @@ struct LbfgsArgs {
     int d, m, max_iter, max_backtracks;
     T c1, backtrack, gtol;
     T *X, *G, *P, *XT, *GT, *FT;  // [N][d] (FT: [N])
-    T *S, *Y, *rho;               // [N][m][d], [N][m][d], [N][m]
+    T *S, *Y, *rho;               // [N][m][d], [N][m][d], [N][m]: 1 / s^T y (two-loop step) or s^T y (CTA step)
     WalkerState<T> *st;           // [N]
     int32_t *act;                 // [N] active walker ids
     int32_t *n_act;               // device scalar
@@ -39,8 +39,9 @@ void launch_lbfgs_step(const LbfgsArgs<T> &a, int n, cudaStream_t s);
 template <typename T>
 void launch_lbfgs_compact(const LbfgsArgs<T> &a, int64_t *n_evals, cudaStream_t s);
 // FP32 step, one CTA per walker, compact-representation direction (lbfgs_cta.cu).
-// With d % 4 == 0 and a.err set, the stored pairs are streamed by bulk copies.
-void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MSY, float *MYY, int num_sms, bool bf16_history,
+// MRI, MYY: per-walker [N][m][m] R^-1 (R = upper(S^T Y)) and Y^T Y, slot-indexed;
+// bf16_history stores the pairs in bf16.
+void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *MYY, int num_sms, bool bf16_history,
                            cudaStream_t s);
 // Algorithmic bytes moved by the FP32 step launches while profiling was on
 // (synchronises the device, then clears the counter); -1 on a CUDA error.

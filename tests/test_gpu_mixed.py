@@ -11,7 +11,7 @@ torch = pytest.importorskip("torch")
 
 import oracle
 import paper_2601_19957_gb300 as sb
-from paper_2601_19957_gb300.instances import workload
+from paper_2601_19957_gb300.instances import SolveConfig, make_instance, workload
 
 pytestmark = pytest.mark.gpu
 
@@ -83,6 +83,19 @@ def test_mixed_evidence_d1024_k8_scaled(prec):
     inst = insts[0]
     c.prec = prec
     c.cand_cap = 64
+    out = sb.evidence(sb.Problem(inst), sb.make_config(c))
+    assert out.n_modes >= 1
+    _check_modes_against_components(inst, out)
+
+
+@pytest.mark.parametrize("prec", [sb.PREC_BF16, sb.PREC_TF32])
+@pytest.mark.parametrize("d,m", [(37, 7), (300, 20), (1000, 13)])
+def test_mixed_evidence_ragged_dimension(prec, d, m):
+    """Dimensions off the 8- and 16-coordinate grid (rows copied with zero padding,
+    k-steps cut by d, warps with no coordinates) and history lengths off the
+    4-pair groups: every mode found is a true component with its exact Laplace term."""
+    inst = make_instance(d, 3, 7000 + d, s_range=(0.05, 0.5), mean_box=(-6, 6), sep=8.0)
+    c = SolveConfig(n_rays=256, n_steps=32, n_starts=256, m=m, seed=7000 + d, prec=prec)
     out = sb.evidence(sb.Problem(inst), sb.make_config(c))
     assert out.n_modes >= 1
     _check_modes_against_components(inst, out)
