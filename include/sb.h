@@ -154,13 +154,17 @@ sb_status sb_refine(const sb_problem *prob, const sb_config *cfg, const double *
 /*
  * Laplace stage in FP64 (Sec. 3.6.4 filters, Sec. 3.7.1 Laplace, App. A.8, A.10):
  * coarse L-inf dedup of the walkers (x, ell, status), FP64 Newton polish with
- * the analytic Hessian H = -hess l and its Cholesky factor, positive-definite /
+ * the analytic Hessian H = -hess l and its Cholesky factor (at most
+ * newton_steps steps; a candidate whose step is below 1e-11 (1 + |x|_inf) in
+ * max norm has converged and stays put, and the polish ends once none moves),
+ * positive-definite /
  * gradient / in-box filters, final dedup, log Z_k = l(x*) + (d/2) log 2pi -
  * sum_i log C_ii (H = C C^T), log Z = LSE_k log Z_k - log V.
  * status may be NULL (all walkers eligible). modes: [cap][d]; logZk, ell_modes:
  * [cap] (ell_modes may be NULL); n_modes: int32 device scalar; logZ: device scalar.
- * Modes are ordered by decreasing l. Synchronises `stream` once (the host reads
- * the number of coarse candidates to size the candidate kernels' grids); zero
+ * Modes are ordered by decreasing l. Synchronises `stream` once to read the
+ * number of coarse candidates (it sizes the candidate kernels' grids) and once
+ * per Newton step to read how many candidates still move; zero
  * modes give logZ = -inf and set SB_ERR_NO_MODES in the status word.
  */
 sb_status sb_laplace(const sb_problem *prob, const sb_config *cfg, const double *x, const double *ell,

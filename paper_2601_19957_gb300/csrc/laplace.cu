@@ -584,22 +584,50 @@ __global__ void __launch_bounds__(CS_THREADS) k_chol_solve_coop(int d, int Gc, c
 }
 
 // ------------------------------------------------------------------ Newton line search
-// mode 0: start (t = 1, trial = x + delta, searching = active & Cholesky ok)
+// mode 0: start (t = 1, trial = x + delta, searching = active & Cholesky ok).
+//   A candidate whose Newton step is already below kNewtonXtol (1 + |x|_inf) in
+//   max norm has converged: it stays where it is (its H factor is the one at
+//   that point) and stops polishing; the others are counted in *n_live.
 // mode 1: decide on the evaluated trial (accept if l_t >= l, else halve)
+constexpr double kNewtonXtol = 1e-11;
 __global__ void __launch_bounds__(256) k_newton_ls(int d, int mode, const int32_t *n_c, const int32_t *info,
                                                    uint8_t *active, uint8_t *searching, int32_t *halvings, double *t,
                                                    double *XC, double *LC, const double *delta, double *XN,
-                                                   const double *LN, const double *pred) {
+                                                   const double *LN, const double *pred, int32_t *n_live) {
     const int c = blockIdx.x;
     if (c >= *n_c) return;
     __shared__ int s_act;
+    __shared__ double s_mx[2][8];
+    bool small = false;
+    if (mode == 0) {  // max |delta| and max |x| of the candidate
+        double md = 0.0, mx = 0.0;
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            md = fmax(md, fabs(delta[(size_t)c * d + i]));
+            mx = fmax(mx, fabs(XC[(size_t)c * d + i]));
+        }
+        md = warp_max(md);
+        mx = warp_max(mx);
+        if ((threadIdx.x & 31) == 0) {
+            s_mx[0][threadIdx.x >> 5] = md;
+            s_mx[1][threadIdx.x >> 5] = mx;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 1; q < 8; ++q) {
+                md = fmax(md, s_mx[0][q]);
+                mx = fmax(mx, s_mx[1][q]);
+            }
+            small = md <= kNewtonXtol * (1.0 + mx);
+        }
+    }
     if (threadIdx.x == 0) {
         int act = 0;
         if (mode == 0) {
-            const int s = active[c] && !info[c];
+            const int s = active[c] && !info[c] && !small;
             if (!s) active[c] = 0;
             halvings[c] = 0;
             t[c] = 1.0;
+            if (s) atomicAdd(n_live, 1);
             if (s && pred[c] <= 1e-10 * (1.0 + fabs(LC[c]))) {
                 // quadratic-convergence regime: the descent test is rounding noise, take t = 1
                 searching[c] = 0;
@@ -851,10 +879,10 @@ void launch_chol_solve_coop(int d, int nc, const double *H, const double *g, con
 
 void launch_newton_ls(int d, int cap, int mode, const int32_t *n_c, const int32_t *info, uint8_t *active,
                       uint8_t *searching, int32_t *halvings, double *t, double *XC, double *LC, const double *delta,
-                      double *XN, const double *LN, const double *pred, cudaStream_t s) {
+                      double *XN, const double *LN, const double *pred, int32_t *n_live, cudaStream_t s) {
     note_launch();
     k_newton_ls<<<cap, 256, 0, s>>>(d, mode, n_c, info, active, searching, halvings, t, XC, LC, delta, XN, LN,
-                                    pred);
+                                    pred, n_live);
 }
 
 void launch_ls_batch_setup(int d, int cap, const int32_t *n_c, const uint8_t *searching, const double *XC,

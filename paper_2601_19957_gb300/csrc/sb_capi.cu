@@ -153,6 +153,7 @@ struct LaplaceWs {
     int32_t *dd_i;
     uint32_t *dd_bar;
     int32_t *p_done, *p_need;  // [K] P_k formed / to form now
+    int32_t *n_live;           // candidates still moving in a Newton step
 };
 
 struct EvidenceWs {
@@ -254,6 +255,7 @@ Layout layout(void *base, const sb_problem *p, const sb_config *c) {
     la.dd_bar = cv.take<uint32_t>(2);
     la.p_done = cv.take<int32_t>(kMaxK);
     la.p_need = cv.take<int32_t>(kMaxK);
+    la.n_live = cv.take<int32_t>(1);
     la.XC = cv.take<double>((size_t)cap * d);
     la.LC = cv.take<double>(cap);
     la.GC = cv.take<double>((size_t)cap * d);
@@ -530,14 +532,22 @@ sb_status run_laplace(const ProbView &pv, const sb_config *c, const Layout &L, c
         launch_hessian_chol(d, K, nc, pv.L, la.P, la.Z, la.R, la.GC, la.n_reps, la.GK, la.H, la.info, s);
     };
     eval_full();
+    // Newton polish, at most newton_steps steps; it ends early once every
+    // candidate's step is below the convergence threshold (one host read of the
+    // count of candidates still moving per step)
     for (int step = 0; step < c->newton_steps; ++step) {
         launch_chol_solve_coop(d, nc, la.H, la.GC, la.n_reps, la.info, la.active, la.delta, la.pred, la.dd_bar,
                                pv.status, s);
+        SB_CUDA_TRY(cudaMemsetAsync(la.n_live, 0, sizeof(int32_t), s));
         launch_newton_ls(d, nc, 0, la.n_reps, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
-                         la.delta, la.XN, la.LN, la.pred, s);
+                         la.delta, la.XN, la.LN, la.pred, la.n_live, s);
+        int32_t h_live = 0;
+        SB_CUDA_TRY(cudaMemcpyAsync(&h_live, la.n_live, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SB_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h_live == 0) break;
         f64_points(pv, la.XN, nullptr, la.n_reps, nc, la.qpart, nullptr, nullptr, la.LN, nullptr, s);
         launch_newton_ls(d, nc, 1, la.n_reps, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
-                         la.delta, la.XN, la.LN, la.pred, s);
+                         la.delta, la.XN, la.LN, la.pred, la.n_live, s);
         launch_ls_batch_setup(d, nc, la.n_reps, la.searching, la.XC, la.delta, la.XN2, la.rows2, la.n_rows2, s);
         f64_points(pv, la.XN2, la.rows2, la.n_rows2, nc * (kHalvings - 1), la.qpart2, nullptr, nullptr, la.LN2,
                    nullptr, s);

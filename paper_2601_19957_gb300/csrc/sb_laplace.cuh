@@ -33,9 +33,12 @@ void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P
 void launch_chol_solve_coop(int d, int nc, const double *H, const double *g, const int32_t *n_c, const int32_t *info,
                             const uint8_t *active, double *delta, double *pred, uint32_t *bar, int32_t *err,
                             cudaStream_t s);
+// Newton line search: mode 0 starts it (t = 1) for the candidates still polishing
+// and counts them in *n_live (a candidate whose step is below 1e-11 (1 + |x|_inf)
+// in max norm has converged and stops where it is); mode 1 decides on the trial.
 void launch_newton_ls(int d, int cap, int mode, const int32_t *n_c, const int32_t *info, uint8_t *active,
                       uint8_t *searching, int32_t *halvings, double *t, double *XC, double *LC, const double *delta,
-                      double *XN, const double *LN, const double *pred, cudaStream_t s);
+                      double *XN, const double *LN, const double *pred, int32_t *n_live, cudaStream_t s);
 // Batched halvings h = 1..kHalvings-1 for the candidates still searching after t = 1.
 void launch_ls_batch_setup(int d, int cap, const int32_t *n_c, const uint8_t *searching, const double *XC,
                            const double *delta, double *XN2, int32_t *rows2, int32_t *n_rows2, cudaStream_t s);
