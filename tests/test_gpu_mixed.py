@@ -99,3 +99,25 @@ def test_mixed_evidence_ragged_dimension(prec, d, m):
     out = sb.evidence(sb.Problem(inst), sb.make_config(c))
     assert out.n_modes >= 1
     _check_modes_against_components(inst, out)
+
+
+@pytest.mark.parametrize("prec", [sb.PREC_BF16, sb.PREC_TF32])
+@pytest.mark.parametrize("d,m", [(64, 5), (300, 20), (1024, 20)])
+def test_mixed_refine_reaches_gaussian_mean(prec, d, m):
+    """The FP32 L-BFGS step on its own (bf16 pairs, tensor-core inner products, R^-1
+    kept per walker; no FP64 polish to hide a poor direction): from uniform starts in
+    the box every walker of a single Gaussian ends CONVERGED or STALLED within one
+    standard deviation of the mean, |L^T (x - mu)|_2 <= 1, where FP32 f stops
+    resolving progress (f ~ 1e3, so |z|^2 is resolved to ~1e-4)."""
+    inst = make_instance(d, 1, 8100 + d, s_range=(0.05, 0.5), mean_box=(-6, 6))
+    n = 64
+    c = SolveConfig(n_rays=n, n_steps=1, n_starts=n, m=m, seed=8100 + d, prec=prec)
+    x0 = np.random.default_rng(8100 + d).uniform(-10.0, 10.0, size=(n, d))
+    out = sb.refine(sb.Problem(inst), sb.make_config(c), torch.as_tensor(x0, device="cuda"))
+    st = out.status.cpu().numpy()
+    assert set(st.tolist()) <= {sb.CONVERGED, sb.STALLED}
+    x = out.x.cpu().numpy()
+    z = (x - inst.mu[0]) @ inst.L[0]  # rows: (L^T (x - mu))^T
+    assert np.sqrt((z * z).sum(1)).max() <= 1.0
+    peak = oracle.loglik(inst, inst.mu[0])
+    assert (peak - out.ell.cpu().numpy()).max() <= 0.5 + 1e-3 * abs(peak)
