@@ -135,10 +135,17 @@ class TensorProblem:
         self.s = _Problem(self.d, self.K, *[t.data_ptr() for t in self.tensors])
 
 
-def host_problem(inst: Instance):
-    """C struct pointing at host numpy arrays (for sb_evidence_host); keeps them alive."""
+def host_problem(inst: Instance, pinned: bool = False):
+    """C struct pointing at host arrays (for sb_evidence_host); keeps them alive.
+    pinned=True places them in page-locked memory (torch pinned tensors)."""
     arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (inst.log_w, inst.mu, inst.L, inst.lo, inst.hi)]
-    s = _Problem(int(inst.d), int(inst.K), *[a.ctypes.data for a in arrs])
+    if pinned:
+        torch = _torch()
+        arrs = [torch.from_numpy(a).pin_memory() for a in arrs]
+        ptrs = [a.data_ptr() for a in arrs]
+    else:
+        ptrs = [a.ctypes.data for a in arrs]
+    s = _Problem(int(inst.d), int(inst.K), *ptrs)
     return s, arrs
 
 
@@ -282,14 +289,33 @@ def evidence_host_workspace(inst: Instance, cfg: _Config) -> Workspace:
     return Workspace(lib().sb_evidence_host_workspace_bytes(C.byref(s), C.byref(cfg)))
 
 
-def evidence_host(inst: Instance, cfg: _Config, ws: Workspace, stream=None):
-    """The whole path on HOST arrays: copies in, solves, copies log Z and the modes out."""
-    s, keep = host_problem(inst)
+class PinnedHost:
+    """Page-locked host copies of one instance and of the outputs of
+    sb_evidence_host, allocated once and reused across calls."""
+
+    def __init__(self, inst: Instance, cfg: _Config):
+        torch = _torch()
+        self.inst = inst
+        self.s, self.keep = host_problem(inst, pinned=True)
+        cap = cfg.cand_cap
+        pin = lambda *shape, dt=torch.float64: torch.zeros(*shape, dtype=dt).pin_memory()
+        self.lz, self.nm = pin(1), pin(1, dt=torch.int32)
+        self.modes, self.zk = pin(cap, inst.d), pin(cap)
+
+
+def evidence_host(inst: Instance, cfg: _Config, ws: Workspace, stream=None, host: PinnedHost = None):
+    """The whole path on HOST arrays: copies in, solves, copies log Z and the modes out.
+    With `host` (a PinnedHost of this instance) the arrays are page-locked."""
     cap = cfg.cand_cap
-    lz = np.zeros(1)
-    nm = np.zeros(1, dtype=np.int32)
-    modes = np.zeros((cap, inst.d))
-    zk = np.zeros(cap)
+    if host is not None:
+        s, keep = host.s, None
+        lz, nm, modes, zk = host.lz.numpy(), host.nm.numpy(), host.modes.numpy(), host.zk.numpy()
+    else:
+        s, keep = host_problem(inst)
+        lz = np.zeros(1)
+        nm = np.zeros(1, dtype=np.int32)
+        modes = np.zeros((cap, inst.d))
+        zk = np.zeros(cap)
     code = lib().sb_evidence_host(C.byref(s), C.byref(cfg), lz.ctypes.data_as(C.c_void_p),
                                   modes.ctypes.data_as(C.c_void_p), zk.ctypes.data_as(C.c_void_p), C.c_int32(cap),
                                   nm.ctypes.data_as(C.c_void_p), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream))
@@ -297,7 +323,7 @@ def evidence_host(inst: Instance, cfg: _Config, ws: Workspace, stream=None):
         raise SbError(code, "sb_evidence_host")
     del keep
     k = min(int(nm[0]), cap)
-    return float(lz[0]), modes[:k], zk[:k], int(nm[0])
+    return float(lz[0]), modes[:k].copy(), zk[:k].copy(), int(nm[0])
 
 
 def evidence_backward(prob, modes, logZk, n_modes: int, grad_logZ: float = 1.0, stream=None):

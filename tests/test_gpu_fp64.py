@@ -177,12 +177,14 @@ def test_evidence_low_d(d, K):
     assert abs(out.logZ - ref.logZ) <= 1e-10 * abs(ref.logZ)
 
 
-def test_evidence_host_buffers_closed_form():
+@pytest.mark.parametrize("pinned", [False, True])
+def test_evidence_host_buffers_closed_form(pinned):
     insts, c = workload(0)
     inst = insts[0]
     cfg = sb.make_config(c)
     ws = sb.evidence_host_workspace(inst, cfg)
-    logZ, modes, zk, nm = sb.evidence_host(inst, cfg, ws)
+    host = sb.PinnedHost(inst, cfg) if pinned else None
+    logZ, modes, zk, nm = sb.evidence_host(inst, cfg, ws, host=host)
     assert nm == 1
     assert abs(math.expm1(logZ + _logV(inst))) < 1e-10
     assert np.abs(modes[0] - inst.mu[0]).max() < 1e-12
