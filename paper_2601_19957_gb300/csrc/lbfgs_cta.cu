@@ -775,10 +775,11 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
         // the two-loop recursion's history traffic: each pair read in both passes
         bytes += (uint64_t)4 * count * d * sizeof(HT);
     }
-    float dp[1];
+    float dp[2];  // grad f . p and |p|^2
     if (count > 0) {
         dp[0] = dotv(g, p);
-        block_sum<CT, 1>(dp, sh.red2[par++ & 1]);
+        dp[1] = dotv(p, p);
+        block_sum<CT, 2>(dp, sh.red2[par++ & 1]);
     }
     if (count == 0 || !(dp[0] < 0.f)) {
         st.count = 0;
@@ -790,9 +791,11 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
         for (int q = 0; q < Cfg<CT>::VPT; ++q)
             p.v[q] = make_float4(-g.v[q].x / gn, -g.v[q].y / gn, -g.v[q].z / gn, -g.v[q].w / gn);
         dp[0] = dotv(g, p);
-        block_sum<CT, 1>(dp, sh.red2[par++ & 1]);
+        dp[1] = dotv(p, p);
+        block_sum<CT, 2>(dp, sh.red2[par++ & 1]);
     }
     st.dphi = dp[0];
+    st.pn = sqrtf(dp[1]);
     st.alpha = 1.f;
     st.bt = 0;
     p.store(a.P + (size_t)w * d, d);
@@ -832,6 +835,8 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
         const int w = a.act[n];
         WalkerState<float> st = a.st[w];  // same address in every thread: one broadcast load
         const float ft = a.FT[w];
+        const float alpha0 = st.alpha, pn0 = st.pn;
+        float dnext = -1.f;  // bound on |new trial - this visit's trial| (see k_tc_need)
         float *X = a.X + (size_t)w * d;
         float *G = a.G + (size_t)w * d;
         Vec<CT, MAP> x, g, xt, gt;
@@ -905,11 +910,13 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                 p.load(a.P + (size_t)w * d, d);
                 lincomb(x, st.alpha, p).store(a.XT + (size_t)w * d, d);
                 bytes += (uint64_t)8 * d;
+                dnext = (alpha0 - st.alpha) * st.pn;
             } else if (st.count > 0 && st.attempt == 0) {
                 st.count = 0;
                 st.head = 0;
                 st.attempt = 1;
                 bytes += direction<CT, HT>(a, w, st, -1, g, x, s_new, y_new, MRI, MYY, sh, par);
+                dnext = st.pn + alpha0 * pn0;  // from the old trial back to x, then out
             } else {
                 st.status = SB_WALKER_STALLED;
             }
@@ -924,9 +931,13 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
             } else {
                 st.attempt = 0;
                 bytes += direction<CT, HT>(a, w, st, new_slot, g, x, s_new, y_new, MRI, MYY, sh, par);
+                dnext = st.pn;  // x is this visit's trial
             }
         }
-        if (threadIdx.x == 0) a.st[w] = st;
+        if (threadIdx.x == 0) {
+            a.st[w] = st;
+            if (a.dist && dnext >= 0.f) a.dist[w] = dnext * 1.0001f;  // margin for the rounding of |p|
+        }
         // No barrier before the next walker: a thread's ring chunks are read by
         // other lanes only in pass 1, which ends with a CTA barrier. The reduction
         // scratch alternates, and every other shared array is rewritten only

@@ -7,6 +7,7 @@
 #include <atomic>
 #include <mutex>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "sb_adjoint.cuh"
@@ -404,8 +405,11 @@ void step_round<double>(const RefineWs<double> &, const LbfgsArgs<double> &a, in
 }
 template <>
 void step_round<float>(const RefineWs<float> &r, const LbfgsArgs<float> &a, int n, cudaStream_t s) {
-    // compact form, CTA per walker
-    launch_lbfgs_step_cta(a, n, r.MRI, r.MYY, device_sms(), kBf16History, s);
+    // compact form, CTA per walker; it leaves the trial-point distance bounds the
+    // next round's component skip reads
+    LbfgsArgs<float> b = a;
+    b.dist = (float *)r.tc.p[kTcDistSlot];
+    launch_lbfgs_step_cta(b, n, r.MRI, r.MYY, device_sms(), kBf16History, s);
 }
 
 template <typename T>
@@ -425,6 +429,7 @@ sb_status run_refine(const ProbView &pv, const sb_config *c, const RefineWs<T> &
     rr.lb = a;
     int64_t *ev = n_evals ? n_evals : r.n_evals;
     launch_lbfgs_init<T>(n, pv.d, starts, a, ev, s);
+    if constexpr (std::is_same<T, float>::value) tc_walkers_reset(r.tc, n, s);
     // every accepted step takes at most 2 (max_backtracks + 1) rounds
     const int64_t cap_rounds = 2 + (int64_t)(c->max_iter + 1) * 2 * (c->max_backtracks + 2);
     int64_t round = 0;
@@ -590,6 +595,7 @@ sb_status prelude(const sb_problem *p, const sb_config *c, void *ws, size_t ws_b
         st = tc_prepare(out.pv, out.L.di.tc, out.s);
         if (st != SB_OK) return st;
         for (int i = 0; i < 4; ++i) out.L.r32.tc.p[i] = out.L.di.tc.p[i];
+        out.L.r32.tc.p[15] = out.L.di.tc.p[15];  // |L_k|_F
         out.L.r32.tc.mapT = out.L.di.tc.mapT;
         out.L.r32.tc.mapB = out.L.di.tc.mapB;
         out.L.r32.tc.bn = out.L.di.tc.bn;

@@ -18,6 +18,7 @@ struct WalkerState {
     int8_t attempt; // 0 first line search of the iteration, 1 retry without history
     int8_t flat;    // consecutive accepted steps without a decrease of f
     int8_t pad[2];
+    T pn;           // |p| of the current direction (CTA step)
 };
 
 template <typename T>
@@ -30,6 +31,7 @@ struct LbfgsArgs {
     int32_t *act;                 // [N] active walker ids
     int32_t *n_act;               // device scalar
     int32_t *err;                 // device status word (SB_DEV_TIMEOUT from bounded waits), may be null
+    T *dist;                      // [N] upper bound on |new trial - previous trial| (CTA step), may be null
 };
 
 template <typename T>

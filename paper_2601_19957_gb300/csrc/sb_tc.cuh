@@ -10,7 +10,7 @@ namespace sb {
 // FP32 means and box centre, z rows, |z|^2 partials, responsibilities, and the
 // TMA descriptors of the two L_k copies (host-side, rebuilt per call).
 struct TcWs {
-    void *p[16];
+    void *p[20];
     size_t rows;
     int prec, bn, d, K, ldz;
     CUtensorMap mapT, mapB;    // B operands: L_k^T (GEMM1) and L_k (GEMM2)
@@ -32,6 +32,10 @@ sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s);
 // u32 [n_rays][d]; chunks of the scratch row capacity.
 sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const float *u32,
                         const double *texit, double *ell_all, cudaStream_t s);
+// Clears the per-walker bounds of the component skip (before a refinement).
+void tc_walkers_reset(const TcWs &t, int n, cudaStream_t s);
+// Slot of TcWs.p holding the per-walker distance bound the L-BFGS step writes.
+constexpr int kTcDistSlot = 14;
 void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, const float *XT, const int32_t *act,
                      const int32_t *n_act, int n, float *FT, float *GT, cudaStream_t s);
 sb_status tc_loglik_points(const ProbView &pv, const sb_config *c, const TcWs &t, const double *x, int n, float *f,

@@ -8,6 +8,9 @@
 // g_n is grad f for f = -l (Sec. 3.2 likelihood, analytic gradient for App. A.5).
 //
 // Data flow per evaluation round:
+//   k_tc_need     (walker rounds) the (128-row block, component) pairs whose term
+//                 can still reach l, from per-walker bounds on |z_k| and on the
+//                 largest term (a skipped term is below FP32 resolution: exactly 0)
 //   k_tc_center   A1[k][n][:] = round(x_n - mu_k), formed in FP32 (walkers gathered
 //                 through the active list, or ray samples c + t u), bf16 or tf32
 //   k_tc_gemm ZR  z = A1 L_k (GEMM1): |z|^2 partials only
@@ -75,6 +78,7 @@ struct TcArgs {
     float *qpart;           // [rows][K][n_ntile]
     const float *R;         // [rows][K]
     const uint32_t *rflag;  // [row blocks][K]: some row of the block has r_nk > 0
+    const uint32_t *zmask;  // [row blocks][K]: GEMM1 |z|^2 pairs to visit (null: all; see k_tc_need)
     int prof;               // profiling class of the launch (-1: by mode)
     float *G;               // [walkers][d] grad f
     int n_ntile;
@@ -219,9 +223,10 @@ __device__ __forceinline__ TileInfo decode_tile(int t, int d, int K, const uint3
         ti.c_lo = (ti.nt * BN) / KC;
         ti.c_hi = (d + KC - 1) / KC;
         ti.nchunks = ti.c_hi - ti.c_lo;
-        // store pass (flags given): only the (block, component) pairs GEMM2 reads
-        // (already the case for a compacted schedule)
-        if (MODE == MODE_ZW && rflag && !glist) ti.skip = !((block_kmask(rflag, ti.mb, K) >> ti.k) & 1u);
+        // store pass (flags given): only the (block, component) pairs GEMM2 reads;
+        // |z|^2 pass (mask given): only the pairs k_tc_need keeps (already the case
+        // for a compacted schedule)
+        if (MODE != MODE_G && rflag && !glist) ti.skip = !((block_kmask(rflag, ti.mb, K) >> ti.k) & 1u);
     }
     return ti;
 }
@@ -261,7 +266,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
     volatile int *s_abort = reinterpret_cast<volatile int *>(s_tmem + 1);
     int *s_wcnt = const_cast<int *>(s_abort) + 1;  // [8] per-warp counts (group compaction)
     int *s_gcount = s_wcnt + 8;
-    int *s_glist = s_gcount + 1;                  // [kMaxGroupList] GEMM1 store pass: groups to visit
+    int *s_glist = s_gcount + 1;                  // [kMaxGroupList] GEMM1 with a mask: groups to visit
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int d = a.d, K = a.K;
@@ -273,13 +278,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
     // order, so that the round-robin deal spreads the work that remains (a
     // fixed stride over all groups would hand every CTA the same component).
     const int n_groups = n_mblk * K;
-    const bool compact = MODE == MODE_ZW && a.rflag != nullptr && n_groups <= kMaxGroupList;
+    // (row block, component) pairs to visit: GEMM2's flags for the store pass, the
+    // component-skip mask for the |z|^2 pass
+    const uint32_t *gmask = MODE == MODE_ZW ? a.rflag : (MODE == MODE_ZR ? a.zmask : nullptr);
+    const bool compact = MODE != MODE_G && gmask != nullptr && n_groups <= kMaxGroupList;
     if (compact) {
         if (threadIdx.x == 0) *s_gcount = 0;
         __syncthreads();
         for (int g0 = 0; g0 < n_groups; g0 += (int)blockDim.x) {
             const int g = g0 + (int)threadIdx.x;
-            const bool act = g < n_groups && ((block_kmask(a.rflag, g / K, K) >> (g % K)) & 1u);
+            const bool act = g < n_groups && ((block_kmask(gmask, g / K, K) >> (g % K)) & 1u);
             const unsigned bal = __ballot_sync(0xffffffffu, act);
             if (lane == 0) s_wcnt[warp] = __popc(bal);
             __syncthreads();
@@ -331,7 +339,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             uint32_t inflight_phase[8];
             int n_inflight = 0;
             for (int it = 0, t = tile_of(0, gsz); t < n_tiles && !*s_abort; t = tile_of(++it, gsz)) {
-                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag, glist, n_mblk);
+                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, MODE == MODE_G ? a.rflag : gmask, glist, n_mblk);
                 if (ti.skip) continue;
                 bool ok = true;
                 for (int q = 0; q < ti.nchunks; ++q) {
@@ -379,7 +387,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             uint32_t acc_phase = 0;
             bool issued = false;
             for (int it = 0, t = tile_of(0, gsz); t < n_tiles && !*s_abort; t = tile_of(++it, gsz)) {
-                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag, glist, n_mblk);
+                const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, MODE == MODE_G ? a.rflag : gmask, glist, n_mblk);
                 if (ti.skip) continue;
                 if (!bwait(&tempty[acc], acc_phase ^ 1, s_abort)) break;
                 tc_fence_after();
@@ -426,7 +434,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int it = 0, t = tile_of(0, gsz); t < n_tiles && !warp_aborted(s_abort); t = tile_of(++it, gsz)) {
-            const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, a.rflag, glist, n_mblk);
+            const TileInfo ti = decode_tile<MODE, BN, KC>(t, d, K, MODE == MODE_G ? a.rflag : gmask, glist, n_mblk);
             if (ti.skip) continue;
             if (!warp_bwait(&tfull[acc], acc_phase, s_abort)) break;
             tc_fence_after();
@@ -530,15 +538,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
 __global__ void __launch_bounds__(128) k_tc_lse(int mode, int K, int n_ntile, const int32_t *n_rows_dev,
                                                 int n_rows_max, const int32_t *act, const float *qpart,
                                                 const double *a_k, float *R, float *FT, double *ell,
-                                                uint32_t *rflag) {
+                                                uint32_t *rflag, const uint32_t *zmask, float *zb, int32_t *jst,
+                                                float *zst) {
     const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = n < n_rows;
+    // components the |z|^2 pass skipped for this row block (zmask): e_k = -inf
+    const uint32_t km = zmask ? block_kmask(zmask, n / BM, K) : 0xffffffffu;
     double e[kMaxK];
     double emax = -INFINITY;
     float s = 0.f;
     if (valid) {
         for (int k = 0; k < K; ++k) {
+            e[k] = -INFINITY;
+            if (!((km >> k) & 1u)) continue;
             const float *qp = qpart + ((size_t)n * K + k) * n_ntile;
             double q = 0.0;
             for (int t = 0; t < n_ntile; ++t) q += (double)qp[t];
@@ -546,6 +559,21 @@ __global__ void __launch_bounds__(128) k_tc_lse(int mode, int K, int n_ntile, co
             emax = fmax(emax, e[k]);
         }
         for (int k = 0; k < K; ++k) s += __expf((float)(e[k] - emax));
+    }
+    if (zb && valid) {
+        // bounds for the next round's skip (k_tc_need): |z_k| of the evaluated
+        // components, lowered by a 1/32 margin for the GEMM's rounding, and the
+        // largest term's |z|, raised by the same margin
+        const int w = act ? act[n] : n;
+        int jm = -1;
+        for (int k = 0; k < K; ++k) {
+            if (!((km >> k) & 1u)) continue;
+            const double q = (a_k[k] - e[k]) * 2.0;
+            if (isfinite(e[k])) zb[(size_t)w * K + k] = __double2float_rd(sqrt(fmax(q, 0.0)) * (1.0 - 1.0 / 32));
+            if (isfinite(e[k]) && e[k] == emax && jm < 0) jm = k;
+        }
+        jst[w] = jm;
+        if (jm >= 0) zst[w] = __double2float_ru(sqrt(fmax((a_k[jm] - e[jm]) * 2.0, 0.0)) * (1.0 + 1.0 / 32));
     }
     const double l = emax + (double)__logf(s);
     if (mode == 1) {
@@ -567,6 +595,71 @@ __global__ void __launch_bounds__(128) k_tc_lse(int mode, int K, int n_ntile, co
         ell[n] = l;
 }
 
+// Component skip of the walker rounds. e_k = a_k - |z_k|^2 / 2 with z_k = L_k^T (x - mu_k);
+// a component whose e_k lies more than kSkipNats below the largest term adds exp(-110)
+// < 2e-48 relative: below FP32 resolution, so the LSE's FP32 exponential and the
+// responsibility r_k it yields are exactly 0 and the component changes neither l
+// nor grad l. Per walker the round before leaves, for every component evaluated
+// there, |z_k| lowered by a 1/32 margin (zb), and the largest term's component j
+// with |z_j| raised by that margin (jst, zst); the L-BFGS step leaves an upper bound
+// D on the distance from that point to the new trial (dist). With |L_k^T v| <=
+// lnorm_k |v| (lnorm_k = |L_k|_F >= |L_k|_2):
+//   |z_k(new)| >= zb_k - lnorm_k D   (stored back as zb_k for a skipped component),
+//   e_j(new) >= a_j - (zst + lnorm_j D)^2 / 2 =: e_lb,
+// and the (row block, component) pair is visited unless every row of the block has
+// a_k - zb_k(new)^2 / 2 < e_lb - kSkipNats. The largest term's component is always
+// visited, so the LSE's maximum is at least e_lb.
+constexpr double kSkipNats = 110.0;
+__global__ void __launch_bounds__(128) k_tc_need(int K, const int32_t *n_rows_dev, int n_rows_max,
+                                                 const int32_t *act, const double *a_k, const float *lnorm, float *zb,
+                                                 const int32_t *jst, const float *zst, const float *dist,
+                                                 uint32_t *zmask) {
+    const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = n < n_rows;
+    const int w = valid ? (act ? act[n] : n) : 0;
+    const int j = valid ? jst[w] : -1;
+    const float D = valid ? dist[w] : 0.f;
+    const bool bounded = j >= 0 && D >= 0.f && isfinite(D);
+    double elb = 0.0;
+    if (bounded) {
+        const double ub = (double)__fmaf_ru(lnorm[j], D, zst[w]);
+        elb = a_k[j] - 0.5 * ub * ub;
+    }
+    for (int k = 0; k < K; ++k) {
+        bool need = valid;
+        if (bounded) {
+            const float b = fmaxf(__fmaf_rd(-lnorm[k], D, zb[(size_t)w * K + k]), 0.f);
+            zb[(size_t)w * K + k] = b;
+            need = !(a_k[k] - 0.5 * (double)b * (double)b < elb - kSkipNats);
+        }
+        const unsigned any = __ballot_sync(0xffffffffu, need);
+        if (any && (threadIdx.x & 31) == 0) atomicOr(&zmask[(size_t)(n / BM) * K + k], 1u);
+    }
+}
+
+// lnorm_k = |L_k|_F (an upper bound on |L_k|_2), rounded up to FP32: one CTA per
+// component, fixed-order sums.
+__global__ void __launch_bounds__(256) k_tc_lnorm(int d, const double *L, float *lnorm) {
+    const int k = blockIdx.x;
+    const double *Lk = L + (size_t)k * d * d;
+    double acc = 0.0;
+    for (int i = 0; i < d; ++i)
+        for (int j = threadIdx.x; j <= i; j += blockDim.x) {
+            const double v = Lk[(size_t)i * d + j];
+            acc = fma(v, v, acc);
+        }
+    __shared__ double part[8];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += part[q];
+        lnorm[k] = __double2float_ru(sqrt(t) * (1.0 + 1e-6));
+    }
+}
+
 // A operand of GEMM1: A1[k][n][i] = round(x_n[i] - mu_k[i]) formed in FP32; x_n is a
 // walker row (through the active list) or the ray sample c + t_j t_exit u_r.
 // Rows from n_rows up to the next multiple of 128 and columns >= d are zeroed.
@@ -577,7 +670,7 @@ __global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int K, i
                                                    const int32_t *n_rows_dev, int n_rows_max, const int32_t *act,
                                                    const float *X, int ld, const float *u32, const double *texit,
                                                    int n_steps, long long flat0, const float *mu32, const float *c32,
-                                                   void *A1) {
+                                                   void *A1, const uint32_t *zmask) {
     constexpr int VE = (PREC == SB_PREC_BF16) ? 8 : 4;  // elements per 16-byte store
     const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
     int rows_pad = (n_rows + BM - 1) / BM * BM;
@@ -632,7 +725,9 @@ __global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int K, i
             }
         }
     }
+    const uint32_t km = zmask ? block_kmask(zmask, n / BM, K) : 0xffffffffu;  // pairs the |z|^2 pass visits
     for (int k = 0; k < K; ++k) {
+        if (!((km >> k) & 1u)) continue;
         float v[VE];
 #pragma unroll
         for (int q = 0; q < VE; ++q) v[q] = 0.f;
@@ -760,7 +855,7 @@ template <int BN, int PREC, int MODE>
 constexpr int smem_bytes() {
     constexpr int STAGES = (BN >= 256) ? 4 : 6;
     return 1024 + STAGES * (BM * ROWB + BN * ROWB) + (2 * STAGES + 5) * 8 + 64 +
-           (MODE == MODE_ZW ? (9 + kMaxGroupList) * 4 : 0);
+           (MODE != MODE_G ? (9 + kMaxGroupList) * 4 : 0);
 }
 
 template <int BN, int PREC, int MODE>
@@ -806,7 +901,7 @@ void launch_gemm_any(int prec, int mode, int bn, const CUtensorMap &mapA, const 
 
 void launch_center(const TcWs &t, int ray_mode, int d, int K, const int32_t *n_rows_dev, int n_rows_max,
                    const int32_t *act, const float *X, const float *u32, const double *texit, int n_steps,
-                   long long flat0, cudaStream_t s) {
+                   long long flat0, cudaStream_t s, const uint32_t *zmask = nullptr) {
     const int ldp = ldp_of(d, t.prec);
     const int ncg = ldp / (t.prec == SB_PREC_BF16 ? 8 : 4);
     int rows = (n_rows_max + BM - 1) / BM * BM;
@@ -816,11 +911,11 @@ void launch_center(const TcWs &t, int ray_mode, int d, int K, const int32_t *n_r
     if (t.prec == SB_PREC_BF16)
         k_tc_center<SB_PREC_BF16><<<grid, 256, 0, s>>>(ray_mode, d, K, (int)t.rows, ldp, n_rows_dev, n_rows_max, act,
                                                       X, d, u32, texit, n_steps, flat0, (const float *)t.p[2],
-                                                      (const float *)t.p[3], t.p[9]);
+                                                      (const float *)t.p[3], t.p[9], zmask);
     else
         k_tc_center<SB_PREC_TF32><<<grid, 256, 0, s>>>(ray_mode, d, K, (int)t.rows, ldp, n_rows_dev, n_rows_max, act,
                                                       X, d, u32, texit, n_steps, flat0, (const float *)t.p[2],
-                                                      (const float *)t.p[3], t.p[9]);
+                                                      (const float *)t.p[3], t.p[9], zmask);
 }
 
 TcArgs base_args(const ProbView &pv, const TcWs &t) {
@@ -846,7 +941,10 @@ TcArgs base_args(const ProbView &pv, const TcWs &t) {
 bool tc_available(int prec) { return (prec == SB_PREC_BF16 || prec == SB_PREC_TF32) && encode_fn() != nullptr; }
 
 // Layout: [0] LT, [1] LB, [2] mu32, [3] c32, [4] Z [K][rows][ldz], [5] qpart, [6] R,
-// [7] X32 (points), [8] G32 (points), [9] A1 [K][rows][ldp] (centred GEMM1 operand)
+// [7] X32 (points), [8] G32 (points), [9] A1 [K][rows][ldp] (centred GEMM1 operand),
+// [10] rflag, and for the component skip of the walker rounds (k_tc_need):
+// [11] zb [rows][K], [12] jst [rows], [13] zst [rows], [14] dist [rows],
+// [15] lnorm [K], [16] zmask [row blocks][K]
 void carve_tc(Carver &cv, TcWs &t, int rows, int d, int K, int prec) {
     const int e = esz(prec), ldp = ldp_of(d, prec), bn = bn_of(d);
     const int nct = (d + 63) / 64;  // partials sized for the narrowest tile the tuner may pick
@@ -868,6 +966,12 @@ void carve_tc(Carver &cv, TcWs &t, int rows, int d, int K, int prec) {
     t.p[8] = cv.take<float>((size_t)rows * d);
     t.p[9] = cv.take<uint8_t>((size_t)K * rows * ldp * e);
     t.p[10] = cv.take<uint32_t>((size_t)(rows / BM) * K);
+    t.p[11] = cv.take<float>((size_t)rows * K);
+    t.p[12] = cv.take<int32_t>((size_t)rows);
+    t.p[13] = cv.take<float>((size_t)rows);
+    t.p[14] = cv.take<float>((size_t)rows);
+    t.p[15] = cv.take<float>((size_t)K);
+    t.p[16] = cv.take<uint32_t>((size_t)(rows / BM) * K);
 }
 
 int tc_ray_chunk(int d, int K, int64_t total) {
@@ -990,6 +1094,8 @@ sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s) {
         k_tc_convert_L<float><<<1184, 256, 0, s>>>(d, K, ldp, pv.L, (float *)t.p[0], (float *)t.p[1]);
     note_launch();
     k_tc_convert_vec<<<(K * d + 255) / 256, 256, 0, s>>>(d, K, pv.mu, pv.c, (float *)t.p[2], (float *)t.p[3]);
+    note_launch();
+    k_tc_lnorm<<<K, 256, 0, s>>>(d, pv.L, (float *)t.p[15]);
     if (!tc_maps_for_rows(t)) return SB_ERR_CUDA;
     t.bn = pick_tile(pv, t, s);
     if (!make_map(&t.mapT, t.p[0], d, d, K, ldp, t.prec, t.bn) || !make_map(&t.mapB, t.p[1], d, d, K, ldp, t.prec, t.bn))
@@ -1008,9 +1114,14 @@ sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, c
         launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
         note_launch();
         k_tc_lse<<<(rows + 127) / 128, 128, 0, s>>>(1, pv.K, a.n_ntile, nullptr, rows, nullptr, a.qpart, pv.a,
-                                                    nullptr, nullptr, ell_all + f0, nullptr);
+                                                    nullptr, nullptr, ell_all + f0, nullptr, nullptr, nullptr,
+                                                    nullptr, nullptr);
     }
     return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
+}
+
+void tc_walkers_reset(const TcWs &t, int n, cudaStream_t s) {
+    cudaMemsetAsync(t.p[12], 0xff, sizeof(int32_t) * (size_t)n, s);  // jst = -1: no bound yet
 }
 
 void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, const float *XT, const int32_t *act,
@@ -1021,15 +1132,25 @@ void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, cons
     a.n_rows_dev = n_act;
     a.n_rows_max = n;
     a.prof = PROF_TC_Z_WALKERS;
-    launch_center(t, 0, pv.d, pv.K, n_act, n, act, XT, nullptr, nullptr, 1, 0, s);
-    // |z|^2 for every component (no z stored), then l, r and the flags of the
-    // (row block, component) pairs with r > 0, then z again for those pairs only,
-    // stored as r z (GEMM2's A operand), then the gradient
+    // the (row block, component) pairs whose terms can still reach l (k_tc_need),
+    // then their centred operand and |z|^2 (no z stored), then l, r and the flags
+    // of the pairs with r > 0, then z again for those pairs only, stored as r z
+    // (GEMM2's A operand), then the gradient
+    uint32_t *zmask = (uint32_t *)t.p[16];
+    cudaMemsetAsync(zmask, 0, sizeof(uint32_t) * ((n + BM - 1) / BM) * pv.K, s);
+    note_launch();
+    k_tc_need<<<(n + 127) / 128, 128, 0, s>>>(pv.K, n_act, n, act, pv.a, (const float *)t.p[15], (float *)t.p[11],
+                                              (const int32_t *)t.p[12], (const float *)t.p[13],
+                                              (const float *)t.p[14], zmask);
+    launch_center(t, 0, pv.d, pv.K, n_act, n, act, XT, nullptr, nullptr, 1, 0, s, zmask);
+    a.zmask = zmask;
     launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
+    a.zmask = nullptr;
     cudaMemsetAsync(t.p[10], 0, sizeof(uint32_t) * ((n + BM - 1) / BM) * pv.K, s);
     note_launch();
     k_tc_lse<<<(n + 127) / 128, 128, 0, s>>>(0, pv.K, a.n_ntile, n_act, n, act, a.qpart, pv.a, (float *)t.p[6], FT,
-                                             nullptr, (uint32_t *)t.p[10]);
+                                             nullptr, (uint32_t *)t.p[10], zmask, (float *)t.p[11],
+                                             (int32_t *)t.p[12], (float *)t.p[13]);
     launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
     a.prof = -1;
     a.G = GT;
@@ -1053,7 +1174,8 @@ sb_status tc_loglik_points(const ProbView &pv, const sb_config *c, const TcWs &t
     cudaMemsetAsync(t.p[10], 0, sizeof(uint32_t) * ((n + BM - 1) / BM) * pv.K, s);
     note_launch();
     k_tc_lse<<<(n + 127) / 128, 128, 0, s>>>(2, pv.K, a.n_ntile, nullptr, n, nullptr, a.qpart, pv.a,
-                                             (float *)t.p[6], nullptr, ell, (uint32_t *)t.p[10]);
+                                             (float *)t.p[6], nullptr, ell, (uint32_t *)t.p[10], nullptr, nullptr,
+                                             nullptr, nullptr);
     if (grad) {
         launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
         a.prof = -1;
