@@ -660,6 +660,43 @@ __global__ void __launch_bounds__(256) k_tc_lnorm(int d, const double *L, float 
     }
 }
 
+// Points whose centred rows for component k are the columns of L_k:
+// X[(kk d + i)][j] = mu_k[j] + L_k[j][i] (j >= i; mu_k[j] above the diagonal),
+// k = k0 + kk, so that the |z_k|^2 pass sums |L_k^T c_i|^2 = |L_k^T L_k|_F^2.
+__global__ void k_tc_lcols(int d, int k0, int kc, const double *L, const float *mu32, float *X) {
+    const size_t tot = (size_t)kc * d * d;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int kk = (int)(e / ((size_t)d * d));
+        const size_t r = e % ((size_t)d * d);
+        const int i = (int)(r / d), j = (int)(r % d);
+        const int k = k0 + kk;
+        const float m = mu32[(size_t)k * d + j];
+        X[e] = j >= i ? m + (float)L[((size_t)k * d + j) * d + i] : m;
+    }
+}
+// lnorm_k = min(|L_k|_F, (1.1 |L_k^T L_k|_F)^(1/2)) from the |z_k|^2 partials of the
+// points above (the 10 % covers the rounding of the tensor-core operands; both are
+// upper bounds on |L_k|_2 = lambda_max(P_k)^(1/2) <= |P_k|_F^(1/2)).
+__global__ void __launch_bounds__(256) k_tc_lnorm_gram(int d, int K, int k0, int n_ntile, const float *qpart,
+                                                       float *lnorm) {
+    const int kk = blockIdx.x, k = k0 + kk;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        const float *qp = qpart + ((size_t)(kk * d + i) * K + k) * n_ntile;
+        for (int t = 0; t < n_ntile; ++t) acc += (double)qp[t];
+    }
+    __shared__ double part[8];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S = 0.0;
+        for (int q = 0; q < 8; ++q) S += part[q];
+        const float g = __double2float_ru(sqrt(1.1 * sqrt(S)));
+        if (isfinite(g) && g > 0.f && g < lnorm[k]) lnorm[k] = g;
+    }
+}
+
 // A operand of GEMM1: A1[k][n][i] = round(x_n[i] - mu_k[i]) formed in FP32; x_n is a
 // walker row (through the active list) or the ray sample c + t_j t_exit u_r.
 // Rows from n_rows up to the next multiple of 128 and columns >= d are zeroed.
@@ -1100,6 +1137,20 @@ sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s) {
     t.bn = pick_tile(pv, t, s);
     if (!make_map(&t.mapT, t.p[0], d, d, K, ldp, t.prec, t.bn) || !make_map(&t.mapB, t.p[1], d, d, K, ldp, t.prec, t.bn))
         return SB_ERR_CUDA;
+    // the component skip's |L_k|_2 bound, tightened through |L_k^T L_k|_F (one |z|^2
+    // pass over d points per component, as many components per pass as the rows hold)
+    const int per = (int)(t.rows / (size_t)d);
+    for (int k0 = 0; per >= 1 && k0 < K; k0 += per) {
+        const int kc = per < K - k0 ? per : K - k0, rows = kc * d;
+        note_launch();
+        k_tc_lcols<<<1184, 256, 0, s>>>(d, k0, kc, pv.L, (const float *)t.p[2], (float *)t.p[7]);
+        TcArgs a = base_args(pv, t);
+        a.n_rows_max = rows;
+        launch_center(t, 0, d, K, nullptr, rows, nullptr, (const float *)t.p[7], nullptr, nullptr, 1, 0, s);
+        launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
+        note_launch();
+        k_tc_lnorm_gram<<<kc, 256, 0, s>>>(d, K, k0, a.n_ntile, a.qpart, (float *)t.p[15]);
+    }
     return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
 }
 
