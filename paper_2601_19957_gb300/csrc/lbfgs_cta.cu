@@ -831,8 +831,12 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
     const int n_act = *a.n_act;
     int par = 0;  // alternation of the reduction scratch (identical in every thread)
     uint64_t bytes = 0;
+    // the next visit's walker id is loaded one visit ahead, so a visit's first
+    // loads (state, vectors) do not wait behind the active-list read
+    int w_next = (int)blockIdx.x < n_act ? a.act[blockIdx.x] : 0;
     for (int n = blockIdx.x; n < n_act; n += gridDim.x) {
-        const int w = a.act[n];
+        const int w = w_next;
+        if (n + (int)gridDim.x < n_act) w_next = a.act[n + gridDim.x];
         WalkerState<float> st = a.st[w];  // same address in every thread: one broadcast load
         const float ft = a.FT[w];
         const float alpha0 = st.alpha, pn0 = st.pn;
