@@ -338,12 +338,13 @@ __global__ void k_lbfgs_init(int n, int d, const double *starts, T *XT, WalkerSt
 }
 
 // Ordered in-place compaction of the active list; counts the evaluations of the round.
-// Chunk b0 writes positions < b0 + 1024 only after all of its reads, and later
-// chunks read positions >= b0 + 1024, so the compaction can run in place.
-// Stable in-place compaction of the active list, one CTA of 1024 threads over
-// chunks of 1024 entries: a ballot per warp, one warp scans the 32 warp counts
-// with shuffles, two barriers per chunk. Writes never pass the chunk being
-// read (output position <= input position).
+// One CTA of 1024 threads over super-chunks of 8 x 1024 entries: every thread
+// first loads its 8 walker ids and their statuses (two memory round trips per
+// super-chunk instead of two per 1024 entries), a barrier, then per 1024-entry
+// chunk a ballot per warp, one warp scans the 32 warp counts with shuffles, two
+// barriers. All reads of a super-chunk precede its writes and every output
+// position is <= its input position, so later super-chunks read untouched entries.
+constexpr int kCompactR = 8;
 template <typename T>
 __global__ void __launch_bounds__(1024) k_lbfgs_compact(const WalkerState<T> *st, int32_t *act, int32_t *n_act,
                                                         int64_t *n_evals) {
@@ -357,30 +358,40 @@ __global__ void __launch_bounds__(1024) k_lbfgs_compact(const WalkerState<T> *st
     }
     __syncthreads();
     int par = 0;
-    for (int b0 = 0; b0 < prev; b0 += 1024, par ^= 1) {
-        const int nidx = b0 + threadIdx.x;
-        const int w = nidx < prev ? act[nidx] : -1;
-        const int keep = (w >= 0) && st[w].status == SB_WALKER_RUNNING;
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) warp_off[wid] = __popc(bal);
-        __syncthreads();
-        const int base = s_base[par];
-        if (wid == 0) {
-            const int c = warp_off[lane];
-            int incl = c;
+    for (int s0 = 0; s0 < prev; s0 += 1024 * kCompactR) {
+        int wv[kCompactR];
+        bool kp[kCompactR];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            warp_off[lane] = incl - c;  // exclusive offsets of the warps
-            if (lane == 31) s_base[par ^ 1] = base + incl;
+        for (int r = 0; r < kCompactR; ++r) {
+            const int nidx = s0 + r * 1024 + (int)threadIdx.x;
+            wv[r] = nidx < prev ? act[nidx] : -1;
         }
-        __syncthreads();
-        const int pos = base + warp_off[wid] + __popc(bal & ((1u << lane) - 1u));
-        if (keep) act[pos] = w;
-        // warp_off is rewritten only after the next chunk's first barrier, which
-        // every thread reaches after this read; s_base alternates between two slots
+#pragma unroll
+        for (int r = 0; r < kCompactR; ++r) kp[r] = wv[r] >= 0 && st[wv[r]].status == SB_WALKER_RUNNING;
+        __syncthreads();  // the super-chunk's reads are done before any of its writes
+#pragma unroll
+        for (int r = 0; r < kCompactR; ++r, par ^= 1) {
+            const unsigned bal = __ballot_sync(0xffffffffu, kp[r]);
+            if (lane == 0) warp_off[wid] = __popc(bal);
+            __syncthreads();
+            const int base = s_base[par];
+            if (wid == 0) {
+                const int c = warp_off[lane];
+                int incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                warp_off[lane] = incl - c;  // exclusive offsets of the warps
+                if (lane == 31) s_base[par ^ 1] = base + incl;
+            }
+            __syncthreads();
+            const int pos = base + warp_off[wid] + __popc(bal & ((1u << lane) - 1u));
+            if (kp[r]) act[pos] = wv[r];
+            // warp_off is rewritten only after the next chunk's first barrier, which
+            // every thread reaches after this read; s_base alternates between two slots
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) *n_act = s_base[par];
