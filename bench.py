@@ -126,33 +126,31 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- cpu baseline
 def cpu_baseline(inst, cfg, seconds):
-    """The FP64 oracle as it stands, on the host cores: L-BFGS walkers from the
-    oracle's own ray starts is too slow at d=1024 for a bounded sample, so the
-    sample is l+grad evaluations of oracle L-BFGS on walkers started at seeded
-    points spread over the prior box, each capped at the iterations that fill
-    about `seconds` of CPU time."""
+    """The FP64 oracle as it stands, on the host cores: a whole oracle solve at
+    d=1024 is far too slow for a bounded sample, so the sample is l+grad
+    evaluations of oracle L-BFGS on batches of walkers started at seeded points
+    spread over the prior box, each batch run to its end, until about
+    `seconds` of wall time."""
     import oracle
 
     oracle.build()
     cores = os.cpu_count() or 1
     rng = np.random.default_rng(7)
-    # time one walker-iteration first to size the sample to ~`seconds`
-    probe = inst.mu[rng.integers(0, inst.K, 1)] + rng.normal(0, 0.2, (1, inst.d))
-    c = type(cfg)(**{**cfg.__dict__, "max_iter": 1})
-    t0 = time.perf_counter()
-    r = oracle.lbfgs(inst, c, probe, n_threads=1)
-    t_one = (time.perf_counter() - t0) / max(r.evals, 1)
+    # batches of `cores` walkers from seeded points spread over the prior box
+    # (like ray samples), each run to its own end, until about `seconds` of
+    # wall time is spent
     n_walk = max(cores, 1)
-    iters = max(1, int(seconds * cores / (t_one * n_walk * 1.2)))
-    c = type(cfg)(**{**cfg.__dict__, "max_iter": iters})
-    # starts spread over the prior box, like ray samples: walkers run to the cap
-    x0 = rng.uniform(inst.lo, inst.hi, (n_walk, inst.d))
-    t0 = time.perf_counter()
-    r = oracle.lbfgs(inst, c, x0, n_threads=cores)
-    dt = time.perf_counter() - t0
-    return {"value": r.evals / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
-            "sample": f"{r.evals} l+grad evaluations of FP64 oracle L-BFGS ({n_walk} walkers x <= {iters} iterations, "
-                      f"d={inst.d}, K={inst.K}) in {dt:.1f} s"}
+    evals, batches, t_total = 0, 0, 0.0
+    while t_total < seconds and batches < 64:
+        x0 = rng.uniform(inst.lo, inst.hi, (n_walk, inst.d))
+        t0 = time.perf_counter()
+        r = oracle.lbfgs(inst, cfg, x0, n_threads=cores)
+        t_total += time.perf_counter() - t0
+        evals += int(r.evals)
+        batches += 1
+    return {"value": evals / t_total, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{evals} l+grad evaluations of FP64 oracle L-BFGS ({batches} batches of {n_walk} walkers "
+                      f"from box-uniform starts, d={inst.d}, K={inst.K}) in {t_total:.1f} s"}
 
 
 # ----------------------------------------------------------------------------- dist helpers

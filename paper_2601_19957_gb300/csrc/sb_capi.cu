@@ -827,7 +827,7 @@ extern "C" sb_status sb_loglik(const sb_problem *p, int32_t prec, const double *
         launch_setup(pv, s);
         sb_config c{};
         c.prec = prec;
-        st = tc_prepare(pv, t, s);
+        st = tc_prepare(pv, t, s, false);  // no walker rounds here
         if (st != SB_OK) return st;
         st = tc_loglik_points(pv, &c, t, x, n, f, grad ? g : nullptr, ell, grad, s);
         if (st != SB_OK) return st;

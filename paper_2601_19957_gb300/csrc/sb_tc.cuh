@@ -26,8 +26,9 @@ bool tc_maps_for_rows(TcWs &t);
 int tc_tuned_tile(int d, int K, int prec);
 // Converts L_k / mu / c into the tensor-core copies, picks the tile width
 // (autotuned once per shape; that first call synchronises the stream) and
-// encodes the tensor maps.
-sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s);
+// encodes the tensor maps. skip_bounds: also the |L_k|_2 bounds the walker
+// rounds' component skip reads (one |z|^2 pass over the columns of every L_k).
+sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s, bool skip_bounds = true);
 // l at every ray sample x_rj = c + t_j t_exit,r u_r from the FP32 directions
 // u32 [n_rays][d]; chunks of the scratch row capacity.
 sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const float *u32,

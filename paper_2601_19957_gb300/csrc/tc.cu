@@ -1121,7 +1121,7 @@ int tc_tuned_tile(int d, int K, int prec) {
     return it == g_tune.end() ? 0 : it->second;
 }
 
-sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s) {
+sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s, bool skip_bounds) {
     const int d = pv.d, K = pv.K;
     const int ldp = ldp_of(d, t.prec);
     note_launch();
@@ -1131,15 +1131,17 @@ sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s) {
         k_tc_convert_L<float><<<1184, 256, 0, s>>>(d, K, ldp, pv.L, (float *)t.p[0], (float *)t.p[1]);
     note_launch();
     k_tc_convert_vec<<<(K * d + 255) / 256, 256, 0, s>>>(d, K, pv.mu, pv.c, (float *)t.p[2], (float *)t.p[3]);
-    note_launch();
-    k_tc_lnorm<<<K, 256, 0, s>>>(d, pv.L, (float *)t.p[15]);
+    if (skip_bounds) {
+        note_launch();
+        k_tc_lnorm<<<K, 256, 0, s>>>(d, pv.L, (float *)t.p[15]);
+    }
     if (!tc_maps_for_rows(t)) return SB_ERR_CUDA;
     t.bn = pick_tile(pv, t, s);
     if (!make_map(&t.mapT, t.p[0], d, d, K, ldp, t.prec, t.bn) || !make_map(&t.mapB, t.p[1], d, d, K, ldp, t.prec, t.bn))
         return SB_ERR_CUDA;
     // the component skip's |L_k|_2 bound, tightened through |L_k^T L_k|_F (one |z|^2
     // pass over d points per component, as many components per pass as the rows hold)
-    const int per = (int)(t.rows / (size_t)d);
+    const int per = skip_bounds ? (int)(t.rows / (size_t)d) : 0;
     for (int k0 = 0; per >= 1 && k0 < K; k0 += per) {
         const int kc = per < K - k0 ? per : K - k0, rows = kc * d;
         note_launch();
