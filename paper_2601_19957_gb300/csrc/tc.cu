@@ -638,26 +638,37 @@ __global__ void __launch_bounds__(128) k_tc_need(int K, const int32_t *n_rows_de
     }
 }
 
-// lnorm_k = |L_k|_F (an upper bound on |L_k|_2), rounded up to FP32: one CTA per
-// component, fixed-order sums.
-__global__ void __launch_bounds__(256) k_tc_lnorm(int d, const double *L, float *lnorm) {
-    const int k = blockIdx.x;
-    const double *Lk = L + (size_t)k * d * d;
+// lnorm_k = |L_k|_F (an upper bound on |L_k|_2), rounded up to FP32: kLnParts CTAs
+// per component sum squares of the lower triangle over contiguous slices of the
+// row-major matrix (partials in a fixed order), then one thread per component
+// adds its partials in order.
+constexpr int kLnParts = 64;
+__global__ void __launch_bounds__(256) k_tc_lnorm_part(int d, const double *L, double *part) {
+    const int k = blockIdx.y, b = blockIdx.x;
+    const size_t dd = (size_t)d * d, per = (dd + kLnParts - 1) / kLnParts;
+    const size_t e0 = (size_t)b * per, e1 = e0 + per < dd ? e0 + per : dd;
+    const double *Lk = L + (size_t)k * dd;
     double acc = 0.0;
-    for (int i = 0; i < d; ++i)
-        for (int j = threadIdx.x; j <= i; j += blockDim.x) {
-            const double v = Lk[(size_t)i * d + j];
-            acc = fma(v, v, acc);
-        }
-    __shared__ double part[8];
+    for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const size_t i = e / d, j = e % d;
+        if (j <= i) acc = fma(Lk[e], Lk[e], acc);
+    }
+    __shared__ double w8[8];
     acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    if ((threadIdx.x & 31) == 0) w8[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int q = 0; q < 8; ++q) t += part[q];
-        lnorm[k] = __double2float_ru(sqrt(t) * (1.0 + 1e-6));
+        for (int q = 0; q < 8; ++q) t += w8[q];
+        part[(size_t)k * kLnParts + b] = t;
     }
+}
+__global__ void k_tc_lnorm_fin(int K, const double *part, float *lnorm) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    double t = 0.0;
+    for (int b = 0; b < kLnParts; ++b) t += part[(size_t)k * kLnParts + b];
+    lnorm[k] = __double2float_ru(sqrt(t) * (1.0 + 1e-6));
 }
 
 // Points whose centred rows for component k are the columns of L_k:
@@ -1131,9 +1142,11 @@ sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s, bool skip_boun
         k_tc_convert_L<float><<<1184, 256, 0, s>>>(d, K, ldp, pv.L, (float *)t.p[0], (float *)t.p[1]);
     note_launch();
     k_tc_convert_vec<<<(K * d + 255) / 256, 256, 0, s>>>(d, K, pv.mu, pv.c, (float *)t.p[2], (float *)t.p[3]);
-    if (skip_bounds) {
+    if (skip_bounds) {  // partials in the qpart scratch (the Gram pass below overwrites it later)
         note_launch();
-        k_tc_lnorm<<<K, 256, 0, s>>>(d, pv.L, (float *)t.p[15]);
+        k_tc_lnorm_part<<<dim3(kLnParts, K), 256, 0, s>>>(d, pv.L, (double *)t.p[5]);
+        note_launch();
+        k_tc_lnorm_fin<<<(K + 63) / 64, 64, 0, s>>>(K, (const double *)t.p[5], (float *)t.p[15]);
     }
     if (!tc_maps_for_rows(t)) return SB_ERR_CUDA;
     t.bn = pick_tile(pv, t, s);
