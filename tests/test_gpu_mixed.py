@@ -121,3 +121,29 @@ def test_mixed_refine_reaches_gaussian_mean(prec, d, m):
     assert np.sqrt((z * z).sum(1)).max() <= 1.0
     peak = oracle.loglik(inst, inst.mu[0])
     assert (peak - out.ell.cpu().numpy()).max() <= 0.5 + 1e-3 * abs(peak)
+
+
+def test_full_size_workload_sampled_against_oracle():
+    """The configuration the bench times (d=1024, K=8, 16384 rays x 64 steps, 16384
+    walkers, m=20, BF16), checked where the oracle can follow one output at a time:
+    32 sampled selected starts' l against the FP64 oracle within the tensor-core
+    error model (c u (|z|^2 + d), c = 16, as in the tensor-core tests), and the whole
+    solve on the same workspace: every mode a component mean with its exact Laplace
+    term, log Z the closed form of the found components."""
+    insts, c = workload(4)
+    inst = insts[0]
+    cfg = sb.make_config(c)
+    prob = sb.Problem(inst)
+    ws = sb.workspace(prob, cfg)
+    starts, ell = sb.discover(prob, cfg, ws=ws)
+    starts, ell = starts.cpu().numpy(), ell.cpu().numpy()
+    a_max = np.max(inst.log_w - 0.5 * inst.d * np.log(2 * np.pi)
+                   + np.log(np.diagonal(inst.L, axis1=1, axis2=2)).sum(1))
+    u = 2.0 ** -9
+    for i in np.random.default_rng(11).choice(c.n_starts, 32, replace=False):
+        le = oracle.loglik(inst, starts[i])
+        q = max(2.0 * (a_max - le), 1.0)
+        assert abs(ell[i] - le) <= 16.0 * u * (q + inst.d), (i, ell[i], le)
+    out = sb.evidence(prob, cfg, ws=ws)
+    assert out.n_modes >= 1
+    _check_modes_against_components(inst, out)
