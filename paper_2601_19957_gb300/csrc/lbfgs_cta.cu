@@ -26,8 +26,9 @@
 //
 // A walker's step is a chain of dependent phases (reductions, the m x m
 // solve), so the SM is kept busy by several walkers at once: CT threads per
-// walker, thread t owning the float4 groups at coordinates 4 (t + q CT),
-// q < VPT = 1024 / (4 CT).
+// walker; with bf16 pairs thread t owns the 8 consecutive coordinates from 8 t
+// (one 16-byte chunk of a stored row), with FP32 pairs the float4 groups at
+// coordinates 4 (t + q CT), q < VPT = 1024 / (4 CT).
 #include <cuda_bf16.h>
 
 #include "sb_lbfgs.cuh"
@@ -40,7 +41,7 @@ template <int CT>
 struct Cfg {
     static constexpr int NW = CT / 32;            // warps per walker
     static constexpr int VPT = kMaxD / (4 * CT);  // float4 groups per thread
-    static constexpr int PG = CT >= 256 ? 3 : 2;  // pairs per pass-1 ring group (5 PG products per warp transpose)
+    static constexpr int PG = CT >= 256 ? 3 : 2;  // FP32 pairs: pairs per ring group (5 PG products per warp transpose)
     static constexpr int MINB = CT >= 256 ? 2 : 4; // CTAs per SM
     static constexpr int DEPTH = CT >= 256 ? 2 : 3; // pair groups in flight (cp.async ring)
     // ring bytes: DEPTH groups x PG pairs x (s, y) x VPT float4 per thread
