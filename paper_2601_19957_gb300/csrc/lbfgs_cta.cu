@@ -21,14 +21,14 @@
 // coefficients, and a second pass forms p = -gamma g - S a + gamma Y w. R^-1,
 // Y^T Y and D live per walker in HBM and are updated incrementally, so the
 // history S, Y is read twice per iteration (the second read mostly from L2)
-// and never re-walked. With bf16 pairs the first pass runs on the tensor
-// cores (mma.sync, the pairs as the B operand; g split into three bf16 terms).
+// and never re-walked. The pairs are stored in bf16, and the first pass runs
+// on the tensor cores (mma.sync, the pairs as the B operand; g split into
+// three bf16 terms).
 //
 // A walker's step is a chain of dependent phases (reductions, the m x m
 // solve), so the SM is kept busy by several walkers at once: CT threads per
-// walker; with bf16 pairs thread t owns the 8 consecutive coordinates from 8 t
-// (one 16-byte chunk of a stored row), with FP32 pairs the float4 groups at
-// coordinates 4 (t + q CT), q < VPT = 1024 / (4 CT).
+// walker, thread t owning the 8 consecutive coordinates from 8 t (one 16-byte
+// chunk of a stored bf16 row).
 #include <cuda_bf16.h>
 
 #include "sb_lbfgs.cuh"
@@ -41,15 +41,12 @@ template <int CT>
 struct Cfg {
     static constexpr int NW = CT / 32;            // warps per walker
     static constexpr int VPT = kMaxD / (4 * CT);  // float4 groups per thread
-    static constexpr int PG = CT >= 256 ? 3 : 2;  // FP32 pairs: pairs per ring group (5 PG products per warp transpose)
-    static constexpr int MINB = CT >= 256 ? 2 : 4; // CTAs per SM
-    static constexpr int DEPTH = CT >= 256 ? 2 : 3; // pair groups in flight (cp.async ring)
-    // ring bytes: DEPTH groups x PG pairs x (s, y) x VPT float4 per thread
-    static constexpr int RING_F4 = DEPTH * PG * 2 * VPT * CT;
-    // bf16 pairs: groups of PGB pairs (one 8-column tensor-core tile of s, y
-    // vectors), DB groups in the same ring (one 16-byte chunk per vector and thread)
+    static constexpr int MINB = 4;                // CTAs per SM
+    // ring of the stored pairs: DB groups of PGB pairs (one 8-column tensor-core
+    // tile of s, y vectors), one 16-byte chunk per stored vector and thread
     static constexpr int PGB = 4;
-    static constexpr int DB = RING_F4 / (PGB * 2 * CT);
+    static constexpr int DB = 3;
+    static constexpr int RING_F4 = DB * PGB * 2 * CT;
 };
 constexpr int kCT = 128;  // threads per walker used by the solver
 
@@ -92,10 +89,10 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                  : "memory");
 }
-// History storage of the stored pairs: FP32, or bf16 (half the bytes of the
-// stream that bounds the step). Inner products, R and Y^T Y are formed
-// from the stored (rounded) vectors, so the direction applies the exact
-// L-BFGS matrix of the pairs as stored.
+// The stored pairs are bf16 (half the bytes of the stream that bounds the
+// step). Inner products, R and Y^T Y are formed from the stored (rounded)
+// vectors, so the direction applies the exact L-BFGS matrix of the pairs as
+// stored.
 __device__ __forceinline__ float4 round_bf16(float4 v) {
     return make_float4(__bfloat162float(__float2bfloat16_rn(v.x)), __bfloat162float(__float2bfloat16_rn(v.y)),
                        __bfloat162float(__float2bfloat16_rn(v.z)), __bfloat162float(__float2bfloat16_rn(v.w)));
@@ -144,18 +141,13 @@ __device__ __forceinline__ void split3_bf16(float v, float &hi, float &mid, floa
     lo = r - mid;
 }
 
-// A vector of d coordinates as this thread's VPT float4 groups. Mapping M = 0
-// (FP32 pairs): group q of thread t holds coordinates 4 (t + q CT) .. +3, so one
-// 16-byte access instruction of a warp covers a contiguous 512-byte stretch.
-// M = 1 (bf16 pairs): thread t holds the 4 VPT consecutive coordinates from
-// 4 VPT t, so its share of a bf16 row is one 16-byte chunk and a warp's copy
-// instruction covers 512 contiguous bytes.
-template <int CT, int M>
+// A vector of d coordinates as this thread's VPT float4 groups: thread t holds
+// the 4 VPT consecutive coordinates from 4 VPT t, so its share of a bf16 row is
+// one 16-byte chunk and a warp's copy instruction covers 512 contiguous bytes.
+template <int CT>
 struct Vec {
     float4 v[Cfg<CT>::VPT];
-    __device__ __forceinline__ static int i0(int q) {
-        return M ? 4 * (Cfg<CT>::VPT * (int)threadIdx.x + q) : 4 * ((int)threadIdx.x + q * CT);
-    }
+    __device__ __forceinline__ static int i0(int q) { return 4 * (Cfg<CT>::VPT * (int)threadIdx.x + q); }
     __device__ __forceinline__ void load(const float *p, int d) {
 #pragma unroll
         for (int q = 0; q < Cfg<CT>::VPT; ++q) v[q] = ld4(p, i0(q), d);
@@ -169,45 +161,45 @@ struct Vec {
         for (int q = 0; q < Cfg<CT>::VPT; ++q) v[q] = zero4();
     }
 };
-template <int CT, int M>
-__device__ __forceinline__ float dotv(const Vec<CT, M> &a, const Vec<CT, M> &b) {
+template <int CT>
+__device__ __forceinline__ float dotv(const Vec<CT> &a, const Vec<CT> &b) {
     float s = 0.f;
 #pragma unroll
     for (int q = 0; q < Cfg<CT>::VPT; ++q) s += dot4(a.v[q], b.v[q]);
     return s;
 }
 // y += c x
-template <int CT, int M>
-__device__ __forceinline__ void axpyv(float c, const Vec<CT, M> &x, Vec<CT, M> &y) {
+template <int CT>
+__device__ __forceinline__ void axpyv(float c, const Vec<CT> &x, Vec<CT> &y) {
 #pragma unroll
     for (int q = 0; q < Cfg<CT>::VPT; ++q) y.v[q] = axpy4(c, x.v[q], y.v[q]);
 }
 // a + c b
-template <int CT, int M>
-__device__ __forceinline__ Vec<CT, M> lincomb(const Vec<CT, M> &a, float c, const Vec<CT, M> &b) {
-    Vec<CT, M> r;
+template <int CT>
+__device__ __forceinline__ Vec<CT> lincomb(const Vec<CT> &a, float c, const Vec<CT> &b) {
+    Vec<CT> r;
 #pragma unroll
     for (int q = 0; q < Cfg<CT>::VPT; ++q) r.v[q] = axpy4(c, b.v[q], a.v[q]);
     return r;
 }
-template <int CT, int M>
-__device__ __forceinline__ Vec<CT, M> subv(const Vec<CT, M> &a, const Vec<CT, M> &b) {
-    Vec<CT, M> r;
+template <int CT>
+__device__ __forceinline__ Vec<CT> subv(const Vec<CT> &a, const Vec<CT> &b) {
+    Vec<CT> r;
 #pragma unroll
     for (int q = 0; q < Cfg<CT>::VPT; ++q)
         r.v[q] = make_float4(a.v[q].x - b.v[q].x, a.v[q].y - b.v[q].y, a.v[q].z - b.v[q].z, a.v[q].w - b.v[q].w);
     return r;
 }
-template <int CT, int M>
-__device__ __forceinline__ bool finitev(const Vec<CT, M> &a) {
+template <int CT>
+__device__ __forceinline__ bool finitev(const Vec<CT> &a) {
     bool f = true;
 #pragma unroll
     for (int q = 0; q < Cfg<CT>::VPT; ++q)
         f = f && isfinite(a.v[q].x) && isfinite(a.v[q].y) && isfinite(a.v[q].z) && isfinite(a.v[q].w);
     return f;
 }
-template <int CT, int M>
-__device__ __forceinline__ float absmaxv(const Vec<CT, M> &a) {
+template <int CT>
+__device__ __forceinline__ float absmaxv(const Vec<CT> &a) {
     float m = 0.f;
 #pragma unroll
     for (int q = 0; q < Cfg<CT>::VPT; ++q)
@@ -236,25 +228,6 @@ __device__ __forceinline__ void block_sum(float (&v)[NV], float *sh) {
         for (int q = 0; q < Cfg<CT>::NW; ++q) t += sh[q * NV + j];
         v[j] = t;
     }
-}
-
-// Reduce 16 per-lane values over the warp with 16 shuffles (recursive halving
-// within each half-warp: at each level a lane keeps one half of its values and
-// adds its partner's copy of that half; then one exchange between the halves).
-// Lanes j and j + 16 return the warp total of value j.
-__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 8; o >= 1; o >>= 1) {
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int j = 0; j < o; ++j) {
-            const float send = up ? v[j] : v[j + o];
-            const float keep = up ? v[j + o] : v[j];
-            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-    }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
 // NV sums and one maximum over the CTA with a single barrier; every thread gets all.
@@ -287,13 +260,11 @@ __device__ __forceinline__ void block_sum_max(float (&v)[NV], float &mx, float *
 // Odd row stride of the m x m matrices: their rows and their columns are both
 // free of shared-memory bank conflicts.
 __host__ __device__ __forceinline__ int mm_ld(int m) { return (m & 1) ? m + 2 : m + 1; }
-// Pass 1's partial sums per ring group and warp: FP32 pairs, the 5 PG products
-// of the group; bf16 pairs, three rows (g, y_new, s_new) x the group's 2 PGB vectors.
+// Pass 1's partial sums per ring group and warp: three rows (g, y_new, s_new) x
+// the group's 2 PGB vectors.
 template <int CT>
 __host__ __device__ __forceinline__ int p1_floats(int m) {
-    const int f = (m + Cfg<CT>::PG - 1) / Cfg<CT>::PG * Cfg<CT>::NW * 5 * Cfg<CT>::PG;
-    const int b = (m + Cfg<CT>::PGB - 1) / Cfg<CT>::PGB * Cfg<CT>::NW * 3 * 2 * Cfg<CT>::PGB;
-    return f > b ? f : b;
+    return (m + Cfg<CT>::PGB - 1) / Cfg<CT>::PGB * Cfg<CT>::NW * 3 * 2 * Cfg<CT>::PGB;
 }
 // Floats of the dynamic area after the ring: R^-1, Y^T Y, pass 1's sums and the
 // six m-vectors (u1, u2, ca, cw, dg, nr).
@@ -438,92 +409,64 @@ __device__ __forceinline__ void solve_mm(Shared<CT> &sh, int c, int cn, float *m
     }
 }
 
-// Stores this thread's coordinates of a history vector (already rounded to HT).
-template <int CT, int M, typename HT>
-__device__ __forceinline__ void store_hist(const Vec<CT, M> &v, HT *row, int d) {
-    if (sizeof(HT) == 4) {
-        v.store(reinterpret_cast<float *>(row), d);
-    } else {  // mapping 1: 8 consecutive coordinates, one 16-byte chunk
-        const int e0 = Vec<CT, M>::i0(0);
-        if ((d & 7) == 0 && e0 + 7 < d) {
-            *reinterpret_cast<uint4 *>(row + e0) = make_uint4(pack2(v.v[0].x, v.v[0].y), pack2(v.v[0].z, v.v[0].w),
-                                                              pack2(v.v[1].x, v.v[1].y), pack2(v.v[1].z, v.v[1].w));
-        } else {
-            const float f[8] = {v.v[0].x, v.v[0].y, v.v[0].z, v.v[0].w, v.v[1].x, v.v[1].y, v.v[1].z, v.v[1].w};
-            __nv_bfloat16 *r = reinterpret_cast<__nv_bfloat16 *>(row);
-            for (int e = 0; e < 8 && e0 + e < d; ++e) r[e0 + e] = __float2bfloat16_rn(f[e]);
-        }
+using bf16 = __nv_bfloat16;
+
+// Stores this thread's coordinates of a history vector (values already bf16):
+// 8 consecutive coordinates, one 16-byte chunk.
+template <int CT>
+__device__ __forceinline__ void store_hist(const Vec<CT> &v, bf16 *row, int d) {
+    const int e0 = Vec<CT>::i0(0);
+    if ((d & 7) == 0 && e0 + 7 < d) {
+        *reinterpret_cast<uint4 *>(row + e0) = make_uint4(pack2(v.v[0].x, v.v[0].y), pack2(v.v[0].z, v.v[0].w),
+                                                          pack2(v.v[1].x, v.v[1].y), pack2(v.v[1].z, v.v[1].w));
+    } else {
+        const float f[8] = {v.v[0].x, v.v[0].y, v.v[0].z, v.v[0].w, v.v[1].x, v.v[1].y, v.v[1].z, v.v[1].w};
+        for (int e = 0; e < 8 && e0 + e < d; ++e) row[e0 + e] = __float2bfloat16_rn(f[e]);
     }
 }
 
 // The shared-memory ring the stored pairs stream through: D slots of PG pairs,
-// blocks of CT 16-byte chunks (chunk j of vector v of pair q of slot sl; U4
-// chunks per vector and thread). Within a block the chunk of thread t sits at
-// t ^ (block % 8), so the same chunk of 8 consecutive blocks (the rows of one
-// ldmatrix) falls in 8 different bank groups.
-template <int CT, typename HT>
+// blocks of CT 16-byte chunks (the chunk of vector v of pair q of slot sl).
+// Within a block the chunk of thread t sits at t ^ (block % 8), so the same
+// chunk of 8 consecutive blocks (the rows of one ldmatrix) falls in 8 different
+// bank groups.
+template <int CT>
 struct Ring {
-    static constexpr bool BF = sizeof(HT) == 2;
-    static constexpr int MAP = BF;
-    static constexpr int PG = BF ? Cfg<CT>::PGB : Cfg<CT>::PG;
-    static constexpr int D = BF ? Cfg<CT>::DB : Cfg<CT>::DEPTH;
-    static constexpr int U4 = BF ? Cfg<CT>::VPT / 2 : Cfg<CT>::VPT;
+    static constexpr int PG = Cfg<CT>::PGB;
+    static constexpr int D = Cfg<CT>::DB;
+    static_assert(Cfg<CT>::VPT == 2, "one 16-byte bf16 chunk (8 coordinates) per stored vector and thread");
     uint4 *base;
     int d;
-    __device__ __forceinline__ uint4 *at(int sl, int q, int v, int j, int t) const {
-        const int b = ((sl * PG + q) * 2 + v) * U4 + j;
+    __device__ __forceinline__ uint4 *at(int sl, int q, int v, int t) const {
+        const int b = (sl * PG + q) * 2 + v;
         return base + (size_t)b * CT + (t ^ (b & 7));
     }
-    // this thread's chunks of a stored row (cp.async, or plain copies zero-padded
+    // this thread's chunk of a stored row (cp.async, or a plain copy zero-padded
     // past d for a ragged end of the row)
-    __device__ __forceinline__ void copy_in(int sl, int q, int v, const HT *row) const {
+    __device__ __forceinline__ void copy_in(int sl, int q, int v, const bf16 *row) const {
+        uint4 *dst = at(sl, q, v, threadIdx.x);
+        const int e0 = Vec<CT>::i0(0);  // 8 consecutive elements
+        if ((d & 7) == 0 && e0 + 7 < d) {
+            cp_async16(dst, row + e0);
+        } else {
+            uint16_t h[8];
+            const uint16_t *src = reinterpret_cast<const uint16_t *>(row);
 #pragma unroll
-        for (int j = 0; j < U4; ++j) {
-            uint4 *dst = at(sl, q, v, j, threadIdx.x);
-            if (BF) {
-                const int e0 = Vec<CT, MAP>::i0(0);  // 8 consecutive elements
-                if ((d & 7) == 0 && e0 + 7 < d) {
-                    cp_async16(dst, row + e0);
-                } else {
-                    uint16_t h[8];
-                    const uint16_t *src = reinterpret_cast<const uint16_t *>(row);
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) h[e] = e0 + e < d ? src[e0 + e] : (uint16_t)0;
-                    *dst = make_uint4(h[0] | (uint32_t)h[1] << 16, h[2] | (uint32_t)h[3] << 16,
-                                      h[4] | (uint32_t)h[5] << 16, h[6] | (uint32_t)h[7] << 16);
-                }
-            } else {
-                const int i0 = Vec<CT, MAP>::i0(j);
-                if ((d & 3) == 0 && i0 + 3 < d) {
-                    cp_async16(dst, row + i0);
-                } else {
-                    for (int e = 0; e < 4 && i0 + e < d; ++e)
-                        cp_async4(reinterpret_cast<float *>(dst) + e, reinterpret_cast<const float *>(row) + i0 + e);
-                }
-            }
+            for (int e = 0; e < 8; ++e) h[e] = e0 + e < d ? src[e0 + e] : (uint16_t)0;
+            *dst = make_uint4(h[0] | (uint32_t)h[1] << 16, h[2] | (uint32_t)h[3] << 16, h[4] | (uint32_t)h[5] << 16,
+                              h[6] | (uint32_t)h[7] << 16);
         }
     }
     // this thread's coordinates of pair q of slot sl
-    __device__ __forceinline__ void fetch(int sl, int q, Vec<CT, MAP> &sv, Vec<CT, MAP> &yv) const {
-        if (BF) {
-            const uint4 a4 = *at(sl, q, 0, 0, threadIdx.x), b4 = *at(sl, q, 1, 0, threadIdx.x);
-            sv.v[0] = unpack4(a4.x, a4.y);
-            sv.v[1] = unpack4(a4.z, a4.w);
-            yv.v[0] = unpack4(b4.x, b4.y);
-            yv.v[1] = unpack4(b4.z, b4.w);
-        } else {
-#pragma unroll
-            for (int j = 0; j < Cfg<CT>::VPT; ++j) {
-                const uint4 a4 = *at(sl, q, 0, j, threadIdx.x), b4 = *at(sl, q, 1, j, threadIdx.x);
-                sv.v[j] = make_float4(__uint_as_float(a4.x), __uint_as_float(a4.y), __uint_as_float(a4.z),
-                                      __uint_as_float(a4.w));
-                yv.v[j] = make_float4(__uint_as_float(b4.x), __uint_as_float(b4.y), __uint_as_float(b4.z),
-                                      __uint_as_float(b4.w));
-            }
-        }
+    __device__ __forceinline__ void fetch(int sl, int q, Vec<CT> &sv, Vec<CT> &yv) const {
+        const uint4 a4 = *at(sl, q, 0, threadIdx.x), b4 = *at(sl, q, 1, threadIdx.x);
+        sv.v[0] = unpack4(a4.x, a4.y);
+        sv.v[1] = unpack4(a4.z, a4.w);
+        yv.v[0] = unpack4(b4.x, b4.y);
+        yv.v[1] = unpack4(b4.z, b4.w);
 #pragma unroll
         for (int j = 0; j < Cfg<CT>::VPT; ++j) {
-            const int i0 = Vec<CT, MAP>::i0(j);
+            const int i0 = Vec<CT>::i0(j);
             if (!(i0 + 3 < d)) {  // ragged tail: lanes past d hold stale data
                 if (i0 + 0 >= d) sv.v[j].x = yv.v[j].x = 0.f;
                 if (i0 + 1 >= d) sv.v[j].y = yv.v[j].y = 0.f;
@@ -532,9 +475,9 @@ struct Ring {
             }
         }
     }
-    // Issues pass-1 group k (logical pairs k PG .. k PG + PG - 1 of the J stored
-    // from slot head) into slot k % D. Always commits.
-    __device__ __forceinline__ void issue1(int k, int J, int head, int m, const HT *S, const HT *Y) const {
+    // Issues group k (logical pairs k PG .. k PG + PG - 1 of the J stored from
+    // slot head) into slot k % D. Always commits.
+    __device__ __forceinline__ void issue(int k, int J, int head, int m, const bf16 *S, const bf16 *Y) const {
         const int sl = k % D;
 #pragma unroll
         for (int q = 0; q < PG; ++q) {
@@ -547,19 +490,6 @@ struct Ring {
         }
         cp_async_commit();
     }
-    // Issues pass-2 group k (logical pairs k PG .., slot k % D). Always commits.
-    __device__ __forceinline__ void issue2(int k, int count, int head, int m, const HT *S, const HT *Y) const {
-#pragma unroll
-        for (int q = 0; q < PG; ++q) {
-            const int i = k * PG + q;
-            if (i >= count) break;
-            int slot = head + i;
-            if (slot >= m) slot -= m;
-            copy_in(k % D, q, 0, S + (size_t)slot * d);
-            copy_in(k % D, q, 1, Y + (size_t)slot * d);
-        }
-        cp_async_commit();
-    }
 };
 
 // Direction for walker state st (count pairs from ring slot head). When
@@ -569,27 +499,25 @@ struct Ring {
 // the unit trial X + P; updates st.dphi / alpha / bt and possibly resets the
 // history (steepest descent when p is not a descent direction). Returns the
 // algorithmic bytes moved.
-template <int CT, typename HT, int MAP = (sizeof(HT) == 2)>
+template <int CT>
 __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<float> &st, int new_slot,
-                              const Vec<CT, MAP> &g_in, const Vec<CT, MAP> &x_in,
-                              const Vec<CT, MAP> &s_new, const Vec<CT, MAP> &y_new, float *MRI, float *MYY,
+                              const Vec<CT> &g_in, const Vec<CT> &x_in,
+                              const Vec<CT> &s_new, const Vec<CT> &y_new, float *MRI, float *MYY,
                               Shared<CT> &sh, int &par) {
-    using RG = Ring<CT, HT>;
-    constexpr bool BF = RG::BF;
-    static_assert(!BF || Cfg<CT>::VPT == 2, "bf16 history: two groups of 4 (8 bytes each) per thread");
+    using RG = Ring<CT>;
     constexpr int PG = RG::PG, D = RG::D, NW = Cfg<CT>::NW;
     const int d = a.d, m = a.m;
     const int count = st.count;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t bytes = 0;
-    Vec<CT, MAP> p;
+    Vec<CT> p;
     p.zero();
-    // x and g are stored at X, G by the caller; the bf16 path reads them back
-    // after pass 1 instead of holding them through it
-    Vec<CT, MAP> g = g_in, x = x_in;
+    // x and g are stored at X, G by the caller; they are read back after pass 1
+    // instead of being held through it
+    Vec<CT> g = g_in, x = x_in;
     if (count > 0) {
-        const HT *S = reinterpret_cast<const HT *>(a.S) + (size_t)w * m * d;
-        const HT *Y = reinterpret_cast<const HT *>(a.Y) + (size_t)w * m * d;
+        const bf16 *S = reinterpret_cast<const bf16 *>(a.S) + (size_t)w * m * d;
+        const bf16 *Y = reinterpret_cast<const bf16 *>(a.Y) + (size_t)w * m * d;
         const RG ring{reinterpret_cast<uint4 *>(sh.ring), d};
         // pass 1 streams the logical pairs (the new one included: it is stored)
         const bool added = new_slot >= 0;
@@ -600,17 +528,17 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
         float *mri_w = MRI + (size_t)w * m * m, *myy_w = MYY + (size_t)w * m * m, *dw = a.rho + (size_t)w * m;
         fetch_mm<CT>(sh, mri_w, myy_w, dw, count, m, st.head, cn);  // committed with ring group 0
 #pragma unroll 1
-        for (int k = 0; k < D - 1; ++k) ring.issue1(k, J, head, m, S, Y);
+        for (int k = 0; k < D - 1; ++k) ring.issue(k, J, head, m, S, Y);
         float *p1 = sh.p1;
-        if constexpr (BF) {
+        {
             // Pass 1 on the tensor cores: per warp (its 256 coordinates, 16 k-steps of
             // 16) and ring group (8 stored vectors s_0 y_0 .. s_3 y_3 as the columns of
             // B), D = A B with the rows of A = (g_hi, g_mid, g_lo, y_new, s_new, 0 ..)
             // at the same coordinates. The A fragments are staged once through this
             // warp's own chunks of ring slot D - 1 (free until group D - 1 is issued into it).
             uint4 *ring4 = reinterpret_cast<uint4 *>(sh.ring);
-            constexpr int SB = (D - 1) * PG * 2 * RG::U4;  // first block of slot D - 1
-            static_assert(2 * PG * RG::U4 >= 5, "slot D - 1 holds the five staged rows");
+            constexpr int SB = (D - 1) * PG * 2;  // first block of slot D - 1
+            static_assert(2 * PG >= 5, "slot D - 1 holds the five staged rows");
             auto stage = [&](int r, int u) { return ring4 + (SB + r) * CT + (u ^ ((SB + r) & 7)); };
             {
                 float hi[8], mi[8], lo[8];
@@ -645,7 +573,7 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
             int nk = (d - 256 * wid + 15) / 16;  // k-steps of this warp inside d (warp-uniform)
             nk = nk < 0 ? 0 : (nk > 16 ? 16 : nk);
             const int gid = lane >> 2, tig = lane & 3;
-            ring.issue1(D - 1, J, head, m, S, Y);  // its slot held the staged operand
+            ring.issue(D - 1, J, head, m, S, Y);  // its slot held the staged operand
             for (int k = 0; k < K1; ++k) {
                 cp_async_wait<D - 1>();
                 __syncwarp();  // every lane's copies of the group are visible to the warp
@@ -659,7 +587,7 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
                     for (int c = 0; c < 16; c += 2) {
                         if (c < nk) {
                             uint32_t b[4];
-                            ldsm_x4(b, ring.at(sl, n >> 1, n & 1, 0, 32 * wid + 2 * (c + (mi8 >> 1)) + (mi8 & 1)));
+                            ldsm_x4(b, ring.at(sl, n >> 1, n & 1, 32 * wid + 2 * (c + (mi8 >> 1)) + (mi8 & 1)));
                             mma_rows8(acc, af[c][0], af[c][1], b[0], b[1]);
                             if (c + 1 < nk) mma_rows8(acc, af[c + 1][0], af[c + 1][1], b[2], b[3]);
                         }
@@ -677,62 +605,19 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
                     }
                 }
                 __syncwarp();  // the warp has read the group before its slot is refilled
-                ring.issue1(k + D, J, head, m, S, Y);
-            }
-        } else {
-            // pass 1: inner products. Each warp reduces its share of a group's 5 PG
-            // products over its lanes and parks the totals in shared scratch; the
-            // warps' totals are summed once after the pass.
-            constexpr int NV = 5 * PG;
-            static_assert(NV <= 16, "one half-warp transpose per group");
-            ring.issue1(D - 1, J, head, m, S, Y);
-            for (int k = 0; k < K1; ++k) {
-                cp_async_wait<D - 1>();
-                const int gi = k, sl = k % D;
-                if (gi < ng1) {
-                    float v[NV];
-#pragma unroll
-                    for (int q = 0; q < PG; ++q) {
-                        Vec<CT, MAP> s4, y4;
-                        if (gi * PG + q < J) {
-                            ring.fetch(sl, q, s4, y4);
-                        } else {
-                            s4.zero();
-                            y4.zero();
-                        }
-                        v[q] = dotv(s4, g);               // u1 = S^T g
-                        v[PG + q] = dotv(y4, g);          // u2 = Y^T g
-                        v[2 * PG + q] = dotv(s4, y_new);  // s_i . y_new
-                        v[3 * PG + q] = dotv(s_new, y4);  // s_new . y_i
-                        v[4 * PG + q] = dotv(y4, y_new);  // y_i . y_new
-                    }
-                    float v16[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) v16[j] = j < NV ? v[j] : 0.f;
-                    const float t = warp_transpose_sum16(v16);
-                    if (lane < NV) p1[(gi * NW + wid) * NV + lane] = t;
-                }
-                ring.issue1(k + D, J, head, m, S, Y);  // into the slot just read (own chunks)
+                ring.issue(k + D, J, head, m, S, Y);
             }
         }
         __syncthreads();
         // product k of logical pair i (k: 0 s.g, 1 y.g, 2 s.y_new, 3 s_new.y, 4 y.y_new):
         // the warps' totals summed in warp order
         auto p1sum = [&](int k, int i) {
-            const int j = i;
-            const float *src;
-            int stride;
-            if constexpr (BF) {
-                constexpr int rk[5] = {0, 0, 1, 2, 1}, ck[5] = {0, 1, 0, 1, 1};
-                src = p1 + ((j / PG) * NW * 3 + rk[k]) * (2 * PG) + 2 * (j % PG) + ck[k];
-                stride = 3 * 2 * PG;
-            } else {
-                src = p1 + (j / PG) * NW * (5 * PG) + k * PG + j % PG;
-                stride = 5 * PG;
-            }
+            // rows (g, y_new, s_new) x columns (s_q, y_q) of the group's warp totals
+            constexpr int rk[5] = {0, 0, 1, 2, 1}, ck[5] = {0, 1, 0, 1, 1};
+            const float *src = p1 + ((i / PG) * NW * 3 + rk[k]) * (2 * PG) + 2 * (i % PG) + ck[k];
             float t = 0.f;
 #pragma unroll
-            for (int q = 0; q < NW; ++q) t += src[q * stride];
+            for (int q = 0; q < NW; ++q) t += src[q * 3 * 2 * PG];
             return t;
         };
         for (int e = threadIdx.x; e < 2 * count; e += CT) {
@@ -744,11 +629,9 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
         bytes += new_mm<CT>(sh, myy_w, dw, count, m, st.head, cn, p1sum);
         const int ng2 = (count + PG - 1) / PG;
 #pragma unroll 1
-        for (int k = 0; k < D; ++k) ring.issue2(k, count, st.head, m, S, Y);  // pass 2's first groups
-        if constexpr (BF) {
-            g.load(a.G + (size_t)w * d, d);
-            x.load(a.X + (size_t)w * d, d);
-        }
+        for (int k = 0; k < D; ++k) ring.issue(k, count, st.head, m, S, Y);  // pass 2's first groups
+        g.load(a.G + (size_t)w * d, d);
+        x.load(a.X + (size_t)w * d, d);
         __syncthreads();
         // the solving warp differs between the CTAs that share an SM (their warp w
         // would otherwise all sit on the same scheduler)
@@ -764,17 +647,17 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
             for (int q = 0; q < PG; ++q) {
                 const int i = k * PG + q;
                 if (i < count) {
-                    Vec<CT, MAP> s4, y4;
+                    Vec<CT> s4, y4;
                     ring.fetch(k % D, q, s4, y4);
                     axpyv(-sh.ca[i], s4, p);
                     axpyv(gam * sh.cw[i], y4, p);
                 }
             }
-            ring.issue2(k + D, count, st.head, m, S, Y);  // this thread's own chunks, just read
+            ring.issue(k + D, count, st.head, m, S, Y);  // this thread's own chunks, just read
         }
         cp_async_wait<0>();  // (only empty groups remain) the ring is free for the next walker
         // the two-loop recursion's history traffic: each pair read in both passes
-        bytes += (uint64_t)4 * count * d * sizeof(HT);
+        bytes += (uint64_t)4 * count * d * sizeof(bf16);
     }
     float dp[2];  // grad f . p and |p|^2
     if (count > 0) {
@@ -807,10 +690,9 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
 // Algorithmic bytes of the L-BFGS step launches (added only while counting is on).
 __device__ unsigned long long g_lbfgs_bytes;
 
-template <int CT, typename HT>
+template <int CT>
 __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float> a, float *MRI, float *MYY,
                                                                 int count_bytes) {
-    constexpr int MAP = sizeof(HT) == 2;  // coordinate mapping (see Vec)
     __shared__ Shared<CT> sh;
     extern __shared__ __align__(16) float4 dyn[];  // [RING_F4] ring, then R, YY [m][ld]
     const int d = a.d, m = a.m;
@@ -844,7 +726,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
         float dnext = -1.f;  // bound on |new trial - this visit's trial| (see k_tc_need)
         float *X = a.X + (size_t)w * d;
         float *G = a.G + (size_t)w * d;
-        Vec<CT, MAP> x, g, xt, gt;
+        Vec<CT> x, g, xt, gt;
         x.load(X, d);
         g.load(G, d);
         xt.load(a.XT + (size_t)w * d, d);
@@ -852,13 +734,11 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
         bytes += (uint64_t)16 * d + 4 + 2 * sizeof(WalkerState<float>);
         // finiteness of the trial gradient, the candidate pair's inner products and
         // max |grad| at the trial, all in one reduction
-        Vec<CT, MAP> s4 = subv(xt, x), y4 = subv(gt, g);
-        if (sizeof(HT) == 2) {  // the pair as it will be stored
+        Vec<CT> s4 = subv(xt, x), y4 = subv(gt, g);
 #pragma unroll
-            for (int q = 0; q < Cfg<CT>::VPT; ++q) {
-                s4.v[q] = round_bf16(s4.v[q]);
-                y4.v[q] = round_bf16(y4.v[q]);
-            }
+        for (int q = 0; q < Cfg<CT>::VPT; ++q) {  // the pair as it will be stored
+            s4.v[q] = round_bf16(s4.v[q]);
+            y4.v[q] = round_bf16(y4.v[q]);
         }
         float r4[4] = {finitev(gt) ? 0.f : 1.f, dotv(s4, s4), dotv(y4, y4), dotv(s4, y4)};
         float gm = absmaxv(gt);
@@ -866,7 +746,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
         const bool finite = isfinite(ft) && r4[0] == 0.f;
         bool newiter = false;
         int new_slot = -1;
-        Vec<CT, MAP> s_new, y_new;
+        Vec<CT> s_new, y_new;
         s_new.zero();
         y_new.zero();
         if (st.phase == 0) {
@@ -891,9 +771,9 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                     slot = st.head;
                     st.head = (st.head + 1) % m;
                 }
-                store_hist<CT, MAP, HT>(s4, reinterpret_cast<HT *>(a.S) + ((size_t)w * m + slot) * d, d);
-                store_hist<CT, MAP, HT>(y4, reinterpret_cast<HT *>(a.Y) + ((size_t)w * m + slot) * d, d);
-                bytes += (uint64_t)2 * d * sizeof(HT);
+                store_hist<CT>(s4, reinterpret_cast<bf16 *>(a.S) + ((size_t)w * m + slot) * d, d);
+                store_hist<CT>(y4, reinterpret_cast<bf16 *>(a.Y) + ((size_t)w * m + slot) * d, d);
+                bytes += (uint64_t)2 * d * sizeof(bf16);
                 new_slot = slot;
                 s_new = s4;
                 y_new = y4;
@@ -911,7 +791,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
             ++st.bt;
             if (st.bt <= a.max_backtracks) {
                 st.alpha *= a.backtrack;
-                Vec<CT, MAP> p;
+                Vec<CT> p;
                 p.load(a.P + (size_t)w * d, d);
                 lincomb(x, st.alpha, p).store(a.XT + (size_t)w * d, d);
                 bytes += (uint64_t)8 * d;
@@ -920,7 +800,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                 st.count = 0;
                 st.head = 0;
                 st.attempt = 1;
-                bytes += direction<CT, HT>(a, w, st, -1, g, x, s_new, y_new, MRI, MYY, sh, par);
+                bytes += direction<CT>(a, w, st, -1, g, x, s_new, y_new, MRI, MYY, sh, par);
                 dnext = st.pn + alpha0 * pn0;  // from the old trial back to x, then out
             } else {
                 st.status = SB_WALKER_STALLED;
@@ -935,7 +815,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                 st.status = SB_WALKER_MAXITER;
             } else {
                 st.attempt = 0;
-                bytes += direction<CT, HT>(a, w, st, new_slot, g, x, s_new, y_new, MRI, MYY, sh, par);
+                bytes += direction<CT>(a, w, st, new_slot, g, x, s_new, y_new, MRI, MYY, sh, par);
                 dnext = st.pn;  // x is this visit's trial
             }
         }
@@ -953,8 +833,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
 
 }  // namespace
 
-void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *MYY, int num_sms, bool bf16_history,
-                           cudaStream_t s) {
+void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *MYY, int num_sms, cudaStream_t s) {
     ProfScope prof(PROF_LBFGS_STEP, s);
     const int count_bytes = prof_enabled() ? 1 : 0;
     int grid = num_sms * Cfg<kCT>::MINB;
@@ -963,16 +842,11 @@ void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *
     static bool attr = false;
     if (!attr) {
         const size_t most = (size_t)Cfg<kCT>::RING_F4 * sizeof(float4) + sizeof(float) * mm_floats<kCT>(kMaxM);
-        cudaFuncSetAttribute(k_lbfgs_cta<kCT, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
-        cudaFuncSetAttribute(k_lbfgs_cta<kCT, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)most);
+        cudaFuncSetAttribute(k_lbfgs_cta<kCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
         attr = true;
     }
     note_launch();
-    if (bf16_history)
-        k_lbfgs_cta<kCT, __nv_bfloat16><<<grid, kCT, dyn, s>>>(a, MRI, MYY, count_bytes);
-    else
-        k_lbfgs_cta<kCT, float><<<grid, kCT, dyn, s>>>(a, MRI, MYY, count_bytes);
+    k_lbfgs_cta<kCT><<<grid, kCT, dyn, s>>>(a, MRI, MYY, count_bytes);
 }
 
 double lbfgs_bytes_take() {

@@ -393,9 +393,6 @@ int device_sms() {
     return n;
 }
 
-// Storage of the mixed path's L-BFGS pairs: bf16 (the step is bound by the
-// history stream; the FP64 Newton polish fixes the final accuracy).
-constexpr bool kBf16History = true;
 
 template <typename T>
 void step_round(const RefineWs<T> &r, const LbfgsArgs<T> &a, int n, cudaStream_t s);
@@ -409,7 +406,7 @@ void step_round<float>(const RefineWs<float> &r, const LbfgsArgs<float> &a, int 
     // next round's component skip reads
     LbfgsArgs<float> b = a;
     b.dist = (float *)r.tc.p[kTcDistSlot];
-    launch_lbfgs_step_cta(b, n, r.MRI, r.MYY, device_sms(), kBf16History, s);
+    launch_lbfgs_step_cta(b, n, r.MRI, r.MYY, device_sms(), s);
 }
 
 template <typename T>

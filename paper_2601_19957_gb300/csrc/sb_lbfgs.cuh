@@ -40,11 +40,10 @@ template <typename T>
 void launch_lbfgs_step(const LbfgsArgs<T> &a, int n, cudaStream_t s);
 template <typename T>
 void launch_lbfgs_compact(const LbfgsArgs<T> &a, int64_t *n_evals, cudaStream_t s);
-// FP32 step, one CTA per walker, compact-representation direction (lbfgs_cta.cu).
-// MRI, MYY: per-walker [N][m][m] R^-1 (R = upper(S^T Y)) and Y^T Y, slot-indexed;
-// bf16_history stores the pairs in bf16.
-void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *MYY, int num_sms, bool bf16_history,
-                           cudaStream_t s);
+// FP32 step, one CTA per walker, compact-representation direction (lbfgs_cta.cu);
+// the stored pairs S, Y are bf16. MRI, MYY: per-walker [N][m][m] R^-1
+// (R = upper(S^T Y)) and Y^T Y, slot-indexed.
+void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *MYY, int num_sms, cudaStream_t s);
 // Algorithmic bytes moved by the FP32 step launches while profiling was on
 // (synchronises the device, then clears the counter); -1 on a CUDA error.
 double lbfgs_bytes_take();
