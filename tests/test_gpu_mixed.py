@@ -147,3 +147,16 @@ def test_full_size_workload_sampled_against_oracle():
     out = sb.evidence(prob, cfg, ws=ws)
     assert out.n_modes >= 1
     _check_modes_against_components(inst, out)
+
+
+@pytest.mark.parametrize("prec", [sb.PREC_BF16, sb.PREC_TF32])
+@pytest.mark.parametrize("d,K,m,n_starts", [(1, 1, 1, 1), (2, 2, 1, 16), (3, 3, 2, 64), (7, 2, 10, 5)])
+def test_mixed_evidence_small_and_degenerate(prec, d, K, m, n_starts):
+    """Degenerate sizes on the tensor-core path: d below one K chunk, a one-pair
+    history, a single walker: the modes found are true components with their
+    exact Laplace terms (the FP64 polish), as at full size."""
+    inst = make_instance(d, K, 7300 + 10 * d + K, s_range=(0.15, 0.4), mean_box=(-6, 6), sep=8.0)
+    c = SolveConfig(n_rays=64, n_steps=16, n_starts=n_starts, m=m, seed=7300 + d, prec=prec)
+    out = sb.evidence(sb.Problem(inst), sb.make_config(c))
+    assert out.n_modes >= 1
+    _check_modes_against_components(inst, out)
