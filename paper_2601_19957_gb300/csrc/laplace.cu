@@ -799,13 +799,12 @@ void launch_dedup(int n, int d, const double *X, const double *ell, const int8_t
                   const DedupScratch &sc, cudaStream_t s) {
     // one CTA per 128 points up to one per SM (kept small so that concurrent
     // solves on other streams can still be co-resident)
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
+    static const int sms = [] {  // thread-safe one-time query (batched solves use several host threads)
+        int dev = 0, n = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : 1;
+    }();
     int G = (n + 127) / 128;
     if (G > sms) G = sms;
     if (G > kDedupMaxGrid) G = kDedupMaxGrid;

@@ -31,6 +31,8 @@
 // chunk of a stored bf16 row).
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "sb_lbfgs.cuh"
 
 namespace sb {
@@ -839,12 +841,11 @@ void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *
     int grid = num_sms * Cfg<kCT>::MINB;
     if (grid > n) grid = n > 0 ? n : 1;
     const size_t dyn = (size_t)Cfg<kCT>::RING_F4 * sizeof(float4) + sizeof(float) * mm_floats<kCT>(a.m);
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag once;  // batched solves launch from several host threads
+    std::call_once(once, [] {
         const size_t most = (size_t)Cfg<kCT>::RING_F4 * sizeof(float4) + sizeof(float) * mm_floats<kCT>(kMaxM);
         cudaFuncSetAttribute(k_lbfgs_cta<kCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
-        attr = true;
-    }
+    });
     note_launch();
     k_lbfgs_cta<kCT><<<grid, kCT, dyn, s>>>(a, MRI, MYY, count_bytes);
 }

@@ -383,13 +383,12 @@ void eval_round<float>(const ProbView &pv, const sb_config *c, const RefineWs<fl
 }
 
 int device_sms() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
+    static const int n = [] {  // thread-safe one-time query
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
     return n;
 }
 
