@@ -349,65 +349,66 @@ __device__ __forceinline__ uint64_t new_mm(Shared<CT> &sh, float *myy, float *dw
     return (c * (c + 1) / 2 + c * c + c) * 4 + (cn >= 0 ? (uint64_t)(3 * c) * 4 : 0);
 }
 
-// Warp that runs the m x m solve: CTAs are dealt to SMs round-robin, so the
-// CTAs co-resident on one SM have consecutive values of blockIdx / (grid / MINB).
-template <int CT>
-__device__ __forceinline__ int solver_warp() {
-    const int per = max(1, (int)gridDim.x / Cfg<CT>::MINB);
-    return (int)(blockIdx.x / per) % Cfg<CT>::NW;
-}
-
-// The m x m part (one warp), with R^-1 in shared memory: the new column of R^-1
-// when a pair was appended (logical cn; RI_i,cn = -(sum_{i<=k<cn} RI_ik R_k,cn) / D_cn,
-// RI_cn,cn = 1 / D_cn, also written to HBM), then w = R^-1 u1, gamma = D_c-1 /
-// (y^T y)_c-1, tv = D w + gamma Y^T Y w - gamma u2 and a = R^-T tv. Each lane
-// forms whole entries (rows lane and lane + 32) with sums in ascending index
-// order. Results in sh.cw, sh.ca, sh.gamma.
+// The m x m part, on the whole CTA, with R^-1 in shared memory: the new column
+// of R^-1 when a pair was appended (logical cn; RI_i,cn = -(sum_{i<=k<cn} RI_ik
+// R_k,cn) / D_cn, RI_cn,cn = 1 / D_cn, also written to HBM), then w = R^-1 u1,
+// gamma = D_c-1 / (y^T y)_c-1, tv = D w + gamma Y^T Y w - gamma u2 and
+// a = R^-T tv. Each entry is a dot product over G threads (strided terms, then a
+// fixed-order shuffle sum), one barrier between the stages. Every thread calls
+// it. Results in sh.cw, sh.ca, sh.gamma.
 template <int CT>
 __device__ __forceinline__ void solve_mm(Shared<CT> &sh, int c, int cn, float *mri, int m, int head) {
-    const int lane = threadIdx.x & 31;
+    const int G = c <= CT / 4 ? 4 : (c <= CT / 2 ? 2 : 1);  // threads per entry
+    const int i = (int)threadIdx.x / G, p = (int)threadIdx.x % G;
     const int LD = sh.ld;
     float *RI = sh.RI;
     const float *YY = sh.YY;
     float *tv = sh.p1;  // pass 1's partial sums are consumed before the solve
+    auto gsum = [&](float v) {  // every lane calls it: full-warp shuffles
+        if (G >= 2) v += __shfl_xor_sync(0xffffffffu, v, 1);
+        if (G >= 4) v += __shfl_xor_sync(0xffffffffu, v, 2);
+        return v;
+    };
     if (cn >= 0) {
         const float dn = sh.nr[cn];
-        int sc = head + cn;
-        if (sc >= m) sc -= m;
-        for (int i = lane; i <= cn; i += 32) {
-            float v;
-            if (i == cn) {
-                v = 1.f / dn;
-            } else {
-                float t = 0.f;
-                for (int k = i; k < cn; ++k) t += RI[i * LD + k] * sh.nr[k];
-                v = -t / dn;
-            }
+        float t = 0.f;
+        if (i < cn)
+            for (int k = i + p; k < cn; k += G) t += RI[i * LD + k] * sh.nr[k];
+        t = gsum(t);
+        if (p == 0 && i <= cn) {
+            const float v = i == cn ? 1.f / dn : -t / dn;
             RI[i * LD + cn] = v;
-            int si = head + i;
+            int si = head + i, sc = head + cn;
             if (si >= m) si -= m;
+            if (sc >= m) sc -= m;
             mri[(size_t)si * m + sc] = v;
         }
-        __syncwarp();
+        __syncthreads();
     }
-    for (int i = lane; i < c; i += 32) {
+    {
         float t = 0.f;
-        for (int k = i; k < c; ++k) t += RI[i * LD + k] * sh.u1[k];
-        sh.cw[i] = t;
+        if (i < c)
+            for (int k = i + p; k < c; k += G) t += RI[i * LD + k] * sh.u1[k];
+        t = gsum(t);
+        if (p == 0 && i < c) sh.cw[i] = t;
     }
-    __syncwarp();
+    __syncthreads();
     const float gam = sh.dg[c - 1] / YY[(c - 1) * LD + (c - 1)];
-    if (lane == 0) sh.gamma = gam;
-    for (int i = lane; i < c; i += 32) {
-        float yyw = 0.f;
-        for (int j = 0; j < c; ++j) yyw += YY[i * LD + j] * sh.cw[j];
-        tv[i] = sh.dg[i] * sh.cw[i] + gam * yyw - gam * sh.u2[i];
-    }
-    __syncwarp();
-    for (int j = lane; j < c; j += 32) {
+    if (threadIdx.x == 0) sh.gamma = gam;
+    {
         float t = 0.f;
-        for (int i = 0; i <= j; ++i) t += RI[i * LD + j] * tv[i];
-        sh.ca[j] = t;
+        if (i < c)
+            for (int j = p; j < c; j += G) t += YY[i * LD + j] * sh.cw[j];
+        t = gsum(t);
+        if (p == 0 && i < c) tv[i] = sh.dg[i] * sh.cw[i] + gam * t - gam * sh.u2[i];
+    }
+    __syncthreads();
+    {
+        float t = 0.f;
+        if (i < c)
+            for (int k = p; k <= i; k += G) t += RI[k * LD + i] * tv[k];
+        t = gsum(t);
+        if (p == 0 && i < c) sh.ca[i] = t;
     }
 }
 
@@ -635,9 +636,7 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
         g.load(a.G + (size_t)w * d, d);
         x.load(a.X + (size_t)w * d, d);
         __syncthreads();
-        // the solving warp differs between the CTAs that share an SM (their warp w
-        // would otherwise all sit on the same scheduler)
-        if (wid == solver_warp<CT>()) solve_mm<CT>(sh, count, cn, mri_w, m, st.head);
+        solve_mm<CT>(sh, count, cn, mri_w, m, st.head);
         __syncthreads();
         // pass 2: p = -gamma g - S a + gamma Y w
         const float gam = sh.gamma;
