@@ -27,9 +27,9 @@ sys.path.insert(0, ROOT)
 
 # DRAM bytes per algorithmic byte of the L-BFGS step with bf16 pairs, measured
 # with ncu over all step launches of one solve at d=1024, K=8, 8192 walkers
-# (41.21 + 9.12 GB DRAM for 72 x 1.200 GB algorithmic): the second pass of the
+# (41.23 + 9.12 GB DRAM for 72 x 1.2005 GB algorithmic): the second pass of the
 # two-loop recursion is mostly served by L2.
-LBFGS_DRAM_PER_ALGORITHMIC_BYTE = 0.583
+LBFGS_DRAM_PER_ALGORITHMIC_BYTE = 0.582
 
 METRIC = "logL+grad evals/sec and evidence solves/sec at d=1024 K=8 vs plain FP64 GPU; |ΔlogZ|"
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
