@@ -57,7 +57,8 @@ def lib():
     if _lib is None:
         _lib = C.CDLL(build())
         _lib.orc_loglik.restype = C.c_double
-        for name in ("orc_select_starts", "orc_discover", "orc_cholesky", "orc_laplace", "orc_evidence"):
+        for name in ("orc_select_starts", "orc_discover", "orc_cholesky", "orc_laplace", "orc_evidence",
+                     "orc_chisao_ray_best", "orc_chisao"):
             getattr(_lib, name).restype = C.c_int
     return _lib
 
@@ -215,3 +216,72 @@ def evidence(inst, cfg, n_threads=1) -> LaplaceResult:
     starts, _ = discover(inst, cfg, n_threads)
     ref = lbfgs(inst, cfg, starts, n_threads)
     return laplace(inst, cfg, ref.x, ref.ell, ref.status, n_threads=n_threads)
+
+
+# ------------------------------------------------------------------ ChiSao (Sec. 3.5.5)
+class _ChisaoConfig(C.Structure):
+    _fields_ = [("n_osc", C.c_int), ("conv_iters", C.c_int), ("anti_steps", C.c_int),
+                ("min_unconverged", C.c_int), ("momentum", C.c_double), ("anti_alpha", C.c_double)]
+
+
+@dataclass
+class ChisaoConfig:
+    """Knobs of the ChiSao oscillation (defaults: the values the paper states where it states one)."""
+
+    n_osc: int = 3
+    conv_iters: int = 1000
+    anti_steps: int = 10
+    min_unconverged: int = 5
+    momentum: float = 0.9
+    anti_alpha: float = 0.01
+
+
+@dataclass
+class ChisaoResult:
+    x: np.ndarray
+    ell: np.ndarray
+    stuck: np.ndarray
+    n_peaks: int
+
+
+def chisao_anticonverge(inst, x, steps, momentum, alpha):
+    """Momentum anti-convergence of the rows of x (returns a new array)."""
+    P = OracleProblem(inst)
+    x = np.array(x, dtype=np.float64).reshape(-1, P.d)
+    lib().orc_chisao_anticonverge(C.byref(P.s), _ptr(x), C.c_int(x.shape[0]), C.c_int(steps),
+                                  C.c_double(momentum), C.c_double(alpha))
+    return x
+
+
+def chisao_directions(d, r, seed, osc, peak, basis=0):
+    """The first r orthonormal directions of one basis, one per row."""
+    Q = np.empty((r, d))
+    lib().orc_chisao_directions(C.c_int(d), C.c_int(r), C.c_uint64(seed), C.c_int(osc), C.c_int(peak),
+                                C.c_int(basis), _ptr(Q))
+    return Q
+
+
+def chisao_ray_best(inst, origin, direction, n_steps, past_valley=False):
+    """(sample index, point, l) of the best sample on the ray to the box boundary."""
+    P = OracleProblem(inst)
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    u = np.ascontiguousarray(direction, dtype=np.float64)
+    x = np.empty(P.d)
+    ell = C.c_double(0.0)
+    j = lib().orc_chisao_ray_best(C.byref(P.s), _ptr(o), _ptr(u), C.c_int(n_steps), C.c_int(int(past_valley)),
+                                  _ptr(x), C.byref(ell))
+    return j, x, ell.value
+
+
+def chisao(inst, cfg, cc: ChisaoConfig, x0, n_threads=1) -> ChisaoResult:
+    P = OracleProblem(inst)
+    c = _cfg(cfg, n_threads)
+    k = _ChisaoConfig(cc.n_osc, cc.conv_iters, cc.anti_steps, cc.min_unconverged, cc.momentum, cc.anti_alpha)
+    x0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(-1, P.d)
+    n = x0.shape[0]
+    xo = np.empty_like(x0)
+    lo = np.empty(n)
+    st = np.empty(n, dtype=np.int8)
+    npk = lib().orc_chisao(C.byref(P.s), C.byref(c), C.byref(k), _ptr(x0), C.c_int(n), _ptr(xo), _ptr(lo),
+                           _ptr(st))
+    return ChisaoResult(xo, lo, st.astype(bool), int(npk))

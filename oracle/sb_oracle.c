@@ -732,3 +732,257 @@ int orc_evidence(const orc_problem *p, const orc_config *c, double *modes, doubl
     free(starts);
     return nm;
 }
+
+/* ------------------------------------------------------------------------ */
+/* ChiSao oscillation around the refinement (Sec. 3.5.5, Algorithm 1).        */
+/* Readings where the paper is silent:                                        */
+/*  - an oscillation's convergence phase is L-BFGS from the current positions */
+/*    with an empty history, capped at conv_iters accepted steps;             */
+/*  - a sample is converged when |grad l|_inf <= eps_grad (1 + |l|) (the     */
+/*    scaled form of the Laplace filter) and sticks when also l >= l_max +    */
+/*    log 0.1 (l_max over all finite samples); "unconverged" samples are the  */
+/*    finite ones that are not converged;                                     */
+/*  - deduplication runs over the stuck samples with the coarse radius        */
+/*    (greedy, l descending, ties to the lower index); the stuck samples that */
+/*    are not representatives are the K_lost duplicates;                      */
+/*  - Repulse Monkey (>= min_unconverged unconverged samples): lost sample   */
+/*    l (index order) shoots a ray from the (l mod n)-th unconverged sample   */
+/*    in a Philox-normal direction (counter (pair, l, osc, 'RPMK')) to        */
+/*    the box boundary and moves to the best of n_steps samples on it;        */
+/*  - Golden Rooster (fewer such samples): lost sample l goes to peak         */
+/*    p = l mod n_peaks (representatives by decreasing l) along direction     */
+/*    c = (l / n_peaks) / 2, sign + for even l / n_peaks and - for odd;       */
+/*    direction c is column c mod d of orthonormal basis c / d of that peak   */
+/*    (modified Gram-Schmidt, i.e. the Q of a QR, of Philox normals with      */
+/*    counter (pair, basis d + column, osc << 16 | p, 'GRST')); on the ray it */
+/*    moves to the best sample beyond the first valley (the first sample      */
+/*    after which l rises), or to the exit sample when l never rises; it      */
+/*    stays off once an oscillation that used it ends with no more peaks than */
+/*    before;                                                                 */
+/*  - ray origins are clamped to the box; ray samples at t_j = (j+1)/n t_exit;*/
+/*  - anti-convergence: every finite sample that is not stuck takes           */
+/*    anti_steps steps v <- momentum v - alpha grad l, x <- x + v (descent on */
+/*    l, so away from the peak it sits near), v = 0 at the start, clamped to  */
+/*    the box after each step; alpha is a fixed step size (no value given in  */
+/*    the paper);                                                             */
+/*  - Hands Like Clouds is not applied (out of scope); the last oscillation   */
+/*    skips reseeding and anti-convergence.                                   */
+/* ------------------------------------------------------------------------ */
+static void box_clamp(const orc_problem *p, double *x) {
+    for (int i = 0; i < p->d; ++i) x[i] = x[i] < p->lo[i] ? p->lo[i] : (x[i] > p->hi[i] ? p->hi[i] : x[i]);
+}
+
+/* d standard normals from Philox blocks with counter (pair, w1, w2, tag). */
+static void philox_normals(int d, uint64_t seed, uint32_t w1, uint32_t w2, uint32_t tag, double *z) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int q = 0; q < (d + 1) / 2; ++q) {
+        uint32_t ctr[4] = {(uint32_t)q, w1, w2, tag};
+        uint32_t o[4];
+        orc_philox4x32_10(ctr, key, o);
+        double u1 = orc_unit(o[0], o[1]);
+        double u2 = orc_unit(o[2], o[3]);
+        double rad = sqrt(-2.0 * log(u1));
+        double th = ORC_TWO_PI * u2;
+        z[2 * q] = rad * cos(th);
+        if (2 * q + 1 < d) z[2 * q + 1] = rad * sin(th);
+    }
+}
+
+void orc_chisao_anticonverge(const orc_problem *p, double *x, int n, int steps, double momentum, double alpha) {
+    const int d = p->d;
+    double *g = (double *)malloc(sizeof(double) * (size_t)d);
+    double *v = (double *)malloc(sizeof(double) * (size_t)d);
+    for (int s = 0; s < n; ++s) {
+        double *xs = x + (size_t)s * d;
+        for (int i = 0; i < d; ++i) v[i] = 0.0;
+        for (int t = 0; t < steps; ++t) {
+            orc_loglik(p, xs, g, NULL);
+            for (int i = 0; i < d; ++i) {
+                v[i] = momentum * v[i] - alpha * g[i];
+                xs[i] = xs[i] + v[i];
+            }
+            box_clamp(p, xs);
+        }
+    }
+    free(v);
+    free(g);
+}
+
+void orc_chisao_directions(int d, int r, uint64_t seed, int osc, int peak, int basis, double *Q) {
+    /* columns j = 0..r-1 of Q (d x r, column j at Q[j*d..]): modified Gram-Schmidt */
+    for (int j = 0; j < r; ++j) {
+        double *qj = Q + (size_t)j * d;
+        philox_normals(d, seed, (uint32_t)basis * (uint32_t)d + (uint32_t)j, ((uint32_t)osc << 16) | (uint32_t)peak,
+                       0x47525354u, qj);
+        for (int k = 0; k < j; ++k) {
+            const double *qk = Q + (size_t)k * d;
+            double dot = 0.0;
+            for (int i = 0; i < d; ++i) dot += qk[i] * qj[i];
+            for (int i = 0; i < d; ++i) qj[i] -= dot * qk[i];
+        }
+        double nrm = 0.0;
+        for (int i = 0; i < d; ++i) nrm += qj[i] * qj[i];
+        nrm = sqrt(nrm);
+        for (int i = 0; i < d; ++i) qj[i] /= nrm;
+    }
+}
+
+int orc_chisao_ray_best(const orc_problem *p, const double *origin, const double *dir, int n_steps, int past_valley,
+                        double *x_out, double *ell_out) {
+    const int d = p->d;
+    double *o = (double *)malloc(sizeof(double) * (size_t)d);
+    double *xt = (double *)malloc(sizeof(double) * (size_t)d);
+    double *ell = (double *)malloc(sizeof(double) * (size_t)(n_steps > 0 ? n_steps : 1));
+    memcpy(o, origin, sizeof(double) * (size_t)d);
+    box_clamp(p, o);
+    double t_exit = INFINITY;
+    for (int i = 0; i < d; ++i) {
+        if (dir[i] > 0.0) {
+            double t = (p->hi[i] - o[i]) / dir[i];
+            if (t < t_exit) t_exit = t;
+        } else if (dir[i] < 0.0) {
+            double t = (p->lo[i] - o[i]) / dir[i];
+            if (t < t_exit) t_exit = t;
+        }
+    }
+    if (!(t_exit < INFINITY)) t_exit = 0.0;
+    for (int j = 0; j < n_steps; ++j) {
+        const double t = ((double)(j + 1) / (double)n_steps) * t_exit;
+        for (int i = 0; i < d; ++i) xt[i] = o[i] + t * dir[i];
+        ell[j] = orc_loglik(p, xt, NULL, NULL);
+    }
+    int j0 = 0;
+    if (past_valley) {
+        /* first sample after which l rises; none: the exit sample */
+        j0 = -1;
+        for (int j = 0; j + 1 < n_steps; ++j)
+            if (ell[j + 1] > ell[j]) {
+                j0 = j + 1;
+                break;
+            }
+        if (j0 < 0) j0 = n_steps - 1;
+    }
+    int best = j0;
+    for (int j = j0 + 1; j < n_steps; ++j)
+        if (ell[j] > ell[best]) best = j;
+    const double t = ((double)(best + 1) / (double)n_steps) * t_exit;
+    for (int i = 0; i < d; ++i) x_out[i] = o[i] + t * dir[i];
+    if (ell_out) *ell_out = ell[best];
+    free(ell);
+    free(xt);
+    free(o);
+    return best;
+}
+
+int orc_chisao(const orc_problem *p, const orc_config *c, const orc_chisao_config *cc, const double *x0, int n,
+               double *x_out, double *ell_out, int8_t *stuck_out) {
+    const int d = p->d;
+    double wmax = 0.0;
+    for (int i = 0; i < d; ++i)
+        if (p->hi[i] - p->lo[i] > wmax) wmax = p->hi[i] - p->lo[i];
+    orc_config cl = *c;
+    cl.max_iter = cc->conv_iters;
+    double *x = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * d);
+    double *xn = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * d);
+    double *ell = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    int8_t *st = (int8_t *)malloc((size_t)(n > 0 ? n : 1));
+    int8_t *stuck = (int8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int8_t *lost = (int8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int8_t *conv = (int8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    orc_rank *order = (orc_rank *)malloc(sizeof(orc_rank) * (size_t)(n > 0 ? n : 1));
+    int *reps = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int *peaks = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    double *dir = (double *)malloc(sizeof(double) * (size_t)d);
+    memcpy(x, x0, sizeof(double) * (size_t)n * d);
+    int gr_on = 1, gr_used_prev = 0, peaks_prev = -1, n_peaks = 0;
+    for (int osc = 0; osc < cc->n_osc; ++osc) {
+        /* convergence phase: all samples released, L-BFGS from where they are */
+        orc_lbfgs(p, &cl, x, n, xn, ell, st, NULL, NULL);
+        memcpy(x, xn, sizeof(double) * (size_t)n * d);
+        /* stick detection */
+        double lmax = -INFINITY;
+        for (int s = 0; s < n; ++s)
+            if (isfinite(ell[s]) && ell[s] > lmax) lmax = ell[s];
+        int ns = 0;
+        for (int s = 0; s < n; ++s) {
+            conv[s] = 0;
+            if (isfinite(ell[s])) {
+                const double l = orc_loglik(p, x + (size_t)s * d, dir, NULL);
+                conv[s] = (int8_t)(max_abs(d, dir) <= c->eps_grad * (1.0 + fabs(l)));
+            }
+            stuck[s] = (int8_t)(conv[s] && ell[s] >= lmax + log(0.1));
+            lost[s] = 0;
+            if (stuck[s]) {
+                order[ns].ell = ell[s];
+                order[ns].idx = s;
+                ++ns;
+            }
+        }
+        /* deduplication of the stuck samples: non-representatives are lost */
+        qsort(order, (size_t)ns, sizeof(orc_rank), rank_cmp);
+        n_peaks = greedy_dedup(d, x, order, ns, c->dedup_coarse * wmax, reps);
+        for (int a = 0; a < ns; ++a) lost[order[a].idx] = 1;
+        for (int r = 0; r < n_peaks; ++r) {
+            peaks[r] = order[reps[r]].idx;
+            lost[peaks[r]] = 0;
+        }
+        for (int s = 0; s < n; ++s)
+            if (lost[s]) stuck[s] = 0;
+        if (gr_used_prev && n_peaks <= peaks_prev) gr_on = 0;
+        gr_used_prev = 0;
+        peaks_prev = n_peaks;
+        if (osc == cc->n_osc - 1) break;
+        /* reseeding of the lost samples */
+        int n_free = 0;
+        for (int s = 0; s < n; ++s)
+            if (!conv[s] && isfinite(ell[s])) ++n_free;
+        int l_ord = 0;
+        for (int s = 0; s < n; ++s) {
+            if (!lost[s]) continue;
+            if (n_free >= cc->min_unconverged) {
+                int which = l_ord % n_free, o = -1;
+                for (int q = 0; q < n; ++q)
+                    if (!conv[q] && isfinite(ell[q]) && which-- == 0) {
+                        o = q;
+                        break;
+                    }
+                philox_normals(d, c->seed, (uint32_t)l_ord, (uint32_t)osc, 0x52504D4Bu, dir);
+                double nrm = 0.0;
+                for (int i = 0; i < d; ++i) nrm += dir[i] * dir[i];
+                nrm = sqrt(nrm);
+                for (int i = 0; i < d; ++i) dir[i] /= nrm;
+                orc_chisao_ray_best(p, x + (size_t)o * d, dir, c->n_steps, 0, x + (size_t)s * d, NULL);
+            } else if (gr_on && n_peaks > 0) {
+                const int pk = l_ord % n_peaks, k = l_ord / n_peaks, cdir = k / 2;
+                const int basis = cdir / d, col = cdir % d;
+                const double sgn = (k % 2 == 0) ? 1.0 : -1.0;
+                double *Q = (double *)malloc(sizeof(double) * (size_t)(col + 1) * d);
+                orc_chisao_directions(d, col + 1, c->seed, osc, pk, basis, Q);
+                for (int i = 0; i < d; ++i) dir[i] = sgn * Q[(size_t)col * d + i];
+                free(Q);
+                orc_chisao_ray_best(p, x + (size_t)peaks[pk] * d, dir, c->n_steps, 1, x + (size_t)s * d, NULL);
+                gr_used_prev = 1;
+            }
+            ++l_ord;
+        }
+        /* anti-convergence of every sample that is not stuck */
+        for (int s = 0; s < n; ++s)
+            if (!stuck[s] && st[s] != ORC_NONFINITE)
+                orc_chisao_anticonverge(p, x + (size_t)s * d, 1, cc->anti_steps, cc->momentum, cc->anti_alpha);
+    }
+    memcpy(x_out, x, sizeof(double) * (size_t)n * d);
+    if (ell_out) memcpy(ell_out, ell, sizeof(double) * (size_t)n);
+    if (stuck_out) memcpy(stuck_out, stuck, (size_t)n);
+    free(dir);
+    free(peaks);
+    free(reps);
+    free(order);
+    free(conv);
+    free(lost);
+    free(stuck);
+    free(st);
+    free(ell);
+    free(xn);
+    free(x);
+    return n_peaks;
+}

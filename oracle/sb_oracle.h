@@ -76,6 +76,24 @@ int orc_laplace(const orc_problem *p, const orc_config *c, const double *x, cons
 int orc_evidence(const orc_problem *p, const orc_config *c, double *modes, double *logZk,
                  int cap, int *n_modes, double *logZ);
 
+/* ChiSao oscillation (Sec. 3.5.5) around the refinement; readings in sb_oracle.c. */
+typedef struct {
+    int n_osc, conv_iters, anti_steps, min_unconverged;
+    double momentum, anti_alpha;
+} orc_chisao_config;
+
+/* anti-convergence of n samples in place: steps momentum descent steps of step size alpha */
+void orc_chisao_anticonverge(const orc_problem *p, double *x, int n, int steps, double momentum, double alpha);
+/* the first r <= d columns (Q[j*d..], j < r) of orthonormal basis `basis` of oscillation osc, peak peak */
+void orc_chisao_directions(int d, int r, uint64_t seed, int osc, int peak, int basis, double *Q);
+/* best of n_steps samples on the ray from origin (clamped to the box) along dir to the box
+ * boundary (past_valley: beyond the first valley); returns the sample index */
+int orc_chisao_ray_best(const orc_problem *p, const double *origin, const double *dir, int n_steps, int past_valley,
+                        double *x_out, double *ell_out);
+/* ChiSao: returns the number of peaks (stuck representatives, flagged in stuck_out) */
+int orc_chisao(const orc_problem *p, const orc_config *c, const orc_chisao_config *cc, const double *x0, int n,
+               double *x_out, double *ell_out, int8_t *stuck_out);
+
 #ifdef __cplusplus
 }
 #endif
