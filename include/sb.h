@@ -257,6 +257,54 @@ int32_t sb_profile_read(double *ms, int64_t *launches);
  * the device; returns -1 on a CUDA error. */
 double sb_profile_bytes(int32_t cls);
 
+/* Knobs of the ChiSao oscillation (Sec. 3.5.5, Algorithm 1). */
+typedef struct sb_chisao_config {
+    int32_t n_osc;           /* oscillations, 1..1024 (3)                                   */
+    int32_t conv_iters;      /* accepted L-BFGS steps per convergence phase (1000)          */
+    int32_t anti_steps;      /* momentum descent steps per anti-convergence phase (10)      */
+    int32_t min_unconverged; /* Repulse Monkey needs this many unconverged samples, >= 1 (5)*/
+    double momentum;         /* mu of the momentum step (0.9)                               */
+    double anti_alpha;       /* step size alpha of the momentum step (0.01)                 */
+} sb_chisao_config;
+
+/* Bytes of device scratch sb_chisao needs (the solve stages' scratch plus its own). */
+size_t sb_chisao_workspace_bytes(const sb_problem *prob, const sb_config *cfg);
+
+/*
+ * ChiSao oscillation (Sec. 3.5.5) of n <= cfg->n_starts samples, FP64 only
+ * (cfg->prec must be SB_PREC_FP64, else SB_ERR_UNSUPPORTED). n_osc times:
+ *   convergence: sb_refine's L-BFGS from the current positions, at most
+ *     conv_iters accepted steps;
+ *   stick test: |grad l|_inf <= eps_grad (1 + |l|) and l >= max l + log 0.1;
+ *   dedup of the stuck samples (greedy L-inf, radius dedup_coarse
+ *     max_i (hi_i - lo_i), decreasing l): representatives stay stuck (the
+ *     peaks), the other stuck samples are lost;
+ *   unless this is the last oscillation, reseeding of the lost samples and
+ *   anti-convergence:
+ *     Repulse Monkey (at least min_unconverged samples fail the gradient
+ *       test): lost sample l (index order) casts a ray from unconverged sample
+ *       l mod n_unconv, clamped to the box, in a Philox-normal unit direction
+ *       (counter (pair, l, oscillation, 'RPMK'), key = seed) to the box face,
+ *       sampled at t_j = (j+1)/n_steps t_exit, and moves to its best sample;
+ *     Golden Rooster (otherwise, while it keeps finding peaks): lost sample l
+ *       goes to peak l mod n_peaks along +-column c mod d of orthonormal basis
+ *       c / d of that peak, c = (l / n_peaks) / 2 (+ for even l / n_peaks),
+ *       the bases the QR of Philox normals (counter (pair, basis d + column,
+ *       oscillation << 16 | peak, 'GRST')), to the best sample past the first
+ *       valley of the ray (the exit sample when l never rises); it stays off
+ *       after an oscillation that used it ends with no more peaks than before;
+ *     anti-convergence: every sample that is not stuck (and not NONFINITE)
+ *       takes anti_steps steps v <- momentum v - anti_alpha grad l,
+ *       x <- x + v (v = 0 at the start), clamped to the box.
+ * x0: [n][d] device; x_out: [n][d]; ell_out: [n] l after the last
+ * convergence phase; stuck_out: int8 [n], 1 at the peaks; n_peaks: int32
+ * device scalar. ws: sb_chisao_workspace_bytes. Synchronises `stream` (host
+ * reads of the peak and list counts each oscillation, and the refinement's).
+ */
+sb_status sb_chisao(const sb_problem *prob, const sb_config *cfg, const sb_chisao_config *cc, const double *x0,
+                    int32_t n, double *x_out, double *ell_out, int8_t *stuck_out, int32_t *n_peaks, void *ws,
+                    size_t ws_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -939,7 +939,7 @@ int orc_chisao(const orc_problem *p, const orc_config *c, const orc_chisao_confi
         int l_ord = 0;
         for (int s = 0; s < n; ++s) {
             if (!lost[s]) continue;
-            if (n_free >= cc->min_unconverged) {
+            if (n_free > 0 && n_free >= cc->min_unconverged) {
                 int which = l_ord % n_free, o = -1;
                 for (int q = 0; q < n; ++q)
                     if (!conv[q] && isfinite(ell[q]) && which-- == 0) {

@@ -68,8 +68,9 @@ def lib():
         L.sb_evidence_backward.restype = C.c_int
         L.sb_evidence_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.sb_chisao_workspace_bytes.restype = C.c_size_t
         for name in ("sb_loglik", "sb_loglik_noalloc", "sb_discover", "sb_refine", "sb_laplace", "sb_evidence", "sb_evidence_host",
-                     "sb_check"):
+                     "sb_check", "sb_chisao"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -230,6 +231,44 @@ def refine(prob: Problem, cfg: _Config, starts, ws: Workspace = None, stream=Non
     _check(lib().sb_refine(C.byref(prob.s), C.byref(cfg), _ptr(starts), C.c_int32(n), _ptr(x), _ptr(ell), _ptr(st),
                            _ptr(it), _ptr(ev), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)), "sb_refine")
     return RefineOut(x, ell, st, it, int(ev.item()))
+
+
+class _ChisaoConfig(C.Structure):
+    _fields_ = [("n_osc", C.c_int32), ("conv_iters", C.c_int32), ("anti_steps", C.c_int32),
+                ("min_unconverged", C.c_int32), ("momentum", C.c_double), ("anti_alpha", C.c_double)]
+
+
+def make_chisao_config(n_osc=3, conv_iters=1000, anti_steps=10, min_unconverged=5, momentum=0.9,
+                       anti_alpha=0.01) -> _ChisaoConfig:
+    return _ChisaoConfig(int(n_osc), int(conv_iters), int(anti_steps), int(min_unconverged), float(momentum),
+                         float(anti_alpha))
+
+
+def chisao_workspace(prob: Problem, cfg: _Config) -> Workspace:
+    return Workspace(int(lib().sb_chisao_workspace_bytes(C.byref(prob.s), C.byref(cfg))))
+
+
+@dataclass
+class ChisaoOut:
+    x: object
+    ell: object
+    stuck: object
+    n_peaks: int
+
+
+def chisao(prob: Problem, cfg: _Config, cc: _ChisaoConfig, x0, ws: Workspace = None, stream=None) -> ChisaoOut:
+    """ChiSao oscillation of the rows of x0 (FP64); the peaks are x[stuck]."""
+    torch = _torch()
+    ws = ws or chisao_workspace(prob, cfg)
+    x0 = x0.to(dtype=torch.float64).contiguous()
+    n = x0.shape[0]
+    x = torch.empty_like(x0)
+    ell = torch.empty(n, dtype=torch.float64, device=x0.device)
+    stuck = torch.empty(n, dtype=torch.int8, device=x0.device)
+    npk = torch.zeros(1, dtype=torch.int32, device=x0.device)
+    _check(lib().sb_chisao(C.byref(prob.s), C.byref(cfg), C.byref(cc), _ptr(x0), C.c_int32(n), _ptr(x), _ptr(ell),
+                           _ptr(stuck), _ptr(npk), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)), "sb_chisao")
+    return ChisaoOut(x, ell, stuck.bool(), int(npk.item()))
 
 
 @dataclass

@@ -1,0 +1,398 @@
+// chisao.cu -- kernels of the ChiSao oscillation (Sec. 3.5.5, Algorithm 1)
+// around the batched refinement: the stick test, the ordered sample lists,
+// the reseeding rays of Repulse Monkey (from unconverged samples, random
+// directions) and Golden Rooster (from the peaks, orthonormal directions),
+// the best sample along each ray, and the momentum anti-convergence step.
+//
+// The refinement, the likelihood evaluations and the L-infinity dedup are the
+// hot path's own kernels; the host loop in sb_capi.cu chains them. Everything
+// here is FP64 with explicitly rounded products and sums where an update
+// formula is applied, and the random directions come from Philox4x32-10 with
+// the seed as key (counters (pair, l, oscillation, 'RPMK') for Repulse Monkey,
+// (pair, basis d + column, oscillation << 16 | peak, 'GRST') for Golden
+// Rooster), two uniforms per block, two normals by Box-Muller.
+#include "sb_chisao.cuh"
+
+namespace sb {
+
+namespace {
+
+constexpr double kLogTenth = -2.302585092994045684;  // log 0.1, rounded to double
+constexpr uint32_t kTagRm = 0x52504D4Bu;             // 'RPMK'
+constexpr uint32_t kTagGr = 0x47525354u;             // 'GRST'
+
+__device__ __forceinline__ double clamp_box(double x, double lo, double hi) {
+    return x < lo ? lo : (x > hi ? hi : x);
+}
+
+// Two standard normals from one Philox block (Box-Muller on 52-bit uniforms).
+__device__ __forceinline__ void normal_pair(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                            uint32_t k1, double &z0, double &z1) {
+    uint32_t c[4] = {c0, c1, c2, c3};
+    philox4x32_10(c, k0, k1);
+    const double u1 = unit_from_words(c[0], c[1]);
+    const double u2 = unit_from_words(c[2], c[3]);
+    const double rad = sqrt(mul_rn(-2.0, log(u1)));
+    const double th = mul_rn(SB_TWO_PI, u2);
+    z0 = mul_rn(rad, cos(th));
+    z1 = mul_rn(rad, sin(th));
+}
+
+// Distance from o along u to the box boundary (whole warp; 0 when u = 0).
+__device__ double exit_length(int lane, int d, const double *o, const double *u, const double *lo, const double *hi) {
+    double t = INFINITY;
+    for (int i = lane; i < d; i += 32) {
+        const double ui = u[i];
+        if (ui > 0.0)
+            t = fmin(t, div_rn(sub_rn(hi[i], o[i]), ui));
+        else if (ui < 0.0)
+            t = fmin(t, div_rn(sub_rn(lo[i], o[i]), ui));
+    }
+    t = warp_min(t);
+    return t < INFINITY ? t : 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_cs_conv(int n, int d, const double *G, const double *ell, double eps,
+                                                 uint8_t *conv) {
+    const int lane = threadIdx.x & 31;
+    const int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (s >= n) return;
+    const double *g = G + (size_t)s * d;
+    double m = 0.0;
+    for (int i = lane; i < d; i += 32) m = fmax(m, fabs(g[i]));
+    m = warp_max(m);
+    if (lane == 0) {
+        const double l = ell[s];
+        conv[s] = (uint8_t)(isfinite(l) && m <= mul_rn(eps, add_rn(1.0, fabs(l))));
+    }
+}
+
+constexpr int CS_CTA = 1024;  // single-CTA list kernels
+
+__global__ void __launch_bounds__(CS_CTA) k_cs_stick(int n, const double *ell, const uint8_t *conv,
+                                                    uint8_t *stuck) {
+    __shared__ double s_m[CS_CTA / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double m = -INFINITY;
+    for (int s = threadIdx.x; s < n; s += CS_CTA) {
+        const double l = ell[s];
+        if (isfinite(l)) m = fmax(m, l);
+    }
+    m = warp_max(m);
+    if (lane == 0) s_m[wid] = m;
+    __syncthreads();
+    if (wid == 0) {
+        double v = s_m[lane];
+        v = warp_max(v);
+        if (lane == 0) s_m[0] = v;
+    }
+    __syncthreads();
+    const double thr = add_rn(s_m[0], kLogTenth);
+    for (int s = threadIdx.x; s < n; s += CS_CTA) stuck[s] = (uint8_t)(conv[s] && ell[s] >= thr);
+}
+
+__global__ void __launch_bounds__(CS_CTA) k_cs_split(int n, const int32_t *reps, const int32_t *n_reps,
+                                                    uint8_t *stuck, uint8_t *lost) {
+    for (int s = threadIdx.x; s < n; s += CS_CTA) lost[s] = stuck[s];
+    __syncthreads();
+    const int nr = *n_reps;
+    for (int r = threadIdx.x; r < nr && r < n; r += CS_CTA) lost[reps[r]] = 0;
+    __syncthreads();
+    for (int s = threadIdx.x; s < n; s += CS_CTA) stuck[s] = (uint8_t)(stuck[s] && !lost[s]);
+}
+
+__global__ void __launch_bounds__(CS_CTA) k_cs_lists(int n, const uint8_t *lost, const uint8_t *conv,
+                                                    const uint8_t *stuck, const int8_t *status, const double *ell,
+                                                    int32_t *lost_list, int32_t *unconv_list, int32_t *moving_list,
+                                                    int32_t *cnt) {
+    __shared__ int s_w[3][CS_CTA / 32];
+    __shared__ int s_base[3];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x < 3) s_base[threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned below = (1u << lane) - 1u;
+    for (int b0 = 0; b0 < n; b0 += CS_CTA) {
+        const int s = b0 + threadIdx.x;
+        bool p0 = false, p1 = false, p2 = false;
+        if (s < n) {
+            p0 = lost[s] != 0;
+            p1 = !conv[s] && isfinite(ell[s]);
+            p2 = !stuck[s] && status[s] != SB_WALKER_NONFINITE;
+        }
+        const unsigned m0 = __ballot_sync(0xffffffffu, p0);
+        const unsigned m1 = __ballot_sync(0xffffffffu, p1);
+        const unsigned m2 = __ballot_sync(0xffffffffu, p2);
+        if (lane == 0) {
+            s_w[0][wid] = __popc(m0);
+            s_w[1][wid] = __popc(m1);
+            s_w[2][wid] = __popc(m2);
+        }
+        __syncthreads();
+        int o0 = s_base[0], o1 = s_base[1], o2 = s_base[2];
+        for (int w = 0; w < wid; ++w) {
+            o0 += s_w[0][w];
+            o1 += s_w[1][w];
+            o2 += s_w[2][w];
+        }
+        if (p0) lost_list[o0 + __popc(m0 & below)] = s;
+        if (p1) unconv_list[o1 + __popc(m1 & below)] = s;
+        if (p2) moving_list[o2 + __popc(m2 & below)] = s;
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            int t = 0;
+            for (int w = 0; w < CS_CTA / 32; ++w) t += s_w[threadIdx.x][w];
+            s_base[threadIdx.x] += t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) cnt[threadIdx.x] = s_base[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256) k_cs_rm_rays(int n_lost, int d, uint32_t k0, uint32_t k1, int osc,
+                                                    const int32_t *unconv_list, int n_unconv, const double *X,
+                                                    const double *lo, const double *hi, double *O, double *U,
+                                                    double *texit) {
+    const int lane = threadIdx.x & 31;
+    const int l = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (l >= n_lost) return;
+    const double *src = X + (size_t)unconv_list[l % n_unconv] * d;
+    double *o = O + (size_t)l * d;
+    double *u = U + (size_t)l * d;
+    for (int i = lane; i < d; i += 32) o[i] = clamp_box(src[i], lo[i], hi[i]);
+    double ss = 0.0;
+    for (int q = lane; q < (d + 1) / 2; q += 32) {
+        double z0, z1;
+        normal_pair((uint32_t)q, (uint32_t)l, (uint32_t)osc, kTagRm, k0, k1, z0, z1);
+        u[2 * q] = z0;
+        ss += z0 * z0;
+        if (2 * q + 1 < d) {
+            u[2 * q + 1] = z1;
+            ss += z1 * z1;
+        }
+    }
+    const double nrm = sqrt(warp_sum(ss));
+    __syncwarp();
+    for (int i = lane; i < d; i += 32) u[i] = div_rn(u[i], nrm);
+    __syncwarp();
+    const double t = exit_length(lane, d, o, u, lo, hi);
+    if (lane == 0) texit[l] = t;
+}
+
+constexpr int CS_BASIS = 256;
+
+__global__ void __launch_bounds__(CS_BASIS) k_cs_bases(int d, uint32_t k0, uint32_t k1, int osc, const int32_t *job_pk,
+                                                       const int32_t *job_b, const int32_t *job_cols,
+                                                       const int64_t *job_off, double *Q) {
+    extern __shared__ double s_h[];  // [d] projections of the current column
+    __shared__ double s_red[CS_BASIS / 32];
+    const int j = blockIdx.x;
+    const int pk = job_pk[j], b = job_b[j], cols = job_cols[j];
+    double *Qj = Q + job_off[j];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = CS_BASIS / 32;
+    const int npairs = (d + 1) / 2;
+    for (int idx = threadIdx.x; idx < cols * npairs; idx += CS_BASIS) {
+        const int c = idx / npairs, q = idx - c * npairs;
+        double z0, z1;
+        normal_pair((uint32_t)q, (uint32_t)(b * d + c), ((uint32_t)osc << 16) | (uint32_t)pk, kTagGr, k0, k1, z0, z1);
+        Qj[(size_t)c * d + 2 * q] = z0;
+        if (2 * q + 1 < d) Qj[(size_t)c * d + 2 * q + 1] = z1;
+    }
+    __syncthreads();
+    for (int c = 0; c < cols; ++c) {
+        double *qc = Qj + (size_t)c * d;
+        for (int pass = 0; pass < 2 && c > 0; ++pass) {
+            for (int k = wid; k < c; k += nw) {
+                const double *qk = Qj + (size_t)k * d;
+                double dot = 0.0;
+                for (int i = lane; i < d; i += 32) dot += qk[i] * qc[i];
+                dot = warp_sum(dot);
+                if (lane == 0) s_h[k] = dot;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < d; i += CS_BASIS) {
+                double acc = 0.0;
+                for (int k = 0; k < c; ++k) acc += s_h[k] * Qj[(size_t)k * d + i];
+                qc[i] -= acc;
+            }
+            __syncthreads();
+        }
+        double ss = 0.0;
+        for (int i = threadIdx.x; i < d; i += CS_BASIS) ss += qc[i] * qc[i];
+        ss = warp_sum(ss);
+        if (lane == 0) s_red[wid] = ss;
+        __syncthreads();
+        if (wid == 0) {
+            double v = lane < nw ? s_red[lane] : 0.0;
+            v = warp_sum(v);
+            if (lane == 0) s_red[0] = v;
+        }
+        __syncthreads();
+        const double nrm = sqrt(s_red[0]);
+        for (int i = threadIdx.x; i < d; i += CS_BASIS) qc[i] = div_rn(qc[i], nrm);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cs_gr_rays(int n_lost, int d, int n_peaks, const int32_t *reps,
+                                                    const double *X, const double *lo, const double *hi,
+                                                    const int32_t *job_start, const int64_t *job_off, const double *Q,
+                                                    double *O, double *U, double *texit) {
+    const int lane = threadIdx.x & 31;
+    const int l = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (l >= n_lost) return;
+    const int pk = l % n_peaks, k = l / n_peaks, cdir = k >> 1;
+    const int b = cdir / d, col = cdir - b * d;
+    const double sgn = (k & 1) ? -1.0 : 1.0;
+    const double *q = Q + job_off[job_start[pk] + b] + (size_t)col * d;
+    const double *src = X + (size_t)reps[pk] * d;
+    double *o = O + (size_t)l * d;
+    double *u = U + (size_t)l * d;
+    for (int i = lane; i < d; i += 32) {
+        o[i] = clamp_box(src[i], lo[i], hi[i]);
+        u[i] = sgn * q[i];
+    }
+    __syncwarp();
+    const double t = exit_length(lane, d, o, u, lo, hi);
+    if (lane == 0) texit[l] = t;
+}
+
+__global__ void __launch_bounds__(256) k_cs_ray_points(int l0, int nl, int n_steps, int d, const double *O,
+                                                       const double *U, const double *texit, double *P) {
+    const int64_t total = (int64_t)nl * n_steps * d;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = idx / d;
+        const int i = (int)(idx - row * d);
+        const int l = l0 + (int)(row / n_steps), j = (int)(row % n_steps);
+        const double t = mul_rn(div_rn((double)(j + 1), (double)n_steps), texit[l]);
+        P[idx] = add_rn(O[(size_t)l * d + i], mul_rn(t, U[(size_t)l * d + i]));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cs_ray_pick(int l0, int nl, int n_steps, int d, int past_valley,
+                                                     const double *ellp, const int32_t *lost_list, const double *O,
+                                                     const double *U, const double *texit, double *X) {
+    const int lane = threadIdx.x & 31;
+    const int r = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (r >= nl) return;
+    const int l = l0 + r;
+    const double *e = ellp + (size_t)r * n_steps;
+    int best = 0;
+    if (lane == 0) {
+        int j0 = 0;
+        if (past_valley) {
+            // past the first valley: the first sample after which l rises; none: the exit sample
+            j0 = -1;
+            for (int j = 0; j + 1 < n_steps; ++j)
+                if (e[j + 1] > e[j]) {
+                    j0 = j + 1;
+                    break;
+                }
+            if (j0 < 0) j0 = n_steps - 1;
+        }
+        best = j0;
+        for (int j = j0 + 1; j < n_steps; ++j)
+            if (e[j] > e[best]) best = j;
+    }
+    best = __shfl_sync(0xffffffffu, best, 0);
+    const double t = mul_rn(div_rn((double)(best + 1), (double)n_steps), texit[l]);
+    double *x = X + (size_t)lost_list[l] * d;
+    for (int i = lane; i < d; i += 32) x[i] = add_rn(O[(size_t)l * d + i], mul_rn(t, U[(size_t)l * d + i]));
+}
+
+__global__ void __launch_bounds__(256) k_cs_momentum(int n, int d, const int32_t *moving_list,
+                                                     const int32_t *n_moving, double m, double alpha,
+                                                     const double *G, double *V, double *X, const double *lo,
+                                                     const double *hi) {
+    const int lane = threadIdx.x & 31;
+    const int e = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (e >= n || e >= *n_moving) return;
+    const size_t base = (size_t)moving_list[e] * d;
+    for (int i = lane; i < d; i += 32) {
+        const double v = sub_rn(mul_rn(m, V[base + i]), mul_rn(alpha, G[base + i]));
+        V[base + i] = v;
+        X[base + i] = clamp_box(add_rn(X[base + i], v), lo[i], hi[i]);
+    }
+}
+
+inline unsigned warp_grid(int64_t warps) { return (unsigned)((warps * 32 + 255) / 256); }
+
+}  // namespace
+
+void launch_cs_conv(int n, int d, const double *G, const double *ell, double eps, uint8_t *conv, cudaStream_t s) {
+    if (n <= 0) return;
+    note_launch();
+    k_cs_conv<<<warp_grid(n), 256, 0, s>>>(n, d, G, ell, eps, conv);
+}
+
+void launch_cs_stick(int n, const double *ell, const uint8_t *conv, uint8_t *stuck, cudaStream_t s) {
+    note_launch();
+    k_cs_stick<<<1, CS_CTA, 0, s>>>(n, ell, conv, stuck);
+}
+
+void launch_cs_split(int n, const int32_t *reps, const int32_t *n_reps, uint8_t *stuck, uint8_t *lost,
+                     cudaStream_t s) {
+    note_launch();
+    k_cs_split<<<1, CS_CTA, 0, s>>>(n, reps, n_reps, stuck, lost);
+}
+
+void launch_cs_lists(int n, const uint8_t *lost, const uint8_t *conv, const uint8_t *stuck, const int8_t *status,
+                     const double *ell, int32_t *lost_list, int32_t *unconv_list, int32_t *moving_list, int32_t *cnt,
+                     cudaStream_t s) {
+    note_launch();
+    k_cs_lists<<<1, CS_CTA, 0, s>>>(n, lost, conv, stuck, status, ell, lost_list, unconv_list, moving_list, cnt);
+}
+
+void launch_cs_rm_rays(int n_lost, int d, uint64_t seed, int osc, const int32_t *unconv_list, int n_unconv,
+                       const double *X, const double *lo, const double *hi, double *O, double *U, double *texit,
+                       cudaStream_t s) {
+    if (n_lost <= 0 || n_unconv <= 0) return;
+    note_launch();
+    k_cs_rm_rays<<<warp_grid(n_lost), 256, 0, s>>>(n_lost, d, (uint32_t)seed, (uint32_t)(seed >> 32), osc,
+                                                   unconv_list, n_unconv, X, lo, hi, O, U, texit);
+}
+
+void launch_cs_bases(int n_jobs, int d, uint64_t seed, int osc, const int32_t *job_pk, const int32_t *job_b,
+                     const int32_t *job_cols, const int64_t *job_off, double *Q, cudaStream_t s) {
+    if (n_jobs <= 0) return;
+    note_launch();
+    k_cs_bases<<<n_jobs, CS_BASIS, sizeof(double) * d, s>>>(d, (uint32_t)seed, (uint32_t)(seed >> 32), osc, job_pk,
+                                                            job_b, job_cols, job_off, Q);
+}
+
+void launch_cs_gr_rays(int n_lost, int d, int n_peaks, const int32_t *reps, const double *X, const double *lo,
+                       const double *hi, const int32_t *job_start, const int64_t *job_off, const double *Q, double *O,
+                       double *U, double *texit, cudaStream_t s) {
+    if (n_lost <= 0 || n_peaks <= 0) return;
+    note_launch();
+    k_cs_gr_rays<<<warp_grid(n_lost), 256, 0, s>>>(n_lost, d, n_peaks, reps, X, lo, hi, job_start, job_off, Q, O, U,
+                                                   texit);
+}
+
+void launch_cs_ray_points(int l0, int nl, int n_steps, int d, const double *O, const double *U, const double *texit,
+                          double *P, cudaStream_t s) {
+    if (nl <= 0) return;
+    const int64_t total = (int64_t)nl * n_steps * d;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    note_launch();
+    k_cs_ray_points<<<(unsigned)blocks, 256, 0, s>>>(l0, nl, n_steps, d, O, U, texit, P);
+}
+
+void launch_cs_ray_pick(int l0, int nl, int n_steps, int d, int past_valley, const double *ellp,
+                        const int32_t *lost_list, const double *O, const double *U, const double *texit, double *X,
+                        cudaStream_t s) {
+    if (nl <= 0) return;
+    note_launch();
+    k_cs_ray_pick<<<warp_grid(nl), 256, 0, s>>>(l0, nl, n_steps, d, past_valley, ellp, lost_list, O, U, texit, X);
+}
+
+void launch_cs_momentum(int n, int d, const int32_t *moving_list, const int32_t *n_moving, double momentum,
+                        double alpha, const double *G, double *V, double *X, const double *lo, const double *hi,
+                        cudaStream_t s) {
+    if (n <= 0) return;
+    note_launch();
+    k_cs_momentum<<<warp_grid(n), 256, 0, s>>>(n, d, moving_list, n_moving, momentum, alpha, G, V, X, lo, hi);
+}
+
+}  // namespace sb

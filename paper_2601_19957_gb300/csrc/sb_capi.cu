@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "sb_adjoint.cuh"
+#include "sb_chisao.cuh"
 #include "sb_internal.cuh"
 #include "sb_laplace.cuh"
 #include "sb_lbfgs.cuh"
@@ -999,3 +1000,220 @@ extern "C" sb_status sb_evidence_batched(const sb_problem *probs, int32_t P, con
 }
 
 extern "C" int32_t sb_tuned_tile(int32_t d, int32_t K, int32_t prec) { return tc_tuned_tile(d, K, prec); }
+
+// ------------------------------------------------------------------ ChiSao (Sec. 3.5.5)
+namespace {
+
+struct ChisaoWs {
+    double *X, *V, *G, *ell, *ellg, *O, *U, *texit, *Q, *P, *ellp, *qp;
+    int8_t *status;
+    uint8_t *conv, *stuck, *lost;
+    int32_t *reps, *n_reps, *lost_list, *unconv_list, *moving_list, *cnt;
+    int32_t *job_start, *job_pk, *job_b, *job_cols;
+    int64_t *job_off;
+    int lc;  // lost samples per chunk of ray samples
+    size_t bytes;
+};
+
+// Carved after the solve stages' layout (offset `off`), for up to n_starts samples.
+ChisaoWs chisao_layout(void *base, size_t off, const sb_problem *p, const sb_config *c) {
+    ChisaoWs w{};
+    Carver cv(base ? static_cast<char *>(base) + off : nullptr);
+    const int n = c->n_starts, d = p->d, K = p->K;
+    w.lc = n / c->n_steps > 0 ? n / c->n_steps : 1;
+    const int rows = w.lc * c->n_steps;
+    w.X = cv.take<double>((size_t)n * d);
+    w.V = cv.take<double>((size_t)n * d);
+    w.G = cv.take<double>((size_t)n * d);
+    w.O = cv.take<double>((size_t)n * d);
+    w.U = cv.take<double>((size_t)n * d);
+    w.Q = cv.take<double>((size_t)n * d);  // Golden Rooster bases: at most one column per lost sample
+    w.ell = cv.take<double>(n);
+    w.ellg = cv.take<double>(n);
+    w.texit = cv.take<double>(n);
+    w.P = cv.take<double>((size_t)rows * d);
+    w.ellp = cv.take<double>(rows);
+    w.qp = cv.take<double>(lik_f64_qpart_elems(d, K, rows));
+    w.status = cv.take<int8_t>(n);
+    w.conv = cv.take<uint8_t>(n);
+    w.stuck = cv.take<uint8_t>(n);
+    w.lost = cv.take<uint8_t>(n);
+    w.reps = cv.take<int32_t>(n);
+    w.n_reps = cv.take<int32_t>(1);
+    w.lost_list = cv.take<int32_t>(n);
+    w.unconv_list = cv.take<int32_t>(n);
+    w.moving_list = cv.take<int32_t>(n);
+    w.cnt = cv.take<int32_t>(4);
+    w.job_start = cv.take<int32_t>((size_t)n + 1);
+    w.job_pk = cv.take<int32_t>(n);
+    w.job_b = cv.take<int32_t>(n);
+    w.job_cols = cv.take<int32_t>(n);
+    w.job_off = cv.take<int64_t>(n);
+    w.bytes = cv.bytes();
+    return w;
+}
+
+sb_status check_chisao(const sb_chisao_config *cc) {
+    if (!cc) return SB_ERR_INVALID_ARG;
+    if (cc->n_osc < 1 || cc->n_osc > 1024 || cc->conv_iters < 0 || cc->anti_steps < 0 || cc->anti_steps > 100000 ||
+        cc->min_unconverged < 1)
+        return SB_ERR_INVALID_ARG;
+    if (!std::isfinite(cc->momentum) || !std::isfinite(cc->anti_alpha)) return SB_ERR_INVALID_ARG;
+    return SB_OK;
+}
+
+// Golden Rooster bases for n_lost lost samples over n_peaks peaks: lost sample l uses
+// direction c = (l / n_peaks) / 2 of peak l mod n_peaks, i.e. column c mod d of basis
+// c / d; every basis a peak needs is one job, its columns only as far as used.
+struct GrJobs {
+    std::vector<int32_t> start, pk, b, cols;
+    std::vector<int64_t> off;
+};
+GrJobs gr_jobs(int n_lost, int n_peaks, int d) {
+    GrJobs j;
+    j.start.assign((size_t)n_peaks + 1, 0);
+    int64_t off = 0;
+    for (int p = 0; p < n_peaks; ++p) {
+        j.start[p] = (int32_t)j.pk.size();
+        const int count = n_lost > p ? (n_lost - p + n_peaks - 1) / n_peaks : 0;
+        if (count == 0) continue;
+        const int cmax = (count - 1) / 2;
+        for (int b = 0; b <= cmax / d; ++b) {
+            const int cols = b < cmax / d ? d : cmax - b * d + 1;
+            j.pk.push_back(p);
+            j.b.push_back(b);
+            j.cols.push_back(cols);
+            j.off.push_back(off);
+            off += (int64_t)cols * d;
+        }
+    }
+    j.start[n_peaks] = (int32_t)j.pk.size();
+    return j;
+}
+
+}  // namespace
+
+extern "C" size_t sb_chisao_workspace_bytes(const sb_problem *p, const sb_config *c) {
+    if (check_problem(p) != SB_OK || check_config(c) != SB_OK) return 0;
+    const size_t base = layout(nullptr, p, c).bytes;
+    return base + chisao_layout(nullptr, base, p, c).bytes;
+}
+
+extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb_chisao_config *cc, const double *x0,
+                               int32_t n, double *x_out, double *ell_out, int8_t *stuck_out, int32_t *n_peaks,
+                               void *ws, size_t ws_bytes, void *stream) {
+    if (!x0 || !x_out || !ell_out || !stuck_out || !n_peaks) return SB_ERR_INVALID_ARG;
+    if (!c || n < 1 || n > c->n_starts) return SB_ERR_INVALID_ARG;
+    sb_status st = check_chisao(cc);
+    if (st != SB_OK) return st;
+    if (c->prec != SB_PREC_FP64) return SB_ERR_UNSUPPORTED;
+    Prelude P;
+    st = prelude(p, c, ws, ws_bytes, stream, P);
+    if (st != SB_OK) return st;
+    const ChisaoWs w = chisao_layout(ws, P.L.bytes, p, c);
+    if (ws_bytes < P.L.bytes + w.bytes) return SB_ERR_WORKSPACE;
+    const int d = p->d;
+    const cudaStream_t s = P.s;
+    const ProbView &pv = P.pv;
+    const auto &la = P.L.la;
+    const auto &r = P.L.r64;
+    sb_config c2 = *c;
+    c2.max_iter = cc->conv_iters;
+    const DedupScratch dds{la.dd_l, la.dd_i, la.dd_bar, pv.status};
+    SB_CUDA_TRY(cudaMemcpyAsync(w.X, x0, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, s));
+    // l and grad l at the samples listed in rows (all n when rows is null)
+    auto grad_at = [&](const int32_t *rows, const int32_t *n_rows_dev, int n_rows) {
+        LikF64Args a = f64_args(pv);
+        a.X = w.X;
+        a.rows = rows;
+        a.n_rows_dev = n_rows_dev;
+        a.n_rows = n_rows;
+        a.qpart = r.qpart;
+        a.Z = r.Z;
+        a.R = r.R;
+        a.ell = w.ellg;
+        a.G = w.G;
+        a.out_by_walker = 1;
+        launch_lik_f64_points(a, true, s);
+    };
+    bool gr_on = true, gr_used_prev = false;
+    int peaks_prev = -1;
+    for (int osc = 0; osc < cc->n_osc; ++osc) {
+        // convergence phase: every sample released, L-BFGS from where it is
+        st = run_refine<double>(pv, &c2, r, w.X, n, w.X, w.ell, w.status, nullptr, nullptr, s);
+        if (st != SB_OK) return st;
+        // stick test, then the dedup of the stuck samples (representatives stay stuck)
+        grad_at(nullptr, nullptr, n);
+        launch_cs_conv(n, d, w.G, w.ell, c->eps_grad, w.conv, s);
+        launch_cs_stick(n, w.ell, w.conv, w.stuck, s);
+        launch_dedup(n, d, w.X, w.ell, nullptr, w.stuck, c->dedup_coarse, pv.wmax, n, w.reps, w.n_reps, la.assigned,
+                     dds, s);
+        launch_cs_split(n, w.reps, w.n_reps, w.stuck, w.lost, s);
+        int32_t h_peaks = 0;
+        SB_CUDA_TRY(cudaMemcpyAsync(&h_peaks, w.n_reps, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SB_CUDA_TRY(cudaStreamSynchronize(s));
+        if (gr_used_prev && h_peaks <= peaks_prev) gr_on = false;
+        gr_used_prev = false;
+        peaks_prev = h_peaks;
+        if (osc == cc->n_osc - 1) break;
+        // reseeding of the lost samples
+        launch_cs_lists(n, w.lost, w.conv, w.stuck, w.status, w.ell, w.lost_list, w.unconv_list, w.moving_list, w.cnt,
+                        s);
+        int32_t h_cnt[3] = {0, 0, 0};
+        SB_CUDA_TRY(cudaMemcpyAsync(h_cnt, w.cnt, sizeof(h_cnt), cudaMemcpyDeviceToHost, s));
+        SB_CUDA_TRY(cudaStreamSynchronize(s));
+        const int n_lost = h_cnt[0], n_unconv = h_cnt[1], n_moving = h_cnt[2];
+        int past_valley = -1;
+        if (n_lost > 0 && n_unconv >= cc->min_unconverged) {
+            launch_cs_rm_rays(n_lost, d, c->seed, osc, w.unconv_list, n_unconv, w.X, pv.lo, pv.hi, w.O, w.U, w.texit,
+                              s);
+            past_valley = 0;
+        } else if (n_lost > 0 && gr_on && h_peaks > 0) {
+            const GrJobs j = gr_jobs(n_lost, h_peaks, d);
+            const int nj = (int)j.pk.size();
+            SB_CUDA_TRY(cudaMemcpyAsync(w.job_start, j.start.data(), sizeof(int32_t) * j.start.size(),
+                                        cudaMemcpyHostToDevice, s));
+            SB_CUDA_TRY(cudaMemcpyAsync(w.job_pk, j.pk.data(), sizeof(int32_t) * nj, cudaMemcpyHostToDevice, s));
+            SB_CUDA_TRY(cudaMemcpyAsync(w.job_b, j.b.data(), sizeof(int32_t) * nj, cudaMemcpyHostToDevice, s));
+            SB_CUDA_TRY(cudaMemcpyAsync(w.job_cols, j.cols.data(), sizeof(int32_t) * nj, cudaMemcpyHostToDevice, s));
+            SB_CUDA_TRY(cudaMemcpyAsync(w.job_off, j.off.data(), sizeof(int64_t) * nj, cudaMemcpyHostToDevice, s));
+            launch_cs_bases(nj, d, c->seed, osc, w.job_pk, w.job_b, w.job_cols, w.job_off, w.Q, s);
+            launch_cs_gr_rays(n_lost, d, h_peaks, w.reps, w.X, pv.lo, pv.hi, w.job_start, w.job_off, w.Q, w.O, w.U,
+                              w.texit, s);
+            SB_CUDA_TRY(cudaStreamSynchronize(s));  // the job tables above are host vectors
+            past_valley = 1;
+            gr_used_prev = true;
+        }
+        if (past_valley >= 0) {
+            for (int l0 = 0; l0 < n_lost; l0 += w.lc) {
+                const int nl = n_lost - l0 < w.lc ? n_lost - l0 : w.lc;
+                launch_cs_ray_points(l0, nl, c->n_steps, d, w.O, w.U, w.texit, w.P, s);
+                LikF64Args a = f64_args(pv);
+                a.X = w.P;
+                a.n_rows = nl * c->n_steps;
+                a.qpart = w.qp;
+                a.ell = w.ellp;
+                a.out_by_walker = 0;
+                launch_lik_f64_points(a, false, s);
+                launch_cs_ray_pick(l0, nl, c->n_steps, d, past_valley, w.ellp, w.lost_list, w.O, w.U, w.texit, w.X,
+                                   s);
+            }
+        }
+        // anti-convergence of every sample that is not stuck
+        if (cc->anti_steps > 0 && n_moving > 0) {
+            SB_CUDA_TRY(cudaMemsetAsync(w.V, 0, sizeof(double) * n * d, s));
+            for (int t = 0; t < cc->anti_steps; ++t) {
+                grad_at(w.moving_list, w.cnt + 2, n_moving);
+                launch_cs_momentum(n_moving, d, w.moving_list, w.cnt + 2, cc->momentum, cc->anti_alpha, w.G, w.V, w.X,
+                                   pv.lo, pv.hi, s);
+            }
+        }
+        SB_CUDA_TRY(cudaGetLastError());
+    }
+    SB_CUDA_TRY(cudaMemcpyAsync(x_out, w.X, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, s));
+    SB_CUDA_TRY(cudaMemcpyAsync(ell_out, w.ell, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    SB_CUDA_TRY(cudaMemcpyAsync(stuck_out, w.stuck, n, cudaMemcpyDeviceToDevice, s));
+    SB_CUDA_TRY(cudaMemcpyAsync(n_peaks, w.n_reps, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    SB_CUDA_TRY(cudaGetLastError());
+    return SB_OK;
+}

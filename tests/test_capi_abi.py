@@ -57,3 +57,23 @@ def test_entry_points_reject_invalid_arguments_before_any_launch():
     buf = (C.c_char * 16)()
     assert L.sb_evidence(C.byref(p), C.byref(cfg), buf, buf, buf, 1, buf, buf, C.c_size_t(16), None) == \
         sb.SB_ERR_WORKSPACE
+
+
+def test_chisao_rejects_bad_config_and_mixed_precision_on_the_host():
+    cfg = sb.make_config(SolveConfig(n_starts=16))
+    p = _fake_problem(8, 1)
+    L = sb.lib()
+    buf = (C.c_char * 16)()
+    cc = sb.make_chisao_config()
+    args = lambda cfg_, cc_: (C.byref(p), C.byref(cfg_), cc_, buf, 4, buf, buf, buf, buf, buf, C.c_size_t(16), None)
+    assert L.sb_chisao(*args(cfg, None)) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_chisao(*args(cfg, C.byref(sb.make_chisao_config(min_unconverged=0)))) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_chisao(*args(cfg, C.byref(sb.make_chisao_config(n_osc=0)))) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_chisao(*args(cfg, C.byref(sb.make_chisao_config(momentum=float("nan"))))) == sb.SB_ERR_INVALID_ARG
+    bf16 = sb.make_config(SolveConfig(n_starts=16, prec=sb.PREC_BF16))
+    assert L.sb_chisao(*args(bf16, C.byref(cc))) == sb.SB_ERR_UNSUPPORTED
+    too_many = (C.byref(p), C.byref(cfg), C.byref(cc), buf, 17, buf, buf, buf, buf, buf, C.c_size_t(16), None)
+    assert L.sb_chisao(*too_many) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_chisao(*args(cfg, C.byref(cc))) == sb.SB_ERR_WORKSPACE
+    base = L.sb_workspace_bytes(C.byref(p), C.byref(cfg))
+    assert L.sb_chisao_workspace_bytes(C.byref(p), C.byref(cfg)) > base > 0
