@@ -58,7 +58,7 @@ def lib():
         _lib = C.CDLL(build())
         _lib.orc_loglik.restype = C.c_double
         for name in ("orc_select_starts", "orc_discover", "orc_cholesky", "orc_laplace", "orc_evidence",
-                     "orc_chisao_ray_best", "orc_chisao"):
+                     "orc_chisao_ray_best", "orc_chisao", "orc_precheck"):
             getattr(_lib, name).restype = C.c_int
     return _lib
 
@@ -285,3 +285,28 @@ def chisao(inst, cfg, cc: ChisaoConfig, x0, n_threads=1) -> ChisaoResult:
     npk = lib().orc_chisao(C.byref(P.s), C.byref(c), C.byref(k), _ptr(x0), C.c_int(n), _ptr(xo), _ptr(lo),
                            _ptr(st))
     return ChisaoResult(xo, lo, st.astype(bool), int(npk))
+
+
+# ------------------------------------------------------------- preprocessing (Sec. 3.4)
+ACTIVE, FLAT, SOFT = 0, 1, 2
+
+
+@dataclass
+class PrecheckResult:
+    s: np.ndarray
+    cls: np.ndarray
+    log_int: float
+    log_vol: float
+    n_active: int
+
+
+def precheck(inst, eps_flat=1e-6, eps_soft=1e-3) -> PrecheckResult:
+    """Sensitivity probe and flat / soft-nuisance classification with the marginal terms."""
+    P = OracleProblem(inst)
+    s = np.empty(P.d)
+    cls = np.empty(P.d, dtype=np.int8)
+    li = C.c_double(0.0)
+    lv = C.c_double(0.0)
+    na = lib().orc_precheck(C.byref(P.s), C.c_double(eps_flat), C.c_double(eps_soft), _ptr(s), _ptr(cls),
+                            C.byref(li), C.byref(lv))
+    return PrecheckResult(s, cls, li.value, lv.value, int(na))

@@ -986,3 +986,77 @@ int orc_chisao(const orc_problem *p, const orc_config *c, const orc_chisao_confi
     free(x);
     return n_peaks;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Preprocessing: dimensional pathology detection (Sec. 3.4, its Algorithm).  */
+/* 2d + 1 evaluations: l at the box centre c and at c +- Delta_i e_i, with    */
+/* Delta_i = (hi_i - lo_i) / 2; sensitivity s_i = |l(c + Delta_i e_i) - l(c)| */
+/* + |l(c - Delta_i e_i) - l(c)|. Flat: s_i < eps_flat median(s); soft:       */
+/* s_i < eps_soft max(s) and not flat; the rest is active. Readings:          */
+/*  - median of an even count is the mean of the two middle values; median    */
+/*    and max run over the finite s_i, and a non-finite s_i is active;        */
+/*  - the marginal integrals: a flat coordinate integrates a constant over    */
+/*    [lo_i, hi_i], log(2 Delta_i) (the paper prints log Delta_i); a soft     */
+/*    one a Gaussian of width sigma_i = Delta_i / sqrt(s_i), 1/2 log 2 pi +   */
+/*    log sigma_i; their sum is *log_int, and *log_vol is the flagged         */
+/*    coordinates' share of log V, sum log(2 Delta_i), so that the evidence   */
+/*    of the full problem is that of the active problem (l with the flagged   */
+/*    coordinates held at c, prior over the active box) + *log_int -          */
+/*    *log_vol.                                                               */
+/* ------------------------------------------------------------------------ */
+static int dbl_cmp(const void *a, const void *b) {
+    const double x = *(const double *)a, y = *(const double *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+int orc_precheck(const orc_problem *p, double eps_flat, double eps_soft, double *s_out, int8_t *cls_out,
+                 double *log_int, double *log_vol) {
+    const int d = p->d;
+    double *c = (double *)malloc(sizeof(double) * (size_t)d);
+    double *x = (double *)malloc(sizeof(double) * (size_t)d);
+    double *fin = (double *)malloc(sizeof(double) * (size_t)d);
+    for (int i = 0; i < d; ++i) c[i] = 0.5 * (p->lo[i] + p->hi[i]);
+    const double l0 = orc_loglik(p, c, NULL, NULL);
+    int nf = 0;
+    for (int i = 0; i < d; ++i) {
+        const double delta = 0.5 * (p->hi[i] - p->lo[i]);
+        memcpy(x, c, sizeof(double) * (size_t)d);
+        x[i] = c[i] + delta;
+        const double lp = orc_loglik(p, x, NULL, NULL);
+        x[i] = c[i] - delta;
+        const double lm = orc_loglik(p, x, NULL, NULL);
+        s_out[i] = fabs(lp - l0) + fabs(lm - l0);
+        if (isfinite(s_out[i])) fin[nf++] = s_out[i];
+    }
+    double med = 0.0, smax = 0.0;
+    if (nf > 0) {
+        qsort(fin, (size_t)nf, sizeof(double), dbl_cmp);
+        med = (nf % 2) ? fin[nf / 2] : 0.5 * (fin[nf / 2 - 1] + fin[nf / 2]);
+        smax = fin[nf - 1];
+    }
+    int n_active = 0;
+    double li = 0.0, lv = 0.0;
+    for (int i = 0; i < d; ++i) {
+        const double delta = 0.5 * (p->hi[i] - p->lo[i]);
+        int8_t cl = 0;
+        if (isfinite(s_out[i])) {
+            if (s_out[i] < eps_flat * med)
+                cl = 1;
+            else if (s_out[i] < eps_soft * smax)
+                cl = 2;
+        }
+        cls_out[i] = cl;
+        if (cl == 0) {
+            ++n_active;
+        } else {
+            lv += log(2.0 * delta);
+            li += (cl == 1) ? log(2.0 * delta) : 0.5 * log(ORC_TWO_PI) + log(delta / sqrt(s_out[i]));
+        }
+    }
+    if (log_int) *log_int = li;
+    if (log_vol) *log_vol = lv;
+    free(fin);
+    free(x);
+    free(c);
+    return n_active;
+}

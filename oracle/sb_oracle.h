@@ -94,6 +94,11 @@ int orc_chisao_ray_best(const orc_problem *p, const double *origin, const double
 int orc_chisao(const orc_problem *p, const orc_config *c, const orc_chisao_config *cc, const double *x0, int n,
                double *x_out, double *ell_out, int8_t *stuck_out);
 
+/* Preprocessing (Sec. 3.4): sensitivities s[d], classes cls[d] (0 active, 1 flat, 2 soft), the flagged
+ * coordinates' marginal log-integral *log_int and log-volume *log_vol; returns the active count. */
+int orc_precheck(const orc_problem *p, double eps_flat, double eps_soft, double *s_out, int8_t *cls_out,
+                 double *log_int, double *log_vol);
+
 #ifdef __cplusplus
 }
 #endif
