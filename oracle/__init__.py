@@ -60,6 +60,8 @@ def lib():
         for name in ("orc_select_starts", "orc_discover", "orc_cholesky", "orc_laplace", "orc_evidence",
                      "orc_chisao_ray_best", "orc_chisao", "orc_precheck"):
             getattr(_lib, name).restype = C.c_int
+        for name in ("orc_uniform_corr_probe", "orc_perp_fraction"):
+            getattr(_lib, name).restype = C.c_double
     return _lib
 
 
@@ -310,3 +312,42 @@ def precheck(inst, eps_flat=1e-6, eps_soft=1e-3) -> PrecheckResult:
     na = lib().orc_precheck(C.byref(P.s), C.c_double(eps_flat), C.c_double(eps_soft), _ptr(s), _ptr(cls),
                             C.byref(li), C.byref(lv))
     return PrecheckResult(s, cls, li.value, lv.value, int(na))
+
+
+# ------------------------------------------ black-box derivatives and rotation (App. A.4, Sec. 3.7.2)
+def fd_grad(inst, x, eps=1e-5):
+    P = OracleProblem(inst)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    g = np.empty(P.d)
+    lib().orc_fd_grad(C.byref(P.s), _ptr(x), C.c_double(eps), _ptr(g))
+    return g
+
+
+def fd_hess_diag(inst, x, eps=1e-4):
+    P = OracleProblem(inst)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    h = np.empty(P.d)
+    lib().orc_fd_hess_diag(C.byref(P.s), _ptr(x), C.c_double(eps), _ptr(h))
+    return h
+
+
+def fd_hess_full(inst, x, eps=1e-4):
+    P = OracleProblem(inst)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    H = np.empty((P.d, P.d))
+    lib().orc_fd_hess_full(C.byref(P.s), _ptr(x), C.c_double(eps), _ptr(H))
+    return H
+
+
+def uniform_corr_probe(inst, x, hdiag, eps=1e-4):
+    P = OracleProblem(inst)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    h = np.ascontiguousarray(hdiag, dtype=np.float64)
+    return float(lib().orc_uniform_corr_probe(C.byref(P.s), _ptr(x), C.c_double(eps), _ptr(h)))
+
+
+def perp_fraction(dtheta, grad, hdiag):
+    dt = np.ascontiguousarray(dtheta, dtype=np.float64)
+    g = np.ascontiguousarray(grad, dtype=np.float64)
+    h = np.ascontiguousarray(hdiag, dtype=np.float64)
+    return float(lib().orc_perp_fraction(C.c_int(len(dt)), _ptr(dt), _ptr(g), _ptr(h)))

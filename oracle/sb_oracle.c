@@ -1060,3 +1060,109 @@ int orc_precheck(const orc_problem *p, double eps_flat, double eps_soft, double 
     free(c);
     return n_active;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Black-box derivatives and rotation detection (App. A.4, Sec. 3.7.2).       */
+/* Central differences of l with step eps along the axes; the Hessians are of */
+/* l itself (negative definite at a maximum), as printed. Readings:           */
+/*  - the full Hessian takes its diagonal from the 2d + 1 axis evaluations    */
+/*    and each off-diagonal pair i < j from four evaluations at              */
+/*    x +- eps e_i +- eps e_j, mirrored to j, i (2 d^2 + 1 evaluations in     */
+/*    all);                                                                   */
+/*  - the uniform-correlation probe takes v^T H v from the second difference  */
+/*    of l along v = (1, ..., 1) / sqrt(d) (the two evaluations x +- eps v)   */
+/*    and a = mean H_ii from the diagonal second differences;                 */
+/*  - the perpendicular step fraction whitens a step and the gradient at its  */
+/*    start by w_i = sqrt(-H_ii): dtheta~ = w dtheta, g~ = grad l / w (the    */
+/*    gradient of l in the whitened coordinates), and f_perp is the part of   */
+/*    dtheta~ orthogonal to g~, relative to |dtheta~|; it is 0 for a zero     */
+/*    step or gradient and NaN when some H_ii >= 0.                           */
+/* ------------------------------------------------------------------------ */
+static double loglik_shift2(const orc_problem *p, const double *x, double *xs, int i, double ai, int j, double aj) {
+    memcpy(xs, x, sizeof(double) * (size_t)p->d);
+    if (i >= 0) xs[i] = x[i] + ai;
+    if (j >= 0) xs[j] = xs[j] + aj;
+    return orc_loglik(p, xs, NULL, NULL);
+}
+
+void orc_fd_grad(const orc_problem *p, const double *x, double eps, double *g) {
+    double *xs = (double *)malloc(sizeof(double) * (size_t)p->d);
+    for (int i = 0; i < p->d; ++i) {
+        const double fp = loglik_shift2(p, x, xs, i, eps, -1, 0.0);
+        const double fm = loglik_shift2(p, x, xs, i, -eps, -1, 0.0);
+        g[i] = (fp - fm) / (2.0 * eps);
+    }
+    free(xs);
+}
+
+void orc_fd_hess_diag(const orc_problem *p, const double *x, double eps, double *hdiag) {
+    double *xs = (double *)malloc(sizeof(double) * (size_t)p->d);
+    const double f0 = orc_loglik(p, x, NULL, NULL);
+    for (int i = 0; i < p->d; ++i) {
+        const double fp = loglik_shift2(p, x, xs, i, eps, -1, 0.0);
+        const double fm = loglik_shift2(p, x, xs, i, -eps, -1, 0.0);
+        hdiag[i] = (fp - 2.0 * f0 + fm) / (eps * eps);
+    }
+    free(xs);
+}
+
+void orc_fd_hess_full(const orc_problem *p, const double *x, double eps, double *H) {
+    const int d = p->d;
+    double *xs = (double *)malloc(sizeof(double) * (size_t)d);
+    double *hd = (double *)malloc(sizeof(double) * (size_t)d);
+    orc_fd_hess_diag(p, x, eps, hd);
+    for (int i = 0; i < d; ++i) {
+        H[(size_t)i * d + i] = hd[i];
+        for (int j = i + 1; j < d; ++j) {
+            const double fpp = loglik_shift2(p, x, xs, i, eps, j, eps);
+            const double fpm = loglik_shift2(p, x, xs, i, eps, j, -eps);
+            const double fmp = loglik_shift2(p, x, xs, i, -eps, j, eps);
+            const double fmm = loglik_shift2(p, x, xs, i, -eps, j, -eps);
+            const double h = (fpp - fpm - fmp + fmm) / (4.0 * eps * eps);
+            H[(size_t)i * d + j] = h;
+            H[(size_t)j * d + i] = h;
+        }
+    }
+    free(hd);
+    free(xs);
+}
+
+double orc_uniform_corr_probe(const orc_problem *p, const double *x, double eps, const double *hdiag) {
+    const int d = p->d;
+    if (d < 2) return 0.0;
+    double *xs = (double *)malloc(sizeof(double) * (size_t)d);
+    const double f0 = orc_loglik(p, x, NULL, NULL);
+    const double vi = 1.0 / sqrt((double)d);
+    for (int i = 0; i < d; ++i) xs[i] = x[i] + eps * vi;
+    const double fp = orc_loglik(p, xs, NULL, NULL);
+    for (int i = 0; i < d; ++i) xs[i] = x[i] - eps * vi;
+    const double fm = orc_loglik(p, xs, NULL, NULL);
+    const double vhv = (fp - 2.0 * f0 + fm) / (eps * eps);
+    double a = 0.0;
+    for (int i = 0; i < d; ++i) a += hdiag[i];
+    a /= (double)d;
+    free(xs);
+    return (vhv - a) / (double)(d - 1);
+}
+
+double orc_perp_fraction(int d, const double *dtheta, const double *grad, const double *hdiag) {
+    double ss = 0.0, gg = 0.0, sg = 0.0;
+    for (int i = 0; i < d; ++i) {
+        if (!(hdiag[i] < 0.0)) return NAN;
+        const double w = sqrt(-hdiag[i]);
+        const double st = w * dtheta[i], gt = grad[i] / w;
+        ss += st * st;
+        gg += gt * gt;
+        sg += st * gt;
+    }
+    if (ss == 0.0 || gg == 0.0) return 0.0;
+    /* dtheta~_perp = dtheta~ - (dtheta~ . g~ / |g~|^2) g~, formed explicitly */
+    const double c = sg / gg;
+    double pp = 0.0;
+    for (int i = 0; i < d; ++i) {
+        const double w = sqrt(-hdiag[i]);
+        const double q = w * dtheta[i] - c * (grad[i] / w);
+        pp += q * q;
+    }
+    return sqrt(pp / ss);
+}

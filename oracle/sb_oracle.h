@@ -99,6 +99,16 @@ int orc_chisao(const orc_problem *p, const orc_config *c, const orc_chisao_confi
 int orc_precheck(const orc_problem *p, double eps_flat, double eps_soft, double *s_out, int8_t *cls_out,
                  double *log_int, double *log_vol);
 
+/* Central-difference derivatives of l (App. A.4), Hessians of l itself: gradient (2d evaluations),
+ * diagonal (2d + 1), full d*d row-major (2 d^2 + 1). */
+void orc_fd_grad(const orc_problem *p, const double *x, double eps, double *g);
+void orc_fd_hess_diag(const orc_problem *p, const double *x, double eps, double *hdiag);
+void orc_fd_hess_full(const orc_problem *p, const double *x, double eps, double *H);
+/* Uniform-correlation probe b = (v^T H v - mean H_ii) / (d - 1), v = 1/sqrt(d) (Sec. 3.7.2). */
+double orc_uniform_corr_probe(const orc_problem *p, const double *x, double eps, const double *hdiag);
+/* Perpendicular step fraction of one step in coordinates whitened by sqrt(-H_ii) (Sec. 3.7.2). */
+double orc_perp_fraction(int d, const double *dtheta, const double *grad, const double *hdiag);
+
 #ifdef __cplusplus
 }
 #endif
