@@ -58,7 +58,7 @@ def lib():
         _lib = C.CDLL(build())
         _lib.orc_loglik.restype = C.c_double
         for name in ("orc_select_starts", "orc_discover", "orc_cholesky", "orc_laplace", "orc_evidence",
-                     "orc_chisao_ray_best", "orc_chisao", "orc_precheck"):
+                     "orc_chisao_ray_best", "orc_chisao", "orc_precheck", "orc_ray_segment"):
             getattr(_lib, name).restype = C.c_int
         for name in ("orc_uniform_corr_probe", "orc_perp_fraction"):
             getattr(_lib, name).restype = C.c_double
@@ -351,3 +351,31 @@ def perp_fraction(dtheta, grad, hdiag):
     g = np.ascontiguousarray(grad, dtype=np.float64)
     h = np.ascontiguousarray(hdiag, dtype=np.float64)
     return float(lib().orc_perp_fraction(C.c_int(len(dt)), _ptr(dt), _ptr(g), _ptr(h)))
+
+
+# ------------------------------------------------ ray families and two-pass sampling (Sec. 3.5.1-3.5.2)
+RAY_V2V, RAY_V2E, RAY_W2W = 1, 2, 3
+
+
+def ray_segment(inst, family, seed, r):
+    """(start, end) of ray r of a family."""
+    P = OracleProblem(inst)
+    a = np.empty(P.d)
+    b = np.empty(P.d)
+    rc = lib().orc_ray_segment(C.byref(P.s), C.c_int(family), C.c_uint64(seed), C.c_int(r), _ptr(a), _ptr(b))
+    if rc != 0:
+        raise ValueError(f"unknown ray family {family}")
+    return a, b
+
+
+def ray_two_pass(inst, start, end, n, delta, n_ref):
+    """(coarse l [n], refined t [n_ref], refined l [n_ref]) along the segment."""
+    P = OracleProblem(inst)
+    a = np.ascontiguousarray(start, dtype=np.float64)
+    b = np.ascontiguousarray(end, dtype=np.float64)
+    lc = np.empty(n)
+    tr = np.empty(n_ref)
+    lr = np.empty(n_ref)
+    lib().orc_ray_two_pass(C.byref(P.s), _ptr(a), _ptr(b), C.c_int(n), C.c_double(delta), C.c_int(n_ref), _ptr(lc),
+                           _ptr(tr), _ptr(lr))
+    return lc, tr, lr

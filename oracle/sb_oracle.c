@@ -1166,3 +1166,124 @@ double orc_perp_fraction(int d, const double *dtheta, const double *grad, const 
     }
     return sqrt(pp / ss);
 }
+
+/* ------------------------------------------------------------------------ */
+/* The other ray families (Sec. 3.5.1) and the two-pass sampling along a ray  */
+/* (Sec. 3.5.2). Readings where the paper is silent:                          */
+/*  - every random draw of ray r of a family comes from Philox blocks with    */
+/*    counter (q, r, family tag, purpose), key = seed; bit b of a stream is   */
+/*    bit b % 32 of word (b / 32) % 4 of block q = b / 128; uniform k of a    */
+/*    stream is orc_unit of words 2 (k % 2), 2 (k % 2) + 1 of block k / 2;    */
+/*    an index below n is (word 0 of block 0 of its stream) * n >> 32;        */
+/*  - V2V: start and end vertex from independent bit streams (purposes 0,     */
+/*    1): coordinate i is hi_i when its bit is 1, else lo_i; an end equal to  */
+/*    the start becomes the antipode;                                         */
+/*  - V2E: start vertex (purpose 0); the end is the midpoint of an edge:      */
+/*    vertex bits (purpose 1) with one free coordinate j (index, purpose 2)   */
+/*    set to the box centre;                                                  */
+/*  - W2W: axis i (index, purpose 2); start on the face x_i = lo_i, end on    */
+/*    x_i = hi_i, every other coordinate uniform in [lo, hi] (purposes 0, 1); */
+/*  - coarse pass: n samples at t_j = j / (n - 1) of the segment (t = 1/2     */
+/*    for n = 1); the active region is {j : l_j > max_j l_j - delta};        */
+/*  - refinement pass: density proportional to the likelihood, piecewise      */
+/*    constant on the coarse cells [t_j - h/2, t_j + h/2] clipped to [0, 1]   */
+/*    (h = 1/(n - 1)), weight exp(l_j - max l) times the cell length on       */
+/*    active cells and 0 elsewhere; n_ref points at the inverse CDF of the    */
+/*    midpoints u_k = (k + 1/2) / n_ref, linear inside a cell.                */
+/* ------------------------------------------------------------------------ */
+enum { ORC_TAG_V2V = 0x56325620u, ORC_TAG_V2E = 0x56324520u, ORC_TAG_W2W = 0x57325720u };
+
+static uint32_t stream_word(uint64_t seed, uint32_t r, uint32_t tag, uint32_t purpose, uint32_t q, int w) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {q, r, tag, purpose};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    return o[w];
+}
+static int stream_bit(uint64_t seed, uint32_t r, uint32_t tag, uint32_t purpose, int b) {
+    return (int)((stream_word(seed, r, tag, purpose, (uint32_t)(b / 128), (b / 32) % 4) >> (b % 32)) & 1u);
+}
+static double stream_unit(uint64_t seed, uint32_t r, uint32_t tag, uint32_t purpose, int k) {
+    const uint32_t q = (uint32_t)(k / 2);
+    const int w = 2 * (k % 2);
+    return orc_unit(stream_word(seed, r, tag, purpose, q, w), stream_word(seed, r, tag, purpose, q, w + 1));
+}
+static int stream_index(uint64_t seed, uint32_t r, uint32_t tag, uint32_t purpose, int n) {
+    return (int)(((uint64_t)stream_word(seed, r, tag, purpose, 0, 0) * (uint64_t)n) >> 32);
+}
+
+int orc_ray_segment(const orc_problem *p, int family, uint64_t seed, int r, double *start, double *end) {
+    const int d = p->d;
+    if (family == ORC_RAY_V2V || family == ORC_RAY_V2E) {
+        const uint32_t tag = family == ORC_RAY_V2V ? ORC_TAG_V2V : ORC_TAG_V2E;
+        int same = 1;
+        for (int i = 0; i < d; ++i) {
+            const int bs = stream_bit(seed, (uint32_t)r, tag, 0, i);
+            const int be = stream_bit(seed, (uint32_t)r, tag, 1, i);
+            start[i] = bs ? p->hi[i] : p->lo[i];
+            end[i] = be ? p->hi[i] : p->lo[i];
+            same &= (bs == be);
+        }
+        if (family == ORC_RAY_V2V) {
+            if (same)
+                for (int i = 0; i < d; ++i) end[i] = start[i] == p->hi[i] ? p->lo[i] : p->hi[i];
+        } else {
+            const int j = stream_index(seed, (uint32_t)r, tag, 2, d);
+            end[j] = 0.5 * (p->lo[j] + p->hi[j]);
+        }
+        return 0;
+    }
+    if (family == ORC_RAY_W2W) {
+        const int ax = stream_index(seed, (uint32_t)r, ORC_TAG_W2W, 2, d);
+        for (int i = 0; i < d; ++i) {
+            const double w = p->hi[i] - p->lo[i];
+            start[i] = p->lo[i] + stream_unit(seed, (uint32_t)r, ORC_TAG_W2W, 0, i) * w;
+            end[i] = p->lo[i] + stream_unit(seed, (uint32_t)r, ORC_TAG_W2W, 1, i) * w;
+        }
+        start[ax] = p->lo[ax];
+        end[ax] = p->hi[ax];
+        return 0;
+    }
+    return -1;
+}
+
+void orc_ray_two_pass(const orc_problem *p, const double *start, const double *end, int n, double delta, int n_ref,
+                      double *ell_coarse, double *t_ref, double *ell_ref) {
+    const int d = p->d;
+    double *x = (double *)malloc(sizeof(double) * (size_t)d);
+    double *cdf = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    double lmax = -INFINITY;
+    for (int j = 0; j < n; ++j) {
+        const double t = n > 1 ? (double)j / (double)(n - 1) : 0.5;
+        for (int i = 0; i < d; ++i) x[i] = start[i] + t * (end[i] - start[i]);
+        ell_coarse[j] = orc_loglik(p, x, NULL, NULL);
+        if (ell_coarse[j] > lmax) lmax = ell_coarse[j];
+    }
+    const double h = n > 1 ? 1.0 / (double)(n - 1) : 1.0;
+    cdf[0] = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const double tc = n > 1 ? (double)j / (double)(n - 1) : 0.5;
+        double a = tc - 0.5 * h, b = tc + 0.5 * h;
+        if (a < 0.0) a = 0.0;
+        if (b > 1.0) b = 1.0;
+        const double w = (ell_coarse[j] > lmax - delta) ? exp(ell_coarse[j] - lmax) * (b - a) : 0.0;
+        cdf[j + 1] = cdf[j] + w;
+    }
+    for (int k = 0; k < n_ref; ++k) {
+        const double u = ((double)k + 0.5) / (double)n_ref * cdf[n];
+        int j = 0;
+        while (j < n - 1 && cdf[j + 1] <= u) ++j; /* cdf[j] <= u < cdf[j + 1]: never an empty cell */
+        const double tc = n > 1 ? (double)j / (double)(n - 1) : 0.5;
+        double a = tc - 0.5 * h, b = tc + 0.5 * h;
+        if (a < 0.0) a = 0.0;
+        if (b > 1.0) b = 1.0;
+        const double cw = cdf[j + 1] - cdf[j];
+        const double fr = cw > 0.0 ? (u - cdf[j]) / cw : 0.5;
+        const double t = a + fr * (b - a);
+        t_ref[k] = t;
+        for (int i = 0; i < d; ++i) x[i] = start[i] + t * (end[i] - start[i]);
+        ell_ref[k] = orc_loglik(p, x, NULL, NULL);
+    }
+    free(cdf);
+    free(x);
+}

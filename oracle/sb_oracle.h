@@ -109,6 +109,14 @@ double orc_uniform_corr_probe(const orc_problem *p, const double *x, double eps,
 /* Perpendicular step fraction of one step in coordinates whitened by sqrt(-H_ii) (Sec. 3.7.2). */
 double orc_perp_fraction(int d, const double *dtheta, const double *grad, const double *hdiag);
 
+/* Ray families (Sec. 3.5.1): segment of ray r from start to end; 0, or -1 for an unknown family. */
+enum { ORC_RAY_V2V = 1, ORC_RAY_V2E = 2, ORC_RAY_W2W = 3 };
+int orc_ray_segment(const orc_problem *p, int family, uint64_t seed, int r, double *start, double *end);
+/* Two-pass sampling along a segment (Sec. 3.5.2): n coarse values, then n_ref points drawn with density
+ * proportional to the likelihood on the active region l > max l - delta: parameters t_ref, values ell_ref. */
+void orc_ray_two_pass(const orc_problem *p, const double *start, const double *end, int n, double delta, int n_ref,
+                      double *ell_coarse, double *t_ref, double *ell_ref);
+
 #ifdef __cplusplus
 }
 #endif
