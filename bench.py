@@ -5,7 +5,7 @@ discover + refine + laplace) on the seeded synthetic d=1024, K=8 mixture.
                     [--workload 4] [--prec bf16|tf32|fp64]
 
 Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on
-the host cores (the reference arm of this build) on a bounded sample of the
+the host cores (the benchmark's reference arm) on a bounded sample of the
 same workload. Under torchrun each rank solves its own replica (no data-path
 collective); value = evaluations of all ranks / max-over-ranks time.
 """
@@ -41,7 +41,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sb", choices=["sb", "reference"])
-    ap.add_argument("--workload", type=int, default=4)
+    ap.add_argument("--workload", type=int, default=4,
+                    help="0: d=8 Gaussian; 1: d=64 K=4 mixture; 2: d=256 correlated Gaussian; "
+                         "3: 512 batched mixtures; 4: d=1024 K=8 mixture")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the forward solve and the d log Z / d (mu, L) adjoint (one JSON line)")
     ap.add_argument("--prec", default="bf16", choices=list(PREC))
@@ -376,7 +378,7 @@ def run_adjoint(sb, args):
 
 
 def run_precision(sb, args):
-    """Workload 2: |dlogZ| per likelihood dtype, with and without the FP64 Newton polish,
+    """Precision table: |dlogZ| per likelihood dtype, with and without the FP64 Newton polish,
     on the d=256 correlated Gaussian (s log-uniform in [0.01, 1], condition number up to 1e4;
     log Z = -log V exactly). Also the evidence solves/sec of each form."""
     import torch
@@ -408,7 +410,7 @@ def run_precision(sb, args):
 
 
 def run_batched(sb, args):
-    """Workload 3: 512 independent problems (d in {16..512}, K in 1..8) per step, one library call."""
+    """Batched mixtures: 512 independent problems (d in {16..512}, K in 1..8) per step, one library call."""
     import torch
     from paper_2601_19957_gb300.instances import workload
 

@@ -42,7 +42,7 @@ typedef enum sb_status {
     SB_ERR_NONFINITE = 4,   /* NaN/Inf in parameters or in a required result   */
     SB_ERR_NO_MODES = 5,    /* no candidate survived the Laplace filters       */
     SB_ERR_TIMEOUT = 6,     /* a bounded device loop ran out of iterations     */
-    SB_ERR_UNSUPPORTED = 7  /* size outside what this build handles (d > 1024) */
+    SB_ERR_UNSUPPORTED = 7  /* size or precision the library does not handle (d > 1024, ...) */
 } sb_status;
 
 /* Arithmetic of the log-likelihood / gradient contractions (discover, refine).
