@@ -46,6 +46,8 @@ def parse():
                          "3: 512 batched mixtures; 4: d=1024 K=8 mixture")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the forward solve and the d log Z / d (mu, L) adjoint (one JSON line)")
+    ap.add_argument("--chisao", action="store_true",
+                    help="time discovery + the ChiSao oscillation (FP64) on the d=64 K=4 mixture (one JSON line)")
     ap.add_argument("--prec", default="bf16", choices=list(PREC))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -197,6 +199,8 @@ def main():
         return run_precision(sb, args)
     if args.adjoint:
         return run_adjoint(sb, args)
+    if args.chisao:
+        return run_chisao(sb, args)
     inst, cfg = workload_cfg(args.workload, args.prec, args.scale)
     prob = sb.Problem(inst)
     c = sb.make_config(cfg)
@@ -374,6 +378,55 @@ def run_adjoint(sb, args):
                       "n_modes": nm, "ms_forward": dt_f * 1e3, "ms_backward": dt_b * 1e3,
                       "backward_fp64_flop_model": 2.0 * nm * d ** 3,
                       "max_abs_dmu": float(dmu.abs().max()), "max_abs_dL": float(dL.abs().max())}))
+    return 0
+
+
+def run_chisao(sb, args):
+    """Discovery followed by the ChiSao oscillation (FP64, 3 oscillations, one sample per
+    discovered start) on the d=64, K=4 mixture; one step = sb_discover + sb_chisao. Reports
+    the time per step, the device time per kernel class, and the components found as peaks
+    against those whose peak passes the stick test and against the plain evidence solve."""
+    import torch
+
+    inst, cfg = workload_cfg(1, "fp64", args.scale)
+    prob = sb.Problem(inst)
+    c = sb.make_config(cfg)
+    cc = sb.make_chisao_config()
+    wsc = sb.chisao_workspace(prob, c)
+    L = sb.lib()
+
+    def step():
+        starts, _ = sb.discover(prob, c, ws=wsc)
+        return sb.chisao(prob, c, cc, starts, ws=wsc)
+
+    for _ in range(max(args.warmup, 1)):
+        out = step()
+    torch.cuda.synchronize()
+    L.sb_profile_enable(1)
+    launches0 = L.sb_launch_count()
+    t0 = time.perf_counter()
+    reps = max(args.steps, 1)
+    for _ in range(reps):
+        out = step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    launches = (L.sb_launch_count() - launches0) // reps
+    L.sb_profile_enable(0)
+    prof_ms = (sb.C.c_double * 8)()
+    prof_n = (sb.C.c_int64 * 8)()
+    L.sb_profile_read(prof_ms, prof_n)
+    peaks = out.x[out.stuck].cpu().numpy()
+    found = sorted({int(np.argmin(np.abs(inst.mu - m).max(1))) for m in peaks})
+    heights = sb.loglik(prob, torch.as_tensor(inst.mu, device="cuda"), want_grad=False).cpu().numpy()
+    expect = [int(k) for k in np.flatnonzero(heights >= heights.max() + math.log(0.1))]
+    plain = sb.evidence(prob, c, ws=wsc)
+    plain_found = sorted({int(np.argmin(np.abs(inst.mu - m).max(1))) for m in plain.modes.cpu().numpy()})
+    names = ["tc_z_walkers", "tc_z_rays", "tc_grad", "lbfgs_step_f32", "f64_z", "f64_grad", "cholesky", "other"]
+    print(json.dumps({"case": "chisao", "workload": workload_name(1, inst, cfg) + ", FP64, 3 oscillations",
+                      "ms_per_step": dt * 1e3, "steps": reps, "launches_per_step": int(launches),
+                      "n_peaks": out.n_peaks, "components_found": found, "components_passing_stick_test": expect,
+                      "components_found_without_chisao": plain_found,
+                      "device_ms_per_step": {nm: prof_ms[i] / reps for i, nm in enumerate(names) if prof_n[i]}}))
     return 0
 
 
