@@ -305,6 +305,27 @@ sb_status sb_chisao(const sb_problem *prob, const sb_config *cfg, const sb_chisa
                     int32_t n, double *x_out, double *ell_out, int8_t *stuck_out, int32_t *n_peaks, void *ws,
                     size_t ws_bytes, void *stream);
 
+/* Bytes of device scratch sb_precheck needs. */
+size_t sb_precheck_workspace_bytes(const sb_problem *prob);
+
+/*
+ * Preprocessing probe (Sec. 3.4): s_i = |l(c + Delta_i e_i) - l(c)| + |l(c - Delta_i e_i) - l(c)|
+ * with c the box centre and Delta_i = (hi_i - lo_i) / 2; a coordinate is flat when
+ * s_i < eps_flat median(s), soft when not flat and s_i < eps_soft max(s), else active
+ * (median and max over the finite s_i; the median of an even count is the mean of the
+ * two middle values; a non-finite s_i is active). The marginal log-integral of the
+ * flagged coordinates is sum over flat log(2 Delta_i) + sum over soft
+ * [1/2 log 2 pi + log(Delta_i / sqrt(s_i))], and their log-volume sum log(2 Delta_i): the
+ * evidence of the full problem is that of the problem over the active coordinates (the
+ * flagged ones held at c) plus log_int minus log_vol. The l differences are formed from
+ * z_k(c) and the rows of L_k, without subtracting two l values.
+ * s: [d]; cls: int8 [d] (0 active, 1 flat, 2 soft); log_int, log_vol: device scalars;
+ * n_active: int32 device scalar. eps_flat, eps_soft >= 0 (defaults 1e-6, 1e-3). d <= 1024.
+ * ws: sb_precheck_workspace_bytes. Asynchronous.
+ */
+sb_status sb_precheck(const sb_problem *prob, double eps_flat, double eps_soft, double *s, int8_t *cls,
+                      double *log_int, double *log_vol, int32_t *n_active, void *ws, size_t ws_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

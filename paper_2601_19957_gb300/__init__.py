@@ -69,6 +69,10 @@ def lib():
         L.sb_evidence_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         L.sb_chisao_workspace_bytes.restype = C.c_size_t
+        L.sb_precheck_workspace_bytes.restype = C.c_size_t
+        L.sb_precheck.restype = C.c_int
+        L.sb_precheck.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         for name in ("sb_loglik", "sb_loglik_noalloc", "sb_discover", "sb_refine", "sb_laplace", "sb_evidence", "sb_evidence_host",
                      "sb_check", "sb_chisao"):
             getattr(L, name).restype = C.c_int
@@ -269,6 +273,30 @@ def chisao(prob: Problem, cfg: _Config, cc: _ChisaoConfig, x0, ws: Workspace = N
     _check(lib().sb_chisao(C.byref(prob.s), C.byref(cfg), C.byref(cc), _ptr(x0), C.c_int32(n), _ptr(x), _ptr(ell),
                            _ptr(stuck), _ptr(npk), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)), "sb_chisao")
     return ChisaoOut(x, ell, stuck.bool(), int(npk.item()))
+
+
+@dataclass
+class PrecheckOut:
+    s: object
+    cls: object
+    log_int: float
+    log_vol: float
+    n_active: int
+
+
+def precheck(prob: Problem, eps_flat: float = 1e-6, eps_soft: float = 1e-3, stream=None) -> PrecheckOut:
+    """Sensitivity probe and flat / soft-nuisance classes (0 active, 1 flat, 2 soft)."""
+    torch = _torch()
+    ws = Workspace(int(lib().sb_precheck_workspace_bytes(C.byref(prob.s))))
+    s = torch.empty(prob.d, dtype=torch.float64, device="cuda")
+    cls = torch.empty(prob.d, dtype=torch.int8, device="cuda")
+    sc = torch.zeros(2, dtype=torch.float64, device="cuda")
+    na = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _check(lib().sb_precheck(C.byref(prob.s), float(eps_flat), float(eps_soft), _ptr(s), _ptr(cls),
+                             C.c_void_p(sc.data_ptr()), C.c_void_p(sc.data_ptr() + 8), _ptr(na), ws.ptr,
+                             ws.nbytes, _stream(stream)), "sb_precheck")
+    v = sc.cpu().numpy()
+    return PrecheckOut(s, cls, float(v[0]), float(v[1]), int(na.item()))
 
 
 @dataclass

@@ -12,6 +12,7 @@
 
 #include "sb_adjoint.cuh"
 #include "sb_chisao.cuh"
+#include "sb_precheck.cuh"
 #include "sb_internal.cuh"
 #include "sb_laplace.cuh"
 #include "sb_lbfgs.cuh"
@@ -1214,6 +1215,68 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
     SB_CUDA_TRY(cudaMemcpyAsync(ell_out, w.ell, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     SB_CUDA_TRY(cudaMemcpyAsync(stuck_out, w.stuck, n, cudaMemcpyDeviceToDevice, s));
     SB_CUDA_TRY(cudaMemcpyAsync(n_peaks, w.n_reps, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    SB_CUDA_TRY(cudaGetLastError());
+    return SB_OK;
+}
+
+// ------------------------------------------------------------------ preprocessing (Sec. 3.4)
+namespace {
+
+struct PrecheckWs {
+    SetupWs su;
+    double *scratch;
+    size_t bytes;
+};
+
+PrecheckWs precheck_layout(void *base, const sb_problem *p) {
+    PrecheckWs w{};
+    Carver cv(base);
+    w.su.hdr = cv.take<WsHeader>(1);
+    w.su.a = cv.take<double>(p->K);
+    w.su.c = cv.take<double>(p->d);
+    w.su.half = cv.take<double>(p->d);
+    w.su.logV = cv.take<double>(1);
+    w.su.wmax = cv.take<double>(1);
+    w.scratch = cv.take<double>(precheck_scratch_elems(p->d, p->K));
+    w.bytes = cv.bytes();
+    return w;
+}
+
+}  // namespace
+
+extern "C" size_t sb_precheck_workspace_bytes(const sb_problem *p) {
+    if (check_problem(p) != SB_OK) return 0;
+    return precheck_layout(nullptr, p).bytes;
+}
+
+extern "C" sb_status sb_precheck(const sb_problem *p, double eps_flat, double eps_soft, double *s, int8_t *cls,
+                                 double *log_int, double *log_vol, int32_t *n_active, void *ws, size_t ws_bytes,
+                                 void *stream) {
+    sb_status st = check_problem(p);
+    if (st != SB_OK) return st;
+    if (!s || !cls || !log_int || !log_vol || !n_active || !ws) return SB_ERR_INVALID_ARG;
+    if (!(eps_flat >= 0.0) || !(eps_soft >= 0.0) || !std::isfinite(eps_flat) || !std::isfinite(eps_soft))
+        return SB_ERR_INVALID_ARG;
+    const PrecheckWs w = precheck_layout(ws, p);
+    if (ws_bytes < w.bytes) return SB_ERR_WORKSPACE;
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    ProbView pv;
+    pv.d = p->d;
+    pv.K = p->K;
+    pv.log_w = p->log_w;
+    pv.mu = p->mu;
+    pv.L = p->L;
+    pv.lo = p->lo;
+    pv.hi = p->hi;
+    pv.a = w.su.a;
+    pv.c = w.su.c;
+    pv.half = w.su.half;
+    pv.logV = w.su.logV;
+    pv.wmax = w.su.wmax;
+    pv.status = &w.su.hdr->status;
+    SB_CUDA_TRY(cudaMemsetAsync(w.su.hdr, 0, sizeof(WsHeader), cs));
+    launch_setup(pv, cs);
+    launch_precheck(pv, eps_flat, eps_soft, w.scratch, s, cls, log_int, log_vol, n_active, cs);
     SB_CUDA_TRY(cudaGetLastError());
     return SB_OK;
 }

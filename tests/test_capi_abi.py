@@ -77,3 +77,16 @@ def test_chisao_rejects_bad_config_and_mixed_precision_on_the_host():
     assert L.sb_chisao(*args(cfg, C.byref(cc))) == sb.SB_ERR_WORKSPACE
     base = L.sb_workspace_bytes(C.byref(p), C.byref(cfg))
     assert L.sb_chisao_workspace_bytes(C.byref(p), C.byref(cfg)) > base > 0
+
+
+def test_precheck_rejects_bad_arguments_on_the_host():
+    p = _fake_problem(8, 1)
+    L = sb.lib()
+    buf = (C.c_char * 16)()
+    ok = lambda ef, es, nbytes: L.sb_precheck(C.byref(p), ef, es, buf, buf, buf, buf, buf, buf, nbytes, None)
+    assert ok(-1.0, 1e-3, 16) == sb.SB_ERR_INVALID_ARG
+    assert ok(1e-6, float("nan"), 16) == sb.SB_ERR_INVALID_ARG
+    assert ok(1e-6, 1e-3, 16) == sb.SB_ERR_WORKSPACE
+    assert L.sb_precheck(C.byref(p), 1e-6, 1e-3, None, buf, buf, buf, buf, buf, 16, None) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_precheck_workspace_bytes(C.byref(p)) > 0
+    assert L.sb_precheck_workspace_bytes(C.byref(_fake_problem(2000, 1))) == 0
