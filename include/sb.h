@@ -305,6 +305,35 @@ sb_status sb_chisao(const sb_problem *prob, const sb_config *cfg, const sb_chisa
                     int32_t n, double *x_out, double *ell_out, int8_t *stuck_out, int32_t *n_peaks, void *ws,
                     size_t ws_bytes, void *stream);
 
+/* Ray families besides the sunburst (Sec. 3.5.1). */
+enum { SB_RAY_V2V = 1, SB_RAY_V2E = 2, SB_RAY_W2W = 3 };
+
+/* Bytes of device scratch sb_segments needs for n_rays rays of n_steps coarse samples. */
+size_t sb_segments_workspace_bytes(const sb_problem *prob, int32_t n_rays, int32_t n_steps);
+
+/*
+ * V2V / V2E / W2W rays and their two-pass sampling (Sec. 3.5.1-3.5.2), FP64.
+ * Ray r of `family` is the segment from a to b: V2V joins two vertices from independent
+ * bit streams (an end equal to the start becomes its antipode); V2E runs from a vertex to
+ * the midpoint of an edge (vertex bits, one free coordinate at the box centre); W2W runs
+ * from a uniform point on the face x_i = lo_i to one on x_i = hi_i of a random axis i. All
+ * draws of ray r come from Philox4x32-10 blocks with counter (block, r, family tag
+ * 'V2V ' / 'V2E ' / 'W2W ', purpose), key = seed: bit b of a stream is bit b % 32 of word
+ * (b / 32) % 4 of block b / 128, uniform k uses words 2 (k % 2), 2 (k % 2) + 1 of block
+ * k / 2 (top 52 bits), an index below n is (word 0 of block 0) n >> 32; purposes 0 and 1
+ * are the start and end streams, 2 the index.
+ * Coarse pass: l at t_j = j / (n_steps - 1) (t = 1/2 for one step). Refinement: n_ref
+ * points drawn with density proportional to the likelihood, piecewise constant on the
+ * coarse cells (clipped to [0, 1]) and zero outside the active region l > max l - delta,
+ * at the inverse CDF of (k + 1/2) / n_ref; their parameters and l.
+ * ends: [2][n_rays][d] (starts, then ends); ell_coarse: [n_rays][n_steps];
+ * t_ref, ell_ref: [n_rays][n_ref] (may be NULL when n_ref = 0). delta >= 0 (+inf: all
+ * active). ws: sb_segments_workspace_bytes. Asynchronous.
+ */
+sb_status sb_segments(const sb_problem *prob, int32_t family, uint64_t seed, int32_t n_rays, int32_t n_steps,
+                      double delta, int32_t n_ref, double *ends, double *ell_coarse, double *t_ref, double *ell_ref,
+                      void *ws, size_t ws_bytes, void *stream);
+
 /* Bytes of device scratch sb_precheck needs. */
 size_t sb_precheck_workspace_bytes(const sb_problem *prob);
 

@@ -70,6 +70,11 @@ def lib():
                                            C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         L.sb_chisao_workspace_bytes.restype = C.c_size_t
         L.sb_precheck_workspace_bytes.restype = C.c_size_t
+        L.sb_segments_workspace_bytes.restype = C.c_size_t
+        L.sb_segments.restype = C.c_int
+        L.sb_segments.argtypes = [C.c_void_p, C.c_int32, C.c_uint64, C.c_int32, C.c_int32, C.c_double, C.c_int32,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                  C.c_void_p]
         L.sb_precheck.restype = C.c_int
         L.sb_precheck.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
@@ -273,6 +278,33 @@ def chisao(prob: Problem, cfg: _Config, cc: _ChisaoConfig, x0, ws: Workspace = N
     _check(lib().sb_chisao(C.byref(prob.s), C.byref(cfg), C.byref(cc), _ptr(x0), C.c_int32(n), _ptr(x), _ptr(ell),
                            _ptr(stuck), _ptr(npk), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)), "sb_chisao")
     return ChisaoOut(x, ell, stuck.bool(), int(npk.item()))
+
+
+RAY_V2V, RAY_V2E, RAY_W2W = 1, 2, 3
+
+
+@dataclass
+class SegmentsOut:
+    start: object
+    end: object
+    ell_coarse: object
+    t_ref: object
+    ell_ref: object
+
+
+def segments(prob: Problem, family: int, seed: int, n_rays: int, n_steps: int, delta: float = float("inf"),
+             n_ref: int = 0, stream=None) -> SegmentsOut:
+    """V2V / V2E / W2W rays with their coarse and likelihood-proportional refined samples (FP64)."""
+    torch = _torch()
+    ws = Workspace(int(lib().sb_segments_workspace_bytes(C.byref(prob.s), int(n_rays), int(n_steps))))
+    ends = torch.empty((2, n_rays, prob.d), dtype=torch.float64, device="cuda")
+    lc = torch.empty((n_rays, n_steps), dtype=torch.float64, device="cuda")
+    tr = torch.empty((n_rays, max(n_ref, 0)), dtype=torch.float64, device="cuda")
+    lr = torch.empty((n_rays, max(n_ref, 0)), dtype=torch.float64, device="cuda")
+    _check(lib().sb_segments(C.byref(prob.s), int(family), int(seed) & ((1 << 64) - 1), int(n_rays), int(n_steps),
+                             float(delta), int(n_ref), _ptr(ends), _ptr(lc), _ptr(tr) if n_ref > 0 else None,
+                             _ptr(lr) if n_ref > 0 else None, ws.ptr, ws.nbytes, _stream(stream)), "sb_segments")
+    return SegmentsOut(ends[0], ends[1], lc, tr, lr)
 
 
 @dataclass

@@ -386,6 +386,14 @@ __global__ void __launch_bounds__(256) k_few_g(LikF64Args a) {
 
 size_t lik_f64_qpart_elems(int d, int K, int rows) { return (size_t)rows * K * ((d + BN - 1) / BN); }
 
+void launch_lik_f64_z(const LikF64Args &a, cudaStream_t s) {
+    if (a.n_rows <= 0) return;
+    dim3 g((a.n_rows + BM - 1) / BM, (a.d + BN - 1) / BN, a.K);
+    ProfScope prof(PROF_F64_Z, s);
+    note_launch();
+    k_zgemm_f64<SRC_GATHER, true><<<g, 256, 0, s>>>(a);
+}
+
 void launch_lik_f64_rays(const LikF64Args &a, cudaStream_t s) {
     if (a.n_rows <= 0) return;
     dim3 g((a.n_rows + BM - 1) / BM, (a.d + BN - 1) / BN, a.K);

@@ -13,6 +13,7 @@
 #include "sb_adjoint.cuh"
 #include "sb_chisao.cuh"
 #include "sb_precheck.cuh"
+#include "sb_segments.cuh"
 #include "sb_internal.cuh"
 #include "sb_laplace.cuh"
 #include "sb_lbfgs.cuh"
@@ -1277,6 +1278,74 @@ extern "C" sb_status sb_precheck(const sb_problem *p, double eps_flat, double ep
     SB_CUDA_TRY(cudaMemsetAsync(w.su.hdr, 0, sizeof(WsHeader), cs));
     launch_setup(pv, cs);
     launch_precheck(pv, eps_flat, eps_soft, w.scratch, s, cls, log_int, log_vol, n_active, cs);
+    SB_CUDA_TRY(cudaGetLastError());
+    return SB_OK;
+}
+
+// ------------------------------------------------------------------ other ray families (Sec. 3.5.1-3.5.2)
+namespace {
+
+struct SegmentsWs {
+    SetupWs su;
+    double *scratch;
+    size_t bytes;
+};
+
+SegmentsWs segments_layout(void *base, const sb_problem *p, int n_rays, int n_steps) {
+    SegmentsWs w{};
+    Carver cv(base);
+    w.su.hdr = cv.take<WsHeader>(1);
+    w.su.a = cv.take<double>(p->K);
+    w.su.c = cv.take<double>(p->d);
+    w.su.half = cv.take<double>(p->d);
+    w.su.logV = cv.take<double>(1);
+    w.su.wmax = cv.take<double>(1);
+    w.scratch = cv.take<double>(segments_scratch_elems(n_rays, n_steps, p->d, p->K));
+    w.bytes = cv.bytes();
+    return w;
+}
+
+bool segments_sizes_ok(int n_rays, int n_steps) {
+    return n_rays >= 1 && n_steps >= 1 && n_rays <= (1 << 24) && (int64_t)n_rays * (n_steps + 1) <= 0x7fffffffLL;
+}
+
+}  // namespace
+
+extern "C" size_t sb_segments_workspace_bytes(const sb_problem *p, int32_t n_rays, int32_t n_steps) {
+    if (check_problem(p) != SB_OK || !segments_sizes_ok(n_rays, n_steps)) return 0;
+    return segments_layout(nullptr, p, n_rays, n_steps).bytes;
+}
+
+extern "C" sb_status sb_segments(const sb_problem *p, int32_t family, uint64_t seed, int32_t n_rays, int32_t n_steps,
+                                 double delta, int32_t n_ref, double *ends, double *ell_coarse, double *t_ref,
+                                 double *ell_ref, void *ws, size_t ws_bytes, void *stream) {
+    sb_status st = check_problem(p);
+    if (st != SB_OK) return st;
+    if (family != SB_RAY_V2V && family != SB_RAY_V2E && family != SB_RAY_W2W) return SB_ERR_INVALID_ARG;
+    if (!segments_sizes_ok(n_rays, n_steps) || n_ref < 0 || (int64_t)n_rays * n_ref > 0x7fffffffLL)
+        return SB_ERR_INVALID_ARG;
+    if (!(delta >= 0.0)) return SB_ERR_INVALID_ARG;  // +inf allowed, NaN refused
+    if (!ends || !ell_coarse || !ws || (n_ref > 0 && (!t_ref || !ell_ref))) return SB_ERR_INVALID_ARG;
+    const SegmentsWs w = segments_layout(ws, p, n_rays, n_steps);
+    if (ws_bytes < w.bytes) return SB_ERR_WORKSPACE;
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    ProbView pv;
+    pv.d = p->d;
+    pv.K = p->K;
+    pv.log_w = p->log_w;
+    pv.mu = p->mu;
+    pv.L = p->L;
+    pv.lo = p->lo;
+    pv.hi = p->hi;
+    pv.a = w.su.a;
+    pv.c = w.su.c;
+    pv.half = w.su.half;
+    pv.logV = w.su.logV;
+    pv.wmax = w.su.wmax;
+    pv.status = &w.su.hdr->status;
+    SB_CUDA_TRY(cudaMemsetAsync(w.su.hdr, 0, sizeof(WsHeader), cs));
+    launch_setup(pv, cs);
+    launch_segments(pv, family, seed, n_rays, n_steps, delta, n_ref, w.scratch, ends, ell_coarse, t_ref, ell_ref, cs);
     SB_CUDA_TRY(cudaGetLastError());
     return SB_OK;
 }

@@ -197,6 +197,8 @@ struct LikF64Args {
 void launch_lik_f64_rays(const LikF64Args &a, cudaStream_t s);                 // values at ray samples
 void launch_lik_f64_points(const LikF64Args &a, bool want_grad, cudaStream_t s);// values (+grads) at points
 size_t lik_f64_qpart_elems(int d, int K, int rows);
+// z_nk = L_k^T (x_n - mu_k) stored in Z (and the |z|^2 partials in qpart) for gathered rows, no l.
+void launch_lik_f64_z(const LikF64Args &a, cudaStream_t s);
 // Same outputs for a handful of points (GEMV-shaped work split; n_rows is the capacity).
 void launch_lik_f64_few(const LikF64Args &a, bool want_grad, cudaStream_t s);
 

@@ -90,3 +90,19 @@ def test_precheck_rejects_bad_arguments_on_the_host():
     assert L.sb_precheck(C.byref(p), 1e-6, 1e-3, None, buf, buf, buf, buf, buf, 16, None) == sb.SB_ERR_INVALID_ARG
     assert L.sb_precheck_workspace_bytes(C.byref(p)) > 0
     assert L.sb_precheck_workspace_bytes(C.byref(_fake_problem(2000, 1))) == 0
+
+
+def test_segments_reject_bad_arguments_on_the_host():
+    p = _fake_problem(8, 1)
+    L = sb.lib()
+    buf = (C.c_char * 16)()
+    call = lambda fam, nr, ns, delta, nref, tr, nbytes: L.sb_segments(C.byref(p), fam, 1, nr, ns, delta, nref, buf,
+                                                                      buf, tr, tr, buf, nbytes, None)
+    assert call(4, 8, 16, 1.0, 4, buf, 16) == sb.SB_ERR_INVALID_ARG  # unknown family
+    assert call(sb.RAY_V2V, 0, 16, 1.0, 4, buf, 16) == sb.SB_ERR_INVALID_ARG
+    assert call(sb.RAY_V2V, 8, 16, float("nan"), 4, buf, 16) == sb.SB_ERR_INVALID_ARG
+    assert call(sb.RAY_V2V, 8, 16, 1.0, 4, None, 16) == sb.SB_ERR_INVALID_ARG  # refined outputs missing
+    assert call(sb.RAY_W2W, 8, 16, float("inf"), 0, None, 16) == sb.SB_ERR_WORKSPACE
+    small = L.sb_segments_workspace_bytes(C.byref(p), 8, 16)
+    assert 0 < small < L.sb_segments_workspace_bytes(C.byref(p), 64, 16)
+    assert L.sb_segments_workspace_bytes(C.byref(p), 0, 16) == 0
