@@ -305,6 +305,28 @@ sb_status sb_chisao(const sb_problem *prob, const sb_config *cfg, const sb_chisa
                     int32_t n, double *x_out, double *ell_out, int8_t *stuck_out, int32_t *n_peaks, void *ws,
                     size_t ws_bytes, void *stream);
 
+/* Bytes of device scratch sb_fd_derivatives needs (full != 0: with the full Hessian). */
+size_t sb_fd_workspace_bytes(const sb_problem *prob, int32_t full);
+
+/*
+ * Black-box derivatives of l at one point by central differences (App. A.4), FP64, and the
+ * uniform-correlation probe (Sec. 3.7.2). l is only evaluated, at the perturbed points
+ *   x +- eps_g e_i (gradient), x and x +- eps_h e_i (Hessian diagonal), x +- eps_h v with
+ *   v = (1, ..., 1)/sqrt(d) (probe), and, when full, x +- eps_h e_i +- eps_h e_j for i < j,
+ * 4d + 3 points plus 2 d (d - 1) for the full Hessian, in batches of the likelihood:
+ *   grad_i = (l(x + eps_g e_i) - l(x - eps_g e_i)) / (2 eps_g)
+ *   H_ii = (l(x + eps_h e_i) - 2 l(x) + l(x - eps_h e_i)) / eps_h^2
+ *   H_ij = H_ji = (l_++ - l_+- - l_-+ + l_--) / (4 eps_h^2)
+ *   b = (v^T H v - mean_i H_ii) / (d - 1) (0 for d = 1), v^T H v the second difference along v.
+ * The Hessians are of l itself (negative definite at a maximum).
+ * x: [d] device; grad: [d] or NULL; hdiag: [d]; H: [d][d] (required when full); b: device
+ * scalar or NULL. eps_g, eps_h > 0 (1e-5 and 1e-4 suit FP64). ws: sb_fd_workspace_bytes.
+ * Asynchronous.
+ */
+sb_status sb_fd_derivatives(const sb_problem *prob, const double *x, double eps_g, double eps_h, int32_t full,
+                            double *grad, double *hdiag, double *H, double *b, void *ws, size_t ws_bytes,
+                            void *stream);
+
 /* Ray families besides the sunburst (Sec. 3.5.1). */
 enum { SB_RAY_V2V = 1, SB_RAY_V2E = 2, SB_RAY_W2W = 3 };
 

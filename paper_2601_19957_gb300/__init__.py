@@ -71,6 +71,10 @@ def lib():
         L.sb_chisao_workspace_bytes.restype = C.c_size_t
         L.sb_precheck_workspace_bytes.restype = C.c_size_t
         L.sb_segments_workspace_bytes.restype = C.c_size_t
+        L.sb_fd_workspace_bytes.restype = C.c_size_t
+        L.sb_fd_derivatives.restype = C.c_int
+        L.sb_fd_derivatives.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         L.sb_segments.restype = C.c_int
         L.sb_segments.argtypes = [C.c_void_p, C.c_int32, C.c_uint64, C.c_int32, C.c_int32, C.c_double, C.c_int32,
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
@@ -278,6 +282,30 @@ def chisao(prob: Problem, cfg: _Config, cc: _ChisaoConfig, x0, ws: Workspace = N
     _check(lib().sb_chisao(C.byref(prob.s), C.byref(cfg), C.byref(cc), _ptr(x0), C.c_int32(n), _ptr(x), _ptr(ell),
                            _ptr(stuck), _ptr(npk), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)), "sb_chisao")
     return ChisaoOut(x, ell, stuck.bool(), int(npk.item()))
+
+
+@dataclass
+class FdOut:
+    grad: object
+    hdiag: object
+    H: object
+    b: float
+
+
+def fd_derivatives(prob: Problem, x, eps_g: float = 1e-5, eps_h: float = 1e-4, full: bool = False,
+                   stream=None) -> FdOut:
+    """Central-difference gradient, Hessian diagonal (and full Hessian) of l at x, and the probe b."""
+    torch = _torch()
+    x = x.to(dtype=torch.float64, device="cuda").contiguous()
+    ws = Workspace(int(lib().sb_fd_workspace_bytes(C.byref(prob.s), int(bool(full)))))
+    g = torch.empty(prob.d, dtype=torch.float64, device="cuda")
+    hd = torch.empty(prob.d, dtype=torch.float64, device="cuda")
+    H = torch.empty((prob.d, prob.d), dtype=torch.float64, device="cuda") if full else None
+    b = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _check(lib().sb_fd_derivatives(C.byref(prob.s), _ptr(x), float(eps_g), float(eps_h), int(bool(full)), _ptr(g),
+                                   _ptr(hd), _ptr(H), _ptr(b), ws.ptr, ws.nbytes, _stream(stream)),
+           "sb_fd_derivatives")
+    return FdOut(g, hd, H, float(b.item()))
 
 
 RAY_V2V, RAY_V2E, RAY_W2W = 1, 2, 3

@@ -14,6 +14,7 @@
 #include "sb_chisao.cuh"
 #include "sb_precheck.cuh"
 #include "sb_segments.cuh"
+#include "sb_fd.cuh"
 #include "sb_internal.cuh"
 #include "sb_laplace.cuh"
 #include "sb_lbfgs.cuh"
@@ -1346,6 +1347,67 @@ extern "C" sb_status sb_segments(const sb_problem *p, int32_t family, uint64_t s
     SB_CUDA_TRY(cudaMemsetAsync(w.su.hdr, 0, sizeof(WsHeader), cs));
     launch_setup(pv, cs);
     launch_segments(pv, family, seed, n_rays, n_steps, delta, n_ref, w.scratch, ends, ell_coarse, t_ref, ell_ref, cs);
+    SB_CUDA_TRY(cudaGetLastError());
+    return SB_OK;
+}
+
+// ------------------------------------------------------------------ black-box derivatives (App. A.4)
+namespace {
+
+struct FdWs {
+    SetupWs su;
+    double *scratch;
+    size_t bytes;
+};
+
+FdWs fd_layout(void *base, const sb_problem *p, bool full) {
+    FdWs w{};
+    Carver cv(base);
+    w.su.hdr = cv.take<WsHeader>(1);
+    w.su.a = cv.take<double>(p->K);
+    w.su.c = cv.take<double>(p->d);
+    w.su.half = cv.take<double>(p->d);
+    w.su.logV = cv.take<double>(1);
+    w.su.wmax = cv.take<double>(1);
+    w.scratch = cv.take<double>(fd_scratch_elems(p->d, p->K, full));
+    w.bytes = cv.bytes();
+    return w;
+}
+
+}  // namespace
+
+extern "C" size_t sb_fd_workspace_bytes(const sb_problem *p, int32_t full) {
+    if (check_problem(p) != SB_OK) return 0;
+    return fd_layout(nullptr, p, full != 0).bytes;
+}
+
+extern "C" sb_status sb_fd_derivatives(const sb_problem *p, const double *x, double eps_g, double eps_h, int32_t full,
+                                       double *grad, double *hdiag, double *H, double *b, void *ws, size_t ws_bytes,
+                                       void *stream) {
+    sb_status st = check_problem(p);
+    if (st != SB_OK) return st;
+    if (!x || !hdiag || !ws || (full && !H)) return SB_ERR_INVALID_ARG;
+    if (!(eps_g > 0.0) || !(eps_h > 0.0) || !std::isfinite(eps_g) || !std::isfinite(eps_h)) return SB_ERR_INVALID_ARG;
+    const FdWs w = fd_layout(ws, p, full != 0);
+    if (ws_bytes < w.bytes) return SB_ERR_WORKSPACE;
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    ProbView pv;
+    pv.d = p->d;
+    pv.K = p->K;
+    pv.log_w = p->log_w;
+    pv.mu = p->mu;
+    pv.L = p->L;
+    pv.lo = p->lo;
+    pv.hi = p->hi;
+    pv.a = w.su.a;
+    pv.c = w.su.c;
+    pv.half = w.su.half;
+    pv.logV = w.su.logV;
+    pv.wmax = w.su.wmax;
+    pv.status = &w.su.hdr->status;
+    SB_CUDA_TRY(cudaMemsetAsync(w.su.hdr, 0, sizeof(WsHeader), cs));
+    launch_setup(pv, cs);
+    launch_fd(pv, x, eps_g, eps_h, full != 0, w.scratch, grad, hdiag, H, b, cs);
     SB_CUDA_TRY(cudaGetLastError());
     return SB_OK;
 }

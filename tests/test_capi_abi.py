@@ -106,3 +106,16 @@ def test_segments_reject_bad_arguments_on_the_host():
     small = L.sb_segments_workspace_bytes(C.byref(p), 8, 16)
     assert 0 < small < L.sb_segments_workspace_bytes(C.byref(p), 64, 16)
     assert L.sb_segments_workspace_bytes(C.byref(p), 0, 16) == 0
+
+
+def test_fd_derivatives_reject_bad_arguments_on_the_host():
+    p = _fake_problem(8, 1)
+    L = sb.lib()
+    buf = (C.c_char * 16)()
+    call = lambda eg, eh, full, H, nbytes: L.sb_fd_derivatives(C.byref(p), buf, eg, eh, full, buf, buf, H, buf, buf,
+                                                               nbytes, None)
+    assert call(0.0, 1e-4, 0, None, 16) == sb.SB_ERR_INVALID_ARG
+    assert call(1e-5, float("inf"), 0, None, 16) == sb.SB_ERR_INVALID_ARG
+    assert call(1e-5, 1e-4, 1, None, 16) == sb.SB_ERR_INVALID_ARG  # full Hessian needs H
+    assert call(1e-5, 1e-4, 0, None, 16) == sb.SB_ERR_WORKSPACE
+    assert 0 < L.sb_fd_workspace_bytes(C.byref(p), 0) < L.sb_fd_workspace_bytes(C.byref(_fake_problem(512, 1)), 1)
