@@ -1221,6 +1221,43 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
     return SB_OK;
 }
 
+// ------------------------------------------------------------------ setup-only entry points
+namespace {
+
+// Carves the per-problem constants (a_k, centre, half-widths, log V) at the start of a
+// workspace; used by the entry points that need no solve-stage layout.
+void carve_setup(Carver &cv, const sb_problem *p, SetupWs &su) {
+    su.hdr = cv.take<WsHeader>(1);
+    su.a = cv.take<double>(p->K);
+    su.c = cv.take<double>(p->d);
+    su.half = cv.take<double>(p->d);
+    su.logV = cv.take<double>(1);
+    su.wmax = cv.take<double>(1);
+}
+
+// The problem view over those constants, computed on `cs` (status word cleared first).
+cudaError_t setup_only(const sb_problem *p, const SetupWs &su, cudaStream_t cs, ProbView &pv) {
+    pv.d = p->d;
+    pv.K = p->K;
+    pv.log_w = p->log_w;
+    pv.mu = p->mu;
+    pv.L = p->L;
+    pv.lo = p->lo;
+    pv.hi = p->hi;
+    pv.a = su.a;
+    pv.c = su.c;
+    pv.half = su.half;
+    pv.logV = su.logV;
+    pv.wmax = su.wmax;
+    pv.status = &su.hdr->status;
+    const cudaError_t e = cudaMemsetAsync(su.hdr, 0, sizeof(WsHeader), cs);
+    if (e != cudaSuccess) return e;
+    launch_setup(pv, cs);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 // ------------------------------------------------------------------ preprocessing (Sec. 3.4)
 namespace {
 
@@ -1233,12 +1270,7 @@ struct PrecheckWs {
 PrecheckWs precheck_layout(void *base, const sb_problem *p) {
     PrecheckWs w{};
     Carver cv(base);
-    w.su.hdr = cv.take<WsHeader>(1);
-    w.su.a = cv.take<double>(p->K);
-    w.su.c = cv.take<double>(p->d);
-    w.su.half = cv.take<double>(p->d);
-    w.su.logV = cv.take<double>(1);
-    w.su.wmax = cv.take<double>(1);
+    carve_setup(cv, p, w.su);
     w.scratch = cv.take<double>(precheck_scratch_elems(p->d, p->K));
     w.bytes = cv.bytes();
     return w;
@@ -1263,21 +1295,7 @@ extern "C" sb_status sb_precheck(const sb_problem *p, double eps_flat, double ep
     if (ws_bytes < w.bytes) return SB_ERR_WORKSPACE;
     const cudaStream_t cs = static_cast<cudaStream_t>(stream);
     ProbView pv;
-    pv.d = p->d;
-    pv.K = p->K;
-    pv.log_w = p->log_w;
-    pv.mu = p->mu;
-    pv.L = p->L;
-    pv.lo = p->lo;
-    pv.hi = p->hi;
-    pv.a = w.su.a;
-    pv.c = w.su.c;
-    pv.half = w.su.half;
-    pv.logV = w.su.logV;
-    pv.wmax = w.su.wmax;
-    pv.status = &w.su.hdr->status;
-    SB_CUDA_TRY(cudaMemsetAsync(w.su.hdr, 0, sizeof(WsHeader), cs));
-    launch_setup(pv, cs);
+    SB_CUDA_TRY(setup_only(p, w.su, cs, pv));
     launch_precheck(pv, eps_flat, eps_soft, w.scratch, s, cls, log_int, log_vol, n_active, cs);
     SB_CUDA_TRY(cudaGetLastError());
     return SB_OK;
@@ -1295,12 +1313,7 @@ struct SegmentsWs {
 SegmentsWs segments_layout(void *base, const sb_problem *p, int n_rays, int n_steps) {
     SegmentsWs w{};
     Carver cv(base);
-    w.su.hdr = cv.take<WsHeader>(1);
-    w.su.a = cv.take<double>(p->K);
-    w.su.c = cv.take<double>(p->d);
-    w.su.half = cv.take<double>(p->d);
-    w.su.logV = cv.take<double>(1);
-    w.su.wmax = cv.take<double>(1);
+    carve_setup(cv, p, w.su);
     w.scratch = cv.take<double>(segments_scratch_elems(n_rays, n_steps, p->d, p->K));
     w.bytes = cv.bytes();
     return w;
@@ -1331,21 +1344,7 @@ extern "C" sb_status sb_segments(const sb_problem *p, int32_t family, uint64_t s
     if (ws_bytes < w.bytes) return SB_ERR_WORKSPACE;
     const cudaStream_t cs = static_cast<cudaStream_t>(stream);
     ProbView pv;
-    pv.d = p->d;
-    pv.K = p->K;
-    pv.log_w = p->log_w;
-    pv.mu = p->mu;
-    pv.L = p->L;
-    pv.lo = p->lo;
-    pv.hi = p->hi;
-    pv.a = w.su.a;
-    pv.c = w.su.c;
-    pv.half = w.su.half;
-    pv.logV = w.su.logV;
-    pv.wmax = w.su.wmax;
-    pv.status = &w.su.hdr->status;
-    SB_CUDA_TRY(cudaMemsetAsync(w.su.hdr, 0, sizeof(WsHeader), cs));
-    launch_setup(pv, cs);
+    SB_CUDA_TRY(setup_only(p, w.su, cs, pv));
     launch_segments(pv, family, seed, n_rays, n_steps, delta, n_ref, w.scratch, ends, ell_coarse, t_ref, ell_ref, cs);
     SB_CUDA_TRY(cudaGetLastError());
     return SB_OK;
@@ -1363,12 +1362,7 @@ struct FdWs {
 FdWs fd_layout(void *base, const sb_problem *p, bool full) {
     FdWs w{};
     Carver cv(base);
-    w.su.hdr = cv.take<WsHeader>(1);
-    w.su.a = cv.take<double>(p->K);
-    w.su.c = cv.take<double>(p->d);
-    w.su.half = cv.take<double>(p->d);
-    w.su.logV = cv.take<double>(1);
-    w.su.wmax = cv.take<double>(1);
+    carve_setup(cv, p, w.su);
     w.scratch = cv.take<double>(fd_scratch_elems(p->d, p->K, full));
     w.bytes = cv.bytes();
     return w;
@@ -1392,21 +1386,7 @@ extern "C" sb_status sb_fd_derivatives(const sb_problem *p, const double *x, dou
     if (ws_bytes < w.bytes) return SB_ERR_WORKSPACE;
     const cudaStream_t cs = static_cast<cudaStream_t>(stream);
     ProbView pv;
-    pv.d = p->d;
-    pv.K = p->K;
-    pv.log_w = p->log_w;
-    pv.mu = p->mu;
-    pv.L = p->L;
-    pv.lo = p->lo;
-    pv.hi = p->hi;
-    pv.a = w.su.a;
-    pv.c = w.su.c;
-    pv.half = w.su.half;
-    pv.logV = w.su.logV;
-    pv.wmax = w.su.wmax;
-    pv.status = &w.su.hdr->status;
-    SB_CUDA_TRY(cudaMemsetAsync(w.su.hdr, 0, sizeof(WsHeader), cs));
-    launch_setup(pv, cs);
+    SB_CUDA_TRY(setup_only(p, w.su, cs, pv));
     launch_fd(pv, x, eps_g, eps_h, full != 0, w.scratch, grad, hdiag, H, b, cs);
     SB_CUDA_TRY(cudaGetLastError());
     return SB_OK;
