@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="time the forward solve and the d log Z / d (mu, L) adjoint (one JSON line)")
     ap.add_argument("--chisao", action="store_true",
-                    help="time discovery + the ChiSao oscillation (FP64) on the d=64 K=4 mixture (one JSON line)")
+                    help="time discovery + the ChiSao oscillation (one JSON line): FP64 on the d=64 K=4 mixture, "
+                         "or --chisao-workload 4 for the d=1024 K=8 mixture at --prec")
+    ap.add_argument("--chisao-workload", type=int, default=1, choices=[1, 4])
     ap.add_argument("--prec", default="bf16", choices=list(PREC))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -382,13 +384,16 @@ def run_adjoint(sb, args):
 
 
 def run_chisao(sb, args):
-    """Discovery followed by the ChiSao oscillation (FP64, 3 oscillations, one sample per
-    discovered start) on the d=64, K=4 mixture; one step = sb_discover + sb_chisao. Reports
+    """Discovery followed by the ChiSao oscillation (3 oscillations, one sample per discovered
+    start): FP64 on the d=64, K=4 mixture, or the d=1024, K=8 mixture at the mixed precision
+    given by --prec; one step = sb_discover + sb_chisao. Reports
     the time per step, the device time per kernel class, and the components found as peaks
     against those whose peak passes the stick test and against the plain evidence solve."""
     import torch
 
-    inst, cfg = workload_cfg(1, "fp64", args.scale)
+    wid = args.chisao_workload
+    prec = "fp64" if wid == 1 else args.prec
+    inst, cfg = workload_cfg(wid, prec, args.scale)
     prob = sb.Problem(inst)
     c = sb.make_config(cfg)
     cc = sb.make_chisao_config()
@@ -422,7 +427,7 @@ def run_chisao(sb, args):
     plain = sb.evidence(prob, c, ws=wsc)
     plain_found = sorted({int(np.argmin(np.abs(inst.mu - m).max(1))) for m in plain.modes.cpu().numpy()})
     names = ["tc_z_walkers", "tc_z_rays", "tc_grad", "lbfgs_step_f32", "f64_z", "f64_grad", "cholesky", "other"]
-    print(json.dumps({"case": "chisao", "workload": workload_name(1, inst, cfg) + ", FP64, 3 oscillations",
+    print(json.dumps({"case": "chisao", "workload": workload_name(wid, inst, cfg) + f", {prec}, 3 oscillations",
                       "ms_per_step": dt * 1e3, "steps": reps, "launches_per_step": int(launches),
                       "n_peaks": out.n_peaks, "components_found": found, "components_passing_stick_test": expect,
                       "components_found_without_chisao": plain_found,

@@ -271,11 +271,17 @@ typedef struct sb_chisao_config {
 size_t sb_chisao_workspace_bytes(const sb_problem *prob, const sb_config *cfg);
 
 /*
- * ChiSao oscillation (Sec. 3.5.5) of n <= cfg->n_starts samples, FP64 only
- * (cfg->prec must be SB_PREC_FP64, else SB_ERR_UNSUPPORTED). n_osc times:
+ * ChiSao oscillation (Sec. 3.5.5) of n <= cfg->n_starts samples. With
+ * cfg->prec = SB_PREC_FP64 everything is FP64; with TF32 / BF16 the refinement is
+ * sb_refine's mixed path, the ray samples and momentum gradients come from the
+ * tensor-core likelihood, and n_starts must be at least n_steps (else
+ * SB_ERR_UNSUPPORTED). n_osc times:
  *   convergence: sb_refine's L-BFGS from the current positions, at most
  *     conv_iters accepted steps;
- *   stick test: |grad l|_inf <= eps_grad (1 + |l|) and l >= max l + log 0.1;
+ *   stick test: converged and l >= max l + log 0.1, converged meaning
+ *     |grad l|_inf <= eps_grad (1 + |l|) in FP64, and the refinement's
+ *     CONVERGED / STALLED state on the mixed path (whose gradients are too
+ *     coarse for that test);
  *   dedup of the stuck samples (greedy L-inf, radius dedup_coarse
  *     max_i (hi_i - lo_i), decreasing l): representatives stay stuck (the
  *     peaks), the other stuck samples are lost;

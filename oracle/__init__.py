@@ -223,7 +223,8 @@ def evidence(inst, cfg, n_threads=1) -> LaplaceResult:
 # ------------------------------------------------------------------ ChiSao (Sec. 3.5.5)
 class _ChisaoConfig(C.Structure):
     _fields_ = [("n_osc", C.c_int), ("conv_iters", C.c_int), ("anti_steps", C.c_int),
-                ("min_unconverged", C.c_int), ("momentum", C.c_double), ("anti_alpha", C.c_double)]
+                ("min_unconverged", C.c_int), ("momentum", C.c_double), ("anti_alpha", C.c_double),
+                ("conv_from_status", C.c_int)]
 
 
 @dataclass
@@ -236,6 +237,7 @@ class ChisaoConfig:
     min_unconverged: int = 5
     momentum: float = 0.9
     anti_alpha: float = 0.01
+    conv_from_status: bool = False
 
 
 @dataclass
@@ -278,7 +280,8 @@ def chisao_ray_best(inst, origin, direction, n_steps, past_valley=False):
 def chisao(inst, cfg, cc: ChisaoConfig, x0, n_threads=1) -> ChisaoResult:
     P = OracleProblem(inst)
     c = _cfg(cfg, n_threads)
-    k = _ChisaoConfig(cc.n_osc, cc.conv_iters, cc.anti_steps, cc.min_unconverged, cc.momentum, cc.anti_alpha)
+    k = _ChisaoConfig(cc.n_osc, cc.conv_iters, cc.anti_steps, cc.min_unconverged, cc.momentum, cc.anti_alpha,
+                      int(bool(cc.conv_from_status)))
     x0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(-1, P.d)
     n = x0.shape[0]
     xo = np.empty_like(x0)

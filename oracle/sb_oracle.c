@@ -741,7 +741,9 @@ int orc_evidence(const orc_problem *p, const orc_config *c, double *modes, doubl
 /*  - a sample is converged when |grad l|_inf <= eps_grad (1 + |l|) (the     */
 /*    scaled form of the Laplace filter) and sticks when also l >= l_max +    */
 /*    log 0.1 (l_max over all finite samples); "unconverged" samples are the  */
-/*    finite ones that are not converged;                                     */
+/*    finite ones that are not converged; with conv_from_status, converged is */
+/*    the refinement's CONVERGED / STALLED state instead (the reading for a   */
+/*    refinement whose gradients are too coarse for the FP64 test);           */
 /*  - deduplication runs over the stuck samples with the coarse radius        */
 /*    (greedy, l descending, ties to the lower index); the stuck samples that */
 /*    are not representatives are the K_lost duplicates;                      */
@@ -907,8 +909,12 @@ int orc_chisao(const orc_problem *p, const orc_config *c, const orc_chisao_confi
         for (int s = 0; s < n; ++s) {
             conv[s] = 0;
             if (isfinite(ell[s])) {
-                const double l = orc_loglik(p, x + (size_t)s * d, dir, NULL);
-                conv[s] = (int8_t)(max_abs(d, dir) <= c->eps_grad * (1.0 + fabs(l)));
+                if (cc->conv_from_status) {
+                    conv[s] = (int8_t)(st[s] == ORC_CONVERGED || st[s] == ORC_STALLED);
+                } else {
+                    const double l = orc_loglik(p, x + (size_t)s * d, dir, NULL);
+                    conv[s] = (int8_t)(max_abs(d, dir) <= c->eps_grad * (1.0 + fabs(l)));
+                }
             }
             stuck[s] = (int8_t)(conv[s] && ell[s] >= lmax + log(0.1));
             lost[s] = 0;

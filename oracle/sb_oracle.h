@@ -80,6 +80,7 @@ int orc_evidence(const orc_problem *p, const orc_config *c, double *modes, doubl
 typedef struct {
     int n_osc, conv_iters, anti_steps, min_unconverged;
     double momentum, anti_alpha;
+    int conv_from_status; /* 1: "converged" is the refinement's CONVERGED / STALLED state (mixed-precision reading) */
 } orc_chisao_config;
 
 /* anti-convergence of n samples in place: steps momentum descent steps of step size alpha */

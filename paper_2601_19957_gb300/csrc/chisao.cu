@@ -67,6 +67,14 @@ __global__ void __launch_bounds__(256) k_cs_conv(int n, int d, const double *G, 
     }
 }
 
+__global__ void __launch_bounds__(256) k_cs_conv_status(int n, const int8_t *status, const double *ell,
+                                                        uint8_t *conv) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int st = status[s];
+    conv[s] = (uint8_t)(isfinite(ell[s]) && (st == SB_WALKER_CONVERGED || st == SB_WALKER_STALLED));
+}
+
 constexpr int CS_CTA = 1024;  // single-CTA list kernels
 
 __global__ void __launch_bounds__(CS_CTA) k_cs_stick(int n, const double *ell, const uint8_t *conv,
@@ -323,6 +331,12 @@ void launch_cs_conv(int n, int d, const double *G, const double *ell, double eps
     if (n <= 0) return;
     note_launch();
     k_cs_conv<<<warp_grid(n), 256, 0, s>>>(n, d, G, ell, eps, conv);
+}
+
+void launch_cs_conv_status(int n, const int8_t *status, const double *ell, uint8_t *conv, cudaStream_t s) {
+    if (n <= 0) return;
+    note_launch();
+    k_cs_conv_status<<<(n + 255) / 256, 256, 0, s>>>(n, status, ell, conv);
 }
 
 void launch_cs_stick(int n, const double *ell, const uint8_t *conv, uint8_t *stuck, cudaStream_t s) {

@@ -1109,7 +1109,9 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
     if (!c || n < 1 || n > c->n_starts) return SB_ERR_INVALID_ARG;
     sb_status st = check_chisao(cc);
     if (st != SB_OK) return st;
-    if (c->prec != SB_PREC_FP64) return SB_ERR_UNSUPPORTED;
+    // the mixed path evaluates ray samples in chunks of at most n_starts rows
+    const bool mixed = c->prec != SB_PREC_FP64;
+    if (mixed && c->n_starts < c->n_steps) return SB_ERR_UNSUPPORTED;
     Prelude P;
     st = prelude(p, c, ws, ws_bytes, stream, P);
     if (st != SB_OK) return st;
@@ -1143,11 +1145,20 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
     int peaks_prev = -1;
     for (int osc = 0; osc < cc->n_osc; ++osc) {
         // convergence phase: every sample released, L-BFGS from where it is
-        st = run_refine<double>(pv, &c2, r, w.X, n, w.X, w.ell, w.status, nullptr, nullptr, s);
+        if (mixed)
+            st = run_refine<float>(pv, &c2, P.L.r32, w.X, n, w.X, w.ell, w.status, nullptr, nullptr, s);
+        else
+            st = run_refine<double>(pv, &c2, r, w.X, n, w.X, w.ell, w.status, nullptr, nullptr, s);
         if (st != SB_OK) return st;
-        // stick test, then the dedup of the stuck samples (representatives stay stuck)
-        grad_at(nullptr, nullptr, n);
-        launch_cs_conv(n, d, w.G, w.ell, c->eps_grad, w.conv, s);
+        // stick test, then the dedup of the stuck samples (representatives stay stuck); the
+        // mixed path's gradients are too coarse for the FP64 gradient test, so there the
+        // refinement's CONVERGED / STALLED state is the test
+        if (mixed) {
+            launch_cs_conv_status(n, w.status, w.ell, w.conv, s);
+        } else {
+            grad_at(nullptr, nullptr, n);
+            launch_cs_conv(n, d, w.G, w.ell, c->eps_grad, w.conv, s);
+        }
         launch_cs_stick(n, w.ell, w.conv, w.stuck, s);
         launch_dedup(n, d, w.X, w.ell, nullptr, w.stuck, c->dedup_coarse, pv.wmax, n, w.reps, w.n_reps, la.assigned,
                      dds, s);
@@ -1191,13 +1202,19 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
             for (int l0 = 0; l0 < n_lost; l0 += w.lc) {
                 const int nl = n_lost - l0 < w.lc ? n_lost - l0 : w.lc;
                 launch_cs_ray_points(l0, nl, c->n_steps, d, w.O, w.U, w.texit, w.P, s);
-                LikF64Args a = f64_args(pv);
-                a.X = w.P;
-                a.n_rows = nl * c->n_steps;
-                a.qpart = w.qp;
-                a.ell = w.ellp;
-                a.out_by_walker = 0;
-                launch_lik_f64_points(a, false, s);
+                if (mixed) {
+                    st = tc_loglik_points(pv, c, P.L.r32.tc, w.P, nl * c->n_steps, nullptr, nullptr, w.ellp, nullptr,
+                                          s);
+                    if (st != SB_OK) return st;
+                } else {
+                    LikF64Args a = f64_args(pv);
+                    a.X = w.P;
+                    a.n_rows = nl * c->n_steps;
+                    a.qpart = w.qp;
+                    a.ell = w.ellp;
+                    a.out_by_walker = 0;
+                    launch_lik_f64_points(a, false, s);
+                }
                 launch_cs_ray_pick(l0, nl, c->n_steps, d, past_valley, w.ellp, w.lost_list, w.O, w.U, w.texit, w.X,
                                    s);
             }
@@ -1206,7 +1223,12 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
         if (cc->anti_steps > 0 && n_moving > 0) {
             SB_CUDA_TRY(cudaMemsetAsync(w.V, 0, sizeof(double) * n * d, s));
             for (int t = 0; t < cc->anti_steps; ++t) {
-                grad_at(w.moving_list, w.cnt + 2, n_moving);
+                if (mixed) {  // every sample's gradient; the step moves the listed ones only
+                    st = tc_loglik_points(pv, c, P.L.r32.tc, w.X, n, nullptr, nullptr, w.ellg, w.G, s);
+                    if (st != SB_OK) return st;
+                } else {
+                    grad_at(w.moving_list, w.cnt + 2, n_moving);
+                }
                 launch_cs_momentum(n_moving, d, w.moving_list, w.cnt + 2, cc->momentum, cc->anti_alpha, w.G, w.V, w.X,
                                    pv.lo, pv.hi, s);
             }

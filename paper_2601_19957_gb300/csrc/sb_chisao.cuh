@@ -6,6 +6,8 @@ namespace sb {
 
 // Gradient test: conv[s] = l_s finite and |G_s|_inf <= eps (1 + |l_s|).
 void launch_cs_conv(int n, int d, const double *G, const double *ell, double eps, uint8_t *conv, cudaStream_t s);
+// Mixed-precision form of the test: conv[s] = l_s finite and status CONVERGED or STALLED.
+void launch_cs_conv_status(int n, const int8_t *status, const double *ell, uint8_t *conv, cudaStream_t s);
 // Stick test over all samples (one CTA): stuck[s] = conv[s] and l_s >= max_finite l + log 0.1.
 void launch_cs_stick(int n, const double *ell, const uint8_t *conv, uint8_t *stuck, cudaStream_t s);
 // After the dedup of the stuck samples: lost = stuck and not a representative; stuck = representative.

@@ -70,7 +70,8 @@ def test_chisao_rejects_bad_config_and_mixed_precision_on_the_host():
     assert L.sb_chisao(*args(cfg, C.byref(sb.make_chisao_config(min_unconverged=0)))) == sb.SB_ERR_INVALID_ARG
     assert L.sb_chisao(*args(cfg, C.byref(sb.make_chisao_config(n_osc=0)))) == sb.SB_ERR_INVALID_ARG
     assert L.sb_chisao(*args(cfg, C.byref(sb.make_chisao_config(momentum=float("nan"))))) == sb.SB_ERR_INVALID_ARG
-    bf16 = sb.make_config(SolveConfig(n_starts=16, prec=sb.PREC_BF16))
+    # the mixed path evaluates ray samples in chunks of n_starts rows: fewer starts than steps is refused
+    bf16 = sb.make_config(SolveConfig(n_starts=16, n_steps=64, prec=sb.PREC_BF16))
     assert L.sb_chisao(*args(bf16, C.byref(cc))) == sb.SB_ERR_UNSUPPORTED
     too_many = (C.byref(p), C.byref(cfg), C.byref(cc), buf, 17, buf, buf, buf, buf, buf, C.c_size_t(16), None)
     assert L.sb_chisao(*too_many) == sb.SB_ERR_INVALID_ARG

@@ -221,3 +221,26 @@ def test_many_unconverged_samples_reseed_by_repulse_monkey():
         assert np.abs(g).max() <= cfg.eps_grad * (1 + abs(res.ell[res.stuck][a]))
         for b in range(a):
             assert np.abs(found[a] - found[b]).max() > cfg.dedup_coarse * wmax
+
+
+def test_status_reading_of_the_stick_test():
+    """conv_from_status: one oscillation sticks the CONVERGED / STALLED samples above the
+    threshold (a MAXITER sample does not stick even at a good l)."""
+    inst = make_instance(3, 3, 61, s_range=(0.4, 1.0), mean_box=(-5, 5), sep=4.0)
+    cfg = SolveConfig(max_iter=1000)
+    x0 = np.random.default_rng(3).uniform(-6, 6, (40, 3))
+    cc = oracle.ChisaoConfig(n_osc=1, conv_iters=6, conv_from_status=True)
+    res = oracle.chisao(inst, cfg, cc, x0)
+    ref = oracle.lbfgs(inst, SolveConfig(max_iter=6), x0)
+    np.testing.assert_array_equal(res.x, ref.x)
+    ok = np.isin(ref.status, [oracle.CONVERGED, oracle.STALLED]) & np.isfinite(ref.ell)
+    lmax = ref.ell[np.isfinite(ref.ell)].max()
+    cand = [s for s in range(40) if ok[s] and ref.ell[s] >= lmax + math.log(0.1)]
+    cand.sort(key=lambda s: (-ref.ell[s], s))
+    wmax = float((inst.hi - inst.lo).max())
+    reps = []
+    for s in cand:
+        if all(np.abs(ref.x[s] - ref.x[r]).max() > cfg.dedup_coarse * wmax for r in reps):
+            reps.append(s)
+    assert np.flatnonzero(res.stuck).tolist() == sorted(reps)
+    assert (ref.status == oracle.MAXITER).any()  # the case has samples the status reading leaves out
