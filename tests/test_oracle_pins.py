@@ -432,3 +432,19 @@ def test_overlapping_modes_4d_sign_and_size():
     assert res.n_modes == 4
     assert rel * claims["overlap_4d_error_sign"] > 0
     assert 1e-3 < rel < 0.2
+
+
+def test_first_step_is_unit_length_and_backtracking_halves():
+    """Readings 8-9 on a 1-d Gaussian (sigma = 0.1, mean 0): the first trial is a unit
+    step against grad f; Armijo (c1 = 1e-4) rejects trials until f drops enough, each
+    rejection multiplying alpha by the backtrack factor. Worked by hand:
+    x0 = 0.3: alpha 1 -> -0.7 (f 24.5 > 4.5), alpha 1/2 -> -0.2 (f 2) accepted;
+    x0 = 0.05: alphas 1, 1/2, 1/4, 1/8 give f 45, 10.1, 2, 0.28 > 0.125, 1/16 -> -0.0125;
+    x0 = 2: alpha 1 -> 1 (f 50 < 200) accepted; factor 1/4 from 0.3: alpha 1/4 -> 0.05."""
+    inst = make_instance(1, 1, 1, s_range=(1.0, 1.0))
+    inst.L[0] = 10.0
+    inst.mu[0] = 0.0
+    for x0, x1, bt in [(0.3, -0.2, 0.5), (0.05, -0.0125, 0.5), (2.0, 1.0, 0.5), (0.3, 0.05, 0.25)]:
+        r = oracle.lbfgs(inst, SolveConfig(max_iter=1, backtrack=bt), np.array([[x0]]))
+        assert r.x[0, 0] == pytest.approx(x1, abs=1e-15)
+        assert r.status[0] == oracle.MAXITER and r.iters[0] == 1
