@@ -426,11 +426,20 @@ def run_chisao(sb, args):
     expect = [int(k) for k in np.flatnonzero(heights >= heights.max() + math.log(0.1))]
     plain = sb.evidence(prob, c, ws=wsc)
     plain_found = sorted({int(np.argmin(np.abs(inst.mu - m).max(1))) for m in plain.modes.cpu().numpy()})
+    # the stick rule keeps only peaks within log 10 of the highest; the Laplace stage run on
+    # every final sample shows which components the oscillation reached
+    lap = sb.laplace(prob, c, out.x, out.ell, ws=wsc)
+    lap_found = sorted({int(np.argmin(np.abs(inst.mu - m).max(1))) for m in lap.modes.cpu().numpy()})
+    logV = float(np.log(inst.hi - inst.lo).sum())
+    closed = float(np.log(np.exp(inst.log_w).sum())) - logV
     names = ["tc_z_walkers", "tc_z_rays", "tc_grad", "lbfgs_step_f32", "f64_z", "f64_grad", "cholesky", "other"]
     print(json.dumps({"case": "chisao", "workload": workload_name(wid, inst, cfg) + f", {prec}, 3 oscillations",
                       "ms_per_step": dt * 1e3, "steps": reps, "launches_per_step": int(launches),
                       "n_peaks": out.n_peaks, "components_found": found, "components_passing_stick_test": expect,
                       "components_found_without_chisao": plain_found,
+                      "components_found_by_laplace_on_all_final_samples": lap_found,
+                      "logZ_laplace_on_all_final_samples": lap.logZ, "logZ_closed_form_all_components": closed,
+                      "logZ_without_chisao": plain.logZ,
                       "device_ms_per_step": {nm: prof_ms[i] / reps for i, nm in enumerate(names) if prof_n[i]}}))
     return 0
 
