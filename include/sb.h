@@ -362,6 +362,19 @@ sb_status sb_segments(const sb_problem *prob, int32_t family, uint64_t seed, int
                       double delta, int32_t n_ref, double *ends, double *ell_coarse, double *t_ref, double *ell_ref,
                       void *ws, size_t ws_bytes, void *stream);
 
+/*
+ * Evidence with ChiSao (Sec. 3.5.5 between discovery and the Laplace stage):
+ * sb_discover, then sb_chisao from the n_starts starts, then sb_laplace over EVERY
+ * final sample (stuck or not, all eligible). The stick rule keeps only peaks within
+ * log 10 of the highest, while the evidence needs every component a sample reached,
+ * so the Laplace stage is not limited to the stuck peaks. Outputs as sb_evidence.
+ * ws: sb_chisao_workspace_bytes. Synchronises `stream`; a device status recorded by
+ * the first two stages is returned before the Laplace stage runs.
+ */
+sb_status sb_evidence_chisao(const sb_problem *prob, const sb_config *cfg, const sb_chisao_config *cc, double *logZ,
+                             double *modes, double *logZk, int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes,
+                             void *stream);
+
 /* Bytes of device scratch sb_precheck needs. */
 size_t sb_precheck_workspace_bytes(const sb_problem *prob);
 

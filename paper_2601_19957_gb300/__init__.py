@@ -83,7 +83,7 @@ def lib():
         L.sb_precheck.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         for name in ("sb_loglik", "sb_loglik_noalloc", "sb_discover", "sb_refine", "sb_laplace", "sb_evidence", "sb_evidence_host",
-                     "sb_check", "sb_chisao"):
+                     "sb_check", "sb_chisao", "sb_evidence_chisao"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -333,6 +333,23 @@ def segments(prob: Problem, family: int, seed: int, n_rays: int, n_steps: int, d
                              float(delta), int(n_ref), _ptr(ends), _ptr(lc), _ptr(tr) if n_ref > 0 else None,
                              _ptr(lr) if n_ref > 0 else None, ws.ptr, ws.nbytes, _stream(stream)), "sb_segments")
     return SegmentsOut(ends[0], ends[1], lc, tr, lr)
+
+
+def evidence_chisao(prob: Problem, cfg: _Config, cc: _ChisaoConfig, cap: Optional[int] = None, ws: Workspace = None,
+                    stream=None) -> "LaplaceOut":
+    """Discovery, the ChiSao oscillation, and the Laplace stage over every final sample."""
+    torch = _torch()
+    ws = ws or chisao_workspace(prob, cfg)
+    cap = cap or cfg.cand_cap
+    modes = torch.empty((cap, prob.d), dtype=torch.float64, device="cuda")
+    zk = torch.empty(cap, dtype=torch.float64, device="cuda")
+    nm = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lz = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _check(lib().sb_evidence_chisao(C.byref(prob.s), C.byref(cfg), C.byref(cc), _ptr(lz), _ptr(modes), _ptr(zk),
+                                    C.c_int32(cap), _ptr(nm), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)),
+           "sb_evidence_chisao")
+    k = min(int(nm.item()), cap)
+    return LaplaceOut(float(lz.item()), modes[:k], zk[:k], None, int(nm.item()))
 
 
 @dataclass

@@ -1243,6 +1243,33 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
     return SB_OK;
 }
 
+extern "C" sb_status sb_evidence_chisao(const sb_problem *p, const sb_config *c, const sb_chisao_config *cc,
+                                        double *logZ, double *modes, double *logZk, int32_t cap, int32_t *n_modes,
+                                        void *ws, size_t ws_bytes, void *stream) {
+    if (!logZ || !modes || !logZk || !n_modes || cap < 1) return SB_ERR_INVALID_ARG;
+    sb_status st = check_problem(p);
+    if (st != SB_OK) return st;
+    st = check_config(c);
+    if (st != SB_OK) return st;
+    st = check_chisao(cc);
+    if (st != SB_OK) return st;
+    if (!ws) return SB_ERR_INVALID_ARG;
+    const Layout L = layout(ws, p, c);
+    if (ws_bytes < L.bytes + chisao_layout(nullptr, L.bytes, p, c).bytes) return SB_ERR_WORKSPACE;
+    const int n = c->n_starts;
+    // discovery into the evidence buffers, ChiSao from its starts (the peak count goes to
+    // n_modes for now), then the Laplace stage over every final sample
+    st = sb_discover(p, c, L.ev.starts, L.ev.ell_starts, ws, ws_bytes, stream);
+    if (st != SB_OK) return st;
+    st = sb_chisao(p, c, cc, L.ev.starts, n, L.ev.x_out, L.ev.ell_out, L.ev.status, n_modes, ws, ws_bytes, stream);
+    if (st != SB_OK) return st;
+    // each stage clears the device status word on entry: surface what the first two recorded
+    st = sb_check(ws, ws_bytes, stream);
+    if (st != SB_OK) return st;
+    return sb_laplace(p, c, L.ev.x_out, L.ev.ell_out, nullptr, n, modes, logZk, nullptr, cap, n_modes, logZ, ws,
+                      ws_bytes, stream);
+}
+
 // ------------------------------------------------------------------ setup-only entry points
 namespace {
 

@@ -120,3 +120,17 @@ def test_fd_derivatives_reject_bad_arguments_on_the_host():
     assert call(1e-5, 1e-4, 1, None, 16) == sb.SB_ERR_INVALID_ARG  # full Hessian needs H
     assert call(1e-5, 1e-4, 0, None, 16) == sb.SB_ERR_WORKSPACE
     assert 0 < L.sb_fd_workspace_bytes(C.byref(p), 0) < L.sb_fd_workspace_bytes(C.byref(_fake_problem(512, 1)), 1)
+
+
+def test_evidence_chisao_rejects_bad_arguments_on_the_host():
+    cfg = sb.make_config(SolveConfig(n_starts=16))
+    p = _fake_problem(8, 1)
+    L = sb.lib()
+    buf = (C.c_char * 16)()
+    cc = sb.make_chisao_config()
+    assert L.sb_evidence_chisao(C.byref(p), C.byref(cfg), None, buf, buf, buf, 4, buf, buf, C.c_size_t(16),
+                                None) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_evidence_chisao(C.byref(p), C.byref(cfg), C.byref(cc), buf, buf, buf, 0, buf, buf, C.c_size_t(16),
+                                None) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_evidence_chisao(C.byref(p), C.byref(cfg), C.byref(cc), buf, buf, buf, 4, buf, buf, C.c_size_t(16),
+                                None) == sb.SB_ERR_WORKSPACE

@@ -244,3 +244,23 @@ def test_status_reading_of_the_stick_test():
             reps.append(s)
     assert np.flatnonzero(res.stuck).tolist() == sorted(reps)
     assert (ref.status == oracle.MAXITER).any()  # the case has samples the status reading leaves out
+
+
+@pytest.mark.parametrize("d,seed,plain_at_most", [(16, 0, 2), (64, 0, 1)])
+def test_laplace_on_all_final_samples_recovers_every_component(d, seed, plain_at_most):
+    """Six separated components: sunburst starts refined by L-BFGS reach only a few basins;
+    after ChiSao the stick rule keeps only peaks within log 10 of the highest, but the
+    Laplace stage run on every final sample finds all six (seeded regression of the
+    method as built)."""
+    inst = make_instance(d, 6, 100 * d + seed, s_range=(0.05, 0.5), mean_box=(-6, 6), sep=8.0)
+    cfg = SolveConfig(n_rays=128, n_steps=64, n_starts=128, m=10, seed=seed)
+    starts, _ = oracle.discover(inst, cfg, n_threads=4)
+    ref = oracle.lbfgs(inst, cfg, starts, n_threads=4)
+    plain = oracle.laplace(inst, cfg, ref.x, ref.ell, ref.status)
+    cs = oracle.chisao(inst, cfg, oracle.ChisaoConfig(n_osc=3), starts, n_threads=4)
+    lap = oracle.laplace(inst, cfg, cs.x, cs.ell)
+    comp = lambda M: sorted({int(np.argmin(np.abs(inst.mu - m).max(1))) for m in M})
+    assert len(comp(plain.modes)) <= plain_at_most
+    assert comp(lap.modes) == list(range(6))
+    logV = float(np.log(inst.hi - inst.lo).sum())
+    assert lap.logZ == pytest.approx(float(np.log(np.exp(inst.log_w).sum())) - logV, abs=1e-9)
