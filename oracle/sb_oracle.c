@@ -16,6 +16,13 @@
  *   Laplace per mode ......................... Sec. 3.7.1, Eq. (laplace-evidence) Sec. 4.2, App. A.3
  *   Cholesky log-determinant (whitening) ..... App. A.8
  *   log-sum-exp over modes ................... Sec. 3.7.3, App. A.10
+ *   ChiSao oscillation ....................... Sec. 3.5.5, Algorithm 1 (CarryTiger)
+ *   preprocessing probe and marginal terms ... Sec. 3.4 and its Algorithm
+ *   central-difference derivatives ........... App. A.4
+ *   rotation detection ....................... Sec. 3.7.2, App. A.6
+ *   V2V / V2E / W2W rays, two-pass sampling .. Sec. 3.5.1-3.5.2
+ * Every function is pinned by tests/test_oracle_*.py to closed forms, library
+ * routines, brute force or hand-worked cases.
  * Where the paper is silent (line search, tolerances, tie-breaks, ray grid) the
  * readings are stated next to the code that takes them.
  */
