@@ -293,10 +293,10 @@ size_t sb_chisao_workspace_bytes(const sb_problem *prob, const sb_config *cfg);
  *       (counter (pair, l, oscillation, 'RPMK'), key = seed) to the box face,
  *       sampled at t_j = (j+1)/n_steps t_exit, and moves to its best sample;
  *     Golden Rooster (otherwise, while it keeps finding peaks): lost sample l
- *       goes to peak l mod n_peaks along +-column c mod d of orthonormal basis
- *       c / d of that peak, c = (l / n_peaks) / 2 (+ for even l / n_peaks),
- *       the bases the QR of Philox normals (counter (pair, basis d + column,
- *       oscillation << 16 | peak, 'GRST')), to the best sample past the first
+ *       goes to peak l mod n_peaks along +-column c mod G of orthonormal group
+ *       c / G of that peak, G = min(d, 64), c = (l / n_peaks) / 2 (+ for even
+ *       l / n_peaks), a group the QR of G Philox-normal vectors (counter (pair,
+ *       group G + column, oscillation << 16 | peak, 'GRST')), to the best sample past the first
  *       valley of the ray (the exit sample when l never rises); it stays off
  *       after an oscillation that used it ends with no more peaks than before;
  *     anti-convergence: every sample that is not stuck (and not NONFINITE)

@@ -258,7 +258,8 @@ def chisao_anticonverge(inst, x, steps, momentum, alpha):
 
 
 def chisao_directions(d, r, seed, osc, peak, basis=0):
-    """The first r orthonormal directions of one basis, one per row."""
+    """The first r (at most min(d, 64)) orthonormal directions of one group, one per row."""
+    r = min(r, d, 64)
     Q = np.empty((r, d))
     lib().orc_chisao_directions(C.c_int(d), C.c_int(r), C.c_uint64(seed), C.c_int(osc), C.c_int(peak),
                                 C.c_int(basis), _ptr(Q))

@@ -761,9 +761,12 @@ int orc_evidence(const orc_problem *p, const orc_config *c, double *modes, doubl
 /*  - Golden Rooster (fewer such samples): lost sample l goes to peak         */
 /*    p = l mod n_peaks (representatives by decreasing l) along direction     */
 /*    c = (l / n_peaks) / 2, sign + for even l / n_peaks and - for odd;       */
-/*    direction c is column c mod d of orthonormal basis c / d of that peak   */
-/*    (modified Gram-Schmidt, i.e. the Q of a QR, of Philox normals with      */
-/*    counter (pair, basis d + column, osc << 16 | p, 'GRST')); on the ray it */
+/*    direction c is column c mod G of orthonormal group c / G of that peak,  */
+/*    G = min(d, 64) (the paper fixes no group size; at most d directions are */
+/*    mutually orthogonal, and groups of at most 64 keep a QR at O(d G^2));   */
+/*    a group is the Q of a QR (modified Gram-Schmidt) of G Philox-normal     */
+/*    vectors, counter (pair, group G + column, osc << 16 | p, 'GRST'); on    */
+/*    the ray it                                                              */
 /*    moves to the best sample beyond the first valley (the first sample      */
 /*    after which l rises), or to the exit sample when l never rises; it      */
 /*    stays off once an oscillation that used it ends with no more peaks than */
@@ -818,10 +821,12 @@ void orc_chisao_anticonverge(const orc_problem *p, double *x, int n, int steps, 
 }
 
 void orc_chisao_directions(int d, int r, uint64_t seed, int osc, int peak, int basis, double *Q) {
+    const int G = d < 64 ? d : 64; /* directions per orthonormal group */
+    if (r > G) r = G;
     /* columns j = 0..r-1 of Q (d x r, column j at Q[j*d..]): modified Gram-Schmidt */
     for (int j = 0; j < r; ++j) {
         double *qj = Q + (size_t)j * d;
-        philox_normals(d, seed, (uint32_t)basis * (uint32_t)d + (uint32_t)j, ((uint32_t)osc << 16) | (uint32_t)peak,
+        philox_normals(d, seed, (uint32_t)basis * (uint32_t)G + (uint32_t)j, ((uint32_t)osc << 16) | (uint32_t)peak,
                        0x47525354u, qj);
         for (int k = 0; k < j; ++k) {
             const double *qk = Q + (size_t)k * d;
@@ -967,7 +972,8 @@ int orc_chisao(const orc_problem *p, const orc_config *c, const orc_chisao_confi
                 orc_chisao_ray_best(p, x + (size_t)o * d, dir, c->n_steps, 0, x + (size_t)s * d, NULL);
             } else if (gr_on && n_peaks > 0) {
                 const int pk = l_ord % n_peaks, k = l_ord / n_peaks, cdir = k / 2;
-                const int basis = cdir / d, col = cdir % d;
+                const int G = d < 64 ? d : 64;
+                const int basis = cdir / G, col = cdir % G;
                 const double sgn = (k % 2 == 0) ? 1.0 : -1.0;
                 double *Q = (double *)malloc(sizeof(double) * (size_t)(col + 1) * d);
                 orc_chisao_directions(d, col + 1, c->seed, osc, pk, basis, Q);

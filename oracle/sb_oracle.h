@@ -85,7 +85,7 @@ typedef struct {
 
 /* anti-convergence of n samples in place: steps momentum descent steps of step size alpha */
 void orc_chisao_anticonverge(const orc_problem *p, double *x, int n, int steps, double momentum, double alpha);
-/* the first r <= d columns (Q[j*d..], j < r) of orthonormal basis `basis` of oscillation osc, peak peak */
+/* the first r <= min(d, 64) columns (Q[j*d..], j < r) of orthonormal group `basis` of oscillation osc, peak peak */
 void orc_chisao_directions(int d, int r, uint64_t seed, int osc, int peak, int basis, double *Q);
 /* best of n_steps samples on the ray from origin (clamped to the box) along dir to the box
  * boundary (past_valley: beyond the first valley); returns the sample index */

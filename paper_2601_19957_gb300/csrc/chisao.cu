@@ -9,8 +9,9 @@
 // here is FP64 with explicitly rounded products and sums where an update
 // formula is applied, and the random directions come from Philox4x32-10 with
 // the seed as key (counters (pair, l, oscillation, 'RPMK') for Repulse Monkey,
-// (pair, basis d + column, oscillation << 16 | peak, 'GRST') for Golden
-// Rooster), two uniforms per block, two normals by Box-Muller.
+// (pair, group G + column, oscillation << 16 | peak, 'GRST') for Golden
+// Rooster, in orthonormal groups of G = min(d, 64) directions), two uniforms
+// per block, two normals by Box-Muller.
 #include "sb_chisao.cuh"
 
 namespace sb {
@@ -20,6 +21,9 @@ namespace {
 constexpr double kLogTenth = -2.302585092994045684;  // log 0.1, rounded to double
 constexpr uint32_t kTagRm = 0x52504D4Bu;             // 'RPMK'
 constexpr uint32_t kTagGr = 0x47525354u;             // 'GRST'
+
+// Golden Rooster directions come in orthonormal groups of min(d, 64).
+__host__ __device__ __forceinline__ int cs_group(int d) { return d < 64 ? d : 64; }
 
 __device__ __forceinline__ double clamp_box(double x, double lo, double hi) {
     return x < lo ? lo : (x > hi ? hi : x);
@@ -198,10 +202,11 @@ __global__ void __launch_bounds__(CS_BASIS) k_cs_bases(int d, uint32_t k0, uint3
     double *Qj = Q + job_off[j];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = CS_BASIS / 32;
     const int npairs = (d + 1) / 2;
+    const int G = cs_group(d);
     for (int idx = threadIdx.x; idx < cols * npairs; idx += CS_BASIS) {
         const int c = idx / npairs, q = idx - c * npairs;
         double z0, z1;
-        normal_pair((uint32_t)q, (uint32_t)(b * d + c), ((uint32_t)osc << 16) | (uint32_t)pk, kTagGr, k0, k1, z0, z1);
+        normal_pair((uint32_t)q, (uint32_t)(b * G + c), ((uint32_t)osc << 16) | (uint32_t)pk, kTagGr, k0, k1, z0, z1);
         Qj[(size_t)c * d + 2 * q] = z0;
         if (2 * q + 1 < d) Qj[(size_t)c * d + 2 * q + 1] = z1;
     }
@@ -249,7 +254,8 @@ __global__ void __launch_bounds__(256) k_cs_gr_rays(int n_lost, int d, int n_pea
     const int l = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     if (l >= n_lost) return;
     const int pk = l % n_peaks, k = l / n_peaks, cdir = k >> 1;
-    const int b = cdir / d, col = cdir - b * d;
+    const int G = cs_group(d);
+    const int b = cdir / G, col = cdir - b * G;
     const double sgn = (k & 1) ? -1.0 : 1.0;
     const double *q = Q + job_off[job_start[pk] + b] + (size_t)col * d;
     const double *src = X + (size_t)reps[pk] * d;

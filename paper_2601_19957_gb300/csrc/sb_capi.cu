@@ -1065,9 +1065,10 @@ sb_status check_chisao(const sb_chisao_config *cc) {
     return SB_OK;
 }
 
-// Golden Rooster bases for n_lost lost samples over n_peaks peaks: lost sample l uses
-// direction c = (l / n_peaks) / 2 of peak l mod n_peaks, i.e. column c mod d of basis
-// c / d; every basis a peak needs is one job, its columns only as far as used.
+// Golden Rooster groups for n_lost lost samples over n_peaks peaks: lost sample l uses
+// direction c = (l / n_peaks) / 2 of peak l mod n_peaks, i.e. column c mod G of
+// orthonormal group c / G, G = min(d, 64); every group a peak needs is one job, its
+// columns only as far as used.
 struct GrJobs {
     std::vector<int32_t> start, pk, b, cols;
     std::vector<int64_t> off;
@@ -1081,8 +1082,9 @@ GrJobs gr_jobs(int n_lost, int n_peaks, int d) {
         const int count = n_lost > p ? (n_lost - p + n_peaks - 1) / n_peaks : 0;
         if (count == 0) continue;
         const int cmax = (count - 1) / 2;
-        for (int b = 0; b <= cmax / d; ++b) {
-            const int cols = b < cmax / d ? d : cmax - b * d + 1;
+        const int G = d < 64 ? d : 64;
+        for (int b = 0; b <= cmax / G; ++b) {
+            const int cols = b < cmax / G ? G : cmax - b * G + 1;
             j.pk.push_back(p);
             j.b.push_back(b);
             j.cols.push_back(cols);

@@ -78,18 +78,22 @@ def _philox_normals(d, seed, w1, w2, tag):
     return z
 
 
-@pytest.mark.parametrize("d,osc,peak,basis", [(1, 0, 0, 0), (6, 1, 3, 0), (9, 2, 0, 2)])
+@pytest.mark.parametrize("d,osc,peak,basis", [(1, 0, 0, 0), (6, 1, 3, 0), (9, 2, 0, 2), (100, 1, 2, 3)])
 def test_directions_are_the_q_of_the_normals(d, osc, peak, basis):
+    """Groups of G = min(d, 64) orthonormal directions: the Q of the QR of G normals."""
     seed = 0x1234_5678_9ABC
-    Q = oracle.chisao_directions(d, d, seed, osc, peak, basis)
-    np.testing.assert_allclose(Q @ Q.T, np.eye(d), atol=1e-13)
-    Z = np.stack([_philox_normals(d, seed, basis * d + j, (osc << 16) | peak, 0x47525354) for j in range(d)], 1)
+    G = min(d, 64)
+    Q = oracle.chisao_directions(d, G, seed, osc, peak, basis)
+    np.testing.assert_allclose(Q @ Q.T, np.eye(G), atol=1e-13)
+    Z = np.stack([_philox_normals(d, seed, basis * G + j, (osc << 16) | peak, 0x47525354) for j in range(G)], 1)
     q, r = np.linalg.qr(Z)
     q = q * np.sign(np.diag(r))[None, :]  # Gram-Schmidt keeps diag(R) > 0
     np.testing.assert_allclose(Q, q.T, atol=1e-12)
     # the first r columns do not depend on the later ones
-    np.testing.assert_array_equal(oracle.chisao_directions(d, max(1, d // 2), seed, osc, peak, basis),
-                                  Q[: max(1, d // 2)])
+    np.testing.assert_array_equal(oracle.chisao_directions(d, max(1, G // 2), seed, osc, peak, basis),
+                                  Q[: max(1, G // 2)])
+    # asking for more than a group gives the group
+    np.testing.assert_array_equal(oracle.chisao_directions(d, G + 5, seed, osc, peak, basis), Q)
 
 
 def test_directions_differ_by_peak_oscillation_and_basis():
