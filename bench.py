@@ -50,6 +50,9 @@ def parse():
                     help="time discovery + the ChiSao oscillation (one JSON line): FP64 on the d=64 K=4 mixture, "
                          "or --chisao-workload 4 for the d=1024 K=8 mixture at --prec")
     ap.add_argument("--chisao-workload", type=int, default=1, choices=[1, 4])
+    ap.add_argument("--next-rows", action="store_true",
+                    help="time the preprocessing probe, the V2V/V2E/W2W segment pass and the black-box "
+                         "derivatives (one JSON line)")
     ap.add_argument("--prec", default="bf16", choices=list(PREC))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -203,6 +206,8 @@ def main():
         return run_adjoint(sb, args)
     if args.chisao:
         return run_chisao(sb, args)
+    if args.next_rows:
+        return run_next_rows(sb, args)
     inst, cfg = workload_cfg(args.workload, args.prec, args.scale)
     prob = sb.Problem(inst)
     c = sb.make_config(cfg)
@@ -451,6 +456,52 @@ def run_chisao(sb, args):
                       "ms_per_evidence_chisao": dt_full * 1e3, "evidence_chisao_n_modes": full.n_modes,
                       "evidence_chisao_logZ": full.logZ,
                       "device_ms_per_step": {nm: prof_ms[i] / reps for i, nm in enumerate(names) if prof_n[i]}}))
+    return 0
+
+
+def run_next_rows(sb, args):
+    """Device time of the preprocessing probe and the segment pass on the d=1024, K=8 mixture
+    and of the black-box derivatives (full Hessian) on the d=64, K=4 mixture, each with its
+    algorithmic work: the probe reads the L_k twice (2 K d^2 x 8 B); the segment pass does one
+    FP64 z GEMM over 2 n_rays end points (2 n_rays K d(d+1)/2 multiply-adds); the derivatives
+    evaluate l at 2 d^2 + 2d + 3 points (K d(d+1) flop each)."""
+    import torch
+
+    reps = max(args.steps, 1)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    big, _ = workload_cfg(4, "fp64")
+    pb = sb.Problem(big)
+    d, K = big.d, big.K
+    ms_pre = timed(lambda: sb.precheck(pb))
+    n_rays, n_steps, n_ref = 4096, 64, 64
+    ms_seg = timed(lambda: sb.segments(pb, sb.RAY_W2W, 7, n_rays, n_steps, 10.0, n_ref))
+    small, _ = workload_cfg(1, "fp64")
+    ps = sb.Problem(small)
+    x = torch.as_tensor(small.mu[0] + 0.1, device="cuda")
+    ms_fd = timed(lambda: sb.fd_derivatives(ps, x, full=True))
+    ds, Ks = small.d, small.K
+    pts = 2 * ds * ds + 2 * ds + 3
+    print(json.dumps({"case": "next-rows",
+                      "precheck": {"workload": f"d={d} K={K}", "ms": ms_pre,
+                                   "algorithmic_GBps": 2 * K * d * d * 8 / (ms_pre * 1e-3) / 1e9},
+                      "segments": {"workload": f"d={d} K={K}, W2W, {n_rays} rays x {n_steps} + {n_ref} samples",
+                                   "ms": ms_seg,
+                                   "fp64_TFLOPs": 2 * n_rays * K * d * (d + 1) / (ms_seg * 1e-3) / 1e12},
+                      "fd_full_hessian": {"workload": f"d={ds} K={Ks}, {pts} points", "ms": ms_fd,
+                                          "l_evals_per_s": pts / (ms_fd * 1e-3)}}))
     return 0
 
 
