@@ -375,6 +375,22 @@ sb_status sb_evidence_chisao(const sb_problem *prob, const sb_config *cfg, const
                              double *modes, double *logZk, int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes,
                              void *stream);
 
+/* Bytes of device scratch sb_ray_loglik_quad needs (form 0 FP64, 1 FP32). */
+size_t sb_ray_loglik_quad_workspace_bytes(const sb_problem *prob, int32_t form, int32_t n_rays);
+
+/*
+ * Sunburst ray likelihoods from three scalars per (ray, component) (Sec. 3.5.1-3.5.2,
+ * a restructuring of the coarse pass): along x(t) = c + tau u_r, tau = ((j + 1) / n_steps)
+ * t_exit,r, z_k = z_k(c) + tau L_k^T u_r, so |z_k|^2 = q0_k + 2 tau q1_rk + tau^2 q2_rk and
+ * ell[r][j] = LSE_k (a_k - |z_k|^2 / 2) needs one triangular GEMM of the directions by each
+ * L_k instead of one per sample. form 0: FP64 GEMM; form 1: FP32 SIMT GEMM (u and L_k
+ * rounded to FP32, FP32 accumulation), the scalars combined in FP64. u: [n_rays][d] device
+ * (unit directions); ell: [n_rays][n_steps]. ws: sb_ray_loglik_quad_workspace_bytes.
+ * Asynchronous. (An experimental form of the coarse pass, not used by sb_discover yet.)
+ */
+sb_status sb_ray_loglik_quad(const sb_problem *prob, int32_t form, const double *u, int32_t n_rays, int32_t n_steps,
+                             double *ell, void *ws, size_t ws_bytes, void *stream);
+
 /* Bytes of device scratch sb_precheck needs. */
 size_t sb_precheck_workspace_bytes(const sb_problem *prob);
 

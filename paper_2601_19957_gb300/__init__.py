@@ -72,6 +72,8 @@ def lib():
         L.sb_precheck_workspace_bytes.restype = C.c_size_t
         L.sb_segments_workspace_bytes.restype = C.c_size_t
         L.sb_fd_workspace_bytes.restype = C.c_size_t
+        L.sb_ray_loglik_quad_workspace_bytes.restype = C.c_size_t
+        L.sb_ray_loglik_quad.restype = C.c_int
         L.sb_fd_derivatives.restype = C.c_int
         L.sb_fd_derivatives.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
@@ -282,6 +284,18 @@ def chisao(prob: Problem, cfg: _Config, cc: _ChisaoConfig, x0, ws: Workspace = N
     _check(lib().sb_chisao(C.byref(prob.s), C.byref(cfg), C.byref(cc), _ptr(x0), C.c_int32(n), _ptr(x), _ptr(ell),
                            _ptr(stuck), _ptr(npk), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)), "sb_chisao")
     return ChisaoOut(x, ell, stuck.bool(), int(npk.item()))
+
+
+def ray_loglik_quad(prob: Problem, u, n_steps: int, form: int = 1, stream=None):
+    """l at the sunburst samples of directions u [n_rays][d] from the quadratic in t (form 0 FP64, 1 FP32)."""
+    torch = _torch()
+    u = u.to(dtype=torch.float64, device="cuda").contiguous()
+    n_rays = u.shape[0]
+    ws = Workspace(int(lib().sb_ray_loglik_quad_workspace_bytes(C.byref(prob.s), int(form), int(n_rays))))
+    ell = torch.empty((n_rays, n_steps), dtype=torch.float64, device="cuda")
+    _check(lib().sb_ray_loglik_quad(C.byref(prob.s), C.c_int32(form), _ptr(u), C.c_int32(n_rays), C.c_int32(n_steps),
+                                    _ptr(ell), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)), "sb_ray_loglik_quad")
+    return ell
 
 
 @dataclass

@@ -15,6 +15,7 @@
 #include "sb_precheck.cuh"
 #include "sb_segments.cuh"
 #include "sb_fd.cuh"
+#include "sb_raysq.cuh"
 #include "sb_internal.cuh"
 #include "sb_laplace.cuh"
 #include "sb_lbfgs.cuh"
@@ -1439,6 +1440,48 @@ extern "C" sb_status sb_fd_derivatives(const sb_problem *p, const double *x, dou
     ProbView pv;
     SB_CUDA_TRY(setup_only(p, w.su, cs, pv));
     launch_fd(pv, x, eps_g, eps_h, full != 0, w.scratch, grad, hdiag, H, b, cs);
+    SB_CUDA_TRY(cudaGetLastError());
+    return SB_OK;
+}
+
+// ------------------------------------------------------------------ ray likelihoods by the quadratic in t
+namespace {
+
+struct RayqWs {
+    SetupWs su;
+    double *scratch;
+    size_t bytes;
+};
+
+RayqWs rayq_layout(void *base, const sb_problem *p, int n_rays, int form) {
+    RayqWs w{};
+    Carver cv(base);
+    carve_setup(cv, p, w.su);
+    w.scratch = cv.take<double>(rayq_scratch_elems(n_rays, p->d, p->K, form));
+    w.bytes = cv.bytes();
+    return w;
+}
+
+}  // namespace
+
+extern "C" size_t sb_ray_loglik_quad_workspace_bytes(const sb_problem *p, int32_t form, int32_t n_rays) {
+    if (check_problem(p) != SB_OK || (form != 0 && form != 1) || n_rays < 1 || n_rays > (1 << 24)) return 0;
+    return rayq_layout(nullptr, p, n_rays, form).bytes;
+}
+
+extern "C" sb_status sb_ray_loglik_quad(const sb_problem *p, int32_t form, const double *u, int32_t n_rays,
+                                        int32_t n_steps, double *ell, void *ws, size_t ws_bytes, void *stream) {
+    sb_status st = check_problem(p);
+    if (st != SB_OK) return st;
+    if ((form != 0 && form != 1) || !u || !ell || !ws) return SB_ERR_INVALID_ARG;
+    if (n_rays < 1 || n_rays > (1 << 24) || n_steps < 1 || (int64_t)n_rays * n_steps > 0x7fffffffLL)
+        return SB_ERR_INVALID_ARG;
+    const RayqWs w = rayq_layout(ws, p, n_rays, form);
+    if (ws_bytes < w.bytes) return SB_ERR_WORKSPACE;
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    ProbView pv;
+    SB_CUDA_TRY(setup_only(p, w.su, cs, pv));
+    launch_ray_loglik_quad(pv, form, u, n_rays, n_steps, w.scratch, ell, cs);
     SB_CUDA_TRY(cudaGetLastError());
     return SB_OK;
 }
