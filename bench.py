@@ -460,8 +460,9 @@ def run_chisao(sb, args):
 
 
 def run_next_rows(sb, args):
-    """Device time of the preprocessing probe and the segment pass on the d=1024, K=8 mixture
-    and of the black-box derivatives (full Hessian) on the d=64, K=4 mixture, each with its
+    """Device time of the preprocessing probe, the segment pass and the experimental quadratic
+    coarse pass (FP32 form, 16384 rays x 64 steps) on the d=1024, K=8 mixture and of the
+    black-box derivatives (full Hessian) on the d=64, K=4 mixture, each with its
     algorithmic work: the probe reads the L_k twice (2 K d^2 x 8 B); the segment pass does one
     FP64 z GEMM over 2 n_rays end points (2 n_rays K d(d+1)/2 multiply-adds); the derivatives
     evaluate l at 2 d^2 + 2d + 3 points (K d(d+1) flop each)."""
@@ -488,6 +489,10 @@ def run_next_rows(sb, args):
     ms_pre = timed(lambda: sb.precheck(pb))
     n_rays, n_steps, n_ref = 4096, 64, 64
     ms_seg = timed(lambda: sb.segments(pb, sb.RAY_W2W, 7, n_rays, n_steps, 10.0, n_ref))
+    g = torch.Generator(device="cpu").manual_seed(11)
+    U = torch.randn((16384, d), generator=g, dtype=torch.float64)
+    U = (U / U.norm(dim=1, keepdim=True)).cuda()
+    ms_rq = timed(lambda: sb.ray_loglik_quad(pb, U, 64, form=1))
     small, _ = workload_cfg(1, "fp64")
     ps = sb.Problem(small)
     x = torch.as_tensor(small.mu[0] + 0.1, device="cuda")
@@ -500,6 +505,8 @@ def run_next_rows(sb, args):
                       "segments": {"workload": f"d={d} K={K}, W2W, {n_rays} rays x {n_steps} + {n_ref} samples",
                                    "ms": ms_seg,
                                    "fp64_TFLOPs": 2 * n_rays * K * d * (d + 1) / (ms_seg * 1e-3) / 1e12},
+                      "ray_loglik_quad_f32": {"workload": f"d={d} K={K}, 16384 rays x 64 steps", "ms": ms_rq,
+                                              "fp32_TFLOPs": 16384 * K * d * (d + 1) / (ms_rq * 1e-3) / 1e12},
                       "fd_full_hessian": {"workload": f"d={ds} K={Ks}, {pts} points", "ms": ms_fd,
                                           "l_evals_per_s": pts / (ms_fd * 1e-3)}}))
     return 0
