@@ -11,7 +11,7 @@
 //   FP64: the batched z GEMM over the rows c and c + u_r (w = z(c + u) - z(c));
 //   FP32: a SIMT triangular GEMM of u_r (rounded to FP32) by L_k (rounded to
 //         FP32) with FP32 accumulation, whose epilogue reduces z_k(c) . w and
-//         |w|^2 over each 64-column tile (the partials are summed in FP64).
+//         |w|^2 over each 128-column tile (the partials are summed in FP64).
 // The terms are large and cancel near a mode (|z(c)|^2 ~ 1e5 at d = 1024), so
 // the FP32 form's error is ~1e-7 of them: sub-nat at such samples.
 #include "sb_raysq.cuh"
@@ -20,7 +20,7 @@ namespace sb {
 
 namespace {
 
-constexpr int QB_M = 64, QB_N = 64, QB_K = 16;
+constexpr int QB_M = 128, QB_N = 128, QB_K = 8;
 
 // t_exit of each ray from the centre (warp per ray): min_i half_i / |u_i|
 __global__ void __launch_bounds__(256) k_rq_texit(int n_rays, int d, const double *u, const double *half,
@@ -78,22 +78,27 @@ __global__ void __launch_bounds__(256) k_rq_to_f32(int64_t n, const double *a, f
         b[e] = (float)a[e];
 }
 
-// FP32 form: per (64 rays, 64 columns j, component k) tile, w[r][j] = sum_{i >= j} L_k[i][j] u_r[i],
-// then partials of z_k(c) . w and |w|^2 over the tile's columns.
+// FP32 form: per (128 rays, 128 columns j, component k) tile, w[r][j] = sum_{i >= j} L_k[i][j] u_r[i]
+// (8 x 8 outputs per thread, rows ty + 16 a, columns tx + 16 b), then partials of z_k(c) . w and
+// |w|^2 over the tile's columns.
 __global__ void __launch_bounds__(256) k_rq_gemm_f32(int n_rays, int d, int K, const float *Uf, const float *Lf,
                                                      const double *zc, float *p1, float *p2) {
     const int r0 = blockIdx.x * QB_M;
     const int jt = blockIdx.y, j0 = jt * QB_N, k = blockIdx.z;
     const int nJT = (d + QB_N - 1) / QB_N;
-    __shared__ float As[QB_K][QB_M + 1];
+    __shared__ float As[QB_K][QB_M + 4];
     __shared__ float Bs[QB_K][QB_N];
     __shared__ float Zc[QB_N];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const float *Lk = Lf + (size_t)k * d * d;
     if (tid < QB_N) Zc[tid] = j0 + tid < d ? (float)zc[(size_t)k * d + j0 + tid] : 0.0f;
-    float acc[4][4] = {};
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
     for (int i0 = (j0 / QB_K) * QB_K; i0 < d; i0 += QB_K) {
-        // A: 64 rays x 16 i (u), B: 16 i x 64 j (L_k rows i, columns j; zero above the diagonal)
+        // A: 128 rays x 8 i (u), B: 8 i x 128 j (L_k rows i, columns j; zero above the diagonal)
         for (int e = tid; e < QB_M * QB_K; e += 256) {
             const int rr = e / QB_K, ii = e - rr * QB_K;
             const int r = r0 + rr, i = i0 + ii;
@@ -107,24 +112,24 @@ __global__ void __launch_bounds__(256) k_rq_gemm_f32(int n_rays, int d, int K, c
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < QB_K; ++kk) {
-            float av[4], bv[4];
+            float av[8], bv[8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) av[q] = As[kk][ty + 16 * q];
+            for (int q = 0; q < 8; ++q) av[q] = As[kk][ty + 16 * q];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) bv[q] = Bs[kk][tx + 16 * q];
+            for (int q = 0; q < 8; ++q) bv[q] = Bs[kk][tx + 16 * q];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 8; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+                for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < 8; ++a) {
         const int r = r0 + ty + 16 * a;
         float s1 = 0.0f, s2 = 0.0f;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < 8; ++b) {
             const int jj = tx + 16 * b;
             s1 = fmaf(Zc[jj], acc[a][b], s1);
             s2 = fmaf(acc[a][b], acc[a][b], s2);
