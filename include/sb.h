@@ -264,7 +264,7 @@ typedef struct sb_chisao_config {
     int32_t anti_steps;      /* momentum descent steps per anti-convergence phase (10)      */
     int32_t min_unconverged; /* Repulse Monkey needs this many unconverged samples, >= 1 (5)*/
     double momentum;         /* mu of the momentum step (0.9)                               */
-    double anti_alpha;       /* step size alpha of the momentum step (0.01)                 */
+    double anti_alpha;       /* step size alpha of the momentum step (0.1)                  */
 } sb_chisao_config;
 
 /* Bytes of device scratch sb_chisao needs (the solve stages' scratch plus its own). */

@@ -236,7 +236,7 @@ class ChisaoConfig:
     anti_steps: int = 10
     min_unconverged: int = 5
     momentum: float = 0.9
-    anti_alpha: float = 0.01
+    anti_alpha: float = 0.1
     conv_from_status: bool = False
 
 

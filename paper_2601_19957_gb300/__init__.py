@@ -254,7 +254,7 @@ class _ChisaoConfig(C.Structure):
 
 
 def make_chisao_config(n_osc=3, conv_iters=1000, anti_steps=10, min_unconverged=5, momentum=0.9,
-                       anti_alpha=0.01) -> _ChisaoConfig:
+                       anti_alpha=0.1) -> _ChisaoConfig:
     return _ChisaoConfig(int(n_osc), int(conv_iters), int(anti_steps), int(min_unconverged), float(momentum),
                          float(anti_alpha))
 

@@ -33,6 +33,7 @@ def _build():
 
 
 def _run(inst, cfg, x0, **cc):
+    cc.setdefault("anti_alpha", 0.01)  # the step size these cases were first validated with
     prob = sb.Problem(inst)
     out = sb.chisao(prob, sb.make_config(cfg), sb.make_chisao_config(**cc), torch.as_tensor(x0, device="cuda"))
     ref = oracle.chisao(inst, cfg, oracle.ChisaoConfig(**cc), x0)

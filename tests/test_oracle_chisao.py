@@ -215,7 +215,8 @@ def test_many_unconverged_samples_reseed_by_repulse_monkey():
     inst = make_instance(3, 3, 71, s_range=(0.3, 1.0), mean_box=(-5, 5), sep=4.0)
     cfg = SolveConfig(n_steps=32, seed=1)
     x0 = np.random.default_rng(4).uniform(-9, 9, (48, 3))
-    res = oracle.chisao(inst, cfg, oracle.ChisaoConfig(n_osc=3, conv_iters=4), x0)
+    # four iterations per phase leave most samples unconverged; a small step keeps some near peaks
+    res = oracle.chisao(inst, cfg, oracle.ChisaoConfig(n_osc=3, conv_iters=4, anti_alpha=0.01), x0)
     assert np.all(np.isfinite(res.x)) and np.all(res.x >= inst.lo) and np.all(res.x <= inst.hi)
     assert 0 < res.n_peaks == res.stuck.sum()
     wmax = float((inst.hi - inst.lo).max())
@@ -268,3 +269,19 @@ def test_laplace_on_all_final_samples_recovers_every_component(d, seed, plain_at
     assert comp(lap.modes) == list(range(6))
     logV = float(np.log(inst.hi - inst.lo).sum())
     assert lap.logZ == pytest.approx(float(np.log(np.exp(inst.log_w).sum())) - logV, abs=1e-9)
+
+
+def test_step_size_of_the_anti_convergence_matters_for_recovery():
+    """Eight components at d = 128 (shaped like the d = 1024 workload): with the Laplace stage
+    over every final sample, a momentum step of 0.1 recovers all eight where 0.01 leaves
+    samples in too few basins (seeded regression of reading 26's default)."""
+    d = 128
+    inst = make_instance(d, 8, 4000 + d, s_range=(0.05, 0.5), mean_box=(-6, 6), sep=10.0)
+    cfg = SolveConfig(n_rays=256, n_steps=64, n_starts=256, m=20, seed=0)
+    starts, _ = oracle.discover(inst, cfg, n_threads=4)
+    found = {}
+    for alpha in (0.01, 0.1):
+        cs = oracle.chisao(inst, cfg, oracle.ChisaoConfig(n_osc=3, anti_alpha=alpha), starts, n_threads=4)
+        lap = oracle.laplace(inst, cfg, cs.x, cs.ell)
+        found[alpha] = {int(np.argmin(np.abs(inst.mu - m).max(1))) for m in lap.modes}
+    assert found[0.1] == set(range(8)) and len(found[0.01]) < 8
