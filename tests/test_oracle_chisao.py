@@ -285,3 +285,17 @@ def test_step_size_of_the_anti_convergence_matters_for_recovery():
         lap = oracle.laplace(inst, cfg, cs.x, cs.ell)
         found[alpha] = {int(np.argmin(np.abs(inst.mu - m).max(1))) for m in lap.modes}
     assert found[0.1] == set(range(8)) and len(found[0.01]) < 8
+
+
+def test_nonfinite_start_is_left_alone():
+    """A NaN start ends NONFINITE: it never sticks, is neither reseeded nor anti-converged,
+    and the other samples find the same peaks as without it."""
+    inst = _isotropic_1d_pair()
+    cfg = SolveConfig(n_steps=64, seed=3)
+    x0 = -5 + np.random.default_rng(0).uniform(-2, 2, (16, 1))
+    ref = oracle.chisao(inst, cfg, oracle.ChisaoConfig(), x0)
+    x1 = np.concatenate([x0, [[np.nan]]])
+    res = oracle.chisao(inst, cfg, oracle.ChisaoConfig(), x1)
+    assert np.isnan(res.x[-1, 0]) and not res.stuck[-1]
+    assert res.n_peaks == ref.n_peaks == 2
+    np.testing.assert_allclose(np.sort(res.x[:-1][res.stuck[:-1]][:, 0]), np.sort(ref.x[ref.stuck][:, 0]), atol=1e-7)
