@@ -57,6 +57,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-chisao", action="store_true",
+                    help="headline step without ChiSao (sunburst-only discovery, refinement, Laplace)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparator")
+    ap.add_argument("--fp64-scale", type=float, default=1.0 / 32,
+                    help="ray and start counts of the FP64 comparator solve, as a fraction of the workload's")
     # profiling cases (small, for ncu captures; not bench lines)
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the tensor-core l+grad contraction on --n-points points")
@@ -75,9 +80,14 @@ def workload_cfg(wid, prec, scale=None):
     return insts[0], cfg
 
 
-def workload_name(wid, inst, cfg):
-    return (f"seeded synthetic Gaussian mixture d={inst.d} K={inst.K}, uniform prior [-10,10]^d, "
+def workload_name(wid, inst, cfg, chisao=None):
+    name = (f"seeded synthetic Gaussian mixture d={inst.d} K={inst.K}, uniform prior [-10,10]^d, "
             f"{cfg.n_rays} sunburst rays x {cfg.n_steps} steps, {cfg.n_starts} L-BFGS starts, m={cfg.m}")
+    if chisao is True:
+        name += ", ChiSao 3 oscillations (anti-convergence step 0.1), Laplace stage over every final sample"
+    elif chisao is False:
+        name += ", sunburst-only discovery"
+    return name
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -213,7 +223,9 @@ def main():
     c = sb.make_config(cfg)
     if args.kernel_only:
         return kernel_only(sb, inst, prob, cfg, args)
-    wsp = sb.workspace(prob, c)
+    use_chisao = not args.no_chisao
+    cc = sb.make_chisao_config()
+    wsp = sb.chisao_workspace(prob, c) if use_chisao else sb.workspace(prob, c)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 512 MB > L2
     L = sb.lib()
@@ -221,26 +233,34 @@ def main():
     closed = float(np.log(np.exp(inst.log_w).sum())) - logV
 
     def one_step():
-        out = sb.evidence(prob, c, ws=wsp, sync_check=False)
-        return out
+        if use_chisao:
+            return sb.evidence_chisao(prob, c, cc, ws=wsp)
+        return sb.evidence(prob, c, ws=wsp, sync_check=False)
+
+    def counts():
+        """(l-only evaluations, l+grad evaluations, modes kept) of the last step."""
+        if use_chisao:
+            ray, lb, anti, nm = sb.chisao_stats(prob, c, wsp)
+            return ray, lb + anti, nm
+        st = (sb.C.c_int64 * 4)()
+        L.sb_evidence_stats(sb.C.byref(prob.s), sb.C.byref(c), wsp.ptr, sb.C.c_size_t(wsp.nbytes), st, sb._stream())
+        return int(st[0]), int(st[1]), int(st[3])
 
     for _ in range(args.warmup):
         out = one_step()
-    st = (sb.C.c_int64 * 4)()
-    L.sb_evidence_stats(sb.C.byref(prob.s), sb.C.byref(c), wsp.ptr, sb.C.c_size_t(wsp.nbytes), st,
-                        sb._stream())
-    evals_per_step = int(st[0]) + int(st[1])
-    n_cand, n_modes = int(st[2]), int(st[3])
 
+    # timed region: CUDA events around the steps on the launching stream, and around the
+    # launches of the dominant kernel class only (the L-BFGS step) for its roofline
     clk = ClockSampler(local)
     clk.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    L.sb_profile_enable(1)
+    L.sb_profile_read(None, None)
+    L.sb_profile_bytes(3)
+    L.sb_profile_classes(1 << 3)
     launches0 = L.sb_launch_count()
-    times = []
-    ev_total = 0
+    times, n_l, n_lg = [], 0, 0
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -250,67 +270,69 @@ def main():
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
-        L.sb_evidence_stats(sb.C.byref(prob.s), sb.C.byref(c), wsp.ptr, sb.C.c_size_t(wsp.nbytes), st, sb._stream())
-        ev_total += int(st[0]) + int(st[1])
+        a1, a2, _ = counts()
+        n_l += a1
+        n_lg += a2
     torch.cuda.synchronize()
     launches = L.sb_launch_count() - launches0
-    L.sb_profile_enable(0)
-    prof_ms = (sb.C.c_double * 8)()
-    prof_n = (sb.C.c_int64 * 8)()
-    L.sb_profile_read(prof_ms, prof_n)
+    L.sb_profile_classes(0)
+    lb_ms_c = (sb.C.c_double * 8)()
+    lb_n_c = (sb.C.c_int64 * 8)()
+    L.sb_profile_read(lb_ms_c, lb_n_c)
     lb_bytes = L.sb_profile_bytes(3)  # algorithmic bytes of the L-BFGS step launches in the timed steps
     clocks = clk.stop()
     t_total = sum(times) / 1e3
     if dist:
-        t_total, ev_total = reduce_over_ranks(t_total, ev_total, dist, "cuda")
-    value = ev_total / t_total
+        t_total, n_lg = reduce_over_ranks(t_total, n_lg, dist, "cuda")
+    value = n_lg / t_total
     ms_per_step = 1e3 * t_total / args.steps
+    l_per_step, lg_per_step, n_modes = counts()
+
+    # per-class device time from a separate pass (events around every launch), untimed
+    L.sb_profile_enable(1)
+    prof_steps = 2
+    for _ in range(prof_steps):
+        one_step()
+    torch.cuda.synchronize()
+    L.sb_profile_enable(0)
+    prof_ms = (sb.C.c_double * 8)()
+    prof_n = (sb.C.c_int64 * 8)()
+    L.sb_profile_read(prof_ms, prof_n)
+    L.sb_profile_bytes(3)
+
     dlogZ = abs(out.logZ - closed)
-    # accuracy given the discovered mode set: each mode is matched to its component
     modes = out.modes.cpu().numpy()
     found = sorted({int(np.argmin(np.abs(inst.mu - m).max(1))) for m in modes})
     closed_found = float(np.log(np.exp(inst.log_w[found]).sum())) - logV if found else -math.inf
     dlogZ_found = abs(out.logZ - closed_found) if found else None
+    accuracy_met = len(found) == inst.K and dlogZ <= 1e-9
 
-    # roofline of the dominant kernel class, measured live in the timed region
     d, K = inst.d, inst.K
-    flop_per_eval = K * d * (d + 1)  # one triangular contraction L_k^T (x - mu_k) over all k
     names = ["tc_z_walkers", "tc_z_rays", "tc_grad", "lbfgs_step", "f64_z", "f64_grad", "cholesky", "other"]
-    share = {names[i]: {"ms": prof_ms[i], "launches": int(prof_n[i])} for i in range(8)}
+    share = {names[i]: {"ms_per_step": prof_ms[i] / prof_steps, "launches_per_step": int(prof_n[i]) // prof_steps}
+             for i in range(8) if prof_n[i]}
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             peaks = json.load(fh)
     except Exception:
         pass
-    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "of measured" if peaks else "of fallback"
-    refine_evals = ev_total - args.steps * int(st[0])
-    ray_evals = args.steps * int(st[0])
-    gemm_ms = prof_ms[0] + prof_ms[1] + prof_ms[2]
-    gemm_flop = (refine_evals * 2 + ray_evals) * flop_per_eval
-    lb_ms = prof_ms[3]
+    lb_ms, lb_n = lb_ms_c[3], max(int(lb_n_c[3]), 1)
     if cfg.prec == 0:
-        peak = 1.25e3  # GFLOP/s-scale FP64 (2 FMA/clk/SM x 152 SMs x 2.07 GHz x 2)
-        gemm_tf = gemm_flop / max(prof_ms[4] + prof_ms[5], 1e-9) / 1e9
-        roof = {"bound": "alu", "achieved": gemm_tf, "peak": peak, "unit": "GFLOP/s", "frac": gemm_tf / peak,
-                "traffic": None, "kernel": "f64_z+f64_grad", "peak_source": "FP64 units x clock (nominal)"}
-    elif gemm_ms >= lb_ms:
-        achieved = gemm_flop / (gemm_ms / 1e3) / 1e12
-        tflops_peak = bf16_peak if cfg.prec == 2 else bf16_peak / 2.0
-        roof = {"bound": "tensor", "achieved": achieved, "peak": tflops_peak, "unit": "TFLOP/s",
-                "frac": achieved / tflops_peak, "traffic": None, "kernel": "k_tc_gemm (z + grad)",
-                "peak_source": peak_src + (" bf16 burst" if cfg.prec == 2 else " bf16 burst / 2 (tf32 nominal ratio)")}
+        roof = fp64_roofline(sb, prof_ms, prof_n, prof_steps, lg_per_step, d, K)
     else:
+        per_launch = lb_bytes / lb_n
         achieved = lb_bytes / (lb_ms / 1e3) / 1e9
-        per_launch = lb_bytes / max(int(prof_n[3]), 1)
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "traffic": per_launch * LBFGS_DRAM_PER_ALGORITHMIC_BYTE if cfg.prec == 2 else None,
-                "traffic_source": "DRAM bytes of all 72 step launches of one 8192-walker solve (ncu), as a "
-                                  "fraction of their algorithmic bytes, times this run's algorithmic bytes",
-                "kernel": "k_lbfgs_cta (FP32 L-BFGS step, bf16 pairs)", "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": per_launch, "ms_per_launch": lb_ms / max(int(prof_n[3]), 1)}
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_lbfgs_cta launches, as a "
+                                  "fraction of their algorithmic bytes, times this run's algorithmic bytes per launch",
+                "kernel": "k_lbfgs_cta (FP32 L-BFGS step, bf16 pairs)", "peak_source": peak_src + " HBM copy",
+                "algorithmic_bytes_per_launch": per_launch, "ms_per_launch": lb_ms / lb_n,
+                "launches_timed": int(lb_n_c[3]),
+                "timing": "CUDA events around every k_lbfgs_cta launch inside the timed steps"}
 
     res = {
         "metric": METRIC,
@@ -325,35 +347,53 @@ def main():
         "vs_baseline": None,
         "dtype": {0: "f64", 1: "tf32", 2: "bf16"}[cfg.prec],
         "data": "synthetic",
-        "config": {"workload": workload_name(args.workload, inst, cfg), "d": d, "K": K, "n_rays": cfg.n_rays,
-                   "n_steps": cfg.n_steps, "n_starts": cfg.n_starts, "m": cfg.m, "prec": args.prec,
-                   "laplace": "fp64", "parallelism": f"replicas x{ws}",
+        "config": {"workload": workload_name(args.workload, inst, cfg, use_chisao),
+                   "d": d, "K": K, "n_rays": cfg.n_rays, "n_steps": cfg.n_steps, "n_starts": cfg.n_starts,
+                   "m": cfg.m, "prec": args.prec, "laplace": "fp64", "chisao": use_chisao,
+                   "parallelism": f"replicas x{ws}",
                    "l2": "512 MB buffer zeroed between timed steps; per-step working set > L2",
-                   "evals_counted": "ray-sample l evaluations + L-BFGS l+grad evaluations per solve"},
+                   "evals_counted": "value: l+grad evaluations (L-BFGS walkers and anti-convergence steps); "
+                                    "l-only evaluations at ray samples are reported apart"},
         "solves_per_sec": ws * args.steps / t_total,
-        "evals_per_step": evals_per_step,
-        "n_candidates": n_cand,
+        "lgrad_evals_per_step": lg_per_step,
+        "l_only_evals_per_step": l_per_step,
+        "l_only_evals_per_sec": ws * args.steps * l_per_step / t_total,
         "n_modes": n_modes,
         "logZ": out.logZ,
+        "logZ_closed_form": closed,
         "abs_dlogZ_vs_closed_form": dlogZ,
         "abs_dlogZ_given_found_modes": dlogZ_found,
         "components_found": f"{len(found)}/{inst.K}",
+        "accuracy_met": accuracy_met,
+        "accuracy_target": "every component found and |dlogZ| vs closed form <= 1e-9",
         "gpu_launches": int(launches),
         "clocks": clocks,
         "roofline": roof,
         "kernel_ms": share,
+        "kernel_ms_source": f"separate profiled pass of {prof_steps} steps (CUDA events around every launch)",
         "step_ms": [round(t, 3) for t in times],
     }
     if rank == 0 and not args.no_e2e:
-        res["e2e"] = e2e_measure(sb, inst, cfg, c, args, evals_per_step)
+        res["e2e"] = e2e_measure(sb, inst, cfg, c, cc if use_chisao else None, args, lg_per_step, flush)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(inst, cfg, args.cpu_seconds)
+    if rank == 0 and not args.no_fp64:
+        res["fp64_gpu"] = fp64_comparator(sb, args, use_chisao)
+        res["fp64_peak"] = fp64_peak(sb)
     if rank == 0:
-        res["fp64_gpu"] = fp64_comparator(sb, inst, prob)
         print(json.dumps(res))
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def fp64_roofline(sb, prof_ms, prof_n, prof_steps, lg_per_step, d, K):
+    """FP64 path: its z and gradient contractions against the measured FP64 FMA peak."""
+    peak = fp64_peak(sb)["tflops"] * 1e3
+    ms = (prof_ms[4] + prof_ms[5]) / prof_steps
+    gflops = lg_per_step * 2 * K * d * (d + 1) / (ms / 1e3) / 1e9
+    return {"bound": "alu", "achieved": gflops, "peak": peak, "unit": "GFLOP/s", "frac": gflops / peak,
+            "traffic": None, "kernel": "f64_z + f64_grad", "peak_source": "of measured FP64 FMA loop (fp64_peak)"}
 
 
 def run_adjoint(sb, args):
@@ -599,60 +639,85 @@ def kernel_only(sb, inst, prob, cfg, args):
     return 0
 
 
-def e2e_measure(sb, inst, cfg, c, args, evals_per_step):
-    """Same metric through sb_evidence_host: host arrays in, log Z and modes out."""
+def e2e_measure(sb, inst, cfg, c, cc, args, lg_per_step, flush):
+    """The same metric through the host-buffer entry point (sb_evidence_chisao_host, or
+    sb_evidence_host without ChiSao): page-locked host arrays in, log Z and the modes out,
+    every copy inside the timed call; the L2 flush runs before each call, outside it."""
     import torch
 
-    wsh = sb.evidence_host_workspace(inst, c)
-    host = sb.PinnedHost(inst, c)  # page-locked inputs and outputs
-    sb.evidence_host(inst, c, wsh, host=host)  # warm
-    t0 = time.perf_counter()
-    n = max(1, min(args.steps, 3))
-    for _ in range(n):
-        logZ, modes, zk, nm = sb.evidence_host(inst, c, wsh, host=host)
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / n
+    host = sb.PinnedHost(inst, c)
+    if cc is not None:
+        wsh = sb.evidence_chisao_host_workspace(inst, c)
+        call = lambda: sb.evidence_chisao_host(inst, c, cc, wsh, host=host)
+    else:
+        wsh = sb.evidence_host_workspace(inst, c)
+        call = lambda: sb.evidence_host(inst, c, wsh, host=host)
+    call()  # warm
+    times = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        logZ, modes, zk, nm = call()  # synchronises: its outputs are on the host when it returns
+        times.append(time.perf_counter() - t0)
+    dt = sum(times) / len(times)
     h2d = 8 * (inst.K + inst.K * inst.d + inst.K * inst.d * inst.d + 2 * inst.d)
     d2h = 8 + 4 + 8 * min(nm, cfg.cand_cap) * (inst.d + 1)
-    return {"value": evals_per_step / dt, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": dt * 1e3, "host_memory": "pinned", "l2": "not flushed between calls"}
+    return {"value": lg_per_step / dt, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": dt * 1e3, "steps": len(times), "host_memory": "pinned",
+            "entry_point": "sb_evidence_chisao_host" if cc is not None else "sb_evidence_host",
+            "l2": "512 MB buffer zeroed before each call (outside the timed call)", "logZ": logZ}
 
 
-def fp64_comparator(sb, inst, prob):
-    """Plain FP64 GPU path: l+grad evals/s of the FP64 CUDA-core kernels on a batch."""
+def fp64_comparator(sb, args, use_chisao):
+    """Plain FP64 GPU path (every stage FP64 on CUDA cores) on the same instance, with the
+    ray and start counts scaled by --fp64-scale (an FP64 solve at full counts takes minutes),
+    next to the mixed-precision path at the same counts."""
     import torch
 
-    rng = np.random.default_rng(11)
-    n = 2048
-    X = torch.as_tensor(inst.mu[rng.integers(0, inst.K, n)] + rng.normal(0, 0.3, (n, inst.d)), device="cuda")
-    wsl = sb.Workspace(sb.lib().sb_loglik_workspace_bytes(sb.C.byref(prob.s), 0, n))
-    sb.loglik(prob, X, prec=0, ws=wsl)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    reps = 2
-    for _ in range(reps):
-        sb.loglik(prob, X, prec=0, ws=wsl)
-    e1.record()
-    e1.synchronize()
-    dt = e0.elapsed_time(e1) / 1e3 / reps
-    flop = n * 2 * inst.K * inst.d * (inst.d + 1)
-    out = {"evals_per_sec": n / dt, "gflops": flop / dt / 1e9, "batch": n}
-    # the tensor-core kernels on the same batch
-    for name, p in (("bf16", 2), ("tf32", 1)):
-        wst = sb.Workspace(sb.lib().sb_loglik_workspace_bytes(sb.C.byref(prob.s), p, n))
-        sb.loglik(prob, X, prec=p, ws=wst)
+    out = {"scale": args.fp64_scale}
+    for name in ("fp64", args.prec):
+        inst, cfg = workload_cfg(args.workload, name, args.fp64_scale)
+        prob = sb.Problem(inst)
+        c = sb.make_config(cfg)
+        cc = sb.make_chisao_config()
+        ws = sb.chisao_workspace(prob, c) if use_chisao else sb.workspace(prob, c)
+        solve = (lambda: sb.evidence_chisao(prob, c, cc, ws=ws)) if use_chisao else (lambda: sb.evidence(prob, c, ws=ws))
+        if name != "fp64":
+            solve()  # warm (the FP64 leg's warm-up is its own first launch set; one solve is long)
         torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(5):
-            sb.loglik(prob, X, prec=p, ws=wst)
+        r = solve()
         e1.record()
         e1.synchronize()
-        dtp = e0.elapsed_time(e1) / 1e3 / 5
-        out[f"{name}_evals_per_sec"] = n / dtp
-        out[f"{name}_speedup_vs_fp64"] = dt / dtp
+        ms = e0.elapsed_time(e1)
+        if use_chisao:
+            ray, lb, anti, _ = sb.chisao_stats(prob, c, ws)
+            lg = lb + anti
+        else:
+            st = (sb.C.c_int64 * 4)()
+            sb.lib().sb_evidence_stats(sb.C.byref(prob.s), sb.C.byref(c), ws.ptr, sb.C.c_size_t(ws.nbytes), st,
+                                       sb._stream())
+            ray, lg = int(st[0]), int(st[1])
+        logV = float(np.log(inst.hi - inst.lo).sum())
+        closed = float(np.log(np.exp(inst.log_w).sum())) - logV
+        found = sorted({int(np.argmin(np.abs(inst.mu - m).max(1))) for m in r.modes.cpu().numpy()})
+        out[name] = {"ms_per_solve": ms, "solves_per_sec": 1e3 / ms, "lgrad_evals_per_sec": lg / (ms / 1e3),
+                     "lgrad_evals": lg, "l_only_evals": ray, "n_starts": cfg.n_starts,
+                     "components_found": f"{len(found)}/{inst.K}", "abs_dlogZ_vs_closed_form": abs(r.logZ - closed)}
+    out["speedup_" + args.prec + "_vs_fp64_solves"] = out["fp64"]["ms_per_solve"] / out[args.prec]["ms_per_solve"]
     return out
+
+
+def fp64_peak(sb):
+    """FP64 FMA throughput of this GPU, measured by the library's own FMA loop kernel."""
+    if not hasattr(fp64_peak, "cache"):
+        tf = float(sb.lib().sb_fp64_fma_peak(None))
+        fp64_peak.cache = {"tflops": tf, "source": "sb_fp64_fma_peak: independent FMA chains on every SM, "
+                                                   "CUDA-event timed, best of 5"}
+    return fp64_peak.cache
 
 
 def run_reference(args, ws, rank):
@@ -672,7 +737,8 @@ def run_reference(args, ws, rank):
     res = {"metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": workload_name(args.workload, inst, cfg), "d": inst.d, "K": inst.K},
+           "config": {"workload": workload_name(args.workload, inst, cfg, not args.no_chisao), "d": inst.d,
+                      "K": inst.K},
            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": vals[0]["cores"], "kind": "oracle",
                             "sample": vals[0]["sample"]},
            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -246,6 +246,10 @@ int64_t sb_launch_count(void);
  * 7 other), clears the record and returns the number of unreadable events. */
 void sb_profile_enable(int on);
 int32_t sb_profile_read(double *ms, int64_t *launches);
+/* Profiling of some classes only: bit c of `mask` times the launches of class c
+ * (sb_profile_enable(1) is mask 0xFF, sb_profile_enable(0) mask 0). Timing one
+ * class keeps the events off every other launch. */
+void sb_profile_classes(uint32_t mask);
 
 /* Algorithmic bytes moved by the launches of profiling class `cls` while
  * profiling was enabled, then clears that count. Only class 3 (the FP32 L-BFGS
@@ -256,6 +260,12 @@ int32_t sb_profile_read(double *ms, int64_t *launches);
  * update of Nocedal & Wright, Alg. 7.4). Other classes return 0. Synchronises
  * the device; returns -1 on a CUDA error. */
 double sb_profile_bytes(int32_t cls);
+
+/* FP64 FMA throughput of the current device in TFLOP/s, the peak the FP64 kernels are
+ * measured against: independent FMA chains on every SM, timed with CUDA events on
+ * `stream`, best of five launches after a warm-up (diagnostics; synchronises the
+ * stream; -1 on a CUDA error). */
+double sb_fp64_fma_peak(void *stream);
 
 /* Knobs of the ChiSao oscillation (Sec. 3.5.5, Algorithm 1). */
 typedef struct sb_chisao_config {
@@ -374,6 +384,25 @@ sb_status sb_segments(const sb_problem *prob, int32_t family, uint64_t seed, int
 sb_status sb_evidence_chisao(const sb_problem *prob, const sb_config *cfg, const sb_chisao_config *cc, double *logZ,
                              double *modes, double *logZk, int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes,
                              void *stream);
+
+/* sb_evidence_chisao with HOST inputs and outputs, as sb_evidence_host: copies the
+ * problem arrays (host pointers in `host_prob`) into `ws`, runs discovery, ChiSao and
+ * the Laplace stage over every final sample, and copies log Z, the mode count, the
+ * modes and their log Z_k back (host pointers; modes / logZk may be NULL). ws must hold
+ * sb_evidence_chisao_host_workspace_bytes. Synchronises `stream`. */
+size_t sb_evidence_chisao_host_workspace_bytes(const sb_problem *host_prob, const sb_config *cfg);
+sb_status sb_evidence_chisao_host(const sb_problem *host_prob, const sb_config *cfg, const sb_chisao_config *cc,
+                                  double *logZ, double *modes, double *logZk, int32_t cap, int32_t *n_modes,
+                                  void *ws, size_t ws_bytes, void *stream);
+
+/* Counters of the last sb_chisao / sb_evidence_chisao call on this workspace
+ * (synchronises `stream`): out[0] l evaluations at ray samples (discovery, when run
+ * through sb_evidence_chisao, and the reseeding rays), out[1] l + grad evaluations
+ * of the L-BFGS convergence phases, out[2] l + grad evaluations of the
+ * anti-convergence steps, out[3] modes kept by the Laplace stage of
+ * sb_evidence_chisao. out: host int64[4]. */
+sb_status sb_chisao_stats(const sb_problem *prob, const sb_config *cfg, void *ws, size_t ws_bytes, int64_t *out,
+                          void *stream);
 
 /* Bytes of device scratch sb_ray_loglik_quad needs (form 0 FP64, 1 FP32). */
 size_t sb_ray_loglik_quad_workspace_bytes(const sb_problem *prob, int32_t form, int32_t n_rays);

@@ -69,6 +69,10 @@ def lib():
         L.sb_evidence_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         L.sb_chisao_workspace_bytes.restype = C.c_size_t
+        L.sb_evidence_chisao_host_workspace_bytes.restype = C.c_size_t
+        L.sb_profile_classes.argtypes = [C.c_uint32]
+        L.sb_fp64_fma_peak.restype = C.c_double
+        L.sb_fp64_fma_peak.argtypes = [C.c_void_p]
         L.sb_precheck_workspace_bytes.restype = C.c_size_t
         L.sb_segments_workspace_bytes.restype = C.c_size_t
         L.sb_fd_workspace_bytes.restype = C.c_size_t
@@ -85,7 +89,7 @@ def lib():
         L.sb_precheck.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         for name in ("sb_loglik", "sb_loglik_noalloc", "sb_discover", "sb_refine", "sb_laplace", "sb_evidence", "sb_evidence_host",
-                     "sb_check", "sb_chisao", "sb_evidence_chisao"):
+                     "sb_check", "sb_chisao", "sb_evidence_chisao", "sb_evidence_chisao_host", "sb_chisao_stats"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -482,6 +486,45 @@ def evidence_host(inst: Instance, cfg: _Config, ws: Workspace, stream=None, host
     del keep
     k = min(int(nm[0]), cap)
     return float(lz[0]), modes[:k].copy(), zk[:k].copy(), int(nm[0])
+
+
+def evidence_chisao_host_workspace(inst: Instance, cfg: _Config) -> Workspace:
+    s, _keep = host_problem(inst)
+    return Workspace(lib().sb_evidence_chisao_host_workspace_bytes(C.byref(s), C.byref(cfg)))
+
+
+def evidence_chisao_host(inst: Instance, cfg: _Config, cc, ws: Workspace, stream=None, host: PinnedHost = None):
+    """Discovery, ChiSao and the Laplace stage on HOST arrays (copies in, solves, copies
+    log Z and the modes out). With `host` (a PinnedHost of this instance) the arrays are
+    page-locked."""
+    cap = cfg.cand_cap
+    if host is not None:
+        s, keep = host.s, None
+        lz, nm, modes, zk = host.lz.numpy(), host.nm.numpy(), host.modes.numpy(), host.zk.numpy()
+    else:
+        s, keep = host_problem(inst)
+        lz = np.zeros(1)
+        nm = np.zeros(1, dtype=np.int32)
+        modes = np.zeros((cap, inst.d))
+        zk = np.zeros(cap)
+    code = lib().sb_evidence_chisao_host(C.byref(s), C.byref(cfg), C.byref(cc), lz.ctypes.data_as(C.c_void_p),
+                                         modes.ctypes.data_as(C.c_void_p), zk.ctypes.data_as(C.c_void_p),
+                                         C.c_int32(cap), nm.ctypes.data_as(C.c_void_p), ws.ptr,
+                                         C.c_size_t(ws.nbytes), _stream(stream))
+    if code not in (SB_OK, SB_ERR_NO_MODES):
+        raise SbError(code, "sb_evidence_chisao_host")
+    del keep
+    k = min(int(nm[0]), cap)
+    return float(lz[0]), modes[:k].copy(), zk[:k].copy(), int(nm[0])
+
+
+def chisao_stats(prob: Problem, cfg: _Config, ws: Workspace, stream=None):
+    """(ray l evaluations, L-BFGS l+grad evaluations, anti-convergence l+grad evaluations,
+    modes kept) of the last ChiSao solve on this workspace."""
+    out = (C.c_int64 * 4)()
+    _check(lib().sb_chisao_stats(C.byref(prob.s), C.byref(cfg), ws.ptr, C.c_size_t(ws.nbytes), out,
+                                 _stream(stream)), "sb_chisao_stats")
+    return tuple(int(v) for v in out)
 
 
 def evidence_backward(prob, modes, logZk, n_modes: int, grad_logZ: float = 1.0, stream=None):

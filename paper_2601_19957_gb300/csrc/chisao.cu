@@ -329,9 +329,18 @@ __global__ void __launch_bounds__(256) k_cs_momentum(int n, int d, const int32_t
     }
 }
 
+__global__ void k_cs_stat_add(int64_t *dst, const int64_t *src, int64_t v) {
+    if (threadIdx.x == 0) *dst += (src ? *src : 0) + v;
+}
+
 inline unsigned warp_grid(int64_t warps) { return (unsigned)((warps * 32 + 255) / 256); }
 
 }  // namespace
+
+void launch_cs_stat_add(int64_t *dst, const int64_t *src, int64_t v, cudaStream_t s) {
+    note_launch();
+    k_cs_stat_add<<<1, 32, 0, s>>>(dst, src, v);
+}
 
 void launch_cs_conv(int n, int d, const double *G, const double *ell, double eps, uint8_t *conv, cudaStream_t s) {
     if (n <= 0) return;

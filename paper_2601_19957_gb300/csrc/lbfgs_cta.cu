@@ -836,7 +836,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
 
 void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *MYY, int num_sms, cudaStream_t s) {
     ProfScope prof(PROF_LBFGS_STEP, s);
-    const int count_bytes = prof_enabled() ? 1 : 0;
+    const int count_bytes = prof_class_on(PROF_LBFGS_STEP) ? 1 : 0;
     int grid = num_sms * Cfg<kCT>::MINB;
     if (grid > n) grid = n > 0 ? n : 1;
     const size_t dyn = (size_t)Cfg<kCT>::RING_F4 * sizeof(float4) + sizeof(float) * mm_floats<kCT>(a.m);

@@ -25,22 +25,39 @@ using namespace sb;
 
 namespace {
 std::atomic<int64_t> g_launches{0};
-std::atomic<int> g_prof_on{0};
+std::atomic<uint32_t> g_prof_mask{0};  // bit c: time the launches of class c
 std::mutex g_prof_mu;
 struct ProfRec {
     int cls;
     cudaEvent_t a, b;
 };
 std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_ev_pool;  // events of read records, reused (no create per launch)
+
+cudaEvent_t pooled_event() {
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (!g_ev_pool.empty()) {
+            cudaEvent_t e = g_ev_pool.back();
+            g_ev_pool.pop_back();
+            return e;
+        }
+    }
+    cudaEvent_t e = nullptr;
+    return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+}
 }  // namespace
 void sb::note_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 sb::ProfScope::ProfScope(int c, cudaStream_t st) : cls(c), s(st), a(nullptr), b(nullptr) {
-    if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    if (!prof_class_on(c)) return;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
-    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
-        a = b = nullptr;
+    a = pooled_event();
+    b = a ? pooled_event() : nullptr;
+    if (!b) {
+        if (a) cudaEventDestroy(a);
+        a = nullptr;
         return;
     }
     cudaEventRecord(a, s);
@@ -52,9 +69,11 @@ sb::ProfScope::~ProfScope() {
     g_prof.push_back({cls, a, b});
 }
 
-bool sb::prof_enabled() { return g_prof_on.load(std::memory_order_relaxed) != 0; }
+bool sb::prof_enabled() { return g_prof_mask.load(std::memory_order_relaxed) != 0; }
+bool sb::prof_class_on(int cls) { return (g_prof_mask.load(std::memory_order_relaxed) >> cls) & 1u; }
 
-extern "C" void sb_profile_enable(int on) { g_prof_on.store(on ? 1 : 0); }
+extern "C" void sb_profile_enable(int on) { g_prof_mask.store(on ? 0xFFu : 0u); }
+extern "C" void sb_profile_classes(uint32_t mask) { g_prof_mask.store(mask & 0xFFu); }
 
 extern "C" double sb_profile_bytes(int32_t cls) {
     if (cls == PROF_LBFGS_STEP) return lbfgs_bytes_take();
@@ -76,8 +95,8 @@ extern "C" int32_t sb_profile_read(double *ms, int64_t *launches) {
         } else {
             ++bad;
         }
-        cudaEventDestroy(r.a);
-        cudaEventDestroy(r.b);
+        g_ev_pool.push_back(r.a);
+        g_ev_pool.push_back(r.b);
     }
     g_prof.clear();
     return bad;
@@ -682,7 +701,7 @@ extern "C" sb_status sb_check(void *ws, size_t ws_bytes, void *stream) {
     return SB_OK;
 }
 
-// ------------------------------------------------------------------ host-buffer entry point
+// ------------------------------------------------------------------ host-buffer entry points
 namespace {
 struct HostLayout {
     double *log_w, *mu, *L, *lo, *hi, *logZ, *modes, *logZk;
@@ -691,7 +710,9 @@ struct HostLayout {
     size_t inner_bytes, bytes;
 };
 
-HostLayout host_layout(void *base, const sb_problem *p, const sb_config *c, int cap) {
+// Device copies of the problem arrays and of the outputs, then `inner_bytes` of
+// scratch for the solve itself.
+HostLayout host_layout(void *base, const sb_problem *p, int cap, size_t inner_bytes) {
     HostLayout h{};
     Carver cv(base);
     const int d = p->d, K = p->K;
@@ -704,29 +725,21 @@ HostLayout host_layout(void *base, const sb_problem *p, const sb_config *c, int 
     h.n_modes = cv.take<int32_t>(1);
     h.modes = cv.take<double>((size_t)cap * d);
     h.logZk = cv.take<double>(cap);
-    sb_problem tmp = *p;
-    h.inner_bytes = layout(nullptr, &tmp, c).bytes;
+    h.inner_bytes = inner_bytes;
     h.inner = cv.take<char>(h.inner_bytes);
     h.bytes = cv.bytes();
     return h;
 }
-}  // namespace
 
-extern "C" size_t sb_evidence_host_workspace_bytes(const sb_problem *hp, const sb_config *c) {
-    if (check_problem(hp) != SB_OK || check_config(c) != SB_OK) return 0;
-    return host_layout(nullptr, hp, c, c->cand_cap).bytes;
-}
-
-extern "C" sb_status sb_evidence_host(const sb_problem *hp, const sb_config *c, double *logZ, double *modes,
-                                      double *logZk, int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes,
-                                      void *stream) {
-    sb_status st = check_problem(hp);
-    if (st != SB_OK) return st;
-    st = check_config(c);
-    if (st != SB_OK) return st;
+// Copies the host problem in, runs `solve` on device buffers, copies log Z, the mode
+// count, the modes and their log Z_k out, and returns the device status word.
+template <typename Solve>
+sb_status host_solve(const sb_problem *hp, const sb_config *c, size_t inner_bytes, double *logZ, double *modes,
+                     double *logZk, int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes, void *stream,
+                     Solve solve) {
     if (!logZ || !n_modes || !ws || cap < 1) return SB_ERR_INVALID_ARG;
     const int ccap = c->cand_cap;
-    HostLayout h = host_layout(ws, hp, c, ccap);
+    HostLayout h = host_layout(ws, hp, ccap, inner_bytes);
     if (ws_bytes < h.bytes) return SB_ERR_WORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int d = hp->d, K = hp->K;
@@ -736,7 +749,7 @@ extern "C" sb_status sb_evidence_host(const sb_problem *hp, const sb_config *c, 
     SB_CUDA_TRY(cudaMemcpyAsync(h.lo, hp->lo, sizeof(double) * d, cudaMemcpyHostToDevice, s));
     SB_CUDA_TRY(cudaMemcpyAsync(h.hi, hp->hi, sizeof(double) * d, cudaMemcpyHostToDevice, s));
     sb_problem dp{d, K, h.log_w, h.mu, h.L, h.lo, h.hi};
-    st = sb_evidence(&dp, c, h.logZ, h.modes, h.logZk, ccap, h.n_modes, h.inner, h.inner_bytes, stream);
+    sb_status st = solve(&dp, h.logZ, h.modes, h.logZk, ccap, h.n_modes, h.inner, h.inner_bytes, stream);
     if (st != SB_OK) return st;
     SB_CUDA_TRY(cudaMemcpyAsync(logZ, h.logZ, sizeof(double), cudaMemcpyDeviceToHost, s));
     SB_CUDA_TRY(cudaMemcpyAsync(n_modes, h.n_modes, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -748,6 +761,24 @@ extern "C" sb_status sb_evidence_host(const sb_problem *hp, const sb_config *c, 
     if (logZk && nc > 0) SB_CUDA_TRY(cudaMemcpyAsync(logZk, h.logZk, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
     SB_CUDA_TRY(cudaStreamSynchronize(s));
     return sb_check(h.inner, h.inner_bytes, stream);
+}
+}  // namespace
+
+extern "C" size_t sb_evidence_host_workspace_bytes(const sb_problem *hp, const sb_config *c) {
+    if (check_problem(hp) != SB_OK || check_config(c) != SB_OK) return 0;
+    return host_layout(nullptr, hp, c->cand_cap, layout(nullptr, hp, c).bytes).bytes;
+}
+
+extern "C" sb_status sb_evidence_host(const sb_problem *hp, const sb_config *c, double *logZ, double *modes,
+                                      double *logZk, int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes,
+                                      void *stream) {
+    sb_status st = check_problem(hp);
+    if (st != SB_OK) return st;
+    st = check_config(c);
+    if (st != SB_OK) return st;
+    return host_solve(hp, c, layout(nullptr, hp, c).bytes, logZ, modes, logZk, cap, n_modes, ws, ws_bytes, stream,
+                      [c](const sb_problem *dp, double *lz, double *md, double *zk, int32_t cp, int32_t *nm,
+                          void *in, size_t inb, void *str) { return sb_evidence(dp, c, lz, md, zk, cp, nm, in, inb, str); });
 }
 
 // ------------------------------------------------------------------ batched log-likelihood
@@ -1015,6 +1046,7 @@ struct ChisaoWs {
     int32_t *reps, *n_reps, *lost_list, *unconv_list, *moving_list, *cnt;
     int32_t *job_start, *job_pk, *job_b, *job_cols;
     int64_t *job_off;
+    int64_t *stats;  // [4] l-only ray evaluations, L-BFGS l+grad, anti-convergence l+grad, -
     int lc;  // lost samples per chunk of ray samples
     size_t bytes;
 };
@@ -1053,6 +1085,7 @@ ChisaoWs chisao_layout(void *base, size_t off, const sb_problem *p, const sb_con
     w.job_b = cv.take<int32_t>(n);
     w.job_cols = cv.take<int32_t>(n);
     w.job_off = cv.take<int64_t>(n);
+    w.stats = cv.take<int64_t>(4);
     w.bytes = cv.bytes();
     return w;
 }
@@ -1128,6 +1161,7 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
     sb_config c2 = *c;
     c2.max_iter = cc->conv_iters;
     const DedupScratch dds{la.dd_l, la.dd_i, la.dd_bar, pv.status};
+    SB_CUDA_TRY(cudaMemsetAsync(w.stats, 0, sizeof(int64_t) * 4, s));
     SB_CUDA_TRY(cudaMemcpyAsync(w.X, x0, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, s));
     // l and grad l at the samples listed in rows (all n when rows is null)
     auto grad_at = [&](const int32_t *rows, const int32_t *n_rows_dev, int n_rows) {
@@ -1153,6 +1187,7 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
         else
             st = run_refine<double>(pv, &c2, r, w.X, n, w.X, w.ell, w.status, nullptr, nullptr, s);
         if (st != SB_OK) return st;
+        launch_cs_stat_add(w.stats + 1, mixed ? P.L.r32.n_evals : r.n_evals, 0, s);
         // stick test, then the dedup of the stuck samples (representatives stay stuck); the
         // mixed path's gradients are too coarse for the FP64 gradient test, so there the
         // refinement's CONVERGED / STALLED state is the test
@@ -1202,6 +1237,7 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
             gr_used_prev = true;
         }
         if (past_valley >= 0) {
+            launch_cs_stat_add(w.stats + 0, nullptr, (int64_t)n_lost * c->n_steps, s);
             for (int l0 = 0; l0 < n_lost; l0 += w.lc) {
                 const int nl = n_lost - l0 < w.lc ? n_lost - l0 : w.lc;
                 launch_cs_ray_points(l0, nl, c->n_steps, d, w.O, w.U, w.texit, w.P, s);
@@ -1224,6 +1260,7 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
         }
         // anti-convergence of every sample that is not stuck
         if (cc->anti_steps > 0 && n_moving > 0) {
+            launch_cs_stat_add(w.stats + 2, nullptr, (int64_t)(mixed ? n : n_moving) * cc->anti_steps, s);
             SB_CUDA_TRY(cudaMemsetAsync(w.V, 0, sizeof(double) * n * d, s));
             for (int t = 0; t < cc->anti_steps; ++t) {
                 if (mixed) {  // every sample's gradient; the step moves the listed ones only
@@ -1266,11 +1303,54 @@ extern "C" sb_status sb_evidence_chisao(const sb_problem *p, const sb_config *c,
     if (st != SB_OK) return st;
     st = sb_chisao(p, c, cc, L.ev.starts, n, L.ev.x_out, L.ev.ell_out, L.ev.status, n_modes, ws, ws_bytes, stream);
     if (st != SB_OK) return st;
+    const ChisaoWs w = chisao_layout(ws, L.bytes, p, c);
+    launch_cs_stat_add(w.stats + 0, nullptr, (int64_t)c->n_rays * c->n_steps, static_cast<cudaStream_t>(stream));
     // each stage clears the device status word on entry: surface what the first two recorded
     st = sb_check(ws, ws_bytes, stream);
     if (st != SB_OK) return st;
     return sb_laplace(p, c, L.ev.x_out, L.ev.ell_out, nullptr, n, modes, logZk, nullptr, cap, n_modes, logZ, ws,
                       ws_bytes, stream);
+}
+
+extern "C" size_t sb_evidence_chisao_host_workspace_bytes(const sb_problem *hp, const sb_config *c) {
+    const size_t inner = sb_chisao_workspace_bytes(hp, c);
+    if (inner == 0) return 0;
+    return host_layout(nullptr, hp, c->cand_cap, inner).bytes;
+}
+
+extern "C" sb_status sb_evidence_chisao_host(const sb_problem *hp, const sb_config *c, const sb_chisao_config *cc,
+                                             double *logZ, double *modes, double *logZk, int32_t cap,
+                                             int32_t *n_modes, void *ws, size_t ws_bytes, void *stream) {
+    sb_status st = check_problem(hp);
+    if (st != SB_OK) return st;
+    st = check_config(c);
+    if (st != SB_OK) return st;
+    st = check_chisao(cc);
+    if (st != SB_OK) return st;
+    return host_solve(hp, c, sb_chisao_workspace_bytes(hp, c), logZ, modes, logZk, cap, n_modes, ws, ws_bytes, stream,
+                      [c, cc](const sb_problem *dp, double *lz, double *md, double *zk, int32_t cp, int32_t *nm,
+                              void *in, size_t inb, void *str) {
+                          return sb_evidence_chisao(dp, c, cc, lz, md, zk, cp, nm, in, inb, str);
+                      });
+}
+
+extern "C" sb_status sb_chisao_stats(const sb_problem *p, const sb_config *c, void *ws, size_t ws_bytes, int64_t *out,
+                                     void *stream) {
+    sb_status st = check_problem(p);
+    if (st != SB_OK) return st;
+    st = check_config(c);
+    if (st != SB_OK) return st;
+    if (!ws || !out) return SB_ERR_INVALID_ARG;
+    const Layout L = layout(ws, p, c);
+    const ChisaoWs w = chisao_layout(ws, L.bytes, p, c);
+    if (ws_bytes < L.bytes + w.bytes) return SB_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t nm = 0;
+    SB_CUDA_TRY(cudaMemcpyAsync(out, w.stats, sizeof(int64_t) * 3, cudaMemcpyDeviceToHost, s));
+    SB_CUDA_TRY(cudaMemcpyAsync(&nm, L.la.n_reps2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SB_CUDA_TRY(cudaStreamSynchronize(s));
+    out[3] = nm;
+    return SB_OK;
 }
 
 // ------------------------------------------------------------------ setup-only entry points

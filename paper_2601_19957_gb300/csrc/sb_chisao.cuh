@@ -44,5 +44,7 @@ void launch_cs_ray_pick(int l0, int nl, int n_steps, int d, int past_valley, con
 void launch_cs_momentum(int n, int d, const int32_t *moving_list, const int32_t *n_moving, double momentum,
                         double alpha, const double *G, double *V, double *X, const double *lo, const double *hi,
                         cudaStream_t s);
+// *dst += *src (when src is given) + v, on the device (evaluation counters).
+void launch_cs_stat_add(int64_t *dst, const int64_t *src, int64_t v, cudaStream_t s);
 
 }  // namespace sb

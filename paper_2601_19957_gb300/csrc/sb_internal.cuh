@@ -156,7 +156,8 @@ enum ProfClass {
     PROF_OTHER = 7,
     PROF_NCLASS = 8
 };
-bool prof_enabled();
+bool prof_enabled();           // some class is being timed
+bool prof_class_on(int cls);   // launches of class cls are being timed
 struct ProfScope {
     int cls;
     cudaStream_t s;
