@@ -14,7 +14,9 @@
  *    [n][d]; the precision Cholesky factors are [K][d][d] (lower triangle used).
  *  - `ws` is caller-owned device scratch of at least the size the matching
  *    *_workspace_bytes query returns (256-byte aligned base). The library
- *    allocates no device memory of its own.
+ *    allocates no device memory of its own; the one exception is the 32 MiB
+ *    file-scope scratch array of sb_loglik_noalloc, which every GPU that loads
+ *    the library holds until the process exits.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Work is enqueued on it. Entry points that must observe device state
  *    (noted per function) synchronise that stream before returning.
@@ -106,13 +108,22 @@ size_t sb_workspace_bytes(const sb_problem *prob, const sb_config *cfg);
  * ws/ws_bytes: the scratch is a 32 MiB array inside this library, held by
  * every GPU that loads it until the process exits. Requests whose
  * sb_loglik_workspace_bytes exceed 32 MiB return SB_ERR_WORKSPACE before any
- * launch. The first call on a device looks up that device's address of the
- * array (make it before any stream capture). Calls that overlap on the GPU
+ * launch. Every call made outside a stream capture looks up this device's
+ * address of the array (so the first call on a device must come before any
+ * capture; a capture reuses the last address looked up). With SB_PREC_BF16 /
+ * SB_PREC_TF32, the first call per (d, K, prec) in a process also runs the
+ * tensor-core tile autotuner, which synchronises the stream: make that call
+ * outside any capture too, or set SB_TUNE=0. Calls that overlap on the GPU
  * (concurrent streams, or several host threads) share the array and race;
  * serialise them. It allocates nothing: no cudaMalloc, no cudaFree.
  */
 sb_status sb_loglik_noalloc(const sb_problem *prob, int32_t prec, const double *x, int32_t n, double *ell,
                             double *grad, void *stream);
+
+/* The device status word of the last sb_loglik_noalloc call (non-finite parameters,
+ * non-positive Cholesky diagonal), which lives in the library's array: synchronises
+ * `stream`, returns it as sb_check does, and clears it. */
+sb_status sb_loglik_noalloc_check(void *stream);
 
 /* Bytes of scratch sb_loglik needs for n points at precision prec. */
 size_t sb_loglik_workspace_bytes(const sb_problem *prob, int32_t prec, int32_t n);

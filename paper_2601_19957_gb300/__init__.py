@@ -88,7 +88,7 @@ def lib():
         L.sb_precheck.restype = C.c_int
         L.sb_precheck.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
-        for name in ("sb_loglik", "sb_loglik_noalloc", "sb_discover", "sb_refine", "sb_laplace", "sb_evidence", "sb_evidence_host",
+        for name in ("sb_loglik", "sb_loglik_noalloc", "sb_loglik_noalloc_check", "sb_discover", "sb_refine", "sb_laplace", "sb_evidence", "sb_evidence_host",
                      "sb_check", "sb_chisao", "sb_evidence_chisao", "sb_evidence_chisao_host", "sb_chisao_stats"):
             getattr(L, name).restype = C.c_int
         _lib = L

@@ -23,17 +23,23 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device (looked up once per device;
-// host code only ever holds the symbol's host-side stand-in otherwise).
-sb_status scratch_address(void **out) {
+// Device address of g_scratch on the current device. Host code holds only the
+// symbol's host-side stand-in, which is not a device address, so the address is
+// asked of the runtime: on every call made outside a stream capture (so that a
+// context that was reset and reloaded the module is seen), and from the value
+// cached by the last such call while the stream is being captured.
+sb_status scratch_address(cudaStream_t s, void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SB_ERR_CUDA;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return SB_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return SB_ERR_CUDA;
         g_addr[dev] = p;
     }
+    if (!g_addr[dev]) return SB_ERR_INVALID_ARG;  // first call on this device made inside a capture
     *out = g_addr[dev];
     return SB_OK;
 }
@@ -46,8 +52,15 @@ extern "C" sb_status sb_loglik_noalloc(const sb_problem *prob, int32_t prec, con
     if (need == 0) return SB_ERR_INVALID_ARG;
     if (need > kScratchBytes) return SB_ERR_WORKSPACE;
     void *ws = nullptr;
-    const sb_status st = scratch_address(&ws);
+    const sb_status st = scratch_address(static_cast<cudaStream_t>(stream), &ws);
     if (st != SB_OK) return st;
     // sb_loglik clears its status header and overwrites every scratch region it reads.
     return sb_loglik(prob, prec, x, n, ell, grad, ws, kScratchBytes, stream);
+}
+
+extern "C" sb_status sb_loglik_noalloc_check(void *stream) {
+    void *ws = nullptr;
+    const sb_status st = scratch_address(static_cast<cudaStream_t>(stream), &ws);
+    if (st != SB_OK) return st;
+    return sb_check(ws, kScratchBytes, stream);
 }
