@@ -1041,6 +1041,7 @@ namespace {
 
 struct ChisaoWs {
     double *X, *V, *G, *ell, *ellg, *O, *U, *texit, *Q, *P, *ellp, *qp;
+    float *O32, *U32;  // FP32 copies of the reseeding rays (mixed path)
     int8_t *status;
     uint8_t *conv, *stuck, *lost;
     int32_t *reps, *n_reps, *lost_list, *unconv_list, *moving_list, *cnt;
@@ -1086,6 +1087,10 @@ ChisaoWs chisao_layout(void *base, size_t off, const sb_problem *p, const sb_con
     w.job_cols = cv.take<int32_t>(n);
     w.job_off = cv.take<int64_t>(n);
     w.stats = cv.take<int64_t>(4);
+    if (c->prec != SB_PREC_FP64) {
+        w.O32 = cv.take<float>((size_t)n * d);
+        w.U32 = cv.take<float>((size_t)n * d);
+    }
     w.bytes = cv.bytes();
     return w;
 }
@@ -1238,14 +1243,18 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
         }
         if (past_valley >= 0) {
             launch_cs_stat_add(w.stats + 0, nullptr, (int64_t)n_lost * c->n_steps, s);
+            if (mixed) {  // the tensor-core pass forms the ray samples itself, in FP32
+                tc_to_f32(w.O, w.O32, (size_t)n_lost * d, s);
+                tc_to_f32(w.U, w.U32, (size_t)n_lost * d, s);
+            }
             for (int l0 = 0; l0 < n_lost; l0 += w.lc) {
                 const int nl = n_lost - l0 < w.lc ? n_lost - l0 : w.lc;
-                launch_cs_ray_points(l0, nl, c->n_steps, d, w.O, w.U, w.texit, w.P, s);
                 if (mixed) {
-                    st = tc_loglik_points(pv, c, P.L.r32.tc, w.P, nl * c->n_steps, nullptr, nullptr, w.ellp, nullptr,
-                                          s);
+                    st = tc_ray_samples(pv, P.L.r32.tc, w.O32, w.U32, w.texit, c->n_steps, (int64_t)l0 * c->n_steps,
+                                        (int64_t)(l0 + nl) * c->n_steps, w.ellp, s);
                     if (st != SB_OK) return st;
                 } else {
+                    launch_cs_ray_points(l0, nl, c->n_steps, d, w.O, w.U, w.texit, w.P, s);
                     LikF64Args a = f64_args(pv);
                     a.X = w.P;
                     a.n_rows = nl * c->n_steps;

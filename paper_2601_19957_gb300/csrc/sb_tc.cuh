@@ -33,6 +33,14 @@ sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s, bool skip_boun
 // u32 [n_rays][d]; chunks of the scratch row capacity.
 sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const float *u32,
                         const double *texit, double *ell_all, cudaStream_t s);
+// l at the ray samples of flat indices [f_begin, f_end) (ray = flat / n_steps,
+// j = flat % n_steps): x = o_ray + ((j + 1) / n_steps) t_exit,ray u_ray formed in FP32
+// inside the centring pass, o32 [rays][d] the rays' origins (the box centre when
+// null); ell[flat - f_begin]. Chunks of the scratch row capacity.
+sb_status tc_ray_samples(const ProbView &pv, const TcWs &t, const float *o32, const float *u32, const double *texit,
+                         int n_steps, int64_t f_begin, int64_t f_end, double *ell, cudaStream_t s);
+// y[e] = (float) x[e], e < n.
+void tc_to_f32(const double *x, float *y, size_t n, cudaStream_t s);
 // Clears the per-walker bounds of the component skip (before a refinement).
 void tc_walkers_reset(const TcWs &t, int n, cudaStream_t s);
 // Slot of TcWs.p holding the per-walker distance bound the L-BFGS step writes.

@@ -13,13 +13,15 @@
 //                 largest term (a skipped term is below FP32 resolution: exactly 0)
 //   k_tc_center   A1[k][n][:] = round(x_n - mu_k), formed in FP32 (walkers gathered
 //                 through the active list, or ray samples c + t u), bf16 or tf32
-//   k_tc_gemm ZR  z = A1 L_k (GEMM1): |z|^2 partials only
+//   k_tc_gemm ZW  z = A1 L_k (GEMM1) for the kept pairs: |z|^2 partials, and z
+//                 itself stored (bf16 / tf32) as Z[k][n][:] when the gradient is wanted
+//                 (ZR: the |z|^2 partials only, for l alone, e.g. at ray samples)
 //   k_tc_lse      l, r; flags of the (128-row block, component) pairs with r > 0
-//   k_tc_gemm ZW  GEMM1 again for the flagged pairs only, z stored as
-//                 A2[k][n][:] = r_nk z_nk (the A operand of GEMM2)
-//   k_tc_gemm G   grad f = sum_k A2_k L_k^T rows over the flagged components (GEMM2)
+//   k_tc_scale_z  Z[k][n][:] = round(r_nk z_nk) for the flagged pairs (the A
+//                 operand of GEMM2; rows with r_nk = 0 become zeros)
+//   k_tc_gemm G   grad f = sum_k Z_k L_k^T rows over the flagged components (GEMM2)
 // With separated modes most responsibilities are exactly 0 in FP32 (the
-// exponent underflows), so the store pass and GEMM2 visit a fraction of the
+// exponent underflows), so the scaling pass and GEMM2 visit a fraction of the
 // K components; the terms they skip are exactly zero.
 // Both operands of both GEMMs reach shared memory by TMA (3-D tensor maps,
 // 128-byte swizzle, out-of-range rows/columns zero-filled), so the MMA
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
     const int n_groups = n_mblk * K;
     // (row block, component) pairs to visit: GEMM2's flags for the store pass, the
     // component-skip mask for the |z|^2 pass
-    const uint32_t *gmask = MODE == MODE_ZW ? a.rflag : (MODE == MODE_ZR ? a.zmask : nullptr);
+    const uint32_t *gmask = MODE == MODE_G ? nullptr : ((MODE == MODE_ZW && a.rflag) ? a.rflag : a.zmask);
     const bool compact = MODE != MODE_G && gmask != nullptr && n_groups <= kMaxGroupList;
     if (compact) {
         if (threadIdx.x == 0) *s_gcount = 0;
@@ -595,6 +597,51 @@ __global__ void __launch_bounds__(128) k_tc_lse(int mode, int K, int n_ntile, co
         ell[n] = l;
 }
 
+// GEMM2's A operand from the stored z: for every (128-row block, component) pair whose
+// flag says some row has r_nk > 0, Z[k][n][:] = round(r_nk z_nk) (rows past the live
+// count, and rows with r_nk = 0, become exact zeros), so GEMM2 adds r_nk L_k z_nk.
+template <int PREC>
+__global__ void __launch_bounds__(256) k_tc_scale_z(int K, int ldz, int z_rows, const int32_t *n_rows_dev,
+                                                    int n_rows_max, const float *R, const uint32_t *rflag, void *Z) {
+    const int mb = blockIdx.x, k = blockIdx.y;
+    if (!rflag[(size_t)mb * K + k]) return;
+    const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
+    constexpr int VE = (PREC == SB_PREC_BF16) ? 8 : 4;  // elements per 16-byte vector
+    const int nv = ldz / VE;
+    for (int e = threadIdx.x; e < BM * nv; e += blockDim.x) {
+        const int row = e / nv, v = e - row * nv;
+        const int n = mb * BM + row;
+        if (n >= z_rows) break;
+        const float r = n < n_rows ? R[(size_t)n * K + k] : 0.f;
+        const size_t off = ((size_t)k * z_rows + n) * ldz + (size_t)v * VE;
+        if (PREC == SB_PREC_BF16) {
+            uint4 *p = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(Z) + off);
+            uint4 q = make_uint4(0u, 0u, 0u, 0u);
+            if (r > 0.f) {
+                const uint4 w = *p;
+                const uint32_t in[4] = {w.x, w.y, w.z, w.w};
+                uint32_t out[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&in[h]);
+                    const float2 f = __bfloat1622float2(b);
+                    out[h] = pack_bf16x2(f.x * r, f.y * r);
+                }
+                q = make_uint4(out[0], out[1], out[2], out[3]);
+            }
+            *p = q;
+        } else {
+            float4 *p = reinterpret_cast<float4 *>(reinterpret_cast<float *>(Z) + off);
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r > 0.f) {
+                const float4 w = *p;
+                q = make_float4(to_tf32(w.x * r), to_tf32(w.y * r), to_tf32(w.z * r), to_tf32(w.w * r));
+            }
+            *p = q;
+        }
+    }
+}
+
 // Component skip of the walker rounds. e_k = a_k - |z_k|^2 / 2 with z_k = L_k^T (x - mu_k);
 // a component whose e_k lies more than kSkipNats below the largest term adds exp(-110)
 // < 2e-48 relative: below FP32 resolution, so the LSE's FP32 exponential and the
@@ -716,9 +763,10 @@ __global__ void __launch_bounds__(256) k_tc_lnorm_gram(int d, int K, int k0, int
 template <int PREC>
 __global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int K, int rows_cap, int ldp,
                                                    const int32_t *n_rows_dev, int n_rows_max, const int32_t *act,
-                                                   const float *X, int ld, const float *u32, const double *texit,
-                                                   int n_steps, long long flat0, const float *mu32, const float *c32,
-                                                   void *A1, const uint32_t *zmask) {
+                                                   const float *X, int ld, const float *u32, const float *o32,
+                                                   const double *texit, int n_steps, long long flat0,
+                                                   const float *mu32, const float *c32, void *A1,
+                                                   const uint32_t *zmask) {
     constexpr int VE = (PREC == SB_PREC_BF16) ? 8 : 4;  // elements per 16-byte store
     const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
     int rows_pad = (n_rows + BM - 1) / BM * BM;
@@ -751,16 +799,18 @@ __global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int K, i
                     if (i0 + q < d) x[q] = xr[i0 + q];
             }
         } else {
-            // FP32 position on the ray: the operand is rounded to bf16 / tf32 below anyway
+            // FP32 position on the ray from its origin (the box centre, or the ray's own
+            // origin o32): the operand is rounded to bf16 / tf32 below anyway
             const long long flat = flat0 + n;
             const int ray = (int)(flat / n_steps), j = (int)(flat - (long long)ray * n_steps);
             const float sc = ((float)(j + 1) / (float)n_steps) * (float)texit[ray];
             const float *ur = u32 + (size_t)ray * d;
+            const float *orig = o32 ? o32 + (size_t)ray * d : c32;
             if (vec) {
 #pragma unroll
                 for (int q = 0; q < VE; q += 4) {
                     const float4 u4 = *reinterpret_cast<const float4 *>(ur + i0 + q);
-                    const float4 c4 = *reinterpret_cast<const float4 *>(c32 + i0 + q);
+                    const float4 c4 = *reinterpret_cast<const float4 *>(orig + i0 + q);
                     x[q] = fmaf(sc, u4.x, c4.x);
                     x[q + 1] = fmaf(sc, u4.y, c4.y);
                     x[q + 2] = fmaf(sc, u4.z, c4.z);
@@ -769,7 +819,7 @@ __global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int K, i
             } else {
 #pragma unroll
                 for (int q = 0; q < VE; ++q)
-                    if (i0 + q < d) x[q] = fmaf(sc, ur[i0 + q], c32[i0 + q]);
+                    if (i0 + q < d) x[q] = fmaf(sc, ur[i0 + q], orig[i0 + q]);
             }
         }
     }
@@ -844,6 +894,11 @@ __global__ void k_tc_points_in(int n, int d, const double *x, float *X) {
     const size_t tot = (size_t)n * d;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x)
         X[e] = (float)x[e];
+}
+
+__global__ void k_tc_to_f32(size_t n, const double *x, float *y) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        y[e] = (float)x[e];
 }
 
 __global__ void k_tc_points_out(int n, int d, const float *G, double *grad) {
@@ -949,7 +1004,7 @@ void launch_gemm_any(int prec, int mode, int bn, const CUtensorMap &mapA, const 
 
 void launch_center(const TcWs &t, int ray_mode, int d, int K, const int32_t *n_rows_dev, int n_rows_max,
                    const int32_t *act, const float *X, const float *u32, const double *texit, int n_steps,
-                   long long flat0, cudaStream_t s, const uint32_t *zmask = nullptr) {
+                   long long flat0, cudaStream_t s, const uint32_t *zmask = nullptr, const float *o32 = nullptr) {
     const int ldp = ldp_of(d, t.prec);
     const int ncg = ldp / (t.prec == SB_PREC_BF16 ? 8 : 4);
     int rows = (n_rows_max + BM - 1) / BM * BM;
@@ -958,11 +1013,11 @@ void launch_center(const TcWs &t, int ray_mode, int d, int K, const int32_t *n_r
     note_launch();
     if (t.prec == SB_PREC_BF16)
         k_tc_center<SB_PREC_BF16><<<grid, 256, 0, s>>>(ray_mode, d, K, (int)t.rows, ldp, n_rows_dev, n_rows_max, act,
-                                                      X, d, u32, texit, n_steps, flat0, (const float *)t.p[2],
+                                                      X, d, u32, o32, texit, n_steps, flat0, (const float *)t.p[2],
                                                       (const float *)t.p[3], t.p[9], zmask);
     else
         k_tc_center<SB_PREC_TF32><<<grid, 256, 0, s>>>(ray_mode, d, K, (int)t.rows, ldp, n_rows_dev, n_rows_max, act,
-                                                      X, d, u32, texit, n_steps, flat0, (const float *)t.p[2],
+                                                      X, d, u32, o32, texit, n_steps, flat0, (const float *)t.p[2],
                                                       (const float *)t.p[3], t.p[9], zmask);
 }
 
@@ -982,6 +1037,17 @@ TcArgs base_args(const ProbView &pv, const TcWs &t) {
     a.n_ntile = (pv.d + t.bn - 1) / t.bn;
     a.err = pv.status;
     return a;
+}
+
+void launch_scale_z(const ProbView &pv, const TcWs &t, const int32_t *n_rows_dev, int n_rows_max, cudaStream_t s) {
+    const dim3 grid((unsigned)((n_rows_max + BM - 1) / BM), (unsigned)pv.K);
+    note_launch();
+    if (t.prec == SB_PREC_BF16)
+        k_tc_scale_z<SB_PREC_BF16><<<grid, 256, 0, s>>>(pv.K, (int)t.ldz, (int)t.rows, n_rows_dev, n_rows_max,
+                                                         (const float *)t.p[6], (const uint32_t *)t.p[10], t.p[4]);
+    else
+        k_tc_scale_z<SB_PREC_TF32><<<grid, 256, 0, s>>>(pv.K, (int)t.ldz, (int)t.rows, n_rows_dev, n_rows_max,
+                                                         (const float *)t.p[6], (const uint32_t *)t.p[10], t.p[4]);
 }
 
 }  // namespace
@@ -1169,21 +1235,31 @@ sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s, bool skip_boun
     return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
 }
 
-sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const float *u32,
-                        const double *texit, double *ell_all, cudaStream_t s) {
-    const int64_t total = (int64_t)c->n_rays * c->n_steps;
-    for (int64_t f0 = 0; f0 < total; f0 += (int64_t)t.rows) {
-        const int rows = (int)((total - f0) < (int64_t)t.rows ? (total - f0) : (int64_t)t.rows);
+sb_status tc_ray_samples(const ProbView &pv, const TcWs &t, const float *o32, const float *u32, const double *texit,
+                         int n_steps, int64_t f_begin, int64_t f_end, double *ell, cudaStream_t s) {
+    for (int64_t f0 = f_begin; f0 < f_end; f0 += (int64_t)t.rows) {
+        const int rows = (int)((f_end - f0) < (int64_t)t.rows ? (f_end - f0) : (int64_t)t.rows);
         TcArgs a = base_args(pv, t);
         a.n_rows_max = rows;
-        launch_center(t, 1, pv.d, pv.K, nullptr, rows, nullptr, nullptr, u32, texit, c->n_steps, f0, s);
+        launch_center(t, 1, pv.d, pv.K, nullptr, rows, nullptr, nullptr, u32, texit, n_steps, f0, s, nullptr, o32);
         launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
         note_launch();
         k_tc_lse<<<(rows + 127) / 128, 128, 0, s>>>(1, pv.K, a.n_ntile, nullptr, rows, nullptr, a.qpart, pv.a,
-                                                    nullptr, nullptr, ell_all + f0, nullptr, nullptr, nullptr,
+                                                    nullptr, nullptr, ell + (f0 - f_begin), nullptr, nullptr, nullptr,
                                                     nullptr, nullptr);
     }
     return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
+}
+
+sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const float *u32,
+                        const double *texit, double *ell_all, cudaStream_t s) {
+    return tc_ray_samples(pv, t, nullptr, u32, texit, c->n_steps, 0, (int64_t)c->n_rays * c->n_steps, ell_all, s);
+}
+
+void tc_to_f32(const double *x, float *y, size_t n, cudaStream_t s) {
+    note_launch();
+    const size_t blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    k_tc_to_f32<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(n, x, y);
 }
 
 void tc_walkers_reset(const TcWs &t, int n, cudaStream_t s) {
@@ -1199,9 +1275,8 @@ void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, cons
     a.n_rows_max = n;
     a.prof = PROF_TC_Z_WALKERS;
     // the (row block, component) pairs whose terms can still reach l (k_tc_need),
-    // then their centred operand and |z|^2 (no z stored), then l, r and the flags
-    // of the pairs with r > 0, then z again for those pairs only, stored as r z
-    // (GEMM2's A operand), then the gradient
+    // then their centred operand, |z|^2 and z, then l, r and the flags of the pairs
+    // with r > 0, then r z for those pairs (GEMM2's A operand), then the gradient
     uint32_t *zmask = (uint32_t *)t.p[16];
     cudaMemsetAsync(zmask, 0, sizeof(uint32_t) * ((n + BM - 1) / BM) * pv.K, s);
     note_launch();
@@ -1210,14 +1285,16 @@ void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, cons
                                               (const float *)t.p[14], zmask);
     launch_center(t, 0, pv.d, pv.K, n_act, n, act, XT, nullptr, nullptr, 1, 0, s, zmask);
     a.zmask = zmask;
-    launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
+    a.rflag = nullptr;  // GEMM1 over the kept pairs: |z|^2 partials and z itself
+    launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
     a.zmask = nullptr;
+    a.rflag = (const uint32_t *)t.p[10];
     cudaMemsetAsync(t.p[10], 0, sizeof(uint32_t) * ((n + BM - 1) / BM) * pv.K, s);
     note_launch();
     k_tc_lse<<<(n + 127) / 128, 128, 0, s>>>(0, pv.K, a.n_ntile, n_act, n, act, a.qpart, pv.a, (float *)t.p[6], FT,
                                              nullptr, (uint32_t *)t.p[10], zmask, (float *)t.p[11],
                                              (int32_t *)t.p[12], (float *)t.p[13]);
-    launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
+    launch_scale_z(pv, t, n_act, n, s);
     a.prof = -1;
     a.G = GT;
     launch_gemm_any(t.prec, MODE_G, t.bn, t.mapZ, t.mapB, a, s);
@@ -1236,14 +1313,17 @@ sb_status tc_loglik_points(const ProbView &pv, const sb_config *c, const TcWs &t
     a.n_rows_max = n;
     a.prof = PROF_TC_Z_WALKERS;
     launch_center(t, 0, pv.d, pv.K, nullptr, n, nullptr, X, nullptr, nullptr, 1, 0, s);
-    launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
+    // with the gradient, GEMM1 also stores z (the A operand of GEMM2 once scaled by r)
+    a.rflag = nullptr;
+    launch_gemm_any(t.prec, grad ? MODE_ZW : MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
+    a.rflag = (const uint32_t *)t.p[10];
     cudaMemsetAsync(t.p[10], 0, sizeof(uint32_t) * ((n + BM - 1) / BM) * pv.K, s);
     note_launch();
     k_tc_lse<<<(n + 127) / 128, 128, 0, s>>>(2, pv.K, a.n_ntile, nullptr, n, nullptr, a.qpart, pv.a,
                                              (float *)t.p[6], nullptr, ell, (uint32_t *)t.p[10], nullptr, nullptr,
                                              nullptr, nullptr);
     if (grad) {
-        launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
+        launch_scale_z(pv, t, nullptr, n, s);
         a.prof = -1;
         a.G = G;
         launch_gemm_any(t.prec, MODE_G, t.bn, t.mapZ, t.mapB, a, s);

@@ -11,8 +11,9 @@ roundoff u_p = 2^-8 or 2^-11; u32 = 2^-24):
  4. |z_k|^2 in FP32 over tiles of at most 256 columns, tiles summed in FP64;
  5. l = LSE_k (a_k - |z_k|^2 / 2) with FP32 exponentials and logarithm;
     r_k = softmax_k in FP32;
- 6. r_k z_kj in FP32, rounded to p; grad_i = -sum_k sum_{j <= i} (r_k z_kj) L_k,ij
-    with exact products and FP32 accumulation over K d terms.
+ 6. z_kj rounded to p when stored, then r_k z_kj in FP32 rounded to p again;
+    grad_i = -sum_k sum_{j <= i} (r_k z_kj) L_k,ij with exact products and FP32
+    accumulation over K d terms.
 So per entry, with S_kj = sum_i |a_i| |L_k,ij| and T_kj = sum_i (|x_i| + |mu_k,i|) |L_k,ij|:
     |dz_kj| <= E_kj = (2 u_p + u_p^2 + u32 + g1 (1 + u_p)^2) S_kj + 2 u32 (1 + u_p)^2 T_kj,
     g1 = (d + 16) 2^-22;
@@ -20,7 +21,7 @@ So per entry, with S_kj = sum_i |a_i| |L_k,ij| and T_kj = sum_i (|x_i| + |mu_k,i
 then l lies between LSE(e - Eq/2) and LSE(e + Eq/2) (LSE is monotone and
 shift-equivariant), r_k between exp(e_k -+ Eq_k/2 - LSE(e +- Eq/2)), and
     |dgrad_i| <= sum_k sum_j |L_k,ij| W_kj,
-    W_kj = R_k E_kj + dr_k |z_kj| + (2 u_p + 2 u32 + g2) (1 + u_p)^2 R_k (|z_kj| + E_kj),
+    W_kj = R_k E_kj + dr_k |z_kj| + (3 u_p + 2 u32 + g2) (1 + u_p)^3 R_k (|z_kj| + E_kj),
     R_k = r_k + dr_k, g2 = (K d + 16) 2^-22,
 plus a floor of 2^-20 (1 + K) for the FP32 exponentials and logarithm of the LSE.
 These are worst cases (every rounding at its extreme, all of one sign); the
@@ -80,7 +81,7 @@ def bounds(inst, X, prec):
     for k in range(K):
         R = (r[:, k] + dr[:, k])[:, None]
         az = np.abs(Z[k])
-        W = R * E[k] + dr[:, k][:, None] * az + (2 * up + 2 * U32 + g2) * (1 + up) ** 2 * R * (az + E[k])
+        W = R * E[k] + dr[:, k][:, None] * az + (3 * up + 2 * U32 + g2) * (1 + up) ** 3 * R * (az + E[k])
         B_g += W @ np.abs(inst.L[k]).T
     return B_l, B_g, ell, r
 
@@ -98,7 +99,8 @@ def sigmas(inst, X, prec):
       dgrad_i = -sum_k [r_k (sum_m a_m da_m P_im + sum_j L_ij (sum_m a_m L_mj dL_mj
                 + z_j dL_ij + z_j dw_j)) + dr_k (P a)_i]
     where the same rounding dL of L_k feeds both contractions (its two terms are
-    bounded by twice their squares), dw is the rounding of r z to p, and
+    bounded by twice their squares), dw the two roundings of the stored z and of r z
+    to p (variance 2 v_p), and
     dr_k = r_k (de_k - sum_m r_m de_m), de = -dq / 2. The FP32 exponentials of the
     LSE add a floor of 4 u32 to l. The FP32 roundings of x, mu_k and their difference
     (before the rounding to p) add v32 (x_i^2 + mu_k,i^2 + a_i^2) per coordinate to the
@@ -143,7 +145,7 @@ def sigmas(inst, X, prec):
         var_g += rk2 * vp * (A2 @ P2)                      # da through P a
         var_g += rk2 * v32 * (F2 @ P2)                     # FP32 x, mu_k and x - mu_k
         var_g += rk2 * 2 * vp * (S @ L2.T + Z2 @ L2.T)    # dL in both contractions
-        var_g += rk2 * vp * (Z2 @ L2.T)                    # dw: r z rounded to p
+        var_g += rk2 * 2 * vp * (Z2 @ L2.T)                # dw: z, then r z, rounded to p
         var_g += rk2 * (K * d) * v32 * (Z2 @ L2.T)        # FP32 accumulation of the gradient
         var_g += rk2 * d * v32 * (S @ L2.T)                # FP32 accumulation of z
         var_g += vr[:, k][:, None] * PA * PA               # responsibilities
