@@ -42,6 +42,21 @@ __device__ __forceinline__ void normal_pair(uint32_t c0, uint32_t c1, uint32_t c
     z1 = mul_rn(rad, sin(th));
 }
 
+// The same two normals in FP32 for the mixed path (the same Philox block; uniforms from
+// the top 24 bits of each 64-bit pair, FP32 transcendentals, as its sunburst directions).
+__device__ __forceinline__ void normal_pair_f32(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                                uint32_t k1, float &z0, float &z1) {
+    uint32_t c[4] = {c0, c1, c2, c3};
+    philox4x32_10(c, k0, k1);
+    const float u1 = ((float)(c[0] >> 8) + 0.5f) * (1.0f / 16777216.0f);
+    const float u2 = ((float)(c[2] >> 8) + 0.5f) * (1.0f / 16777216.0f);
+    const float rad = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    z0 = rad * cs;
+    z1 = rad * sn;
+}
+
 // Distance from o along u to the box boundary (whole warp; 0 when u = 0).
 __device__ double exit_length(int lane, int d, const double *o, const double *u, const double *lo, const double *hi) {
     double t = INFINITY;
@@ -192,11 +207,17 @@ __global__ void __launch_bounds__(256) k_cs_rm_rays(int n_lost, int d, uint32_t 
 
 constexpr int CS_BASIS = 256;
 
+// One orthonormal group per CTA: the Philox normals orthogonalised column by column by
+// classical Gram-Schmidt with a second pass, and normalised, in arithmetic T: FP64 on
+// the FP64 path; FP32 (normals included) on the mixed path, whose rays are formed in
+// FP32 anyway and on whose GB300 FP64 units the d G^2 QR would be the slowest step of a
+// reseeding. Q stays FP64 in memory.
+template <typename T>
 __global__ void __launch_bounds__(CS_BASIS) k_cs_bases(int d, uint32_t k0, uint32_t k1, int osc, const int32_t *job_pk,
                                                        const int32_t *job_b, const int32_t *job_cols,
                                                        const int64_t *job_off, double *Q) {
     extern __shared__ double s_h[];  // [d] projections of the current column
-    __shared__ double s_red[CS_BASIS / 32];
+    __shared__ T s_red[CS_BASIS / 32];
     const int j = blockIdx.x;
     const int pk = job_pk[j], b = job_b[j], cols = job_cols[j];
     double *Qj = Q + job_off[j];
@@ -205,43 +226,56 @@ __global__ void __launch_bounds__(CS_BASIS) k_cs_bases(int d, uint32_t k0, uint3
     const int G = cs_group(d);
     for (int idx = threadIdx.x; idx < cols * npairs; idx += CS_BASIS) {
         const int c = idx / npairs, q = idx - c * npairs;
-        double z0, z1;
-        normal_pair((uint32_t)q, (uint32_t)(b * G + c), ((uint32_t)osc << 16) | (uint32_t)pk, kTagGr, k0, k1, z0, z1);
-        Qj[(size_t)c * d + 2 * q] = z0;
-        if (2 * q + 1 < d) Qj[(size_t)c * d + 2 * q + 1] = z1;
+        T z0, z1;
+        if (sizeof(T) == sizeof(double)) {
+            double a0, a1;
+            normal_pair((uint32_t)q, (uint32_t)(b * G + c), ((uint32_t)osc << 16) | (uint32_t)pk, kTagGr, k0, k1, a0,
+                        a1);
+            z0 = (T)a0;
+            z1 = (T)a1;
+        } else {
+            float a0, a1;
+            normal_pair_f32((uint32_t)q, (uint32_t)(b * G + c), ((uint32_t)osc << 16) | (uint32_t)pk, kTagGr, k0, k1,
+                            a0, a1);
+            z0 = (T)a0;
+            z1 = (T)a1;
+        }
+        Qj[(size_t)c * d + 2 * q] = (double)z0;
+        if (2 * q + 1 < d) Qj[(size_t)c * d + 2 * q + 1] = (double)z1;
     }
     __syncthreads();
+    T *sh = reinterpret_cast<T *>(s_h);
     for (int c = 0; c < cols; ++c) {
         double *qc = Qj + (size_t)c * d;
         for (int pass = 0; pass < 2 && c > 0; ++pass) {
             for (int k = wid; k < c; k += nw) {
                 const double *qk = Qj + (size_t)k * d;
-                double dot = 0.0;
-                for (int i = lane; i < d; i += 32) dot += qk[i] * qc[i];
+                T dot = 0;
+                for (int i = lane; i < d; i += 32) dot += (T)qk[i] * (T)qc[i];
                 dot = warp_sum(dot);
-                if (lane == 0) s_h[k] = dot;
+                if (lane == 0) sh[k] = dot;
             }
             __syncthreads();
             for (int i = threadIdx.x; i < d; i += CS_BASIS) {
-                double acc = 0.0;
-                for (int k = 0; k < c; ++k) acc += s_h[k] * Qj[(size_t)k * d + i];
-                qc[i] -= acc;
+                T acc = 0;
+                for (int k = 0; k < c; ++k) acc += sh[k] * (T)Qj[(size_t)k * d + i];
+                qc[i] = (double)((T)qc[i] - acc);
             }
             __syncthreads();
         }
-        double ss = 0.0;
-        for (int i = threadIdx.x; i < d; i += CS_BASIS) ss += qc[i] * qc[i];
+        T ss = 0;
+        for (int i = threadIdx.x; i < d; i += CS_BASIS) ss += (T)qc[i] * (T)qc[i];
         ss = warp_sum(ss);
         if (lane == 0) s_red[wid] = ss;
         __syncthreads();
         if (wid == 0) {
-            double v = lane < nw ? s_red[lane] : 0.0;
+            T v = lane < nw ? s_red[lane] : (T)0;
             v = warp_sum(v);
             if (lane == 0) s_red[0] = v;
         }
         __syncthreads();
-        const double nrm = sqrt(s_red[0]);
-        for (int i = threadIdx.x; i < d; i += CS_BASIS) qc[i] = div_rn(qc[i], nrm);
+        const T nrm = sqrt(s_red[0]);
+        for (int i = threadIdx.x; i < d; i += CS_BASIS) qc[i] = (double)div_rn((T)qc[i], nrm);
         __syncthreads();
     }
 }
@@ -382,11 +416,15 @@ void launch_cs_rm_rays(int n_lost, int d, uint64_t seed, int osc, const int32_t 
 }
 
 void launch_cs_bases(int n_jobs, int d, uint64_t seed, int osc, const int32_t *job_pk, const int32_t *job_b,
-                     const int32_t *job_cols, const int64_t *job_off, double *Q, cudaStream_t s) {
+                     const int32_t *job_cols, const int64_t *job_off, double *Q, bool fp32, cudaStream_t s) {
     if (n_jobs <= 0) return;
     note_launch();
-    k_cs_bases<<<n_jobs, CS_BASIS, sizeof(double) * d, s>>>(d, (uint32_t)seed, (uint32_t)(seed >> 32), osc, job_pk,
-                                                            job_b, job_cols, job_off, Q);
+    if (fp32)
+        k_cs_bases<float><<<n_jobs, CS_BASIS, sizeof(double) * d, s>>>(d, (uint32_t)seed, (uint32_t)(seed >> 32), osc,
+                                                                       job_pk, job_b, job_cols, job_off, Q);
+    else
+        k_cs_bases<double><<<n_jobs, CS_BASIS, sizeof(double) * d, s>>>(d, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                                                        osc, job_pk, job_b, job_cols, job_off, Q);
 }
 
 void launch_cs_gr_rays(int n_lost, int d, int n_peaks, const int32_t *reps, const double *X, const double *lo,

@@ -265,13 +265,15 @@ __global__ void __launch_bounds__(256) k_precision(int d, const double *L, doubl
 }
 
 // Components whose P_k the Hessians are about to read: r_ck != 0 at some live
-// candidate and P_k not formed yet (the Hessian skips r == 0 terms, so the
-// other P_k are never read). Marks them formed.
-__global__ void k_precision_need(int K, const double *R, const int32_t *n_c, int32_t *done, int32_t *need) {
+// candidate whose responsibilities are not one-hot, and P_k not formed yet (the
+// Hessian skips r == 0 terms and copies L_k at one-hot candidates, so the other
+// P_k are never read). Marks them formed.
+__global__ void k_precision_need(int K, const double *R, const int32_t *n_c, const int32_t *onehot, int32_t *done,
+                                 int32_t *need) {
     const int k = threadIdx.x;
     if (k >= K) return;
     bool any = false;
-    for (int c = 0; c < *n_c; ++c) any = any || R[(size_t)c * K + k] != 0.0;
+    for (int c = 0; c < *n_c; ++c) any = any || (R[(size_t)c * K + k] != 0.0 && !(onehot && onehot[c] >= 0));
     const bool nk = any && !done[k];
     need[k] = nk ? 1 : 0;
     if (nk) done[k] = 1;
@@ -308,14 +310,38 @@ __global__ void __launch_bounds__(256) k_comp_grads(int d, int K, const double *
     }
 }
 
-// H[c][i][i2] = gbar_i gbar_i2 + sum_k r_k (P_k[i][i2] - g_ki g_ki2)
+// onehot[c] = k when candidate c's FP64 responsibilities are exactly r_ck = 1 and 0 for
+// every other component, else -1. There H = sum_k r_k (P_k - g_k g_k^T) + gbar gbar^T
+// with gbar = g_k is exactly P_k = L_k L_k^T, whose Cholesky factor is L_k itself.
+__global__ void k_onehot(int K, const double *R, const int32_t *n_c, int cap, int32_t *onehot) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cap) return;
+    int k1 = -1;
+    bool ok = c < *n_c;
+    for (int k = 0; ok && k < K; ++k) {
+        const double r = R[(size_t)c * K + k];
+        if (r == 1.0 && k1 < 0)
+            k1 = k;
+        else if (r != 0.0)
+            ok = false;
+    }
+    onehot[c] = ok ? k1 : -1;
+}
+
+// H[c][i][i2] = gbar_i gbar_i2 + sum_k r_k (P_k[i][i2] - g_ki g_ki2); at a one-hot
+// candidate the lower triangle of its factor L_k instead (the blocked Cholesky skips it)
 __global__ void __launch_bounds__(256) k_hessian(int d, int K, const double *P, const double *GK, const double *R,
-                                                 const double *gbar, const int32_t *n_c, double *H) {
+                                                 const double *gbar, const int32_t *n_c, const int32_t *onehot,
+                                                 const double *L, double *H) {
     const int c = blockIdx.y;
     if (c >= *n_c) return;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)d * d) return;
     const int i = (int)(e / d), i2 = (int)(e % d);
+    if (onehot && onehot[c] >= 0) {
+        H[(size_t)c * d * d + e] = i2 <= i ? L[(size_t)onehot[c] * d * d + e] : 0.0;
+        return;
+    }
     const double *gb = gbar + (size_t)c * d;
     double h = gb[i] * gb[i2];
     for (int k = 0; k < K; ++k) {
@@ -336,9 +362,9 @@ __global__ void __launch_bounds__(256) k_hessian(int d, int K, const double *P, 
 // every thread at the same step.
 constexpr int DIAG_THREADS = 256;
 __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(int d, int kb, double *H, const int32_t *n_c,
-                                                             int32_t *info) {
+                                                             const int32_t *onehot, int32_t *info) {
     const int c = blockIdx.x;
-    if (c >= *n_c || info[c]) return;
+    if (c >= *n_c || info[c] || (onehot && onehot[c] >= 0)) return;
     double *A = H + (size_t)c * d * d;
     __shared__ double a[NB][NB + 1];
     const int o = kb * NB;
@@ -387,9 +413,9 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(int d, int kb, doub
 // are spread over four warps (four schedulers).
 constexpr int TRSM_THREADS = 128;
 __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_panel(int d, int kb, double *H, const int32_t *n_c,
-                                                             const int32_t *info) {
+                                                             const int32_t *onehot, const int32_t *info) {
     const int c = blockIdx.y, ib = kb + 1 + blockIdx.x;
-    if (c >= *n_c || info[c]) return;
+    if (c >= *n_c || info[c] || (onehot && onehot[c] >= 0)) return;
     const int nblk = (d + NB - 1) / NB;
     if (ib >= nblk) return;
     double *A = H + (size_t)c * d * d;
@@ -433,9 +459,9 @@ __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_panel(int d, int kb, doub
 
 // Trailing update A[ib][jb] -= A[ib][kb] A[jb][kb]^T for kb < jb <= ib.
 __global__ void __launch_bounds__(256) k_syrk_update(int d, int kb, double *H, const int32_t *n_c,
-                                                     const int32_t *info) {
+                                                     const int32_t *onehot, const int32_t *info) {
     const int c = blockIdx.z;
-    if (c >= *n_c || info[c]) return;
+    if (c >= *n_c || info[c] || (onehot && onehot[c] >= 0)) return;
     const int ib = kb + 1 + blockIdx.y, jb = kb + 1 + blockIdx.x;
     if (jb > ib) return;
     const int nblk = (d + NB - 1) / NB;
@@ -829,10 +855,15 @@ void launch_precision(int d, int K, const double *L, double *P, cudaStream_t s) 
     k_precision<<<g, 256, 0, s>>>(d, L, P, nullptr);
 }
 
-void launch_precision_needed(int d, int K, const double *L, const double *R, const int32_t *n_c, int32_t *done,
-                             int32_t *need, double *P, cudaStream_t s) {
+void launch_onehot(int K, const double *R, const int32_t *n_c, int cap, int32_t *onehot, cudaStream_t s) {
     note_launch();
-    k_precision_need<<<1, kMaxK, 0, s>>>(K, R, n_c, done, need);
+    k_onehot<<<(cap + 127) / 128, 128, 0, s>>>(K, R, n_c, cap, onehot);
+}
+
+void launch_precision_needed(int d, int K, const double *L, const double *R, const int32_t *n_c, int32_t *done,
+                             int32_t *need, double *P, cudaStream_t s, const int32_t *onehot) {
+    note_launch();
+    k_precision_need<<<1, kMaxK, 0, s>>>(K, R, n_c, onehot, done, need);
     dim3 g((d + PT - 1) / PT, (d + PT - 1) / PT, K);
     note_launch();
     k_precision<<<g, 256, 0, s>>>(d, L, P, need);
@@ -840,24 +871,24 @@ void launch_precision_needed(int d, int K, const double *L, const double *R, con
 
 void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P, const double *Z, const double *R,
                          const double *gbar, const int32_t *n_c, double *GK, double *H, int32_t *info,
-                         cudaStream_t s) {
+                         cudaStream_t s, const int32_t *onehot) {
     note_launch();
     k_comp_grads<<<dim3(cap, K, kGradSlices), 256, sizeof(double) * d, s>>>(d, K, L, Z, R, n_c, GK);
     const int64_t dd = (int64_t)d * d;
     note_launch();
-    k_hessian<<<dim3((unsigned)((dd + 255) / 256), cap), 256, 0, s>>>(d, K, P, GK, R, gbar, n_c, H);
+    k_hessian<<<dim3((unsigned)((dd + 255) / 256), cap), 256, 0, s>>>(d, K, P, GK, R, gbar, n_c, onehot, L, H);
     cudaMemsetAsync(info, 0, sizeof(int32_t) * cap, s);
     const int nblk = (d + NB - 1) / NB;
     ProfScope prof(PROF_CHOLESKY, s);
     for (int kb = 0; kb < nblk; ++kb) {
         note_launch();
-        k_potrf_diag<<<cap, DIAG_THREADS, 0, s>>>(d, kb, H, n_c, info);
+        k_potrf_diag<<<cap, DIAG_THREADS, 0, s>>>(d, kb, H, n_c, onehot, info);
         const int rest = nblk - kb - 1;
         if (rest > 0) {
             note_launch();
-            k_trsm_panel<<<dim3(rest, cap), TRSM_THREADS, 0, s>>>(d, kb, H, n_c, info);
+            k_trsm_panel<<<dim3(rest, cap), TRSM_THREADS, 0, s>>>(d, kb, H, n_c, onehot, info);
             note_launch();
-            k_syrk_update<<<dim3(rest, rest, cap), 256, 0, s>>>(d, kb, H, n_c, info);
+            k_syrk_update<<<dim3(rest, rest, cap), 256, 0, s>>>(d, kb, H, n_c, onehot, info);
         }
     }
 }

@@ -179,6 +179,7 @@ struct LaplaceWs {
     uint32_t *dd_bar;
     int32_t *p_done, *p_need;  // [K] P_k formed / to form now
     int32_t *n_live;           // candidates still moving in a Newton step
+    int32_t *onehot;           // [cap] component k when a candidate's responsibilities are one-hot, else -1
 };
 
 struct EvidenceWs {
@@ -281,6 +282,7 @@ Layout layout(void *base, const sb_problem *p, const sb_config *c) {
     la.p_done = cv.take<int32_t>(kMaxK);
     la.p_need = cv.take<int32_t>(kMaxK);
     la.n_live = cv.take<int32_t>(1);
+    la.onehot = cv.take<int32_t>(cap);
     la.XC = cv.take<double>((size_t)cap * d);
     la.LC = cv.take<double>(cap);
     la.GC = cv.take<double>((size_t)cap * d);
@@ -553,8 +555,10 @@ sb_status run_laplace(const ProbView &pv, const sb_config *c, const Layout &L, c
     // l, grad l, H and its Cholesky factor at every candidate
     auto eval_full = [&]() {
         f64_points(pv, la.XC, nullptr, la.n_reps, nc, la.qpart, la.Z, la.R, la.LC, la.GC, s);
-        launch_precision_needed(d, K, pv.L, la.R, la.n_reps, la.p_done, la.p_need, la.P, s);
-        launch_hessian_chol(d, K, nc, pv.L, la.P, la.Z, la.R, la.GC, la.n_reps, la.GK, la.H, la.info, s);
+        launch_onehot(K, la.R, la.n_reps, nc, la.onehot, s);
+        launch_precision_needed(d, K, pv.L, la.R, la.n_reps, la.p_done, la.p_need, la.P, s, la.onehot);
+        launch_hessian_chol(d, K, nc, pv.L, la.P, la.Z, la.R, la.GC, la.n_reps, la.GK, la.H, la.info, s,
+                            la.onehot);
     };
     eval_full();
     // Newton polish, at most newton_steps steps; it ends early once every
@@ -1234,7 +1238,7 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
             SB_CUDA_TRY(cudaMemcpyAsync(w.job_b, j.b.data(), sizeof(int32_t) * nj, cudaMemcpyHostToDevice, s));
             SB_CUDA_TRY(cudaMemcpyAsync(w.job_cols, j.cols.data(), sizeof(int32_t) * nj, cudaMemcpyHostToDevice, s));
             SB_CUDA_TRY(cudaMemcpyAsync(w.job_off, j.off.data(), sizeof(int64_t) * nj, cudaMemcpyHostToDevice, s));
-            launch_cs_bases(nj, d, c->seed, osc, w.job_pk, w.job_b, w.job_cols, w.job_off, w.Q, s);
+            launch_cs_bases(nj, d, c->seed, osc, w.job_pk, w.job_b, w.job_cols, w.job_off, w.Q, mixed, s);
             launch_cs_gr_rays(n_lost, d, h_peaks, w.reps, w.X, pv.lo, pv.hi, w.job_start, w.job_off, w.Q, w.O, w.U,
                               w.texit, s);
             SB_CUDA_TRY(cudaStreamSynchronize(s));  // the job tables above are host vectors

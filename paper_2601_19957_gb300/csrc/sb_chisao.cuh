@@ -27,7 +27,7 @@ void launch_cs_rm_rays(int n_lost, int d, uint64_t seed, int osc, const int32_t 
 // b[j] of peak pk[j]: Philox normals (counter (pair, b d + c, osc << 16 | pk, 'GRST')) made orthonormal
 // in column order (classical Gram-Schmidt, two passes).
 void launch_cs_bases(int n_jobs, int d, uint64_t seed, int osc, const int32_t *job_pk, const int32_t *job_b,
-                     const int32_t *job_cols, const int64_t *job_off, double *Q, cudaStream_t s);
+                     const int32_t *job_cols, const int64_t *job_off, double *Q, bool fp32, cudaStream_t s);
 // Golden Rooster rays: lost sample l -> peak pk = l mod n_peaks, direction c = (l / n_peaks) / 2 with sign
 // + for even l / n_peaks, column c mod d of basis c / d; origin = the peak clamped to the box.
 void launch_cs_gr_rays(int n_lost, int d, int n_peaks, const int32_t *reps, const double *X, const double *lo,

@@ -22,11 +22,17 @@ void launch_gather_rows(int d, int cap, const double *X, const int32_t *idx, con
 void launch_precision(int d, int K, const double *L, double *P, cudaStream_t s);
 // P_k only for the components with r != 0 at some live candidate that are not
 // formed yet (done[K] is cleared by the caller before the first call).
+// onehot[c] = k when candidate c's responsibilities R[c] are exactly one-hot at k
+// (then H = P_k and its Cholesky factor is L_k), else -1; for c < cap.
+void launch_onehot(int K, const double *R, const int32_t *n_c, int cap, int32_t *onehot, cudaStream_t s);
+// P_k for the components some candidate's Hessian reads (one-hot candidates read none).
 void launch_precision_needed(int d, int K, const double *L, const double *R, const int32_t *n_c, int32_t *done,
-                             int32_t *need, double *P, cudaStream_t s);
+                             int32_t *need, double *P, cudaStream_t s, const int32_t *onehot = nullptr);
+// H and its lower Cholesky factor in place for every live candidate; with onehot,
+// the one-hot candidates take L_k as their factor (no assembly, no factorisation).
 void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P, const double *Z, const double *R,
                          const double *gbar, const int32_t *n_c, double *GK, double *H, int32_t *info,
-                         cudaStream_t s);
+                         cudaStream_t s, const int32_t *onehot = nullptr);
 // Newton step (C C^T) delta = g and g^T delta / 2 for the live candidates, over
 // nc * Gc co-resident CTAs (cooperative launch, one bounded grid barrier per
 // 32-row block and direction); nc = live candidates (host).
