@@ -18,8 +18,20 @@
  *    file-scope scratch array of sb_loglik_noalloc, which every GPU that loads
  *    the library holds until the process exits.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
- *    Work is enqueued on it. Entry points that must observe device state
- *    (noted per function) synchronise that stream before returning.
+ *    Work is enqueued on it. The solve entry points (sb_discover, sb_refine,
+ *    sb_laplace, sb_evidence, sb_chisao, sb_evidence_chisao, sb_evidence_batched)
+ *    read nothing back to the host: every count and stopping decision stays on the
+ *    device (the refinement's loop is a WHILE conditional node of a CUDA graph),
+ *    so a caller can capture them into a graph of its own. Called outside a
+ *    capture they run as a CUDA graph the library captures once per distinct set
+ *    of arguments and replays on `stream` ("graph mode"); with SB_EAGER=1 in the
+ *    environment, or while per-launch profiling is on, they run eagerly instead
+ *    (the host reads the active walker count after every 8 rounds). The first
+ *    BF16 / TF32 call per (d, K, prec) runs the tile autotuner, which
+ *    synchronises the stream: make it outside a capture (inside one, that shape
+ *    takes the heuristic tile). Entry points that must observe device state
+ *    (noted per function: host-buffer calls, sb_check, the statistics)
+ *    synchronise that stream before returning.
  *  - Argument errors are detected on the host and returned before any launch.
  *    Problems only visible on the device (non-finite parameters, lo >= hi,
  *    non-positive Cholesky diagonal, zero modes) are recorded in a status word
@@ -156,7 +168,9 @@ sb_status sb_discover(const sb_problem *prob, const sb_config *cfg, double *star
  * status_out (SB_WALKER_*). starts: [n][d]; x_out: [n][d]; ell_out: [n];
  * status_out: int8 [n]; iters_out: int32 [n] accepted steps (may be NULL);
  * n_evals: int64 device scalar, total l+grad evaluations (may be NULL).
- * Synchronises `stream` (the host polls the active-walker count).
+ * Asynchronous; the rounds run until no walker is active, decided on the device
+ * (batches of 8 rounds; at most 2 + (max_iter + 1) 2 (max_backtracks + 2) rounds,
+ * a bound no run reaches, else SB_ERR_TIMEOUT in the status word).
  */
 sb_status sb_refine(const sb_problem *prob, const sb_config *cfg, const double *starts, int32_t n, double *x_out,
                     double *ell_out, int8_t *status_out, int32_t *iters_out, int64_t *n_evals, void *ws,
@@ -173,17 +187,20 @@ sb_status sb_refine(const sb_problem *prob, const sb_config *cfg, const double *
  * sum_i log C_ii (H = C C^T), log Z = LSE_k log Z_k - log V.
  * status may be NULL (all walkers eligible). modes: [cap][d]; logZk, ell_modes:
  * [cap] (ell_modes may be NULL); n_modes: int32 device scalar; logZ: device scalar.
- * Modes are ordered by decreasing l. Synchronises `stream` once to read the
- * number of coarse candidates (it sizes the candidate kernels' grids) and once
- * per Newton step to read how many candidates still move; zero
- * modes give logZ = -inf and set SB_ERR_NO_MODES in the status word.
+ * Modes are ordered by decreasing l. Asynchronous: the candidate kernels are
+ * sized by cand_cap and read the candidate count on the device, and a Newton step
+ * after which no candidate moves leaves the remaining steps empty. At a candidate
+ * whose FP64 responsibilities are exactly one-hot (component k), H = P_k and its
+ * Cholesky factor is L_k itself (no factorisation). Zero modes give logZ = -inf
+ * and set SB_ERR_NO_MODES in the status word.
  */
 sb_status sb_laplace(const sb_problem *prob, const sb_config *cfg, const double *x, const double *ell,
                      const int8_t *status, int32_t n, double *modes, double *logZk, double *ell_modes, int32_t cap,
                      int32_t *n_modes, double *logZ, void *ws, size_t ws_bytes, void *stream);
 
 /* discover + refine + laplace on device buffers (the whole hot path).
- * logZ, n_modes: device scalars; modes [cap][d]; logZk [cap]. Synchronises `stream`. */
+ * logZ, n_modes: device scalars; modes [cap][d]; logZk [cap]. Asynchronous and
+ * capturable (see the conventions); sb_check reads the status word afterwards. */
 sb_status sb_evidence(const sb_problem *prob, const sb_config *cfg, double *logZ, double *modes, double *logZk,
                       int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes, void *stream);
 
@@ -214,12 +231,13 @@ sb_status sb_evidence_backward(const sb_problem *prob, const double *modes, cons
 
 /*
  * Many independent evidence problems (uneven d and K) in one call: problem i
- * is solved by sb_evidence on worker stream i % n_workers, each worker with
- * its own host thread and workspace slice, so the problems' kernels overlap on
- * the GPU. probs: HOST array of P problems (their arrays are device pointers);
- * logZ: device [P]; n_modes: device int32 [P]. The work starts after what is
- * already queued on `stream`; the call returns when every problem is solved.
- * Device-side conditions (e.g. zero modes) are per problem: logZ = -inf.
+ * is solved as sb_evidence does on worker stream i % n_workers (forked from and
+ * joined back into `stream`), each worker with its own workspace slice, so the
+ * problems' kernels overlap on the GPU. In graph mode the whole batch is one
+ * CUDA graph (captured once per distinct argument set, then one launch per
+ * call). probs: HOST array of P problems (their arrays are device pointers);
+ * logZ: device [P]; n_modes: device int32 [P]. Asynchronous. Device-side
+ * conditions (e.g. zero modes) are per problem: logZ = -inf.
  */
 size_t sb_evidence_batched_workspace_bytes(const sb_problem *probs, int32_t P, const sb_config *cfg,
                                            int32_t n_workers);
@@ -325,8 +343,9 @@ size_t sb_chisao_workspace_bytes(const sb_problem *prob, const sb_config *cfg);
  *       x <- x + v (v = 0 at the start), clamped to the box.
  * x0: [n][d] device; x_out: [n][d]; ell_out: [n] l after the last
  * convergence phase; stuck_out: int8 [n], 1 at the peaks; n_peaks: int32
- * device scalar. ws: sb_chisao_workspace_bytes. Synchronises `stream` (host
- * reads of the peak and list counts each oscillation, and the refinement's).
+ * device scalar. ws: sb_chisao_workspace_bytes. Asynchronous: the stick test,
+ * the lists, the branch and the Golden Rooster groups are decided on the device
+ * (the mixed path forms its Golden Rooster groups in FP32).
  */
 sb_status sb_chisao(const sb_problem *prob, const sb_config *cfg, const sb_chisao_config *cc, const double *x0,
                     int32_t n, double *x_out, double *ell_out, int8_t *stuck_out, int32_t *n_peaks, void *ws,
@@ -389,8 +408,8 @@ sb_status sb_segments(const sb_problem *prob, int32_t family, uint64_t seed, int
  * final sample (stuck or not, all eligible). The stick rule keeps only peaks within
  * log 10 of the highest, while the evidence needs every component a sample reached,
  * so the Laplace stage is not limited to the stuck peaks. Outputs as sb_evidence.
- * ws: sb_chisao_workspace_bytes. Synchronises `stream`; a device status recorded by
- * the first two stages is returned before the Laplace stage runs.
+ * ws: sb_chisao_workspace_bytes. Asynchronous and capturable; the status word
+ * collects what every stage records (sb_check).
  */
 sb_status sb_evidence_chisao(const sb_problem *prob, const sb_config *cfg, const sb_chisao_config *cc, double *logZ,
                              double *modes, double *logZk, int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes,

@@ -354,18 +354,20 @@ def segments(prob: Problem, family: int, seed: int, n_rays: int, n_steps: int, d
 
 
 def evidence_chisao(prob: Problem, cfg: _Config, cc: _ChisaoConfig, cap: Optional[int] = None, ws: Workspace = None,
-                    stream=None) -> "LaplaceOut":
-    """Discovery, the ChiSao oscillation, and the Laplace stage over every final sample."""
-    torch = _torch()
+                    stream=None, out: Optional["EvidenceBuffers"] = None, sync_check: bool = True) -> "LaplaceOut":
+    """Discovery, the ChiSao oscillation, and the Laplace stage over every final sample
+    (`out` as for evidence)."""
     ws = ws or chisao_workspace(prob, cfg)
-    cap = cap or cfg.cand_cap
-    modes = torch.empty((cap, prob.d), dtype=torch.float64, device="cuda")
-    zk = torch.empty(cap, dtype=torch.float64, device="cuda")
-    nm = torch.zeros(1, dtype=torch.int32, device="cuda")
-    lz = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out = out or EvidenceBuffers(prob.d, cap or cfg.cand_cap)
+    cap = out.cap
+    modes, zk, nm, lz = out.modes, out.zk, out.nm, out.lz
     _check(lib().sb_evidence_chisao(C.byref(prob.s), C.byref(cfg), C.byref(cc), _ptr(lz), _ptr(modes), _ptr(zk),
                                     C.c_int32(cap), _ptr(nm), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)),
            "sb_evidence_chisao")
+    if sync_check:
+        code = lib().sb_check(ws.ptr, C.c_size_t(ws.nbytes), _stream(stream))
+        if code not in (SB_OK, SB_ERR_NO_MODES):
+            raise SbError(code, "sb_evidence_chisao")
     k = min(int(nm.item()), cap)
     return LaplaceOut(float(lz.item()), modes[:k], zk[:k], None, int(nm.item()))
 
@@ -427,15 +429,28 @@ def laplace(prob: Problem, cfg: _Config, x, ell, status=None, cap: Optional[int]
     return LaplaceOut(float(lz.item()), modes[:k], zk[:k], lm[:k], int(nm.item()))
 
 
+class EvidenceBuffers:
+    """Device outputs of one evidence call (log Z, mode count, modes, log Z_k), kept
+    across calls: a call with the same problem, knobs, workspace and buffers replays
+    the library's cached graph instead of capturing a new one."""
+
+    def __init__(self, d: int, cap: int):
+        torch = _torch()
+        self.cap = int(cap)
+        self.modes = torch.zeros((cap, d), dtype=torch.float64, device="cuda")
+        self.zk = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        self.nm = torch.zeros(1, dtype=torch.int32, device="cuda")
+        self.lz = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+
 def evidence(prob: Problem, cfg: _Config, cap: Optional[int] = None, ws: Workspace = None, stream=None,
-             sync_check: bool = True) -> LaplaceOut:
-    torch = _torch()
+             sync_check: bool = True, out: Optional[EvidenceBuffers] = None) -> LaplaceOut:
+    """discover + refine + laplace. With `out`, the results are written into (and the
+    returned modes / log Z_k are views of) those buffers."""
     ws = ws or workspace(prob, cfg)
-    cap = cap or cfg.cand_cap
-    modes = torch.empty((cap, prob.d), dtype=torch.float64, device="cuda")
-    zk = torch.empty(cap, dtype=torch.float64, device="cuda")
-    nm = torch.zeros(1, dtype=torch.int32, device="cuda")
-    lz = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out = out or EvidenceBuffers(prob.d, cap or cfg.cand_cap)
+    cap = out.cap
+    modes, zk, nm, lz = out.modes, out.zk, out.nm, out.lz
     _check(lib().sb_evidence(C.byref(prob.s), C.byref(cfg), _ptr(lz), _ptr(modes), _ptr(zk), C.c_int32(cap),
                              _ptr(nm), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)), "sb_evidence")
     if sync_check:
@@ -574,16 +589,24 @@ def evidence_autograd(mu, L, log_w, lo, hi, cfg: _Config):
     return _autograd_function().apply(mu, L, log_w, lo, hi, cfg)
 
 
-def evidence_batched(problems, cfg: _Config, n_workers: int = 8, stream=None):
+def batched_workspace(problems, cfg: _Config, n_workers: int = 8) -> Workspace:
+    P = len(problems)
+    arr = (_Problem * P)(*[p.s for p in problems])
+    return Workspace(lib().sb_evidence_batched_workspace_bytes(arr, P, C.byref(cfg), int(n_workers)))
+
+
+def evidence_batched(problems, cfg: _Config, n_workers: int = 8, stream=None, ws: Workspace = None, out=None):
     """Solve many independent problems (list of Problem) in one library call.
-    Returns (logZ, n_modes) as CUDA tensors of length P."""
+    Returns (logZ, n_modes) as CUDA tensors of length P (the tensors of `out`, a
+    (logZ, n_modes) pair kept across calls, when given: with the same workspace the
+    call then replays the library's cached graph)."""
     torch = _torch()
     P = len(problems)
     arr = (_Problem * P)(*[p.s for p in problems])
-    nbytes = lib().sb_evidence_batched_workspace_bytes(arr, P, C.byref(cfg), int(n_workers))
-    ws = Workspace(nbytes)
-    logZ = torch.empty(P, dtype=torch.float64, device="cuda")
-    nm = torch.empty(P, dtype=torch.int32, device="cuda")
+    ws = ws or batched_workspace(problems, cfg, n_workers)
+    if out is None:
+        out = (torch.empty(P, dtype=torch.float64, device="cuda"), torch.empty(P, dtype=torch.int32, device="cuda"))
+    logZ, nm = out
     _check(lib().sb_evidence_batched(arr, P, C.byref(cfg), _ptr(logZ), _ptr(nm), int(n_workers), ws.ptr,
                                      C.c_size_t(ws.nbytes), _stream(stream)), "sb_evidence_batched")
     return logZ, nm

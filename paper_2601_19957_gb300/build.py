@@ -17,7 +17,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 OBJ_DIR = os.path.join(ROOT, "_build", "obj")
 LIB = os.path.join(OUT_DIR, "libsb.so")
 
-SOURCES = ["setup.cu", "lik_f64.cu", "rays.cu", "lbfgs.cu", "lbfgs_cta.cu", "laplace.cu", "tc.cu", "sb_capi.cu", "noalloc.cu", "adjoint.cu", "chisao.cu", "precheck.cu", "segments.cu", "fd.cu", "raysq.cu", "peak.cu"]
+SOURCES = ["setup.cu", "lik_f64.cu", "rays.cu", "lbfgs.cu", "lbfgs_cta.cu", "laplace.cu", "tc.cu", "sb_capi.cu", "noalloc.cu", "adjoint.cu", "chisao.cu", "precheck.cu", "segments.cu", "fd.cu", "raysq.cu", "peak.cu", "graph.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",
          "--expt-relaxed-constexpr"]

@@ -22,6 +22,10 @@ constexpr double kLogTenth = -2.302585092994045684;  // log 0.1, rounded to doub
 constexpr uint32_t kTagRm = 0x52504D4Bu;             // 'RPMK'
 constexpr uint32_t kTagGr = 0x47525354u;             // 'GRST'
 
+// Device-side oscillation state (int32 slots of the workspace).
+constexpr int kCsGrOn = 0, kCsGrUsed = 1, kCsPeaksPrev = 2, kCsBranch = 3, kCsJobs = 4;
+constexpr int kBranchNone = 0, kBranchRm = 1, kBranchGr = 2;
+
 // Golden Rooster directions come in orthonormal groups of min(d, 64).
 __host__ __device__ __forceinline__ int cs_group(int d) { return d < 64 ? d : 64; }
 
@@ -175,13 +179,14 @@ __global__ void __launch_bounds__(CS_CTA) k_cs_lists(int n, const uint8_t *lost,
     if (threadIdx.x < 3) cnt[threadIdx.x] = s_base[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(256) k_cs_rm_rays(int n_lost, int d, uint32_t k0, uint32_t k1, int osc,
-                                                    const int32_t *unconv_list, int n_unconv, const double *X,
-                                                    const double *lo, const double *hi, double *O, double *U,
-                                                    double *texit) {
+__global__ void __launch_bounds__(256) k_cs_rm_rays(int d, uint32_t k0, uint32_t k1, int osc,
+                                                    const int32_t *unconv_list, const int32_t *cnt,
+                                                    const int32_t *state, const double *X, const double *lo,
+                                                    const double *hi, double *O, double *U, double *texit) {
     const int lane = threadIdx.x & 31;
     const int l = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    if (l >= n_lost) return;
+    if (state[kCsBranch] != kBranchRm || l >= cnt[0]) return;
+    const int n_unconv = cnt[1];
     const double *src = X + (size_t)unconv_list[l % n_unconv] * d;
     double *o = O + (size_t)l * d;
     double *u = U + (size_t)l * d;
@@ -215,10 +220,11 @@ constexpr int CS_BASIS = 256;
 template <typename T>
 __global__ void __launch_bounds__(CS_BASIS) k_cs_bases(int d, uint32_t k0, uint32_t k1, int osc, const int32_t *job_pk,
                                                        const int32_t *job_b, const int32_t *job_cols,
-                                                       const int64_t *job_off, double *Q) {
+                                                       const int64_t *job_off, const int32_t *state, double *Q) {
     extern __shared__ double s_h[];  // [d] projections of the current column
     __shared__ T s_red[CS_BASIS / 32];
     const int j = blockIdx.x;
+    if (state[kCsBranch] != kBranchGr || j >= state[kCsJobs]) return;
     const int pk = job_pk[j], b = job_b[j], cols = job_cols[j];
     double *Qj = Q + job_off[j];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = CS_BASIS / 32;
@@ -280,13 +286,15 @@ __global__ void __launch_bounds__(CS_BASIS) k_cs_bases(int d, uint32_t k0, uint3
     }
 }
 
-__global__ void __launch_bounds__(256) k_cs_gr_rays(int n_lost, int d, int n_peaks, const int32_t *reps,
+__global__ void __launch_bounds__(256) k_cs_gr_rays(int d, const int32_t *n_peaks_dev, const int32_t *reps,
                                                     const double *X, const double *lo, const double *hi,
                                                     const int32_t *job_start, const int64_t *job_off, const double *Q,
-                                                    double *O, double *U, double *texit) {
+                                                    const int32_t *cnt, const int32_t *state, double *O, double *U,
+                                                    double *texit) {
     const int lane = threadIdx.x & 31;
     const int l = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    if (l >= n_lost) return;
+    if (state[kCsBranch] != kBranchGr || l >= cnt[0]) return;
+    const int n_peaks = *n_peaks_dev;
     const int pk = l % n_peaks, k = l / n_peaks, cdir = k >> 1;
     const int G = cs_group(d);
     const int b = cdir / G, col = cdir - b * G;
@@ -304,9 +312,10 @@ __global__ void __launch_bounds__(256) k_cs_gr_rays(int n_lost, int d, int n_pea
     if (lane == 0) texit[l] = t;
 }
 
-__global__ void __launch_bounds__(256) k_cs_ray_points(int l0, int nl, int n_steps, int d, const double *O,
-                                                       const double *U, const double *texit, double *P) {
-    const int64_t total = (int64_t)nl * n_steps * d;
+__global__ void __launch_bounds__(256) k_cs_ray_points(int l0, int n_steps, int d, const double *O,
+                                                       const double *U, const double *texit, const int32_t *rows,
+                                                       double *P) {
+    const int64_t total = (int64_t)(*rows) * d;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = idx / d;
@@ -317,12 +326,14 @@ __global__ void __launch_bounds__(256) k_cs_ray_points(int l0, int nl, int n_ste
     }
 }
 
-__global__ void __launch_bounds__(256) k_cs_ray_pick(int l0, int nl, int n_steps, int d, int past_valley,
-                                                     const double *ellp, const int32_t *lost_list, const double *O,
-                                                     const double *U, const double *texit, double *X) {
+__global__ void __launch_bounds__(256) k_cs_ray_pick(int l0, int n_steps, int d, const int32_t *rows,
+                                                     const int32_t *state, const double *ellp,
+                                                     const int32_t *lost_list, const double *O, const double *U,
+                                                     const double *texit, double *X) {
     const int lane = threadIdx.x & 31;
     const int r = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    if (r >= nl) return;
+    if (r >= *rows / n_steps) return;
+    const int past_valley = state[kCsBranch] == kBranchGr;
     const int l = l0 + r;
     const double *e = ellp + (size_t)r * n_steps;
     int best = 0;
@@ -367,6 +378,81 @@ __global__ void k_cs_stat_add(int64_t *dst, const int64_t *src, int64_t v) {
     if (threadIdx.x == 0) *dst += (src ? *src : 0) + v;
 }
 
+__global__ void k_cs_stat_add32(int64_t *dst, const int32_t *src, int64_t mult) {
+    if (threadIdx.x == 0) *dst += (int64_t)(*src) * mult;
+}
+
+__global__ void k_cs_state_init(int32_t *state) {
+    if (threadIdx.x == 0) {
+        state[kCsGrOn] = 1;
+        state[kCsGrUsed] = 0;
+        state[kCsPeaksPrev] = -1;
+        state[kCsBranch] = kBranchNone;
+        state[kCsJobs] = 0;
+    }
+}
+
+// After the stick test and its dedup: Golden Rooster stays off for good once an
+// oscillation that used it ends with no more peaks than the one before.
+__global__ void k_cs_osc_state(const int32_t *n_peaks, int32_t *state) {
+    if (threadIdx.x != 0) return;
+    const int peaks = *n_peaks;
+    if (state[kCsGrUsed] && peaks <= state[kCsPeaksPrev]) state[kCsGrOn] = 0;
+    state[kCsGrUsed] = 0;
+    state[kCsPeaksPrev] = peaks;
+}
+
+// The reseeding branch from the sample lists (cnt: lost, unconverged, moving): Repulse
+// Monkey with enough unconverged samples, else Golden Rooster while it is on and there
+// are peaks, else none. For Golden Rooster, the groups of orthonormal directions: lost
+// sample l uses direction c = (l / n_peaks) / 2 of peak l mod n_peaks, column c mod G of
+// group c / G (G = min(d, 64)); every group a peak needs is one job, its columns only as
+// far as used. The ray samples the branch evaluates go to stats[0].
+__global__ void k_cs_branch(const int32_t *cnt, const int32_t *n_peaks_dev, int min_unconv, int d, int n_steps,
+                            int32_t *state, int32_t *job_start, int32_t *job_pk, int32_t *job_b, int32_t *job_cols,
+                            int64_t *job_off, int64_t *stats) {
+    if (threadIdx.x != 0) return;
+    const int n_lost = cnt[0], n_unconv = cnt[1], n_peaks = *n_peaks_dev;
+    int br = kBranchNone;
+    if (n_lost > 0 && n_unconv >= min_unconv)
+        br = kBranchRm;
+    else if (n_lost > 0 && state[kCsGrOn] && n_peaks > 0)
+        br = kBranchGr;
+    state[kCsBranch] = br;
+    if (br != kBranchNone) stats[0] += (int64_t)n_lost * n_steps;
+    if (br != kBranchGr) return;
+    state[kCsGrUsed] = 1;
+    const int G = cs_group(d);
+    int nj = 0;
+    int64_t off = 0;
+    for (int p = 0; p < n_peaks; ++p) {
+        job_start[p] = nj;
+        const int count = n_lost > p ? (n_lost - p + n_peaks - 1) / n_peaks : 0;
+        if (count == 0) continue;
+        const int cmax = (count - 1) / 2;
+        for (int b = 0; b <= cmax / G; ++b) {
+            const int cols = b < cmax / G ? G : cmax - b * G + 1;
+            job_pk[nj] = p;
+            job_b[nj] = b;
+            job_cols[nj] = cols;
+            job_off[nj] = off;
+            off += (int64_t)cols * d;
+            ++nj;
+        }
+    }
+    job_start[n_peaks] = nj;
+    state[kCsJobs] = nj;
+}
+
+// Rows (ray samples) of the reseeding chunk of lost samples l0 .. l0 + lc - 1.
+__global__ void k_cs_chunk_rows(const int32_t *cnt, const int32_t *state, int l0, int lc, int n_steps,
+                                int32_t *rows) {
+    if (threadIdx.x != 0) return;
+    int nl = state[kCsBranch] != kBranchNone ? cnt[0] - l0 : 0;
+    nl = nl < 0 ? 0 : (nl > lc ? lc : nl);
+    *rows = nl * n_steps;
+}
+
 inline unsigned warp_grid(int64_t warps) { return (unsigned)((warps * 32 + 255) / 256); }
 
 }  // namespace
@@ -406,52 +492,83 @@ void launch_cs_lists(int n, const uint8_t *lost, const uint8_t *conv, const uint
     k_cs_lists<<<1, CS_CTA, 0, s>>>(n, lost, conv, stuck, status, ell, lost_list, unconv_list, moving_list, cnt);
 }
 
-void launch_cs_rm_rays(int n_lost, int d, uint64_t seed, int osc, const int32_t *unconv_list, int n_unconv,
-                       const double *X, const double *lo, const double *hi, double *O, double *U, double *texit,
-                       cudaStream_t s) {
-    if (n_lost <= 0 || n_unconv <= 0) return;
+void launch_cs_rm_rays(int n, int d, uint64_t seed, int osc, const int32_t *unconv_list, const int32_t *cnt,
+                       const int32_t *state, const double *X, const double *lo, const double *hi, double *O, double *U,
+                       double *texit, cudaStream_t s) {
+    if (n <= 0) return;
     note_launch();
-    k_cs_rm_rays<<<warp_grid(n_lost), 256, 0, s>>>(n_lost, d, (uint32_t)seed, (uint32_t)(seed >> 32), osc,
-                                                   unconv_list, n_unconv, X, lo, hi, O, U, texit);
+    k_cs_rm_rays<<<warp_grid(n), 256, 0, s>>>(d, (uint32_t)seed, (uint32_t)(seed >> 32), osc, unconv_list, cnt, state,
+                                              X, lo, hi, O, U, texit);
 }
 
-void launch_cs_bases(int n_jobs, int d, uint64_t seed, int osc, const int32_t *job_pk, const int32_t *job_b,
-                     const int32_t *job_cols, const int64_t *job_off, double *Q, bool fp32, cudaStream_t s) {
-    if (n_jobs <= 0) return;
+void launch_cs_bases(int max_jobs, int d, uint64_t seed, int osc, const int32_t *job_pk, const int32_t *job_b,
+                     const int32_t *job_cols, const int64_t *job_off, const int32_t *state, double *Q, bool fp32,
+                     cudaStream_t s) {
+    if (max_jobs <= 0) return;
     note_launch();
     if (fp32)
-        k_cs_bases<float><<<n_jobs, CS_BASIS, sizeof(double) * d, s>>>(d, (uint32_t)seed, (uint32_t)(seed >> 32), osc,
-                                                                       job_pk, job_b, job_cols, job_off, Q);
+        k_cs_bases<float><<<max_jobs, CS_BASIS, sizeof(double) * d, s>>>(
+            d, (uint32_t)seed, (uint32_t)(seed >> 32), osc, job_pk, job_b, job_cols, job_off, state, Q);
     else
-        k_cs_bases<double><<<n_jobs, CS_BASIS, sizeof(double) * d, s>>>(d, (uint32_t)seed, (uint32_t)(seed >> 32),
-                                                                        osc, job_pk, job_b, job_cols, job_off, Q);
+        k_cs_bases<double><<<max_jobs, CS_BASIS, sizeof(double) * d, s>>>(
+            d, (uint32_t)seed, (uint32_t)(seed >> 32), osc, job_pk, job_b, job_cols, job_off, state, Q);
 }
 
-void launch_cs_gr_rays(int n_lost, int d, int n_peaks, const int32_t *reps, const double *X, const double *lo,
-                       const double *hi, const int32_t *job_start, const int64_t *job_off, const double *Q, double *O,
-                       double *U, double *texit, cudaStream_t s) {
-    if (n_lost <= 0 || n_peaks <= 0) return;
+void launch_cs_gr_rays(int n, int d, const int32_t *n_peaks, const int32_t *reps, const double *X, const double *lo,
+                       const double *hi, const int32_t *job_start, const int64_t *job_off, const double *Q,
+                       const int32_t *cnt, const int32_t *state, double *O, double *U, double *texit,
+                       cudaStream_t s) {
+    if (n <= 0) return;
     note_launch();
-    k_cs_gr_rays<<<warp_grid(n_lost), 256, 0, s>>>(n_lost, d, n_peaks, reps, X, lo, hi, job_start, job_off, Q, O, U,
-                                                   texit);
+    k_cs_gr_rays<<<warp_grid(n), 256, 0, s>>>(d, n_peaks, reps, X, lo, hi, job_start, job_off, Q, cnt, state, O, U,
+                                              texit);
 }
 
-void launch_cs_ray_points(int l0, int nl, int n_steps, int d, const double *O, const double *U, const double *texit,
-                          double *P, cudaStream_t s) {
-    if (nl <= 0) return;
-    const int64_t total = (int64_t)nl * n_steps * d;
+void launch_cs_ray_points(int l0, int lc, int n_steps, int d, const double *O, const double *U, const double *texit,
+                          const int32_t *rows, double *P, cudaStream_t s) {
+    if (lc <= 0) return;
+    const int64_t total = (int64_t)lc * n_steps * d;
     int64_t blocks = (total + 255) / 256;
     if (blocks > 65535) blocks = 65535;
     note_launch();
-    k_cs_ray_points<<<(unsigned)blocks, 256, 0, s>>>(l0, nl, n_steps, d, O, U, texit, P);
+    k_cs_ray_points<<<(unsigned)blocks, 256, 0, s>>>(l0, n_steps, d, O, U, texit, rows, P);
 }
 
-void launch_cs_ray_pick(int l0, int nl, int n_steps, int d, int past_valley, const double *ellp,
-                        const int32_t *lost_list, const double *O, const double *U, const double *texit, double *X,
-                        cudaStream_t s) {
-    if (nl <= 0) return;
+void launch_cs_ray_pick(int l0, int lc, int n_steps, int d, const int32_t *rows, const int32_t *state,
+                        const double *ellp, const int32_t *lost_list, const double *O, const double *U,
+                        const double *texit, double *X, cudaStream_t s) {
+    if (lc <= 0) return;
     note_launch();
-    k_cs_ray_pick<<<warp_grid(nl), 256, 0, s>>>(l0, nl, n_steps, d, past_valley, ellp, lost_list, O, U, texit, X);
+    k_cs_ray_pick<<<warp_grid(lc), 256, 0, s>>>(l0, n_steps, d, rows, state, ellp, lost_list, O, U, texit, X);
+}
+
+void launch_cs_state_init(int32_t *state, cudaStream_t s) {
+    note_launch();
+    k_cs_state_init<<<1, 32, 0, s>>>(state);
+}
+
+void launch_cs_osc_state(const int32_t *n_peaks, int32_t *state, cudaStream_t s) {
+    note_launch();
+    k_cs_osc_state<<<1, 32, 0, s>>>(n_peaks, state);
+}
+
+void launch_cs_branch(const int32_t *cnt, const int32_t *n_peaks, int min_unconv, int d, int n_steps, int32_t *state,
+                      int32_t *job_start, int32_t *job_pk, int32_t *job_b, int32_t *job_cols, int64_t *job_off,
+                      int64_t *stats, cudaStream_t s) {
+    note_launch();
+    k_cs_branch<<<1, 32, 0, s>>>(cnt, n_peaks, min_unconv, d, n_steps, state, job_start, job_pk, job_b, job_cols,
+                                 job_off, stats);
+}
+
+void launch_cs_chunk_rows(const int32_t *cnt, const int32_t *state, int l0, int lc, int n_steps, int32_t *rows,
+                          cudaStream_t s) {
+    note_launch();
+    k_cs_chunk_rows<<<1, 32, 0, s>>>(cnt, state, l0, lc, n_steps, rows);
+}
+
+void launch_cs_stat_add32(int64_t *dst, const int32_t *src, int64_t mult, cudaStream_t s) {
+    note_launch();
+    k_cs_stat_add32<<<1, 32, 0, s>>>(dst, src, mult);
 }
 
 void launch_cs_momentum(int n, int d, const int32_t *moving_list, const int32_t *n_moving, double momentum,

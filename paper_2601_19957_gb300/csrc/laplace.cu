@@ -332,9 +332,12 @@ __global__ void k_onehot(int K, const double *R, const int32_t *n_c, int cap, in
 // candidate the lower triangle of its factor L_k instead (the blocked Cholesky skips it)
 __global__ void __launch_bounds__(256) k_hessian(int d, int K, const double *P, const double *GK, const double *R,
                                                  const double *gbar, const int32_t *n_c, const int32_t *onehot,
-                                                 const double *L, double *H) {
+                                                 const double *L, double *H, int32_t *info) {
     const int c = blockIdx.y;
     if (c >= *n_c) return;
+    // a fresh factorisation of this candidate follows (candidates past the count keep
+    // their factor and its success flag)
+    if (blockIdx.x == 0 && threadIdx.x == 0) info[c] = 0;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)d * d) return;
     const int i = (int)(e / d), i2 = (int)(e % d);
@@ -490,17 +493,19 @@ __global__ void __launch_bounds__(256) k_syrk_update(int d, int kb, double *H, c
 }
 
 // Solve (C C^T) delta = g for each candidate still polishing and the model
-// increase g^T delta / 2: Gc CTAs per candidate (cooperative launch,
-// one bounded grid barrier per 32-row block and direction). CTA (c, q) owns the
-// row blocks J with J % Gc == q. Forward (C y = g): in step I the owner of block
-// I (already updated by every earlier step, by itself) solves the diagonal block
-// and publishes y_I; after the barrier every owner subtracts C_JI y_I from its
-// blocks J > I. The owner of block I + 1 has then finished block I + 1's last
-// update before it solves it in step I + 1, so one barrier per step suffices.
-// Backward (C^T delta = y) mirrors it with (C^T)_JI = (C_IJ)^T for J < I.
-// The right-hand side lives in delta[c] (global, read past L1 after barriers).
+// increase g^T delta / 2 (cooperative launch, one bounded grid barrier per 32-row
+// block and direction). The grid is split into slots of Gc CTAs (Gc from the
+// candidate count on the device, 1 to 16); slot j serves candidates j, j + slots,
+// ... in turn, and CTA q of a slot owns the row blocks J with J % Gc == q of each.
+// Forward (C y = g): in step I the owner of block I (already updated by every
+// earlier step, by itself) solves the diagonal block and publishes y_I; after the
+// barrier every owner subtracts C_JI y_I from its blocks J > I. The owner of block
+// I + 1 has then finished block I + 1's last update before it solves it in step
+// I + 1, so one barrier per step suffices. Backward (C^T delta = y) mirrors it
+// with (C^T)_JI = (C_IJ)^T for J < I. The right-hand side lives in delta[c]
+// (global, read past L1 after barriers).
 constexpr int CS_THREADS = 256;
-__global__ void __launch_bounds__(CS_THREADS) k_chol_solve_coop(int d, int Gc, const double *H, const double *g,
+__global__ void __launch_bounds__(CS_THREADS) k_chol_solve_coop(int d, const double *H, const double *g,
                                                                 const int32_t *n_c, const int32_t *info,
                                                                 const uint8_t *active, double *delta, double *pred,
                                                                 uint32_t *bar, int32_t *err) {
@@ -508,18 +513,31 @@ __global__ void __launch_bounds__(CS_THREADS) k_chol_solve_coop(int d, int Gc, c
     __shared__ double dinv[32];
     __shared__ double xs[32];
     __shared__ double part[8];
-    const int c = blockIdx.x / Gc, q = blockIdx.x % Gc;
-    const bool live = c < *n_c && !info[c] && active[c];
+    __shared__ double red[8][33];
+    // the candidate count is the same value in every CTA, so either all CTAs leave
+    // here or all reach every grid barrier
+    const int ncand = *n_c;
+    if (ncand <= 0) return;
+    int Gc = (int)gridDim.x / ncand;
+    Gc = Gc < 1 ? 1 : (Gc > 16 ? 16 : Gc);
+    const int slots = (int)gridDim.x / Gc;
+    const int slot = blockIdx.x / Gc, q = blockIdx.x % Gc;
+    const int c0 = slot < slots ? slot : ncand;  // CTAs past the last whole slot serve nothing
     const int nb = (d + 31) / 32;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const double *C = H + (size_t)c * d * d;
-    double *y = delta + (size_t)c * d;
-    if (live)
+    auto live = [&](int c) { return !info[c] && active[c]; };
+    for (int c = c0; c < ncand; c += slots) {
+        if (!live(c)) continue;
+        double *y = delta + (size_t)c * d;
         for (int J = q; J < nb; J += Gc)
-            for (int i = J * 32 + (int)threadIdx.x; i < min(d, J * 32 + 32); i += CS_THREADS) y[i] = g[(size_t)c * d + i];
+            for (int i = J * 32 + (int)threadIdx.x; i < min(d, J * 32 + 32); i += CS_THREADS)
+                y[i] = g[(size_t)c * d + i];
+    }
     __syncthreads();
-    // the owner's diagonal solve of block I (lower: forward; upper: with C^T)
-    auto diag = [&](int I, bool upper) {
+    // the owner's diagonal solve of block I of candidate c (lower: forward; upper: with C^T)
+    auto diag = [&](int c, int I, bool upper) {
+        const double *C = H + (size_t)c * d * d;
+        double *y = delta + (size_t)c * d;
         const int r0 = I * 32, rows = min(32, d - r0);
         for (int e = threadIdx.x; e < 32 * 32; e += CS_THREADS) {
             const int i = e / 32, j = e % 32;
@@ -550,62 +568,78 @@ __global__ void __launch_bounds__(CS_THREADS) k_chol_solve_coop(int d, int Gc, c
     };
     // forward
     for (int I = 0; I < nb; ++I) {
-        if (live && I % Gc == q) diag(I, false);
+        if (I % Gc == q)
+            for (int c = c0; c < ncand; c += slots)
+                if (live(c)) diag(c, I, false);
         if (!grid_barrier(bar, gridDim.x, err)) return;
-        if (!live) continue;
         const int r0 = I * 32, rows = min(32, d - r0);
-        if (threadIdx.x < 32) xs[threadIdx.x] = threadIdx.x < rows ? __ldcg(y + r0 + threadIdx.x) : 0.0;
-        __syncthreads();
-        // y_J -= C_JI y_I for owned J > I: warp per output row
-        for (int J = I + 1; J < nb; ++J) {
-            if (J % Gc != q) continue;
-            const int j0 = J * 32, jr = min(32, d - j0);
-            for (int rr = wid; rr < jr; rr += CS_THREADS / 32) {
-                const double a = lane < rows ? C[(size_t)(j0 + rr) * d + r0 + lane] * xs[lane] : 0.0;
-                const double sum = warp_sum(a);
-                if (lane == 0) y[j0 + rr] -= sum;
+        for (int c = c0; c < ncand; c += slots) {
+            if (!live(c)) continue;
+            const double *C = H + (size_t)c * d * d;
+            double *y = delta + (size_t)c * d;
+            if (threadIdx.x < 32) xs[threadIdx.x] = threadIdx.x < rows ? __ldcg(y + r0 + threadIdx.x) : 0.0;
+            __syncthreads();
+            // y_J -= C_JI y_I for owned J > I: warp per output row
+            for (int J = I + 1; J < nb; ++J) {
+                if (J % Gc != q) continue;
+                const int j0 = J * 32, jr = min(32, d - j0);
+                for (int rr = wid; rr < jr; rr += CS_THREADS / 32) {
+                    const double a = lane < rows ? C[(size_t)(j0 + rr) * d + r0 + lane] * xs[lane] : 0.0;
+                    const double sum = warp_sum(a);
+                    if (lane == 0) y[j0 + rr] -= sum;
+                }
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
     // backward
     for (int I = nb - 1; I >= 0; --I) {
-        if (live && I % Gc == q) diag(I, true);
+        if (I % Gc == q)
+            for (int c = c0; c < ncand; c += slots)
+                if (live(c)) diag(c, I, true);
         if (!grid_barrier(bar, gridDim.x, err)) return;
-        if (!live) continue;
         const int r0 = I * 32, rows = min(32, d - r0);
-        if (threadIdx.x < 32) xs[threadIdx.x] = threadIdx.x < rows ? __ldcg(y + r0 + threadIdx.x) : 0.0;
-        __syncthreads();
-        // y_J -= (C_IJ)^T x_I for owned J < I: thread per output column j (coalesced rows of C)
-        for (int J = 0; J < I; ++J) {
-            if (J % Gc != q) continue;
-            const int j0 = J * 32;
-            // 8 warps split the 32 rows of block I; lane = column j
-            double a = 0.0;
-            for (int i = wid; i < rows; i += CS_THREADS / 32) a += C[(size_t)(r0 + i) * d + j0 + lane] * xs[i];
-            __shared__ double red[8][33];
-            red[wid][lane] = a;
+        for (int c = c0; c < ncand; c += slots) {
+            if (!live(c)) continue;
+            const double *C = H + (size_t)c * d * d;
+            double *y = delta + (size_t)c * d;
+            if (threadIdx.x < 32) xs[threadIdx.x] = threadIdx.x < rows ? __ldcg(y + r0 + threadIdx.x) : 0.0;
             __syncthreads();
-            if (wid == 0) {
-                double t = 0.0;
-                for (int w = 0; w < CS_THREADS / 32; ++w) t += red[w][lane];
-                y[j0 + lane] -= t;
+            // y_J -= (C_IJ)^T x_I for owned J < I: thread per output column j (coalesced rows of C)
+            for (int J = 0; J < I; ++J) {
+                if (J % Gc != q) continue;
+                const int j0 = J * 32;
+                // 8 warps split the 32 rows of block I; lane = column j
+                double a = 0.0;
+                for (int i = wid; i < rows; i += CS_THREADS / 32) a += C[(size_t)(r0 + i) * d + j0 + lane] * xs[i];
+                red[wid][lane] = a;
+                __syncthreads();
+                if (wid == 0) {
+                    double t = 0.0;
+                    for (int w = 0; w < CS_THREADS / 32; ++w) t += red[w][lane];
+                    y[j0 + lane] -= t;
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
     if (!grid_barrier(bar, gridDim.x, err)) return;
-    // model increase of l along the Newton step: g^T delta / 2 (first CTA of the candidate)
-    if (!live || q != 0) return;
-    double gd = 0.0;
-    for (int i = threadIdx.x; i < d; i += CS_THREADS) gd += g[(size_t)c * d + i] * __ldcg(y + i);
-    gd = warp_sum(gd);
-    if (lane == 0) part[wid] = gd;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < CS_THREADS / 32; ++w) t += part[w];
-        pred[c] = 0.5 * t;
+    // model increase of l along the Newton step: g^T delta / 2 (first CTA of the slot)
+    if (q != 0) return;
+    for (int c = c0; c < ncand; c += slots) {
+        if (!live(c)) continue;
+        const double *y = delta + (size_t)c * d;
+        double gd = 0.0;
+        for (int i = threadIdx.x; i < d; i += CS_THREADS) gd += g[(size_t)c * d + i] * __ldcg(y + i);
+        gd = warp_sum(gd);
+        if (lane == 0) part[wid] = gd;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < CS_THREADS / 32; ++w) t += part[w];
+            pred[c] = 0.5 * t;
+        }
+        __syncthreads();
     }
 }
 
@@ -876,8 +910,8 @@ void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P
     k_comp_grads<<<dim3(cap, K, kGradSlices), 256, sizeof(double) * d, s>>>(d, K, L, Z, R, n_c, GK);
     const int64_t dd = (int64_t)d * d;
     note_launch();
-    k_hessian<<<dim3((unsigned)((dd + 255) / 256), cap), 256, 0, s>>>(d, K, P, GK, R, gbar, n_c, onehot, L, H);
-    cudaMemsetAsync(info, 0, sizeof(int32_t) * cap, s);
+    k_hessian<<<dim3((unsigned)((dd + 255) / 256), cap), 256, 0, s>>>(d, K, P, GK, R, gbar, n_c, onehot, L, H,
+                                                                        info);
     const int nblk = (d + NB - 1) / NB;
     ProfScope prof(PROF_CHOLESKY, s);
     for (int kb = 0; kb < nblk; ++kb) {
@@ -893,18 +927,36 @@ void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P
     }
 }
 
-void launch_chol_solve_coop(int d, int nc, const double *H, const double *g, const int32_t *n_c, const int32_t *info,
+int laplace_sms() {
+    static const int n = [] {  // thread-safe one-time query
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
+    return n;
+}
+
+void launch_chol_solve_coop(int d, int cap, const double *H, const double *g, const int32_t *n_c, const int32_t *info,
                             const uint8_t *active, double *delta, double *pred, uint32_t *bar, int32_t *err,
                             cudaStream_t s) {
-    // CTAs per candidate: enough to spread the updates, few enough for one wave
-    int Gc = 144 / (nc > 0 ? nc : 1);
-    if (Gc > 16) Gc = 16;
-    if (Gc < 1) Gc = 1;
-    int G = nc * Gc;
+    // one CTA per SM at most (a cooperative grid must be co-resident), up to 16 per
+    // candidate of the cap; the kernel divides them among the live candidates
+    int G = laplace_sms();
+    if (G > 16 * cap) G = 16 * cap;
     cudaMemsetAsync(bar, 0, 2 * sizeof(uint32_t), s);
-    void *args[] = {&d, &Gc, &H, &g, &n_c, &info, &active, &delta, &pred, &bar, &err};
+    void *args[] = {&d, &H, &g, &n_c, &info, &active, &delta, &pred, &bar, &err};
     note_launch();
     cudaLaunchCooperativeKernel((const void *)k_chol_solve_coop, dim3(G), dim3(CS_THREADS), args, 0, s);
+}
+
+__global__ void k_set_eff(int32_t *n_eff, const int32_t *n_reps, const int32_t *n_live) {
+    if (threadIdx.x == 0) *n_eff = (!n_live || *n_live > 0) ? *n_reps : 0;
+}
+
+void launch_set_eff(int32_t *n_eff, const int32_t *n_reps, const int32_t *n_live, cudaStream_t s) {
+    note_launch();
+    k_set_eff<<<1, 32, 0, s>>>(n_eff, n_reps, n_live);
 }
 
 void launch_newton_ls(int d, int cap, int mode, const int32_t *n_c, const int32_t *info, uint8_t *active,

@@ -5,8 +5,8 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
-#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -20,6 +20,7 @@
 #include "sb_laplace.cuh"
 #include "sb_lbfgs.cuh"
 #include "sb_tc.cuh"
+#include "sb_graph.cuh"
 
 using namespace sb;
 
@@ -166,6 +167,7 @@ struct RefineWs {
     LbfgsArgs<T> lb;
     float *MRI, *MYY;  // [N][m][m] R^-1 (R = upper(S^T Y)) and Y^T Y, slot-indexed (FP32 compact-form step)
     int64_t *n_evals;
+    int64_t *round;         // rounds run (device-decided loop)
     double *qpart, *Z, *R;  // FP64 evaluation
     TcWs tc;                // mixed-precision evaluation
 };
@@ -180,6 +182,7 @@ struct LaplaceWs {
     int32_t *p_done, *p_need;  // [K] P_k formed / to form now
     int32_t *n_live;           // candidates still moving in a Newton step
     int32_t *onehot;           // [cap] component k when a candidate's responsibilities are one-hot, else -1
+    int32_t *n_eff;            // candidates a Newton step's evaluations run on (0 once none moves)
 };
 
 struct EvidenceWs {
@@ -221,6 +224,7 @@ void carve_refine(Carver &cv, RefineWs<T> &r, int n, int d, int K, int m, bool f
     a.act = cv.take<int32_t>((size_t)n);
     a.n_act = cv.take<int32_t>(1);
     r.n_evals = cv.take<int64_t>(1);
+    r.round = cv.take<int64_t>(1);
     if (fp64_eval) {
         r.qpart = cv.take<double>(lik_f64_qpart_elems(d, K, n));
         r.Z = cv.take<double>((size_t)n * K * d);
@@ -283,6 +287,7 @@ Layout layout(void *base, const sb_problem *p, const sb_config *c) {
     la.p_need = cv.take<int32_t>(kMaxK);
     la.n_live = cv.take<int32_t>(1);
     la.onehot = cv.take<int32_t>(cap);
+    la.n_eff = cv.take<int32_t>(1);
     la.XC = cv.take<double>((size_t)cap * d);
     la.LC = cv.take<double>(cap);
     la.GC = cv.take<double>((size_t)cap * d);
@@ -452,64 +457,37 @@ sb_status run_refine(const ProbView &pv, const sb_config *c, const RefineWs<T> &
     int64_t *ev = n_evals ? n_evals : r.n_evals;
     launch_lbfgs_init<T>(n, pv.d, starts, a, ev, s);
     if constexpr (std::is_same<T, float>::value) tc_walkers_reset(r.tc, n, s);
-    // every accepted step takes at most 2 (max_backtracks + 1) rounds
+    // every accepted step takes at most 2 (max_backtracks + 2) rounds
     const int64_t cap_rounds = 2 + (int64_t)(c->max_iter + 1) * 2 * (c->max_backtracks + 2);
-    int64_t round = 0;
-    // Small problems are launch-bound: capture one batch of rounds into a CUDA
-    // graph and replay it. Large ones keep direct launches (their kernels take
-    // far longer than a launch, and the per-kernel profiling stays available).
-    const bool use_graph = (int64_t)pv.d * n <= ((int64_t)1 << 20);
-    cudaGraphExec_t ge = nullptr;
-    int64_t per_batch = 0;
-    if (use_graph) {
-        // The caller's stream may be the legacy default stream, which cannot be
-        // captured: record on a private stream and replay the graph on the caller's.
-        cudaStream_t cs = nullptr;
-        SB_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t g = nullptr;
-        const int64_t before = sb_launch_count();
-        cudaError_t ec = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (ec == cudaSuccess) {
-            for (int b = 0; b < kRoundsPerPoll; ++b) {
-                eval_round<T>(pv, c, rr, n, cs);
-                step_round<T>(rr, a, n, cs);
-                launch_lbfgs_compact<T>(a, ev, cs);
-            }
-            ec = cudaStreamEndCapture(cs, &g);
+    auto batch = [&](cudaStream_t bs) {
+        for (int b = 0; b < kRoundsPerPoll; ++b) {
+            eval_round<T>(pv, c, rr, n, bs);
+            step_round<T>(rr, a, n, bs);
+            launch_lbfgs_compact<T>(a, ev, bs);
         }
-        per_batch = sb_launch_count() - before;
-        note_launch(-per_batch);  // counted per replay below
-        cudaStreamDestroy(cs);
-        if (ec != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            return SB_ERR_CUDA;
+    };
+    if (stream_capturing(s)) {
+        // the rounds as the body of a WHILE node whose condition the device sets after
+        // every batch (walkers still active and the round cap not reached)
+        SB_CUDA_TRY(cudaMemsetAsync(r.round, 0, sizeof(int64_t), s));
+        const sb_status st = capture_while(s, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
+            batch(bs);
+            launch_loop_cond(h, r.round, kRoundsPerPoll, cap_rounds, a.n_act, pv.status, bs);
+            return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
+        });
+        if (st != SB_OK) return st;
+    } else {
+        // eager: the host reads the active count after every batch of rounds
+        int64_t round = 0;
+        while (true) {
+            batch(s);
+            round += kRoundsPerPoll;
+            int32_t h_act = 0;
+            SB_CUDA_TRY(cudaMemcpyAsync(&h_act, a.n_act, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            SB_CUDA_TRY(cudaStreamSynchronize(s));
+            if (h_act == 0 || round >= cap_rounds) break;
         }
-        cudaGraphDestroy(g);
     }
-    while (true) {
-        if (ge) {
-            if (cudaGraphLaunch(ge, s) != cudaSuccess) {
-                cudaGraphExecDestroy(ge);
-                return SB_ERR_CUDA;
-            }
-            note_launch(per_batch);
-        } else {
-            for (int b = 0; b < kRoundsPerPoll; ++b) {
-                eval_round<T>(pv, c, rr, n, s);
-                step_round<T>(rr, a, n, s);
-                launch_lbfgs_compact<T>(a, ev, s);
-            }
-        }
-        round += kRoundsPerPoll;
-        int32_t h_act = 0;
-        if (cudaMemcpyAsync(&h_act, a.n_act, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
-            if (ge) cudaGraphExecDestroy(ge);
-            return SB_ERR_CUDA;
-        }
-        if (h_act == 0 || round >= cap_rounds) break;
-    }
-    if (ge) cudaGraphExecDestroy(ge);
     launch_lbfgs_finish<T>(n, pv.d, a, x_out, ell_out, status_out, iters_out, pv.status, s);
     SB_CUDA_TRY(cudaGetLastError());
     return SB_OK;
@@ -543,50 +521,42 @@ sb_status run_laplace(const ProbView &pv, const sb_config *c, const Layout &L, c
     launch_dedup(n, d, x, ell, status, nullptr, c->dedup_coarse, pv.wmax, cap, la.reps, la.n_reps, la.assigned, dds,
                  s);
     launch_gather_rows(d, cap, x, la.reps, la.n_reps, la.XC, ell, la.LC, s);
-    // The candidate kernels below take one CTA (or a grid slice) per candidate;
-    // sizing their grids by the live count instead of cand_cap spares launching
-    // and retiring the idle blocks (most of a launch when two candidates of 256
-    // remain). The kernels still read the count on the device.
-    int32_t h_reps = 0;
-    SB_CUDA_TRY(cudaMemcpyAsync(&h_reps, la.n_reps, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    SB_CUDA_TRY(cudaStreamSynchronize(s));
-    const int nc = h_reps < 1 ? 1 : (h_reps > cap ? cap : h_reps);
-    SB_CUDA_TRY(cudaMemsetAsync(la.active, 1, nc, s));
-    // l, grad l, H and its Cholesky factor at every candidate
-    auto eval_full = [&]() {
-        f64_points(pv, la.XC, nullptr, la.n_reps, nc, la.qpart, la.Z, la.R, la.LC, la.GC, s);
-        launch_onehot(K, la.R, la.n_reps, nc, la.onehot, s);
-        launch_precision_needed(d, K, pv.L, la.R, la.n_reps, la.p_done, la.p_need, la.P, s, la.onehot);
-        launch_hessian_chol(d, K, nc, pv.L, la.P, la.Z, la.R, la.GC, la.n_reps, la.GK, la.H, la.info, s,
-                            la.onehot);
+    // Every candidate kernel below is sized by cand_cap and reads the candidate count
+    // (n_reps, or n_eff inside a Newton step) on the device: no host read, so the
+    // stage can sit in a captured graph.
+    SB_CUDA_TRY(cudaMemsetAsync(la.active, 1, cap, s));
+    // l, grad l, H and its Cholesky factor at every candidate (of the first *nc)
+    auto eval_full = [&](const int32_t *nc) {
+        f64_points(pv, la.XC, nullptr, nc, cap, la.qpart, la.Z, la.R, la.LC, la.GC, s);
+        launch_onehot(K, la.R, nc, cap, la.onehot, s);
+        launch_precision_needed(d, K, pv.L, la.R, nc, la.p_done, la.p_need, la.P, s, la.onehot);
+        launch_hessian_chol(d, K, cap, pv.L, la.P, la.Z, la.R, la.GC, nc, la.GK, la.H, la.info, s, la.onehot);
     };
-    eval_full();
-    // Newton polish, at most newton_steps steps; it ends early once every
-    // candidate's step is below the convergence threshold (one host read of the
-    // count of candidates still moving per step)
+    eval_full(la.n_reps);
+    // Newton polish, newton_steps steps; a step's evaluations run on n_eff candidates,
+    // which drops to zero once no candidate's Newton step is above the convergence
+    // threshold (the rest of the polish is then empty launches)
+    launch_set_eff(la.n_eff, la.n_reps, nullptr, s);
     for (int step = 0; step < c->newton_steps; ++step) {
-        launch_chol_solve_coop(d, nc, la.H, la.GC, la.n_reps, la.info, la.active, la.delta, la.pred, la.dd_bar,
+        launch_chol_solve_coop(d, cap, la.H, la.GC, la.n_eff, la.info, la.active, la.delta, la.pred, la.dd_bar,
                                pv.status, s);
         SB_CUDA_TRY(cudaMemsetAsync(la.n_live, 0, sizeof(int32_t), s));
-        launch_newton_ls(d, nc, 0, la.n_reps, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
+        launch_newton_ls(d, cap, 0, la.n_eff, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
                          la.delta, la.XN, la.LN, la.pred, la.n_live, s);
-        int32_t h_live = 0;
-        SB_CUDA_TRY(cudaMemcpyAsync(&h_live, la.n_live, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        SB_CUDA_TRY(cudaStreamSynchronize(s));
-        if (h_live == 0) break;
-        f64_points(pv, la.XN, nullptr, la.n_reps, nc, la.qpart, nullptr, nullptr, la.LN, nullptr, s);
-        launch_newton_ls(d, nc, 1, la.n_reps, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
+        launch_set_eff(la.n_eff, la.n_reps, la.n_live, s);
+        f64_points(pv, la.XN, nullptr, la.n_eff, cap, la.qpart, nullptr, nullptr, la.LN, nullptr, s);
+        launch_newton_ls(d, cap, 1, la.n_eff, la.info, la.active, la.searching, la.halvings, la.t, la.XC, la.LC,
                          la.delta, la.XN, la.LN, la.pred, la.n_live, s);
-        launch_ls_batch_setup(d, nc, la.n_reps, la.searching, la.XC, la.delta, la.XN2, la.rows2, la.n_rows2, s);
-        f64_points(pv, la.XN2, la.rows2, la.n_rows2, nc * (kHalvings - 1), la.qpart2, nullptr, nullptr, la.LN2,
+        launch_ls_batch_setup(d, cap, la.n_eff, la.searching, la.XC, la.delta, la.XN2, la.rows2, la.n_rows2, s);
+        f64_points(pv, la.XN2, la.rows2, la.n_rows2, cap * (kHalvings - 1), la.qpart2, nullptr, nullptr, la.LN2,
                    nullptr, s);
-        launch_ls_batch_decide(d, nc, la.n_reps, la.searching, la.active, la.XC, la.LC, la.XN2, la.LN2, s);
-        eval_full();
+        launch_ls_batch_decide(d, cap, la.n_eff, la.searching, la.active, la.XC, la.LC, la.XN2, la.LN2, s);
+        eval_full(la.n_eff);
     }
     SB_CUDA_TRY(cudaMemsetAsync(la.keep, 0, cap, s));
-    launch_cand_stats(d, nc, la.XC, la.LC, la.GC, la.H, la.info, pv.lo, pv.hi, c->eps_grad, la.n_reps, la.keep,
+    launch_cand_stats(d, cap, la.XC, la.LC, la.GC, la.H, la.info, pv.lo, pv.hi, c->eps_grad, la.n_reps, la.keep,
                       la.logZk_c, s);
-    launch_dedup(nc, d, la.XC, la.LC, nullptr, la.keep, c->dedup_tol, pv.wmax, cap, la.reps2, la.n_reps2,
+    launch_dedup(cap, d, la.XC, la.LC, nullptr, la.keep, c->dedup_tol, pv.wmax, cap, la.reps2, la.n_reps2,
                  la.assigned, dds, s);
     launch_laplace_final(d, la.XC, la.LC, la.logZk_c, la.n_reps, la.reps2, la.n_reps2, pv.logV, cap_out, modes, logZk,
                          ell_modes, n_modes, logZ, pv.status, s);
@@ -629,6 +599,35 @@ sb_status prelude(const sb_problem *p, const sb_config *c, void *ws, size_t ws_b
     return SB_OK;
 }
 
+// Host-side checks of a solve call (the size of the workspace included).
+sb_status check_call(const sb_problem *p, const sb_config *c, const void *ws, size_t ws_bytes, bool chisao);
+
+// Key of a graph-mode call: the entry point, the problem's shape and arrays, the knobs
+// and the workspace (the caller adds its own outputs).
+GraphKey call_key(int fn, const sb_problem *p, const sb_config *c, const void *ws, size_t ws_bytes) {
+    GraphKey k;
+    k.add((uint64_t)fn);
+    k.add((uint64_t)p->d);
+    k.add((uint64_t)p->K);
+    for (const void *q : {(const void *)p->log_w, (const void *)p->mu, (const void *)p->L, (const void *)p->lo,
+                          (const void *)p->hi})
+        k.add_ptr(q);
+    k.add_bytes(*c);
+    k.add_ptr(ws);
+    k.add((uint64_t)ws_bytes);
+    return k;
+}
+
+// Before a graph-mode capture of a mixed-precision call whose shape the tile autotuner
+// has not seen: one eager prelude on the caller's stream, which times the tiles (the
+// capture itself cannot synchronise).
+void pretune(const sb_problem *p, const sb_config *c, void *ws, size_t ws_bytes, cudaStream_t s) {
+    if (c->prec == SB_PREC_FP64 || stream_capturing(s) || !graph_mode_for(s)) return;
+    if (tc_tuned_tile(p->d, p->K, c->prec) != 0) return;
+    Prelude P;
+    (void)prelude(p, c, ws, ws_bytes, s, P);
+}
+
 }  // namespace
 
 extern "C" size_t sb_workspace_bytes(const sb_problem *p, const sb_config *c) {
@@ -650,12 +649,23 @@ extern "C" sb_status sb_refine(const sb_problem *p, const sb_config *c, const do
                                int64_t *n_evals, void *ws, size_t ws_bytes, void *stream) {
     if (!starts || !x_out || !ell_out || !status_out) return SB_ERR_INVALID_ARG;
     if (!c || n < 1 || n > c->n_starts) return SB_ERR_INVALID_ARG;
-    Prelude P;
-    sb_status st = prelude(p, c, ws, ws_bytes, stream, P);
+    sb_status st = check_call(p, c, ws, ws_bytes, false);
     if (st != SB_OK) return st;
-    if (c->prec == SB_PREC_FP64)
-        return run_refine<double>(P.pv, c, P.L.r64, starts, n, x_out, ell_out, status_out, iters_out, n_evals, P.s);
-    return run_refine<float>(P.pv, c, P.L.r32, starts, n, x_out, ell_out, status_out, iters_out, n_evals, P.s);
+    cudaStream_t s0 = static_cast<cudaStream_t>(stream);
+    GraphKey key = call_key(3, p, c, ws, ws_bytes);
+    for (const void *q : {(const void *)starts, (const void *)x_out, (const void *)ell_out, (const void *)status_out,
+                          (const void *)iters_out, (const void *)n_evals})
+        key.add_ptr(q);
+    key.add((uint64_t)n);
+    pretune(p, c, ws, ws_bytes, s0);
+    return run_graph_or_direct(s0, key, [&](cudaStream_t s) {
+        Prelude P;
+        sb_status r = prelude(p, c, ws, ws_bytes, s, P);
+        if (r != SB_OK) return r;
+        if (c->prec == SB_PREC_FP64)
+            return run_refine<double>(P.pv, c, P.L.r64, starts, n, x_out, ell_out, status_out, iters_out, n_evals, s);
+        return run_refine<float>(P.pv, c, P.L.r32, starts, n, x_out, ell_out, status_out, iters_out, n_evals, s);
+    });
 }
 
 extern "C" sb_status sb_laplace(const sb_problem *p, const sb_config *c, const double *x, const double *ell,
@@ -670,25 +680,41 @@ extern "C" sb_status sb_laplace(const sb_problem *p, const sb_config *c, const d
     return run_laplace(P.pv, c, P.L, x, ell, status, n, modes, logZk, ell_modes, cap, n_modes, logZ, P.s);
 }
 
+// discover + refine + laplace on one prelude (the whole hot path), no host read.
+static sb_status enqueue_evidence(const sb_problem *p, const sb_config *c, double *logZ, double *modes, double *logZk,
+                           int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes, cudaStream_t s) {
+    Prelude P;
+    sb_status st = prelude(p, c, ws, ws_bytes, s, P);
+    if (st != SB_OK) return st;
+    const auto &ev = P.L.ev;
+    st = run_discover(P.pv, c, P.L, ev.starts, ev.ell_starts, s);
+    if (st != SB_OK) return st;
+    if (c->prec == SB_PREC_FP64)
+        st = run_refine<double>(P.pv, c, P.L.r64, ev.starts, c->n_starts, ev.x_out, ev.ell_out, ev.status, nullptr,
+                                nullptr, s);
+    else
+        st = run_refine<float>(P.pv, c, P.L.r32, ev.starts, c->n_starts, ev.x_out, ev.ell_out, ev.status, nullptr,
+                               nullptr, s);
+    if (st != SB_OK) return st;
+    return run_laplace(P.pv, c, P.L, ev.x_out, ev.ell_out, ev.status, c->n_starts, modes, logZk, nullptr, cap,
+                       n_modes, logZ, s);
+}
+
 extern "C" sb_status sb_evidence(const sb_problem *p, const sb_config *c, double *logZ, double *modes,
                                  double *logZk, int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes,
                                  void *stream) {
     if (!logZ || !modes || !logZk || !n_modes || cap < 1) return SB_ERR_INVALID_ARG;
-    Prelude P;
-    sb_status st = prelude(p, c, ws, ws_bytes, stream, P);
+    sb_status st = check_call(p, c, ws, ws_bytes, false);
     if (st != SB_OK) return st;
-    const auto &ev = P.L.ev;
-    st = run_discover(P.pv, c, P.L, ev.starts, ev.ell_starts, P.s);
-    if (st != SB_OK) return st;
-    if (c->prec == SB_PREC_FP64)
-        st = run_refine<double>(P.pv, c, P.L.r64, ev.starts, c->n_starts, ev.x_out, ev.ell_out, ev.status, nullptr,
-                                nullptr, P.s);
-    else
-        st = run_refine<float>(P.pv, c, P.L.r32, ev.starts, c->n_starts, ev.x_out, ev.ell_out, ev.status, nullptr,
-                               nullptr, P.s);
-    if (st != SB_OK) return st;
-    return run_laplace(P.pv, c, P.L, ev.x_out, ev.ell_out, ev.status, c->n_starts, modes, logZk, nullptr, cap,
-                       n_modes, logZ, P.s);
+    cudaStream_t s0 = static_cast<cudaStream_t>(stream);
+    GraphKey key = call_key(4, p, c, ws, ws_bytes);
+    for (const void *q : {(const void *)logZ, (const void *)modes, (const void *)logZk, (const void *)n_modes})
+        key.add_ptr(q);
+    key.add((uint64_t)cap);
+    pretune(p, c, ws, ws_bytes, s0);
+    return run_graph_or_direct(s0, key, [&](cudaStream_t s) {
+        return enqueue_evidence(p, c, logZ, modes, logZk, cap, n_modes, ws, ws_bytes, s);
+    });
 }
 
 extern "C" sb_status sb_check(void *ws, size_t ws_bytes, void *stream) {
@@ -981,6 +1007,31 @@ extern "C" size_t sb_evidence_batched_workspace_bytes(const sb_problem *probs, i
     return (size_t)w * batched_slice_bytes(probs, P, c);
 }
 
+namespace {
+// Worker streams and fork / join events of this host thread (created once per device).
+struct Workers {
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+};
+Workers *workers_for(int W) {
+    thread_local std::map<int, Workers> pools;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    Workers &wk = pools[dev];
+    if (!wk.fork && cudaEventCreateWithFlags(&wk.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    while ((int)wk.streams.size() < W) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        wk.streams.push_back(st);
+        wk.joins.push_back(ev);
+    }
+    return &wk;
+}
+}  // namespace
+
 extern "C" sb_status sb_evidence_batched(const sb_problem *probs, int32_t P, const sb_config *c, double *logZ,
                                          int32_t *n_modes, int32_t n_workers, void *ws, size_t ws_bytes,
                                          void *stream) {
@@ -991,51 +1042,48 @@ extern "C" sb_status sb_evidence_batched(const sb_problem *probs, int32_t P, con
         st = check_problem(&probs[i]);
         if (st != SB_OK) return st;
     }
+    if (c->prec != SB_PREC_FP64 && !tc_available(c->prec)) return SB_ERR_UNSUPPORTED;
     const int32_t W = n_workers < P ? n_workers : P;
     const size_t slice = batched_slice_bytes(probs, P, c);
     if (ws_bytes < (size_t)W * slice) return SB_ERR_WORKSPACE;
-    cudaStream_t caller = static_cast<cudaStream_t>(stream);
-    int dev = 0;
-    SB_CUDA_TRY(cudaGetDevice(&dev));
-    cudaEvent_t ready;
-    SB_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-    SB_CUDA_TRY(cudaEventRecord(ready, caller));
-    std::vector<sb_status> res(W, SB_OK);
-    std::vector<std::thread> pool;
-    for (int32_t w = 0; w < W; ++w) {
-        pool.emplace_back([&, w]() {
-            cudaSetDevice(dev);
-            cudaStream_t s;
-            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-                res[w] = SB_ERR_CUDA;
-                return;
-            }
-            cudaStreamWaitEvent(s, ready, 0);
+    int dmax = 1;
+    for (int32_t i = 0; i < P; ++i) dmax = probs[i].d > dmax ? probs[i].d : dmax;
+    cudaStream_t s0 = static_cast<cudaStream_t>(stream);
+    Workers *wk = workers_for(W);
+    if (!wk) return SB_ERR_CUDA;
+    // the tile autotuner times each new shape once, outside the capture, on the slice of
+    // the worker that will solve it
+    for (int32_t i = 0; i < P; ++i) pretune(&probs[i], c, static_cast<char *>(ws) + (size_t)(i % W) * slice, slice, s0);
+    GraphKey key;
+    key.add(5);
+    key.add((uint64_t)P);
+    key.add((uint64_t)W);
+    for (int32_t i = 0; i < P; ++i) key.add_bytes(probs[i]);
+    key.add_bytes(*c);
+    for (const void *q : {(const void *)logZ, (const void *)n_modes, (const void *)ws}) key.add_ptr(q);
+    key.add((uint64_t)ws_bytes);
+    // problem i on worker i % W, in order (the worker's problems share its workspace
+    // slice); the workers fork from the caller's stream and join back into it
+    return run_graph_or_direct(s0, key, [&](cudaStream_t s) {
+        SB_CUDA_TRY(cudaEventRecord(wk->fork, s));
+        for (int32_t w = 0; w < W; ++w) SB_CUDA_TRY(cudaStreamWaitEvent(wk->streams[w], wk->fork, 0));
+        for (int32_t i = 0; i < P; ++i) {
+            const int32_t w = i % W;
             char *base = static_cast<char *>(ws) + (size_t)w * slice;
             Carver cv(base);
-            int dmax = 1;
-            for (int32_t i = 0; i < P; ++i) dmax = probs[i].d > dmax ? probs[i].d : dmax;
             double *modes = cv.take<double>((size_t)c->cand_cap * dmax);
             double *zk = cv.take<double>((size_t)c->cand_cap);
             void *inner = base + cv.bytes();
-            const size_t inner_bytes = slice - cv.bytes();
-            for (int32_t i = w; i < P; i += W) {
-                const sb_status r = sb_evidence(&probs[i], c, logZ + i, modes, zk, c->cand_cap, n_modes + i, inner,
-                                                inner_bytes, s);
-                if (r != SB_OK) {
-                    res[w] = r;
-                    break;
-                }
-            }
-            cudaStreamSynchronize(s);
-            cudaStreamDestroy(s);
-        });
-    }
-    for (auto &t : pool) t.join();
-    cudaEventDestroy(ready);
-    for (auto r : res)
-        if (r != SB_OK) return r;
-    return SB_OK;
+            const sb_status r = enqueue_evidence(&probs[i], c, logZ + i, modes, zk, c->cand_cap, n_modes + i, inner,
+                                                 slice - cv.bytes(), wk->streams[w]);
+            if (r != SB_OK) return r;
+        }
+        for (int32_t w = 0; w < W; ++w) {
+            SB_CUDA_TRY(cudaEventRecord(wk->joins[w], wk->streams[w]));
+            SB_CUDA_TRY(cudaStreamWaitEvent(s, wk->joins[w], 0));
+        }
+        return SB_OK;
+    });
 }
 
 extern "C" int32_t sb_tuned_tile(int32_t d, int32_t K, int32_t prec) { return tc_tuned_tile(d, K, prec); }
@@ -1052,6 +1100,8 @@ struct ChisaoWs {
     int32_t *job_start, *job_pk, *job_b, *job_cols;
     int64_t *job_off;
     int64_t *stats;  // [4] l-only ray evaluations, L-BFGS l+grad, anti-convergence l+grad, -
+    int32_t *state;  // [8] the oscillations' device-side state (see launch_cs_state_init)
+    int32_t *rows;   // ray samples of the current reseeding chunk
     int lc;  // lost samples per chunk of ray samples
     size_t bytes;
 };
@@ -1091,6 +1141,8 @@ ChisaoWs chisao_layout(void *base, size_t off, const sb_problem *p, const sb_con
     w.job_cols = cv.take<int32_t>(n);
     w.job_off = cv.take<int64_t>(n);
     w.stats = cv.take<int64_t>(4);
+    w.state = cv.take<int32_t>(8);
+    w.rows = cv.take<int32_t>(1);
     if (c->prec != SB_PREC_FP64) {
         w.O32 = cv.take<float>((size_t)n * d);
         w.U32 = cv.take<float>((size_t)n * d);
@@ -1108,37 +1160,20 @@ sb_status check_chisao(const sb_chisao_config *cc) {
     return SB_OK;
 }
 
-// Golden Rooster groups for n_lost lost samples over n_peaks peaks: lost sample l uses
-// direction c = (l / n_peaks) / 2 of peak l mod n_peaks, i.e. column c mod G of
-// orthonormal group c / G, G = min(d, 64); every group a peak needs is one job, its
-// columns only as far as used.
-struct GrJobs {
-    std::vector<int32_t> start, pk, b, cols;
-    std::vector<int64_t> off;
-};
-GrJobs gr_jobs(int n_lost, int n_peaks, int d) {
-    GrJobs j;
-    j.start.assign((size_t)n_peaks + 1, 0);
-    int64_t off = 0;
-    for (int p = 0; p < n_peaks; ++p) {
-        j.start[p] = (int32_t)j.pk.size();
-        const int count = n_lost > p ? (n_lost - p + n_peaks - 1) / n_peaks : 0;
-        if (count == 0) continue;
-        const int cmax = (count - 1) / 2;
-        const int G = d < 64 ? d : 64;
-        for (int b = 0; b <= cmax / G; ++b) {
-            const int cols = b < cmax / G ? G : cmax - b * G + 1;
-            j.pk.push_back(p);
-            j.b.push_back(b);
-            j.cols.push_back(cols);
-            j.off.push_back(off);
-            off += (int64_t)cols * d;
-        }
-    }
-    j.start[n_peaks] = (int32_t)j.pk.size();
-    return j;
-}
+}  // namespace
 
+namespace {
+sb_status check_call(const sb_problem *p, const sb_config *c, const void *ws, size_t ws_bytes, bool chisao) {
+    sb_status st = check_problem(p);
+    if (st != SB_OK) return st;
+    st = check_config(c);
+    if (st != SB_OK) return st;
+    if (!ws) return SB_ERR_INVALID_ARG;
+    if (c->prec != SB_PREC_FP64 && !tc_available(c->prec)) return SB_ERR_UNSUPPORTED;
+    size_t need = layout(nullptr, p, c).bytes;
+    if (chisao) need += chisao_layout(nullptr, need, p, c).bytes;
+    return ws_bytes < need ? SB_ERR_WORKSPACE : SB_OK;
+}
 }  // namespace
 
 extern "C" size_t sb_chisao_workspace_bytes(const sb_problem *p, const sb_config *c) {
@@ -1147,30 +1182,26 @@ extern "C" size_t sb_chisao_workspace_bytes(const sb_problem *p, const sb_config
     return base + chisao_layout(nullptr, base, p, c).bytes;
 }
 
-extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb_chisao_config *cc, const double *x0,
-                               int32_t n, double *x_out, double *ell_out, int8_t *stuck_out, int32_t *n_peaks,
-                               void *ws, size_t ws_bytes, void *stream) {
-    if (!x0 || !x_out || !ell_out || !stuck_out || !n_peaks) return SB_ERR_INVALID_ARG;
-    if (!c || n < 1 || n > c->n_starts) return SB_ERR_INVALID_ARG;
-    sb_status st = check_chisao(cc);
-    if (st != SB_OK) return st;
-    // the mixed path evaluates ray samples in chunks of at most n_starts rows
-    const bool mixed = c->prec != SB_PREC_FP64;
-    if (mixed && c->n_starts < c->n_steps) return SB_ERR_UNSUPPORTED;
-    Prelude P;
-    st = prelude(p, c, ws, ws_bytes, stream, P);
-    if (st != SB_OK) return st;
-    const ChisaoWs w = chisao_layout(ws, P.L.bytes, p, c);
-    if (ws_bytes < P.L.bytes + w.bytes) return SB_ERR_WORKSPACE;
-    const int d = p->d;
-    const cudaStream_t s = P.s;
+namespace {
+
+// The ChiSao oscillation (Sec. 3.5.5, Algorithm 1) of the n samples at x0 after a
+// prelude: every decision that depends on device state (which samples stick, are
+// lost or move, which reseeding branch runs, the Golden Rooster groups) is taken by
+// kernels, so the host only enqueues and the whole loop can sit in a captured graph.
+sb_status run_chisao(const Prelude &P, const sb_config *c, const sb_chisao_config *cc, const ChisaoWs &w,
+                     const double *x0, int n, double *x_out, double *ell_out, int8_t *stuck_out, int32_t *n_peaks,
+                     cudaStream_t s) {
+    const int d = P.pv.d;
     const ProbView &pv = P.pv;
     const auto &la = P.L.la;
     const auto &r = P.L.r64;
+    const bool mixed = c->prec != SB_PREC_FP64;
+    sb_status st = SB_OK;
     sb_config c2 = *c;
     c2.max_iter = cc->conv_iters;
     const DedupScratch dds{la.dd_l, la.dd_i, la.dd_bar, pv.status};
     SB_CUDA_TRY(cudaMemsetAsync(w.stats, 0, sizeof(int64_t) * 4, s));
+    launch_cs_state_init(w.state, s);
     SB_CUDA_TRY(cudaMemcpyAsync(w.X, x0, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, s));
     // l and grad l at the samples listed in rows (all n when rows is null)
     auto grad_at = [&](const int32_t *rows, const int32_t *n_rows_dev, int n_rows) {
@@ -1187,8 +1218,6 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
         a.out_by_walker = 1;
         launch_lik_f64_points(a, true, s);
     };
-    bool gr_on = true, gr_used_prev = false;
-    int peaks_prev = -1;
     for (int osc = 0; osc < cc->n_osc; ++osc) {
         // convergence phase: every sample released, L-BFGS from where it is
         if (mixed)
@@ -1210,79 +1239,58 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
         launch_dedup(n, d, w.X, w.ell, nullptr, w.stuck, c->dedup_coarse, pv.wmax, n, w.reps, w.n_reps, la.assigned,
                      dds, s);
         launch_cs_split(n, w.reps, w.n_reps, w.stuck, w.lost, s);
-        int32_t h_peaks = 0;
-        SB_CUDA_TRY(cudaMemcpyAsync(&h_peaks, w.n_reps, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        SB_CUDA_TRY(cudaStreamSynchronize(s));
-        if (gr_used_prev && h_peaks <= peaks_prev) gr_on = false;
-        gr_used_prev = false;
-        peaks_prev = h_peaks;
+        launch_cs_osc_state(w.n_reps, w.state, s);
         if (osc == cc->n_osc - 1) break;
-        // reseeding of the lost samples
+        // reseeding of the lost samples: the branch and its job tables on the device
         launch_cs_lists(n, w.lost, w.conv, w.stuck, w.status, w.ell, w.lost_list, w.unconv_list, w.moving_list, w.cnt,
                         s);
-        int32_t h_cnt[3] = {0, 0, 0};
-        SB_CUDA_TRY(cudaMemcpyAsync(h_cnt, w.cnt, sizeof(h_cnt), cudaMemcpyDeviceToHost, s));
-        SB_CUDA_TRY(cudaStreamSynchronize(s));
-        const int n_lost = h_cnt[0], n_unconv = h_cnt[1], n_moving = h_cnt[2];
-        int past_valley = -1;
-        if (n_lost > 0 && n_unconv >= cc->min_unconverged) {
-            launch_cs_rm_rays(n_lost, d, c->seed, osc, w.unconv_list, n_unconv, w.X, pv.lo, pv.hi, w.O, w.U, w.texit,
-                              s);
-            past_valley = 0;
-        } else if (n_lost > 0 && gr_on && h_peaks > 0) {
-            const GrJobs j = gr_jobs(n_lost, h_peaks, d);
-            const int nj = (int)j.pk.size();
-            SB_CUDA_TRY(cudaMemcpyAsync(w.job_start, j.start.data(), sizeof(int32_t) * j.start.size(),
-                                        cudaMemcpyHostToDevice, s));
-            SB_CUDA_TRY(cudaMemcpyAsync(w.job_pk, j.pk.data(), sizeof(int32_t) * nj, cudaMemcpyHostToDevice, s));
-            SB_CUDA_TRY(cudaMemcpyAsync(w.job_b, j.b.data(), sizeof(int32_t) * nj, cudaMemcpyHostToDevice, s));
-            SB_CUDA_TRY(cudaMemcpyAsync(w.job_cols, j.cols.data(), sizeof(int32_t) * nj, cudaMemcpyHostToDevice, s));
-            SB_CUDA_TRY(cudaMemcpyAsync(w.job_off, j.off.data(), sizeof(int64_t) * nj, cudaMemcpyHostToDevice, s));
-            launch_cs_bases(nj, d, c->seed, osc, w.job_pk, w.job_b, w.job_cols, w.job_off, w.Q, mixed, s);
-            launch_cs_gr_rays(n_lost, d, h_peaks, w.reps, w.X, pv.lo, pv.hi, w.job_start, w.job_off, w.Q, w.O, w.U,
-                              w.texit, s);
-            SB_CUDA_TRY(cudaStreamSynchronize(s));  // the job tables above are host vectors
-            past_valley = 1;
-            gr_used_prev = true;
+        launch_cs_branch(w.cnt, w.n_reps, cc->min_unconverged, d, c->n_steps, w.state, w.job_start, w.job_pk, w.job_b,
+                         w.job_cols, w.job_off, w.stats, s);
+        launch_cs_rm_rays(n, d, c->seed, osc, w.unconv_list, w.cnt, w.state, w.X, pv.lo, pv.hi, w.O, w.U, w.texit,
+                          s);
+        launch_cs_bases(n, d, c->seed, osc, w.job_pk, w.job_b, w.job_cols, w.job_off, w.state, w.Q, mixed, s);
+        launch_cs_gr_rays(n, d, w.n_reps, w.reps, w.X, pv.lo, pv.hi, w.job_start, w.job_off, w.Q, w.cnt, w.state, w.O,
+                          w.U, w.texit, s);
+        if (mixed) {  // the tensor-core pass forms the ray samples itself, in FP32
+            tc_to_f32(w.O, w.O32, (size_t)n * d, s);
+            tc_to_f32(w.U, w.U32, (size_t)n * d, s);
         }
-        if (past_valley >= 0) {
-            launch_cs_stat_add(w.stats + 0, nullptr, (int64_t)n_lost * c->n_steps, s);
-            if (mixed) {  // the tensor-core pass forms the ray samples itself, in FP32
-                tc_to_f32(w.O, w.O32, (size_t)n_lost * d, s);
-                tc_to_f32(w.U, w.U32, (size_t)n_lost * d, s);
+        for (int l0 = 0; l0 < n; l0 += w.lc) {
+            const int lc = n - l0 < w.lc ? n - l0 : w.lc;
+            launch_cs_chunk_rows(w.cnt, w.state, l0, lc, c->n_steps, w.rows, s);
+            if (mixed) {
+                st = tc_ray_chunk(pv, P.L.r32.tc, w.O32, w.U32, w.texit, c->n_steps, (int64_t)l0 * c->n_steps,
+                                  lc * c->n_steps, w.rows, w.ellp, s);
+                if (st != SB_OK) return st;
+            } else {
+                launch_cs_ray_points(l0, lc, c->n_steps, d, w.O, w.U, w.texit, w.rows, w.P, s);
+                LikF64Args a = f64_args(pv);
+                a.X = w.P;
+                a.n_rows = lc * c->n_steps;
+                a.n_rows_dev = w.rows;
+                a.qpart = w.qp;
+                a.ell = w.ellp;
+                a.out_by_walker = 0;
+                launch_lik_f64_points(a, false, s);
             }
-            for (int l0 = 0; l0 < n_lost; l0 += w.lc) {
-                const int nl = n_lost - l0 < w.lc ? n_lost - l0 : w.lc;
-                if (mixed) {
-                    st = tc_ray_samples(pv, P.L.r32.tc, w.O32, w.U32, w.texit, c->n_steps, (int64_t)l0 * c->n_steps,
-                                        (int64_t)(l0 + nl) * c->n_steps, w.ellp, s);
-                    if (st != SB_OK) return st;
-                } else {
-                    launch_cs_ray_points(l0, nl, c->n_steps, d, w.O, w.U, w.texit, w.P, s);
-                    LikF64Args a = f64_args(pv);
-                    a.X = w.P;
-                    a.n_rows = nl * c->n_steps;
-                    a.qpart = w.qp;
-                    a.ell = w.ellp;
-                    a.out_by_walker = 0;
-                    launch_lik_f64_points(a, false, s);
-                }
-                launch_cs_ray_pick(l0, nl, c->n_steps, d, past_valley, w.ellp, w.lost_list, w.O, w.U, w.texit, w.X,
-                                   s);
-            }
+            launch_cs_ray_pick(l0, lc, c->n_steps, d, w.rows, w.state, w.ellp, w.lost_list, w.O, w.U, w.texit, w.X,
+                               s);
         }
-        // anti-convergence of every sample that is not stuck
-        if (cc->anti_steps > 0 && n_moving > 0) {
-            launch_cs_stat_add(w.stats + 2, nullptr, (int64_t)(mixed ? n : n_moving) * cc->anti_steps, s);
+        // anti-convergence of every sample that is not stuck (the moving list)
+        if (cc->anti_steps > 0) {
+            if (mixed)
+                launch_cs_stat_add(w.stats + 2, nullptr, (int64_t)n * cc->anti_steps, s);
+            else
+                launch_cs_stat_add32(w.stats + 2, w.cnt + 2, cc->anti_steps, s);
             SB_CUDA_TRY(cudaMemsetAsync(w.V, 0, sizeof(double) * n * d, s));
             for (int t = 0; t < cc->anti_steps; ++t) {
                 if (mixed) {  // every sample's gradient; the step moves the listed ones only
                     st = tc_loglik_points(pv, c, P.L.r32.tc, w.X, n, nullptr, nullptr, w.ellg, w.G, s);
                     if (st != SB_OK) return st;
                 } else {
-                    grad_at(w.moving_list, w.cnt + 2, n_moving);
+                    grad_at(w.moving_list, w.cnt + 2, n);
                 }
-                launch_cs_momentum(n_moving, d, w.moving_list, w.cnt + 2, cc->momentum, cc->anti_alpha, w.G, w.V, w.X,
+                launch_cs_momentum(n, d, w.moving_list, w.cnt + 2, cc->momentum, cc->anti_alpha, w.G, w.V, w.X,
                                    pv.lo, pv.hi, s);
             }
         }
@@ -1296,33 +1304,70 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
     return SB_OK;
 }
 
+}  // namespace
+
+extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb_chisao_config *cc, const double *x0,
+                               int32_t n, double *x_out, double *ell_out, int8_t *stuck_out, int32_t *n_peaks,
+                               void *ws, size_t ws_bytes, void *stream) {
+    if (!x0 || !x_out || !ell_out || !stuck_out || !n_peaks) return SB_ERR_INVALID_ARG;
+    if (!c || n < 1 || n > c->n_starts) return SB_ERR_INVALID_ARG;
+    sb_status st = check_chisao(cc);
+    if (st != SB_OK) return st;
+    // the mixed path evaluates ray samples in chunks of at most n_starts rows
+    if (c->prec != SB_PREC_FP64 && c->n_starts < c->n_steps) return SB_ERR_UNSUPPORTED;
+    st = check_call(p, c, ws, ws_bytes, true);
+    if (st != SB_OK) return st;
+    cudaStream_t s0 = static_cast<cudaStream_t>(stream);
+    GraphKey key = call_key(1, p, c, ws, ws_bytes);
+    key.add_bytes(*cc);
+    for (const void *q : {(const void *)x0, (const void *)x_out, (const void *)ell_out, (const void *)stuck_out,
+                          (const void *)n_peaks})
+        key.add_ptr(q);
+    key.add((uint64_t)n);
+    pretune(p, c, ws, ws_bytes, s0);
+    return run_graph_or_direct(s0, key, [&](cudaStream_t s) {
+        Prelude P;
+        sb_status r = prelude(p, c, ws, ws_bytes, s, P);
+        if (r != SB_OK) return r;
+        const ChisaoWs w = chisao_layout(ws, P.L.bytes, p, c);
+        return run_chisao(P, c, cc, w, x0, n, x_out, ell_out, stuck_out, n_peaks, s);
+    });
+}
+
 extern "C" sb_status sb_evidence_chisao(const sb_problem *p, const sb_config *c, const sb_chisao_config *cc,
                                         double *logZ, double *modes, double *logZk, int32_t cap, int32_t *n_modes,
                                         void *ws, size_t ws_bytes, void *stream) {
     if (!logZ || !modes || !logZk || !n_modes || cap < 1) return SB_ERR_INVALID_ARG;
-    sb_status st = check_problem(p);
+    sb_status st = check_chisao(cc);
     if (st != SB_OK) return st;
-    st = check_config(c);
+    if (c && c->prec != SB_PREC_FP64 && c->n_starts < c->n_steps) return SB_ERR_UNSUPPORTED;
+    st = check_call(p, c, ws, ws_bytes, true);
     if (st != SB_OK) return st;
-    st = check_chisao(cc);
-    if (st != SB_OK) return st;
-    if (!ws) return SB_ERR_INVALID_ARG;
-    const Layout L = layout(ws, p, c);
-    if (ws_bytes < L.bytes + chisao_layout(nullptr, L.bytes, p, c).bytes) return SB_ERR_WORKSPACE;
-    const int n = c->n_starts;
-    // discovery into the evidence buffers, ChiSao from its starts (the peak count goes to
-    // n_modes for now), then the Laplace stage over every final sample
-    st = sb_discover(p, c, L.ev.starts, L.ev.ell_starts, ws, ws_bytes, stream);
-    if (st != SB_OK) return st;
-    st = sb_chisao(p, c, cc, L.ev.starts, n, L.ev.x_out, L.ev.ell_out, L.ev.status, n_modes, ws, ws_bytes, stream);
-    if (st != SB_OK) return st;
-    const ChisaoWs w = chisao_layout(ws, L.bytes, p, c);
-    launch_cs_stat_add(w.stats + 0, nullptr, (int64_t)c->n_rays * c->n_steps, static_cast<cudaStream_t>(stream));
-    // each stage clears the device status word on entry: surface what the first two recorded
-    st = sb_check(ws, ws_bytes, stream);
-    if (st != SB_OK) return st;
-    return sb_laplace(p, c, L.ev.x_out, L.ev.ell_out, nullptr, n, modes, logZk, nullptr, cap, n_modes, logZ, ws,
-                      ws_bytes, stream);
+    cudaStream_t s0 = static_cast<cudaStream_t>(stream);
+    GraphKey key = call_key(2, p, c, ws, ws_bytes);
+    key.add_bytes(*cc);
+    for (const void *q : {(const void *)logZ, (const void *)modes, (const void *)logZk, (const void *)n_modes})
+        key.add_ptr(q);
+    key.add((uint64_t)cap);
+    pretune(p, c, ws, ws_bytes, s0);
+    // discovery into the evidence buffers, ChiSao from its starts (its peak count goes to
+    // n_modes for now), then the Laplace stage over every final sample; one prelude, so
+    // the device status word collects what every stage records
+    return run_graph_or_direct(s0, key, [&](cudaStream_t s) {
+        Prelude P;
+        sb_status r = prelude(p, c, ws, ws_bytes, s, P);
+        if (r != SB_OK) return r;
+        const auto &ev = P.L.ev;
+        const int n = c->n_starts;
+        r = run_discover(P.pv, c, P.L, ev.starts, ev.ell_starts, s);
+        if (r != SB_OK) return r;
+        const ChisaoWs w = chisao_layout(ws, P.L.bytes, p, c);
+        r = run_chisao(P, c, cc, w, ev.starts, n, ev.x_out, ev.ell_out, ev.status, n_modes, s);
+        if (r != SB_OK) return r;
+        launch_cs_stat_add(w.stats + 0, nullptr, (int64_t)c->n_rays * c->n_steps, s);
+        return run_laplace(P.pv, c, P.L, ev.x_out, ev.ell_out, nullptr, n, modes, logZk, nullptr, cap, n_modes, logZ,
+                           s);
+    });
 }
 
 extern "C" size_t sb_evidence_chisao_host_workspace_bytes(const sb_problem *hp, const sb_config *c) {

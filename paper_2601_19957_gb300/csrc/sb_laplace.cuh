@@ -34,11 +34,15 @@ void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P
                          const double *gbar, const int32_t *n_c, double *GK, double *H, int32_t *info,
                          cudaStream_t s, const int32_t *onehot = nullptr);
 // Newton step (C C^T) delta = g and g^T delta / 2 for the live candidates, over
-// nc * Gc co-resident CTAs (cooperative launch, one bounded grid barrier per
-// 32-row block and direction); nc = live candidates (host).
-void launch_chol_solve_coop(int d, int nc, const double *H, const double *g, const int32_t *n_c, const int32_t *info,
+// co-resident CTAs (cooperative launch, one bounded grid barrier per 32-row block
+// and direction; at most one per SM and 16 per candidate of the cap, divided among
+// the *n_c candidates on the device).
+void launch_chol_solve_coop(int d, int cap, const double *H, const double *g, const int32_t *n_c, const int32_t *info,
                             const uint8_t *active, double *delta, double *pred, uint32_t *bar, int32_t *err,
                             cudaStream_t s);
+// *n_eff = *n_reps when *n_live > 0 (or n_live is null), else 0: the candidate count the
+// rest of a Newton step runs on (zero once no candidate moves).
+void launch_set_eff(int32_t *n_eff, const int32_t *n_reps, const int32_t *n_live, cudaStream_t s);
 // Newton line search: mode 0 starts it (t = 1) for the candidates still polishing
 // and counts them in *n_live (a candidate whose step is below 1e-11 (1 + |x|_inf)
 // in max norm has converged and stops where it is); mode 1 decides on the trial.

@@ -23,6 +23,8 @@ int tc_ray_chunk(int d, int K, int64_t total);
 // Encodes the A-operand tensor maps of this scratch (depends on its row capacity).
 bool tc_maps_for_rows(TcWs &t);
 // Tile width the autotuner chose for (d, K, prec) in this process (0: not tuned yet).
+// A first call made inside a stream capture cannot time the candidates: it takes the
+// heuristic width and leaves the shape untuned.
 int tc_tuned_tile(int d, int K, int prec);
 // Converts L_k / mu / c into the tensor-core copies, picks the tile width
 // (autotuned once per shape; that first call synchronises the stream) and
@@ -39,6 +41,10 @@ sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, c
 // null); ell[flat - f_begin]. Chunks of the scratch row capacity.
 sb_status tc_ray_samples(const ProbView &pv, const TcWs &t, const float *o32, const float *u32, const double *texit,
                          int n_steps, int64_t f_begin, int64_t f_end, double *ell, cudaStream_t s);
+// One chunk of ray samples with the row count on the device (*n_rows_dev <= rows_max
+// <= the scratch rows): flat indices f0 .. f0 + *n_rows_dev - 1, ell[flat - f0].
+sb_status tc_ray_chunk(const ProbView &pv, const TcWs &t, const float *o32, const float *u32, const double *texit,
+                       int n_steps, int64_t f0, int rows_max, const int32_t *n_rows_dev, double *ell, cudaStream_t s);
 // y[e] = (float) x[e], e < n.
 void tc_to_f32(const double *x, float *y, size_t n, cudaStream_t s);
 // Clears the per-walker bounds of the component skip (before a refinement).

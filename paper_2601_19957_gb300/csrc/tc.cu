@@ -1173,6 +1173,9 @@ int pick_tile(const ProbView &pv, TcWs &t, cudaStream_t s) {
     auto it = g_tune.find(key);
     if (it != g_tune.end()) return it->second;
     int bn = bn_of(pv.d);
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cst) != cudaSuccess || cst != cudaStreamCaptureStatusNone)
+        return bn;  // no timing inside a capture: the heuristic width, not remembered
     if (!(off && off[0] == '0')) {
         // widest tile first; a narrower one must be at least 3 % faster to win,
         // so timing noise between near-equal tiles does not flip the choice
@@ -1248,6 +1251,20 @@ sb_status tc_ray_samples(const ProbView &pv, const TcWs &t, const float *o32, co
                                                     nullptr, nullptr, ell + (f0 - f_begin), nullptr, nullptr, nullptr,
                                                     nullptr, nullptr);
     }
+    return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
+}
+
+sb_status tc_ray_chunk(const ProbView &pv, const TcWs &t, const float *o32, const float *u32, const double *texit,
+                       int n_steps, int64_t f0, int rows_max, const int32_t *n_rows_dev, double *ell, cudaStream_t s) {
+    TcArgs a = base_args(pv, t);
+    a.n_rows_max = rows_max;
+    a.n_rows_dev = n_rows_dev;
+    launch_center(t, 1, pv.d, pv.K, n_rows_dev, rows_max, nullptr, nullptr, u32, texit, n_steps, f0, s, nullptr, o32);
+    launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
+    note_launch();
+    k_tc_lse<<<(rows_max + 127) / 128, 128, 0, s>>>(1, pv.K, a.n_ntile, n_rows_dev, rows_max, nullptr, a.qpart, pv.a,
+                                                    nullptr, nullptr, ell, nullptr, nullptr, nullptr, nullptr,
+                                                    nullptr);
     return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
 }
 
