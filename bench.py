@@ -620,22 +620,24 @@ def run_batched(sb, args):
     probs = [sb.Problem(i) for i in insts]
     c = sb.make_config(cfg)
     workers = 16
-    ws = sb.batched_workspace(probs, c, workers)
+    use_chisao = not args.no_chisao
+    cc = sb.make_chisao_config() if use_chisao else None
+    ws = sb.batched_workspace(probs, c, workers, chisao=use_chisao)
     out = (torch.empty(len(probs), dtype=torch.float64, device="cuda"),
            torch.empty(len(probs), dtype=torch.int32, device="cuda"))
     t0 = time.perf_counter()
-    sb.evidence_batched(probs, c, n_workers=workers, ws=ws, out=out)  # tunes the tiles, captures the graph
+    sb.evidence_batched(probs, c, n_workers=workers, ws=ws, out=out, cc=cc)  # tunes the tiles, captures the graph
     torch.cuda.synchronize()
     first_s = time.perf_counter() - t0
     for _ in range(max(args.warmup - 1, 0)):
-        sb.evidence_batched(probs, c, n_workers=workers, ws=ws, out=out)
+        sb.evidence_batched(probs, c, n_workers=workers, ws=ws, out=out, cc=cc)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        logZ, nm = sb.evidence_batched(probs, c, n_workers=workers, ws=ws, out=out)
+        logZ, nm = sb.evidence_batched(probs, c, n_workers=workers, ws=ws, out=out, cc=cc)
     e1.record(stream)
     e1.synchronize()
     dt = e0.elapsed_time(e1) / 1e3 / args.steps
@@ -645,7 +647,8 @@ def run_batched(sb, args):
     closed = np.array([np.log(np.exp(i.log_w).sum()) for i in insts]) - logV
     allk = nmv == np.array([i.K for i in insts])
     print(json.dumps({"case": "batched", "workload": "512 problems, d in {16..512}, K in 1..8, 256 starts each, "
-                                                     "m=10, TF32 likelihood, FP64 Laplace",
+                                                     "m=10, TF32 likelihood, FP64 Laplace"
+                                                     + (", ChiSao 3 oscillations" if use_chisao else ""),
                       "problems": len(insts), "ms_per_batch": dt * 1e3, "problems_per_sec": len(insts) / dt,
                       "prec": {1: "tf32", 2: "bf16", 0: "fp64"}[cfg.prec], "workers": workers,
                       "execution": "one cached CUDA graph per call (device-decided refinement loops)",

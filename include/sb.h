@@ -415,6 +415,18 @@ sb_status sb_evidence_chisao(const sb_problem *prob, const sb_config *cfg, const
                              double *modes, double *logZk, int32_t cap, int32_t *n_modes, void *ws, size_t ws_bytes,
                              void *stream);
 
+/*
+ * sb_evidence_batched with ChiSao: every problem is solved as sb_evidence_chisao does
+ * (discovery, the ChiSao oscillation, the Laplace stage over every final sample), on
+ * the same worker streams and, in graph mode, in one CUDA graph. ws:
+ * sb_evidence_chisao_batched_workspace_bytes. Asynchronous.
+ */
+size_t sb_evidence_chisao_batched_workspace_bytes(const sb_problem *probs, int32_t P, const sb_config *cfg,
+                                                  int32_t n_workers);
+sb_status sb_evidence_chisao_batched(const sb_problem *probs, int32_t P, const sb_config *cfg,
+                                     const sb_chisao_config *cc, double *logZ, int32_t *n_modes, int32_t n_workers,
+                                     void *ws, size_t ws_bytes, void *stream);
+
 /* sb_evidence_chisao with HOST inputs and outputs, as sb_evidence_host: copies the
  * problem arrays (host pointers in `host_prob`) into `ws`, runs discovery, ChiSao and
  * the Laplace stage over every final sample, and copies log Z, the mode count, the

@@ -62,6 +62,8 @@ def lib():
         L.sb_evidence_host_workspace_bytes.restype = C.c_size_t
         L.sb_evidence_backward_workspace_bytes.restype = C.c_size_t
         L.sb_evidence_batched_workspace_bytes.restype = C.c_size_t
+        L.sb_evidence_chisao_batched_workspace_bytes.restype = C.c_size_t
+        L.sb_evidence_chisao_batched.restype = C.c_int
         L.sb_evidence_batched.restype = C.c_int
         L.sb_profile_bytes.restype = C.c_double
         L.sb_profile_bytes.argtypes = [C.c_int32]
@@ -589,24 +591,31 @@ def evidence_autograd(mu, L, log_w, lo, hi, cfg: _Config):
     return _autograd_function().apply(mu, L, log_w, lo, hi, cfg)
 
 
-def batched_workspace(problems, cfg: _Config, n_workers: int = 8) -> Workspace:
+def batched_workspace(problems, cfg: _Config, n_workers: int = 8, chisao: bool = False) -> Workspace:
     P = len(problems)
     arr = (_Problem * P)(*[p.s for p in problems])
-    return Workspace(lib().sb_evidence_batched_workspace_bytes(arr, P, C.byref(cfg), int(n_workers)))
+    q = lib().sb_evidence_chisao_batched_workspace_bytes if chisao else lib().sb_evidence_batched_workspace_bytes
+    return Workspace(q(arr, P, C.byref(cfg), int(n_workers)))
 
 
-def evidence_batched(problems, cfg: _Config, n_workers: int = 8, stream=None, ws: Workspace = None, out=None):
-    """Solve many independent problems (list of Problem) in one library call.
-    Returns (logZ, n_modes) as CUDA tensors of length P (the tensors of `out`, a
-    (logZ, n_modes) pair kept across calls, when given: with the same workspace the
-    call then replays the library's cached graph)."""
+def evidence_batched(problems, cfg: _Config, n_workers: int = 8, stream=None, ws: Workspace = None, out=None,
+                     cc: Optional[_ChisaoConfig] = None):
+    """Solve many independent problems (list of Problem) in one library call (with the
+    ChiSao oscillation when cc is given). Returns (logZ, n_modes) as CUDA tensors of
+    length P (the tensors of `out`, a (logZ, n_modes) pair kept across calls, when
+    given: with the same workspace the call then replays the library's cached graph)."""
     torch = _torch()
     P = len(problems)
     arr = (_Problem * P)(*[p.s for p in problems])
-    ws = ws or batched_workspace(problems, cfg, n_workers)
+    ws = ws or batched_workspace(problems, cfg, n_workers, chisao=cc is not None)
     if out is None:
         out = (torch.empty(P, dtype=torch.float64, device="cuda"), torch.empty(P, dtype=torch.int32, device="cuda"))
     logZ, nm = out
+    if cc is not None:
+        _check(lib().sb_evidence_chisao_batched(arr, P, C.byref(cfg), C.byref(cc), _ptr(logZ), _ptr(nm),
+                                                int(n_workers), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)),
+               "sb_evidence_chisao_batched")
+        return logZ, nm
     _check(lib().sb_evidence_batched(arr, P, C.byref(cfg), _ptr(logZ), _ptr(nm), int(n_workers), ws.ptr,
                                      C.c_size_t(ws.nbytes), _stream(stream)), "sb_evidence_batched")
     return logZ, nm

@@ -978,114 +978,6 @@ extern "C" sb_status sb_evidence_backward(const sb_problem *p, const double *mod
     return adjoint_run(pv, B.adj, modes, logZk, n_modes, grad_logZ, dmu, dL, s);
 }
 
-// ------------------------------------------------------------------ batched problems
-// Independent problems of uneven d and K run on `n_workers` worker streams,
-// each with its own host thread (the refine stage polls its stream) and its own
-// slice of the workspace; problem i goes to worker i % n_workers.
-namespace {
-size_t batched_slice_bytes(const sb_problem *probs, int32_t P, const sb_config *c) {
-    size_t mx = 0;
-    for (int32_t i = 0; i < P; ++i) {
-        const size_t b = layout(nullptr, &probs[i], c).bytes;
-        if (b > mx) mx = b;
-    }
-    // per-problem modes buffer [cand_cap][d_max] and logZk [cand_cap]
-    int dmax = 1;
-    for (int32_t i = 0; i < P; ++i) dmax = probs[i].d > dmax ? probs[i].d : dmax;
-    const size_t extra = ((size_t)c->cand_cap * dmax * sizeof(double) + 255) / 256 * 256 +
-                         ((size_t)c->cand_cap * sizeof(double) + 255) / 256 * 256;
-    return (mx + extra + 255) / 256 * 256;
-}
-}  // namespace
-
-extern "C" size_t sb_evidence_batched_workspace_bytes(const sb_problem *probs, int32_t P, const sb_config *c,
-                                                      int32_t n_workers) {
-    if (!probs || P < 1 || n_workers < 1 || check_config(c) != SB_OK) return 0;
-    for (int32_t i = 0; i < P; ++i)
-        if (check_problem(&probs[i]) != SB_OK) return 0;
-    const int32_t w = n_workers < P ? n_workers : P;
-    return (size_t)w * batched_slice_bytes(probs, P, c);
-}
-
-namespace {
-// Worker streams and fork / join events of this host thread (created once per device).
-struct Workers {
-    std::vector<cudaStream_t> streams;
-    std::vector<cudaEvent_t> joins;
-    cudaEvent_t fork = nullptr;
-};
-Workers *workers_for(int W) {
-    thread_local std::map<int, Workers> pools;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    Workers &wk = pools[dev];
-    if (!wk.fork && cudaEventCreateWithFlags(&wk.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
-    while ((int)wk.streams.size() < W) {
-        cudaStream_t st = nullptr;
-        cudaEvent_t ev = nullptr;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return nullptr;
-        wk.streams.push_back(st);
-        wk.joins.push_back(ev);
-    }
-    return &wk;
-}
-}  // namespace
-
-extern "C" sb_status sb_evidence_batched(const sb_problem *probs, int32_t P, const sb_config *c, double *logZ,
-                                         int32_t *n_modes, int32_t n_workers, void *ws, size_t ws_bytes,
-                                         void *stream) {
-    if (!probs || P < 1 || n_workers < 1 || !logZ || !n_modes || !ws) return SB_ERR_INVALID_ARG;
-    sb_status st = check_config(c);
-    if (st != SB_OK) return st;
-    for (int32_t i = 0; i < P; ++i) {
-        st = check_problem(&probs[i]);
-        if (st != SB_OK) return st;
-    }
-    if (c->prec != SB_PREC_FP64 && !tc_available(c->prec)) return SB_ERR_UNSUPPORTED;
-    const int32_t W = n_workers < P ? n_workers : P;
-    const size_t slice = batched_slice_bytes(probs, P, c);
-    if (ws_bytes < (size_t)W * slice) return SB_ERR_WORKSPACE;
-    int dmax = 1;
-    for (int32_t i = 0; i < P; ++i) dmax = probs[i].d > dmax ? probs[i].d : dmax;
-    cudaStream_t s0 = static_cast<cudaStream_t>(stream);
-    Workers *wk = workers_for(W);
-    if (!wk) return SB_ERR_CUDA;
-    // the tile autotuner times each new shape once, outside the capture, on the slice of
-    // the worker that will solve it
-    for (int32_t i = 0; i < P; ++i) pretune(&probs[i], c, static_cast<char *>(ws) + (size_t)(i % W) * slice, slice, s0);
-    GraphKey key;
-    key.add(5);
-    key.add((uint64_t)P);
-    key.add((uint64_t)W);
-    for (int32_t i = 0; i < P; ++i) key.add_bytes(probs[i]);
-    key.add_bytes(*c);
-    for (const void *q : {(const void *)logZ, (const void *)n_modes, (const void *)ws}) key.add_ptr(q);
-    key.add((uint64_t)ws_bytes);
-    // problem i on worker i % W, in order (the worker's problems share its workspace
-    // slice); the workers fork from the caller's stream and join back into it
-    return run_graph_or_direct(s0, key, [&](cudaStream_t s) {
-        SB_CUDA_TRY(cudaEventRecord(wk->fork, s));
-        for (int32_t w = 0; w < W; ++w) SB_CUDA_TRY(cudaStreamWaitEvent(wk->streams[w], wk->fork, 0));
-        for (int32_t i = 0; i < P; ++i) {
-            const int32_t w = i % W;
-            char *base = static_cast<char *>(ws) + (size_t)w * slice;
-            Carver cv(base);
-            double *modes = cv.take<double>((size_t)c->cand_cap * dmax);
-            double *zk = cv.take<double>((size_t)c->cand_cap);
-            void *inner = base + cv.bytes();
-            const sb_status r = enqueue_evidence(&probs[i], c, logZ + i, modes, zk, c->cand_cap, n_modes + i, inner,
-                                                 slice - cv.bytes(), wk->streams[w]);
-            if (r != SB_OK) return r;
-        }
-        for (int32_t w = 0; w < W; ++w) {
-            SB_CUDA_TRY(cudaEventRecord(wk->joins[w], wk->streams[w]));
-            SB_CUDA_TRY(cudaStreamWaitEvent(s, wk->joins[w], 0));
-        }
-        return SB_OK;
-    });
-}
-
 extern "C" int32_t sb_tuned_tile(int32_t d, int32_t K, int32_t prec) { return tc_tuned_tile(d, K, prec); }
 
 // ------------------------------------------------------------------ ChiSao (Sec. 3.5.5)
@@ -1334,6 +1226,26 @@ extern "C" sb_status sb_chisao(const sb_problem *p, const sb_config *c, const sb
     });
 }
 
+namespace {
+// discover + ChiSao + Laplace over every final sample, on one prelude, no host read.
+sb_status enqueue_evidence_chisao(const sb_problem *p, const sb_config *c, const sb_chisao_config *cc, double *logZ,
+                                  double *modes, double *logZk, int32_t cap, int32_t *n_modes, void *ws,
+                                  size_t ws_bytes, cudaStream_t s) {
+    Prelude P;
+    sb_status r = prelude(p, c, ws, ws_bytes, s, P);
+    if (r != SB_OK) return r;
+    const auto &ev = P.L.ev;
+    const int n = c->n_starts;
+    r = run_discover(P.pv, c, P.L, ev.starts, ev.ell_starts, s);
+    if (r != SB_OK) return r;
+    const ChisaoWs w = chisao_layout(ws, P.L.bytes, p, c);
+    r = run_chisao(P, c, cc, w, ev.starts, n, ev.x_out, ev.ell_out, ev.status, n_modes, s);
+    if (r != SB_OK) return r;
+    launch_cs_stat_add(w.stats + 0, nullptr, (int64_t)c->n_rays * c->n_steps, s);
+    return run_laplace(P.pv, c, P.L, ev.x_out, ev.ell_out, nullptr, n, modes, logZk, nullptr, cap, n_modes, logZ, s);
+}
+}  // namespace
+
 extern "C" sb_status sb_evidence_chisao(const sb_problem *p, const sb_config *c, const sb_chisao_config *cc,
                                         double *logZ, double *modes, double *logZk, int32_t cap, int32_t *n_modes,
                                         void *ws, size_t ws_bytes, void *stream) {
@@ -1354,19 +1266,7 @@ extern "C" sb_status sb_evidence_chisao(const sb_problem *p, const sb_config *c,
     // n_modes for now), then the Laplace stage over every final sample; one prelude, so
     // the device status word collects what every stage records
     return run_graph_or_direct(s0, key, [&](cudaStream_t s) {
-        Prelude P;
-        sb_status r = prelude(p, c, ws, ws_bytes, s, P);
-        if (r != SB_OK) return r;
-        const auto &ev = P.L.ev;
-        const int n = c->n_starts;
-        r = run_discover(P.pv, c, P.L, ev.starts, ev.ell_starts, s);
-        if (r != SB_OK) return r;
-        const ChisaoWs w = chisao_layout(ws, P.L.bytes, p, c);
-        r = run_chisao(P, c, cc, w, ev.starts, n, ev.x_out, ev.ell_out, ev.status, n_modes, s);
-        if (r != SB_OK) return r;
-        launch_cs_stat_add(w.stats + 0, nullptr, (int64_t)c->n_rays * c->n_steps, s);
-        return run_laplace(P.pv, c, P.L, ev.x_out, ev.ell_out, nullptr, n, modes, logZk, nullptr, cap, n_modes, logZ,
-                           s);
+        return enqueue_evidence_chisao(p, c, cc, logZ, modes, logZk, cap, n_modes, ws, ws_bytes, s);
     });
 }
 
@@ -1409,6 +1309,150 @@ extern "C" sb_status sb_chisao_stats(const sb_problem *p, const sb_config *c, vo
     SB_CUDA_TRY(cudaStreamSynchronize(s));
     out[3] = nm;
     return SB_OK;
+}
+
+// ------------------------------------------------------------------ batched problems
+// Independent problems of uneven d and K run on `n_workers` worker streams,
+// each with its own host thread (the refine stage polls its stream) and its own
+// slice of the workspace; problem i goes to worker i % n_workers.
+namespace {
+size_t batched_slice_bytes(const sb_problem *probs, int32_t P, const sb_config *c, bool chisao) {
+    size_t mx = 0;
+    for (int32_t i = 0; i < P; ++i) {
+        size_t b = layout(nullptr, &probs[i], c).bytes;
+        if (chisao) b += chisao_layout(nullptr, b, &probs[i], c).bytes;
+        if (b > mx) mx = b;
+    }
+    // per-problem modes buffer [cand_cap][d_max] and logZk [cand_cap]
+    int dmax = 1;
+    for (int32_t i = 0; i < P; ++i) dmax = probs[i].d > dmax ? probs[i].d : dmax;
+    const size_t extra = ((size_t)c->cand_cap * dmax * sizeof(double) + 255) / 256 * 256 +
+                         ((size_t)c->cand_cap * sizeof(double) + 255) / 256 * 256;
+    return (mx + extra + 255) / 256 * 256;
+}
+}  // namespace
+
+extern "C" size_t sb_evidence_batched_workspace_bytes(const sb_problem *probs, int32_t P, const sb_config *c,
+                                                      int32_t n_workers) {
+    if (!probs || P < 1 || n_workers < 1 || check_config(c) != SB_OK) return 0;
+    for (int32_t i = 0; i < P; ++i)
+        if (check_problem(&probs[i]) != SB_OK) return 0;
+    const int32_t w = n_workers < P ? n_workers : P;
+    return (size_t)w * batched_slice_bytes(probs, P, c, false);
+}
+
+extern "C" size_t sb_evidence_chisao_batched_workspace_bytes(const sb_problem *probs, int32_t P, const sb_config *c,
+                                                             int32_t n_workers) {
+    if (!probs || P < 1 || n_workers < 1 || check_config(c) != SB_OK) return 0;
+    for (int32_t i = 0; i < P; ++i)
+        if (check_problem(&probs[i]) != SB_OK) return 0;
+    const int32_t w = n_workers < P ? n_workers : P;
+    return (size_t)w * batched_slice_bytes(probs, P, c, true);
+}
+
+namespace {
+// Worker streams and fork / join events of this host thread (created once per device).
+struct Workers {
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+};
+Workers *workers_for(int W) {
+    thread_local std::map<int, Workers> pools;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    Workers &wk = pools[dev];
+    if (!wk.fork && cudaEventCreateWithFlags(&wk.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    while ((int)wk.streams.size() < W) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        wk.streams.push_back(st);
+        wk.joins.push_back(ev);
+    }
+    return &wk;
+}
+}  // namespace
+
+namespace {
+// The batch of P problems (with ChiSao when cc is given) on W worker streams forked from
+// and joined into the caller's stream; one cached graph in graph mode.
+sb_status batched(const sb_problem *probs, int32_t P, const sb_config *c, const sb_chisao_config *cc, double *logZ,
+                  int32_t *n_modes, int32_t n_workers, void *ws, size_t ws_bytes, void *stream) {
+    if (!probs || P < 1 || n_workers < 1 || !logZ || !n_modes || !ws) return SB_ERR_INVALID_ARG;
+    sb_status st = check_config(c);
+    if (st != SB_OK) return st;
+    if (cc) {
+        st = check_chisao(cc);
+        if (st != SB_OK) return st;
+        if (c->prec != SB_PREC_FP64 && c->n_starts < c->n_steps) return SB_ERR_UNSUPPORTED;
+    }
+    for (int32_t i = 0; i < P; ++i) {
+        st = check_problem(&probs[i]);
+        if (st != SB_OK) return st;
+    }
+    if (c->prec != SB_PREC_FP64 && !tc_available(c->prec)) return SB_ERR_UNSUPPORTED;
+    const int32_t W = n_workers < P ? n_workers : P;
+    const size_t slice = batched_slice_bytes(probs, P, c, cc != nullptr);
+    if (ws_bytes < (size_t)W * slice) return SB_ERR_WORKSPACE;
+    int dmax = 1;
+    for (int32_t i = 0; i < P; ++i) dmax = probs[i].d > dmax ? probs[i].d : dmax;
+    cudaStream_t s0 = static_cast<cudaStream_t>(stream);
+    Workers *wk = workers_for(W);
+    if (!wk) return SB_ERR_CUDA;
+    // the tile autotuner times each new shape once, outside the capture, on the slice of
+    // the worker that will solve it
+    for (int32_t i = 0; i < P; ++i) pretune(&probs[i], c, static_cast<char *>(ws) + (size_t)(i % W) * slice, slice, s0);
+    GraphKey key;
+    key.add(cc ? 6 : 5);
+    key.add((uint64_t)P);
+    key.add((uint64_t)W);
+    for (int32_t i = 0; i < P; ++i) key.add_bytes(probs[i]);
+    key.add_bytes(*c);
+    if (cc) key.add_bytes(*cc);
+    for (const void *q : {(const void *)logZ, (const void *)n_modes, (const void *)ws}) key.add_ptr(q);
+    key.add((uint64_t)ws_bytes);
+    // problem i on worker i % W, in order (the worker's problems share its workspace
+    // slice); the workers fork from the caller's stream and join back into it
+    return run_graph_or_direct(s0, key, [&](cudaStream_t s) {
+        SB_CUDA_TRY(cudaEventRecord(wk->fork, s));
+        for (int32_t w = 0; w < W; ++w) SB_CUDA_TRY(cudaStreamWaitEvent(wk->streams[w], wk->fork, 0));
+        for (int32_t i = 0; i < P; ++i) {
+            const int32_t w = i % W;
+            char *base = static_cast<char *>(ws) + (size_t)w * slice;
+            Carver cv(base);
+            double *modes = cv.take<double>((size_t)c->cand_cap * dmax);
+            double *zk = cv.take<double>((size_t)c->cand_cap);
+            void *inner = base + cv.bytes();
+            const size_t inner_bytes = slice - cv.bytes();
+            const sb_status r =
+                cc ? enqueue_evidence_chisao(&probs[i], c, cc, logZ + i, modes, zk, c->cand_cap, n_modes + i, inner,
+                                             inner_bytes, wk->streams[w])
+                   : enqueue_evidence(&probs[i], c, logZ + i, modes, zk, c->cand_cap, n_modes + i, inner, inner_bytes,
+                                      wk->streams[w]);
+            if (r != SB_OK) return r;
+        }
+        for (int32_t w = 0; w < W; ++w) {
+            SB_CUDA_TRY(cudaEventRecord(wk->joins[w], wk->streams[w]));
+            SB_CUDA_TRY(cudaStreamWaitEvent(s, wk->joins[w], 0));
+        }
+        return SB_OK;
+    });
+}
+}  // namespace
+
+extern "C" sb_status sb_evidence_batched(const sb_problem *probs, int32_t P, const sb_config *c, double *logZ,
+                                         int32_t *n_modes, int32_t n_workers, void *ws, size_t ws_bytes,
+                                         void *stream) {
+    return batched(probs, P, c, nullptr, logZ, n_modes, n_workers, ws, ws_bytes, stream);
+}
+
+extern "C" sb_status sb_evidence_chisao_batched(const sb_problem *probs, int32_t P, const sb_config *c,
+                                                const sb_chisao_config *cc, double *logZ, int32_t *n_modes,
+                                                int32_t n_workers, void *ws, size_t ws_bytes, void *stream) {
+    if (!cc) return SB_ERR_INVALID_ARG;
+    return batched(probs, P, c, cc, logZ, n_modes, n_workers, ws, ws_bytes, stream);
 }
 
 // ------------------------------------------------------------------ setup-only entry points
