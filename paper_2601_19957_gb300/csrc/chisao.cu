@@ -453,6 +453,43 @@ __global__ void k_cs_chunk_rows(const int32_t *cnt, const int32_t *state, int l0
     *rows = nl * n_steps;
 }
 
+// The momentum step of the mixed path in FP32 (warp per moving sample): GT holds
+// grad f = -grad l of the tensor-core evaluation, so v <- m v + alpha GT,
+// x <- clamp(x + v); dist[s] bounds the distance the sample moved (the next
+// evaluation's component skip reads it; clamping only shortens the move).
+__global__ void __launch_bounds__(256) k_cs_momentum_f32(int n, int d, const int32_t *moving_list,
+                                                         const int32_t *n_moving, float m, float alpha,
+                                                         const float *GT, float *V, float *X, const double *lo,
+                                                         const double *hi, float *dist) {
+    const int lane = threadIdx.x & 31;
+    const int e = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (e >= n || e >= *n_moving) return;
+    const int smp = moving_list[e];
+    const size_t base = (size_t)smp * d;
+    float mv = 0.f;
+    for (int i = lane; i < d; i += 32) {
+        const float v = fmaf(m, V[base + i], alpha * GT[base + i]);
+        V[base + i] = v;
+        const float x0 = X[base + i];
+        const float x1 = fminf(fmaxf(x0 + v, (float)lo[i]), (float)hi[i]);
+        X[base + i] = x1;
+        const float dx = x1 - x0;
+        mv = fmaf(dx, dx, mv);
+    }
+    mv = warp_sum(mv);
+    if (lane == 0) dist[smp] = __fsqrt_ru(mv) * 1.0001f;
+}
+
+// X[s] = (double) X32[s] for the moving samples (the others keep their FP64 positions).
+__global__ void __launch_bounds__(256) k_cs_scatter_moving(int n, int d, const int32_t *moving_list,
+                                                           const int32_t *n_moving, const float *X32, double *X) {
+    const int lane = threadIdx.x & 31;
+    const int e = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (e >= n || e >= *n_moving) return;
+    const size_t base = (size_t)moving_list[e] * d;
+    for (int i = lane; i < d; i += 32) X[base + i] = (double)X32[base + i];
+}
+
 inline unsigned warp_grid(int64_t warps) { return (unsigned)((warps * 32 + 255) / 256); }
 
 }  // namespace
@@ -540,6 +577,22 @@ void launch_cs_ray_pick(int l0, int lc, int n_steps, int d, const int32_t *rows,
     if (lc <= 0) return;
     note_launch();
     k_cs_ray_pick<<<warp_grid(lc), 256, 0, s>>>(l0, n_steps, d, rows, state, ellp, lost_list, O, U, texit, X);
+}
+
+void launch_cs_momentum_f32(int n, int d, const int32_t *moving_list, const int32_t *n_moving, double momentum,
+                            double alpha, const float *GT, float *V, float *X, const double *lo, const double *hi,
+                            float *dist, cudaStream_t s) {
+    if (n <= 0) return;
+    note_launch();
+    k_cs_momentum_f32<<<warp_grid(n), 256, 0, s>>>(n, d, moving_list, n_moving, (float)momentum, (float)alpha, GT, V,
+                                                   X, lo, hi, dist);
+}
+
+void launch_cs_scatter_moving(int n, int d, const int32_t *moving_list, const int32_t *n_moving, const float *X32,
+                              double *X, cudaStream_t s) {
+    if (n <= 0) return;
+    note_launch();
+    k_cs_scatter_moving<<<warp_grid(n), 256, 0, s>>>(n, d, moving_list, n_moving, X32, X);
 }
 
 void launch_cs_state_init(int32_t *state, cudaStream_t s) {

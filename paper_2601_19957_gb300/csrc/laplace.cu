@@ -17,6 +17,7 @@
 //  * log Z_k = l(x*) + (d/2) log 2pi - sum_i log C_ii (Sec. 3.7.1 with the
 //    whitening identity of App. A.8) and log Z = LSE_k log Z_k - log V
 //    (Sec. 3.7.3, App. A.10, Sec. 3.2).
+#include "sb_graph.cuh"
 #include "sb_laplace.cuh"
 
 namespace sb {
@@ -903,6 +904,18 @@ void launch_precision_needed(int d, int K, const double *L, const double *R, con
     k_precision<<<g, 256, 0, s>>>(d, L, P, need);
 }
 
+// Condition of the blocked factorisation: some live candidate is not one-hot.
+__global__ void k_chol_needed(cudaGraphConditionalHandle h, const int32_t *n_c, const int32_t *onehot) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    const int nc = *n_c;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x)
+        if (onehot[c] < 0) any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
 void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P, const double *Z, const double *R,
                          const double *gbar, const int32_t *n_c, double *GK, double *H, int32_t *info,
                          cudaStream_t s, const int32_t *onehot) {
@@ -913,18 +926,35 @@ void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P
     k_hessian<<<dim3((unsigned)((dd + 255) / 256), cap), 256, 0, s>>>(d, K, P, GK, R, gbar, n_c, onehot, L, H,
                                                                         info);
     const int nblk = (d + NB - 1) / NB;
-    ProfScope prof(PROF_CHOLESKY, s);
-    for (int kb = 0; kb < nblk; ++kb) {
-        note_launch();
-        k_potrf_diag<<<cap, DIAG_THREADS, 0, s>>>(d, kb, H, n_c, onehot, info);
-        const int rest = nblk - kb - 1;
-        if (rest > 0) {
+    auto factor = [&](cudaStream_t fs) {
+        ProfScope prof(PROF_CHOLESKY, fs);
+        for (int kb = 0; kb < nblk; ++kb) {
             note_launch();
-            k_trsm_panel<<<dim3(rest, cap), TRSM_THREADS, 0, s>>>(d, kb, H, n_c, onehot, info);
-            note_launch();
-            k_syrk_update<<<dim3(rest, rest, cap), 256, 0, s>>>(d, kb, H, n_c, onehot, info);
+            k_potrf_diag<<<cap, DIAG_THREADS, 0, fs>>>(d, kb, H, n_c, onehot, info);
+            const int rest = nblk - kb - 1;
+            if (rest > 0) {
+                note_launch();
+                k_trsm_panel<<<dim3(rest, cap), TRSM_THREADS, 0, fs>>>(d, kb, H, n_c, onehot, info);
+                note_launch();
+                k_syrk_update<<<dim3(rest, rest, cap), 256, 0, fs>>>(d, kb, H, n_c, onehot, info);
+            }
         }
+    };
+    // in a graph, the factorisation is the body of an IF node that runs only when some
+    // live candidate is not one-hot (its launches would otherwise all be idle CTAs)
+    if (onehot && stream_capturing(s)) {
+        const sb_status st = capture_if(
+            s,
+            [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+                note_launch();
+                k_chol_needed<<<1, 256, 0, cs>>>(h, n_c, onehot);
+            },
+            factor);
+        if (st == SB_OK) return;
+        // the node could not be added: factor unconditionally (a capture left broken by
+        // the failure reports it when it ends)
     }
+    factor(s);
 }
 
 int laplace_sms() {

@@ -1170,20 +1170,30 @@ sb_status run_chisao(const Prelude &P, const sb_config *c, const sb_chisao_confi
         }
         // anti-convergence of every sample that is not stuck (the moving list)
         if (cc->anti_steps > 0) {
-            if (mixed)
-                launch_cs_stat_add(w.stats + 2, nullptr, (int64_t)n * cc->anti_steps, s);
-            else
-                launch_cs_stat_add32(w.stats + 2, w.cnt + 2, cc->anti_steps, s);
-            SB_CUDA_TRY(cudaMemsetAsync(w.V, 0, sizeof(double) * n * d, s));
-            for (int t = 0; t < cc->anti_steps; ++t) {
-                if (mixed) {  // every sample's gradient; the step moves the listed ones only
-                    st = tc_loglik_points(pv, c, P.L.r32.tc, w.X, n, nullptr, nullptr, w.ellg, w.G, s);
-                    if (st != SB_OK) return st;
-                } else {
-                    grad_at(w.moving_list, w.cnt + 2, n);
+            launch_cs_stat_add32(w.stats + 2, w.cnt + 2, cc->anti_steps, s);
+            if (mixed) {
+                // in FP32 on the walker evaluation of the refinement: the moving samples
+                // only, with the component skip (every component at the first step, then
+                // the bounds moved by the distance of each momentum step)
+                const TcWs &t = P.L.r32.tc;
+                float *X32 = w.O32, *V32 = w.U32;  // free once the reseeding rays are evaluated
+                tc_to_f32(w.X, X32, (size_t)n * d, s);
+                SB_CUDA_TRY(cudaMemsetAsync(V32, 0, sizeof(float) * n * d, s));
+                tc_walkers_reset(t, n, s);
+                for (int step = 0; step < cc->anti_steps; ++step) {
+                    tc_eval_walkers(pv, c, t, X32, w.moving_list, w.cnt + 2, n, P.L.r32.lb.FT, P.L.r32.lb.GT, s);
+                    launch_cs_momentum_f32(n, d, w.moving_list, w.cnt + 2, cc->momentum, cc->anti_alpha,
+                                           P.L.r32.lb.GT, V32, X32, pv.lo, pv.hi,
+                                           static_cast<float *>(t.p[kTcDistSlot]), s);
                 }
-                launch_cs_momentum(n, d, w.moving_list, w.cnt + 2, cc->momentum, cc->anti_alpha, w.G, w.V, w.X,
-                                   pv.lo, pv.hi, s);
+                launch_cs_scatter_moving(n, d, w.moving_list, w.cnt + 2, X32, w.X, s);
+            } else {
+                SB_CUDA_TRY(cudaMemsetAsync(w.V, 0, sizeof(double) * n * d, s));
+                for (int step = 0; step < cc->anti_steps; ++step) {
+                    grad_at(w.moving_list, w.cnt + 2, n);
+                    launch_cs_momentum(n, d, w.moving_list, w.cnt + 2, cc->momentum, cc->anti_alpha, w.G, w.V, w.X,
+                                       pv.lo, pv.hi, s);
+                }
             }
         }
         SB_CUDA_TRY(cudaGetLastError());

@@ -72,6 +72,14 @@ void launch_cs_ray_pick(int l0, int lc, int n_steps, int d, const int32_t *rows,
 void launch_cs_momentum(int n, int d, const int32_t *moving_list, const int32_t *n_moving, double momentum,
                         double alpha, const double *G, double *V, double *X, const double *lo, const double *hi,
                         cudaStream_t s);
+// The mixed path's momentum step in FP32 on the moving samples: GT = grad f (= -grad l),
+// v <- m v + alpha GT, x <- clamp(x + v); dist[s] = an upper bound on the move.
+void launch_cs_momentum_f32(int n, int d, const int32_t *moving_list, const int32_t *n_moving, double momentum,
+                            double alpha, const float *GT, float *V, float *X, const double *lo, const double *hi,
+                            float *dist, cudaStream_t s);
+// X[s] = (double) X32[s] for the moving samples.
+void launch_cs_scatter_moving(int n, int d, const int32_t *moving_list, const int32_t *n_moving, const float *X32,
+                              double *X, cudaStream_t s);
 // *dst += *src (when src is given) + v, on the device (evaluation counters).
 void launch_cs_stat_add(int64_t *dst, const int64_t *src, int64_t v, cudaStream_t s);
 // *dst += *src mult, on the device.

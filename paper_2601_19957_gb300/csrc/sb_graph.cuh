@@ -69,6 +69,46 @@ sb_status capture_while(cudaStream_t s, F body) {
     return SB_OK;
 }
 
+// Adds to the capture in progress on s an IF node whose body is what body(cs) enqueues
+// on the stream cs. set_cond(s, h) enqueues, before the node, a kernel that sets the
+// condition through h (it is 0 at every launch of the graph until then).
+template <typename C, typename F>
+sb_status capture_if(cudaStream_t s, C set_cond, F body) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamGetCaptureInfo(s, &st, nullptr, &g) != cudaSuccess || st != cudaStreamCaptureStatusActive)
+        return SB_ERR_CUDA;
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault) != cudaSuccess) return SB_ERR_CUDA;
+    set_cond(s, h);
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edata = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, &edata, &nd) != cudaSuccess ||
+        st != cudaStreamCaptureStatusActive)
+        return SB_ERR_CUDA;
+    std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+    std::vector<cudaGraphEdgeData> ev;
+    if (edata) ev.assign(edata, edata + nd);
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, dv.data(), edata ? ev.data() : nullptr, nd, &p) != cudaSuccess) return SB_ERR_CUDA;
+    cudaGraph_t bg = p.conditional.phGraph_out[0];
+    cudaStream_t cs = body_stream();
+    if (!cs || cudaStreamBeginCaptureToGraph(cs, bg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return SB_ERR_CUDA;
+    body(cs);
+    cudaGraph_t out = nullptr;
+    if (cudaStreamEndCapture(cs, &out) != cudaSuccess) return SB_ERR_CUDA;
+    if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+        return SB_ERR_CUDA;
+    return SB_OK;
+}
+
 // Cached executable graphs, keyed by every argument that shapes the captured work
 // (pointers, sizes, knobs). Runs `enqueue` on a capture stream the first time a key
 // is seen, instantiates the graph, and launches the instance on s (each time).
