@@ -832,7 +832,81 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
     if (count_bytes && threadIdx.x == 0 && bytes) atomicAdd(&g_lbfgs_bytes, (unsigned long long)bytes);
 }
 
+// The active list of the mixed path, compacted and grouped by each walker's dominant
+// component (key[w], the component of the largest term at its latest evaluation;
+// -1 goes last), keeping the list order inside a group: the evaluation round skips
+// (128-row block, component) pairs no row of the block needs, and walkers of
+// different basins interleaved in one block would make every block need every
+// component. Skipped terms are exactly zero, so the grouping changes no result. One
+// CTA: bucket totals, their exclusive sums, then 1024-entry chunks in order, each
+// thread's rank among its warp's equal keys (__match_any_sync) plus the earlier
+// warps' and chunks' counts of its bucket; the sorted list goes to tmp, then back.
+constexpr int kSortBuckets = kMaxK + 1;
+__global__ void __launch_bounds__(1024) k_lbfgs_compact_by_key(const WalkerState<float> *st, int32_t *act,
+                                                               int32_t *n_act, int64_t *n_evals, const int32_t *key,
+                                                               int K, int32_t *tmp) {
+    __shared__ int total[kSortBuckets], start[kSortBuckets], run[kSortBuckets];
+    __shared__ int wcnt[32][kSortBuckets];
+    const int prev = *n_act;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nb = K + 1;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) total[b] = 0;
+    if (threadIdx.x == 0 && n_evals) *n_evals += prev;
+    __syncthreads();
+    auto bucket_of = [&](int w) {
+        const int k = key[w];
+        return (k >= 0 && k < K) ? k : K;
+    };
+    for (int i = threadIdx.x; i < prev; i += blockDim.x) {
+        const int w = act[i];
+        if (st[w].status == SB_WALKER_RUNNING) atomicAdd(&total[bucket_of(w)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int b = 0; b < nb; ++b) {
+            start[b] = acc;
+            run[b] = 0;
+            acc += total[b];
+        }
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < prev; c0 += blockDim.x) {
+        const int i = c0 + (int)threadIdx.x;
+        const int w = i < prev ? act[i] : -1;
+        const bool keep = w >= 0 && st[w].status == SB_WALKER_RUNNING;
+        const int b = keep ? bucket_of(w) : -1;  // -1: dropped (its own match group)
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        for (int q = lane; q < nb; q += 32) wcnt[wid][q] = 0;
+        __syncwarp();
+        if (keep && rank == 0) wcnt[wid][b] = __popc(peers);
+        __syncthreads();
+        int off = 0;
+        if (keep)
+            for (int v = 0; v < wid; ++v) off += wcnt[v][b];
+        if (keep) tmp[start[b] + run[b] + off + rank] = w;
+        __syncthreads();  // every thread has read run[] and wcnt[] of this chunk
+        for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+            int t = 0;
+            for (int v = 0; v < 32; ++v) t += wcnt[v][q];
+            run[q] += t;
+        }
+        __syncthreads();
+    }
+    int n_new = 0;
+    for (int b = 0; b < nb; ++b) n_new += total[b];
+    for (int i = threadIdx.x; i < n_new; i += blockDim.x) act[i] = tmp[i];
+    if (threadIdx.x == 0) *n_act = n_new;
+}
+
 }  // namespace
+
+void launch_lbfgs_compact_by_key(const LbfgsArgs<float> &a, int64_t *n_evals, const int32_t *key, int K, int32_t *tmp,
+                                 cudaStream_t s) {
+    note_launch();
+    k_lbfgs_compact_by_key<<<1, 1024, 0, s>>>(a.st, a.act, a.n_act, n_evals, key, K, tmp);
+}
 
 void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *MYY, int num_sms, cudaStream_t s) {
     ProfScope prof(PROF_LBFGS_STEP, s);

@@ -168,6 +168,7 @@ struct RefineWs {
     float *MRI, *MYY;  // [N][m][m] R^-1 (R = upper(S^T Y)) and Y^T Y, slot-indexed (FP32 compact-form step)
     int64_t *n_evals;
     int64_t *round;         // rounds run (device-decided loop)
+    int32_t *act_tmp;       // [N] scratch of the grouped compaction (mixed path)
     double *qpart, *Z, *R;  // FP64 evaluation
     TcWs tc;                // mixed-precision evaluation
 };
@@ -231,6 +232,7 @@ void carve_refine(Carver &cv, RefineWs<T> &r, int n, int d, int K, int m, bool f
         r.R = cv.take<double>((size_t)n * K);
     } else {
         carve_tc(cv, r.tc, n, d, K, prec);
+        r.act_tmp = cv.take<int32_t>((size_t)n);
         r.MRI = cv.take<float>((size_t)n * m * m);
         r.MYY = cv.take<float>((size_t)n * m * m);
     }
@@ -463,7 +465,10 @@ sb_status run_refine(const ProbView &pv, const sb_config *c, const RefineWs<T> &
         for (int b = 0; b < kRoundsPerPoll; ++b) {
             eval_round<T>(pv, c, rr, n, bs);
             step_round<T>(rr, a, n, bs);
-            launch_lbfgs_compact<T>(a, ev, bs);
+            if constexpr (std::is_same<T, float>::value)  // walkers grouped by dominant component
+                launch_lbfgs_compact_by_key(a, ev, static_cast<const int32_t *>(r.tc.p[12]), pv.K, r.act_tmp, bs);
+            else
+                launch_lbfgs_compact<T>(a, ev, bs);
         }
     };
     if (stream_capturing(s)) {

@@ -44,6 +44,10 @@ void launch_lbfgs_compact(const LbfgsArgs<T> &a, int64_t *n_evals, cudaStream_t 
 // the stored pairs S, Y are bf16. MRI, MYY: per-walker [N][m][m] R^-1
 // (R = upper(S^T Y)) and Y^T Y, slot-indexed.
 void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *MYY, int num_sms, cudaStream_t s);
+// Compaction of the mixed path's active list, grouped by key[w] (the walker's dominant
+// component, 0..K-1; others last), the list order kept inside a group; tmp: [N] scratch.
+void launch_lbfgs_compact_by_key(const LbfgsArgs<float> &a, int64_t *n_evals, const int32_t *key, int K, int32_t *tmp,
+                                 cudaStream_t s);
 // Algorithmic bytes moved by the FP32 step launches while profiling was on
 // (synchronises the device, then clears the counter); -1 on a CUDA error.
 double lbfgs_bytes_take();
