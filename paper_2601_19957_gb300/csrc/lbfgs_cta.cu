@@ -150,13 +150,29 @@ template <int CT>
 struct Vec {
     float4 v[Cfg<CT>::VPT];
     __device__ __forceinline__ static int i0(int q) { return 4 * (Cfg<CT>::VPT * (int)threadIdx.x + q); }
+    // EVEN: d % (4 VPT) == 0, so a thread holds all of its coordinates or none
+    template <bool EVEN>
     __device__ __forceinline__ void load(const float *p, int d) {
+        if (EVEN) {
+            const bool own = i0(0) < d;
 #pragma unroll
-        for (int q = 0; q < Cfg<CT>::VPT; ++q) v[q] = ld4(p, i0(q), d);
+            for (int q = 0; q < Cfg<CT>::VPT; ++q)
+                v[q] = own ? *reinterpret_cast<const float4 *>(p + i0(q)) : zero4();
+        } else {
+#pragma unroll
+            for (int q = 0; q < Cfg<CT>::VPT; ++q) v[q] = ld4(p, i0(q), d);
+        }
     }
+    template <bool EVEN>
     __device__ __forceinline__ void store(float *p, int d) const {
+        if (EVEN) {
+            if (i0(0) < d)
 #pragma unroll
-        for (int q = 0; q < Cfg<CT>::VPT; ++q) st4(p, i0(q), d, v[q]);
+                for (int q = 0; q < Cfg<CT>::VPT; ++q) *reinterpret_cast<float4 *>(p + i0(q)) = v[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < Cfg<CT>::VPT; ++q) st4(p, i0(q), d, v[q]);
+        }
     }
     __device__ __forceinline__ void zero() {
 #pragma unroll
@@ -416,10 +432,11 @@ using bf16 = __nv_bfloat16;
 
 // Stores this thread's coordinates of a history vector (values already bf16):
 // 8 consecutive coordinates, one 16-byte chunk.
-template <int CT>
+template <int CT, bool EVEN>
 __device__ __forceinline__ void store_hist(const Vec<CT> &v, bf16 *row, int d) {
     const int e0 = Vec<CT>::i0(0);
-    if ((d & 7) == 0 && e0 + 7 < d) {
+    if (EVEN && e0 >= d) return;
+    if (EVEN || ((d & 7) == 0 && e0 + 7 < d)) {
         *reinterpret_cast<uint4 *>(row + e0) = make_uint4(pack2(v.v[0].x, v.v[0].y), pack2(v.v[0].z, v.v[0].w),
                                                           pack2(v.v[1].x, v.v[1].y), pack2(v.v[1].z, v.v[1].w));
     } else {
@@ -433,7 +450,7 @@ __device__ __forceinline__ void store_hist(const Vec<CT> &v, bf16 *row, int d) {
 // Within a block the chunk of thread t sits at t ^ (block % 8), so the same
 // chunk of 8 consecutive blocks (the rows of one ldmatrix) falls in 8 different
 // bank groups.
-template <int CT>
+template <int CT, bool EVEN>
 struct Ring {
     static constexpr int PG = Cfg<CT>::PGB;
     static constexpr int D = Cfg<CT>::DB;
@@ -449,7 +466,12 @@ struct Ring {
     __device__ __forceinline__ void copy_in(int sl, int q, int v, const bf16 *row) const {
         uint4 *dst = at(sl, q, v, threadIdx.x);
         const int e0 = Vec<CT>::i0(0);  // 8 consecutive elements
-        if ((d & 7) == 0 && e0 + 7 < d) {
+        if (EVEN) {
+            if (e0 < d)
+                cp_async16(dst, row + e0);
+            else
+                *dst = make_uint4(0u, 0u, 0u, 0u);
+        } else if ((d & 7) == 0 && e0 + 7 < d) {
             cp_async16(dst, row + e0);
         } else {
             uint16_t h[8];
@@ -467,6 +489,7 @@ struct Ring {
         sv.v[1] = unpack4(a4.z, a4.w);
         yv.v[0] = unpack4(b4.x, b4.y);
         yv.v[1] = unpack4(b4.z, b4.w);
+        if (EVEN) return;  // chunks past d are copied in as zeros
 #pragma unroll
         for (int j = 0; j < Cfg<CT>::VPT; ++j) {
             const int i0 = Vec<CT>::i0(j);
@@ -502,12 +525,12 @@ struct Ring {
 // the unit trial X + P; updates st.dphi / alpha / bt and possibly resets the
 // history (steepest descent when p is not a descent direction). Returns the
 // algorithmic bytes moved.
-template <int CT>
+template <int CT, bool EVEN>
 __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<float> &st, int new_slot,
                               const Vec<CT> &g_in, const Vec<CT> &x_in,
                               const Vec<CT> &s_new, const Vec<CT> &y_new, float *MRI, float *MYY,
                               Shared<CT> &sh, int &par) {
-    using RG = Ring<CT>;
+    using RG = Ring<CT, EVEN>;
     constexpr int PG = RG::PG, D = RG::D, NW = Cfg<CT>::NW;
     const int d = a.d, m = a.m;
     const int count = st.count;
@@ -633,8 +656,8 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
         const int ng2 = (count + PG - 1) / PG;
 #pragma unroll 1
         for (int k = 0; k < D; ++k) ring.issue(k, count, st.head, m, S, Y);  // pass 2's first groups
-        g.load(a.G + (size_t)w * d, d);
-        x.load(a.X + (size_t)w * d, d);
+        g.template load<EVEN>(a.G + (size_t)w * d, d);
+        x.template load<EVEN>(a.X + (size_t)w * d, d);
         __syncthreads();
         solve_mm<CT>(sh, count, cn, mri_w, m, st.head);
         __syncthreads();
@@ -683,15 +706,15 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
     st.pn = sqrtf(dp[1]);
     st.alpha = 1.f;
     st.bt = 0;
-    p.store(a.P + (size_t)w * d, d);
-    lincomb(x, 1.f, p).store(a.XT + (size_t)w * d, d);
+    p.template store<EVEN>(a.P + (size_t)w * d, d);
+    lincomb(x, 1.f, p).template store<EVEN>(a.XT + (size_t)w * d, d);
     return bytes + (uint64_t)8 * d;
 }
 
 // Algorithmic bytes of the L-BFGS step launches (added only while counting is on).
 __device__ unsigned long long g_lbfgs_bytes;
 
-template <int CT>
+template <int CT, bool EVEN>
 __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float> a, float *MRI, float *MYY,
                                                                 int count_bytes) {
     __shared__ Shared<CT> sh;
@@ -728,10 +751,10 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
         float *X = a.X + (size_t)w * d;
         float *G = a.G + (size_t)w * d;
         Vec<CT> x, g, xt, gt;
-        x.load(X, d);
-        g.load(G, d);
-        xt.load(a.XT + (size_t)w * d, d);
-        gt.load(a.GT + (size_t)w * d, d);
+        x.template load<EVEN>(X, d);
+        g.template load<EVEN>(G, d);
+        xt.template load<EVEN>(a.XT + (size_t)w * d, d);
+        gt.template load<EVEN>(a.GT + (size_t)w * d, d);
         bytes += (uint64_t)16 * d + 4 + 2 * sizeof(WalkerState<float>);
         // finiteness of the trial gradient, the candidate pair's inner products and
         // max |grad| at the trial, all in one reduction
@@ -753,8 +776,8 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
         if (st.phase == 0) {
             x = xt;
             g = gt;
-            x.store(X, d);
-            g.store(G, d);
+            x.template store<EVEN>(X, d);
+            g.template store<EVEN>(G, d);
             bytes += (uint64_t)8 * d;
             st.f = ft;
             st.phase = 1;
@@ -772,8 +795,8 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                     slot = st.head;
                     st.head = (st.head + 1) % m;
                 }
-                store_hist<CT>(s4, reinterpret_cast<bf16 *>(a.S) + ((size_t)w * m + slot) * d, d);
-                store_hist<CT>(y4, reinterpret_cast<bf16 *>(a.Y) + ((size_t)w * m + slot) * d, d);
+                store_hist<CT, EVEN>(s4, reinterpret_cast<bf16 *>(a.S) + ((size_t)w * m + slot) * d, d);
+                store_hist<CT, EVEN>(y4, reinterpret_cast<bf16 *>(a.Y) + ((size_t)w * m + slot) * d, d);
                 bytes += (uint64_t)2 * d * sizeof(bf16);
                 new_slot = slot;
                 s_new = s4;
@@ -782,8 +805,8 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
             st.flat = (ft >= st.f) ? st.flat + 1 : 0;
             x = xt;
             g = gt;
-            x.store(X, d);
-            g.store(G, d);
+            x.template store<EVEN>(X, d);
+            g.template store<EVEN>(G, d);
             bytes += (uint64_t)8 * d;
             st.f = ft;
             ++st.it;
@@ -793,15 +816,15 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
             if (st.bt <= a.max_backtracks) {
                 st.alpha *= a.backtrack;
                 Vec<CT> p;
-                p.load(a.P + (size_t)w * d, d);
-                lincomb(x, st.alpha, p).store(a.XT + (size_t)w * d, d);
+                p.template load<EVEN>(a.P + (size_t)w * d, d);
+                lincomb(x, st.alpha, p).template store<EVEN>(a.XT + (size_t)w * d, d);
                 bytes += (uint64_t)8 * d;
                 dnext = (alpha0 - st.alpha) * st.pn;
             } else if (st.count > 0 && st.attempt == 0) {
                 st.count = 0;
                 st.head = 0;
                 st.attempt = 1;
-                bytes += direction<CT>(a, w, st, -1, g, x, s_new, y_new, MRI, MYY, sh, par);
+                bytes += direction<CT, EVEN>(a, w, st, -1, g, x, s_new, y_new, MRI, MYY, sh, par);
                 dnext = st.pn + alpha0 * pn0;  // from the old trial back to x, then out
             } else {
                 st.status = SB_WALKER_STALLED;
@@ -816,7 +839,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                 st.status = SB_WALKER_MAXITER;
             } else {
                 st.attempt = 0;
-                bytes += direction<CT>(a, w, st, new_slot, g, x, s_new, y_new, MRI, MYY, sh, par);
+                bytes += direction<CT, EVEN>(a, w, st, new_slot, g, x, s_new, y_new, MRI, MYY, sh, par);
                 dnext = st.pn;  // x is this visit's trial
             }
         }
@@ -837,67 +860,137 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
 // -1 goes last), keeping the list order inside a group: the evaluation round skips
 // (128-row block, component) pairs no row of the block needs, and walkers of
 // different basins interleaved in one block would make every block need every
-// component. Skipped terms are exactly zero, so the grouping changes no result. One
-// CTA: bucket totals, their exclusive sums, then 1024-entry chunks in order, each
-// thread's rank among its warp's equal keys (__match_any_sync) plus the earlier
-// warps' and chunks' counts of its bucket; the sorted list goes to tmp, then back.
+// component. Skipped terms are exactly zero, so the grouping changes no result.
+// One CTA, two passes over the list, both in chunks of kCompactE consecutive entries
+// per thread (so lane, then warp order is list order). Pass 1 gathers each entry's
+// walker, status and key (independent loads), packs (bucket, walker) and counts the
+// buckets (per warp, then across warps); their exclusive sums give each bucket's
+// first output slot. Pass 2: per bucket present in a warp, a lane's rank is a warp
+// scan of the per-lane counts and the warp's offset a scan over the warps' totals
+// after the bucket's entries from earlier chunks; every entry goes straight to its
+// slot of act, which pass 1 has read in full. A list longer than one chunk parks the
+// packed entries in tmp between the passes; a shorter one keeps them in registers.
 constexpr int kSortBuckets = kMaxK + 1;
+constexpr int kCompactE = 16;                    // consecutive entries per thread
+constexpr int kCompactChunk = 1024 * kCompactE;  // entries per chunk
+constexpr int kPackShift = 25;                   // packed entry: bucket << 25 | walker
+constexpr uint32_t kPackDrop = 0xffffffffu;      // a dropped entry (bucket field 127)
+static_assert(kSortBuckets < 127, "the bucket field holds 7 bits");
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Buckets present in this warp's entries (bit b for bucket b < nb).
+__device__ __forceinline__ uint64_t warp_buckets(const uint32_t (&pk)[kCompactE], int nb) {
+    uint64_t present = 0;
+#pragma unroll
+    for (int e = 0; e < kCompactE; ++e) {
+        const uint32_t b = pk[e] >> kPackShift;
+        if (b < (uint32_t)nb) present |= 1ull << b;
+    }
+    return (uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)present) |
+           ((uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)(present >> 32)) << 32);
+}
+__device__ __forceinline__ int count_bucket(const uint32_t (&pk)[kCompactE], int b) {
+    int cnt = 0;
+#pragma unroll
+    for (int e = 0; e < kCompactE; ++e) cnt += (pk[e] >> kPackShift) == (uint32_t)b;
+    return cnt;
+}
+
 __global__ void __launch_bounds__(1024) k_lbfgs_compact_by_key(const WalkerState<float> *st, int32_t *act,
                                                                int32_t *n_act, int64_t *n_evals, const int32_t *key,
-                                                               int K, int32_t *tmp) {
-    __shared__ int total[kSortBuckets], start[kSortBuckets], run[kSortBuckets];
-    __shared__ int wcnt[32][kSortBuckets];
+                                                               int K, uint32_t *tmp) {
+    __shared__ int total[kSortBuckets], base[kSortBuckets];
+    __shared__ int wtot[32][kSortBuckets], woff[32][kSortBuckets];
     const int prev = *n_act;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nb = K + 1;
+    const bool parked = prev > kCompactChunk;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) total[b] = 0;
     if (threadIdx.x == 0 && n_evals) *n_evals += prev;
     __syncthreads();
-    auto bucket_of = [&](int w) {
-        const int k = key[w];
-        return (k >= 0 && k < K) ? k : K;
-    };
-    for (int i = threadIdx.x; i < prev; i += blockDim.x) {
-        const int w = act[i];
-        if (st[w].status == SB_WALKER_RUNNING) atomicAdd(&total[bucket_of(w)], 1);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int b = 0; b < nb; ++b) {
-            start[b] = acc;
-            run[b] = 0;
-            acc += total[b];
+    uint32_t pk[kCompactE];
+    // pass 1
+    for (int c0 = 0; c0 < prev; c0 += kCompactChunk) {
+        const int s0 = c0 + (int)threadIdx.x * kCompactE;
+        int w[kCompactE], k[kCompactE];
+        bool run[kCompactE];
+#pragma unroll
+        for (int e = 0; e < kCompactE; ++e) w[e] = s0 + e < prev ? act[s0 + e] : -1;
+#pragma unroll
+        for (int e = 0; e < kCompactE; ++e) {
+            run[e] = w[e] >= 0 && st[w[e]].status == SB_WALKER_RUNNING;
+            k[e] = w[e] >= 0 ? key[w[e]] : -1;
+        }
+#pragma unroll
+        for (int e = 0; e < kCompactE; ++e) {
+            const int b = (k[e] >= 0 && k[e] < K) ? k[e] : K;
+            pk[e] = run[e] ? ((uint32_t)b << kPackShift) | (uint32_t)w[e] : kPackDrop;
+            if (parked && s0 + e < prev) tmp[s0 + e] = pk[e];
+        }
+        for (uint64_t m = warp_buckets(pk, nb); m; m &= m - 1) {
+            const int b = __ffsll((long long)m) - 1;
+            const int sum = __reduce_add_sync(0xffffffffu, count_bucket(pk, b));
+            if (lane == 0) atomicAdd(&total[b], sum);
         }
     }
     __syncthreads();
-    for (int c0 = 0; c0 < prev; c0 += blockDim.x) {
-        const int i = c0 + (int)threadIdx.x;
-        const int w = i < prev ? act[i] : -1;
-        const bool keep = w >= 0 && st[w].status == SB_WALKER_RUNNING;
-        const int b = keep ? bucket_of(w) : -1;  // -1: dropped (its own match group)
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        const int rank = __popc(peers & ((1u << lane) - 1u));
-        for (int q = lane; q < nb; q += 32) wcnt[wid][q] = 0;
+    if (wid == 0) {  // exclusive sums of the bucket totals, 32 buckets at a time
+        int carry = 0;
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+            const int b = b0 + lane;
+            const int v = b < nb ? total[b] : 0;
+            const int incl = warp_incl_scan(v);
+            if (b < nb) base[b] = carry + incl - v;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) *n_act = carry;
+    }
+    __syncthreads();
+    // pass 2
+    for (int c0 = 0; c0 < prev; c0 += kCompactChunk) {
+        const int s0 = c0 + (int)threadIdx.x * kCompactE;
+        if (parked) {
+#pragma unroll
+            for (int e = 0; e < kCompactE; ++e) pk[e] = s0 + e < prev ? tmp[s0 + e] : kPackDrop;
+        }
+        const uint64_t wpres = warp_buckets(pk, nb);
+        for (int b = lane; b < nb; b += 32) wtot[wid][b] = 0;
         __syncwarp();
-        if (keep && rank == 0) wcnt[wid][b] = __popc(peers);
-        __syncthreads();
-        int off = 0;
-        if (keep)
-            for (int v = 0; v < wid; ++v) off += wcnt[v][b];
-        if (keep) tmp[start[b] + run[b] + off + rank] = w;
-        __syncthreads();  // every thread has read run[] and wcnt[] of this chunk
-        for (int q = threadIdx.x; q < nb; q += blockDim.x) {
-            int t = 0;
-            for (int v = 0; v < 32; ++v) t += wcnt[v][q];
-            run[q] += t;
+        for (uint64_t m = wpres; m; m &= m - 1) {
+            const int b = __ffsll((long long)m) - 1;
+            const int incl = warp_incl_scan(count_bucket(pk, b));
+            if (lane == 31) wtot[wid][b] = incl;
         }
         __syncthreads();
+        // per bucket: the warps' offsets (scan over the 32 warps' totals) after the
+        // entries of the bucket from earlier chunks
+        for (int b = wid; b < nb; b += 32) {
+            const int v = wtot[lane][b];
+            const int incl = warp_incl_scan(v);
+            woff[lane][b] = base[b] + incl - v;
+            __syncwarp();
+            if (lane == 31) base[b] += incl;
+        }
+        __syncthreads();
+        for (uint64_t m = wpres; m; m &= m - 1) {
+            const int b = __ffsll((long long)m) - 1;
+            const int cnt = count_bucket(pk, b);
+            int pos = woff[wid][b] + warp_incl_scan(cnt) - cnt;
+#pragma unroll
+            for (int e = 0; e < kCompactE; ++e)
+                if ((pk[e] >> kPackShift) == (uint32_t)b) act[pos++] = (int32_t)(pk[e] & ((1u << kPackShift) - 1u));
+        }
+        __syncthreads();  // wtot, woff and base are rewritten by the next chunk
     }
-    int n_new = 0;
-    for (int b = 0; b < nb; ++b) n_new += total[b];
-    for (int i = threadIdx.x; i < n_new; i += blockDim.x) act[i] = tmp[i];
-    if (threadIdx.x == 0) *n_act = n_new;
 }
 
 }  // namespace
@@ -905,8 +998,11 @@ __global__ void __launch_bounds__(1024) k_lbfgs_compact_by_key(const WalkerState
 void launch_lbfgs_compact_by_key(const LbfgsArgs<float> &a, int64_t *n_evals, const int32_t *key, int K, int32_t *tmp,
                                  cudaStream_t s) {
     note_launch();
-    k_lbfgs_compact_by_key<<<1, 1024, 0, s>>>(a.st, a.act, a.n_act, n_evals, key, K, tmp);
+    k_lbfgs_compact_by_key<<<1, 1024, 0, s>>>(a.st, a.act, a.n_act, n_evals, key, K,
+                                              reinterpret_cast<uint32_t *>(tmp));
 }
+
+bool lbfgs_compact_by_key_fits(int n) { return n >= 0 && n < (1 << kPackShift); }
 
 void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *MYY, int num_sms, cudaStream_t s) {
     ProfScope prof(PROF_LBFGS_STEP, s);
@@ -917,10 +1013,15 @@ void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *
     static std::once_flag once;  // batched solves launch from several host threads
     std::call_once(once, [] {
         const size_t most = (size_t)Cfg<kCT>::RING_F4 * sizeof(float4) + sizeof(float) * mm_floats<kCT>(kMaxM);
-        cudaFuncSetAttribute(k_lbfgs_cta<kCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+        cudaFuncSetAttribute(k_lbfgs_cta<kCT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+        cudaFuncSetAttribute(k_lbfgs_cta<kCT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     });
     note_launch();
-    k_lbfgs_cta<kCT><<<grid, kCT, dyn, s>>>(a, MRI, MYY, count_bytes);
+    // d a multiple of 8 (one whole 16-byte chunk per thread or none): no per-element bounds
+    if (a.d % (4 * Cfg<kCT>::VPT) == 0)
+        k_lbfgs_cta<kCT, true><<<grid, kCT, dyn, s>>>(a, MRI, MYY, count_bytes);
+    else
+        k_lbfgs_cta<kCT, false><<<grid, kCT, dyn, s>>>(a, MRI, MYY, count_bytes);
 }
 
 double lbfgs_bytes_take() {

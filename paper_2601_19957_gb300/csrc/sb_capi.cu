@@ -465,10 +465,14 @@ sb_status run_refine(const ProbView &pv, const sb_config *c, const RefineWs<T> &
         for (int b = 0; b < kRoundsPerPoll; ++b) {
             eval_round<T>(pv, c, rr, n, bs);
             step_round<T>(rr, a, n, bs);
-            if constexpr (std::is_same<T, float>::value)  // walkers grouped by dominant component
-                launch_lbfgs_compact_by_key(a, ev, static_cast<const int32_t *>(r.tc.p[12]), pv.K, r.act_tmp, bs);
-            else
-                launch_lbfgs_compact<T>(a, ev, bs);
+            bool keyed = false;
+            if constexpr (std::is_same<T, float>::value) {  // walkers grouped by dominant component
+                if (lbfgs_compact_by_key_fits(n)) {
+                    launch_lbfgs_compact_by_key(a, ev, static_cast<const int32_t *>(r.tc.p[12]), pv.K, r.act_tmp, bs);
+                    keyed = true;
+                }
+            }
+            if (!keyed) launch_lbfgs_compact<T>(a, ev, bs);
         }
     };
     if (stream_capturing(s)) {

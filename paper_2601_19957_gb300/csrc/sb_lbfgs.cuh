@@ -48,6 +48,9 @@ void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *
 // component, 0..K-1; others last), the list order kept inside a group; tmp: [N] scratch.
 void launch_lbfgs_compact_by_key(const LbfgsArgs<float> &a, int64_t *n_evals, const int32_t *key, int K, int32_t *tmp,
                                  cudaStream_t s);
+// Whether n walkers fit the keyed compaction (walker ids below 2^25; else the plain
+// compaction runs, with the same results).
+bool lbfgs_compact_by_key_fits(int n);
 // Algorithmic bytes moved by the FP32 step launches while profiling was on
 // (synchronises the device, then clears the counter); -1 on a CUDA error.
 double lbfgs_bytes_take();

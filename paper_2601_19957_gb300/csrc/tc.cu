@@ -16,9 +16,11 @@
 //   k_tc_gemm ZW  z = A1 L_k (GEMM1) for the kept pairs: |z|^2 partials, and z
 //                 itself stored (bf16 / tf32) as Z[k][n][:] when the gradient is wanted
 //                 (ZR: the |z|^2 partials only, for l alone, e.g. at ray samples)
-//   k_tc_lse      l, r; flags of the (128-row block, component) pairs with r > 0
+//   k_tc_lse      l, r; flags of the (128-row block, component) pairs with r > 0,
+//                 marking those whose live rows all have r = 1 exactly
 //   k_tc_scale_z  Z[k][n][:] = round(r_nk z_nk) for the flagged pairs (the A
-//                 operand of GEMM2; rows with r_nk = 0 become zeros)
+//                 operand of GEMM2; rows with r_nk = 0 become zeros), except the
+//                 pairs with r = 1 throughout, where it is the identity
 //   k_tc_gemm G   grad f = sum_k Z_k L_k^T rows over the flagged components (GEMM2)
 // With separated modes most responsibilities are exactly 0 in FP32 (the
 // exponent underflows), so the scaling pass and GEMM2 visit a fraction of the
@@ -79,7 +81,7 @@ struct TcArgs {
     int ldz, z_rows;
     float *qpart;           // [rows][K][n_ntile]
     const float *R;         // [rows][K]
-    const uint32_t *rflag;  // [row blocks][K]: some row of the block has r_nk > 0
+    const uint32_t *rflag;  // [row blocks][K]: 1 some row of the block has r_nk > 0; 3 every live row r_nk = 1
     const uint32_t *zmask;  // [row blocks][K]: GEMM1 |z|^2 pairs to visit (null: all; see k_tc_need)
     int prof;               // profiling class of the launch (-1: by mode)
     float *G;               // [walkers][d] grad f
@@ -171,25 +173,26 @@ struct TileInfo {
     int mb, nt, k;     // row block, output column tile, component (GEMM1)
     int c_lo, c_hi;    // K-chunk range (GEMM1) or chunk count per component (GEMM2: c_hi)
     int nchunks;
-    uint32_t kmask;    // GEMM2: components with r_nk > 0 somewhere in the row block
+    uint64_t kmask;    // GEMM2: components with r_nk > 0 somewhere in the row block
     bool skip;         // GEMM1 store pass: this (row block, component) is not needed
 };
 
 // Components with r_nk > 0 at some row of row block mb (all when no flags are
-// given); a block with none keeps component 0 (non-finite or empty rows).
-__device__ __forceinline__ uint32_t block_kmask(const uint32_t *rflag, int mb, int K) {
-    uint32_t m = 0;
+// given); a block with none keeps component 0 (non-finite or empty rows). One bit
+// per component (K <= 64).
+__device__ __forceinline__ uint64_t block_kmask(const uint32_t *rflag, int mb, int K) {
+    uint64_t m = 0;
     for (int k = 0; k < K; ++k)
-        if (!rflag || rflag[(size_t)mb * K + k]) m |= 1u << k;
-    return m ? m : 1u;
+        if (!rflag || rflag[(size_t)mb * K + k]) m |= 1ull << k;
+    return m ? m : 1ull;
 }
 
 // Component of GEMM2 chunk q: the (q / c_hi)-th set bit of the tile's mask.
 __device__ __forceinline__ int chunk_component(const TileInfo &ti, int q) {
     int idx = q / ti.c_hi;
-    uint32_t m = ti.kmask;
+    uint64_t m = ti.kmask;
     while (idx-- > 0) m &= m - 1;
-    return __ffs(m) - 1;
+    return __ffsll((long long)m) - 1;
 }
 
 template <int MODE, int BN, int KC>
@@ -215,7 +218,7 @@ __device__ __forceinline__ TileInfo decode_tile(int t, int d, int K, const uint3
         // exactly nothing to the gradient: their chunks are not visited (every
         // role reads the same flags, so the three agree on the chunk list)
         ti.kmask = block_kmask(rflag, ti.mb, K);
-        ti.nchunks = __popc(ti.kmask) * ti.c_hi;
+        ti.nchunks = __popcll(ti.kmask) * ti.c_hi;
     } else {
         // column tiles of one (row block, component) are adjacent in the schedule, so
         // CTAs that run together gather the same x rows (served from L2)
@@ -228,7 +231,7 @@ __device__ __forceinline__ TileInfo decode_tile(int t, int d, int K, const uint3
         // store pass (flags given): only the (block, component) pairs GEMM2 reads;
         // |z|^2 pass (mask given): only the pairs k_tc_need keeps (already the case
         // for a compacted schedule)
-        if (MODE != MODE_G && rflag && !glist) ti.skip = !((block_kmask(rflag, ti.mb, K) >> ti.k) & 1u);
+        if (MODE != MODE_G && rflag && !glist) ti.skip = !((block_kmask(rflag, ti.mb, K) >> ti.k) & 1ull);
     }
     return ti;
 }
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
         __syncthreads();
         for (int g0 = 0; g0 < n_groups; g0 += (int)blockDim.x) {
             const int g = g0 + (int)threadIdx.x;
-            const bool act = g < n_groups && ((block_kmask(gmask, g / K, K) >> (g % K)) & 1u);
+            const bool act = g < n_groups && ((block_kmask(gmask, g / K, K) >> (g % K)) & 1ull);
             const unsigned bal = __ballot_sync(0xffffffffu, act);
             if (lane == 0) s_wcnt[warp] = __popc(bal);
             __syncthreads();
@@ -498,13 +501,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                                 }
                             }
                         } else {
+                            // rounded to tf32 as stored (as bf16 is by its packing), so that a
+                            // pair the scaling pass skips is GEMM2's operand as it stands
                             float *zr = reinterpret_cast<float *>(a.Z) + zrow;
 #pragma unroll
                             for (int e = 0; e < 32; e += 4)
                                 if (col + e + 4 <= a.ldz)
                                     *reinterpret_cast<float4 *>(zr + e) =
-                                        make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]),
-                                                    __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
+                                        make_float4(to_tf32(__uint_as_float(v[e])), to_tf32(__uint_as_float(v[e + 1])),
+                                                    to_tf32(__uint_as_float(v[e + 2])),
+                                                    to_tf32(__uint_as_float(v[e + 3])));
                         }
                     }
                 }
@@ -546,14 +552,14 @@ __global__ void __launch_bounds__(128) k_tc_lse(int mode, int K, int n_ntile, co
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = n < n_rows;
     // components the |z|^2 pass skipped for this row block (zmask): e_k = -inf
-    const uint32_t km = zmask ? block_kmask(zmask, n / BM, K) : 0xffffffffu;
+    const uint64_t km = zmask ? block_kmask(zmask, n / BM, K) : ~0ull;
     double e[kMaxK];
     double emax = -INFINITY;
     float s = 0.f;
     if (valid) {
         for (int k = 0; k < K; ++k) {
             e[k] = -INFINITY;
-            if (!((km >> k) & 1u)) continue;
+            if (!((km >> k) & 1ull)) continue;
             const float *qp = qpart + ((size_t)n * K + k) * n_ntile;
             double q = 0.0;
             for (int t = 0; t < n_ntile; ++t) q += (double)qp[t];
@@ -569,7 +575,7 @@ __global__ void __launch_bounds__(128) k_tc_lse(int mode, int K, int n_ntile, co
         const int w = act ? act[n] : n;
         int jm = -1;
         for (int k = 0; k < K; ++k) {
-            if (!((km >> k) & 1u)) continue;
+            if (!((km >> k) & 1ull)) continue;
             const double q = (a_k[k] - e[k]) * 2.0;
             if (isfinite(e[k])) zb[(size_t)w * K + k] = __double2float_rd(sqrt(fmax(q, 0.0)) * (1.0 - 1.0 / 32));
             if (isfinite(e[k]) && e[k] == emax && jm < 0) jm = k;
@@ -583,12 +589,31 @@ __global__ void __launch_bounds__(128) k_tc_lse(int mode, int K, int n_ntile, co
         return;
     }
     const float inv = 1.f / s;
+    // One CTA is one 128-row block. Flag of (block, component k): bit 0 when some row
+    // has r_nk > 0; bit 1 as well when every live row has r_nk == 1 exactly (all other
+    // terms of each row underflow), where r z = z and the scaling pass is skipped.
+    __shared__ unsigned long long s_any, s_one;
+    if (threadIdx.x == 0) {
+        s_any = 0ull;
+        s_one = ~0ull;
+    }
+    __syncthreads();
+    uint64_t any_m = 0, one_m = 0;
     for (int k = 0; k < K; ++k) {
         const float r = valid ? __expf((float)(e[k] - emax)) * inv : 0.f;
         if (valid) R[(size_t)n * K + k] = r;
-        // row block of 128 rows = four whole warps: one flag per (block, component)
-        const unsigned any = __ballot_sync(0xffffffffu, r > 0.f);
-        if (rflag && any && (threadIdx.x & 31) == 0) atomicOr(&rflag[(size_t)(n / 128) * K + k], 1u);
+        if (__any_sync(0xffffffffu, r > 0.f)) any_m |= 1ull << k;
+        if (__all_sync(0xffffffffu, !valid || r == 1.f)) one_m |= 1ull << k;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicOr(&s_any, (unsigned long long)any_m);
+        atomicAnd(&s_one, (unsigned long long)one_m);
+    }
+    __syncthreads();
+    if (rflag && (int)threadIdx.x < K) {
+        const int k = threadIdx.x;
+        const bool any = (s_any >> k) & 1ull, one = (s_one >> k) & 1ull;
+        rflag[(size_t)blockIdx.x * K + k] = any ? (one ? 3u : 1u) : 0u;
     }
     if (!valid) return;
     if (mode == 0)
@@ -600,44 +625,55 @@ __global__ void __launch_bounds__(128) k_tc_lse(int mode, int K, int n_ntile, co
 // GEMM2's A operand from the stored z: for every (128-row block, component) pair whose
 // flag says some row has r_nk > 0, Z[k][n][:] = round(r_nk z_nk) (rows past the live
 // count, and rows with r_nk = 0, become exact zeros), so GEMM2 adds r_nk L_k z_nk.
+// Pairs whose live rows all have r_nk = 1 (flag 3) keep the stored z, which is already
+// rounded: round(1 z) = z. Their rows past the live count keep stale values, which
+// reach only GEMM2 output rows that are not stored (each output row depends on its
+// own A row alone).
 template <int PREC>
 __global__ void __launch_bounds__(256) k_tc_scale_z(int K, int ldz, int z_rows, const int32_t *n_rows_dev,
                                                     int n_rows_max, const float *R, const uint32_t *rflag, void *Z) {
     const int mb = blockIdx.x, k = blockIdx.y;
-    if (!rflag[(size_t)mb * K + k]) return;
+    if (rflag[(size_t)mb * K + k] != 1u) return;
     const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
     constexpr int VE = (PREC == SB_PREC_BF16) ? 8 : 4;  // elements per 16-byte vector
-    const int nv = ldz / VE;
-    for (int e = threadIdx.x; e < BM * nv; e += blockDim.x) {
-        const int row = e / nv, v = e - row * nv;
-        const int n = mb * BM + row;
-        if (n >= z_rows) break;
-        const float r = n < n_rows ? R[(size_t)n * K + k] : 0.f;
-        const size_t off = ((size_t)k * z_rows + n) * ldz + (size_t)v * VE;
-        if (PREC == SB_PREC_BF16) {
-            uint4 *p = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(Z) + off);
+    constexpr int NB = 16;                              // vectors in flight per thread
+    const int nv = ldz / VE, tot = BM * nv;
+    uint4 *Zv = reinterpret_cast<uint4 *>(Z);  // 16-byte vectors (ldz is a multiple of 64 elements)
+    for (int e0 = 0; e0 < tot; e0 += NB * (int)blockDim.x) {
+        // every load of the batch is issued before the first store
+        uint4 w[NB];
+        float r[NB];
+        size_t at[NB];
+        bool in[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            const int e = e0 + (int)threadIdx.x + j * (int)blockDim.x;
+            const int row = e / nv, v = e - row * nv;
+            const int n = mb * BM + row;
+            in[j] = e < tot && n < z_rows;
+            r[j] = (in[j] && n < n_rows) ? R[(size_t)n * K + k] : 0.f;
+            at[j] = (((size_t)k * z_rows + n) * ldz) / VE + (size_t)v;
+            w[j] = (in[j] && r[j] > 0.f) ? Zv[at[j]] : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            if (!in[j]) continue;
             uint4 q = make_uint4(0u, 0u, 0u, 0u);
-            if (r > 0.f) {
-                const uint4 w = *p;
-                const uint32_t in[4] = {w.x, w.y, w.z, w.w};
+            if (r[j] > 0.f) {
+                const uint32_t src[4] = {w[j].x, w[j].y, w[j].z, w[j].w};
                 uint32_t out[4];
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
-                    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&in[h]);
-                    const float2 f = __bfloat1622float2(b);
-                    out[h] = pack_bf16x2(f.x * r, f.y * r);
+                    if (PREC == SB_PREC_BF16) {
+                        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&src[h]));
+                        out[h] = pack_bf16x2(f.x * r[j], f.y * r[j]);
+                    } else {
+                        out[h] = __float_as_uint(to_tf32(__uint_as_float(src[h]) * r[j]));
+                    }
                 }
                 q = make_uint4(out[0], out[1], out[2], out[3]);
             }
-            *p = q;
-        } else {
-            float4 *p = reinterpret_cast<float4 *>(reinterpret_cast<float *>(Z) + off);
-            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r > 0.f) {
-                const float4 w = *p;
-                q = make_float4(to_tf32(w.x * r), to_tf32(w.y * r), to_tf32(w.z * r), to_tf32(w.w * r));
-            }
-            *p = q;
+            Zv[at[j]] = q;
         }
     }
 }
@@ -823,9 +859,9 @@ __global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int K, i
             }
         }
     }
-    const uint32_t km = zmask ? block_kmask(zmask, n / BM, K) : 0xffffffffu;  // pairs the |z|^2 pass visits
+    const uint64_t km = zmask ? block_kmask(zmask, n / BM, K) : ~0ull;  // pairs the |z|^2 pass visits
     for (int k = 0; k < K; ++k) {
-        if (!((km >> k) & 1u)) continue;
+        if (!((km >> k) & 1ull)) continue;
         float v[VE];
 #pragma unroll
         for (int q = 0; q < VE; ++q) v[q] = 0.f;
