@@ -34,6 +34,7 @@
 #include <mutex>
 
 #include "sb_lbfgs.cuh"
+#include "sb_ptx.cuh"
 
 namespace sb {
 
@@ -44,12 +45,17 @@ struct Cfg {
     static constexpr int NW = CT / 32;            // warps per walker
     static constexpr int VPT = kMaxD / (4 * CT);  // float4 groups per thread
     static constexpr int MINB = 4;                // CTAs per SM
-    // ring of the stored pairs: DB groups of PGB pairs (one 8-column tensor-core
-    // tile of s, y vectors), one 16-byte chunk per stored vector and thread
+    // ring of the stored pairs: DB slots of PGB pairs (one 8-column tensor-core tile
+    // of s, y vectors), each stored row up to kMaxD bf16 coordinates plus 16 bytes:
+    // row r of a slot starts 16 r bytes further into the 128-byte bank window than
+    // row 0, so the same 16-byte chunk of the 8 rows falls in 8 different bank groups
     static constexpr int PGB = 4;
     static constexpr int DB = 3;
-    static constexpr int RING_F4 = DB * PGB * 2 * CT;
+    static constexpr int ROW_B = kMaxD * 2 + 16;
+    static constexpr int SLOT_B = 2 * PGB * ROW_B;
+    static constexpr int RING_B = DB * SLOT_B;
 };
+
 constexpr int kCT = 128;  // threads per walker used by the solver
 
 // Vector accesses need 16-byte aligned rows: d % 4 == 0 (rows start at multiples of d).
@@ -78,14 +84,8 @@ __device__ __forceinline__ float4 axpy4(float a, float4 x, float4 y) {
 }
 __device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
-// Per-thread asynchronous copies global -> shared (16 bytes, L2 only). A thread
-// only ever reads back the chunks it copied itself, so completing its own
-// groups (cp.async.wait_group) is all the synchronisation the ring needs.
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
-}
+// Per-thread asynchronous copies global -> shared of the m x m state (4 bytes each),
+// completed by the copying thread's own cp.async.wait_group before a CTA barrier.
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
@@ -275,6 +275,14 @@ __device__ __forceinline__ void block_sum_max(float (&v)[NV], float &mx, float *
     mx = m;
 }
 
+// The dynamic shared memory of the step kernel: the pair ring (Cfg RING_B bytes),
+// then R^-1 and Y^T Y (logical order, stride ld), pass 1's per-warp partial sums and
+// the m-vectors S^T g, Y^T g, the direction's coefficients a, w, D = diag(S^T Y) and
+// the new pair's column of R. Addresses are formed from the array and m (registers),
+// not kept in shared memory, so that no access waits on a pointer load.
+extern __shared__ __align__(16) float4 lb_dyn[];
+__device__ __forceinline__ unsigned char *ring_base() { return reinterpret_cast<unsigned char *>(lb_dyn); }
+
 // Odd row stride of the m x m matrices: their rows and their columns are both
 // free of shared-memory bank conflicts.
 __host__ __device__ __forceinline__ int mm_ld(int m) { return (m & 1) ? m + 2 : m + 1; }
@@ -290,20 +298,30 @@ template <int CT>
 __host__ __device__ __forceinline__ int mm_floats(int m) {
     return 2 * m * mm_ld(m) + p1_floats<CT>(m) + 6 * m;
 }
+template <int CT>
+struct Lay {
+    int m, ld;
+    __device__ __forceinline__ explicit Lay(int m_) : m(m_), ld(mm_ld(m_)) {}
+    __device__ __forceinline__ float *RI() const { return reinterpret_cast<float *>(ring_base() + Cfg<CT>::RING_B); }
+    __device__ __forceinline__ float *YY() const { return RI() + m * ld; }
+    __device__ __forceinline__ float *p1() const { return YY() + m * ld; }
+    __device__ __forceinline__ float *u1() const { return p1() + p1_floats<CT>(m); }
+    __device__ __forceinline__ float *u2() const { return u1() + m; }
+    __device__ __forceinline__ float *ca() const { return u2() + m; }
+    __device__ __forceinline__ float *cw() const { return ca() + m; }
+    __device__ __forceinline__ float *dg() const { return cw() + m; }
+    __device__ __forceinline__ float *nr() const { return dg() + m; }
+};
 
 template <int CT>
 struct Shared {
     float red2[2][Cfg<CT>::NW * 32];  // reduction scratch, used alternately (see block_sum)
-    // m-vectors (dynamic): S^T g, Y^T g; the direction's coefficients a, w;
-    // D = diag(S^T Y); the new pair's column of R
-    float *u1, *u2, *ca, *cw, *dg, *nr;
     float gamma;
-    // dynamic shared memory: the pair ring, R^-1 and Y^T Y (logical order,
-    // stride ld), then pass 1's per-warp partial sums
-    float4 *ring;
-    float *RI, *YY, *p1;
-    int ld;
     uint4 zero16;  // a zero row for the unused rows of the tensor-core operand
+    // per warp and ring slot: completion of the bulk copies of the warp's quarter of
+    // the slot's rows; set when a bounded wait gave up (every wait then gives up)
+    uint64_t full[Cfg<CT>::NW][Cfg<CT>::DB];
+    int abort;
 };
 
 // The m x m state of a walker, slot-indexed in HBM (logical pair i sits in slot
@@ -314,11 +332,12 @@ struct Shared {
 // trailing block of R^-1), so the direction needs matvecs, not substitutions.
 //
 // Copies the walker's R^-1, Y^T Y and D into shared memory in logical order as
-// 4-byte asynchronous copies that complete with the first ring group; the new
+// 4-byte asynchronous copies (one copy group, waited for before the solve); the new
 // pair's row and column (logical cn, or -1) are skipped: pass 1 supplies them.
 template <int CT>
-__device__ __forceinline__ void fetch_mm(Shared<CT> &sh, const float *mri, const float *myy, const float *dw,
+__device__ __forceinline__ void fetch_mm(const Lay<CT> &L, const float *mri, const float *myy, const float *dw,
                                          int count, int m, int head, int cn) {
+    float *RI = L.RI(), *YY = L.YY(), *dg = L.dg();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = wid; i < count; i += Cfg<CT>::NW) {
         if (i == cn) continue;
@@ -328,20 +347,21 @@ __device__ __forceinline__ void fetch_mm(Shared<CT> &sh, const float *mri, const
             if (j == cn) continue;
             int sj = head + j;
             if (sj >= m) sj -= m;
-            if (j >= i) cp_async4(sh.RI + i * sh.ld + j, mri + (size_t)si * m + sj);
-            cp_async4(sh.YY + i * sh.ld + j, myy + (size_t)si * m + sj);
+            if (j >= i) cp_async4(RI + i * L.ld + j, mri + (size_t)si * m + sj);
+            cp_async4(YY + i * L.ld + j, myy + (size_t)si * m + sj);
         }
-        if (lane == 0) cp_async4(sh.dg + i, dw + si);
+        if (lane == 0) cp_async4(dg + i, dw + si);
     }
 }
 // The new pair's part of the state from pass 1: Y^T Y's row and column (y_i .
 // y_new) into shared memory and HBM, R's new column (s_i . y_new, the last entry
-// being D_new) into sh.nr and D_new into sh.dg and HBM. R^-1's new column is
+// being D_new) into nr and D_new into dg and HBM. R^-1's new column is
 // formed by the solver. Returns the bytes of m x m state moved this visit.
 template <int CT, typename P1>
-__device__ __forceinline__ uint64_t new_mm(Shared<CT> &sh, float *myy, float *dw, int count, int m, int head, int cn,
+__device__ __forceinline__ uint64_t new_mm(const Lay<CT> &L, float *myy, float *dw, int count, int m, int head, int cn,
                                            P1 p1sum) {
     if (cn >= 0) {
+        float *YY = L.YY(), *nr = L.nr(), *dg = L.dg();
         for (int e = threadIdx.x; e < 2 * count - 1; e += CT) {
             // e < count: column cn, row e; else row cn, column e - count
             const int i = e < count ? e : cn, j = e < count ? cn : e - count;
@@ -350,12 +370,12 @@ __device__ __forceinline__ uint64_t new_mm(Shared<CT> &sh, float *myy, float *dw
             if (si >= m) si -= m;
             if (sj >= m) sj -= m;
             myy[(size_t)si * m + sj] = yy;
-            sh.YY[i * sh.ld + j] = yy;
+            YY[i * L.ld + j] = yy;
             if (e < count) {
                 const float r = p1sum(2, i);
-                sh.nr[i] = r;
+                nr[i] = r;
                 if (i == cn) {
-                    sh.dg[cn] = r;
+                    dg[cn] = r;
                     dw[si] = r;
                 }
             }
@@ -371,25 +391,27 @@ __device__ __forceinline__ uint64_t new_mm(Shared<CT> &sh, float *myy, float *dw
 // gamma = D_c-1 / (y^T y)_c-1, tv = D w + gamma Y^T Y w - gamma u2 and
 // a = R^-T tv. Each entry is a dot product over G threads (strided terms, then a
 // fixed-order shuffle sum), one barrier between the stages. Every thread calls
-// it. Results in sh.cw, sh.ca, sh.gamma.
+// it. Results in cw, ca and sh.gamma.
 template <int CT>
-__device__ __forceinline__ void solve_mm(Shared<CT> &sh, int c, int cn, float *mri, int m, int head) {
+__device__ __forceinline__ void solve_mm(Shared<CT> &sh, const Lay<CT> &L, int c, int cn, float *mri, int m, int head) {
     const int G = c <= CT / 4 ? 4 : (c <= CT / 2 ? 2 : 1);  // threads per entry
     const int i = (int)threadIdx.x / G, p = (int)threadIdx.x % G;
-    const int LD = sh.ld;
-    float *RI = sh.RI;
-    const float *YY = sh.YY;
-    float *tv = sh.p1;  // pass 1's partial sums are consumed before the solve
+    const int LD = L.ld;
+    float *RI = L.RI();
+    const float *YY = L.YY();
+    float *tv = L.p1();  // pass 1's partial sums are consumed before the solve
+    const float *nr = L.nr(), *u1 = L.u1(), *u2 = L.u2(), *dg = L.dg();
+    float *cw = L.cw(), *ca = L.ca();
     auto gsum = [&](float v) {  // every lane calls it: full-warp shuffles
         if (G >= 2) v += __shfl_xor_sync(0xffffffffu, v, 1);
         if (G >= 4) v += __shfl_xor_sync(0xffffffffu, v, 2);
         return v;
     };
     if (cn >= 0) {
-        const float dn = sh.nr[cn];
+        const float dn = nr[cn];
         float t = 0.f;
         if (i < cn)
-            for (int k = i + p; k < cn; k += G) t += RI[i * LD + k] * sh.nr[k];
+            for (int k = i + p; k < cn; k += G) t += RI[i * LD + k] * nr[k];
         t = gsum(t);
         if (p == 0 && i <= cn) {
             const float v = i == cn ? 1.f / dn : -t / dn;
@@ -404,19 +426,19 @@ __device__ __forceinline__ void solve_mm(Shared<CT> &sh, int c, int cn, float *m
     {
         float t = 0.f;
         if (i < c)
-            for (int k = i + p; k < c; k += G) t += RI[i * LD + k] * sh.u1[k];
+            for (int k = i + p; k < c; k += G) t += RI[i * LD + k] * u1[k];
         t = gsum(t);
-        if (p == 0 && i < c) sh.cw[i] = t;
+        if (p == 0 && i < c) cw[i] = t;
     }
     __syncthreads();
-    const float gam = sh.dg[c - 1] / YY[(c - 1) * LD + (c - 1)];
+    const float gam = dg[c - 1] / YY[(c - 1) * LD + (c - 1)];
     if (threadIdx.x == 0) sh.gamma = gam;
     {
         float t = 0.f;
         if (i < c)
-            for (int j = p; j < c; j += G) t += YY[i * LD + j] * sh.cw[j];
+            for (int j = p; j < c; j += G) t += YY[i * LD + j] * cw[j];
         t = gsum(t);
-        if (p == 0 && i < c) tv[i] = sh.dg[i] * sh.cw[i] + gam * t - gam * sh.u2[i];
+        if (p == 0 && i < c) tv[i] = dg[i] * cw[i] + gam * t - gam * u2[i];
     }
     __syncthreads();
     {
@@ -424,115 +446,141 @@ __device__ __forceinline__ void solve_mm(Shared<CT> &sh, int c, int cn, float *m
         if (i < c)
             for (int k = p; k <= i; k += G) t += RI[k * LD + i] * tv[k];
         t = gsum(t);
-        if (p == 0 && i < c) sh.ca[i] = t;
+        if (p == 0 && i < c) ca[i] = t;
     }
 }
 
 using bf16 = __nv_bfloat16;
 
-// Stores this thread's coordinates of a history vector (values already bf16):
-// 8 consecutive coordinates, one 16-byte chunk.
-template <int CT, bool EVEN>
-__device__ __forceinline__ void store_hist(const Vec<CT> &v, bf16 *row, int d) {
+// Stores this thread's chunk of a history row (values already bf16; coordinates past
+// d are zero in the vector): 8 consecutive coordinates, one 16-byte store, for every
+// chunk inside the row pitch.
+template <int CT>
+__device__ __forceinline__ void store_hist(const Vec<CT> &v, bf16 *row, int ldh) {
     const int e0 = Vec<CT>::i0(0);
-    if (EVEN && e0 >= d) return;
-    if (EVEN || ((d & 7) == 0 && e0 + 7 < d)) {
-        *reinterpret_cast<uint4 *>(row + e0) = make_uint4(pack2(v.v[0].x, v.v[0].y), pack2(v.v[0].z, v.v[0].w),
-                                                          pack2(v.v[1].x, v.v[1].y), pack2(v.v[1].z, v.v[1].w));
-    } else {
-        const float f[8] = {v.v[0].x, v.v[0].y, v.v[0].z, v.v[0].w, v.v[1].x, v.v[1].y, v.v[1].z, v.v[1].w};
-        for (int e = 0; e < 8 && e0 + e < d; ++e) row[e0 + e] = __float2bfloat16_rn(f[e]);
-    }
+    if (e0 >= ldh) return;
+    *reinterpret_cast<uint4 *>(row + e0) = make_uint4(pack2(v.v[0].x, v.v[0].y), pack2(v.v[0].z, v.v[0].w),
+                                                      pack2(v.v[1].x, v.v[1].y), pack2(v.v[1].z, v.v[1].w));
 }
 
-// The shared-memory ring the stored pairs stream through: D slots of PG pairs,
-// blocks of CT 16-byte chunks (the chunk of vector v of pair q of slot sl).
-// Within a block the chunk of thread t sits at t ^ (block % 8), so the same
-// chunk of 8 consecutive blocks (the rows of one ldmatrix) falls in 8 different
-// bank groups.
-template <int CT, bool EVEN>
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// The ring the stored pairs stream through (Cfg: DB slots of PGB pairs; row 2 q + v of
+// a slot is vector v (0: s, 1: y) of its pair q). Warp w owns coordinates
+// 256 w .. 256 w + 255 of every row (its threads' chunks) and moves them itself:
+// one bulk copy per stored row, completing on the warp's barrier of the slot, so the
+// warps stream independently and a slot is refilled once its own warp has read it.
+template <int CT>
 struct Ring {
-    static constexpr int PG = Cfg<CT>::PGB;
-    static constexpr int D = Cfg<CT>::DB;
+    static constexpr int PG = Cfg<CT>::PGB, D = Cfg<CT>::DB;
     static_assert(Cfg<CT>::VPT == 2, "one 16-byte bf16 chunk (8 coordinates) per stored vector and thread");
-    uint4 *base;
-    int d;
-    __device__ __forceinline__ uint4 *at(int sl, int q, int v, int t) const {
-        const int b = (sl * PG + q) * 2 + v;
-        return base + (size_t)b * CT + (t ^ (b & 7));
+    static_assert(2 * PG <= 32, "one copying lane per row of a slot");
+    Shared<CT> &sh;
+    int ldh, m, head, J, cn;  // row pitch, history size, first slot, pairs in the ring, new pair (or -1)
+    const bf16 *S, *Y;
+    uint32_t &ph;   // barrier parity per slot (this warp)
+    uint32_t pend;  // slots with copies issued and not yet waited for
+
+    __device__ __forceinline__ unsigned char *row(int sl, int r) const {
+        return ring_base() + sl * Cfg<CT>::SLOT_B + r * Cfg<CT>::ROW_B;
     }
-    // this thread's chunk of a stored row (cp.async, or a plain copy zero-padded
-    // past d for a ragged end of the row)
-    __device__ __forceinline__ void copy_in(int sl, int q, int v, const bf16 *row) const {
-        uint4 *dst = at(sl, q, v, threadIdx.x);
-        const int e0 = Vec<CT>::i0(0);  // 8 consecutive elements
-        if (EVEN) {
-            if (e0 < d)
-                cp_async16(dst, row + e0);
-            else
-                *dst = make_uint4(0u, 0u, 0u, 0u);
-        } else if ((d & 7) == 0 && e0 + 7 < d) {
-            cp_async16(dst, row + e0);
-        } else {
-            uint16_t h[8];
-            const uint16_t *src = reinterpret_cast<const uint16_t *>(row);
+    // this thread's chunk of row r of slot sl
+    __device__ __forceinline__ uint4 *chunk(int sl, int r) const {
+        return reinterpret_cast<uint4 *>(row(sl, r)) + threadIdx.x;
+    }
+    // Group k (logical pairs k PG .. k PG + PG - 1 below J) into slot sl. The visit's
+    // new pair comes from registers (s_new, y_new: this thread's chunk), not HBM.
+    // whether some warp gave up a wait (the same answer in every lane of the warp)
+    __device__ __forceinline__ bool aborted() const {
+        return __any_sync(0xffffffffu, *reinterpret_cast<volatile int *>(&sh.abort) != 0);
+    }
+    __device__ __forceinline__ void issue(int k, int sl, const Vec<CT> &s_new, const Vec<CT> &y_new) {
+        if (aborted()) return;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const int c0 = 8 * 32 * wid;  // this warp's first coordinate
+        const int qn = ldh - c0 < 0 ? 0 : (ldh - c0 > 256 ? 256 : ldh - c0);
+        const uint32_t qb = 2u * (uint32_t)qn;
+        int nrows = 0;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) h[e] = e0 + e < d ? src[e0 + e] : (uint16_t)0;
-            *dst = make_uint4(h[0] | (uint32_t)h[1] << 16, h[2] | (uint32_t)h[3] << 16, h[4] | (uint32_t)h[5] << 16,
-                              h[6] | (uint32_t)h[7] << 16);
+        for (int q = 0; q < PG; ++q) {
+            const int j = k * PG + q;
+            if (j < J && j != cn) nrows += 2;
         }
+        // the warp has read the slot; generic writes into it (the staged operand, the
+        // register rows) were ordered before the async proxy by the caller's fence
+        __syncwarp();
+        if (lane == 0) mbar_arrive_tx(&sh.full[wid][sl], (uint32_t)nrows * qb);
+        __syncwarp();
+        if (lane < 2 * PG && qb) {
+            const int q = lane >> 1, v = lane & 1, j = k * PG + q;
+            if (j < J && j != cn) {
+                int slot = head + j;
+                if (slot >= m) slot -= m;
+                bulk_g2s(row(sl, 2 * q + v) + 2 * c0, (v ? Y : S) + (size_t)slot * ldh + c0, qb, &sh.full[wid][sl]);
+            }
+        }
+        if (cn >= k * PG && cn < k * PG + PG && Vec<CT>::i0(0) < ldh) {
+            const int q = cn - k * PG;
+            *chunk(sl, 2 * q) = make_uint4(pack2(s_new.v[0].x, s_new.v[0].y), pack2(s_new.v[0].z, s_new.v[0].w),
+                                           pack2(s_new.v[1].x, s_new.v[1].y), pack2(s_new.v[1].z, s_new.v[1].w));
+            *chunk(sl, 2 * q + 1) = make_uint4(pack2(y_new.v[0].x, y_new.v[0].y), pack2(y_new.v[0].z, y_new.v[0].w),
+                                               pack2(y_new.v[1].x, y_new.v[1].y), pack2(y_new.v[1].z, y_new.v[1].w));
+        }
+        pend |= 1u << sl;
+    }
+    // Bounded wait for slot sl (every lane of the warp, the outcome made uniform);
+    // false once any warp of the CTA gave up.
+    __device__ __forceinline__ bool wait(int sl) {
+        const int wid = threadIdx.x >> 5;
+        const bool ok = __all_sync(0xffffffffu, bwait(&sh.full[wid][sl], (ph >> sl) & 1u, &sh.abort));
+        if (ok) {
+            ph ^= 1u << sl;
+            pend &= ~(1u << sl);
+        }
+        __syncwarp();  // the copies and the warp's register rows are visible to the warp
+        return ok;
+    }
+    // After a wait gave up: bounded waits for the copies still in flight into this
+    // warp's slots, so that none lands after the CTA has moved on.
+    __device__ __forceinline__ void drain() {
+        const int wid = threadIdx.x >> 5;
+        for (int sl = 0; sl < D; ++sl) {
+            if (!((pend >> sl) & 1u)) continue;
+            for (long long it = 0; it < kSpinLimit; ++it)
+                if (mbar_try_wait(&sh.full[wid][sl], (ph >> sl) & 1u)) break;
+        }
+        pend = 0;
     }
     // this thread's coordinates of pair q of slot sl
     __device__ __forceinline__ void fetch(int sl, int q, Vec<CT> &sv, Vec<CT> &yv) const {
-        const uint4 a4 = *at(sl, q, 0, threadIdx.x), b4 = *at(sl, q, 1, threadIdx.x);
+        const uint4 a4 = *chunk(sl, 2 * q), b4 = *chunk(sl, 2 * q + 1);
         sv.v[0] = unpack4(a4.x, a4.y);
         sv.v[1] = unpack4(a4.z, a4.w);
         yv.v[0] = unpack4(b4.x, b4.y);
         yv.v[1] = unpack4(b4.z, b4.w);
-        if (EVEN) return;  // chunks past d are copied in as zeros
-#pragma unroll
-        for (int j = 0; j < Cfg<CT>::VPT; ++j) {
-            const int i0 = Vec<CT>::i0(j);
-            if (!(i0 + 3 < d)) {  // ragged tail: lanes past d hold stale data
-                if (i0 + 0 >= d) sv.v[j].x = yv.v[j].x = 0.f;
-                if (i0 + 1 >= d) sv.v[j].y = yv.v[j].y = 0.f;
-                if (i0 + 2 >= d) sv.v[j].z = yv.v[j].z = 0.f;
-                if (i0 + 3 >= d) sv.v[j].w = yv.v[j].w = 0.f;
-            }
-        }
-    }
-    // Issues group k (logical pairs k PG .. k PG + PG - 1 of the J stored from
-    // slot head) into slot k % D. Always commits.
-    __device__ __forceinline__ void issue(int k, int J, int head, int m, const bf16 *S, const bf16 *Y) const {
-        const int sl = k % D;
-#pragma unroll
-        for (int q = 0; q < PG; ++q) {
-            const int j = k * PG + q;
-            if (j >= J) break;
-            int slot = head + j;
-            if (slot >= m) slot -= m;
-            copy_in(sl, q, 0, S + (size_t)slot * d);
-            copy_in(sl, q, 1, Y + (size_t)slot * d);
-        }
-        cp_async_commit();
     }
 };
 
 // Direction for walker state st (count pairs from ring slot head). When
 // new_slot >= 0 the pair in that slot was stored this visit (the newest, logical
 // index count - 1; s_new, y_new) and its column of R, row and column of Y^T Y
-// come from the same pass. Writes P and
-// the unit trial X + P; updates st.dphi / alpha / bt and possibly resets the
-// history (steepest descent when p is not a descent direction). Returns the
-// algorithmic bytes moved.
+// come from the same pass. Writes P and the unit trial X + P; updates st.dphi /
+// alpha / bt and possibly resets the history (steepest descent when p is not a
+// descent direction). Returns the algorithmic bytes moved.
+//
+// Pass 1 streams the pairs oldest first; at its end the ring holds the newest
+// min(groups, DB) groups, so pass 2 walks the groups newest first: those are read
+// where they are, and each slot it frees is refilled with the group DB older (the
+// same slot, g mod DB), the only ones read from HBM (L2) again.
 template <int CT, bool EVEN>
 __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<float> &st, int new_slot,
-                              const Vec<CT> &g_in, const Vec<CT> &x_in,
-                              const Vec<CT> &s_new, const Vec<CT> &y_new, float *MRI, float *MYY,
-                              Shared<CT> &sh, int &par) {
-    using RG = Ring<CT, EVEN>;
+                              const Vec<CT> &g_in, const Vec<CT> &x_in, const Vec<CT> &s_new, const Vec<CT> &y_new,
+                              float *MRI, float *MYY, Shared<CT> &sh, const Lay<CT> &L, int &par, uint32_t &ph) {
+    using RG = Ring<CT>;
     constexpr int PG = RG::PG, D = RG::D, NW = Cfg<CT>::NW;
-    const int d = a.d, m = a.m;
+    const int d = a.d, m = a.m, ldh = hist_ld(d);
     const int count = st.count;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t bytes = 0;
@@ -542,44 +590,45 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
     // instead of being held through it
     Vec<CT> g = g_in, x = x_in;
     if (count > 0) {
-        const bf16 *S = reinterpret_cast<const bf16 *>(a.S) + (size_t)w * m * d;
-        const bf16 *Y = reinterpret_cast<const bf16 *>(a.Y) + (size_t)w * m * d;
-        const RG ring{reinterpret_cast<uint4 *>(sh.ring), d};
-        // pass 1 streams the logical pairs (the new one included: it is stored)
         const bool added = new_slot >= 0;
-        const int J = count, head = st.head;
-        const int ng1 = (J + PG - 1) / PG;
-        const int K1 = ng1;
         const int cn = added ? count - 1 : -1;
+        RG ring{sh,
+                ldh,
+                m,
+                st.head,
+                count,
+                cn,
+                reinterpret_cast<const bf16 *>(a.S) + (size_t)w * m * ldh,
+                reinterpret_cast<const bf16 *>(a.Y) + (size_t)w * m * ldh,
+                ph,
+                0u};
+        const int ng = (count + PG - 1) / PG;
         float *mri_w = MRI + (size_t)w * m * m, *myy_w = MYY + (size_t)w * m * m, *dw = a.rho + (size_t)w * m;
-        fetch_mm<CT>(sh, mri_w, myy_w, dw, count, m, st.head, cn);  // committed with ring group 0
 #pragma unroll 1
-        for (int k = 0; k < D - 1; ++k) ring.issue(k, J, head, m, S, Y);
-        float *p1 = sh.p1;
+        for (int k = 0; k < D - 1 && k < ng; ++k) ring.issue(k, k, s_new, y_new);
+        float *p1 = L.p1();
         {
             // Pass 1 on the tensor cores: per warp (its 256 coordinates, 16 k-steps of
-            // 16) and ring group (8 stored vectors s_0 y_0 .. s_3 y_3 as the columns of
-            // B), D = A B with the rows of A = (g_hi, g_mid, g_lo, y_new, s_new, 0 ..)
-            // at the same coordinates. The A fragments are staged once through this
-            // warp's own chunks of ring slot D - 1 (free until group D - 1 is issued into it).
-            uint4 *ring4 = reinterpret_cast<uint4 *>(sh.ring);
-            constexpr int SB = (D - 1) * PG * 2;  // first block of slot D - 1
-            static_assert(2 * PG >= 5, "slot D - 1 holds the five staged rows");
-            auto stage = [&](int r, int u) { return ring4 + (SB + r) * CT + (u ^ ((SB + r) & 7)); };
+            // 16) and group (8 stored vectors s_0 y_0 .. s_3 y_3 as the columns of B),
+            // D = A B with the rows of A = (g_hi, g_mid, g_lo, y_new, s_new, 0 ..) at the
+            // same coordinates. The A fragments are staged once through this warp's
+            // own chunks of ring slot D - 1 (free until group D - 1 is issued into it).
             {
                 float hi[8], mi[8], lo[8];
                 const float gv[8] = {g.v[0].x, g.v[0].y, g.v[0].z, g.v[0].w, g.v[1].x, g.v[1].y, g.v[1].z, g.v[1].w};
 #pragma unroll
                 for (int e = 0; e < 8; ++e) split3_bf16(gv[e], hi[e], mi[e], lo[e]);
-                const int t = threadIdx.x;  // row r in block SB + r, this thread's chunk
-                *stage(0, t) = make_uint4(pack2(hi[0], hi[1]), pack2(hi[2], hi[3]), pack2(hi[4], hi[5]), pack2(hi[6], hi[7]));
-                *stage(1, t) = make_uint4(pack2(mi[0], mi[1]), pack2(mi[2], mi[3]), pack2(mi[4], mi[5]), pack2(mi[6], mi[7]));
-                *stage(2, t) = make_uint4(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]), pack2(lo[4], lo[5]), pack2(lo[6], lo[7]));
+                *ring.chunk(D - 1, 0) =
+                    make_uint4(pack2(hi[0], hi[1]), pack2(hi[2], hi[3]), pack2(hi[4], hi[5]), pack2(hi[6], hi[7]));
+                *ring.chunk(D - 1, 1) =
+                    make_uint4(pack2(mi[0], mi[1]), pack2(mi[2], mi[3]), pack2(mi[4], mi[5]), pack2(mi[6], mi[7]));
+                *ring.chunk(D - 1, 2) =
+                    make_uint4(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]), pack2(lo[4], lo[5]), pack2(lo[6], lo[7]));
                 // s_new, y_new are bf16 values already (the pair as stored): exact
-                *stage(3, t) = make_uint4(pack2(y_new.v[0].x, y_new.v[0].y), pack2(y_new.v[0].z, y_new.v[0].w),
-                                          pack2(y_new.v[1].x, y_new.v[1].y), pack2(y_new.v[1].z, y_new.v[1].w));
-                *stage(4, t) = make_uint4(pack2(s_new.v[0].x, s_new.v[0].y), pack2(s_new.v[0].z, s_new.v[0].w),
-                                          pack2(s_new.v[1].x, s_new.v[1].y), pack2(s_new.v[1].z, s_new.v[1].w));
+                *ring.chunk(D - 1, 3) = make_uint4(pack2(y_new.v[0].x, y_new.v[0].y), pack2(y_new.v[0].z, y_new.v[0].w),
+                                                   pack2(y_new.v[1].x, y_new.v[1].y), pack2(y_new.v[1].z, y_new.v[1].w));
+                *ring.chunk(D - 1, 4) = make_uint4(pack2(s_new.v[0].x, s_new.v[0].y), pack2(s_new.v[0].z, s_new.v[0].w),
+                                                   pack2(s_new.v[1].x, s_new.v[1].y), pack2(s_new.v[1].z, s_new.v[1].w));
             }
             __syncwarp();
             const int mi8 = lane >> 3, ri8 = lane & 7;  // ldmatrix: matrix and row this lane addresses
@@ -587,53 +636,54 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
 #pragma unroll
             for (int c = 0; c < 16; c += 2) {
                 const int u = 32 * wid + 2 * (c + (mi8 >> 1)) + (mi8 & 1);  // chunk (thread) index
-                const void *row = ri8 < 5 ? (const void *)stage(ri8, u) : (const void *)&sh.zero16;
+                const void *src = ri8 < 5 ? (const void *)(ring.row(D - 1, ri8) + 16 * u) : (const void *)&sh.zero16;
                 uint32_t r[4];
-                ldsm_x4(r, row);
+                ldsm_x4(r, src);
                 af[c][0] = r[0];
                 af[c][1] = r[1];
                 af[c + 1][0] = r[2];
                 af[c + 1][1] = r[3];
             }
-            __syncwarp();  // the staging chunks are read before slot D - 1 is refilled
             int nk = (d - 256 * wid + 15) / 16;  // k-steps of this warp inside d (warp-uniform)
             nk = nk < 0 ? 0 : (nk > 16 ? 16 : nk);
             const int gid = lane >> 2, tig = lane & 3;
-            ring.issue(D - 1, J, head, m, S, Y);  // its slot held the staged operand
-            for (int k = 0; k < K1; ++k) {
-                cp_async_wait<D - 1>();
-                __syncwarp();  // every lane's copies of the group are visible to the warp
-                const int gi = k, sl = k % D;
-                if (gi < ng1) {
-                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-                    // B rows: vector n = ri8 mod 2 PG of the group (pair n / 2, s or y); with
-                    // 2 PG < 8 the remaining columns repeat it and are not read back
-                    const int n = ri8 % (2 * PG);
+            // the staged operand is written (generic proxy) before the copies into its slot
+            fence_proxy_async_smem();
+            if (D - 1 < ng) ring.issue(D - 1, D - 1, s_new, y_new);
+            // the m x m state, needed after pass 1 (issued after the fence, which then
+            // has no copies of this thread to wait for)
+            fetch_mm<CT>(L, mri_w, myy_w, dw, count, m, st.head, cn);
+            cp_async_commit();
+            for (int k = 0; k < ng; ++k) {
+                const int sl = k % D;
+                if (!ring.wait(sl)) break;
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                // B rows: the group's 8 stored vectors (pair n / 2, s or y)
 #pragma unroll
-                    for (int c = 0; c < 16; c += 2) {
-                        if (c < nk) {
-                            uint32_t b[4];
-                            ldsm_x4(b, ring.at(sl, n >> 1, n & 1, 32 * wid + 2 * (c + (mi8 >> 1)) + (mi8 & 1)));
-                            mma_rows8(acc, af[c][0], af[c][1], b[0], b[1]);
-                            if (c + 1 < nk) mma_rows8(acc, af[c + 1][0], af[c + 1][1], b[2], b[3]);
-                        }
-                    }
-                    // g . v = (g_hi + g_mid) . v + g_lo . v from rows 0, 1, 2
-                    const float h0 = __shfl_down_sync(0xffffffffu, acc[0], 4);
-                    const float l0 = __shfl_down_sync(0xffffffffu, acc[0], 8);
-                    const float h1 = __shfl_down_sync(0xffffffffu, acc[1], 4);
-                    const float l1 = __shfl_down_sync(0xffffffffu, acc[1], 8);
-                    const int r = gid == 0 ? 0 : gid == 3 ? 1 : gid == 4 ? 2 : -1;
-                    if (r >= 0 && tig < PG) {
-                        const float2 o = gid == 0 ? make_float2((acc[0] + h0) + l0, (acc[1] + h1) + l1)
-                                                  : make_float2(acc[0], acc[1]);
-                        *reinterpret_cast<float2 *>(p1 + ((gi * NW + wid) * 3 + r) * (2 * PG) + 2 * tig) = o;
+                for (int c = 0; c < 16; c += 2) {
+                    if (c < nk) {
+                        uint32_t b[4];
+                        ldsm_x4(b, ring.row(sl, ri8) + 16 * (32 * wid + 2 * (c + (mi8 >> 1)) + (mi8 & 1)));
+                        mma_rows8(acc, af[c][0], af[c][1], b[0], b[1]);
+                        if (c + 1 < nk) mma_rows8(acc, af[c + 1][0], af[c + 1][1], b[2], b[3]);
                     }
                 }
+                // g . v = (g_hi + g_mid) . v + g_lo . v from rows 0, 1, 2
+                const float h0 = __shfl_down_sync(0xffffffffu, acc[0], 4);
+                const float l0 = __shfl_down_sync(0xffffffffu, acc[0], 8);
+                const float h1 = __shfl_down_sync(0xffffffffu, acc[1], 4);
+                const float l1 = __shfl_down_sync(0xffffffffu, acc[1], 8);
+                const int r = gid == 0 ? 0 : gid == 3 ? 1 : gid == 4 ? 2 : -1;
+                if (r >= 0 && tig < PG) {
+                    const float2 o = gid == 0 ? make_float2((acc[0] + h0) + l0, (acc[1] + h1) + l1)
+                                              : make_float2(acc[0], acc[1]);
+                    *reinterpret_cast<float2 *>(p1 + ((k * NW + wid) * 3 + r) * (2 * PG) + 2 * tig) = o;
+                }
                 __syncwarp();  // the warp has read the group before its slot is refilled
-                ring.issue(k + D, J, head, m, S, Y);
+                if (k + D < ng) ring.issue(k + D, sl, s_new, y_new);
             }
         }
+        cp_async_wait<0>();  // the m x m state
         __syncthreads();
         // product k of logical pair i (k: 0 s.g, 1 y.g, 2 s.y_new, 3 s_new.y, 4 y.y_new):
         // the warps' totals summed in warp order
@@ -646,40 +696,45 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
             for (int q = 0; q < NW; ++q) t += src[q * 3 * 2 * PG];
             return t;
         };
-        for (int e = threadIdx.x; e < 2 * count; e += CT) {
-            if (e < count)
-                sh.u1[e] = p1sum(0, e);
-            else
-                sh.u2[e - count] = p1sum(1, e - count);
+        {
+            float *u1 = L.u1(), *u2 = L.u2();
+            for (int e = threadIdx.x; e < 2 * count; e += CT) {
+                if (e < count)
+                    u1[e] = p1sum(0, e);
+                else
+                    u2[e - count] = p1sum(1, e - count);
+            }
         }
-        bytes += new_mm<CT>(sh, myy_w, dw, count, m, st.head, cn, p1sum);
-        const int ng2 = (count + PG - 1) / PG;
-#pragma unroll 1
-        for (int k = 0; k < D; ++k) ring.issue(k, count, st.head, m, S, Y);  // pass 2's first groups
+        bytes += new_mm<CT>(L, myy_w, dw, count, m, st.head, cn, p1sum);
         g.template load<EVEN>(a.G + (size_t)w * d, d);
         x.template load<EVEN>(a.X + (size_t)w * d, d);
         __syncthreads();
-        solve_mm<CT>(sh, count, cn, mri_w, m, st.head);
+        solve_mm<CT>(sh, L, count, cn, mri_w, m, st.head);
         __syncthreads();
-        // pass 2: p = -gamma g - S a + gamma Y w
+        // pass 2: p = -gamma g - S a + gamma Y w, the groups newest first
         const float gam = sh.gamma;
         p.zero();
         axpyv(-gam, g, p);
-        for (int k = 0; k < ng2; ++k) {
-            cp_async_wait<D - 1>();
+        const int r0 = ng > D ? ng - D : 0;  // groups below r0 are no longer in the ring
+        const float *ca = L.ca(), *cw = L.cw();
+        // the new pair's register rows (generic proxy) before the refills of their slot
+        fence_proxy_async_smem();
+        for (int k = ng - 1; k >= 0; --k) {
+            const int sl = k % D;
+            if (k < r0 && !ring.wait(sl)) break;
 #pragma unroll
             for (int q = 0; q < PG; ++q) {
                 const int i = k * PG + q;
                 if (i < count) {
                     Vec<CT> s4, y4;
-                    ring.fetch(k % D, q, s4, y4);
-                    axpyv(-sh.ca[i], s4, p);
-                    axpyv(gam * sh.cw[i], y4, p);
+                    ring.fetch(sl, q, s4, y4);
+                    axpyv(-ca[i], s4, p);
+                    axpyv(gam * cw[i], y4, p);
                 }
             }
-            ring.issue(k + D, count, st.head, m, S, Y);  // this thread's own chunks, just read
+            if (k - D >= 0) ring.issue(k - D, sl, s_new, y_new);  // after this warp read the slot
         }
-        cp_async_wait<0>();  // (only empty groups remain) the ring is free for the next walker
+        if (ring.pend) ring.drain();  // only after a wait gave up
         // the two-loop recursion's history traffic: each pair read in both passes
         bytes += (uint64_t)4 * count * d * sizeof(bf16);
     }
@@ -718,24 +773,22 @@ template <int CT, bool EVEN>
 __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float> a, float *MRI, float *MYY,
                                                                 int count_bytes) {
     __shared__ Shared<CT> sh;
-    extern __shared__ __align__(16) float4 dyn[];  // [RING_F4] ring, then R, YY [m][ld]
-    const int d = a.d, m = a.m;
+    const int d = a.d, m = a.m, ldh = hist_ld(d);
+    const Lay<CT> L(m);
+    // the ring starts zeroed: chunks past the row pitch are never copied into and must
+    // read as zeros where a k-step of pass 1 straddles the end of the coordinates
+    for (int e = threadIdx.x; e < Cfg<CT>::RING_B / 16; e += CT) lb_dyn[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (threadIdx.x == 0) {
-        sh.ring = dyn;
-        sh.ld = mm_ld(m);
-        sh.RI = reinterpret_cast<float *>(dyn + Cfg<CT>::RING_F4);
-        sh.YY = sh.RI + (size_t)m * sh.ld;
-        sh.p1 = sh.YY + (size_t)m * sh.ld;
-        sh.u1 = sh.p1 + p1_floats<CT>(m);
-        sh.u2 = sh.u1 + m;
-        sh.ca = sh.u2 + m;
-        sh.cw = sh.ca + m;
-        sh.dg = sh.cw + m;
-        sh.nr = sh.dg + m;
+        sh.abort = 0;
+        for (int q = 0; q < Cfg<CT>::NW; ++q)
+            for (int sl = 0; sl < Cfg<CT>::DB; ++sl) mbar_init(&sh.full[q][sl], 1);
+        mbar_fence_init();
         sh.zero16 = make_uint4(0u, 0u, 0u, 0u);
     }
+    fence_proxy_async_smem();  // the zeroing before any copy into the ring
     __syncthreads();
     const int n_act = *a.n_act;
+    uint32_t ph = 0;  // barrier parity of this warp's ring slots
     int par = 0;  // alternation of the reduction scratch (identical in every thread)
     uint64_t bytes = 0;
     // the next visit's walker id is loaded one visit ahead, so a visit's first
@@ -795,8 +848,8 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                     slot = st.head;
                     st.head = (st.head + 1) % m;
                 }
-                store_hist<CT, EVEN>(s4, reinterpret_cast<bf16 *>(a.S) + ((size_t)w * m + slot) * d, d);
-                store_hist<CT, EVEN>(y4, reinterpret_cast<bf16 *>(a.Y) + ((size_t)w * m + slot) * d, d);
+                store_hist<CT>(s4, reinterpret_cast<bf16 *>(a.S) + ((size_t)w * m + slot) * ldh, ldh);
+                store_hist<CT>(y4, reinterpret_cast<bf16 *>(a.Y) + ((size_t)w * m + slot) * ldh, ldh);
                 bytes += (uint64_t)2 * d * sizeof(bf16);
                 new_slot = slot;
                 s_new = s4;
@@ -824,7 +877,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                 st.count = 0;
                 st.head = 0;
                 st.attempt = 1;
-                bytes += direction<CT, EVEN>(a, w, st, -1, g, x, s_new, y_new, MRI, MYY, sh, par);
+                bytes += direction<CT, EVEN>(a, w, st, -1, g, x, s_new, y_new, MRI, MYY, sh, L, par, ph);
                 dnext = st.pn + alpha0 * pn0;  // from the old trial back to x, then out
             } else {
                 st.status = SB_WALKER_STALLED;
@@ -839,7 +892,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                 st.status = SB_WALKER_MAXITER;
             } else {
                 st.attempt = 0;
-                bytes += direction<CT, EVEN>(a, w, st, new_slot, g, x, s_new, y_new, MRI, MYY, sh, par);
+                bytes += direction<CT, EVEN>(a, w, st, new_slot, g, x, s_new, y_new, MRI, MYY, sh, L, par, ph);
                 dnext = st.pn;  // x is this visit's trial
             }
         }
@@ -847,11 +900,13 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
             a.st[w] = st;
             if (a.dist && dnext >= 0.f) a.dist[w] = dnext * 1.0001f;  // margin for the rounding of |p|
         }
-        // No barrier before the next walker: a thread's ring chunks are read by
-        // other lanes only in pass 1, which ends with a CTA barrier. The reduction
-        // scratch alternates, and every other shared array is rewritten only
-        // after the next walker's first reduction barrier.
+        // No barrier before the next walker: a warp's part of the ring is read and
+        // refilled by that warp alone. The reduction scratch alternates, and every
+        // other shared array is rewritten only after the next walker's first
+        // reduction barrier.
+        if (*reinterpret_cast<volatile int *>(&sh.abort)) break;  // set before a CTA barrier of this visit
     }
+    if (*reinterpret_cast<volatile int *>(&sh.abort) && threadIdx.x == 0 && a.err) atomicOr(a.err, SB_DEV_TIMEOUT);
     if (count_bytes && threadIdx.x == 0 && bytes) atomicAdd(&g_lbfgs_bytes, (unsigned long long)bytes);
 }
 
@@ -1009,10 +1064,10 @@ void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *
     const int count_bytes = prof_class_on(PROF_LBFGS_STEP) ? 1 : 0;
     int grid = num_sms * Cfg<kCT>::MINB;
     if (grid > n) grid = n > 0 ? n : 1;
-    const size_t dyn = (size_t)Cfg<kCT>::RING_F4 * sizeof(float4) + sizeof(float) * mm_floats<kCT>(a.m);
+    const size_t dyn = (size_t)Cfg<kCT>::RING_B + sizeof(float) * mm_floats<kCT>(a.m);
     static std::once_flag once;  // batched solves launch from several host threads
     std::call_once(once, [] {
-        const size_t most = (size_t)Cfg<kCT>::RING_F4 * sizeof(float4) + sizeof(float) * mm_floats<kCT>(kMaxM);
+        const size_t most = (size_t)Cfg<kCT>::RING_B + sizeof(float) * mm_floats<kCT>(kMaxM);
         cudaFuncSetAttribute(k_lbfgs_cta<kCT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
         cudaFuncSetAttribute(k_lbfgs_cta<kCT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     });

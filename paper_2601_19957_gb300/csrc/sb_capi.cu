@@ -218,8 +218,11 @@ void carve_refine(Carver &cv, RefineWs<T> &r, int n, int d, int K, int m, bool f
     a.XT = cv.take<T>((size_t)n * d);
     a.GT = cv.take<T>((size_t)n * d);
     a.FT = cv.take<T>((size_t)n);
-    a.S = cv.take<T>((size_t)n * m * d);
-    a.Y = cv.take<T>((size_t)n * m * d);
+    // the mixed path's pairs are bf16 rows of hist_ld(d) elements (as many T = float
+    // as half of that)
+    const size_t hist = fp64_eval ? (size_t)n * m * d : (size_t)n * m * (hist_ld(d) / 2);
+    a.S = cv.take<T>(hist);
+    a.Y = cv.take<T>(hist);
     a.rho = cv.take<T>((size_t)n * m);
     a.st = cv.take<WalkerState<T>>((size_t)n);
     a.act = cv.take<int32_t>((size_t)n);

@@ -26,7 +26,8 @@ struct LbfgsArgs {
     int d, m, max_iter, max_backtracks;
     T c1, backtrack, gtol;
     T *X, *G, *P, *XT, *GT, *FT;  // [N][d] (FT: [N])
-    T *S, *Y, *rho;               // [N][m][d], [N][m][d], [N][m]: 1 / s^T y (two-loop step) or s^T y (CTA step)
+    T *S, *Y, *rho;               // [N][m][d] (bf16 [N][m][hist_ld(d)] for the CTA step), [N][m]: 1 / s^T y
+                                  // (two-loop step) or s^T y (CTA step)
     WalkerState<T> *st;           // [N]
     int32_t *act;                 // [N] active walker ids
     int32_t *n_act;               // device scalar
@@ -40,8 +41,11 @@ template <typename T>
 void launch_lbfgs_step(const LbfgsArgs<T> &a, int n, cudaStream_t s);
 template <typename T>
 void launch_lbfgs_compact(const LbfgsArgs<T> &a, int64_t *n_evals, cudaStream_t s);
+// Row pitch (elements) of the mixed path's stored bf16 pairs: whole 16-byte chunks, so
+// that every stored row can be moved by bulk copies; coordinates d .. pitch - 1 hold zeros.
+__host__ __device__ __forceinline__ int hist_ld(int d) { return (d + 7) / 8 * 8; }
 // FP32 step, one CTA per walker, compact-representation direction (lbfgs_cta.cu);
-// the stored pairs S, Y are bf16. MRI, MYY: per-walker [N][m][m] R^-1
+// the stored pairs S, Y are bf16 ([N][m][hist_ld(d)]). MRI, MYY: per-walker [N][m][m] R^-1
 // (R = upper(S^T Y)) and Y^T Y, slot-indexed.
 void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *MYY, int num_sms, cudaStream_t s);
 // Compaction of the mixed path's active list, grouped by key[w] (the walker's dominant
