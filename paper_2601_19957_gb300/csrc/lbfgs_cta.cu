@@ -34,7 +34,6 @@
 #include <mutex>
 
 #include "sb_lbfgs.cuh"
-#include "sb_ptx.cuh"
 
 namespace sb {
 
@@ -84,8 +83,13 @@ __device__ __forceinline__ float4 axpy4(float a, float4 x, float4 y) {
 }
 __device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
-// Per-thread asynchronous copies global -> shared of the m x m state (4 bytes each),
-// completed by the copying thread's own cp.async.wait_group before a CTA barrier.
+// Per-thread asynchronous copies global -> shared (16 bytes of a stored row, L2 only;
+// 4 bytes of the m x m state). A thread completes its own copy groups
+// (cp.async.wait_group); a warp barrier then makes them visible to the warp.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
@@ -318,10 +322,6 @@ struct Shared {
     float red2[2][Cfg<CT>::NW * 32];  // reduction scratch, used alternately (see block_sum)
     float gamma;
     uint4 zero16;  // a zero row for the unused rows of the tensor-core operand
-    // per warp and ring slot: completion of the bulk copies of the warp's quarter of
-    // the slot's rows; set when a bounded wait gave up (every wait then gives up)
-    uint64_t full[Cfg<CT>::NW][Cfg<CT>::DB];
-    int abort;
 };
 
 // The m x m state of a walker, slot-indexed in HBM (logical pair i sits in slot
@@ -463,25 +463,18 @@ __device__ __forceinline__ void store_hist(const Vec<CT> &v, bf16 *row, int ldh)
                                                       pack2(v.v[1].x, v.v[1].y), pack2(v.v[1].z, v.v[1].w));
 }
 
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 // The ring the stored pairs stream through (Cfg: DB slots of PGB pairs; row 2 q + v of
-// a slot is vector v (0: s, 1: y) of its pair q). Warp w owns coordinates
-// 256 w .. 256 w + 255 of every row (its threads' chunks) and moves them itself:
-// one bulk copy per stored row, completing on the warp's barrier of the slot, so the
-// warps stream independently and a slot is refilled once its own warp has read it.
+// a slot is vector v (0: s, 1: y) of its pair q). Each thread copies and reads its own
+// 16-byte chunk of every row (cp.async); pass 1's tensor-core operands also read the
+// chunks of the other lanes of the warp, after a warp barrier. Every issue commits one
+// copy group (empty when there is nothing to copy), so a wait for the group issued
+// D - 1 issues earlier is cp.async.wait_group D - 1.
 template <int CT>
 struct Ring {
     static constexpr int PG = Cfg<CT>::PGB, D = Cfg<CT>::DB;
     static_assert(Cfg<CT>::VPT == 2, "one 16-byte bf16 chunk (8 coordinates) per stored vector and thread");
-    static_assert(2 * PG <= 32, "one copying lane per row of a slot");
-    Shared<CT> &sh;
     int ldh, m, head, J, cn;  // row pitch, history size, first slot, pairs in the ring, new pair (or -1)
     const bf16 *S, *Y;
-    uint32_t &ph;   // barrier parity per slot (this warp)
-    uint32_t pend;  // slots with copies issued and not yet waited for
 
     __device__ __forceinline__ unsigned char *row(int sl, int r) const {
         return ring_base() + sl * Cfg<CT>::SLOT_B + r * Cfg<CT>::ROW_B;
@@ -490,68 +483,34 @@ struct Ring {
     __device__ __forceinline__ uint4 *chunk(int sl, int r) const {
         return reinterpret_cast<uint4 *>(row(sl, r)) + threadIdx.x;
     }
-    // Group k (logical pairs k PG .. k PG + PG - 1 below J) into slot sl. The visit's
-    // new pair comes from registers (s_new, y_new: this thread's chunk), not HBM.
-    // whether some warp gave up a wait (the same answer in every lane of the warp)
-    __device__ __forceinline__ bool aborted() const {
-        return __any_sync(0xffffffffu, *reinterpret_cast<volatile int *>(&sh.abort) != 0);
-    }
-    __device__ __forceinline__ void issue(int k, int sl, const Vec<CT> &s_new, const Vec<CT> &y_new) {
-        if (aborted()) return;
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        const int c0 = 8 * 32 * wid;  // this warp's first coordinate
-        const int qn = ldh - c0 < 0 ? 0 : (ldh - c0 > 256 ? 256 : ldh - c0);
-        const uint32_t qb = 2u * (uint32_t)qn;
-        int nrows = 0;
+    // Group k (logical pairs k PG .. k PG + PG - 1 below J; none for k < 0) into slot sl.
+    // The visit's new pair comes from registers (s_new, y_new), not HBM.
+    __device__ __forceinline__ void issue(int k, int sl, const Vec<CT> &s_new, const Vec<CT> &y_new) const {
+        const int e0 = Vec<CT>::i0(0);
+        if (k >= 0 && e0 < ldh) {
 #pragma unroll
-        for (int q = 0; q < PG; ++q) {
-            const int j = k * PG + q;
-            if (j < J && j != cn) nrows += 2;
-        }
-        // the warp has read the slot; generic writes into it (the staged operand, the
-        // register rows) were ordered before the async proxy by the caller's fence
-        __syncwarp();
-        if (lane == 0) mbar_arrive_tx(&sh.full[wid][sl], (uint32_t)nrows * qb);
-        __syncwarp();
-        if (lane < 2 * PG && qb) {
-            const int q = lane >> 1, v = lane & 1, j = k * PG + q;
-            if (j < J && j != cn) {
+            for (int q = 0; q < PG; ++q) {
+                const int j = k * PG + q;
+                if (j >= J) break;
+                if (j == cn) {
+                    *chunk(sl, 2 * q) = make_uint4(pack2(s_new.v[0].x, s_new.v[0].y), pack2(s_new.v[0].z, s_new.v[0].w),
+                                                   pack2(s_new.v[1].x, s_new.v[1].y), pack2(s_new.v[1].z, s_new.v[1].w));
+                    *chunk(sl, 2 * q + 1) = make_uint4(pack2(y_new.v[0].x, y_new.v[0].y), pack2(y_new.v[0].z, y_new.v[0].w),
+                                                       pack2(y_new.v[1].x, y_new.v[1].y), pack2(y_new.v[1].z, y_new.v[1].w));
+                    continue;
+                }
                 int slot = head + j;
                 if (slot >= m) slot -= m;
-                bulk_g2s(row(sl, 2 * q + v) + 2 * c0, (v ? Y : S) + (size_t)slot * ldh + c0, qb, &sh.full[wid][sl]);
+                cp_async16(chunk(sl, 2 * q), S + (size_t)slot * ldh + e0);
+                cp_async16(chunk(sl, 2 * q + 1), Y + (size_t)slot * ldh + e0);
             }
         }
-        if (cn >= k * PG && cn < k * PG + PG && Vec<CT>::i0(0) < ldh) {
-            const int q = cn - k * PG;
-            *chunk(sl, 2 * q) = make_uint4(pack2(s_new.v[0].x, s_new.v[0].y), pack2(s_new.v[0].z, s_new.v[0].w),
-                                           pack2(s_new.v[1].x, s_new.v[1].y), pack2(s_new.v[1].z, s_new.v[1].w));
-            *chunk(sl, 2 * q + 1) = make_uint4(pack2(y_new.v[0].x, y_new.v[0].y), pack2(y_new.v[0].z, y_new.v[0].w),
-                                               pack2(y_new.v[1].x, y_new.v[1].y), pack2(y_new.v[1].z, y_new.v[1].w));
-        }
-        pend |= 1u << sl;
+        cp_async_commit();
     }
-    // Bounded wait for slot sl (every lane of the warp, the outcome made uniform);
-    // false once any warp of the CTA gave up.
-    __device__ __forceinline__ bool wait(int sl) {
-        const int wid = threadIdx.x >> 5;
-        const bool ok = __all_sync(0xffffffffu, bwait(&sh.full[wid][sl], (ph >> sl) & 1u, &sh.abort));
-        if (ok) {
-            ph ^= 1u << sl;
-            pend &= ~(1u << sl);
-        }
-        __syncwarp();  // the copies and the warp's register rows are visible to the warp
-        return ok;
-    }
-    // After a wait gave up: bounded waits for the copies still in flight into this
-    // warp's slots, so that none lands after the CTA has moved on.
-    __device__ __forceinline__ void drain() {
-        const int wid = threadIdx.x >> 5;
-        for (int sl = 0; sl < D; ++sl) {
-            if (!((pend >> sl) & 1u)) continue;
-            for (long long it = 0; it < kSpinLimit; ++it)
-                if (mbar_try_wait(&sh.full[wid][sl], (ph >> sl) & 1u)) break;
-        }
-        pend = 0;
+    // the group issued D - 1 issues ago has landed, and is visible to the warp
+    __device__ __forceinline__ void wait() const {
+        cp_async_wait<D - 1>();
+        __syncwarp();
     }
     // this thread's coordinates of pair q of slot sl
     __device__ __forceinline__ void fetch(int sl, int q, Vec<CT> &sv, Vec<CT> &yv) const {
@@ -577,7 +536,7 @@ struct Ring {
 template <int CT, bool EVEN>
 __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<float> &st, int new_slot,
                               const Vec<CT> &g_in, const Vec<CT> &x_in, const Vec<CT> &s_new, const Vec<CT> &y_new,
-                              float *MRI, float *MYY, Shared<CT> &sh, const Lay<CT> &L, int &par, uint32_t &ph) {
+                              float *MRI, float *MYY, Shared<CT> &sh, const Lay<CT> &L, int &par) {
     using RG = Ring<CT>;
     constexpr int PG = RG::PG, D = RG::D, NW = Cfg<CT>::NW;
     const int d = a.d, m = a.m, ldh = hist_ld(d);
@@ -592,20 +551,12 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
     if (count > 0) {
         const bool added = new_slot >= 0;
         const int cn = added ? count - 1 : -1;
-        RG ring{sh,
-                ldh,
-                m,
-                st.head,
-                count,
-                cn,
-                reinterpret_cast<const bf16 *>(a.S) + (size_t)w * m * ldh,
-                reinterpret_cast<const bf16 *>(a.Y) + (size_t)w * m * ldh,
-                ph,
-                0u};
+        const RG ring{ldh, m, st.head, count, cn, reinterpret_cast<const bf16 *>(a.S) + (size_t)w * m * ldh,
+                      reinterpret_cast<const bf16 *>(a.Y) + (size_t)w * m * ldh};
         const int ng = (count + PG - 1) / PG;
         float *mri_w = MRI + (size_t)w * m * m, *myy_w = MYY + (size_t)w * m * m, *dw = a.rho + (size_t)w * m;
 #pragma unroll 1
-        for (int k = 0; k < D - 1 && k < ng; ++k) ring.issue(k, k, s_new, y_new);
+        for (int k = 0; k < D - 1; ++k) ring.issue(k, k, s_new, y_new);
         float *p1 = L.p1();
         {
             // Pass 1 on the tensor cores: per warp (its 256 coordinates, 16 k-steps of
@@ -647,27 +598,28 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
             int nk = (d - 256 * wid + 15) / 16;  // k-steps of this warp inside d (warp-uniform)
             nk = nk < 0 ? 0 : (nk > 16 ? 16 : nk);
             const int gid = lane >> 2, tig = lane & 3;
-            // the staged operand is written (generic proxy) before the copies into its slot
-            fence_proxy_async_smem();
-            if (D - 1 < ng) ring.issue(D - 1, D - 1, s_new, y_new);
-            // the m x m state, needed after pass 1 (issued after the fence, which then
-            // has no copies of this thread to wait for)
+            __syncwarp();
             fetch_mm<CT>(L, mri_w, myy_w, dw, count, m, st.head, cn);
-            cp_async_commit();
+            ring.issue(D - 1, D - 1, s_new, y_new);
             for (int k = 0; k < ng; ++k) {
                 const int sl = k % D;
-                if (!ring.wait(sl)) break;
-                float acc[4] = {0.f, 0.f, 0.f, 0.f};
-                // B rows: the group's 8 stored vectors (pair n / 2, s or y)
+                ring.wait();
+                // B rows: the group's 8 stored vectors (pair n / 2, s or y); the k-steps
+                // accumulate into four independent sets (k-step mod 4), summed after, so
+                // that the MMAs are not one dependent chain
+                float a4[4][4] = {};
 #pragma unroll
                 for (int c = 0; c < 16; c += 2) {
                     if (c < nk) {
                         uint32_t b[4];
                         ldsm_x4(b, ring.row(sl, ri8) + 16 * (32 * wid + 2 * (c + (mi8 >> 1)) + (mi8 & 1)));
-                        mma_rows8(acc, af[c][0], af[c][1], b[0], b[1]);
-                        if (c + 1 < nk) mma_rows8(acc, af[c + 1][0], af[c + 1][1], b[2], b[3]);
+                        mma_rows8(a4[c & 3], af[c][0], af[c][1], b[0], b[1]);
+                        if (c + 1 < nk) mma_rows8(a4[(c + 1) & 3], af[c + 1][0], af[c + 1][1], b[2], b[3]);
                     }
                 }
+                float acc[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[e] = (a4[0][e] + a4[1][e]) + (a4[2][e] + a4[3][e]);
                 // g . v = (g_hi + g_mid) . v + g_lo . v from rows 0, 1, 2
                 const float h0 = __shfl_down_sync(0xffffffffu, acc[0], 4);
                 const float l0 = __shfl_down_sync(0xffffffffu, acc[0], 8);
@@ -680,7 +632,7 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
                     *reinterpret_cast<float2 *>(p1 + ((k * NW + wid) * 3 + r) * (2 * PG) + 2 * tig) = o;
                 }
                 __syncwarp();  // the warp has read the group before its slot is refilled
-                if (k + D < ng) ring.issue(k + D, sl, s_new, y_new);
+                ring.issue(k + D < ng ? k + D : -1, sl, s_new, y_new);
             }
         }
         cp_async_wait<0>();  // the m x m state
@@ -717,11 +669,9 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
         axpyv(-gam, g, p);
         const int r0 = ng > D ? ng - D : 0;  // groups below r0 are no longer in the ring
         const float *ca = L.ca(), *cw = L.cw();
-        // the new pair's register rows (generic proxy) before the refills of their slot
-        fence_proxy_async_smem();
         for (int k = ng - 1; k >= 0; --k) {
             const int sl = k % D;
-            if (k < r0 && !ring.wait(sl)) break;
+            if (k < r0) ring.wait();
 #pragma unroll
             for (int q = 0; q < PG; ++q) {
                 const int i = k * PG + q;
@@ -732,9 +682,9 @@ __device__ uint64_t direction(const LbfgsArgs<float> &a, int w, WalkerState<floa
                     axpyv(gam * cw[i], y4, p);
                 }
             }
-            if (k - D >= 0) ring.issue(k - D, sl, s_new, y_new);  // after this warp read the slot
+            ring.issue(k - D, sl, s_new, y_new);  // this thread's own chunks, just read
         }
-        if (ring.pend) ring.drain();  // only after a wait gave up
+        cp_async_wait<0>();  // (only empty groups remain) the ring is free for the next walker
         // the two-loop recursion's history traffic: each pair read in both passes
         bytes += (uint64_t)4 * count * d * sizeof(bf16);
     }
@@ -779,16 +729,10 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
     // read as zeros where a k-step of pass 1 straddles the end of the coordinates
     for (int e = threadIdx.x; e < Cfg<CT>::RING_B / 16; e += CT) lb_dyn[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (threadIdx.x == 0) {
-        sh.abort = 0;
-        for (int q = 0; q < Cfg<CT>::NW; ++q)
-            for (int sl = 0; sl < Cfg<CT>::DB; ++sl) mbar_init(&sh.full[q][sl], 1);
-        mbar_fence_init();
         sh.zero16 = make_uint4(0u, 0u, 0u, 0u);
     }
-    fence_proxy_async_smem();  // the zeroing before any copy into the ring
     __syncthreads();
     const int n_act = *a.n_act;
-    uint32_t ph = 0;  // barrier parity of this warp's ring slots
     int par = 0;  // alternation of the reduction scratch (identical in every thread)
     uint64_t bytes = 0;
     // the next visit's walker id is loaded one visit ahead, so a visit's first
@@ -877,7 +821,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                 st.count = 0;
                 st.head = 0;
                 st.attempt = 1;
-                bytes += direction<CT, EVEN>(a, w, st, -1, g, x, s_new, y_new, MRI, MYY, sh, L, par, ph);
+                bytes += direction<CT, EVEN>(a, w, st, -1, g, x, s_new, y_new, MRI, MYY, sh, L, par);
                 dnext = st.pn + alpha0 * pn0;  // from the old trial back to x, then out
             } else {
                 st.status = SB_WALKER_STALLED;
@@ -892,7 +836,7 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
                 st.status = SB_WALKER_MAXITER;
             } else {
                 st.attempt = 0;
-                bytes += direction<CT, EVEN>(a, w, st, new_slot, g, x, s_new, y_new, MRI, MYY, sh, L, par, ph);
+                bytes += direction<CT, EVEN>(a, w, st, new_slot, g, x, s_new, y_new, MRI, MYY, sh, L, par);
                 dnext = st.pn;  // x is this visit's trial
             }
         }
@@ -900,13 +844,11 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
             a.st[w] = st;
             if (a.dist && dnext >= 0.f) a.dist[w] = dnext * 1.0001f;  // margin for the rounding of |p|
         }
-        // No barrier before the next walker: a warp's part of the ring is read and
-        // refilled by that warp alone. The reduction scratch alternates, and every
-        // other shared array is rewritten only after the next walker's first
-        // reduction barrier.
-        if (*reinterpret_cast<volatile int *>(&sh.abort)) break;  // set before a CTA barrier of this visit
+        // No barrier before the next walker: a thread's ring chunks are read by
+        // other lanes only in pass 1, behind warp barriers, and every copy group has
+        // completed. The reduction scratch alternates, and every other shared array
+        // is rewritten only after the next walker's first reduction barrier.
     }
-    if (*reinterpret_cast<volatile int *>(&sh.abort) && threadIdx.x == 0 && a.err) atomicOr(a.err, SB_DEV_TIMEOUT);
     if (count_bytes && threadIdx.x == 0 && bytes) atomicAdd(&g_lbfgs_bytes, (unsigned long long)bytes);
 }
 

@@ -42,7 +42,7 @@ void launch_lbfgs_step(const LbfgsArgs<T> &a, int n, cudaStream_t s);
 template <typename T>
 void launch_lbfgs_compact(const LbfgsArgs<T> &a, int64_t *n_evals, cudaStream_t s);
 // Row pitch (elements) of the mixed path's stored bf16 pairs: whole 16-byte chunks, so
-// that every stored row can be moved by bulk copies; coordinates d .. pitch - 1 hold zeros.
+// that every stored row is moved in aligned 16-byte copies; coordinates d .. pitch - 1 hold zeros.
 __host__ __device__ __forceinline__ int hist_ld(int d) { return (d + 7) / 8 * 8; }
 // FP32 step, one CTA per walker, compact-representation direction (lbfgs_cta.cu);
 // the stored pairs S, Y are bf16 ([N][m][hist_ld(d)]). MRI, MYY: per-walker [N][m][m] R^-1
