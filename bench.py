@@ -25,11 +25,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes per algorithmic byte of the L-BFGS step with bf16 pairs, measured
-# with ncu over all step launches of one solve at d=1024, K=8, 8192 walkers
-# (41.23 + 9.12 GB DRAM for 72 x 1.2005 GB algorithmic): the second pass of the
-# two-loop recursion is mostly served by L2.
-LBFGS_DRAM_PER_ALGORITHMIC_BYTE = 0.582
+# DRAM bytes per algorithmic byte of the L-BFGS step with bf16 pairs: ncu
+# dram__bytes_read.sum + dram__bytes_write.sum of step launches 40-42 of a solve at
+# d=1024, K=8, 8192 walkers (2.831 GB in all) against the step's own algorithmic-byte
+# count for the same three launches (4.889 GB). The second pass of the two-loop
+# recursion is served by the shared-memory ring (the newest groups) and L2.
+LBFGS_DRAM_PER_ALGORITHMIC_BYTE = 0.579
 
 METRIC = "logL+grad evals/sec and evidence solves/sec at d=1024 K=8 vs plain FP64 GPU; |ΔlogZ|"
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2}

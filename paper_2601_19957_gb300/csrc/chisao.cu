@@ -12,6 +12,8 @@
 // (pair, group G + column, oscillation << 16 | peak, 'GRST') for Golden
 // Rooster, in orthonormal groups of G = min(d, 64) directions), two uniforms
 // per block, two normals by Box-Muller.
+#include <mutex>
+
 #include "sb_chisao.cuh"
 
 namespace sb {
@@ -211,26 +213,43 @@ __global__ void __launch_bounds__(256) k_cs_rm_rays(int d, uint32_t k0, uint32_t
 }
 
 constexpr int CS_BASIS = 256;
+// Golden Rooster groups as the Q of a Cholesky QR, twice (CholeskyQR2): the Gram
+// matrix of the columns over row tiles, its Cholesky factor L (R = L^T), R^-1 by
+// back substitution, then A <- A R^-1; the second pass restores orthogonality to
+// working precision (Gaussian columns are well conditioned: cond ~ (sqrt d + sqrt G) /
+// (sqrt d - sqrt G)). The Q of a QR with positive diag(R) is unique, so this is the
+// Q Gram-Schmidt gives, up to rounding.
+constexpr int CS_QR_MAXC = 64;                                          // columns of a group (cs_group)
+constexpr int CS_QR_TILE = 64;                                          // rows per tile
+constexpr int CS_QR_LD = CS_QR_MAXC + 1;                                // row stride of the shared arrays
+constexpr int CS_QR_PER_T = (CS_QR_MAXC * (CS_QR_MAXC + 1) / 2 + CS_BASIS - 1) / CS_BASIS;  // Gram entries a thread
+template <typename T>
+constexpr size_t cs_qr_smem() {
+    return sizeof(T) * (size_t)(CS_QR_TILE + 2 * CS_QR_MAXC) * CS_QR_LD;
+}
 
-// One orthonormal group per CTA: the Philox normals orthogonalised column by column by
-// classical Gram-Schmidt with a second pass, and normalised, in arithmetic T: FP64 on
-// the FP64 path; FP32 (normals included) on the mixed path, whose rays are formed in
-// FP32 anyway and on whose GB300 FP64 units the d G^2 QR would be the slowest step of a
-// reseeding. Q stays FP64 in memory.
+// One orthonormal group per CTA: the Q factor of the Philox normals (CholeskyQR2, as
+// above), in arithmetic T: FP64 on the FP64 path; FP32 (normals included) on the mixed
+// path, whose rays are formed in FP32 anyway and on whose GB300 FP64 units the d G^2 QR
+// would be the slowest step of a reseeding. Q stays FP64 in memory.
 template <typename T>
 __global__ void __launch_bounds__(CS_BASIS) k_cs_bases(int d, uint32_t k0, uint32_t k1, int osc, const int32_t *job_pk,
                                                        const int32_t *job_b, const int32_t *job_cols,
                                                        const int64_t *job_off, const int32_t *state, double *Q) {
-    extern __shared__ double s_h[];  // [d] projections of the current column
-    __shared__ T s_red[CS_BASIS / 32];
+    // [CS_QR_TILE][CS_QR_LD] rows of the job's columns, the Gram matrix / its Cholesky
+    // factor, and the inverse of R = L^T, each CS_QR_LD wide
+    extern __shared__ __align__(16) unsigned char cs_qr_smem[];
+    T *tile = reinterpret_cast<T *>(cs_qr_smem);
+    T *Lm = tile + CS_QR_TILE * CS_QR_LD;
+    T *Ri = Lm + CS_QR_MAXC * CS_QR_LD;
     const int j = blockIdx.x;
     if (state[kCsBranch] != kBranchGr || j >= state[kCsJobs]) return;
-    const int pk = job_pk[j], b = job_b[j], cols = job_cols[j];
+    const int pk = job_pk[j], b = job_b[j], n = job_cols[j];
     double *Qj = Q + job_off[j];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = CS_BASIS / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int npairs = (d + 1) / 2;
     const int G = cs_group(d);
-    for (int idx = threadIdx.x; idx < cols * npairs; idx += CS_BASIS) {
+    for (int idx = threadIdx.x; idx < n * npairs; idx += CS_BASIS) {
         const int c = idx / npairs, q = idx - c * npairs;
         T z0, z1;
         if (sizeof(T) == sizeof(double)) {
@@ -250,39 +269,93 @@ __global__ void __launch_bounds__(CS_BASIS) k_cs_bases(int d, uint32_t k0, uint3
         if (2 * q + 1 < d) Qj[(size_t)c * d + 2 * q + 1] = (double)z1;
     }
     __syncthreads();
-    T *sh = reinterpret_cast<T *>(s_h);
-    for (int c = 0; c < cols; ++c) {
-        double *qc = Qj + (size_t)c * d;
-        for (int pass = 0; pass < 2 && c > 0; ++pass) {
-            for (int k = wid; k < c; k += nw) {
-                const double *qk = Qj + (size_t)k * d;
-                T dot = 0;
-                for (int i = lane; i < d; i += 32) dot += (T)qk[i] * (T)qc[i];
-                dot = warp_sum(dot);
-                if (lane == 0) sh[k] = dot;
+    const int ne = n * (n + 1) / 2;  // Gram entries (k <= l)
+    // thread t owns entries t, t + CS_BASIS, ... of the upper triangle (row-major
+    // order): entry (ek, el), or ek = -1
+    int ek[CS_QR_PER_T], el[CS_QR_PER_T];
+#pragma unroll
+    for (int q = 0; q < CS_QR_PER_T; ++q) {
+        const int e = threadIdx.x + q * CS_BASIS;
+        int k = 0, rem = e;  // row k of the upper triangle holds n - k entries
+        while (k < n && rem >= n - k) {
+            rem -= n - k;
+            ++k;
+        }
+        ek[q] = e < ne ? k : -1;
+        el[q] = k + rem;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+        // Gram matrix A^T A over tiles of CS_QR_TILE rows
+        T acc[CS_QR_PER_T];
+#pragma unroll
+        for (int q = 0; q < CS_QR_PER_T; ++q) acc[q] = 0;
+        for (int i0 = 0; i0 < d; i0 += CS_QR_TILE) {
+            const int rows = d - i0 < CS_QR_TILE ? d - i0 : CS_QR_TILE;
+            for (int e = threadIdx.x; e < CS_QR_TILE * n; e += CS_BASIS) {
+                const int c = e / CS_QR_TILE, r = e - c * CS_QR_TILE;
+                tile[r * CS_QR_LD + c] = r < rows ? (T)Qj[(size_t)c * d + i0 + r] : (T)0;
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < d; i += CS_BASIS) {
-                T acc = 0;
-                for (int k = 0; k < c; ++k) acc += sh[k] * (T)Qj[(size_t)k * d + i];
-                qc[i] = (double)((T)qc[i] - acc);
+#pragma unroll
+            for (int q = 0; q < CS_QR_PER_T; ++q) {
+                if (ek[q] >= 0) {
+                    const int k = ek[q], l = el[q];
+                    T s = 0;
+                    for (int r = 0; r < rows; ++r) s += tile[r * CS_QR_LD + k] * tile[r * CS_QR_LD + l];
+                    acc[q] += s;
+                }
             }
             __syncthreads();
         }
-        T ss = 0;
-        for (int i = threadIdx.x; i < d; i += CS_BASIS) ss += (T)qc[i] * (T)qc[i];
-        ss = warp_sum(ss);
-        if (lane == 0) s_red[wid] = ss;
+#pragma unroll
+        for (int q = 0; q < CS_QR_PER_T; ++q)
+            if (ek[q] >= 0) Lm[el[q] * CS_QR_LD + ek[q]] = acc[q];  // lower triangle: Lm[l][k] = (A^T A)_kl
         __syncthreads();
+        // Cholesky A^T A = L L^T (one warp, column by column; rows i = lane, lane + 32)
         if (wid == 0) {
-            T v = lane < nw ? s_red[lane] : (T)0;
-            v = warp_sum(v);
-            if (lane == 0) s_red[0] = v;
+            for (int c = 0; c < n; ++c) {
+                T s = 0;
+                for (int p = lane; p < c; p += 32) s += Lm[c * CS_QR_LD + p] * Lm[c * CS_QR_LD + p];
+                s = warp_sum(s);
+                const T dcc = sqrt(Lm[c * CS_QR_LD + c] - s);
+                for (int i = c + 1 + lane; i < n; i += 32) {
+                    T t = Lm[i * CS_QR_LD + c];
+                    for (int p = 0; p < c; ++p) t -= Lm[i * CS_QR_LD + p] * Lm[c * CS_QR_LD + p];
+                    Lm[i * CS_QR_LD + c] = div_rn(t, dcc);
+                }
+                __syncwarp();
+                if (lane == 0) Lm[c * CS_QR_LD + c] = dcc;
+                __syncwarp();
+            }
         }
         __syncthreads();
-        const T nrm = sqrt(s_red[0]);
-        for (int i = threadIdx.x; i < d; i += CS_BASIS) qc[i] = (double)div_rn((T)qc[i], nrm);
+        // Ri = R^-1 for R = L^T (upper): column c by back substitution, one thread each
+        for (int c = threadIdx.x; c < n; c += CS_BASIS) {
+            Ri[c * CS_QR_LD + c] = div_rn((T)1, Lm[c * CS_QR_LD + c]);
+            for (int i = c - 1; i >= 0; --i) {
+                T t = 0;
+                for (int p = i + 1; p <= c; ++p) t += Lm[p * CS_QR_LD + i] * Ri[p * CS_QR_LD + c];  // R_ip = L_pi
+                Ri[i * CS_QR_LD + c] = div_rn(-t, Lm[i * CS_QR_LD + i]);
+            }
+        }
         __syncthreads();
+        // A <- A R^-1, tile by tile (the tile is read from HBM before it is overwritten)
+        for (int i0 = 0; i0 < d; i0 += CS_QR_TILE) {
+            const int rows = d - i0 < CS_QR_TILE ? d - i0 : CS_QR_TILE;
+            for (int e = threadIdx.x; e < CS_QR_TILE * n; e += CS_BASIS) {
+                const int c = e / CS_QR_TILE, r = e - c * CS_QR_TILE;
+                tile[r * CS_QR_LD + c] = r < rows ? (T)Qj[(size_t)c * d + i0 + r] : (T)0;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < CS_QR_TILE * n; e += CS_BASIS) {
+                const int c = e / CS_QR_TILE, r = e - c * CS_QR_TILE;
+                if (r >= rows) continue;
+                T t = 0;
+                for (int p = 0; p <= c; ++p) t += tile[r * CS_QR_LD + p] * Ri[p * CS_QR_LD + c];
+                Qj[(size_t)c * d + i0 + r] = (double)t;
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -542,12 +615,17 @@ void launch_cs_bases(int max_jobs, int d, uint64_t seed, int osc, const int32_t 
                      const int32_t *job_cols, const int64_t *job_off, const int32_t *state, double *Q, bool fp32,
                      cudaStream_t s) {
     if (max_jobs <= 0) return;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_cs_bases<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs_qr_smem<float>());
+        cudaFuncSetAttribute(k_cs_bases<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs_qr_smem<double>());
+    });
     note_launch();
     if (fp32)
-        k_cs_bases<float><<<max_jobs, CS_BASIS, sizeof(double) * d, s>>>(
+        k_cs_bases<float><<<max_jobs, CS_BASIS, cs_qr_smem<float>(), s>>>(
             d, (uint32_t)seed, (uint32_t)(seed >> 32), osc, job_pk, job_b, job_cols, job_off, state, Q);
     else
-        k_cs_bases<double><<<max_jobs, CS_BASIS, sizeof(double) * d, s>>>(
+        k_cs_bases<double><<<max_jobs, CS_BASIS, cs_qr_smem<double>(), s>>>(
             d, (uint32_t)seed, (uint32_t)(seed >> 32), osc, job_pk, job_b, job_cols, job_off, state, Q);
 }
 

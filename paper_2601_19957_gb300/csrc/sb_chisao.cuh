@@ -43,8 +43,8 @@ void launch_cs_rm_rays(int n, int d, uint64_t seed, int osc, const int32_t *unco
 // Golden Rooster groups (when the branch is 2; job j < the job count, grid for
 // max_jobs): job j fills cols[j] orthonormal columns (column c at Q + off[j] + c d) of
 // group b[j] of peak pk[j]: Philox normals (counter (pair, b G + c, osc << 16 | pk,
-// 'GRST')) made orthonormal in column order (classical Gram-Schmidt, two passes), in
-// FP32 when fp32, else FP64.
+// 'GRST')) made orthonormal in column order (the Q factor of their QR, by Cholesky QR
+// applied twice), in FP32 when fp32, else FP64.
 void launch_cs_bases(int max_jobs, int d, uint64_t seed, int osc, const int32_t *job_pk, const int32_t *job_b,
                      const int32_t *job_cols, const int64_t *job_off, const int32_t *state, double *Q, bool fp32,
                      cudaStream_t s);
