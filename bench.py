@@ -54,7 +54,9 @@ def parse():
     ap.add_argument("--next-rows", action="store_true",
                     help="time the preprocessing probe, the V2V/V2E/W2W segment pass and the black-box "
                          "derivatives (one JSON line)")
-    ap.add_argument("--prec", default="bf16", choices=list(PREC))
+    ap.add_argument("--prec", default=None, choices=list(PREC),
+                    help="likelihood precision; default the workload's own: fp64 for 0 and 1, tf32 for 3, "
+                         "bf16 for 2 (which reports every precision) and 4")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -68,7 +70,10 @@ def parse():
                     help="time only the tensor-core l+grad contraction on --n-points points")
     ap.add_argument("--n-points", type=int, default=16384)
     ap.add_argument("--scale", type=float, default=None, help="scale ray/start counts (profiling only)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.prec is None:
+        args.prec = {0: "fp64", 1: "fp64", 2: "bf16", 3: "tf32", 4: "bf16"}[args.workload]
+    return args
 
 
 def workload_cfg(wid, prec, scale=None):
@@ -401,7 +406,7 @@ def main():
         res["e2e"] = e2e_measure(sb, inst, cfg, c, cc if use_chisao else None, args, lg_per_step, flush)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(inst, cfg, args.cpu_seconds)
-    if rank == 0 and not args.no_fp64:
+    if rank == 0 and not args.no_fp64 and args.prec != "fp64":  # an FP64 line is its own comparator
         res["fp64_gpu"] = fp64_comparator(sb, args, use_chisao)
         res["fp64_peak"] = fp64_peak(sb)
     if rank == 0:
@@ -421,15 +426,19 @@ def fp64_roofline(sb, prof_ms, prof_n, prof_steps, lg_per_step, d, K):
 
 
 def run_adjoint(sb, args):
-    """Forward log Z and the hand-written adjoint d log Z / d mu_k, d log Z / d L_k
-    (FP64, H recomputed at each mode) on the d=1024, K=8 workload."""
+    """Forward log Z (the headline solve: discovery, ChiSao, Laplace over every final
+    sample; sunburst-only with --no-chisao) and the hand-written adjoint d log Z / d mu_k,
+    d log Z / d L_k (FP64, H recomputed at each mode) on the d=1024, K=8 workload."""
     import torch
 
     inst, cfg = workload_cfg(args.workload, args.prec, args.scale)
     prob = sb.Problem(inst)
     c = sb.make_config(cfg)
-    wsp = sb.workspace(prob, c)
-    out = sb.evidence(prob, c, ws=wsp)
+    use_chisao = not args.no_chisao
+    cc = sb.make_chisao_config()
+    wsp = sb.chisao_workspace(prob, c) if use_chisao else sb.workspace(prob, c)
+    forward = (lambda: sb.evidence_chisao(prob, c, cc, ws=wsp)) if use_chisao else (lambda: sb.evidence(prob, c, ws=wsp))
+    out = forward()
     for _ in range(max(args.warmup, 1)):
         sb.evidence_backward(prob, out.modes, out.logZk, out.n_modes)
     torch.cuda.synchronize()
@@ -441,11 +450,12 @@ def run_adjoint(sb, args):
     dt_b = (time.perf_counter() - t0) / reps
     t0 = time.perf_counter()
     for _ in range(reps):
-        out = sb.evidence(prob, c, ws=wsp)
+        out = forward()
     torch.cuda.synchronize()
     dt_f = (time.perf_counter() - t0) / reps
     d, K, nm = inst.d, inst.K, out.n_modes
     print(json.dumps({"case": "adjoint", "workload": f"d={d} K={K}, {cfg.n_starts} starts, m={cfg.m}",
+                      "forward": "discovery + ChiSao + Laplace" if use_chisao else "sunburst-only discovery + Laplace",
                       "n_modes": nm, "ms_forward": dt_f * 1e3, "ms_backward": dt_b * 1e3,
                       "backward_fp64_flop_model": 2.0 * nm * d ** 3,
                       "max_abs_dmu": float(dmu.abs().max()), "max_abs_dL": float(dL.abs().max())}))
@@ -616,7 +626,7 @@ def run_batched(sb, args):
     from paper_2601_19957_gb300.instances import workload
 
     insts, cfg = workload(3, scale=args.scale)
-    cfg.prec = PREC[args.prec] if args.prec != "bf16" else PREC["tf32"]
+    cfg.prec = PREC[args.prec]
     cfg.cand_cap = 32
     probs = [sb.Problem(i) for i in insts]
     c = sb.make_config(cfg)
