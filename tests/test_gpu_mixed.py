@@ -133,6 +133,49 @@ def test_mixed_refine_reaches_gaussian_mean(prec, d, m):
     assert (peak - out.ell.cpu().numpy()).max() <= 0.5 + 1e-3 * abs(peak)
 
 
+@pytest.mark.parametrize("prec", [sb.PREC_BF16, sb.PREC_TF32])
+def test_mixed_refine_walkers_independent_of_batch(prec):
+    """A walker's refinement depends on its own start alone: its rows of a tensor-core
+    round do not depend on the rows that share its 128-row block (the pairs a block
+    skips contribute exact zeros to every row) and its L-BFGS step reads no other
+    walker. So 40000 walkers refined in one call, where the compaction of the active
+    list takes its multi-chunk path (beyond 16384 entries), end bit for bit where the
+    same starts end in calls of at most 16000 walkers."""
+    inst = make_instance(16, 3, 5150, s_range=(0.05, 0.5), mean_box=(-6, 6), sep=8.0)
+    n = 40000
+    c = sb.make_config(SolveConfig(n_rays=1024, n_steps=64, n_starts=n, m=10, seed=17, prec=prec))
+    prob = sb.Problem(inst)
+    starts = torch.as_tensor(np.random.default_rng(9).uniform(-10.0, 10.0, (n, inst.d)), device="cuda")
+    ws = sb.workspace(prob, c)
+    whole = sb.refine(prob, c, starts, ws=ws)
+    wx, wl, wst, wit = whole.x.clone(), whole.ell.clone(), whole.status.clone(), whole.iters.clone()
+    parts = [sb.refine(prob, c, starts[i:i + 16000], ws=ws) for i in range(0, n, 16000)]
+    assert torch.equal(wx, torch.cat([p.x for p in parts]))
+    assert torch.equal(wl, torch.cat([p.ell for p in parts]))
+    assert torch.equal(wst, torch.cat([p.status for p in parts]))
+    assert torch.equal(wit, torch.cat([p.iters for p in parts]))
+    assert whole.n_evals == sum(p.n_evals for p in parts)
+
+
+@pytest.mark.parametrize("prec", [sb.PREC_BF16, sb.PREC_TF32])
+def test_mixed_refine_components_beyond_32(prec):
+    """K = 40: walkers started near components 32..39 keep those components in the
+    walker rounds' component skip (one mask bit per component, up to 64) and end at
+    their means, |L_k^T (x - mu_k)|_2 <= 1, as in the single-Gaussian test."""
+    inst = make_instance(16, 40, 4400, s_range=(0.05, 0.5), mean_box=(-6, 6), sep=8.0)
+    rng = np.random.default_rng(41)
+    ks = np.arange(32, 40).repeat(32)
+    n = len(ks)
+    x0 = inst.mu[ks] + rng.normal(0, 0.05, (n, inst.d))
+    c = SolveConfig(n_rays=n, n_steps=1, n_starts=n, m=10, seed=41, prec=prec)
+    out = sb.refine(sb.Problem(inst), sb.make_config(c), torch.as_tensor(x0, device="cuda"))
+    assert set(out.status.cpu().numpy().tolist()) <= {sb.CONVERGED, sb.STALLED}
+    x = out.x.cpu().numpy()
+    for t, k in enumerate(ks):
+        z = (x[t] - inst.mu[k]) @ inst.L[k]
+        assert np.sqrt(z @ z) <= 1.0, (t, k)
+
+
 def test_full_size_workload_sampled_against_oracle():
     """The configuration the bench times (d=1024, K=8, 16384 rays x 64 steps, 16384
     walkers, m=20, BF16, ChiSao), checked where the oracle can follow one output at a

@@ -119,3 +119,16 @@ def test_tc_gradient_overlapping_and_mixed_blocks(prec):
     X = np.where((np.arange(n) % 2 == 0)[:, None], between, near)
     X[256:384] = inst.mu[1] + rng.normal(0, 0.05, (128, inst.d))
     _check(inst, X, prec)
+
+
+@pytest.mark.parametrize("prec", [sb.PREC_BF16, sb.PREC_TF32])
+def test_tc_loglik_components_beyond_32(prec):
+    """K = 40: the component masks of the tensor-core path hold one bit per component
+    (up to 64), so points near components 32..39 get those components' terms in l and
+    their chunks in the gradient GEMM (a 32-bit mask would drop them: l would miss its
+    largest term and the gradient would be the other components' alone)."""
+    inst = make_instance(16, 40, 4400, s_range=(0.05, 0.5), mean_box=(-6, 6), sep=8.0)
+    rng = np.random.default_rng(40)
+    ks = np.concatenate([np.arange(32, 40).repeat(24), rng.integers(0, 40, 64)])
+    X = inst.mu[ks] + rng.normal(0, 0.1, (len(ks), inst.d))
+    _check(inst, X, prec)
