@@ -326,6 +326,7 @@ void adjoint_carve(Carver &cv, AdjWs &w, int d, int K) {
     w.pi = cv.take<double>(kMaxAdjModes);
     w.info = cv.take<int32_t>(1);
     w.one = cv.take<int32_t>(1);
+    w.bar = cv.take<uint32_t>(2);
 }
 
 sb_status adjoint_run(const ProbView &pv, const AdjWs &w, const double *modes, const double *logZk, int n_modes,
@@ -362,7 +363,7 @@ sb_status adjoint_run(const ProbView &pv, const AdjWs &w, const double *modes, c
         la.grad_sign = -1.0;
         la.out_by_walker = 0;
         launch_lik_f64_few(la, true, s);
-        launch_hessian_chol(d, K, 1, pv.L, w.P, w.Z, w.R, w.gbar, w.one, w.GK, w.H, w.info, s);
+        launch_hessian_chol(d, K, 1, pv.L, w.P, w.Z, w.R, w.gbar, w.one, w.GK, w.H, w.info, w.bar, pv.status, s);
         // W [g_0 .. g_{K-1}, gbar]
         note_launch();
         k_pack_rhs<<<(d * (K + 1) + 255) / 256, 256, 0, s>>>(d, K, w.GK, w.gbar, w.R, w.V);

@@ -17,6 +17,8 @@
 //  * log Z_k = l(x*) + (d/2) log 2pi - sum_i log C_ii (Sec. 3.7.1 with the
 //    whitening identity of App. A.8) and log Z = LSE_k log Z_k - log V
 //    (Sec. 3.7.3, App. A.10, Sec. 3.2).
+#include <vector>
+
 #include "sb_graph.cuh"
 #include "sb_laplace.cuh"
 
@@ -358,23 +360,27 @@ __global__ void __launch_bounds__(256) k_hessian(int d, int K, const double *P, 
 }
 
 // ------------------------------------------------------------------ blocked Cholesky
+// Right-looking, NB x NB blocks, every live candidate of a batch at once, in one
+// cooperative launch: for each block step kb, (A) the diagonal block of every
+// candidate, (B) its panel blocks below, (C) the trailing blocks, with a bounded grid
+// barrier after each phase (a launch per phase and step waited on the previous one's
+// launch latency: 96 dependent launches per factorisation at d = 1024). Blocks written
+// by one CTA are read by others after a barrier, so every read of H bypasses L1.
+//
 // Diagonal block factor, 256 threads, one barrier per column. Step j updates the
 // trailing lower triangle with the unscaled pivot column, a_ik -= a_ij a_kj / a_jj
 // (= L_ij L_kj), every thread taking 1 / a_jj itself; column j is final after
 // step j (later steps touch only columns > j), so the columns are scaled by
-// 1 / sqrt(a_jj) once at the end. A pivot <= 0 (not positive definite) stops
-// every thread at the same step.
-constexpr int DIAG_THREADS = 256;
-__global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(int d, int kb, double *H, const int32_t *n_c,
-                                                             const int32_t *onehot, int32_t *info) {
-    const int c = blockIdx.x;
-    if (c >= *n_c || info[c] || (onehot && onehot[c] >= 0)) return;
-    double *A = H + (size_t)c * d * d;
+// 1 / sqrt(a_jj) once at the end. A pivot <= 0 (not positive definite) sets the
+// candidate's info flag (read by every CTA after the next barrier).
+constexpr int CF_THREADS = 256;
+__device__ void potrf_block(int d, int kb, double *A, int32_t *info_c) {
     __shared__ double a[NB][NB + 1];
     const int o = kb * NB;
-    for (int e = threadIdx.x; e < NB * NB; e += DIAG_THREADS) {
+    for (int e = threadIdx.x; e < NB * NB; e += CF_THREADS) {
         const int i = e / NB, j = e % NB;
-        a[i][j] = (o + i < d && o + j < d) ? A[(size_t)(o + i) * d + o + j] : (i == j ? 1.0 : 0.0);  // identity padding
+        a[i][j] = (o + i < d && o + j < d) ? __ldcg(&A[(size_t)(o + i) * d + o + j])
+                                           : (i == j ? 1.0 : 0.0);  // identity padding
     }
     __syncthreads();
     bool bad = false;
@@ -386,7 +392,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(int d, int kb, doub
         }
         const double ip = 1.0 / p;
         const int m = NB - 1 - j;
-        for (int e = threadIdx.x; e < m * (m + 1) / 2; e += DIAG_THREADS) {
+        for (int e = threadIdx.x; e < m * (m + 1) / 2; e += CF_THREADS) {
             // e -> (ii >= kk) in the packed lower triangle of the trailing block
             int ii = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
             while (ii * (ii + 1) / 2 > e) --ii;
@@ -398,53 +404,50 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(int d, int kb, doub
         __syncthreads();
     }
     if (bad) {
-        if (threadIdx.x == 0) info[c] = 1;
+        if (threadIdx.x == 0) *info_c = 1;
+        __syncthreads();
         return;
     }
-    for (int e = threadIdx.x; e < NB * NB; e += DIAG_THREADS) {
+    for (int e = threadIdx.x; e < NB * NB; e += CF_THREADS) {
         const int i = e / NB, j = e % NB;
         if (o + i < d && o + j < d && j <= i) {
             const double r = rsqrt(a[j][j]);
             A[(size_t)(o + i) * d + o + j] = i == j ? a[j][j] * r : a[i][j] * r;
         }
     }
+    __syncthreads();  // the shared block is free for the next item
 }
 
-// Panel: A[ib][kb] <- A[ib][kb] L_kk^{-T}. 128 threads: thread (r, part) holds row r's
+// Panel: A[ib][kb] <- A[ib][kb] L_kk^{-T}. Threads 0..127: thread (r, part) holds row r's
 // columns part, part + 4, ... in registers; per column j the owner scales by
 // 1 / L_jj (reciprocals taken once, in parallel) and publishes it, then every
-// thread updates its later columns. One barrier per column; the FP64 updates
-// are spread over four warps (four schedulers).
+// thread updates its later columns. One barrier per column (every thread of the
+// CTA takes part in them); the FP64 updates are spread over four warps.
 constexpr int TRSM_THREADS = 128;
-__global__ void __launch_bounds__(TRSM_THREADS) k_trsm_panel(int d, int kb, double *H, const int32_t *n_c,
-                                                             const int32_t *onehot, const int32_t *info) {
-    const int c = blockIdx.y, ib = kb + 1 + blockIdx.x;
-    if (c >= *n_c || info[c] || (onehot && onehot[c] >= 0)) return;
-    const int nblk = (d + NB - 1) / NB;
-    if (ib >= nblk) return;
-    double *A = H + (size_t)c * d * d;
+__device__ void trsm_block(int d, int kb, int ib, double *A) {
     __shared__ double l[NB][NB + 1];
     __shared__ double xs[NB][NB + 1];
     __shared__ double inv[NB];
     const int o = kb * NB;
-    for (int e = threadIdx.x; e < NB * NB; e += TRSM_THREADS) {
+    for (int e = threadIdx.x; e < NB * NB; e += CF_THREADS) {
         const int i = e / NB, j = e % NB;
-        l[i][j] = (o + i < d && o + j < d) ? A[(size_t)(o + i) * d + o + j] : (i == j ? 1.0 : 0.0);
+        l[i][j] = (o + i < d && o + j < d) ? __ldcg(&A[(size_t)(o + i) * d + o + j]) : (i == j ? 1.0 : 0.0);
     }
     __syncthreads();
+    const bool act = threadIdx.x < TRSM_THREADS;
     if (threadIdx.x < NB) inv[threadIdx.x] = 1.0 / l[threadIdx.x][threadIdx.x];
-    const int r = threadIdx.x & (NB - 1), part = threadIdx.x >> 5;
+    const int r = threadIdx.x & (NB - 1), part = (threadIdx.x >> 5) & 3;
     const int row = ib * NB + r;
     double x[NB / 4];
 #pragma unroll
     for (int q = 0; q < NB / 4; ++q) {
         const int j = part + 4 * q;
-        x[q] = (row < d && o + j < d) ? A[(size_t)row * d + o + j] : 0.0;
+        x[q] = (act && row < d && o + j < d) ? __ldcg(&A[(size_t)row * d + o + j]) : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-        if (part == (j & 3)) {
+        if (act && part == (j & 3)) {
             x[j >> 2] *= inv[j];
             xs[r][j] = x[j >> 2];
         }
@@ -454,30 +457,25 @@ __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_panel(int d, int kb, doub
         for (int q = 0; q < NB / 4; ++q)
             if (part + 4 * q > j) x[q] -= xj * l[part + 4 * q][j];
     }
+    if (act) {
 #pragma unroll
-    for (int q = 0; q < NB / 4; ++q) {
-        const int j = part + 4 * q;
-        if (row < d && o + j < d) A[(size_t)row * d + o + j] = x[q];
+        for (int q = 0; q < NB / 4; ++q) {
+            const int j = part + 4 * q;
+            if (row < d && o + j < d) A[(size_t)row * d + o + j] = x[q];
+        }
     }
+    __syncthreads();  // the shared blocks are free for the next item
 }
 
 // Trailing update A[ib][jb] -= A[ib][kb] A[jb][kb]^T for kb < jb <= ib.
-__global__ void __launch_bounds__(256) k_syrk_update(int d, int kb, double *H, const int32_t *n_c,
-                                                     const int32_t *onehot, const int32_t *info) {
-    const int c = blockIdx.z;
-    if (c >= *n_c || info[c] || (onehot && onehot[c] >= 0)) return;
-    const int ib = kb + 1 + blockIdx.y, jb = kb + 1 + blockIdx.x;
-    if (jb > ib) return;
-    const int nblk = (d + NB - 1) / NB;
-    if (ib >= nblk) return;
-    double *A = H + (size_t)c * d * d;
+__device__ void syrk_block(int d, int kb, int ib, int jb, double *A) {
     __shared__ double pa[NB][NB + 1], pb[NB][NB + 1];
     const int o = kb * NB;
-    for (int e = threadIdx.x; e < NB * NB; e += 256) {
+    for (int e = threadIdx.x; e < NB * NB; e += CF_THREADS) {
         const int r = e / NB, q = e % NB;
         const int ia = ib * NB + r, ja = jb * NB + r, col = o + q;
-        pa[r][q] = (ia < d && col < d) ? A[(size_t)ia * d + col] : 0.0;
-        pb[r][q] = (ja < d && col < d) ? A[(size_t)ja * d + col] : 0.0;
+        pa[r][q] = (ia < d && col < d) ? __ldcg(&A[(size_t)ia * d + col]) : 0.0;
+        pb[r][q] = (ja < d && col < d) ? __ldcg(&A[(size_t)ja * d + col]) : 0.0;
     }
     __syncthreads();
     const int tx = threadIdx.x % NB, ty = threadIdx.x / NB;  // ty 0..7
@@ -489,7 +487,46 @@ __global__ void __launch_bounds__(256) k_syrk_update(int d, int kb, double *H, c
         double s = 0.0;
 #pragma unroll
         for (int q = 0; q < NB; ++q) s += pa[r][q] * pb[tx][q];
-        A[(size_t)i * d + j] -= s;
+        A[(size_t)i * d + j] = __ldcg(&A[(size_t)i * d + j]) - s;
+    }
+    __syncthreads();  // the shared blocks are free for the next item
+}
+
+// Whether candidate c is factored here: live, not failed, and not one-hot (a one-hot
+// candidate's factor is L_k, copied in place by k_hessian). info[c] is read after a
+// grid barrier, so every CTA sees the same value.
+__device__ __forceinline__ bool chol_live(int c, const int32_t *onehot, const int32_t *info) {
+    return !(onehot && onehot[c] >= 0) && *reinterpret_cast<const volatile int32_t *>(&info[c]) == 0;
+}
+
+__global__ void __launch_bounds__(CF_THREADS) k_chol_coop(int d, double *H, const int32_t *n_c,
+                                                         const int32_t *onehot, int32_t *info, uint32_t *bar,
+                                                         int32_t *err) {
+    // the candidate count is the same value in every CTA, so all CTAs reach every barrier
+    const int nc = *n_c;
+    const int nblk = (d + NB - 1) / NB;
+    for (int kb = 0; kb < nblk; ++kb) {
+        for (int c = blockIdx.x; c < nc; c += gridDim.x)
+            if (chol_live(c, onehot, info)) potrf_block(d, kb, H + (size_t)c * d * d, info + c);
+        if (!grid_barrier(bar, gridDim.x, err)) return;
+        const int rest = nblk - kb - 1;
+        if (rest == 0) break;
+        for (int it = blockIdx.x; it < nc * rest; it += gridDim.x) {
+            const int c = it / rest;
+            if (chol_live(c, onehot, info)) trsm_block(d, kb, kb + 1 + it % rest, H + (size_t)c * d * d);
+        }
+        if (!grid_barrier(bar, gridDim.x, err)) return;
+        const int tri = rest * (rest + 1) / 2;  // trailing blocks (ii >= jj) per candidate
+        for (int it = blockIdx.x; it < nc * tri; it += gridDim.x) {
+            const int c = it / tri, e = it - c * tri;
+            if (!chol_live(c, onehot, info)) continue;
+            int ii = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+            while (ii * (ii + 1) / 2 > e) --ii;
+            while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+            const int jj = e - ii * (ii + 1) / 2;
+            syrk_block(d, kb, kb + 1 + ii, kb + 1 + jj, H + (size_t)c * d * d);
+        }
+        if (!grid_barrier(bar, gridDim.x, err)) return;
     }
 }
 
@@ -916,29 +953,29 @@ __global__ void k_chol_needed(cudaGraphConditionalHandle h, const int32_t *n_c, 
     if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
+int laplace_sms();
+
 void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P, const double *Z, const double *R,
                          const double *gbar, const int32_t *n_c, double *GK, double *H, int32_t *info,
-                         cudaStream_t s, const int32_t *onehot) {
+                         uint32_t *bar, int32_t *err, cudaStream_t s, const int32_t *onehot) {
     note_launch();
     k_comp_grads<<<dim3(cap, K, kGradSlices), 256, sizeof(double) * d, s>>>(d, K, L, Z, R, n_c, GK);
     const int64_t dd = (int64_t)d * d;
     note_launch();
     k_hessian<<<dim3((unsigned)((dd + 255) / 256), cap), 256, 0, s>>>(d, K, P, GK, R, gbar, n_c, onehot, L, H,
                                                                         info);
-    const int nblk = (d + NB - 1) / NB;
     auto factor = [&](cudaStream_t fs) {
         ProfScope prof(PROF_CHOLESKY, fs);
-        for (int kb = 0; kb < nblk; ++kb) {
-            note_launch();
-            k_potrf_diag<<<cap, DIAG_THREADS, 0, fs>>>(d, kb, H, n_c, onehot, info);
-            const int rest = nblk - kb - 1;
-            if (rest > 0) {
-                note_launch();
-                k_trsm_panel<<<dim3(rest, cap), TRSM_THREADS, 0, fs>>>(d, kb, H, n_c, onehot, info);
-                note_launch();
-                k_syrk_update<<<dim3(rest, rest, cap), 256, 0, fs>>>(d, kb, H, n_c, onehot, info);
-            }
-        }
+        // one CTA per SM (a cooperative grid must be co-resident), no more than the
+        // largest phase's items
+        const int nblk = (d + NB - 1) / NB;
+        const long long items = (long long)cap * (nblk - 1) * nblk / 2;
+        int G = laplace_sms();
+        if (items < G) G = (int)(items > 0 ? items : 1);
+        cudaMemsetAsync(bar, 0, 2 * sizeof(uint32_t), fs);
+        void *args[] = {&d, &H, &n_c, &onehot, &info, &bar, &err};
+        note_launch();
+        cudaLaunchCooperativeKernel((const void *)k_chol_coop, dim3(G), dim3(CF_THREADS), args, 0, fs);
     };
     // in a graph, the factorisation is the body of an IF node that runs only when some
     // live candidate is not one-hot (its launches would otherwise all be idle CTAs)
@@ -953,6 +990,19 @@ void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P
         if (st == SB_OK) return;
         // the node could not be added: factor unconditionally (a capture left broken by
         // the failure reports it when it ends)
+    } else if (onehot && !stream_capturing(s)) {
+        // eager mode (host reads allowed): the same decision on the host, so that an
+        // all-one-hot candidate set launches no idle factorisation kernels either
+        int32_t nc = 0;
+        std::vector<int32_t> oh((size_t)cap);
+        if (cudaMemcpyAsync(&nc, n_c, sizeof(int32_t), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+            cudaMemcpyAsync(oh.data(), onehot, sizeof(int32_t) * (size_t)cap, cudaMemcpyDeviceToHost, s) ==
+                cudaSuccess &&
+            cudaStreamSynchronize(s) == cudaSuccess) {
+            bool any = false;
+            for (int c = 0; c < nc && c < cap; ++c) any = any || oh[(size_t)c] < 0;
+            if (!any) return;
+        }
     }
     factor(s);
 }

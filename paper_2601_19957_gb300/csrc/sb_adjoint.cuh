@@ -12,6 +12,7 @@ constexpr int kMaxAdjModes = 1024;
 struct AdjWs {
     double *P, *H, *M, *Z, *R, *qpart, *gbar, *ell, *GK, *V, *T, *cvec, *eps, *gam, *u, *trWP, *pi;
     int32_t *info, *one;
+    uint32_t *bar;  // grid-barrier state of the cooperative factorisation
 };
 
 void adjoint_carve(Carver &cv, AdjWs &w, int d, int K);

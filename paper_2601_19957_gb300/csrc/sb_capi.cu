@@ -542,7 +542,8 @@ sb_status run_laplace(const ProbView &pv, const sb_config *c, const Layout &L, c
         f64_points(pv, la.XC, nullptr, nc, cap, la.qpart, la.Z, la.R, la.LC, la.GC, s);
         launch_onehot(K, la.R, nc, cap, la.onehot, s);
         launch_precision_needed(d, K, pv.L, la.R, nc, la.p_done, la.p_need, la.P, s, la.onehot);
-        launch_hessian_chol(d, K, cap, pv.L, la.P, la.Z, la.R, la.GC, nc, la.GK, la.H, la.info, s, la.onehot);
+        launch_hessian_chol(d, K, cap, pv.L, la.P, la.Z, la.R, la.GC, nc, la.GK, la.H, la.info, la.dd_bar, pv.status, s,
+                            la.onehot);
     };
     eval_full(la.n_reps);
     // Newton polish, newton_steps steps; a step's evaluations run on n_eff candidates,

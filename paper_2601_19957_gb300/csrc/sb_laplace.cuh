@@ -30,9 +30,11 @@ void launch_precision_needed(int d, int K, const double *L, const double *R, con
                              int32_t *need, double *P, cudaStream_t s, const int32_t *onehot = nullptr);
 // H and its lower Cholesky factor in place for every live candidate; with onehot,
 // the one-hot candidates take L_k as their factor (no assembly, no factorisation).
+// The factorisation is one cooperative launch (bar: 2 words of grid-barrier state; a
+// barrier wait that runs out records SB_DEV_TIMEOUT in *err).
 void launch_hessian_chol(int d, int K, int cap, const double *L, const double *P, const double *Z, const double *R,
                          const double *gbar, const int32_t *n_c, double *GK, double *H, int32_t *info,
-                         cudaStream_t s, const int32_t *onehot = nullptr);
+                         uint32_t *bar, int32_t *err, cudaStream_t s, const int32_t *onehot = nullptr);
 // Newton step (C C^T) delta = g and g^T delta / 2 for the live candidates, over
 // co-resident CTAs (cooperative launch, one bounded grid barrier per 32-row block
 // and direction; at most one per SM and 16 per candidate of the cap, divided among
