@@ -26,7 +26,11 @@
 // tr(W P_k) = <W L_k, L_k>_F. Components with r_k == 0 contribute exactly zero
 // and are skipped. H is recomputed at every mode (not stored by the forward),
 // factored H = C C^T, and W is applied through triangular solves: W B =
-// C^-T (C^-1 B) for the d right-hand sides of L_k and for vectors.
+// C^-T (C^-1 B) for the d right-hand sides of L_k and for vectors. At a one-hot
+// mode (r_k = 1, the other r exactly 0) H = P_k and C = L_k, so W L_k = L_k^-T:
+// tr(W P_k) = d and lower[W L_k] = diag(1 / L_ii), with no d x d solve. Products
+// with P_k are formed as L_k (L_k^T v); P_k itself is built only for the Hessian
+// of a mode that is not one-hot.
 #include "sb_adjoint.cuh"
 
 namespace sb {
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(256) k_trace_WP(int d, const double *M, const 
 // or with Wt known form c, eps, gam (stage 1). Vectors of length d in global scratch.
 __global__ void __launch_bounds__(256) k_adj_stage(int stage, int d, int K, const double *R, const double *GK,
                                                    const double *gbar, const double *WV, const double *trWP,
-                                                   const double *P, const double *Wt, double *t_out, double *eps,
+                                                   const double *PY, const double *Wt, double *t_out, double *eps,
                                                    double *gam, double *cvec) {
     __shared__ double sh[8];
     __shared__ double s_beta[kMaxK];
@@ -235,11 +239,8 @@ __global__ void __launch_bounds__(256) k_adj_stage(int stage, int d, int K, cons
                 if (r == 0.0) continue;
                 const double e1 = r * (s_beta[k] - sb);
                 ti += e1 * GK[(size_t)k * d + i];
-                // (P_k gam'_k)_i = 2 r sum_j P_k[i][j] (W gbar - W g_k)_j
-                const double *Pk = P + (size_t)k * d * d + (size_t)i * d;
-                double pg = 0.0;
-                for (int j = 0; j < d; ++j) pg += Pk[j] * (WV[(size_t)j * nv + K] - WV[(size_t)j * nv + k]);
-                ti -= 2.0 * r * pg;
+                // (P_k gam'_k)_i = 2 r (P_k (W gbar - W g_k))_i, formed apart (PY)
+                ti -= 2.0 * r * PY[(size_t)k * d + i];
             }
             t_out[i] = ti;
         }
@@ -256,18 +257,29 @@ __global__ void __launch_bounds__(256) k_adj_stage(int stage, int d, int K, cons
     }
 }
 
-// dmu_k += pi (-eps_k g_k + P_k gam_k): one CTA per component, thread per row.
-__global__ void __launch_bounds__(256) k_adj_dmu(int d, int K, double pi, const double *R, const double *eps,
-                                                 const double *GK, const double *P, const double *gam, double *dmu) {
-    const int k = blockIdx.y;
-    if (R[k] == 0.0) return;
+// dmu_k += pi (-eps_k g_k + P_k gam_k) for one component, P_k gam_k given (y).
+__global__ void __launch_bounds__(256) k_adj_dmu(int d, int k, double pi, const double *eps, const double *GK,
+                                                 const double *y, double *dmu) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d) return;
-    const double *Pk = P + (size_t)k * d * d + (size_t)i * d;
-    const double *gk = gam + (size_t)k * d;
+    dmu[(size_t)k * d + i] += pi * (-eps[k] * GK[(size_t)k * d + i] + y[i]);
+}
+
+// v = W gbar - W g_k (columns K and k of WV [d][K + 1]).
+__global__ void __launch_bounds__(256) k_adj_wdiff(int d, int K, int k, const double *WV, double *v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < d) v[i] = WV[(size_t)i * (K + 1) + K] - WV[(size_t)i * (K + 1) + k];
+}
+
+// y = L_k u (lower triangular), a warp per row: y_i = sum_{j <= i} L[i][j] u_j.
+__global__ void __launch_bounds__(256) k_adj_Lu(int d, const double *Lk, const double *u, double *y) {
+    const int lane = threadIdx.x & 31;
+    const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (i >= d) return;
     double s = 0.0;
-    for (int j = 0; j < d; ++j) s += Pk[j] * gk[j];
-    dmu[(size_t)k * d + i] += pi * (-eps[k] * GK[(size_t)k * d + i] + s);
+    for (int j = lane; j <= i; j += 32) s += Lk[(size_t)i * d + j] * u[j];
+    s = warp_sum(s);
+    if (lane == 0) y[i] = s;
 }
 
 // L^T gam for component k (u[j] = sum_i L[i][j] gam[i]).
@@ -280,6 +292,8 @@ __global__ void __launch_bounds__(256) k_adj_Ltg(int d, const double *Lk, const 
 }
 
 // dL_k += pi lower[ eps (diag(1/L) - delta z^T) - gam z^T - delta u^T - r M ],  M = W L_k, u = L^T gam.
+// M null: the one-hot case W = (L_k L_k^T)^-1, where W L_k = L_k^-T, whose lower
+// triangle is diag(1 / L_ii).
 __global__ void __launch_bounds__(256) k_adj_dL(int d, double pi, double r, double eps, const double *Lk,
                                                 const double *x, const double *mu, const double *z, const double *gam,
                                                 const double *u, const double *M, double *dL) {
@@ -288,10 +302,15 @@ __global__ void __launch_bounds__(256) k_adj_dL(int d, double pi, double r, doub
         const int i = (int)(e / d), j = (int)(e % d);
         if (j > i) continue;
         const double di = x[i] - mu[i];
-        double v = -eps * di * z[j] - gam[i] * z[j] - di * u[j] - r * M[e];
+        const double wl = M ? M[e] : (i == j ? 1.0 / Lk[e] : 0.0);
+        double v = -eps * di * z[j] - gam[i] * z[j] - di * u[j] - r * wl;
         if (i == j) v += eps / Lk[e];
         dL[e] += pi * v;
     }
+}
+
+__global__ void k_set_f64(double *p, double v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
 }
 
 __global__ void k_softmax_pi(int n, const double *logZk, double g, double *pi) {
@@ -323,9 +342,12 @@ void adjoint_carve(Carver &cv, AdjWs &w, int d, int K) {
     w.gam = cv.take<double>((size_t)K * d);
     w.u = cv.take<double>(d);
     w.trWP = cv.take<double>(K);
+    w.PY = cv.take<double>((size_t)K * d);
+    w.y = cv.take<double>(d);
     w.pi = cv.take<double>(kMaxAdjModes);
     w.info = cv.take<int32_t>(1);
     w.one = cv.take<int32_t>(1);
+    w.onehot = cv.take<int32_t>(1);
     w.bar = cv.take<uint32_t>(2);
 }
 
@@ -339,7 +361,9 @@ sb_status adjoint_run(const ProbView &pv, const AdjWs &w, const double *modes, c
     SB_CUDA_TRY(cudaMemcpyAsync(w.one, &one, sizeof(int32_t), cudaMemcpyHostToDevice, s));
     note_launch();
     k_softmax_pi<<<1, 32, 0, s>>>(n_modes, logZk, grad_logZ, w.pi);
-    launch_precision(d, K, pv.L, w.P, s);
+    // P_k = L_k L_k^T is formed only for the Hessian at a mode that is not one-hot;
+    // every product with P_k below is L_k (L_k^T v)
+    bool p_ready = false;
     std::vector<double> pis(n_modes), Rh(K), epsh(K);
     SB_CUDA_TRY(cudaMemcpyAsync(pis.data(), w.pi, sizeof(double) * n_modes, cudaMemcpyDeviceToHost, s));
     SB_CUDA_TRY(cudaStreamSynchronize(s));
@@ -363,16 +387,38 @@ sb_status adjoint_run(const ProbView &pv, const AdjWs &w, const double *modes, c
         la.grad_sign = -1.0;
         la.out_by_walker = 0;
         launch_lik_f64_few(la, true, s);
-        launch_hessian_chol(d, K, 1, pv.L, w.P, w.Z, w.R, w.gbar, w.one, w.GK, w.H, w.info, w.bar, pv.status, s);
+        SB_CUDA_TRY(cudaMemcpyAsync(Rh.data(), w.R, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+        SB_CUDA_TRY(cudaStreamSynchronize(s));
+        // at a one-hot mode (r_k = 1, every other r exactly 0) H = P_k, whose factor is
+        // L_k: copied, not assembled and factored (as in the Laplace stage)
+        int oh = -1, nz = 0;
+        for (int k = 0; k < K; ++k)
+            if (Rh[k] != 0.0) {
+                ++nz;
+                oh = Rh[k] == 1.0 ? k : -2;
+            }
+        if (nz != 1 || oh < 0) oh = -1;
+        if (oh < 0 && !p_ready) {
+            launch_precision(d, K, pv.L, w.P, s);
+            p_ready = true;
+        }
+        launch_onehot(K, w.R, w.one, 1, w.onehot, s);
+        launch_hessian_chol(d, K, 1, pv.L, w.P, w.Z, w.R, w.gbar, w.one, w.GK, w.H, w.info, w.bar, pv.status, s,
+                            w.onehot);
         // W [g_0 .. g_{K-1}, gbar]
         note_launch();
         k_pack_rhs<<<(d * (K + 1) + 255) / 256, 256, 0, s>>>(d, K, w.GK, w.gbar, w.R, w.V);
         apply_W(d, K + 1, w.H, w.V, s);
-        SB_CUDA_TRY(cudaMemcpyAsync(Rh.data(), w.R, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
-        SB_CUDA_TRY(cudaStreamSynchronize(s));
-        // W L_k and tr(W P_k) = <W L_k, L_k>_F for the components with r_k > 0
+        // W L_k and tr(W P_k) = <W L_k, L_k>_F for the components with r_k > 0. At a
+        // one-hot mode the factor is L_k, so W L_k = L_k^-T and tr(W P_k) = d exactly:
+        // no d x d solve
         for (int k = 0; k < K; ++k) {
             if (Rh[k] == 0.0) continue;
+            if (k == oh) {
+                note_launch();
+                k_set_f64<<<1, 32, 0, s>>>(w.trWP + k, (double)d);
+                continue;
+            }
             double *Mk = w.M + (size_t)k * d * d;
             note_launch();
             k_copy_lower<<<1184, 256, 0, s>>>(d, pv.L + (size_t)k * d * d, Mk);
@@ -380,28 +426,42 @@ sb_status adjoint_run(const ProbView &pv, const AdjWs &w, const double *modes, c
             note_launch();
             k_trace_WP<<<1, 256, 0, s>>>(d, Mk, pv.L + (size_t)k * d * d, w.trWP + k);
         }
+        // P_k (W gbar - W g_k) for the components with r_k > 0
+        for (int k = 0; k < K; ++k) {
+            if (Rh[k] == 0.0) continue;
+            const double *Lk = pv.L + (size_t)k * d * d;
+            note_launch();
+            k_adj_wdiff<<<(d + 255) / 256, 256, 0, s>>>(d, K, k, w.V, w.y);
+            note_launch();
+            k_adj_Ltg<<<(d + 255) / 256, 256, 0, s>>>(d, Lk, w.y, w.u);
+            note_launch();
+            k_adj_Lu<<<(d * 32 + 255) / 256, 256, 0, s>>>(d, Lk, w.u, w.PY + (size_t)k * d);
+        }
         // t = grad_x log det H, then v = W t (in place)
         note_launch();
-        k_adj_stage<<<1, 256, 0, s>>>(0, d, K, w.R, w.GK, w.gbar, w.V, w.trWP, w.P, nullptr, w.T, nullptr, nullptr,
+        k_adj_stage<<<1, 256, 0, s>>>(0, d, K, w.R, w.GK, w.gbar, w.V, w.trWP, w.PY, nullptr, w.T, nullptr, nullptr,
                                       nullptr);
         apply_W(d, 1, w.H, w.T, s);
         // c, eps_k, gam_k
         note_launch();
-        k_adj_stage<<<1, 256, 0, s>>>(1, d, K, w.R, w.GK, w.gbar, w.V, w.trWP, w.P, w.T, nullptr, w.eps, w.gam,
+        k_adj_stage<<<1, 256, 0, s>>>(1, d, K, w.R, w.GK, w.gbar, w.V, w.trWP, w.PY, w.T, nullptr, w.eps, w.gam,
                                       w.cvec);
-        note_launch();
-        k_adj_dmu<<<dim3((d + 255) / 256, K), 256, 0, s>>>(d, K, pis[mo], w.R, w.eps, w.GK, w.P, w.gam, dmu);
         SB_CUDA_TRY(cudaMemcpyAsync(epsh.data(), w.eps, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
         SB_CUDA_TRY(cudaStreamSynchronize(s));
         for (int k = 0; k < K; ++k) {
             if (Rh[k] == 0.0) continue;
             const double *Lk = pv.L + (size_t)k * d * d;
+            // u = L_k^T gam_k, then P_k gam_k = L_k u for dmu_k
             note_launch();
             k_adj_Ltg<<<(d + 255) / 256, 256, 0, s>>>(d, Lk, w.gam + (size_t)k * d, w.u);
             note_launch();
+            k_adj_Lu<<<(d * 32 + 255) / 256, 256, 0, s>>>(d, Lk, w.u, w.y);
+            note_launch();
+            k_adj_dmu<<<(d + 255) / 256, 256, 0, s>>>(d, k, pis[mo], w.eps, w.GK, w.y, dmu);
+            note_launch();
             k_adj_dL<<<1184, 256, 0, s>>>(d, pis[mo], Rh[k], epsh[k], Lk, x, pv.mu + (size_t)k * d,
-                                          w.Z + (size_t)k * d, w.gam + (size_t)k * d, w.u, w.M + (size_t)k * d * d,
-                                          dL + (size_t)k * d * d);
+                                          w.Z + (size_t)k * d, w.gam + (size_t)k * d, w.u,
+                                          k == oh ? nullptr : w.M + (size_t)k * d * d, dL + (size_t)k * d * d);
         }
     }
     SB_CUDA_TRY(cudaGetLastError());

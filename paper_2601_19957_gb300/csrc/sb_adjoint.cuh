@@ -11,7 +11,8 @@ constexpr int kMaxAdjModes = 1024;
 
 struct AdjWs {
     double *P, *H, *M, *Z, *R, *qpart, *gbar, *ell, *GK, *V, *T, *cvec, *eps, *gam, *u, *trWP, *pi;
-    int32_t *info, *one;
+    double *PY, *y;  // P_k (W gbar - W g_k) per component [K][d]; a d-vector
+    int32_t *info, *one, *onehot;
     uint32_t *bar;  // grid-barrier state of the cooperative factorisation
 };
 
