@@ -606,6 +606,7 @@ def run_next_rows(sb, args):
     U = torch.randn((16384, d), generator=g, dtype=torch.float64)
     U = (U / U.norm(dim=1, keepdim=True)).cuda()
     ms_rq = timed(lambda: sb.ray_loglik_quad(pb, U, 64, form=1))
+    ms_rq2 = timed(lambda: sb.ray_loglik_quad(pb, U, 64, form=2))
     small, _ = workload_cfg(1, "fp64")
     ps = sb.Problem(small)
     x = torch.as_tensor(small.mu[0] + 0.1, device="cuda")
@@ -620,6 +621,9 @@ def run_next_rows(sb, args):
                                    "fp64_TFLOPs": 2 * n_rays * K * d * (d + 1) / (ms_seg * 1e-3) / 1e12},
                       "ray_loglik_quad_f32": {"workload": f"d={d} K={K}, 16384 rays x 64 steps", "ms": ms_rq,
                                               "fp32_TFLOPs": 16384 * K * d * (d + 1) / (ms_rq * 1e-3) / 1e12},
+                      "ray_loglik_quad_bf16_split": {"workload": f"d={d} K={K}, 16384 rays x 64 steps", "ms": ms_rq2,
+                                                     "tensor_TFLOPs_3_products":
+                                                         3 * 16384 * K * d * (d + 1) / (ms_rq2 * 1e-3) / 1e12},
                       "fd_full_hessian": {"workload": f"d={ds} K={Ks}, {pts} points", "ms": ms_fd,
                                           "l_evals_per_s": pts / (ms_fd * 1e-3)}}))
     return 0

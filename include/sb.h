@@ -446,7 +446,8 @@ sb_status sb_evidence_chisao_host(const sb_problem *host_prob, const sb_config *
 sb_status sb_chisao_stats(const sb_problem *prob, const sb_config *cfg, void *ws, size_t ws_bytes, int64_t *out,
                           void *stream);
 
-/* Bytes of device scratch sb_ray_loglik_quad needs (form 0 FP64, 1 FP32). */
+/* Bytes of device scratch sb_ray_loglik_quad needs (form 0 FP64, 1 FP32, 2 BF16 and
+ * 3 TF32 tensor-core split products); 0 for an invalid form or problem. */
 size_t sb_ray_loglik_quad_workspace_bytes(const sb_problem *prob, int32_t form, int32_t n_rays);
 
 /*
@@ -455,9 +456,13 @@ size_t sb_ray_loglik_quad_workspace_bytes(const sb_problem *prob, int32_t form, 
  * t_exit,r, z_k = z_k(c) + tau L_k^T u_r, so |z_k|^2 = q0_k + 2 tau q1_rk + tau^2 q2_rk and
  * ell[r][j] = LSE_k (a_k - |z_k|^2 / 2) needs one triangular GEMM of the directions by each
  * L_k instead of one per sample. form 0: FP64 GEMM; form 1: FP32 SIMT GEMM (u and L_k
- * rounded to FP32, FP32 accumulation), the scalars combined in FP64. u: [n_rays][d] device
- * (unit directions); ell: [n_rays][n_steps]. ws: sb_ray_loglik_quad_workspace_bytes.
- * Asynchronous. (An experimental form of the coarse pass, not used by sb_discover yet.)
+ * rounded to FP32, FP32 accumulation); forms 2 and 3: the tensor-core GEMM sb_discover
+ * runs at BF16 / TF32 (u and L_k each split into a high part and the rounded remainder,
+ * w = u_hi L_hi + u_lo L_hi + u_hi L_lo with FP32 accumulation, about FP32 accuracy).
+ * The scalars are combined in FP64 in every form. u: [n_rays][d] device (unit
+ * directions); ell: [n_rays][n_steps]. ws: sb_ray_loglik_quad_workspace_bytes.
+ * Asynchronous. SB_ERR_INVALID_ARG for a form outside 0..3, n_rays < 1 or n_steps < 1;
+ * SB_ERR_UNSUPPORTED for forms 2, 3 on a device without tcgen05.
  */
 sb_status sb_ray_loglik_quad(const sb_problem *prob, int32_t form, const double *u, int32_t n_rays, int32_t n_steps,
                              double *ell, void *ws, size_t ws_bytes, void *stream);

@@ -56,51 +56,6 @@ __global__ void __launch_bounds__(256) k_ray_dirs(int d, int n_rays, uint32_t k0
     if (lane == 0) texit[r] = tmin;
 }
 
-// The same directions for the tensor-core path, in FP32 (the operands are
-// rounded to bf16 / tf32 afterwards): the same Philox counters, uniforms from
-// the top 24 bits of each 64-bit pair, Box-Muller with FP32 transcendentals.
-// Writes the FP32 copy read by the centring kernel and its FP64 widening (for
-// the start points).
-__global__ void __launch_bounds__(256) k_ray_dirs_f32(int d, int n_rays, uint32_t k0, uint32_t k1, const double *half,
-                                                      float *u32, double *u, double *texit) {
-    const int lane = threadIdx.x & 31;
-    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (r >= n_rays) return;
-    float *ur = u32 + (size_t)r * d;
-    const int npairs = (d + 1) / 2;
-    float ss = 0.f;
-    for (int p = lane; p < npairs; p += 32) {
-        uint32_t c[4] = {(uint32_t)p, (uint32_t)r, 0x52415953u, 0u};
-        philox4x32_10(c, k0, k1);
-        const float u1 = ((float)(c[0] >> 8) + 0.5f) * (1.0f / 16777216.0f);
-        const float u2 = ((float)(c[2] >> 8) + 0.5f) * (1.0f / 16777216.0f);
-        const float rad = sqrtf(-2.0f * logf(u1));
-        float sn, cs;
-        sincospif(2.0f * u2, &sn, &cs);
-        const float x0 = rad * cs;
-        ur[2 * p] = x0;
-        ss += x0 * x0;
-        if (2 * p + 1 < d) {
-            const float x1 = rad * sn;
-            ur[2 * p + 1] = x1;
-            ss += x1 * x1;
-        }
-    }
-    const float inv = 1.0f / sqrtf(warp_sum(ss));
-    __syncwarp();
-    float tmin = INFINITY;
-    double *uw = u + (size_t)r * d;
-    for (int i = lane; i < d; i += 32) {
-        const float v = ur[i] * inv;
-        ur[i] = v;
-        uw[i] = (double)v;
-        const float au = fabsf(v);
-        if (au > 0.f) tmin = fminf(tmin, (float)half[i] / au);
-    }
-    tmin = warp_min(tmin);
-    if (lane == 0) texit[r] = (double)tmin;
-}
-
 // One warp per ray: tier and rank of every sample, histogram of buckets.
 __global__ void __launch_bounds__(128) k_ray_bucket(const double *ell, int n_rays, int S, int32_t *bucket,
                                                     uint32_t *hist) {
@@ -280,15 +235,11 @@ __global__ void __launch_bounds__(256) k_gather_starts(int d, const double *c, c
 
 size_t select_blocks(int64_t total) { return (size_t)((total + SEL_BLOCK - 1) / SEL_BLOCK); }
 
-void launch_ray_dirs(int d, int n_rays, uint64_t seed, const ProbView &pv, double *u, double *texit, float *u32,
-                     cudaStream_t s) {
+void launch_ray_dirs(int d, int n_rays, uint64_t seed, const ProbView &pv, double *u, double *texit, cudaStream_t s) {
     const int warps_per_block = 8;
     const unsigned grid = (unsigned)((n_rays + warps_per_block - 1) / warps_per_block);
     note_launch();
-    if (u32)
-        k_ray_dirs_f32<<<grid, 256, 0, s>>>(d, n_rays, (uint32_t)seed, (uint32_t)(seed >> 32), pv.half, u32, u, texit);
-    else
-        k_ray_dirs<<<grid, 256, 0, s>>>(d, n_rays, (uint32_t)seed, (uint32_t)(seed >> 32), pv.half, u, texit);
+    k_ray_dirs<<<grid, 256, 0, s>>>(d, n_rays, (uint32_t)seed, (uint32_t)(seed >> 32), pv.half, u, texit);
 }
 
 void launch_select_starts(const double *ell_all, int n_rays, int n_steps, int n_starts, const SelectWs &w,

@@ -207,6 +207,11 @@ size_t rayq_scratch_elems(int n_rays, int d, int K, int form) {
     return e;
 }
 
+void launch_ray_texit(const ProbView &pv, const double *u, int n_rays, double *texit, cudaStream_t s) {
+    note_launch();
+    k_rq_texit<<<(unsigned)(((int64_t)n_rays * 32 + 255) / 256), 256, 0, s>>>(n_rays, pv.d, u, pv.half, texit);
+}
+
 void launch_ray_loglik_quad(const ProbView &pv, int form, const double *u, int n_rays, int n_steps, double *scratch,
                             double *ell, cudaStream_t s) {
     const int d = pv.d, K = pv.K;

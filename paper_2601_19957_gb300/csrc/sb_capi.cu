@@ -156,10 +156,10 @@ struct SetupWs {
 
 struct DiscoverWs {
     double *u, *texit, *ell_all, *qpart;
-    float *u32;  // FP32 copy of the directions (tensor-core path)
     int chunk;
     SelectWs sel;
-    TcWs tc;  // tensor-core scratch (mixed precision)
+    TcWs tc;        // tensor-core scratch (mixed precision)
+    TcQuadWs quad;  // the rays' quadratic form (mixed precision)
 };
 
 template <typename T>
@@ -263,7 +263,7 @@ Layout layout(void *base, const sb_problem *p, const sb_config *c) {
         L.di.qpart = cv.take<double>(lik_f64_qpart_elems(d, K, L.di.chunk));
     else {
         carve_tc(cv, L.di.tc, tc_ray_chunk(d, K, total), d, K, c->prec);
-        L.di.u32 = cv.take<float>((size_t)c->n_rays * d);
+        carve_tc_quad(cv, L.di.quad, c->n_rays, d, K, c->prec);
     }
     L.di.sel.bucket = cv.take<int32_t>(total);
     L.di.sel.hist = cv.take<uint32_t>(c->n_steps * 2 > 256 ? c->n_steps * 2 : 256);
@@ -366,7 +366,7 @@ sb_status run_discover(const ProbView &pv, const sb_config *c, const Layout &L, 
                        cudaStream_t s) {
     const int d = pv.d;
     const int64_t total = (int64_t)c->n_rays * c->n_steps;
-    launch_ray_dirs(d, c->n_rays, c->seed, pv, L.di.u, L.di.texit, c->prec == SB_PREC_FP64 ? nullptr : L.di.u32, s);
+    launch_ray_dirs(d, c->n_rays, c->seed, pv, L.di.u, L.di.texit, s);
     if (c->prec == SB_PREC_FP64) {
         for (int64_t f0 = 0; f0 < total; f0 += L.di.chunk) {
             const int rows = (int)((total - f0) < L.di.chunk ? (total - f0) : L.di.chunk);
@@ -382,7 +382,9 @@ sb_status run_discover(const ProbView &pv, const sb_config *c, const Layout &L, 
             launch_lik_f64_rays(a, s);
         }
     } else {
-        const sb_status st = tc_ray_loglik(pv, c, L.di.tc, L.di.u32, L.di.texit, L.di.ell_all, s);
+        // one GEMM of the directions, l at the samples from three scalars per (ray, component)
+        const sb_status st = tc_ray_loglik_quad(pv, c->n_rays, c->n_steps, c->prec, L.di.tc.bn, L.di.quad, L.di.u,
+                                                L.di.texit, L.di.ell_all, s);
         if (st != SB_OK) return st;
     }
     launch_select_starts(L.di.ell_all, c->n_rays, c->n_steps, c->n_starts, L.di.sel, s);
@@ -1654,7 +1656,8 @@ namespace {
 
 struct RayqWs {
     SetupWs su;
-    double *scratch;
+    double *scratch;  // forms 0, 1: the FP64 / FP32 forms' scratch; forms 2, 3: t_exit
+    TcQuadWs quad;    // forms 2, 3 (tensor-core GEMM of the split directions)
     size_t bytes;
 };
 
@@ -1662,7 +1665,12 @@ RayqWs rayq_layout(void *base, const sb_problem *p, int n_rays, int form) {
     RayqWs w{};
     Carver cv(base);
     carve_setup(cv, p, w.su);
-    w.scratch = cv.take<double>(rayq_scratch_elems(n_rays, p->d, p->K, form));
+    if (form <= 1)
+        w.scratch = cv.take<double>(rayq_scratch_elems(n_rays, p->d, p->K, form));
+    else {
+        w.scratch = cv.take<double>(n_rays);
+        carve_tc_quad(cv, w.quad, n_rays, p->d, p->K, form == 2 ? SB_PREC_BF16 : SB_PREC_TF32);
+    }
     w.bytes = cv.bytes();
     return w;
 }
@@ -1670,7 +1678,7 @@ RayqWs rayq_layout(void *base, const sb_problem *p, int n_rays, int form) {
 }  // namespace
 
 extern "C" size_t sb_ray_loglik_quad_workspace_bytes(const sb_problem *p, int32_t form, int32_t n_rays) {
-    if (check_problem(p) != SB_OK || (form != 0 && form != 1) || n_rays < 1 || n_rays > (1 << 24)) return 0;
+    if (check_problem(p) != SB_OK || form < 0 || form > 3 || n_rays < 1 || n_rays > (1 << 24)) return 0;
     return rayq_layout(nullptr, p, n_rays, form).bytes;
 }
 
@@ -1678,7 +1686,7 @@ extern "C" sb_status sb_ray_loglik_quad(const sb_problem *p, int32_t form, const
                                         int32_t n_steps, double *ell, void *ws, size_t ws_bytes, void *stream) {
     sb_status st = check_problem(p);
     if (st != SB_OK) return st;
-    if ((form != 0 && form != 1) || !u || !ell || !ws) return SB_ERR_INVALID_ARG;
+    if (form < 0 || form > 3 || !u || !ell || !ws) return SB_ERR_INVALID_ARG;
     if (n_rays < 1 || n_rays > (1 << 24) || n_steps < 1 || (int64_t)n_rays * n_steps > 0x7fffffffLL)
         return SB_ERR_INVALID_ARG;
     const RayqWs w = rayq_layout(ws, p, n_rays, form);
@@ -1686,7 +1694,15 @@ extern "C" sb_status sb_ray_loglik_quad(const sb_problem *p, int32_t form, const
     const cudaStream_t cs = static_cast<cudaStream_t>(stream);
     ProbView pv;
     SB_CUDA_TRY(setup_only(p, w.su, cs, pv));
-    launch_ray_loglik_quad(pv, form, u, n_rays, n_steps, w.scratch, ell, cs);
+    if (form <= 1)
+        launch_ray_loglik_quad(pv, form, u, n_rays, n_steps, w.scratch, ell, cs);
+    else {
+        const int prec = form == 2 ? SB_PREC_BF16 : SB_PREC_TF32;
+        if (!tc_available(prec)) return SB_ERR_UNSUPPORTED;
+        launch_ray_texit(pv, u, n_rays, w.scratch, cs);
+        st = tc_ray_loglik_quad(pv, n_rays, n_steps, prec, 0, w.quad, u, w.scratch, ell, cs);
+        if (st != SB_OK) return st;
+    }
     SB_CUDA_TRY(cudaGetLastError());
     return SB_OK;
 }

@@ -204,10 +204,8 @@ void launch_lik_f64_z(const LikF64Args &a, cudaStream_t s);
 void launch_lik_f64_few(const LikF64Args &a, bool want_grad, cudaStream_t s);
 
 // rays.cu
-// FP64 directions (u32 == nullptr), or FP32 ones for the tensor-core path written
-// to u32 and widened into u.
-void launch_ray_dirs(int d, int n_rays, uint64_t seed, const ProbView &pv, double *u, double *texit, float *u32,
-                     cudaStream_t s);
+// FP64 unit directions u [n_rays][d] and their exit lengths from the box centre.
+void launch_ray_dirs(int d, int n_rays, uint64_t seed, const ProbView &pv, double *u, double *texit, cudaStream_t s);
 struct SelectWs {
     int32_t *bucket;     // [total]
     uint32_t *hist;      // [max(2*S, 256)]

@@ -31,10 +31,6 @@ int tc_tuned_tile(int d, int K, int prec);
 // encodes the tensor maps. skip_bounds: also the |L_k|_2 bounds the walker
 // rounds' component skip reads (one |z|^2 pass over the columns of every L_k).
 sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s, bool skip_bounds = true);
-// l at every ray sample x_rj = c + t_j t_exit,r u_r from the FP32 directions
-// u32 [n_rays][d]; chunks of the scratch row capacity.
-sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const float *u32,
-                        const double *texit, double *ell_all, cudaStream_t s);
 // l at the ray samples of flat indices [f_begin, f_end) (ray = flat / n_steps,
 // j = flat % n_steps): x = o_ray + ((j + 1) / n_steps) t_exit,ray u_ray formed in FP32
 // inside the centring pass, o32 [rays][d] the rays' origins (the box centre when
@@ -47,6 +43,27 @@ sb_status tc_ray_chunk(const ProbView &pv, const TcWs &t, const float *o32, cons
                        int n_steps, int64_t f0, int rows_max, const int32_t *n_rows_dev, double *ell, cudaStream_t s);
 // y[e] = (float) x[e], e < n.
 void tc_to_f32(const double *x, float *y, size_t n, cudaStream_t s);
+
+// The sunburst rays from the box centre c as a quadratic form (Sec. 3.5.1-3.5.2):
+// along ray r, z_k(c + tau u_r) = z_k(c) + tau w_rk with w_rk = L_k^T u_r, so l at
+// every sample of the ray follows from q0_k = |z_k(c)|^2, q1_rk = z_k(c) . w_rk and
+// q2_rk = |w_rk|^2, tau = ((j + 1) / n_steps) t_exit,r. z_k(c) is FP64; w comes from
+// one tensor-core GEMM of the n_rays directions (not of n_rays n_steps samples) whose
+// operands are split into high and low parts, u_hi L_hi + u_lo L_hi + u_hi L_lo, close
+// to FP32 accuracy: near a mode the three terms cancel (|z_k(c)|^2 ~ 1e6 at d = 1024).
+struct TcQuadWs {
+    void *A2, *B2;                   // [rows][2 dK] direction splits, [K][d][2 dK] L_k^T splits
+    float *alpha, *qpart1, *qpart2;  // [K][ald] z_k(c) in FP32 (zero past d); partials [rows][K][nct]
+    double *zc, *zq, *q0;            // [K][d] z_k(c), its FP64 |z|^2 partials, [K] |z_k(c)|^2
+    int rows, dK, ald;
+    CUtensorMap mapU, mapL;
+};
+void carve_tc_quad(Carver &cv, TcQuadWs &q, int n_rays, int d, int K, int prec);
+// l at every ray sample from the FP64 directions u [n_rays][d] and t_exit; ell_all[r n_steps + j].
+// bn: the GEMM's column tile (64, 128 or 256; 0: the width tuned for (d, K, prec) in
+// this process, else the heuristic one). pv needs a_k, mu, L and c.
+sb_status tc_ray_loglik_quad(const ProbView &pv, int n_rays, int n_steps, int prec, int bn, TcQuadWs q,
+                             const double *u, const double *texit, double *ell_all, cudaStream_t s);
 // Clears the per-walker bounds of the component skip (before a refinement).
 void tc_walkers_reset(const TcWs &t, int n, cudaStream_t s);
 // Slot of TcWs.p holding the per-walker distance bound the L-BFGS step writes.

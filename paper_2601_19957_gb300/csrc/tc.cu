@@ -61,8 +61,9 @@ constexpr int ROWB = 128;  // bytes of one K chunk per row (one swizzle atom row
 constexpr int THREADS = 192;
 constexpr int kMaxGroupList = 4096;  // store-pass groups compacted in shared memory
 
-// MODE_ZW: GEMM1 storing z (walkers/points); MODE_ZR: GEMM1 values only (ray samples); MODE_G: GEMM2
-enum { MODE_ZW = 0, MODE_ZR = 1, MODE_G = 2 };
+// MODE_ZW: GEMM1 storing z (walkers/points); MODE_ZR: GEMM1 values only (ray samples); MODE_G: GEMM2;
+// MODE_Q: GEMM1 of split operands (ray directions, the quadratic form of a sunburst ray)
+enum { MODE_ZW = 0, MODE_ZR = 1, MODE_G = 2, MODE_Q = 3 };
 
 struct TcArgs {
     int d, K, ld;           // ld: row stride of X (elements)
@@ -87,6 +88,12 @@ struct TcArgs {
     float *G;               // [walkers][d] grad f
     int n_ntile;
     int32_t *err;
+    // MODE_Q: A = [u_hi | u_lo], B = [L_k^T hi | L_k^T lo], segments qseg elements apart;
+    // the epilogue also sums qalpha[k][j] w_j (partials qpart1) beside w_j^2 (qpart),
+    // qalpha rows qald >= the column tiles' span apart, zero past d
+    const float *qalpha;
+    float *qpart1;
+    int qseg, qald;
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -227,7 +234,8 @@ __device__ __forceinline__ TileInfo decode_tile(int t, int d, int K, const uint3
         ti.mb = t / (K * nct);
         ti.c_lo = (ti.nt * BN) / KC;
         ti.c_hi = (d + KC - 1) / KC;
-        ti.nchunks = ti.c_hi - ti.c_lo;
+        // MODE_Q: the triangle's chunks three times, for the products lo hi, hi lo, hi hi
+        ti.nchunks = (ti.c_hi - ti.c_lo) * (MODE == MODE_Q ? 3 : 1);
         // store pass (flags given): only the (block, component) pairs GEMM2 reads;
         // |z|^2 pass (mask given): only the pairs k_tc_need keeps (already the case
         // for a compacted schedule)
@@ -353,15 +361,29 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                         break;
                     }
                     mbar_arrive_tx(&full[stage], A_BYTES + B_BYTES);
-                    int kk, c0;
+                    int kk, c0, cA, kA;
                     if (MODE == MODE_G) {
                         kk = chunk_component(ti, q);
                         c0 = (q % ti.c_hi) * KC;
+                        cA = c0;
+                        kA = kk;
+                    } else if (MODE == MODE_Q) {
+                        // segment 0: u_lo L_hi, 1: u_hi L_lo, 2: u_hi L_hi (one A row per ray);
+                        // the small products first, so that only the last third of the
+                        // accumulation steps adds to an accumulator of full magnitude
+                        const int nc = ti.c_hi - ti.c_lo, seg = q / nc;
+                        kk = ti.k;
+                        const int cc = (ti.c_lo + q - seg * nc) * KC;
+                        cA = (seg == 0 ? a.qseg : 0) + cc;
+                        c0 = (seg == 1 ? a.qseg : 0) + cc;
+                        kA = 0;
                     } else {
                         kk = ti.k;
                         c0 = (ti.c_lo + q) * KC;
+                        cA = c0;
+                        kA = kk;
                     }
-                    tma_load_3d(sA + stage * A_BYTES, &tmapA, &full[stage], c0, ti.mb * BM, kk);
+                    tma_load_3d(sA + stage * A_BYTES, &tmapA, &full[stage], cA, ti.mb * BM, kA);
                     tma_load_3d(sB + stage * B_BYTES, &tmapB, &full[stage], c0, ti.nt * BN, kk);
                     inflight_stage[n_inflight % 8] = stage;
                     inflight_phase[n_inflight % 8] = phase;
@@ -452,7 +474,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             const float sc = scaled ? (valid ? a.R[(size_t)n * K + ti.k] : 0.f) : 1.f;
             const bool store_row = MODE == MODE_ZW && (valid || (scaled && n < a.z_rows));
             const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * BN);
-            float q2 = 0.f;
+            float q2 = 0.f, q1 = 0.f;
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 uint32_t v[32];
@@ -478,6 +500,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                     for (int e = 0; e < 32; ++e) {
                         const float z = __uint_as_float(v[e]);
                         q2 = fmaf(z, z, q2);
+                    }
+                    if (MODE == MODE_Q) {
+                        const float *al = a.qalpha + (size_t)ti.k * a.qald + col;  // zero past d
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) q1 = fmaf(al[e], __uint_as_float(v[e]), q1);
                     }
                     if (store_row && col < a.ldz) {
                         if (scaled)
@@ -515,7 +542,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                     }
                 }
             }
-            if (MODE != MODE_G && !scaled && valid) a.qpart[((size_t)n * K + ti.k) * a.n_ntile + ti.nt] = q2;
+            if (MODE != MODE_G && !scaled && valid) {
+                a.qpart[((size_t)n * K + ti.k) * a.n_ntile + ti.nt] = q2;
+                if (MODE == MODE_Q) a.qpart1[((size_t)n * K + ti.k) * a.n_ntile + ti.nt] = q1;
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
@@ -551,37 +581,42 @@ __global__ void __launch_bounds__(128) k_tc_lse(int mode, int K, int n_ntile, co
     const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = n < n_rows;
-    // components the |z|^2 pass skipped for this row block (zmask): e_k = -inf
+    // components the |z|^2 pass skipped for this row block (zmask): e_k = -inf. Each
+    // pass below recomputes e_k from the partials (the same sum in the same order, so
+    // the same value), which keeps the terms out of a local-memory array.
     const uint64_t km = zmask ? block_kmask(zmask, n / BM, K) : ~0ull;
-    double e[kMaxK];
+    auto term = [&](int k) -> double {
+        if (!((km >> k) & 1ull)) return -INFINITY;
+        const float *qp = qpart + ((size_t)n * K + k) * n_ntile;
+        double q = 0.0;
+        for (int t = 0; t < n_ntile; ++t) q += (double)qp[t];
+        return a_k[k] - 0.5 * q;
+    };
     double emax = -INFINITY;
     float s = 0.f;
     if (valid) {
-        for (int k = 0; k < K; ++k) {
-            e[k] = -INFINITY;
-            if (!((km >> k) & 1ull)) continue;
-            const float *qp = qpart + ((size_t)n * K + k) * n_ntile;
-            double q = 0.0;
-            for (int t = 0; t < n_ntile; ++t) q += (double)qp[t];
-            e[k] = a_k[k] - 0.5 * q;
-            emax = fmax(emax, e[k]);
-        }
-        for (int k = 0; k < K; ++k) s += __expf((float)(e[k] - emax));
-    }
-    if (zb && valid) {
+        for (int k = 0; k < K; ++k) emax = fmax(emax, term(k));
         // bounds for the next round's skip (k_tc_need): |z_k| of the evaluated
         // components, lowered by a 1/32 margin for the GEMM's rounding, and the
         // largest term's |z|, raised by the same margin
-        const int w = act ? act[n] : n;
+        const int w = zb ? (act ? act[n] : n) : 0;
         int jm = -1;
+        double ejm = 0.0;
         for (int k = 0; k < K; ++k) {
-            if (!((km >> k) & 1ull)) continue;
-            const double q = (a_k[k] - e[k]) * 2.0;
-            if (isfinite(e[k])) zb[(size_t)w * K + k] = __double2float_rd(sqrt(fmax(q, 0.0)) * (1.0 - 1.0 / 32));
-            if (isfinite(e[k]) && e[k] == emax && jm < 0) jm = k;
+            const double e = term(k);
+            s += __expf((float)(e - emax));
+            if (zb && isfinite(e)) {
+                zb[(size_t)w * K + k] = __double2float_rd(sqrt(fmax((a_k[k] - e) * 2.0, 0.0)) * (1.0 - 1.0 / 32));
+                if (e == emax && jm < 0) {
+                    jm = k;
+                    ejm = e;
+                }
+            }
         }
-        jst[w] = jm;
-        if (jm >= 0) zst[w] = __double2float_ru(sqrt(fmax((a_k[jm] - e[jm]) * 2.0, 0.0)) * (1.0 + 1.0 / 32));
+        if (zb) {
+            jst[w] = jm;
+            if (jm >= 0) zst[w] = __double2float_ru(sqrt(fmax((a_k[jm] - ejm) * 2.0, 0.0)) * (1.0 + 1.0 / 32));
+        }
     }
     const double l = emax + (double)__logf(s);
     if (mode == 1) {
@@ -600,7 +635,7 @@ __global__ void __launch_bounds__(128) k_tc_lse(int mode, int K, int n_ntile, co
     __syncthreads();
     uint64_t any_m = 0, one_m = 0;
     for (int k = 0; k < K; ++k) {
-        const float r = valid ? __expf((float)(e[k] - emax)) * inv : 0.f;
+        const float r = valid ? __expf((float)(term(k) - emax)) * inv : 0.f;
         if (valid) R[(size_t)n * K + k] = r;
         if (__any_sync(0xffffffffu, r > 0.f)) any_m |= 1ull << k;
         if (__all_sync(0xffffffffu, !valid || r == 1.f)) one_m |= 1ull << k;
@@ -1009,7 +1044,8 @@ void launch_gemm(const CUtensorMap &mapA, const CUtensorMap &map, const TcArgs &
     int grid = num_sms();
     if (groups < grid) grid = (int)(groups > 0 ? groups : 1);
     ProfScope prof(a.prof >= 0 ? a.prof
-                               : (MODE == MODE_ZW ? PROF_TC_Z_WALKERS : (MODE == MODE_ZR ? PROF_TC_Z_RAYS : PROF_TC_GRAD)),
+                               : (MODE == MODE_ZW ? PROF_TC_Z_WALKERS
+                                                  : ((MODE == MODE_ZR || MODE == MODE_Q) ? PROF_TC_Z_RAYS : PROF_TC_GRAD)),
                    s);
     note_launch();
     k_tc_gemm<BN, PREC, MODE><<<grid, THREADS, SM, s>>>(mapA, map, a);
@@ -1030,10 +1066,12 @@ void launch_gemm_any(int prec, int mode, int bn, const CUtensorMap &mapA, const 
     if (prec == SB_PREC_BF16) {
         if (mode == MODE_ZW) launch_gemm_bn<SB_PREC_BF16, MODE_ZW>(bn, mapA, map, a, s);
         else if (mode == MODE_ZR) launch_gemm_bn<SB_PREC_BF16, MODE_ZR>(bn, mapA, map, a, s);
+        else if (mode == MODE_Q) launch_gemm_bn<SB_PREC_BF16, MODE_Q>(bn, mapA, map, a, s);
         else launch_gemm_bn<SB_PREC_BF16, MODE_G>(bn, mapA, map, a, s);
     } else {
         if (mode == MODE_ZW) launch_gemm_bn<SB_PREC_TF32, MODE_ZW>(bn, mapA, map, a, s);
         else if (mode == MODE_ZR) launch_gemm_bn<SB_PREC_TF32, MODE_ZR>(bn, mapA, map, a, s);
+        else if (mode == MODE_Q) launch_gemm_bn<SB_PREC_TF32, MODE_Q>(bn, mapA, map, a, s);
         else launch_gemm_bn<SB_PREC_TF32, MODE_G>(bn, mapA, map, a, s);
     }
 }
@@ -1304,9 +1342,173 @@ sb_status tc_ray_chunk(const ProbView &pv, const TcWs &t, const float *o32, cons
     return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
 }
 
-sb_status tc_ray_loglik(const ProbView &pv, const sb_config *c, const TcWs &t, const float *u32,
-                        const double *texit, double *ell_all, cudaStream_t s) {
-    return tc_ray_samples(pv, t, nullptr, u32, texit, c->n_steps, 0, (int64_t)c->n_rays * c->n_steps, ell_all, s);
+
+// ------------------------------------------------------------------ quadratic form of the rays
+// x split into hi + lo of the operand precision: hi = round(x), lo = round(x - hi)
+template <int PREC>
+__device__ __forceinline__ void split_op(double x, float &hi, float &lo) {
+    if (PREC == SB_PREC_BF16) {
+        hi = __bfloat162float(__double2bfloat16(x));
+        lo = __bfloat162float(__double2bfloat16(x - (double)hi));
+    } else {
+        hi = to_tf32((float)x);
+        lo = to_tf32((float)(x - (double)hi));
+    }
+}
+template <int PREC>
+__device__ __forceinline__ void put_op(void *base, size_t e, float v) {
+    if (PREC == SB_PREC_BF16)
+        reinterpret_cast<__nv_bfloat16 *>(base)[e] = __float2bfloat16_rn(v);  // exact: v is a bf16 value
+    else
+        reinterpret_cast<float *>(base)[e] = v;
+}
+
+// A2[r][0 .. dK) = hi(u_r), A2[r][dK .. 2 dK) = lo(u_r); zeros past d and past n_rays
+template <int PREC>
+__global__ void k_q_split_rows(int n_rays, int rows, int d, int dK, const double *u, void *A2) {
+    const size_t tot = (size_t)rows * dK;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / dK), i = (int)(e % dK);
+        float hi = 0.f, lo = 0.f;
+        if (r < n_rays && i < d) split_op<PREC>(u[(size_t)r * d + i], hi, lo);
+        put_op<PREC>(A2, (size_t)r * 2 * dK + i, hi);
+        put_op<PREC>(A2, (size_t)r * 2 * dK + dK + i, lo);
+    }
+}
+
+// B2[k][j][i] = hi(L_k[i][j]), B2[k][j][dK + i] = lo(L_k[i][j]) for i >= j (L_k^T, the
+// operand of GEMM1), zeros elsewhere
+template <int PREC>
+__global__ void k_q_split_LT(int d, int K, int dK, const double *L, void *B2) {
+    const size_t tot = (size_t)K * d * dK;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / ((size_t)d * dK));
+        const size_t rem = e % ((size_t)d * dK);
+        const int j = (int)(rem / dK), i = (int)(rem % dK);
+        float hi = 0.f, lo = 0.f;
+        if (i < d && i >= j) split_op<PREC>(L[((size_t)k * d + i) * d + j], hi, lo);
+        const size_t row = ((size_t)k * d + j) * 2 * dK;
+        put_op<PREC>(B2, row + i, hi);
+        put_op<PREC>(B2, row + dK + i, lo);
+    }
+}
+
+// alpha[k][j] = (float) z_k(c)_j (zero for d <= j < ald) and q0[k] = |z_k(c)|^2 (FP64,
+// partials in a fixed order): one CTA per component
+__global__ void __launch_bounds__(256) k_q_alpha(int d, int ald, const double *zc, float *alpha, double *q0) {
+    const int k = blockIdx.x;
+    double s = 0.0;
+    for (int j = threadIdx.x; j < ald; j += blockDim.x) {
+        const double z = j < d ? zc[(size_t)k * d + j] : 0.0;
+        alpha[(size_t)k * ald + j] = (float)z;
+        s = fma(z, z, s);
+    }
+    __shared__ double part[8];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += part[q];
+        q0[k] = t;
+    }
+}
+
+// l at sample j of ray r: |z_k|^2 = q0_k + 2 tau q1_rk + tau^2 q2_rk in FP64 (q1, q2 the
+// FP64 sums of the column tiles' FP32 partials), tau = ((j + 1) / n_steps) t_exit,r;
+// the LSE as in k_tc_lse (FP64 terms, FP32 exponentials of the shifted terms)
+__global__ void __launch_bounds__(256) k_q_ell(int n_rays, int n_steps, int K, int n_ntile, const double *a_k,
+                                               const double *q0, const float *qp1, const float *qp2,
+                                               const double *texit, double *ell) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n_rays * n_steps) return;
+    const int r = (int)(e / n_steps), j = (int)(e - (int64_t)r * n_steps);
+    const double tau = ((double)(j + 1) / (double)n_steps) * texit[r];
+    auto term = [&](int k) {
+        const float *p1 = qp1 + ((size_t)r * K + k) * n_ntile;
+        const float *p2 = qp2 + ((size_t)r * K + k) * n_ntile;
+        double q1 = 0.0, q2 = 0.0;
+        for (int t = 0; t < n_ntile; ++t) {
+            q1 += (double)p1[t];
+            q2 += (double)p2[t];
+        }
+        return a_k[k] - 0.5 * (q0[k] + tau * (2.0 * q1 + tau * q2));
+    };
+    double emax = -INFINITY;
+    for (int k = 0; k < K; ++k) emax = fmax(emax, term(k));
+    float s = 0.f;
+    for (int k = 0; k < K; ++k) s += __expf((float)(term(k) - emax));
+    ell[e] = emax + (double)__logf(s);
+}
+
+void carve_tc_quad(Carver &cv, TcQuadWs &q, int n_rays, int d, int K, int prec) {
+    const int e = esz(prec), kc = 128 / e;
+    const int nct = (d + 63) / 64;  // partials sized for the narrowest tile the tuner may pick
+    q.rows = (n_rays + BM - 1) / BM * BM;
+    q.dK = (d + kc - 1) / kc * kc;  // whole 128-byte chunks per segment: no chunk straddles two
+    q.ald = (d + 255) / 256 * 256;  // the widest column tile's span
+    q.A2 = cv.take<uint8_t>((size_t)q.rows * 2 * q.dK * e);
+    q.B2 = cv.take<uint8_t>((size_t)K * d * 2 * q.dK * e);
+    q.alpha = cv.take<float>((size_t)K * q.ald);
+    q.qpart1 = cv.take<float>((size_t)q.rows * K * nct);
+    q.qpart2 = cv.take<float>((size_t)q.rows * K * nct);
+    q.zc = cv.take<double>((size_t)K * d);
+    q.zq = cv.take<double>(lik_f64_qpart_elems(d, K, 1));
+    q.q0 = cv.take<double>((size_t)K);
+}
+
+sb_status tc_ray_loglik_quad(const ProbView &pv, int n_rays, int n_steps, int prec, int bn, TcQuadWs q,
+                             const double *u, const double *texit, double *ell_all, cudaStream_t s) {
+    const int d = pv.d, K = pv.K;
+    if (bn <= 0) bn = tc_tuned_tile(d, K, prec);
+    if (bn <= 0) bn = bn_of(d);
+    const unsigned gs = 1184;
+    note_launch();
+    note_launch();
+    if (prec == SB_PREC_BF16) {
+        k_q_split_rows<SB_PREC_BF16><<<gs, 256, 0, s>>>(n_rays, q.rows, d, q.dK, u, q.A2);
+        k_q_split_LT<SB_PREC_BF16><<<gs, 256, 0, s>>>(d, K, q.dK, pv.L, q.B2);
+    } else {
+        k_q_split_rows<SB_PREC_TF32><<<gs, 256, 0, s>>>(n_rays, q.rows, d, q.dK, u, q.A2);
+        k_q_split_LT<SB_PREC_TF32><<<gs, 256, 0, s>>>(d, K, q.dK, pv.L, q.B2);
+    }
+    // z_k(c) in FP64 (one point), then its FP32 copy and |z_k(c)|^2
+    LikF64Args la{};
+    la.d = d;
+    la.K = K;
+    la.mu = pv.mu;
+    la.L = pv.L;
+    la.a = pv.a;
+    la.X = pv.c;
+    la.n_rows = 1;
+    la.Z = q.zc;
+    la.qpart = q.zq;
+    launch_lik_f64_z(la, s);
+    note_launch();
+    k_q_alpha<<<K, 256, 0, s>>>(d, q.ald, q.zc, q.alpha, q.q0);
+    if (!make_map(&q.mapU, q.A2, 2 * q.dK, q.rows, 1, 2 * q.dK, prec, BM) ||
+        !make_map(&q.mapL, q.B2, 2 * q.dK, d, K, 2 * q.dK, prec, bn))
+        return SB_ERR_CUDA;
+    TcArgs a{};
+    a.d = d;
+    a.K = K;
+    a.prof = -1;
+    a.n_ntile = (d + bn - 1) / bn;
+    a.err = pv.status;
+    a.n_rows_max = n_rays;
+    a.qpart = q.qpart2;
+    a.qpart1 = q.qpart1;
+    a.qalpha = q.alpha;
+    a.qseg = q.dK;
+    a.qald = q.ald;
+    a.zmask = nullptr;
+    a.rflag = nullptr;
+    launch_gemm_any(prec, MODE_Q, bn, q.mapU, q.mapL, a, s);
+    const int64_t ns = (int64_t)n_rays * n_steps;
+    note_launch();
+    k_q_ell<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(n_rays, n_steps, K, a.n_ntile, pv.a, q.q0, q.qpart1,
+                                                         q.qpart2, texit, ell_all);
+    return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
 }
 
 void tc_to_f32(const double *x, float *y, size_t n, cudaStream_t s) {

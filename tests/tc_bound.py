@@ -150,3 +150,151 @@ def sigmas(inst, X, prec):
         var_g += rk2 * d * v32 * (S @ L2.T)                # FP32 accumulation of z
         var_g += vr[:, k][:, None] * PA * PA               # responsibilities
     return s_l, np.sqrt(var_g)
+
+
+def _quad_parts(inst, X):
+    """Per sample (x = c + tau u on a sunburst ray from the box centre c): tau = |x - c|,
+    u = (x - c) / tau, and the components' a_k."""
+    X = np.asarray(X, dtype=np.float64)
+    c = 0.5 * (inst.lo + inst.hi)
+    D = X - c
+    tau = np.sqrt((D * D).sum(1))
+    U = D / np.where(tau > 0, tau, 1.0)[:, None]
+    a_k = inst.log_w - 0.5 * inst.d * np.log(2 * np.pi) + np.log(np.diagonal(inst.L, axis1=1, axis2=2)).sum(1)
+    return c, tau, U, a_k
+
+
+def _quad_form(prec, d):
+    """(worst-case and variance coefficients of one product u_i L_ij, accumulation steps
+    of w_j, column tile of the |w|^2 and alpha . w partials) of a quadratic ray form:
+    prec 2 / 1 the tensor-core split products at bf16 / tf32 (three split residuals of
+    at most u_p^2 each, one of them the omitted u_lo L_lo; 3 d accumulation steps; tiles
+    of 256 columns), prec 0 the FP32 SIMT form (u and L_k rounded to FP32; d
+    accumulation steps; tiles of 128 columns)."""
+    if prec == 0:
+        return 2 * U32 + U32 * U32, 2 * U32 ** 2 / 3.0, d, 128
+    up = U_P[prec]
+    return 3 * up * up, up ** 4, 3 * d, 256
+
+
+def quad_bounds(inst, X, prec):
+    """Worst case of a quadratic ray pass at ray samples X [n, d] (prec as _quad_form):
+    w_j = sum_i u_i L_ij with the operand error of _quad_form and FP32 accumulation over
+    n_acc terms; q1 = alpha . w and q2 = |w|^2 summed in FP32 over column tiles of
+    n_tile, the tiles in FP64; alpha in FP32; |z|^2 = q0 + 2 tau q1 + tau^2 q2 in FP64.
+    With E_j = (e_op + n_acc 2^-23)(1 + u_p)^2 sum_i |u_i| |L_ij|:
+        d|z|^2 <= 2 tau sum_j |z_j| E_j + tau^2 sum_j E_j^2
+                  + n_tile 2^-23 (tau^2 q2 + 2 tau sum_j |alpha_j w_j|) + 2^-24 2 tau sum_j |alpha_j w_j|
+                  + 8 2^-53 (q0 + 2 tau |q1| + tau^2 q2),
+    and l lies between LSE(e - d|z|^2 / 2) and LSE(e + d|z|^2 / 2), plus the FP32 LSE floor.
+    Returns (B_l [n], l [n])."""
+    c, tau, U, a_k = _quad_parts(inst, X)
+    d, K = inst.d, inst.K
+    e_op, _, n_acc, n_tile = _quad_form(prec, d)
+    up = U_P.get(prec, U32)
+    cb = (e_op + n_acc * 2.0 ** -23) * (1 + up) ** 2
+    q = np.empty((X.shape[0], K))
+    dq = np.empty((X.shape[0], K))
+    for k in range(K):
+        Lk = inst.L[k]
+        al = (c - inst.mu[k]) @ Lk
+        W = U @ Lk
+        Z = al[None, :] + tau[:, None] * W
+        E = cb * (np.abs(U) @ np.abs(Lk))
+        aw = np.abs(al[None, :] * W).sum(1)
+        q2 = (W * W).sum(1)
+        q1 = (al[None, :] * W).sum(1)
+        q0 = float(al @ al)
+        q[:, k] = (Z * Z).sum(1)
+        dq[:, k] = (2 * tau * (np.abs(Z) * E).sum(1) + tau ** 2 * (E * E).sum(1)
+                    + n_tile * 2.0 ** -23 * (tau ** 2 * q2 + 2 * tau * aw) + 2.0 ** -24 * 2 * tau * aw
+                    + 8 * 2.0 ** -53 * (q0 + 2 * tau * np.abs(q1) + tau ** 2 * q2))
+    ee = a_k[None, :] - 0.5 * q
+    ell = _lse(ee)
+    hi = _lse(ee + 0.5 * dq)
+    lo = _lse(ee - 0.5 * dq)
+    return np.maximum(hi - ell, ell - lo) + 2.0 ** -20 * (1 + K), ell
+
+
+def quad_sigmas(inst, X, prec):
+    """Standard deviation of a quadratic ray pass's error at ray samples X (prec as
+    _quad_form) under the first-order model of independent roundings: each product
+    u_i L_ij carries the operand variance of _quad_form, an FP32 accumulation step
+    v32 = u32^2 / 3 of the partial sum (n_acc steps for w_j, n_tile for the tile partials
+    of q1 and q2). To first order d|z|^2 = 2 tau z . dw plus the tile partials' rounding:
+        Var d|z_k|^2 = 4 tau^2 sum_j z_j^2 Var dw_j
+                       + n_tile v32 (tau^4 q2^2 + 4 tau^2 (sum_j |alpha_j w_j|)^2) / n_tiles
+                       + 4 tau^2 v32 sum_j (alpha_j w_j)^2,
+    Var dw_j = (v_op + n_acc v32) sum_i u_i^2 L_ij^2, and dl = -1/2 sum_k r_k d|z_k|^2
+    (independent components) with the FP32 LSE floor 4 u32."""
+    c, tau, U, a_k = _quad_parts(inst, X)
+    v32 = U32 ** 2 / 3.0
+    d, K = inst.d, inst.K
+    _, v_op, n_acc, n_tile = _quad_form(prec, d)
+    n_tiles = max(1, -(-d // n_tile))
+    q = np.empty((X.shape[0], K))
+    vq = np.empty((X.shape[0], K))
+    for k in range(K):
+        Lk = inst.L[k]
+        al = (c - inst.mu[k]) @ Lk
+        W = U @ Lk
+        Z = al[None, :] + tau[:, None] * W
+        Vw = (v_op + n_acc * v32) * ((U * U) @ (Lk * Lk))
+        aw = np.abs(al[None, :] * W).sum(1)
+        q2 = (W * W).sum(1)
+        q[:, k] = (Z * Z).sum(1)
+        vq[:, k] = (4 * tau ** 2 * (Z * Z * Vw).sum(1)
+                    + n_tile * v32 * (tau ** 4 * q2 ** 2 + 4 * tau ** 2 * aw ** 2) / n_tiles
+                    + 4 * tau ** 2 * v32 * ((al[None, :] * W) ** 2).sum(1))
+    ee = a_k[None, :] - 0.5 * q
+    r = np.exp(ee - _lse(ee)[:, None])
+    return np.sqrt(0.25 * (r * r * vq).sum(1) + (4 * U32) ** 2)
+
+
+def quad_bias(inst, X, prec):
+    """Signed first-order effect on l of tensor-core accumulation steps that each shrink
+    the accumulator of w_j = sum_i u_i L_ij by 2^-24 of its magnitude (rounding toward
+    zero). The split products run the small ones first, so only the last segment's
+    n_j = ceil((d - j) / k) + 1 steps add to an accumulator of full magnitude (k the
+    products one instruction sums: 16 for bf16, 8 for tf32) and w_j becomes
+    (1 - n_j 2^-24) w_j:
+        d|z_k|^2 = -2 tau sum_j n_j 2^-24 z_kj w_kj,   dl = -1/2 sum_k r_k d|z_k|^2.
+    Zero for the FP32 SIMT form (prec 0: round-to-nearest FMA chains)."""
+    c, tau, U, a_k = _quad_parts(inst, X)
+    if prec == 0:
+        return np.zeros(X.shape[0])
+    d, K = inst.d, inst.K
+    kin = 16 if prec == 2 else 8
+    nj = np.ceil((d - np.arange(d)) / kin) + 1
+    q = np.empty((X.shape[0], K))
+    dq = np.empty((X.shape[0], K))
+    for k in range(K):
+        Lk = inst.L[k]
+        al = (c - inst.mu[k]) @ Lk
+        W = U @ Lk
+        Z = al[None, :] + tau[:, None] * W
+        q[:, k] = (Z * Z).sum(1)
+        dq[:, k] = -2 * tau * 2.0 ** -24 * (Z * W * nj[None, :]).sum(1)
+    ee = a_k[None, :] - 0.5 * q
+    r = np.exp(ee - _lse(ee)[:, None])
+    return -0.5 * (r * dq).sum(1)
+
+
+# A quadratic ray pass's error at a sample is the accumulation bias, between 0 and
+# quad_bias, plus independent roundings within C_Q of quad_sigmas, and never beyond
+# quad_bounds. On a GB300 the largest distance outside [0, bias] over the parity cases
+# was 1.05 standard deviations (BF16, d = 64) and the fitted bias fraction 0.35 - 0.42.
+# A dropped K chunk moves w_j by a partial sum of its column, a swapped or repeated split
+# segment by u_p |w_j| (2^8 or 2^11 times the split residual the model allows): either
+# is thousands of standard deviations.
+C_Q = 4.0
+
+
+def check_ray_samples(inst, X, dl, prec):
+    """Asserts the errors dl = l_gpu - l_oracle at ray samples X fit the model above."""
+    s = quad_sigmas(inst, X, prec)
+    B, _ = quad_bounds(inst, X, prec)
+    bias = quad_bias(inst, X, prec)
+    out = np.maximum(np.minimum(0.0, bias) - dl, dl - np.maximum(0.0, bias)) / s
+    assert out.max() <= C_Q, (int(np.argmax(out)), float(out.max()))
+    assert (np.abs(dl) <= B).all(), float((np.abs(dl) / B).max())

@@ -140,9 +140,11 @@ def test_ray_loglik_quad_rejects_bad_arguments_on_the_host():
     p = _fake_problem(8, 1)
     L = sb.lib()
     buf = (C.c_char * 16)()
-    assert L.sb_ray_loglik_quad(C.byref(p), 2, buf, 4, 8, buf, buf, C.c_size_t(16), None) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_ray_loglik_quad(C.byref(p), 4, buf, 4, 8, buf, buf, C.c_size_t(16), None) == sb.SB_ERR_INVALID_ARG
     assert L.sb_ray_loglik_quad(C.byref(p), 1, buf, 0, 8, buf, buf, C.c_size_t(16), None) == sb.SB_ERR_INVALID_ARG
     assert L.sb_ray_loglik_quad(C.byref(p), 1, buf, 4, 8, buf, buf, C.c_size_t(16), None) == sb.SB_ERR_WORKSPACE
     assert L.sb_ray_loglik_quad_workspace_bytes(C.byref(p), 0, 4) > 0
     assert L.sb_ray_loglik_quad_workspace_bytes(C.byref(p), 1, 4) > 0
-    assert L.sb_ray_loglik_quad_workspace_bytes(C.byref(p), 3, 4) == 0
+    assert L.sb_ray_loglik_quad_workspace_bytes(C.byref(p), 2, 4) > 0
+    assert L.sb_ray_loglik_quad_workspace_bytes(C.byref(p), 3, 4) > 0
+    assert L.sb_ray_loglik_quad_workspace_bytes(C.byref(p), 4, 4) == 0

@@ -176,16 +176,43 @@ def test_mixed_refine_components_beyond_32(prec):
         assert np.sqrt(z @ z) <= 1.0, (t, k)
 
 
+def _check_ray_samples(inst, X, ell, prec):
+    """Discovery's l at ray samples comes from the quadratic form of each ray (split
+    tensor-core products): its error model is tc_bound.check_ray_samples."""
+    ref = np.array([oracle.loglik(inst, x) for x in X])
+    tc_bound.check_ray_samples(inst, X, ell - ref, prec)
+
+
+@pytest.mark.parametrize("prec", [sb.PREC_BF16, sb.PREC_TF32])
+@pytest.mark.parametrize("d,K,n_rays,n_steps", [(64, 4, 64, 16), (300, 3, 32, 32), (200, 2, 130, 8),
+                                                (1024, 8, 32, 64), (7, 2, 16, 8), (1, 1, 4, 4)])
+def test_discover_quadratic_ray_pass_against_oracle(prec, d, K, n_rays, n_steps):
+    """Every ray sample (n_starts = n_rays x n_steps, so that discovery returns all of
+    them) against the FP64 oracle's l at the returned point: ragged d (300, 200, 7, 1
+    against 64-element bf16 and 32-element tf32 chunks), ragged ray blocks (130 rays
+    over 128-row tiles), the bench's d = 1024, K = 8 instance."""
+    if d == 1024:
+        inst = workload(4)[0][0]
+    else:
+        inst = make_instance(d, K, 900 + d, s_range=(0.05, 0.5), mean_box=(-6, 6), sep=8.0)
+    c = SolveConfig(n_rays=n_rays, n_steps=n_steps, n_starts=n_rays * n_steps, m=10, seed=7, prec=prec)
+    starts, ell = sb.discover(sb.Problem(inst), sb.make_config(c))
+    X, ell = starts.cpu().numpy(), ell.cpu().numpy()
+    assert X.shape == (n_rays * n_steps, d)
+    ref_x, _ = oracle.discover(inst, c)
+    # the same sample set (discovery returns every sample, in its own order)
+    key = lambda A: A[np.lexsort(A.T[::-1])]
+    assert np.abs(key(X) - key(ref_x)).max() <= 1e-13 * (1 + np.abs(ref_x).max())
+    _check_ray_samples(inst, X, ell, prec)
+
+
 def test_full_size_workload_sampled_against_oracle():
     """The configuration the bench times (d=1024, K=8, 16384 rays x 64 steps, 16384
     walkers, m=20, BF16, ChiSao), checked where the oracle can follow one output at a
-    time: 64 sampled selected starts' l against the FP64 oracle within C_SIGMA standard
-    deviations of the tensor-core rounding model (tests/tc_bound.py, the constant of the
-    tensor-core tests) and inside its worst case; then the whole pipeline on the same
-    workspace: all eight components, every mode a component mean with its exact Laplace
-    term, log Z the closed form to 1e-9."""
-    from test_gpu_tc import C_SIGMA
-
+    time: 64 sampled selected starts' l against the FP64 oracle within the quadratic
+    ray pass's error model (tc_bound.check_ray_samples); then the whole
+    pipeline on the same workspace: all eight components, every mode a component mean
+    with its exact Laplace term, log Z the closed form to 1e-9."""
     insts, c = workload(4)
     inst = insts[0]
     cfg = sb.make_config(c)
@@ -194,11 +221,7 @@ def test_full_size_workload_sampled_against_oracle():
     starts, ell = sb.discover(prob, cfg, ws=ws)
     starts, ell = starts.cpu().numpy(), ell.cpu().numpy()
     pick = np.random.default_rng(11).choice(c.n_starts, 64, replace=False)
-    s_l, _ = tc_bound.sigmas(inst, starts[pick], sb.PREC_BF16)
-    B_l, _, _, _ = tc_bound.bounds(inst, starts[pick], sb.PREC_BF16)
-    for t, i in enumerate(pick):
-        dl = abs(ell[i] - oracle.loglik(inst, starts[i]))
-        assert dl <= C_SIGMA[sb.PREC_BF16] * s_l[t] and dl <= B_l[t], (i, dl, s_l[t])
+    _check_ray_samples(inst, starts[pick], ell[pick], sb.PREC_BF16)
     out = sb.evidence_chisao(prob, cfg, sb.make_chisao_config(), ws=ws)
     found = _check_modes_against_components(inst, out)
     assert found.tolist() == list(range(inst.K))

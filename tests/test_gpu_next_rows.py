@@ -24,6 +24,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle
+import tc_bound
 import paper_2601_19957_gb300 as sb
 from paper_2601_19957_gb300.instances import SolveConfig, make_instance, workload
 
@@ -168,3 +169,20 @@ def test_ray_loglik_quad_fp64_matches_oracle(d, K, n_rays, n_steps):
     # |z(t)|^2 = q0 + 2 tau q1 + tau^2 q2 cancels terms as large as the largest |l| on the ray
     scale = 1.0 + np.abs(ref).max(1, keepdims=True)
     assert np.all(np.abs(ell - ref) <= 1e-12 * scale), np.max(np.abs(ell - ref) / scale)
+
+
+@pytest.mark.parametrize("form", [1, 2, 3])
+@pytest.mark.parametrize("d,K,n_rays,n_steps", [(8, 1, 64, 16), (64, 4, 300, 64), (130, 3, 129, 33), (1, 2, 5, 3)])
+def test_ray_loglik_quad_mixed_forms_match_oracle(form, d, K, n_rays, n_steps):
+    """The FP32 SIMT form (1) and the tensor-core split forms (2 BF16, 3 TF32) at every
+    sample of the oracle's rays, within the quadratic ray pass's error model
+    (tc_bound.check_ray_samples; FP32: operands rounded to FP32, no accumulation bias)."""
+    inst = make_instance(d, K, 700 + d, s_range=(0.05, 0.5), mean_box=(-6, 6), sep=8.0 if K > 1 else 0.0)
+    cfg = SolveConfig(n_rays=n_rays, n_steps=n_steps, n_starts=1, seed=d)
+    u, te, ref = oracle.ray_loglik(inst, cfg)
+    ell = sb.ray_loglik_quad(sb.Problem(inst), torch.as_tensor(u, device="cuda"), n_steps, form=form).cpu().numpy()
+    c = 0.5 * (inst.lo + inst.hi)
+    tau = (np.arange(1, n_steps + 1) / n_steps)[None, :] * te[:, None]
+    X = (c[None, None, :] + tau[:, :, None] * u[:, None, :]).reshape(-1, d)
+    prec = {1: 0, 2: sb.PREC_BF16, 3: sb.PREC_TF32}[form]
+    tc_bound.check_ray_samples(inst, X, (ell - ref).reshape(-1), prec)
