@@ -45,14 +45,77 @@ __global__ void __launch_bounds__(256) k_ray_dirs(int d, int n_rays, uint32_t k0
     }
     const double nrm = sqrt(warp_sum(ss));
     __syncwarp();
-    double tmin = INFINITY;
-    for (int i = lane; i < d; i += 32) {
-        const double v = div_rn(ur[i], nrm);
-        ur[i] = v;
-        const double au = fabs(v);
-        if (au > 0.0) tmin = fmin(tmin, div_rn(half[i], au));
+    for (int i = lane; i < d; i += 32) ur[i] = div_rn(ur[i], nrm);
+    __syncwarp();
+    const double tmin = warp_exit_min(lane, d, ur, half);
+    if (lane == 0) texit[r] = tmin;
+}
+
+// The same rays for the mixed-precision path, generated in FP32 (the tensor-core
+// operands carry fewer bits): the same Philox counters, uniforms from the top 24 bits
+// of each 64-bit pair, Box-Muller with FP32 transcendentals, normalised in FP32 and
+// widened to FP64; t_exit in FP64 for the widened direction, so the last sample of a
+// ray lies on the box surface.
+__global__ void __launch_bounds__(256) k_ray_dirs_f32(int d, int n_rays, uint32_t k0, uint32_t k1, const double *half,
+                                                      double *u, double *texit) {
+    const int lane = threadIdx.x & 31;
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= n_rays) return;
+    double *ur = u + (size_t)r * d;
+    const int npairs = (d + 1) / 2;
+    constexpr int kPer = 16;  // pairs a lane keeps in registers before the norm is known
+    float x[2 * kPer];
+    float ss = 0.f;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int p = lane + 32 * q;
+        x[2 * q] = x[2 * q + 1] = 0.f;
+        if (p < npairs) {
+            uint32_t c[4] = {(uint32_t)p, (uint32_t)r, 0x52415953u, 0u};
+            philox4x32_10(c, k0, k1);
+            const float u1 = ((float)(c[0] >> 8) + 0.5f) * (1.0f / 16777216.0f);
+            const float u2 = ((float)(c[2] >> 8) + 0.5f) * (1.0f / 16777216.0f);
+            const float rad = sqrtf(-2.0f * logf(u1));
+            float sn, cs;
+            sincospif(2.0f * u2, &sn, &cs);
+            x[2 * q] = rad * cs;
+            x[2 * q + 1] = 2 * p + 1 < d ? rad * sn : 0.f;
+            ss += x[2 * q] * x[2 * q] + x[2 * q + 1] * x[2 * q + 1];
+        }
     }
-    tmin = warp_min(tmin);
+    // pairs beyond the register block (d > 1024) are stored unnormalised first
+    for (int p = lane + 32 * kPer; p < npairs; p += 32) {
+        uint32_t c[4] = {(uint32_t)p, (uint32_t)r, 0x52415953u, 0u};
+        philox4x32_10(c, k0, k1);
+        const float u1 = ((float)(c[0] >> 8) + 0.5f) * (1.0f / 16777216.0f);
+        const float u2 = ((float)(c[2] >> 8) + 0.5f) * (1.0f / 16777216.0f);
+        const float rad = sqrtf(-2.0f * logf(u1));
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        const float x0 = rad * cs;
+        ur[2 * p] = x0;
+        ss += x0 * x0;
+        if (2 * p + 1 < d) {
+            const float x1 = rad * sn;
+            ur[2 * p + 1] = x1;
+            ss += x1 * x1;
+        }
+    }
+    const float inv = 1.0f / sqrtf(warp_sum(ss));
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int p = lane + 32 * q;
+        if (p < npairs) {
+            ur[2 * p] = (double)(x[2 * q] * inv);
+            if (2 * p + 1 < d) ur[2 * p + 1] = (double)(x[2 * q + 1] * inv);
+        }
+    }
+    for (int p = lane + 32 * kPer; p < npairs; p += 32) {
+        ur[2 * p] = (double)((float)ur[2 * p] * inv);
+        if (2 * p + 1 < d) ur[2 * p + 1] = (double)((float)ur[2 * p + 1] * inv);
+    }
+    __syncwarp();
+    const double tmin = warp_exit_min(lane, d, ur, half);
     if (lane == 0) texit[r] = tmin;
 }
 
@@ -235,11 +298,15 @@ __global__ void __launch_bounds__(256) k_gather_starts(int d, const double *c, c
 
 size_t select_blocks(int64_t total) { return (size_t)((total + SEL_BLOCK - 1) / SEL_BLOCK); }
 
-void launch_ray_dirs(int d, int n_rays, uint64_t seed, const ProbView &pv, double *u, double *texit, cudaStream_t s) {
+void launch_ray_dirs(int d, int n_rays, uint64_t seed, const ProbView &pv, double *u, double *texit, bool fp32,
+                     cudaStream_t s) {
     const int warps_per_block = 8;
     const unsigned grid = (unsigned)((n_rays + warps_per_block - 1) / warps_per_block);
     note_launch();
-    k_ray_dirs<<<grid, 256, 0, s>>>(d, n_rays, (uint32_t)seed, (uint32_t)(seed >> 32), pv.half, u, texit);
+    if (fp32)
+        k_ray_dirs_f32<<<grid, 256, 0, s>>>(d, n_rays, (uint32_t)seed, (uint32_t)(seed >> 32), pv.half, u, texit);
+    else
+        k_ray_dirs<<<grid, 256, 0, s>>>(d, n_rays, (uint32_t)seed, (uint32_t)(seed >> 32), pv.half, u, texit);
 }
 
 void launch_select_starts(const double *ell_all, int n_rays, int n_steps, int n_starts, const SelectWs &w,

@@ -28,12 +28,7 @@ __global__ void __launch_bounds__(256) k_rq_texit(int n_rays, int d, const doubl
     const int lane = threadIdx.x & 31;
     const int r = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     if (r >= n_rays) return;
-    double t = INFINITY;
-    for (int i = lane; i < d; i += 32) {
-        const double a = fabs(u[(size_t)r * d + i]);
-        if (a > 0.0) t = fmin(t, div_rn(half[i], a));
-    }
-    t = warp_min(t);
+    const double t = warp_exit_min(lane, d, u + (size_t)r * d, half);
     if (lane == 0) texit[r] = t;
 }
 

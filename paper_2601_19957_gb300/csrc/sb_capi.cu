@@ -366,7 +366,7 @@ sb_status run_discover(const ProbView &pv, const sb_config *c, const Layout &L, 
                        cudaStream_t s) {
     const int d = pv.d;
     const int64_t total = (int64_t)c->n_rays * c->n_steps;
-    launch_ray_dirs(d, c->n_rays, c->seed, pv, L.di.u, L.di.texit, s);
+    launch_ray_dirs(d, c->n_rays, c->seed, pv, L.di.u, L.di.texit, c->prec != SB_PREC_FP64, s);
     if (c->prec == SB_PREC_FP64) {
         for (int64_t f0 = 0; f0 < total; f0 += L.di.chunk) {
             const int rows = (int)((total - f0) < L.di.chunk ? (total - f0) : L.di.chunk);

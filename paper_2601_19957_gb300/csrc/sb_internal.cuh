@@ -80,6 +80,11 @@ __device__ __forceinline__ double warp_min(double v) {
     for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
 __device__ __forceinline__ int warp_and(int v) { return __all_sync(0xffffffffu, v); }
 
 // Round-to-nearest arithmetic without contraction, so update formulas match a
@@ -92,6 +97,32 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+
+// t_exit = min_i half_i / |u_i| over the coordinates i = lane, lane + 32, ... of one
+// warp (u_i = 0 skipped; INFINITY when every u_i is 0), each quotient rounded to
+// nearest in FP64, without dividing every coordinate in FP64: FP32 quotients (three
+// roundings, relative error below 2^-21 for values in [1e-30, 1e30]) bound the
+// smallest one, and only coordinates within 2^-18 of that bound, or outside the
+// range where the FP32 error holds, are divided in FP64. The FP64 quotient is
+// monotone in the exact one, so the result is the plain minimum of all of them.
+__device__ __forceinline__ double warp_exit_min(int lane, int d, const double *u, const double *half) {
+    constexpr float kLo = 1e-30f, kHi = 1e30f;
+    float est = INFINITY;
+    for (int i = lane; i < d; i += 32) {
+        const float a = (float)fabs(u[i]), h = (float)half[i];
+        if (a >= kLo && h >= kLo && h <= kHi) est = fminf(est, __fdiv_rn(h, a));
+    }
+    const float thr = warp_min(est) * (1.0f + 0x1p-18f);
+    double t = INFINITY;
+    for (int i = lane; i < d; i += 32) {
+        const double au = fabs(u[i]);
+        if (!(au > 0.0)) continue;
+        const float a = (float)au, h = (float)half[i];
+        if (a >= kLo && h >= kLo && h <= kHi && __fdiv_rn(h, a) > thr) continue;
+        t = fmin(t, __ddiv_rn(half[i], au));
+    }
+    return warp_min(t);
+}
 
 __device__ __forceinline__ bool is_finite(double v) { return isfinite(v); }
 __device__ __forceinline__ bool is_finite(float v) { return isfinite(v); }
@@ -204,8 +235,11 @@ void launch_lik_f64_z(const LikF64Args &a, cudaStream_t s);
 void launch_lik_f64_few(const LikF64Args &a, bool want_grad, cudaStream_t s);
 
 // rays.cu
-// FP64 unit directions u [n_rays][d] and their exit lengths from the box centre.
-void launch_ray_dirs(int d, int n_rays, uint64_t seed, const ProbView &pv, double *u, double *texit, cudaStream_t s);
+// Unit directions u [n_rays][d] and their exit lengths from the box centre: FP64
+// Box-Muller (fp32 = false, the oracle's directions) or FP32 Box-Muller widened to FP64
+// (fp32 = true, for the mixed-precision path; t_exit exact for the widened directions).
+void launch_ray_dirs(int d, int n_rays, uint64_t seed, const ProbView &pv, double *u, double *texit, bool fp32,
+                     cudaStream_t s);
 struct SelectWs {
     int32_t *bucket;     // [total]
     uint32_t *hist;      // [max(2*S, 256)]

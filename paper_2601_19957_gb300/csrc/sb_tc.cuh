@@ -54,7 +54,8 @@ void tc_to_f32(const double *x, float *y, size_t n, cudaStream_t s);
 struct TcQuadWs {
     void *A2, *B2;                   // [rows][2 dK] direction splits, [K][d][2 dK] L_k^T splits
     float *alpha, *qpart1, *qpart2;  // [K][ald] z_k(c) in FP32 (zero past d); partials [rows][K][nct]
-    double *zc, *zq, *q0;            // [K][d] z_k(c), its FP64 |z|^2 partials, [K] |z_k(c)|^2
+    double *zc, *q0;                 // [K][d] z_k(c), [K] |z_k(c)|^2
+    double2 *q12;                    // [n_rays][K] (z_k(c) . w_rk, |w_rk|^2) in FP64
     int rows, dK, ald;
     CUtensorMap mapU, mapL;
 };

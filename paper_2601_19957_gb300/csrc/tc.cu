@@ -1393,6 +1393,29 @@ __global__ void k_q_split_LT(int d, int K, int dK, const double *L, void *B2) {
     }
 }
 
+// z_k(c)_j = sum_{i >= j} (c_i - mu_k,i) L_k,ij in FP64: one CTA per (32 columns,
+// component), a lane per column (rows of L_k read 256 bytes at a time), the eight
+// warps over interleaved rows, their partials summed in a fixed order
+__global__ void __launch_bounds__(256) k_q_zc(int d, const double *c, const double *mu, const double *L,
+                                              double *zc) {
+    const int k = blockIdx.y, j0 = blockIdx.x * 32, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = j0 + lane;
+    const double *Lk = L + (size_t)k * d * d;
+    const double *mk = mu + (size_t)k * d;
+    double s = 0.0;
+    if (j < d)
+        for (int i = j0 + w; i < d; i += 8)
+            if (i >= j) s = fma(c[i] - mk[i], Lk[(size_t)i * d + j], s);
+    __shared__ double part[8][32];
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && j < d) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += part[q][lane];
+        zc[(size_t)k * d + j] = t;
+    }
+}
+
 // alpha[k][j] = (float) z_k(c)_j (zero for d <= j < ald) and q0[k] = |z_k(c)|^2 (FP64,
 // partials in a fixed order): one CTA per component
 __global__ void __launch_bounds__(256) k_q_alpha(int d, int ald, const double *zc, float *alpha, double *q0) {
@@ -1414,25 +1437,36 @@ __global__ void __launch_bounds__(256) k_q_alpha(int d, int ald, const double *z
     }
 }
 
-// l at sample j of ray r: |z_k|^2 = q0_k + 2 tau q1_rk + tau^2 q2_rk in FP64 (q1, q2 the
-// FP64 sums of the column tiles' FP32 partials), tau = ((j + 1) / n_steps) t_exit,r;
-// the LSE as in k_tc_lse (FP64 terms, FP32 exponentials of the shifted terms)
-__global__ void __launch_bounds__(256) k_q_ell(int n_rays, int n_steps, int K, int n_ntile, const double *a_k,
-                                               const double *q0, const float *qp1, const float *qp2,
-                                               const double *texit, double *ell) {
+// (q1, q2)[r][k]: the FP64 sums of ray r's column-tile partials (FP32) of z_k(c) . w_rk
+// and |w_rk|^2, one thread per (ray, component)
+__global__ void __launch_bounds__(256) k_q_sum(int n_rk, int n_ntile, const float *qp1, const float *qp2,
+                                               double2 *q12) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_rk) return;
+    const float *p1 = qp1 + (size_t)e * n_ntile;
+    const float *p2 = qp2 + (size_t)e * n_ntile;
+    double q1 = 0.0, q2 = 0.0;
+    for (int t = 0; t < n_ntile; ++t) {
+        q1 += (double)p1[t];
+        q2 += (double)p2[t];
+    }
+    q12[e] = make_double2(q1, q2);
+}
+
+// l at sample j of ray r: |z_k|^2 = q0_k + 2 tau q1_rk + tau^2 q2_rk in FP64,
+// tau = ((j + 1) / n_steps) t_exit,r; the LSE as in k_tc_lse (FP64 terms, FP32
+// exponentials of the shifted terms). The threads of a warp mostly share a ray, so
+// its coefficients are broadcast loads.
+__global__ void __launch_bounds__(256) k_q_ell(int n_rays, int n_steps, int K, const double *a_k, const double *q0,
+                                               const double2 *q12, const double *texit, double *ell) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= (int64_t)n_rays * n_steps) return;
     const int r = (int)(e / n_steps), j = (int)(e - (int64_t)r * n_steps);
     const double tau = ((double)(j + 1) / (double)n_steps) * texit[r];
+    const double2 *qr = q12 + (size_t)r * K;
     auto term = [&](int k) {
-        const float *p1 = qp1 + ((size_t)r * K + k) * n_ntile;
-        const float *p2 = qp2 + ((size_t)r * K + k) * n_ntile;
-        double q1 = 0.0, q2 = 0.0;
-        for (int t = 0; t < n_ntile; ++t) {
-            q1 += (double)p1[t];
-            q2 += (double)p2[t];
-        }
-        return a_k[k] - 0.5 * (q0[k] + tau * (2.0 * q1 + tau * q2));
+        const double2 q = qr[k];
+        return a_k[k] - 0.5 * (q0[k] + tau * (2.0 * q.x + tau * q.y));
     };
     double emax = -INFINITY;
     for (int k = 0; k < K; ++k) emax = fmax(emax, term(k));
@@ -1453,8 +1487,8 @@ void carve_tc_quad(Carver &cv, TcQuadWs &q, int n_rays, int d, int K, int prec) 
     q.qpart1 = cv.take<float>((size_t)q.rows * K * nct);
     q.qpart2 = cv.take<float>((size_t)q.rows * K * nct);
     q.zc = cv.take<double>((size_t)K * d);
-    q.zq = cv.take<double>(lik_f64_qpart_elems(d, K, 1));
     q.q0 = cv.take<double>((size_t)K);
+    q.q12 = cv.take<double2>((size_t)n_rays * K);
 }
 
 sb_status tc_ray_loglik_quad(const ProbView &pv, int n_rays, int n_steps, int prec, int bn, TcQuadWs q,
@@ -1473,17 +1507,8 @@ sb_status tc_ray_loglik_quad(const ProbView &pv, int n_rays, int n_steps, int pr
         k_q_split_LT<SB_PREC_TF32><<<gs, 256, 0, s>>>(d, K, q.dK, pv.L, q.B2);
     }
     // z_k(c) in FP64 (one point), then its FP32 copy and |z_k(c)|^2
-    LikF64Args la{};
-    la.d = d;
-    la.K = K;
-    la.mu = pv.mu;
-    la.L = pv.L;
-    la.a = pv.a;
-    la.X = pv.c;
-    la.n_rows = 1;
-    la.Z = q.zc;
-    la.qpart = q.zq;
-    launch_lik_f64_z(la, s);
+    note_launch();
+    k_q_zc<<<dim3((unsigned)((d + 31) / 32), (unsigned)K), 256, 0, s>>>(d, pv.c, pv.mu, pv.L, q.zc);
     note_launch();
     k_q_alpha<<<K, 256, 0, s>>>(d, q.ald, q.zc, q.alpha, q.q0);
     if (!make_map(&q.mapU, q.A2, 2 * q.dK, q.rows, 1, 2 * q.dK, prec, BM) ||
@@ -1506,8 +1531,9 @@ sb_status tc_ray_loglik_quad(const ProbView &pv, int n_rays, int n_steps, int pr
     launch_gemm_any(prec, MODE_Q, bn, q.mapU, q.mapL, a, s);
     const int64_t ns = (int64_t)n_rays * n_steps;
     note_launch();
-    k_q_ell<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(n_rays, n_steps, K, a.n_ntile, pv.a, q.q0, q.qpart1,
-                                                         q.qpart2, texit, ell_all);
+    k_q_sum<<<(unsigned)((n_rays * K + 255) / 256), 256, 0, s>>>(n_rays * K, a.n_ntile, q.qpart1, q.qpart2, q.q12);
+    note_launch();
+    k_q_ell<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(n_rays, n_steps, K, pv.a, q.q0, q.q12, texit, ell_all);
     return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
 }
 

@@ -199,10 +199,18 @@ def test_discover_quadratic_ray_pass_against_oracle(prec, d, K, n_rays, n_steps)
     starts, ell = sb.discover(sb.Problem(inst), sb.make_config(c))
     X, ell = starts.cpu().numpy(), ell.cpu().numpy()
     assert X.shape == (n_rays * n_steps, d)
+    # every sample, in flat order (ray r, step j): the oracle's rays, with directions
+    # drawn in FP32 (the same Philox counters; Box-Muller in FP32), each ray's last sample
+    # on the box surface and sample j at (j + 1) / n_steps of it
     ref_x, _ = oracle.discover(inst, c)
-    # the same sample set (discovery returns every sample, in its own order)
-    key = lambda A: A[np.lexsort(A.T[::-1])]
-    assert np.abs(key(X) - key(ref_x)).max() <= 1e-13 * (1 + np.abs(ref_x).max())
+    cen, half = 0.5 * (inst.lo + inst.hi), 0.5 * (inst.hi - inst.lo)
+    D = (X - cen).reshape(n_rays, n_steps, d)
+    R = (ref_x - cen).reshape(n_rays, n_steps, d)
+    cos = (D[:, -1] * R[:, -1]).sum(1) / np.linalg.norm(D[:, -1], axis=1) / np.linalg.norm(R[:, -1], axis=1)
+    assert cos.min() >= 1 - 1e-6, cos.min()
+    assert np.abs(np.abs(D[:, -1] / half).max(1) - 1).max() <= 1e-12
+    frac = (np.arange(1, n_steps + 1) / n_steps)[None, :, None]
+    assert np.abs(D - frac * D[:, -1:]).max() <= 1e-12 * np.abs(D).max()
     _check_ray_samples(inst, X, ell, prec)
 
 
