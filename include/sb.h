@@ -467,6 +467,29 @@ size_t sb_ray_loglik_quad_workspace_bytes(const sb_problem *prob, int32_t form, 
 sb_status sb_ray_loglik_quad(const sb_problem *prob, int32_t form, const double *u, int32_t n_rays, int32_t n_steps,
                              double *ell, void *ws, size_t ws_bytes, void *stream);
 
+/* Bytes of device scratch sb_ray_loglik_origins needs (form 2 BF16, 3 TF32); 0 for
+ * another form or an invalid problem. */
+size_t sb_ray_loglik_origins_workspace_bytes(const sb_problem *prob, int32_t form, int32_t n_rays);
+
+/*
+ * Ray likelihoods from per-ray origins, the rays ChiSao's reseeding casts (Sec. 3.5.5:
+ * Repulse Monkey rays from unconverged samples, Golden Rooster rays from the peaks):
+ * along x(t) = o_r + tau u_r, tau = ((j + 1) / n_steps) t_exit,r with t_exit,r the
+ * distance from o_r along u_r to the box surface,
+ *     z_k(x) = z_k(o_r) + tau L_k^T u_r,  |z_k|^2 = q0_rk + 2 tau q1_rk + tau^2 q2_rk,
+ * with z_k(o_r) = o_r L_k - mu_k L_k from a tensor-core GEMM of the origins and
+ * L_k^T u_r from one of the directions (operands split into high and low parts at
+ * BF16 (form 2) or TF32 (form 3), FP32 accumulation; z_k(o_r) kept in FP32), the
+ * scalars combined in FP64 and ell[r][j] = LSE_k (a_k - |z_k|^2 / 2).
+ * o, u: [n_rays][d] device (origins inside the box, unit directions); ell:
+ * [n_rays][n_steps] device; texit: [n_rays] device or NULL. ws:
+ * sb_ray_loglik_origins_workspace_bytes. Asynchronous. SB_ERR_INVALID_ARG for another
+ * form, n_rays < 1 or n_steps < 1; SB_ERR_UNSUPPORTED on a device without tcgen05.
+ */
+sb_status sb_ray_loglik_origins(const sb_problem *prob, int32_t form, const double *o, const double *u,
+                                int32_t n_rays, int32_t n_steps, double *ell, double *texit, void *ws,
+                                size_t ws_bytes, void *stream);
+
 /* Bytes of device scratch sb_precheck needs. */
 size_t sb_precheck_workspace_bytes(const sb_problem *prob);
 

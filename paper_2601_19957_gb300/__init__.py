@@ -80,6 +80,8 @@ def lib():
         L.sb_fd_workspace_bytes.restype = C.c_size_t
         L.sb_ray_loglik_quad_workspace_bytes.restype = C.c_size_t
         L.sb_ray_loglik_quad.restype = C.c_int
+        L.sb_ray_loglik_origins_workspace_bytes.restype = C.c_size_t
+        L.sb_ray_loglik_origins.restype = C.c_int
         L.sb_fd_derivatives.restype = C.c_int
         L.sb_fd_derivatives.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
@@ -302,6 +304,22 @@ def ray_loglik_quad(prob: Problem, u, n_steps: int, form: int = 1, stream=None):
     _check(lib().sb_ray_loglik_quad(C.byref(prob.s), C.c_int32(form), _ptr(u), C.c_int32(n_rays), C.c_int32(n_steps),
                                     _ptr(ell), ws.ptr, C.c_size_t(ws.nbytes), _stream(stream)), "sb_ray_loglik_quad")
     return ell
+
+
+def ray_loglik_origins(prob: Problem, o, u, n_steps: int, form: int = 2, stream=None):
+    """l at the samples of rays from origins o [n_rays][d] along unit directions u (form 2
+    BF16, 3 TF32 tensor-core split products); returns (ell [n_rays][n_steps], t_exit)."""
+    torch = _torch()
+    o = o.to(dtype=torch.float64, device="cuda").contiguous()
+    u = u.to(dtype=torch.float64, device="cuda").contiguous()
+    n_rays = u.shape[0]
+    ws = Workspace(int(lib().sb_ray_loglik_origins_workspace_bytes(C.byref(prob.s), int(form), int(n_rays))))
+    ell = torch.empty((n_rays, n_steps), dtype=torch.float64, device="cuda")
+    te = torch.empty(n_rays, dtype=torch.float64, device="cuda")
+    _check(lib().sb_ray_loglik_origins(C.byref(prob.s), C.c_int32(form), _ptr(o), _ptr(u), C.c_int32(n_rays),
+                                       C.c_int32(n_steps), _ptr(ell), _ptr(te), ws.ptr, C.c_size_t(ws.nbytes),
+                                       _stream(stream)), "sb_ray_loglik_origins")
+    return ell, te
 
 
 @dataclass

@@ -602,6 +602,22 @@ void launch_cs_lists(int n, const uint8_t *lost, const uint8_t *conv, const uint
     k_cs_lists<<<1, CS_CTA, 0, s>>>(n, lost, conv, stuck, status, ell, lost_list, unconv_list, moving_list, cnt);
 }
 
+__global__ void __launch_bounds__(256) k_cs_exit(int n, int d, const double *O, const double *U, const double *lo,
+                                                 const double *hi, double *texit) {
+    const int lane = threadIdx.x & 31;
+    const int l = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (l >= n) return;
+    const double t = exit_length(lane, d, O + (size_t)l * d, U + (size_t)l * d, lo, hi);
+    if (lane == 0) texit[l] = t;
+}
+
+void launch_cs_exit(int n, int d, const double *O, const double *U, const double *lo, const double *hi, double *texit,
+                    cudaStream_t s) {
+    if (n <= 0) return;
+    note_launch();
+    k_cs_exit<<<warp_grid(n), 256, 0, s>>>(n, d, O, U, lo, hi, texit);
+}
+
 void launch_cs_rm_rays(int n, int d, uint64_t seed, int osc, const int32_t *unconv_list, const int32_t *cnt,
                        const int32_t *state, const double *X, const double *lo, const double *hi, double *O, double *U,
                        double *texit, cudaStream_t s) {

@@ -1008,8 +1008,10 @@ struct ChisaoWs {
     int64_t *job_off;
     int64_t *stats;  // [4] l-only ray evaluations, L-BFGS l+grad, anti-convergence l+grad, -
     int32_t *state;  // [8] the oscillations' device-side state (see launch_cs_state_init)
-    int32_t *rows;   // ray samples of the current reseeding chunk
-    int lc;  // lost samples per chunk of ray samples
+    int32_t *rows;   // [0] ray samples of the current reseeding chunk (all rays: mixed path), [1] its rays
+    int lc;  // lost samples per chunk of ray samples (FP64 path)
+    TcQuadWs quad;    // mixed path: the reseeding rays' quadratic form (split operands, partials)
+    TcOriginWs orig;  // mixed path: z_k at the rays' origins
     size_t bytes;
 };
 
@@ -1029,9 +1031,13 @@ ChisaoWs chisao_layout(void *base, size_t off, const sb_problem *p, const sb_con
     w.ell = cv.take<double>(n);
     w.ellg = cv.take<double>(n);
     w.texit = cv.take<double>(n);
-    w.P = cv.take<double>((size_t)rows * d);
-    w.ellp = cv.take<double>(rows);
-    w.qp = cv.take<double>(lik_f64_qpart_elems(d, K, rows));
+    const bool mixed = c->prec != SB_PREC_FP64;
+    if (!mixed) {
+        w.P = cv.take<double>((size_t)rows * d);
+        w.qp = cv.take<double>(lik_f64_qpart_elems(d, K, rows));
+    }
+    // the mixed path evaluates every reseeding ray in one pass
+    w.ellp = cv.take<double>(mixed ? (size_t)n * c->n_steps : (size_t)rows);
     w.status = cv.take<int8_t>(n);
     w.conv = cv.take<uint8_t>(n);
     w.stuck = cv.take<uint8_t>(n);
@@ -1049,10 +1055,12 @@ ChisaoWs chisao_layout(void *base, size_t off, const sb_problem *p, const sb_con
     w.job_off = cv.take<int64_t>(n);
     w.stats = cv.take<int64_t>(4);
     w.state = cv.take<int32_t>(8);
-    w.rows = cv.take<int32_t>(1);
-    if (c->prec != SB_PREC_FP64) {
+    w.rows = cv.take<int32_t>(2);
+    if (mixed) {
         w.O32 = cv.take<float>((size_t)n * d);
         w.U32 = cv.take<float>((size_t)n * d);
+        carve_tc_quad(cv, w.quad, n, d, K, c->prec);
+        carve_tc_origins(cv, w.orig, n, d, K, c->prec);
     }
     w.bytes = cv.bytes();
     return w;
@@ -1109,6 +1117,10 @@ sb_status run_chisao(const Prelude &P, const sb_config *c, const sb_chisao_confi
     const DedupScratch dds{la.dd_l, la.dd_i, la.dd_bar, pv.status};
     SB_CUDA_TRY(cudaMemsetAsync(w.stats, 0, sizeof(int64_t) * 4, s));
     launch_cs_state_init(w.state, s);
+    if (mixed) {
+        st = tc_quad_prepare_origins(pv, c->prec, w.quad, w.orig, s);
+        if (st != SB_OK) return st;
+    }
     SB_CUDA_TRY(cudaMemcpyAsync(w.X, x0, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, s));
     // l and grad l at the samples listed in rows (all n when rows is null)
     auto grad_at = [&](const int32_t *rows, const int32_t *n_rows_dev, int n_rows) {
@@ -1158,18 +1170,20 @@ sb_status run_chisao(const Prelude &P, const sb_config *c, const sb_chisao_confi
         launch_cs_bases(n, d, c->seed, osc, w.job_pk, w.job_b, w.job_cols, w.job_off, w.state, w.Q, mixed, s);
         launch_cs_gr_rays(n, d, w.n_reps, w.reps, w.X, pv.lo, pv.hi, w.job_start, w.job_off, w.Q, w.cnt, w.state, w.O,
                           w.U, w.texit, s);
-        if (mixed) {  // the tensor-core pass forms the ray samples itself, in FP32
-            tc_to_f32(w.O, w.O32, (size_t)n * d, s);
-            tc_to_f32(w.U, w.U32, (size_t)n * d, s);
+        if (mixed) {
+            // every ray in one quadratic-form pass: two split GEMMs over the rays (origins,
+            // directions), then l at each sample from three scalars per (ray, component)
+            launch_cs_chunk_rows(w.cnt, w.state, 0, n, c->n_steps, w.rows, s);
+            launch_cs_chunk_rows(w.cnt, w.state, 0, n, 1, w.rows + 1, s);
+            st = tc_ray_origins_quad(pv, n, c->n_steps, c->prec, P.L.r32.tc.bn, w.quad, w.orig, w.O, w.U, w.texit,
+                                     w.rows + 1, w.rows, w.ellp, s);
+            if (st != SB_OK) return st;
+            launch_cs_ray_pick(0, n, c->n_steps, d, w.rows, w.state, w.ellp, w.lost_list, w.O, w.U, w.texit, w.X, s);
         }
-        for (int l0 = 0; l0 < n; l0 += w.lc) {
+        for (int l0 = 0; !mixed && l0 < n; l0 += w.lc) {
             const int lc = n - l0 < w.lc ? n - l0 : w.lc;
             launch_cs_chunk_rows(w.cnt, w.state, l0, lc, c->n_steps, w.rows, s);
-            if (mixed) {
-                st = tc_ray_chunk(pv, P.L.r32.tc, w.O32, w.U32, w.texit, c->n_steps, (int64_t)l0 * c->n_steps,
-                                  lc * c->n_steps, w.rows, w.ellp, s);
-                if (st != SB_OK) return st;
-            } else {
+            {
                 launch_cs_ray_points(l0, lc, c->n_steps, d, w.O, w.U, w.texit, w.rows, w.P, s);
                 LikF64Args a = f64_args(pv);
                 a.X = w.P;
@@ -1675,7 +1689,57 @@ RayqWs rayq_layout(void *base, const sb_problem *p, int n_rays, int form) {
     return w;
 }
 
+struct RayoWs {
+    SetupWs su;
+    double *texit;
+    TcQuadWs quad;
+    TcOriginWs orig;
+    size_t bytes;
+};
+
+RayoWs rayo_layout(void *base, const sb_problem *p, int n_rays, int form) {
+    RayoWs w{};
+    Carver cv(base);
+    carve_setup(cv, p, w.su);
+    const int prec = form == 2 ? SB_PREC_BF16 : SB_PREC_TF32;
+    w.texit = cv.take<double>(n_rays);
+    carve_tc_quad(cv, w.quad, n_rays, p->d, p->K, prec);
+    carve_tc_origins(cv, w.orig, n_rays, p->d, p->K, prec);
+    w.bytes = cv.bytes();
+    return w;
+}
+
 }  // namespace
+
+extern "C" size_t sb_ray_loglik_origins_workspace_bytes(const sb_problem *p, int32_t form, int32_t n_rays) {
+    if (check_problem(p) != SB_OK || (form != 2 && form != 3) || n_rays < 1 || n_rays > (1 << 24)) return 0;
+    return rayo_layout(nullptr, p, n_rays, form).bytes;
+}
+
+extern "C" sb_status sb_ray_loglik_origins(const sb_problem *p, int32_t form, const double *o, const double *u,
+                                           int32_t n_rays, int32_t n_steps, double *ell, double *texit, void *ws,
+                                           size_t ws_bytes, void *stream) {
+    sb_status st = check_problem(p);
+    if (st != SB_OK) return st;
+    if ((form != 2 && form != 3) || !o || !u || !ell || !ws) return SB_ERR_INVALID_ARG;
+    if (n_rays < 1 || n_rays > (1 << 24) || n_steps < 1 || (int64_t)n_rays * n_steps > 0x7fffffffLL)
+        return SB_ERR_INVALID_ARG;
+    const RayoWs w = rayo_layout(ws, p, n_rays, form);
+    if (ws_bytes < w.bytes) return SB_ERR_WORKSPACE;
+    const int prec = form == 2 ? SB_PREC_BF16 : SB_PREC_TF32;
+    if (!tc_available(prec)) return SB_ERR_UNSUPPORTED;
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    ProbView pv;
+    SB_CUDA_TRY(setup_only(p, w.su, cs, pv));
+    launch_cs_exit(n_rays, p->d, o, u, pv.lo, pv.hi, w.texit, cs);
+    st = tc_quad_prepare_origins(pv, prec, w.quad, w.orig, cs);
+    if (st != SB_OK) return st;
+    st = tc_ray_origins_quad(pv, n_rays, n_steps, prec, 0, w.quad, w.orig, o, u, w.texit, nullptr, nullptr, ell, cs);
+    if (st != SB_OK) return st;
+    if (texit) SB_CUDA_TRY(cudaMemcpyAsync(texit, w.texit, sizeof(double) * n_rays, cudaMemcpyDeviceToDevice, cs));
+    SB_CUDA_TRY(cudaGetLastError());
+    return SB_OK;
+}
 
 extern "C" size_t sb_ray_loglik_quad_workspace_bytes(const sb_problem *p, int32_t form, int32_t n_rays) {
     if (check_problem(p) != SB_OK || form < 0 || form > 3 || n_rays < 1 || n_rays > (1 << 24)) return 0;

@@ -37,6 +37,10 @@ void launch_cs_branch(const int32_t *cnt, const int32_t *n_peaks, int min_unconv
 // Repulse Monkey rays (when the branch is 1; lost sample l < cnt[0], grid for n):
 // origin = unconverged sample (l mod cnt[1]) clamped to the box, direction a unit
 // Philox-normal vector (counter (pair, l, osc, 'RPMK')), t_exit to the box face.
+// t_exit,l = min over u_li != 0 of (hi_i - o_li) / u_li or (lo_i - o_li) / u_li (0 when
+// no coordinate moves): the distance from origin o_l along u_l to the box surface.
+void launch_cs_exit(int n, int d, const double *O, const double *U, const double *lo, const double *hi, double *texit,
+                    cudaStream_t s);
 void launch_cs_rm_rays(int n, int d, uint64_t seed, int osc, const int32_t *unconv_list, const int32_t *cnt,
                        const int32_t *state, const double *X, const double *lo, const double *hi, double *O, double *U,
                        double *texit, cudaStream_t s);

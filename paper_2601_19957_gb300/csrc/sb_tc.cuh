@@ -31,16 +31,6 @@ int tc_tuned_tile(int d, int K, int prec);
 // encodes the tensor maps. skip_bounds: also the |L_k|_2 bounds the walker
 // rounds' component skip reads (one |z|^2 pass over the columns of every L_k).
 sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s, bool skip_bounds = true);
-// l at the ray samples of flat indices [f_begin, f_end) (ray = flat / n_steps,
-// j = flat % n_steps): x = o_ray + ((j + 1) / n_steps) t_exit,ray u_ray formed in FP32
-// inside the centring pass, o32 [rays][d] the rays' origins (the box centre when
-// null); ell[flat - f_begin]. Chunks of the scratch row capacity.
-sb_status tc_ray_samples(const ProbView &pv, const TcWs &t, const float *o32, const float *u32, const double *texit,
-                         int n_steps, int64_t f_begin, int64_t f_end, double *ell, cudaStream_t s);
-// One chunk of ray samples with the row count on the device (*n_rows_dev <= rows_max
-// <= the scratch rows): flat indices f0 .. f0 + *n_rows_dev - 1, ell[flat - f0].
-sb_status tc_ray_chunk(const ProbView &pv, const TcWs &t, const float *o32, const float *u32, const double *texit,
-                       int n_steps, int64_t f0, int rows_max, const int32_t *n_rows_dev, double *ell, cudaStream_t s);
 // y[e] = (float) x[e], e < n.
 void tc_to_f32(const double *x, float *y, size_t n, cudaStream_t s);
 
@@ -65,6 +55,25 @@ void carve_tc_quad(Carver &cv, TcQuadWs &q, int n_rays, int d, int K, int prec);
 // this process, else the heuristic one). pv needs a_k, mu, L and c.
 sb_status tc_ray_loglik_quad(const ProbView &pv, int n_rays, int n_steps, int prec, int bn, TcQuadWs q,
                              const double *u, const double *texit, double *ell_all, cudaStream_t s);
+// Rays from per-ray origins, x = o_r + tau u_r, in the same quadratic form:
+// z_k(o_r + tau u_r) = z_k(o_r) + tau w_rk, z_k(o_r) = o_r L_k - mu_k L_k from a split
+// GEMM of the origins (FP32 result, stored, with the FP32 -mu_k L_k added in the
+// epilogue), w_rk from a split GEMM of the directions whose epilogue takes the
+// dot products with the stored z_k(o_r).
+struct TcOriginWs {
+    float *zo, *off, *qp0;  // [rows][K][ald] z_k(o_r); [K][ald] -mu_k L_k (FP32); [rows][K][nct] |z|^2 partials
+    double *negm, *q0k;     // [K][d] -mu_k L_k (FP64); [K] scratch
+    double *q0r;            // [rows][K] |z_k(o_r)|^2
+};
+void carve_tc_origins(Carver &cv, TcOriginWs &o, int n_rays, int d, int K, int prec);
+// Split L_k^T into q.B2 and -mu_k L_k into o.off (once per problem and call).
+sb_status tc_quad_prepare_origins(const ProbView &pv, int prec, TcQuadWs q, TcOriginWs o, cudaStream_t s);
+// l at sample j of ray r < *n_rays_dev (flat r n_steps + j < *n_samples_dev, both on
+// the device, at most n_cap rays): ell[r n_steps + j], tau = ((j + 1) / n_steps)
+// t_exit,r. O, U: [n_cap][d] FP64 origins and unit directions. q must hold n_cap rays.
+sb_status tc_ray_origins_quad(const ProbView &pv, int n_cap, int n_steps, int prec, int bn, TcQuadWs q, TcOriginWs o,
+                              const double *O, const double *U, const double *texit, const int32_t *n_rays_dev,
+                              const int32_t *n_samples_dev, double *ell, cudaStream_t s);
 // Clears the per-walker bounds of the component skip (before a refinement).
 void tc_walkers_reset(const TcWs &t, int n, cudaStream_t s);
 // Slot of TcWs.p holding the per-walker distance bound the L-BFGS step writes.

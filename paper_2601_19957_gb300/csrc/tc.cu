@@ -61,23 +61,15 @@ constexpr int ROWB = 128;  // bytes of one K chunk per row (one swizzle atom row
 constexpr int THREADS = 192;
 constexpr int kMaxGroupList = 4096;  // store-pass groups compacted in shared memory
 
-// MODE_ZW: GEMM1 storing z (walkers/points); MODE_ZR: GEMM1 values only (ray samples); MODE_G: GEMM2;
+// MODE_ZW: GEMM1 storing z (walkers/points); MODE_ZR: GEMM1 values only (points); MODE_G: GEMM2;
 // MODE_Q: GEMM1 of split operands (ray directions, the quadratic form of a sunburst ray)
 enum { MODE_ZW = 0, MODE_ZR = 1, MODE_G = 2, MODE_Q = 3 };
 
 struct TcArgs {
-    int d, K, ld;           // ld: row stride of X (elements)
+    int d, K;
     const int32_t *n_rows_dev;
     int n_rows_max;
     const int32_t *act;     // compact row -> walker id (null: identity)
-    const float *X;         // walker points (FP32)
-    const float *mu32;      // [K][d]
-    const float *c32;       // [d] box centre
-    const double *u;        // [n_rays][d] ray directions (FP64)
-    const float *u32;       // [n_rays][d] ray directions (FP32 copy read by the producers)
-    const double *texit;    // [n_rays]
-    int n_steps;
-    long long flat0;
     void *Z;                // [K][z_rows][ldz] z rows, component-major (bf16 or fp32)
     int ldz, z_rows;
     float *qpart;           // [rows][K][n_ntile]
@@ -94,6 +86,12 @@ struct TcArgs {
     const float *qalpha;
     float *qpart1;
     int qseg, qald;
+    // MODE_Q origin pass (qzout given): z = acc + qoff[k][j] (qoff = -mu_k L_k in FP32) is
+    // stored to qzout[row][k][0 .. qald) and its |z|^2 summed into qpart; qalpha_rows: the
+    // alpha of a row is qalpha[row][k] (an origin pass's z) instead of qalpha[k]
+    float *qzout;
+    const float *qoff;
+    int qalpha_rows;
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -496,13 +494,28 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                         }
                     }
                 } else {
+                    if (MODE == MODE_Q && a.qzout) {
+                        // origin pass: z_k(o) = o L_k - mu_k L_k (zero past d: both terms are)
+                        const float *off = a.qoff + (size_t)ti.k * a.qald + col;
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) v[e] = __float_as_uint(__uint_as_float(v[e]) + off[e]);
+                        if (valid) {
+                            float *zo = a.qzout + ((size_t)n * K + ti.k) * a.qald + col;
+#pragma unroll
+                            for (int e = 0; e < 32; e += 4)
+                                *reinterpret_cast<float4 *>(zo + e) =
+                                    make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]),
+                                                __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
+                        }
+                    }
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
                         const float z = __uint_as_float(v[e]);
                         q2 = fmaf(z, z, q2);
                     }
-                    if (MODE == MODE_Q) {
-                        const float *al = a.qalpha + (size_t)ti.k * a.qald + col;  // zero past d
+                    if (MODE == MODE_Q && a.qalpha) {
+                        const float *al = a.qalpha + (a.qalpha_rows ? ((size_t)n * K + ti.k) : (size_t)ti.k) * a.qald +
+                                          col;  // zero past d
 #pragma unroll
                         for (int e = 0; e < 32; ++e) q1 = fmaf(al[e], __uint_as_float(v[e]), q1);
                     }
@@ -544,7 +557,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
             }
             if (MODE != MODE_G && !scaled && valid) {
                 a.qpart[((size_t)n * K + ti.k) * a.n_ntile + ti.nt] = q2;
-                if (MODE == MODE_Q) a.qpart1[((size_t)n * K + ti.k) * a.n_ntile + ti.nt] = q1;
+                if (MODE == MODE_Q && a.qpart1) a.qpart1[((size_t)n * K + ti.k) * a.n_ntile + ti.nt] = q1;
             }
             tc_fence_before();
             __syncwarp();
@@ -827,17 +840,14 @@ __global__ void __launch_bounds__(256) k_tc_lnorm_gram(int d, int K, int k0, int
 }
 
 // A operand of GEMM1: A1[k][n][i] = round(x_n[i] - mu_k[i]) formed in FP32; x_n is a
-// walker row (through the active list) or the ray sample c + t_j t_exit u_r.
+// walker row (through the active list).
 // Rows from n_rows up to the next multiple of 128 and columns >= d are zeroed.
 // One thread per (row, 16-byte column group): x is formed once and the thread
 // writes that column group for every component.
 template <int PREC>
-__global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int K, int rows_cap, int ldp,
-                                                   const int32_t *n_rows_dev, int n_rows_max, const int32_t *act,
-                                                   const float *X, int ld, const float *u32, const float *o32,
-                                                   const double *texit, int n_steps, long long flat0,
-                                                   const float *mu32, const float *c32, void *A1,
-                                                   const uint32_t *zmask) {
+__global__ void __launch_bounds__(256) k_tc_center(int d, int K, int rows_cap, int ldp, const int32_t *n_rows_dev,
+                                                   int n_rows_max, const int32_t *act, const float *X, int ld,
+                                                   const float *mu32, void *A1, const uint32_t *zmask) {
     constexpr int VE = (PREC == SB_PREC_BF16) ? 8 : 4;  // elements per 16-byte store
     const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
     int rows_pad = (n_rows + BM - 1) / BM * BM;
@@ -853,45 +863,20 @@ __global__ void __launch_bounds__(256) k_tc_center(int ray_mode, int d, int K, i
 #pragma unroll
     for (int q = 0; q < VE; ++q) x[q] = 0.f;
     if (live) {
-        if (!ray_mode) {
-            const float *xr = X + (size_t)(act ? act[n] : n) * ld;
-            if (vec && (ld & 3) == 0) {
+        const float *xr = X + (size_t)(act ? act[n] : n) * ld;
+        if (vec && (ld & 3) == 0) {
 #pragma unroll
-                for (int q = 0; q < VE; q += 4) {
-                    const float4 t = *reinterpret_cast<const float4 *>(xr + i0 + q);
-                    x[q] = t.x;
-                    x[q + 1] = t.y;
-                    x[q + 2] = t.z;
-                    x[q + 3] = t.w;
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < VE; ++q)
-                    if (i0 + q < d) x[q] = xr[i0 + q];
+            for (int q = 0; q < VE; q += 4) {
+                const float4 t = *reinterpret_cast<const float4 *>(xr + i0 + q);
+                x[q] = t.x;
+                x[q + 1] = t.y;
+                x[q + 2] = t.z;
+                x[q + 3] = t.w;
             }
         } else {
-            // FP32 position on the ray from its origin (the box centre, or the ray's own
-            // origin o32): the operand is rounded to bf16 / tf32 below anyway
-            const long long flat = flat0 + n;
-            const int ray = (int)(flat / n_steps), j = (int)(flat - (long long)ray * n_steps);
-            const float sc = ((float)(j + 1) / (float)n_steps) * (float)texit[ray];
-            const float *ur = u32 + (size_t)ray * d;
-            const float *orig = o32 ? o32 + (size_t)ray * d : c32;
-            if (vec) {
 #pragma unroll
-                for (int q = 0; q < VE; q += 4) {
-                    const float4 u4 = *reinterpret_cast<const float4 *>(ur + i0 + q);
-                    const float4 c4 = *reinterpret_cast<const float4 *>(orig + i0 + q);
-                    x[q] = fmaf(sc, u4.x, c4.x);
-                    x[q + 1] = fmaf(sc, u4.y, c4.y);
-                    x[q + 2] = fmaf(sc, u4.z, c4.z);
-                    x[q + 3] = fmaf(sc, u4.w, c4.w);
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < VE; ++q)
-                    if (i0 + q < d) x[q] = fmaf(sc, ur[i0 + q], orig[i0 + q]);
-            }
+            for (int q = 0; q < VE; ++q)
+                if (i0 + q < d) x[q] = xr[i0 + q];
         }
     }
     const uint64_t km = zmask ? block_kmask(zmask, n / BM, K) : ~0ull;  // pairs the |z|^2 pass visits
@@ -1076,9 +1061,8 @@ void launch_gemm_any(int prec, int mode, int bn, const CUtensorMap &mapA, const 
     }
 }
 
-void launch_center(const TcWs &t, int ray_mode, int d, int K, const int32_t *n_rows_dev, int n_rows_max,
-                   const int32_t *act, const float *X, const float *u32, const double *texit, int n_steps,
-                   long long flat0, cudaStream_t s, const uint32_t *zmask = nullptr, const float *o32 = nullptr) {
+void launch_center(const TcWs &t, int d, int K, const int32_t *n_rows_dev, int n_rows_max, const int32_t *act,
+                   const float *X, cudaStream_t s, const uint32_t *zmask = nullptr) {
     const int ldp = ldp_of(d, t.prec);
     const int ncg = ldp / (t.prec == SB_PREC_BF16 ? 8 : 4);
     int rows = (n_rows_max + BM - 1) / BM * BM;
@@ -1086,21 +1070,17 @@ void launch_center(const TcWs &t, int ray_mode, int d, int K, const int32_t *n_r
     const dim3 grid((unsigned)(((long long)rows * ncg + 255) / 256));
     note_launch();
     if (t.prec == SB_PREC_BF16)
-        k_tc_center<SB_PREC_BF16><<<grid, 256, 0, s>>>(ray_mode, d, K, (int)t.rows, ldp, n_rows_dev, n_rows_max, act,
-                                                      X, d, u32, o32, texit, n_steps, flat0, (const float *)t.p[2],
-                                                      (const float *)t.p[3], t.p[9], zmask);
+        k_tc_center<SB_PREC_BF16><<<grid, 256, 0, s>>>(d, K, (int)t.rows, ldp, n_rows_dev, n_rows_max, act, X, d,
+                                                      (const float *)t.p[2], t.p[9], zmask);
     else
-        k_tc_center<SB_PREC_TF32><<<grid, 256, 0, s>>>(ray_mode, d, K, (int)t.rows, ldp, n_rows_dev, n_rows_max, act,
-                                                      X, d, u32, o32, texit, n_steps, flat0, (const float *)t.p[2],
-                                                      (const float *)t.p[3], t.p[9], zmask);
+        k_tc_center<SB_PREC_TF32><<<grid, 256, 0, s>>>(d, K, (int)t.rows, ldp, n_rows_dev, n_rows_max, act, X, d,
+                                                      (const float *)t.p[2], t.p[9], zmask);
 }
 
 TcArgs base_args(const ProbView &pv, const TcWs &t) {
     TcArgs a{};
     a.d = pv.d;
     a.K = pv.K;
-    a.mu32 = (const float *)t.p[2];
-    a.c32 = (const float *)t.p[3];
     a.Z = t.p[4];
     a.ldz = ldz_of(pv.d);
     a.z_rows = (int)t.rows;
@@ -1304,44 +1284,13 @@ sb_status tc_prepare(const ProbView &pv, TcWs &t, cudaStream_t s, bool skip_boun
         k_tc_lcols<<<1184, 256, 0, s>>>(d, k0, kc, pv.L, (const float *)t.p[2], (float *)t.p[7]);
         TcArgs a = base_args(pv, t);
         a.n_rows_max = rows;
-        launch_center(t, 0, d, K, nullptr, rows, nullptr, (const float *)t.p[7], nullptr, nullptr, 1, 0, s);
+        launch_center(t, d, K, nullptr, rows, nullptr, (const float *)t.p[7], s);
         launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
         note_launch();
         k_tc_lnorm_gram<<<kc, 256, 0, s>>>(d, K, k0, a.n_ntile, a.qpart, (float *)t.p[15]);
     }
     return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
 }
-
-sb_status tc_ray_samples(const ProbView &pv, const TcWs &t, const float *o32, const float *u32, const double *texit,
-                         int n_steps, int64_t f_begin, int64_t f_end, double *ell, cudaStream_t s) {
-    for (int64_t f0 = f_begin; f0 < f_end; f0 += (int64_t)t.rows) {
-        const int rows = (int)((f_end - f0) < (int64_t)t.rows ? (f_end - f0) : (int64_t)t.rows);
-        TcArgs a = base_args(pv, t);
-        a.n_rows_max = rows;
-        launch_center(t, 1, pv.d, pv.K, nullptr, rows, nullptr, nullptr, u32, texit, n_steps, f0, s, nullptr, o32);
-        launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
-        note_launch();
-        k_tc_lse<<<(rows + 127) / 128, 128, 0, s>>>(1, pv.K, a.n_ntile, nullptr, rows, nullptr, a.qpart, pv.a,
-                                                    nullptr, nullptr, ell + (f0 - f_begin), nullptr, nullptr, nullptr,
-                                                    nullptr, nullptr);
-    }
-    return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
-}
-
-sb_status tc_ray_chunk(const ProbView &pv, const TcWs &t, const float *o32, const float *u32, const double *texit,
-                       int n_steps, int64_t f0, int rows_max, const int32_t *n_rows_dev, double *ell, cudaStream_t s) {
-    TcArgs a = base_args(pv, t);
-    a.n_rows_max = rows_max;
-    a.n_rows_dev = n_rows_dev;
-    launch_center(t, 1, pv.d, pv.K, n_rows_dev, rows_max, nullptr, nullptr, u32, texit, n_steps, f0, s, nullptr, o32);
-    launch_gemm_any(t.prec, MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
-    note_launch();
-    k_tc_lse<<<(rows_max + 127) / 128, 128, 0, s>>>(1, pv.K, a.n_ntile, n_rows_dev, rows_max, nullptr, a.qpart, pv.a,
-                                                    nullptr, nullptr, ell, nullptr, nullptr, nullptr, nullptr,
-                                                    nullptr);
-    return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
-}
-
 
 // ------------------------------------------------------------------ quadratic form of the rays
 // x split into hi + lo of the operand precision: hi = round(x), lo = round(x - hi)
@@ -1363,9 +1312,16 @@ __device__ __forceinline__ void put_op(void *base, size_t e, float v) {
         reinterpret_cast<float *>(base)[e] = v;
 }
 
-// A2[r][0 .. dK) = hi(u_r), A2[r][dK .. 2 dK) = lo(u_r); zeros past d and past n_rays
+// A2[r][0 .. dK) = hi(u_r), A2[r][dK .. 2 dK) = lo(u_r); zeros past d and past the ray
+// count (n_rays, or *n_dev when given), rows past the count's last 128-row block untouched
 template <int PREC>
-__global__ void k_q_split_rows(int n_rays, int rows, int d, int dK, const double *u, void *A2) {
+__global__ void k_q_split_rows(int n_rays, int rows, int d, int dK, const double *u, void *A2, const int32_t *n_dev) {
+    if (n_dev) {
+        const int c = *n_dev < n_rays ? *n_dev : n_rays;
+        const int rb = (c + BM - 1) / BM * BM;
+        n_rays = c;
+        rows = rb < rows ? rb : rows;
+    }
     const size_t tot = (size_t)rows * dK;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
         const int r = (int)(e / dK), i = (int)(e % dK);
@@ -1393,9 +1349,9 @@ __global__ void k_q_split_LT(int d, int K, int dK, const double *L, void *B2) {
     }
 }
 
-// z_k(c)_j = sum_{i >= j} (c_i - mu_k,i) L_k,ij in FP64: one CTA per (32 columns,
-// component), a lane per column (rows of L_k read 256 bytes at a time), the eight
-// warps over interleaved rows, their partials summed in a fixed order
+// z_k(c)_j = sum_{i >= j} (c_i - mu_k,i) L_k,ij in FP64 (c null: -mu_k L_k): one CTA per
+// (32 columns, component), a lane per column (rows of L_k read 256 bytes at a time),
+// the eight warps over interleaved rows, their partials summed in a fixed order
 __global__ void __launch_bounds__(256) k_q_zc(int d, const double *c, const double *mu, const double *L,
                                               double *zc) {
     const int k = blockIdx.y, j0 = blockIdx.x * 32, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1405,7 +1361,7 @@ __global__ void __launch_bounds__(256) k_q_zc(int d, const double *c, const doub
     double s = 0.0;
     if (j < d)
         for (int i = j0 + w; i < d; i += 8)
-            if (i >= j) s = fma(c[i] - mk[i], Lk[(size_t)i * d + j], s);
+            if (i >= j) s = fma(c ? c[i] - mk[i] : -mk[i], Lk[(size_t)i * d + j], s);
     __shared__ double part[8][32];
     part[w][lane] = s;
     __syncthreads();
@@ -1439,10 +1395,13 @@ __global__ void __launch_bounds__(256) k_q_alpha(int d, int ald, const double *z
 
 // (q1, q2)[r][k]: the FP64 sums of ray r's column-tile partials (FP32) of z_k(c) . w_rk
 // and |w_rk|^2, one thread per (ray, component)
+// (qp0 given: also q0r[r][k], the sum of the origin pass's |z_k(o_r)|^2 partials; K and
+// the ray count *n_dev bound the pairs when n_dev is given)
 __global__ void __launch_bounds__(256) k_q_sum(int n_rk, int n_ntile, const float *qp1, const float *qp2,
-                                               double2 *q12) {
+                                               double2 *q12, const float *qp0, double *q0r, int K,
+                                               const int32_t *n_dev) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n_rk) return;
+    if (e >= n_rk || (n_dev && e >= *n_dev * K)) return;
     const float *p1 = qp1 + (size_t)e * n_ntile;
     const float *p2 = qp2 + (size_t)e * n_ntile;
     double q1 = 0.0, q2 = 0.0;
@@ -1451,22 +1410,32 @@ __global__ void __launch_bounds__(256) k_q_sum(int n_rk, int n_ntile, const floa
         q2 += (double)p2[t];
     }
     q12[e] = make_double2(q1, q2);
+    if (qp0) {
+        const float *p0 = qp0 + (size_t)e * n_ntile;
+        double q0 = 0.0;
+        for (int t = 0; t < n_ntile; ++t) q0 += (double)p0[t];
+        q0r[e] = q0;
+    }
 }
 
 // l at sample j of ray r: |z_k|^2 = q0_k + 2 tau q1_rk + tau^2 q2_rk in FP64,
 // tau = ((j + 1) / n_steps) t_exit,r; the LSE as in k_tc_lse (FP64 terms, FP32
 // exponentials of the shifted terms). The threads of a warp mostly share a ray, so
 // its coefficients are broadcast loads.
+// (q0r given: q0 of ray r is q0r[r][k], the ray's own origin; ns_dev given: samples
+// past *ns_dev are skipped)
 __global__ void __launch_bounds__(256) k_q_ell(int n_rays, int n_steps, int K, const double *a_k, const double *q0,
-                                               const double2 *q12, const double *texit, double *ell) {
+                                               const double2 *q12, const double *texit, double *ell,
+                                               const double *q0r, const int32_t *ns_dev) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= (int64_t)n_rays * n_steps) return;
+    if (e >= (int64_t)n_rays * n_steps || (ns_dev && e >= *ns_dev)) return;
     const int r = (int)(e / n_steps), j = (int)(e - (int64_t)r * n_steps);
     const double tau = ((double)(j + 1) / (double)n_steps) * texit[r];
     const double2 *qr = q12 + (size_t)r * K;
+    const double *q0k = q0r ? q0r + (size_t)r * K : q0;
     auto term = [&](int k) {
         const double2 q = qr[k];
-        return a_k[k] - 0.5 * (q0[k] + tau * (2.0 * q.x + tau * q.y));
+        return a_k[k] - 0.5 * (q0k[k] + tau * (2.0 * q.x + tau * q.y));
     };
     double emax = -INFINITY;
     for (int k = 0; k < K; ++k) emax = fmax(emax, term(k));
@@ -1500,10 +1469,10 @@ sb_status tc_ray_loglik_quad(const ProbView &pv, int n_rays, int n_steps, int pr
     note_launch();
     note_launch();
     if (prec == SB_PREC_BF16) {
-        k_q_split_rows<SB_PREC_BF16><<<gs, 256, 0, s>>>(n_rays, q.rows, d, q.dK, u, q.A2);
+        k_q_split_rows<SB_PREC_BF16><<<gs, 256, 0, s>>>(n_rays, q.rows, d, q.dK, u, q.A2, nullptr);
         k_q_split_LT<SB_PREC_BF16><<<gs, 256, 0, s>>>(d, K, q.dK, pv.L, q.B2);
     } else {
-        k_q_split_rows<SB_PREC_TF32><<<gs, 256, 0, s>>>(n_rays, q.rows, d, q.dK, u, q.A2);
+        k_q_split_rows<SB_PREC_TF32><<<gs, 256, 0, s>>>(n_rays, q.rows, d, q.dK, u, q.A2, nullptr);
         k_q_split_LT<SB_PREC_TF32><<<gs, 256, 0, s>>>(d, K, q.dK, pv.L, q.B2);
     }
     // z_k(c) in FP64 (one point), then its FP32 copy and |z_k(c)|^2
@@ -1531,9 +1500,92 @@ sb_status tc_ray_loglik_quad(const ProbView &pv, int n_rays, int n_steps, int pr
     launch_gemm_any(prec, MODE_Q, bn, q.mapU, q.mapL, a, s);
     const int64_t ns = (int64_t)n_rays * n_steps;
     note_launch();
-    k_q_sum<<<(unsigned)((n_rays * K + 255) / 256), 256, 0, s>>>(n_rays * K, a.n_ntile, q.qpart1, q.qpart2, q.q12);
+    k_q_sum<<<(unsigned)((n_rays * K + 255) / 256), 256, 0, s>>>(n_rays * K, a.n_ntile, q.qpart1, q.qpart2, q.q12,
+                                                                 nullptr, nullptr, K, nullptr);
     note_launch();
-    k_q_ell<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(n_rays, n_steps, K, pv.a, q.q0, q.q12, texit, ell_all);
+    k_q_ell<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(n_rays, n_steps, K, pv.a, q.q0, q.q12, texit, ell_all,
+                                                         nullptr, nullptr);
+    return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
+}
+
+void carve_tc_origins(Carver &cv, TcOriginWs &o, int n_rays, int d, int K, int prec) {
+    (void)prec;
+    const int nct = (d + 63) / 64;
+    const int rows = (n_rays + BM - 1) / BM * BM;
+    const int ald = (d + 255) / 256 * 256;
+    o.zo = cv.take<float>((size_t)rows * K * ald);
+    o.off = cv.take<float>((size_t)K * ald);
+    o.qp0 = cv.take<float>((size_t)rows * K * nct);
+    o.negm = cv.take<double>((size_t)K * d);
+    o.q0k = cv.take<double>((size_t)K);
+    o.q0r = cv.take<double>((size_t)rows * K);
+}
+
+sb_status tc_quad_prepare_origins(const ProbView &pv, int prec, TcQuadWs q, TcOriginWs o, cudaStream_t s) {
+    const int d = pv.d, K = pv.K;
+    const unsigned gs = 1184;
+    note_launch();
+    if (prec == SB_PREC_BF16)
+        k_q_split_LT<SB_PREC_BF16><<<gs, 256, 0, s>>>(d, K, q.dK, pv.L, q.B2);
+    else
+        k_q_split_LT<SB_PREC_TF32><<<gs, 256, 0, s>>>(d, K, q.dK, pv.L, q.B2);
+    // -mu_k L_k in FP64, then its FP32 copy (the origin pass's offset)
+    note_launch();
+    k_q_zc<<<dim3((unsigned)((d + 31) / 32), (unsigned)K), 256, 0, s>>>(d, nullptr, pv.mu, pv.L, o.negm);
+    note_launch();
+    k_q_alpha<<<K, 256, 0, s>>>(d, q.ald, o.negm, o.off, o.q0k);
+    return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
+}
+
+sb_status tc_ray_origins_quad(const ProbView &pv, int n_cap, int n_steps, int prec, int bn, TcQuadWs q, TcOriginWs o,
+                              const double *O, const double *U, const double *texit, const int32_t *n_rays_dev,
+                              const int32_t *n_samples_dev, double *ell, cudaStream_t s) {
+    const int d = pv.d, K = pv.K;
+    if (bn <= 0) bn = tc_tuned_tile(d, K, prec);
+    if (bn <= 0) bn = bn_of(d);
+    const unsigned gs = 1184;
+    if (!make_map(&q.mapU, q.A2, 2 * q.dK, q.rows, 1, 2 * q.dK, prec, BM) ||
+        !make_map(&q.mapL, q.B2, 2 * q.dK, d, K, 2 * q.dK, prec, bn))
+        return SB_ERR_CUDA;
+    auto split = [&](const double *src) {
+        note_launch();
+        if (prec == SB_PREC_BF16)
+            k_q_split_rows<SB_PREC_BF16><<<gs, 256, 0, s>>>(n_cap, q.rows, d, q.dK, src, q.A2, n_rays_dev);
+        else
+            k_q_split_rows<SB_PREC_TF32><<<gs, 256, 0, s>>>(n_cap, q.rows, d, q.dK, src, q.A2, n_rays_dev);
+    };
+    TcArgs a{};
+    a.d = d;
+    a.K = K;
+    a.prof = -1;
+    a.n_ntile = (d + bn - 1) / bn;
+    a.err = pv.status;
+    a.n_rows_max = n_cap;
+    a.n_rows_dev = n_rays_dev;
+    a.qseg = q.dK;
+    a.qald = q.ald;
+    // origins: z_k(o_r) stored (FP32) with its |z|^2 partials
+    split(O);
+    a.qzout = o.zo;
+    a.qoff = o.off;
+    a.qpart = o.qp0;
+    launch_gemm_any(prec, MODE_Q, bn, q.mapU, q.mapL, a, s);
+    // directions: w_rk = L_k^T u_r, z_k(o_r) . w_rk and |w_rk|^2 partials
+    split(U);
+    a.qzout = nullptr;
+    a.qoff = nullptr;
+    a.qalpha = o.zo;
+    a.qalpha_rows = 1;
+    a.qpart = q.qpart2;
+    a.qpart1 = q.qpart1;
+    launch_gemm_any(prec, MODE_Q, bn, q.mapU, q.mapL, a, s);
+    note_launch();
+    k_q_sum<<<(unsigned)((n_cap * K + 255) / 256), 256, 0, s>>>(n_cap * K, a.n_ntile, q.qpart1, q.qpart2, q.q12, o.qp0,
+                                                                o.q0r, K, n_rays_dev);
+    const int64_t ns = (int64_t)n_cap * n_steps;
+    note_launch();
+    k_q_ell<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(n_cap, n_steps, K, pv.a, nullptr, q.q12, texit, ell, o.q0r,
+                                                         n_samples_dev);
     return cudaGetLastError() == cudaSuccess ? SB_OK : SB_ERR_CUDA;
 }
 
@@ -1564,7 +1616,7 @@ void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, cons
     k_tc_need<<<(n + 127) / 128, 128, 0, s>>>(pv.K, n_act, n, act, pv.a, (const float *)t.p[15], (float *)t.p[11],
                                               (const int32_t *)t.p[12], (const float *)t.p[13],
                                               (const float *)t.p[14], zmask);
-    launch_center(t, 0, pv.d, pv.K, n_act, n, act, XT, nullptr, nullptr, 1, 0, s, zmask);
+    launch_center(t, pv.d, pv.K, n_act, n, act, XT, s, zmask);
     a.zmask = zmask;
     a.rflag = nullptr;  // GEMM1 over the kept pairs: |z|^2 partials and z itself
     launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
@@ -1593,7 +1645,7 @@ sb_status tc_loglik_points(const ProbView &pv, const sb_config *c, const TcWs &t
     TcArgs a = base_args(pv, t);
     a.n_rows_max = n;
     a.prof = PROF_TC_Z_WALKERS;
-    launch_center(t, 0, pv.d, pv.K, nullptr, n, nullptr, X, nullptr, nullptr, 1, 0, s);
+    launch_center(t, pv.d, pv.K, nullptr, n, nullptr, X, s);
     // with the gradient, GEMM1 also stores z (the A operand of GEMM2 once scaled by r)
     a.rflag = nullptr;
     launch_gemm_any(t.prec, grad ? MODE_ZW : MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);

@@ -152,16 +152,16 @@ def sigmas(inst, X, prec):
     return s_l, np.sqrt(var_g)
 
 
-def _quad_parts(inst, X):
-    """Per sample (x = c + tau u on a sunburst ray from the box centre c): tau = |x - c|,
-    u = (x - c) / tau, and the components' a_k."""
+def _quad_parts(inst, X, O=None):
+    """Per sample x = o + tau u on a ray from its origin o (O [n, d], the box centre when
+    None): tau = |x - o|, u = (x - o) / tau, the origins, and the components' a_k."""
     X = np.asarray(X, dtype=np.float64)
-    c = 0.5 * (inst.lo + inst.hi)
-    D = X - c
+    O = np.broadcast_to(0.5 * (inst.lo + inst.hi), X.shape) if O is None else np.asarray(O, dtype=np.float64)
+    D = X - O
     tau = np.sqrt((D * D).sum(1))
     U = D / np.where(tau > 0, tau, 1.0)[:, None]
     a_k = inst.log_w - 0.5 * inst.d * np.log(2 * np.pi) + np.log(np.diagonal(inst.L, axis1=1, axis2=2)).sum(1)
-    return c, tau, U, a_k
+    return O, tau, U, a_k
 
 
 def _quad_form(prec, d):
@@ -177,38 +177,57 @@ def _quad_form(prec, d):
     return 3 * up * up, up ** 4, 3 * d, 256
 
 
-def quad_bounds(inst, X, prec):
+def _quad_terms(inst, X, prec, O):
+    """Per component: alpha = z_k(o) (exact), the origins' product o L_k and -mu_k L_k
+    (origin pass), w = L_k^T u, z(tau) = alpha + tau w, for every sample."""
+    Og, tau, U, a_k = _quad_parts(inst, X, O)
+    for k in range(inst.K):
+        Lk = inst.L[k]
+        oL = Og @ Lk
+        mL = inst.mu[k] @ Lk
+        al = oL - mL[None, :] if O is not None else np.broadcast_to((Og[0] - inst.mu[k]) @ Lk, oL.shape)
+        W = U @ Lk
+        yield k, Lk, Og, tau, U, a_k, oL, mL, al, W, al + tau[:, None] * W
+
+
+def quad_bounds(inst, X, prec, O=None):
     """Worst case of a quadratic ray pass at ray samples X [n, d] (prec as _quad_form):
     w_j = sum_i u_i L_ij with the operand error of _quad_form and FP32 accumulation over
     n_acc terms; q1 = alpha . w and q2 = |w|^2 summed in FP32 over column tiles of
-    n_tile, the tiles in FP64; alpha in FP32; |z|^2 = q0 + 2 tau q1 + tau^2 q2 in FP64.
-    With E_j = (e_op + n_acc 2^-23)(1 + u_p)^2 sum_i |u_i| |L_ij|:
+    n_tile, the tiles in FP64; |z|^2 = q0 + 2 tau q1 + tau^2 q2 in FP64. With
+    E_j = (e_op + n_acc 2^-23)(1 + u_p)^2 sum_i |u_i| |L_ij|:
         d|z|^2 <= 2 tau sum_j |z_j| E_j + tau^2 sum_j E_j^2
                   + n_tile 2^-23 (tau^2 q2 + 2 tau sum_j |alpha_j w_j|) + 2^-24 2 tau sum_j |alpha_j w_j|
-                  + 8 2^-53 (q0 + 2 tau |q1| + tau^2 q2),
-    and l lies between LSE(e - d|z|^2 / 2) and LSE(e + d|z|^2 / 2), plus the FP32 LSE floor.
+                  + 8 2^-53 (q0 + 2 tau |q1| + tau^2 q2).
+    Rays from the box centre (O None) take alpha = z_k(c) in FP64 (q0 exact, alpha
+    rounded to FP32 for q1). Rays from origins O (the origin pass): alpha = o L_k - mu_k L_k
+    from the same split products plus the FP32 -mu_k L_k, kept in FP32, so alpha_j is off
+    by Eo_j = (e_op + n_acc 2^-23)(1 + u_p)^2 sum_i |o_i| |L_ij| + 2^-23 (|(o L)_j| +
+    |(mu L)_j| + |alpha_j|), which adds 2 sum_j |z_j| Eo_j + sum_j (Eo_j + tau E_j)^2 - ... (taken
+    whole: (Eo_j + tau E_j) in place of tau E_j) and n_tile 2^-23 q0 for q0's tiles.
+    l lies between LSE(e - d|z|^2 / 2) and LSE(e + d|z|^2 / 2), plus the FP32 LSE floor.
     Returns (B_l [n], l [n])."""
-    c, tau, U, a_k = _quad_parts(inst, X)
     d, K = inst.d, inst.K
     e_op, _, n_acc, n_tile = _quad_form(prec, d)
     up = U_P.get(prec, U32)
     cb = (e_op + n_acc * 2.0 ** -23) * (1 + up) ** 2
-    q = np.empty((X.shape[0], K))
-    dq = np.empty((X.shape[0], K))
-    for k in range(K):
-        Lk = inst.L[k]
-        al = (c - inst.mu[k]) @ Lk
-        W = U @ Lk
-        Z = al[None, :] + tau[:, None] * W
-        E = cb * (np.abs(U) @ np.abs(Lk))
-        aw = np.abs(al[None, :] * W).sum(1)
+    n = np.asarray(X).shape[0]
+    q = np.empty((n, K))
+    dq = np.empty((n, K))
+    for k, Lk, Og, tau, U, a_k, oL, mL, al, W, Z in _quad_terms(inst, X, prec, O):
+        E = tau[:, None] * cb * (np.abs(U) @ np.abs(Lk))
+        if O is not None:
+            E = E + cb * (np.abs(Og) @ np.abs(Lk)) + 2.0 ** -23 * (np.abs(oL) + np.abs(mL)[None, :] + np.abs(al))
+        aw = np.abs(al * W).sum(1)
         q2 = (W * W).sum(1)
-        q1 = (al[None, :] * W).sum(1)
-        q0 = float(al @ al)
+        q1 = (al * W).sum(1)
+        q0 = (al * al).sum(1)
         q[:, k] = (Z * Z).sum(1)
-        dq[:, k] = (2 * tau * (np.abs(Z) * E).sum(1) + tau ** 2 * (E * E).sum(1)
+        dq[:, k] = (2 * (np.abs(Z) * E).sum(1) + (E * E).sum(1)
                     + n_tile * 2.0 ** -23 * (tau ** 2 * q2 + 2 * tau * aw) + 2.0 ** -24 * 2 * tau * aw
                     + 8 * 2.0 ** -53 * (q0 + 2 * tau * np.abs(q1) + tau ** 2 * q2))
+        if O is not None:
+            dq[:, k] += n_tile * 2.0 ** -23 * q0
     ee = a_k[None, :] - 0.5 * q
     ell = _lse(ee)
     hi = _lse(ee + 0.5 * dq)
@@ -216,65 +235,70 @@ def quad_bounds(inst, X, prec):
     return np.maximum(hi - ell, ell - lo) + 2.0 ** -20 * (1 + K), ell
 
 
-def quad_sigmas(inst, X, prec):
+def quad_sigmas(inst, X, prec, O=None):
     """Standard deviation of a quadratic ray pass's error at ray samples X (prec as
     _quad_form) under the first-order model of independent roundings: each product
     u_i L_ij carries the operand variance of _quad_form, an FP32 accumulation step
     v32 = u32^2 / 3 of the partial sum (n_acc steps for w_j, n_tile for the tile partials
-    of q1 and q2). To first order d|z|^2 = 2 tau z . dw plus the tile partials' rounding:
-        Var d|z_k|^2 = 4 tau^2 sum_j z_j^2 Var dw_j
-                       + n_tile v32 (tau^4 q2^2 + 4 tau^2 (sum_j |alpha_j w_j|)^2) / n_tiles
-                       + 4 tau^2 v32 sum_j (alpha_j w_j)^2,
-    Var dw_j = (v_op + n_acc v32) sum_i u_i^2 L_ij^2, and dl = -1/2 sum_k r_k d|z_k|^2
+    of q0, q1 and q2). To first order d|z|^2 = 2 z . (d alpha + tau dw) plus the tile
+    partials' rounding:
+        Var d|z_k|^2 = 4 sum_j z_j^2 (Var d alpha_j + tau^2 Var dw_j)
+                       + n_tile v32 (tau^4 q2^2 + 4 tau^2 (sum_j |alpha_j w_j|)^2 [+ q0^2]) / n_tiles,
+    Var dw_j = (v_op + n_acc v32) sum_i u_i^2 L_ij^2; from the box centre d alpha is the
+    FP32 rounding of alpha in q1 alone (4 tau^2 v32 sum_j (alpha_j w_j)^2), from origins
+    (the origin pass, q0 from FP32 tiles too) Var d alpha_j = (v_op + n_acc v32)
+    sum_i o_i^2 L_ij^2 + v32 ((o L)_j^2 + (mu L)_j^2 + alpha_j^2). dl = -1/2 sum_k r_k d|z_k|^2
     (independent components) with the FP32 LSE floor 4 u32."""
-    c, tau, U, a_k = _quad_parts(inst, X)
     v32 = U32 ** 2 / 3.0
     d, K = inst.d, inst.K
     _, v_op, n_acc, n_tile = _quad_form(prec, d)
     n_tiles = max(1, -(-d // n_tile))
-    q = np.empty((X.shape[0], K))
-    vq = np.empty((X.shape[0], K))
-    for k in range(K):
-        Lk = inst.L[k]
-        al = (c - inst.mu[k]) @ Lk
-        W = U @ Lk
-        Z = al[None, :] + tau[:, None] * W
-        Vw = (v_op + n_acc * v32) * ((U * U) @ (Lk * Lk))
-        aw = np.abs(al[None, :] * W).sum(1)
+    n = np.asarray(X).shape[0]
+    q = np.empty((n, K))
+    vq = np.empty((n, K))
+    for k, Lk, Og, tau, U, a_k, oL, mL, al, W, Z in _quad_terms(inst, X, prec, O):
+        L2 = Lk * Lk
+        Vw = (v_op + n_acc * v32) * ((U * U) @ L2)
+        aw = np.abs(al * W).sum(1)
         q2 = (W * W).sum(1)
+        q0 = (al * al).sum(1)
         q[:, k] = (Z * Z).sum(1)
-        vq[:, k] = (4 * tau ** 2 * (Z * Z * Vw).sum(1)
-                    + n_tile * v32 * (tau ** 4 * q2 ** 2 + 4 * tau ** 2 * aw ** 2) / n_tiles
-                    + 4 * tau ** 2 * v32 * ((al[None, :] * W) ** 2).sum(1))
+        tiles = tau ** 4 * q2 ** 2 + 4 * tau ** 2 * aw ** 2
+        if O is None:
+            Va = 0.0
+            extra = 4 * tau ** 2 * v32 * ((al * W) ** 2).sum(1)
+        else:
+            Va = (v_op + n_acc * v32) * ((Og * Og) @ L2) + v32 * (oL ** 2 + mL[None, :] ** 2 + al ** 2)
+            extra = 0.0
+            tiles = tiles + q0 ** 2
+        vq[:, k] = (4 * (Z * Z * (Va + tau[:, None] ** 2 * Vw)).sum(1)
+                    + n_tile * v32 * tiles / n_tiles + extra)
     ee = a_k[None, :] - 0.5 * q
     r = np.exp(ee - _lse(ee)[:, None])
     return np.sqrt(0.25 * (r * r * vq).sum(1) + (4 * U32) ** 2)
 
 
-def quad_bias(inst, X, prec):
+def quad_bias(inst, X, prec, O=None):
     """Signed first-order effect on l of tensor-core accumulation steps that each shrink
-    the accumulator of w_j = sum_i u_i L_ij by 2^-24 of its magnitude (rounding toward
-    zero). The split products run the small ones first, so only the last segment's
-    n_j = ceil((d - j) / k) + 1 steps add to an accumulator of full magnitude (k the
-    products one instruction sums: 16 for bf16, 8 for tf32) and w_j becomes
-    (1 - n_j 2^-24) w_j:
-        d|z_k|^2 = -2 tau sum_j n_j 2^-24 z_kj w_kj,   dl = -1/2 sum_k r_k d|z_k|^2.
+    an accumulator by 2^-24 of its magnitude (rounding toward zero). The split products
+    run the small ones first, so only the last segment's n_j = ceil((d - j) / k) + 1 steps
+    add to an accumulator of full magnitude (k the products one instruction sums: 16 for
+    bf16, 8 for tf32): w_j becomes (1 - n_j 2^-24) w_j and, for the origin pass, (o L)_j
+    becomes (1 - n_j 2^-24) (o L)_j, so that
+        d|z_k|^2 = -2 sum_j n_j 2^-24 z_kj (tau w_kj [+ (o L_k)_j]),   dl = -1/2 sum_k r_k d|z_k|^2.
     Zero for the FP32 SIMT form (prec 0: round-to-nearest FMA chains)."""
-    c, tau, U, a_k = _quad_parts(inst, X)
+    n = np.asarray(X).shape[0]
     if prec == 0:
-        return np.zeros(X.shape[0])
+        return np.zeros(n)
     d, K = inst.d, inst.K
     kin = 16 if prec == 2 else 8
     nj = np.ceil((d - np.arange(d)) / kin) + 1
-    q = np.empty((X.shape[0], K))
-    dq = np.empty((X.shape[0], K))
-    for k in range(K):
-        Lk = inst.L[k]
-        al = (c - inst.mu[k]) @ Lk
-        W = U @ Lk
-        Z = al[None, :] + tau[:, None] * W
+    q = np.empty((n, K))
+    dq = np.empty((n, K))
+    for k, Lk, Og, tau, U, a_k, oL, mL, al, W, Z in _quad_terms(inst, X, prec, O):
         q[:, k] = (Z * Z).sum(1)
-        dq[:, k] = -2 * tau * 2.0 ** -24 * (Z * W * nj[None, :]).sum(1)
+        acc = tau[:, None] * W + (oL if O is not None else 0.0)
+        dq[:, k] = -2 * 2.0 ** -24 * (Z * acc * nj[None, :]).sum(1)
     ee = a_k[None, :] - 0.5 * q
     r = np.exp(ee - _lse(ee)[:, None])
     return -0.5 * (r * dq).sum(1)
@@ -290,11 +314,12 @@ def quad_bias(inst, X, prec):
 C_Q = 4.0
 
 
-def check_ray_samples(inst, X, dl, prec):
-    """Asserts the errors dl = l_gpu - l_oracle at ray samples X fit the model above."""
-    s = quad_sigmas(inst, X, prec)
-    B, _ = quad_bounds(inst, X, prec)
-    bias = quad_bias(inst, X, prec)
+def check_ray_samples(inst, X, dl, prec, O=None):
+    """Asserts the errors dl = l_gpu - l_oracle at ray samples X (rays from the box
+    centre, or from the per-sample origins O) fit the model above."""
+    s = quad_sigmas(inst, X, prec, O)
+    B, _ = quad_bounds(inst, X, prec, O)
+    bias = quad_bias(inst, X, prec, O)
     out = np.maximum(np.minimum(0.0, bias) - dl, dl - np.maximum(0.0, bias)) / s
     assert out.max() <= C_Q, (int(np.argmax(out)), float(out.max()))
     assert (np.abs(dl) <= B).all(), float((np.abs(dl) / B).max())

@@ -148,3 +148,21 @@ def test_ray_loglik_quad_rejects_bad_arguments_on_the_host():
     assert L.sb_ray_loglik_quad_workspace_bytes(C.byref(p), 2, 4) > 0
     assert L.sb_ray_loglik_quad_workspace_bytes(C.byref(p), 3, 4) > 0
     assert L.sb_ray_loglik_quad_workspace_bytes(C.byref(p), 4, 4) == 0
+
+
+def test_ray_loglik_origins_rejects_bad_arguments_on_the_host():
+    p = _fake_problem(8, 1)
+    L = sb.lib()
+    buf = (C.c_char * 16)()
+    for form in (0, 1, 4):
+        assert L.sb_ray_loglik_origins(C.byref(p), form, buf, buf, 4, 8, buf, None, buf, C.c_size_t(16),
+                                       None) == sb.SB_ERR_INVALID_ARG
+        assert L.sb_ray_loglik_origins_workspace_bytes(C.byref(p), form, 4) == 0
+    assert L.sb_ray_loglik_origins(C.byref(p), 2, buf, buf, 0, 8, buf, None, buf, C.c_size_t(16),
+                                   None) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_ray_loglik_origins(C.byref(p), 2, buf, buf, 4, 0, buf, None, buf, C.c_size_t(16),
+                                   None) == sb.SB_ERR_INVALID_ARG
+    assert L.sb_ray_loglik_origins(C.byref(p), 3, buf, buf, 4, 8, buf, None, buf, C.c_size_t(16),
+                                   None) == sb.SB_ERR_WORKSPACE
+    assert L.sb_ray_loglik_origins_workspace_bytes(C.byref(p), 2, 4) > 0
+    assert L.sb_ray_loglik_origins_workspace_bytes(C.byref(p), 3, 4) > 0

@@ -186,3 +186,36 @@ def test_ray_loglik_quad_mixed_forms_match_oracle(form, d, K, n_rays, n_steps):
     X = (c[None, None, :] + tau[:, :, None] * u[:, None, :]).reshape(-1, d)
     prec = {1: 0, 2: sb.PREC_BF16, 3: sb.PREC_TF32}[form]
     tc_bound.check_ray_samples(inst, X, (ell - ref).reshape(-1), prec)
+
+
+@pytest.mark.parametrize("form", [2, 3])
+@pytest.mark.parametrize("d,K,n_rays,n_steps", [(64, 4, 130, 16), (300, 3, 70, 24), (1024, 8, 64, 16), (7, 2, 40, 8),
+                                                (1, 1, 9, 5)])
+def test_ray_loglik_origins_matches_oracle(form, d, K, n_rays, n_steps):
+    """Rays from per-ray origins (the reseeding rays of ChiSao): half the origins near a
+    component mean (Golden Rooster rays start at peaks), half uniform in the box (Repulse
+    Monkey rays start at unconverged samples). t_exit against its definition (bit for
+    bit), l at every sample against the FP64 oracle within the quadratic ray pass's error
+    model for an origin pass (tc_bound.check_ray_samples with the origins)."""
+    if d == 1024:
+        inst = workload(4)[0][0]
+    else:
+        inst = make_instance(d, K, 800 + d, s_range=(0.05, 0.5), mean_box=(-6, 6), sep=8.0 if K > 1 else 0.0)
+    rng = np.random.default_rng(900 + d)
+    O = rng.uniform(inst.lo, inst.hi, (n_rays, d))
+    near = np.arange(n_rays) % 2 == 0
+    ks = rng.integers(0, inst.K, n_rays)
+    O[near] = np.clip(inst.mu[ks[near]] + 0.01 * rng.standard_normal((near.sum(), d)), inst.lo, inst.hi)
+    U = rng.standard_normal((n_rays, d))
+    U /= np.linalg.norm(U, axis=1, keepdims=True)
+    ell, te = sb.ray_loglik_origins(sb.Problem(inst), torch.as_tensor(O), torch.as_tensor(U), n_steps, form=form)
+    ell, te = ell.cpu().numpy(), te.cpu().numpy()
+    with np.errstate(divide="ignore", invalid="ignore"):
+        cand = np.where(U > 0, (inst.hi - O) / U, np.where(U < 0, (inst.lo - O) / U, np.inf))
+    np.testing.assert_array_equal(te, cand.min(1))
+    tau = (np.arange(1, n_steps + 1) / n_steps)[None, :] * te[:, None]
+    X = (O[:, None, :] + tau[:, :, None] * U[:, None, :]).reshape(-1, d)
+    Orep = np.repeat(O, n_steps, axis=0)
+    ref = np.array([oracle.loglik(inst, x) for x in X])
+    prec = {2: sb.PREC_BF16, 3: sb.PREC_TF32}[form]
+    tc_bound.check_ray_samples(inst, X, ell.reshape(-1) - ref, prec, O=Orep)
