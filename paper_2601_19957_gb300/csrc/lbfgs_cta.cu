@@ -858,20 +858,20 @@ __global__ void __launch_bounds__(CT, Cfg<CT>::MINB) k_lbfgs_cta(LbfgsArgs<float
 // (128-row block, component) pairs no row of the block needs, and walkers of
 // different basins interleaved in one block would make every block need every
 // component. Skipped terms are exactly zero, so the grouping changes no result.
-// One CTA, two passes over the list, both in chunks of kCompactE consecutive entries
-// per thread (so lane, then warp order is list order). Pass 1 gathers each entry's
-// walker, status and key (independent loads), packs (bucket, walker) and counts the
-// buckets (per warp, then across warps); their exclusive sums give each bucket's
-// first output slot. Pass 2: per bucket present in a warp, a lane's rank is a warp
-// scan of the per-lane counts and the warp's offset a scan over the warps' totals
-// after the bucket's entries from earlier chunks; every entry goes straight to its
-// slot of act, which pass 1 has read in full. A list longer than one chunk parks the
-// packed entries in tmp between the passes; a shorter one keeps them in registers.
+// Two launches over G CTAs, CTA c owning the list entries [c R, (c + 1) R), R = E x
+// threads, E consecutive entries per thread (lane, then warp, then CTA order is list
+// order). The first gathers every entry's walker, status and key (independent loads,
+// spread over the GPU), packs (bucket, walker) into tmp and counts the buckets per
+// CTA; the second reads the G x buckets count table, so CTA c knows where each
+// bucket starts and how many entries of it the CTAs before c hold, ranks its entries
+// per warp and places each in act. tmp decouples the two, as entries move between
+// CTAs' ranges.
 constexpr int kSortBuckets = kMaxK + 1;
-constexpr int kCompactE = 16;                    // consecutive entries per thread
-constexpr int kCompactChunk = 1024 * kCompactE;  // entries per chunk
-constexpr int kPackShift = 25;                   // packed entry: bucket << 25 | walker
-constexpr uint32_t kPackDrop = 0xffffffffu;      // a dropped entry (bucket field 127)
+constexpr int kCompactE = 16;        // most entries per thread
+constexpr int kCkThreads = 256;      // threads per CTA
+constexpr int kCkMinBlocks = 64;     // CTAs for a short list (one entry per thread up to 16384)
+constexpr int kPackShift = 25;       // packed entry: bucket << 25 | walker
+constexpr uint32_t kPackDrop = 0xffffffffu;  // a dropped entry (bucket field 127)
 static_assert(kSortBuckets < 127, "the bucket field holds 7 bits");
 
 __device__ __forceinline__ int warp_incl_scan(int v) {
@@ -885,118 +885,141 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
 }
 
 // Buckets present in this warp's entries (bit b for bucket b < nb).
-__device__ __forceinline__ uint64_t warp_buckets(const uint32_t (&pk)[kCompactE], int nb) {
+__device__ __forceinline__ uint64_t warp_buckets(const uint32_t (&pk)[kCompactE], int E, int nb) {
     uint64_t present = 0;
 #pragma unroll
     for (int e = 0; e < kCompactE; ++e) {
         const uint32_t b = pk[e] >> kPackShift;
-        if (b < (uint32_t)nb) present |= 1ull << b;
+        if (e < E && b < (uint32_t)nb) present |= 1ull << b;
     }
     return (uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)present) |
            ((uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)(present >> 32)) << 32);
 }
-__device__ __forceinline__ int count_bucket(const uint32_t (&pk)[kCompactE], int b) {
+__device__ __forceinline__ int count_bucket(const uint32_t (&pk)[kCompactE], int E, int b) {
     int cnt = 0;
 #pragma unroll
-    for (int e = 0; e < kCompactE; ++e) cnt += (pk[e] >> kPackShift) == (uint32_t)b;
+    for (int e = 0; e < kCompactE; ++e) cnt += (e < E && (pk[e] >> kPackShift) == (uint32_t)b);
     return cnt;
 }
+// entries per thread for prev entries over G CTAs
+__device__ __forceinline__ int compact_E(int prev, int G) {
+    const int per = G * kCkThreads;
+    return (prev + per - 1) / per;
+}
 
-__global__ void __launch_bounds__(1024) k_lbfgs_compact_by_key(const WalkerState<float> *st, int32_t *act,
-                                                               int32_t *n_act, int64_t *n_evals, const int32_t *key,
-                                                               int K, uint32_t *tmp) {
-    __shared__ int total[kSortBuckets], base[kSortBuckets];
-    __shared__ int wtot[32][kSortBuckets], woff[32][kSortBuckets];
-    const int prev = *n_act;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nb = K + 1;
-    const bool parked = prev > kCompactChunk;
+// cnt: [G][nb] bucket counts, then cnt[G nb] = the list length before compaction
+__global__ void __launch_bounds__(kCkThreads) k_compact_count(const WalkerState<float> *st, const int32_t *act,
+                                                              const int32_t *n_act, const int32_t *key, int K,
+                                                              uint32_t *tmp, int32_t *cnt) {
+    __shared__ int total[kSortBuckets];
+    const int prev = *n_act, G = (int)gridDim.x, nb = K + 1;
+    const int E = compact_E(prev, G);
+    const int lane = threadIdx.x & 31;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) total[b] = 0;
-    if (threadIdx.x == 0 && n_evals) *n_evals += prev;
     __syncthreads();
+    const int s0 = ((int)blockIdx.x * kCkThreads + (int)threadIdx.x) * E;
+    int w[kCompactE];
     uint32_t pk[kCompactE];
-    // pass 1
-    for (int c0 = 0; c0 < prev; c0 += kCompactChunk) {
-        const int s0 = c0 + (int)threadIdx.x * kCompactE;
-        int w[kCompactE], k[kCompactE];
-        bool run[kCompactE];
 #pragma unroll
-        for (int e = 0; e < kCompactE; ++e) w[e] = s0 + e < prev ? act[s0 + e] : -1;
+    for (int e = 0; e < kCompactE; ++e) w[e] = (e < E && s0 + e < prev) ? act[s0 + e] : -1;
 #pragma unroll
-        for (int e = 0; e < kCompactE; ++e) {
-            run[e] = w[e] >= 0 && st[w[e]].status == SB_WALKER_RUNNING;
-            k[e] = w[e] >= 0 ? key[w[e]] : -1;
-        }
-#pragma unroll
-        for (int e = 0; e < kCompactE; ++e) {
-            const int b = (k[e] >= 0 && k[e] < K) ? k[e] : K;
-            pk[e] = run[e] ? ((uint32_t)b << kPackShift) | (uint32_t)w[e] : kPackDrop;
-            if (parked && s0 + e < prev) tmp[s0 + e] = pk[e];
-        }
-        for (uint64_t m = warp_buckets(pk, nb); m; m &= m - 1) {
-            const int b = __ffsll((long long)m) - 1;
-            const int sum = __reduce_add_sync(0xffffffffu, count_bucket(pk, b));
-            if (lane == 0) atomicAdd(&total[b], sum);
-        }
+    for (int e = 0; e < kCompactE; ++e) {
+        const bool run = w[e] >= 0 && st[w[e]].status == SB_WALKER_RUNNING;
+        const int k = w[e] >= 0 ? key[w[e]] : -1;
+        const int b = (k >= 0 && k < K) ? k : K;
+        pk[e] = run ? ((uint32_t)b << kPackShift) | (uint32_t)w[e] : kPackDrop;
+        if (e < E && s0 + e < prev) tmp[s0 + e] = pk[e];
+    }
+    for (uint64_t m = warp_buckets(pk, E, nb); m; m &= m - 1) {
+        const int b = __ffsll((long long)m) - 1;
+        const int sum = __reduce_add_sync(0xffffffffu, count_bucket(pk, E, b));
+        if (lane == 0) atomicAdd(&total[b], sum);
     }
     __syncthreads();
-    if (wid == 0) {  // exclusive sums of the bucket totals, 32 buckets at a time
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) cnt[(size_t)blockIdx.x * nb + b] = total[b];
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[(size_t)G * nb] = prev;
+}
+
+__global__ void __launch_bounds__(kCkThreads) k_compact_place(int32_t *act, int32_t *n_act, int64_t *n_evals, int K,
+                                                              const uint32_t *tmp, const int32_t *cnt) {
+    constexpr int NW = kCkThreads / 32;
+    __shared__ int off[kSortBuckets];             // this CTA's first slot of each bucket
+    __shared__ int wtot[NW][kSortBuckets], woff[NW][kSortBuckets];
+    const int G = (int)gridDim.x, nb = K + 1, c = (int)blockIdx.x;
+    const int prev = cnt[(size_t)G * nb];
+    const int E = compact_E(prev, G);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (wid == 0) {
+        // per bucket: all CTAs' total and the CTAs before c; then the exclusive sums of
+        // the totals, 32 buckets at a time
         int carry = 0;
         for (int b0 = 0; b0 < nb; b0 += 32) {
             const int b = b0 + lane;
-            const int v = b < nb ? total[b] : 0;
-            const int incl = warp_incl_scan(v);
-            if (b < nb) base[b] = carry + incl - v;
+            int tot = 0, before = 0;
+            if (b < nb)
+                for (int q = 0; q < G; ++q) {
+                    const int v = cnt[(size_t)q * nb + b];
+                    tot += v;
+                    before += q < c ? v : 0;
+                }
+            const int incl = warp_incl_scan(tot);
+            if (b < nb) off[b] = carry + incl - tot + before;
             carry += __shfl_sync(0xffffffffu, incl, 31);
         }
-        if (lane == 0) *n_act = carry;
+        if (c == 0 && lane == 0) {
+            *n_act = carry;
+            if (n_evals) *n_evals += prev;
+        }
+    }
+    const int s0 = (c * kCkThreads + (int)threadIdx.x) * E;
+    uint32_t pk[kCompactE];
+#pragma unroll
+    for (int e = 0; e < kCompactE; ++e) pk[e] = (e < E && s0 + e < prev) ? tmp[s0 + e] : kPackDrop;
+    const uint64_t wpres = warp_buckets(pk, E, nb);
+    for (int b = lane; b < nb; b += 32) wtot[wid][b] = 0;
+    __syncwarp();
+    for (uint64_t m = wpres; m; m &= m - 1) {
+        const int b = __ffsll((long long)m) - 1;
+        const int incl = warp_incl_scan(count_bucket(pk, E, b));
+        if (lane == 31) wtot[wid][b] = incl;
     }
     __syncthreads();
-    // pass 2
-    for (int c0 = 0; c0 < prev; c0 += kCompactChunk) {
-        const int s0 = c0 + (int)threadIdx.x * kCompactE;
-        if (parked) {
+    // per bucket: the warps' offsets (a scan over the NW warps' totals)
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        int run = off[b];
+        for (int q = 0; q < NW; ++q) {
+            woff[q][b] = run;
+            run += wtot[q][b];
+        }
+    }
+    __syncthreads();
+    for (uint64_t m = wpres; m; m &= m - 1) {
+        const int b = __ffsll((long long)m) - 1;
+        const int n_b = count_bucket(pk, E, b);
+        int pos = woff[wid][b] + warp_incl_scan(n_b) - n_b;
 #pragma unroll
-            for (int e = 0; e < kCompactE; ++e) pk[e] = s0 + e < prev ? tmp[s0 + e] : kPackDrop;
-        }
-        const uint64_t wpres = warp_buckets(pk, nb);
-        for (int b = lane; b < nb; b += 32) wtot[wid][b] = 0;
-        __syncwarp();
-        for (uint64_t m = wpres; m; m &= m - 1) {
-            const int b = __ffsll((long long)m) - 1;
-            const int incl = warp_incl_scan(count_bucket(pk, b));
-            if (lane == 31) wtot[wid][b] = incl;
-        }
-        __syncthreads();
-        // per bucket: the warps' offsets (scan over the 32 warps' totals) after the
-        // entries of the bucket from earlier chunks
-        for (int b = wid; b < nb; b += 32) {
-            const int v = wtot[lane][b];
-            const int incl = warp_incl_scan(v);
-            woff[lane][b] = base[b] + incl - v;
-            __syncwarp();
-            if (lane == 31) base[b] += incl;
-        }
-        __syncthreads();
-        for (uint64_t m = wpres; m; m &= m - 1) {
-            const int b = __ffsll((long long)m) - 1;
-            const int cnt = count_bucket(pk, b);
-            int pos = woff[wid][b] + warp_incl_scan(cnt) - cnt;
-#pragma unroll
-            for (int e = 0; e < kCompactE; ++e)
-                if ((pk[e] >> kPackShift) == (uint32_t)b) act[pos++] = (int32_t)(pk[e] & ((1u << kPackShift) - 1u));
-        }
-        __syncthreads();  // wtot, woff and base are rewritten by the next chunk
+        for (int e = 0; e < kCompactE; ++e)
+            if (e < E && (pk[e] >> kPackShift) == (uint32_t)b) act[pos++] = (int32_t)(pk[e] & ((1u << kPackShift) - 1u));
     }
 }
 
 }  // namespace
 
-void launch_lbfgs_compact_by_key(const LbfgsArgs<float> &a, int64_t *n_evals, const int32_t *key, int K, int32_t *tmp,
-                                 cudaStream_t s) {
+int lbfgs_compact_blocks(int n) {
+    const int per = kCkThreads * kCompactE;
+    const int need = (n + per - 1) / per;
+    return need > kCkMinBlocks ? need : kCkMinBlocks;
+}
+
+size_t lbfgs_compact_cnt_elems(int n) { return (size_t)lbfgs_compact_blocks(n) * kSortBuckets + 1; }
+
+void launch_lbfgs_compact_by_key(const LbfgsArgs<float> &a, int n, int64_t *n_evals, const int32_t *key, int K,
+                                 int32_t *tmp, int32_t *cnt, cudaStream_t s) {
+    const int G = lbfgs_compact_blocks(n);
     note_launch();
-    k_lbfgs_compact_by_key<<<1, 1024, 0, s>>>(a.st, a.act, a.n_act, n_evals, key, K,
-                                              reinterpret_cast<uint32_t *>(tmp));
+    k_compact_count<<<G, kCkThreads, 0, s>>>(a.st, a.act, a.n_act, key, K, reinterpret_cast<uint32_t *>(tmp), cnt);
+    note_launch();
+    k_compact_place<<<G, kCkThreads, 0, s>>>(a.act, a.n_act, n_evals, K, reinterpret_cast<const uint32_t *>(tmp), cnt);
 }
 
 bool lbfgs_compact_by_key_fits(int n) { return n >= 0 && n < (1 << kPackShift); }

@@ -169,6 +169,7 @@ struct RefineWs {
     int64_t *n_evals;
     int64_t *round;         // rounds run (device-decided loop)
     int32_t *act_tmp;       // [N] scratch of the grouped compaction (mixed path)
+    int32_t *act_cnt;       // its per-CTA bucket counts
     double *qpart, *Z, *R;  // FP64 evaluation
     TcWs tc;                // mixed-precision evaluation
 };
@@ -236,6 +237,7 @@ void carve_refine(Carver &cv, RefineWs<T> &r, int n, int d, int K, int m, bool f
     } else {
         carve_tc(cv, r.tc, n, d, K, prec);
         r.act_tmp = cv.take<int32_t>((size_t)n);
+        r.act_cnt = cv.take<int32_t>(lbfgs_compact_cnt_elems(n));
         r.MRI = cv.take<float>((size_t)n * m * m);
         r.MYY = cv.take<float>((size_t)n * m * m);
     }
@@ -473,7 +475,8 @@ sb_status run_refine(const ProbView &pv, const sb_config *c, const RefineWs<T> &
             bool keyed = false;
             if constexpr (std::is_same<T, float>::value) {  // walkers grouped by dominant component
                 if (lbfgs_compact_by_key_fits(n)) {
-                    launch_lbfgs_compact_by_key(a, ev, static_cast<const int32_t *>(r.tc.p[12]), pv.K, r.act_tmp, bs);
+                    launch_lbfgs_compact_by_key(a, n, ev, static_cast<const int32_t *>(r.tc.p[12]), pv.K, r.act_tmp,
+                                                r.act_cnt, bs);
                     keyed = true;
                 }
             }

@@ -48,10 +48,13 @@ __host__ __device__ __forceinline__ int hist_ld(int d) { return (d + 7) / 8 * 8;
 // the stored pairs S, Y are bf16 ([N][m][hist_ld(d)]). MRI, MYY: per-walker [N][m][m] R^-1
 // (R = upper(S^T Y)) and Y^T Y, slot-indexed.
 void launch_lbfgs_step_cta(const LbfgsArgs<float> &a, int n, float *MRI, float *MYY, int num_sms, cudaStream_t s);
-// Compaction of the mixed path's active list, grouped by key[w] (the walker's dominant
-// component, 0..K-1; others last), the list order kept inside a group; tmp: [N] scratch.
-void launch_lbfgs_compact_by_key(const LbfgsArgs<float> &a, int64_t *n_evals, const int32_t *key, int K, int32_t *tmp,
-                                 cudaStream_t s);
+// Compaction of the mixed path's active list (at most n entries), grouped by key[w]
+// (the walker's dominant component, 0..K-1; others last), the list order kept inside a
+// group; tmp: [n] scratch, cnt: lbfgs_compact_cnt_elems(n) scratch.
+void launch_lbfgs_compact_by_key(const LbfgsArgs<float> &a, int n, int64_t *n_evals, const int32_t *key, int K,
+                                 int32_t *tmp, int32_t *cnt, cudaStream_t s);
+int lbfgs_compact_blocks(int n);
+size_t lbfgs_compact_cnt_elems(int n);
 // Whether n walkers fit the keyed compaction (walker ids below 2^25; else the plain
 // compaction runs, with the same results).
 bool lbfgs_compact_by_key_fits(int n);

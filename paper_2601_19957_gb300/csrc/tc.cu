@@ -681,11 +681,13 @@ template <int PREC>
 __global__ void __launch_bounds__(256) k_tc_scale_z(int K, int ldz, int z_rows, const int32_t *n_rows_dev,
                                                     int n_rows_max, const float *R, const uint32_t *rflag, void *Z) {
     const int mb = blockIdx.x, k = blockIdx.y;
-    if (rflag[(size_t)mb * K + k] != 1u) return;
     const int n_rows = n_rows_dev ? *n_rows_dev : n_rows_max;
+    if (mb * BM >= n_rows || rflag[(size_t)mb * K + k] != 1u) return;
     constexpr int VE = (PREC == SB_PREC_BF16) ? 8 : 4;  // elements per 16-byte vector
     constexpr int NB = 16;                              // vectors in flight per thread
-    const int nv = ldz / VE, tot = BM * nv;
+    // the block's rows are split over gridDim.z CTAs (more loads in flight per pair)
+    const int rows = BM / (int)gridDim.z, row0 = (int)blockIdx.z * rows;
+    const int nv = ldz / VE, tot = rows * nv;
     uint4 *Zv = reinterpret_cast<uint4 *>(Z);  // 16-byte vectors (ldz is a multiple of 64 elements)
     for (int e0 = 0; e0 < tot; e0 += NB * (int)blockDim.x) {
         // every load of the batch is issued before the first store
@@ -696,7 +698,7 @@ __global__ void __launch_bounds__(256) k_tc_scale_z(int K, int ldz, int z_rows, 
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
             const int e = e0 + (int)threadIdx.x + j * (int)blockDim.x;
-            const int row = e / nv, v = e - row * nv;
+            const int row = row0 + e / nv, v = e % nv;
             const int n = mb * BM + row;
             in[j] = e < tot && n < z_rows;
             r[j] = (in[j] && n < n_rows) ? R[(size_t)n * K + k] : 0.f;
@@ -1094,7 +1096,7 @@ TcArgs base_args(const ProbView &pv, const TcWs &t) {
 }
 
 void launch_scale_z(const ProbView &pv, const TcWs &t, const int32_t *n_rows_dev, int n_rows_max, cudaStream_t s) {
-    const dim3 grid((unsigned)((n_rows_max + BM - 1) / BM), (unsigned)pv.K);
+    const dim3 grid((unsigned)((n_rows_max + BM - 1) / BM), (unsigned)pv.K, 4u);
     note_launch();
     if (t.prec == SB_PREC_BF16)
         k_tc_scale_z<SB_PREC_BF16><<<grid, 256, 0, s>>>(pv.K, (int)t.ldz, (int)t.rows, n_rows_dev, n_rows_max,
