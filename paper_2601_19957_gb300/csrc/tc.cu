@@ -759,6 +759,11 @@ __global__ void __launch_bounds__(128) k_tc_need(int K, const int32_t *n_rows_de
         const double ub = (double)__fmaf_ru(lnorm[j], D, zst[w]);
         elb = a_k[j] - 0.5 * ub * ub;
     }
+    // one CTA is one 128-row block: it writes every component's word of its block
+    __shared__ unsigned long long s_need;
+    if (threadIdx.x == 0) s_need = 0ull;
+    __syncthreads();
+    uint64_t mk = 0;
     for (int k = 0; k < K; ++k) {
         bool need = valid;
         if (bounded) {
@@ -766,9 +771,11 @@ __global__ void __launch_bounds__(128) k_tc_need(int K, const int32_t *n_rows_de
             zb[(size_t)w * K + k] = b;
             need = !(a_k[k] - 0.5 * (double)b * (double)b < elb - kSkipNats);
         }
-        const unsigned any = __ballot_sync(0xffffffffu, need);
-        if (any && (threadIdx.x & 31) == 0) atomicOr(&zmask[(size_t)(n / BM) * K + k], 1u);
+        if (__any_sync(0xffffffffu, need)) mk |= 1ull << k;
     }
+    if ((threadIdx.x & 31) == 0 && mk) atomicOr(&s_need, (unsigned long long)mk);
+    __syncthreads();
+    if ((int)threadIdx.x < K) zmask[(size_t)blockIdx.x * K + threadIdx.x] = (uint32_t)((s_need >> threadIdx.x) & 1ull);
 }
 
 // lnorm_k = |L_k|_F (an upper bound on |L_k|_2), rounded up to FP32: kLnParts CTAs
@@ -1613,7 +1620,6 @@ void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, cons
     // then their centred operand, |z|^2 and z, then l, r and the flags of the pairs
     // with r > 0, then r z for those pairs (GEMM2's A operand), then the gradient
     uint32_t *zmask = (uint32_t *)t.p[16];
-    cudaMemsetAsync(zmask, 0, sizeof(uint32_t) * ((n + BM - 1) / BM) * pv.K, s);
     note_launch();
     k_tc_need<<<(n + 127) / 128, 128, 0, s>>>(pv.K, n_act, n, act, pv.a, (const float *)t.p[15], (float *)t.p[11],
                                               (const int32_t *)t.p[12], (const float *)t.p[13],
@@ -1623,8 +1629,7 @@ void tc_eval_walkers(const ProbView &pv, const sb_config *c, const TcWs &t, cons
     a.rflag = nullptr;  // GEMM1 over the kept pairs: |z|^2 partials and z itself
     launch_gemm_any(t.prec, MODE_ZW, t.bn, t.mapA1, t.mapT, a, s);
     a.zmask = nullptr;
-    a.rflag = (const uint32_t *)t.p[10];
-    cudaMemsetAsync(t.p[10], 0, sizeof(uint32_t) * ((n + BM - 1) / BM) * pv.K, s);
+    a.rflag = (const uint32_t *)t.p[10];  // written for every block by k_tc_lse
     note_launch();
     k_tc_lse<<<(n + 127) / 128, 128, 0, s>>>(0, pv.K, a.n_ntile, n_act, n, act, a.qpart, pv.a, (float *)t.p[6], FT,
                                              nullptr, (uint32_t *)t.p[10], zmask, (float *)t.p[11],
@@ -1651,8 +1656,7 @@ sb_status tc_loglik_points(const ProbView &pv, const sb_config *c, const TcWs &t
     // with the gradient, GEMM1 also stores z (the A operand of GEMM2 once scaled by r)
     a.rflag = nullptr;
     launch_gemm_any(t.prec, grad ? MODE_ZW : MODE_ZR, t.bn, t.mapA1, t.mapT, a, s);
-    a.rflag = (const uint32_t *)t.p[10];
-    cudaMemsetAsync(t.p[10], 0, sizeof(uint32_t) * ((n + BM - 1) / BM) * pv.K, s);
+    a.rflag = (const uint32_t *)t.p[10];  // written for every block by k_tc_lse
     note_launch();
     k_tc_lse<<<(n + 127) / 128, 128, 0, s>>>(2, pv.K, a.n_ntile, nullptr, n, nullptr, a.qpart, pv.a,
                                              (float *)t.p[6], nullptr, ell, (uint32_t *)t.p[10], nullptr, nullptr,
