@@ -138,9 +138,9 @@ def test_mixed_refine_walkers_independent_of_batch(prec):
     """A walker's refinement depends on its own start alone: its rows of a tensor-core
     round do not depend on the rows that share its 128-row block (the pairs a block
     skips contribute exact zeros to every row) and its L-BFGS step reads no other
-    walker. So 40000 walkers refined in one call, where the compaction of the active
-    list takes its multi-chunk path (beyond 16384 entries), end bit for bit where the
-    same starts end in calls of at most 16000 walkers."""
+    walker. So 40000 walkers refined in one call, where every thread of the active
+    list's compaction holds several entries (40000 over 64 CTAs of 256 threads), end
+    bit for bit where the same starts end in calls of at most 16000 walkers."""
     inst = make_instance(16, 3, 5150, s_range=(0.05, 0.5), mean_box=(-6, 6), sep=8.0)
     n = 40000
     c = sb.make_config(SolveConfig(n_rays=1024, n_steps=64, n_starts=n, m=10, seed=17, prec=prec))
