@@ -63,15 +63,37 @@ __device__ __forceinline__ void normal_pair_f32(uint32_t c0, uint32_t c1, uint32
     z1 = rad * sn;
 }
 
-// Distance from o along u to the box boundary (whole warp; 0 when u = 0).
+// Distance from o along u to the box boundary (whole warp; 0 when u = 0): the minimum
+// over u_i != 0 of (hi_i - o_i) / u_i or (lo_i - o_i) / u_i, each rounded to nearest in
+// FP64. Only candidates are divided in FP64: FP32 quotients (relative error below
+// 2^-21 for magnitudes in [1e-30, 1e30]) bound the smallest, and a coordinate is divided
+// when its estimate lies within 2^-18 of that bound, or when its numerator and u_i are
+// outside that range or of opposite signs (an origin outside the box). The FP64
+// quotient is monotone in the exact one, so the result is the plain minimum.
 __device__ double exit_length(int lane, int d, const double *o, const double *u, const double *lo, const double *hi) {
+    auto est_of = [&](int i, double &num) -> float {  // -1: always a candidate
+        const double ui = u[i];
+        num = ui > 0.0 ? sub_rn(hi[i], o[i]) : sub_rn(lo[i], o[i]);
+        if (num == 0.0) return 0.f;  // exact
+        if ((num > 0.0) != (ui > 0.0)) return -1.f;
+        return exit_estimate(fabs(ui), fabs(num));
+    };
+    float est = INFINITY;
+    for (int i = lane; i < d; i += 32) {
+        if (u[i] == 0.0) continue;
+        double num;
+        const float e = est_of(i, num);
+        if (e >= 0.f) est = fminf(est, e);
+    }
+    const float thr = warp_min(est) * (1.0f + 0x1p-18f);
     double t = INFINITY;
     for (int i = lane; i < d; i += 32) {
         const double ui = u[i];
-        if (ui > 0.0)
-            t = fmin(t, div_rn(sub_rn(hi[i], o[i]), ui));
-        else if (ui < 0.0)
-            t = fmin(t, div_rn(sub_rn(lo[i], o[i]), ui));
+        if (!(ui > 0.0 || ui < 0.0)) continue;
+        double num;
+        const float e = est_of(i, num);
+        if (e >= 0.f && e > thr) continue;
+        t = fmin(t, div_rn(num, ui));
     }
     t = warp_min(t);
     return t < INFINITY ? t : 0.0;

@@ -264,7 +264,7 @@ Layout layout(void *base, const sb_problem *p, const sb_config *c) {
     if (fp64)
         L.di.qpart = cv.take<double>(lik_f64_qpart_elems(d, K, L.di.chunk));
     else {
-        carve_tc(cv, L.di.tc, tc_ray_chunk(d, K, total), d, K, c->prec);
+        carve_tc(cv, L.di.tc, tc_setup_rows(total), d, K, c->prec);
         carve_tc_quad(cv, L.di.quad, c->n_rays, d, K, c->prec);
     }
     L.di.sel.bucket = cv.take<int32_t>(total);

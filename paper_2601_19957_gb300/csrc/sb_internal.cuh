@@ -101,24 +101,30 @@ __device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, 
 // t_exit = min_i half_i / |u_i| over the coordinates i = lane, lane + 32, ... of one
 // warp (u_i = 0 skipped; INFINITY when every u_i is 0), each quotient rounded to
 // nearest in FP64, without dividing every coordinate in FP64: FP32 quotients (three
-// roundings, relative error below 2^-21 for values in [1e-30, 1e30]) bound the
-// smallest one, and only coordinates within 2^-18 of that bound, or outside the
-// range where the FP32 error holds, are divided in FP64. The FP64 quotient is
-// monotone in the exact one, so the result is the plain minimum of all of them.
-__device__ __forceinline__ double warp_exit_min(int lane, int d, const double *u, const double *half) {
+// roundings, relative error below 2^-21 when operands and quotient lie in
+// [1e-30, 1e30]) bound the smallest one, and only coordinates within 2^-18 of that
+// bound, or outside that range, are divided in FP64. The FP64 quotient is monotone in
+// the exact one, so the result is the plain minimum of all of them.
+__device__ __forceinline__ float exit_estimate(double au, double h64) {  // -1: always divide in FP64
     constexpr float kLo = 1e-30f, kHi = 1e30f;
+    const float a = (float)au, h = (float)h64;
+    if (!(a >= kLo && a <= kHi) || !(h >= kLo && h <= kHi)) return -1.f;
+    const float e = __fdiv_rn(h, a);
+    return e >= kLo && e <= kHi ? e : -1.f;
+}
+__device__ __forceinline__ double warp_exit_min(int lane, int d, const double *u, const double *half) {
     float est = INFINITY;
     for (int i = lane; i < d; i += 32) {
-        const float a = (float)fabs(u[i]), h = (float)half[i];
-        if (a >= kLo && h >= kLo && h <= kHi) est = fminf(est, __fdiv_rn(h, a));
+        const float e = exit_estimate(fabs(u[i]), half[i]);
+        if (e >= 0.f) est = fminf(est, e);
     }
     const float thr = warp_min(est) * (1.0f + 0x1p-18f);
     double t = INFINITY;
     for (int i = lane; i < d; i += 32) {
         const double au = fabs(u[i]);
         if (!(au > 0.0)) continue;
-        const float a = (float)au, h = (float)half[i];
-        if (a >= kLo && h >= kLo && h <= kHi && __fdiv_rn(h, a) > thr) continue;
+        const float e = exit_estimate(au, half[i]);
+        if (e >= 0.f && e > thr) continue;
         t = fmin(t, __ddiv_rn(half[i], au));
     }
     return warp_min(t);

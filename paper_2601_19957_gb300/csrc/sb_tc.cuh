@@ -19,7 +19,9 @@ struct TcWs {
 
 bool tc_available(int prec);
 void carve_tc(Carver &cv, TcWs &t, int rows, int d, int K, int prec);
-int tc_ray_chunk(int d, int K, int64_t total);
+// Rows of the scratch that holds the problem's tensor-core copies of L_k, mu and c
+// (the autotuner's and the skip bounds' passes run on it), for total ray samples.
+int tc_setup_rows(int64_t total);
 // Encodes the A-operand tensor maps of this scratch (depends on its row capacity).
 bool tc_maps_for_rows(TcWs &t);
 // Tile width the autotuner chose for (d, K, prec) in this process (0: not tuned yet).

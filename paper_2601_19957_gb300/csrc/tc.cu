@@ -1151,11 +1151,9 @@ void carve_tc(Carver &cv, TcWs &t, int rows, int d, int K, int prec) {
     t.p[16] = cv.take<uint32_t>((size_t)(rows / BM) * K);
 }
 
-int tc_ray_chunk(int d, int K, int64_t total) {
-    (void)d;
-    (void)K;
-    const int64_t b = 32768;  // centred operand of a chunk: K x 32768 x d elements
-    return (int)(total < b ? total : b);
+int tc_setup_rows(int64_t total) {
+    // the tile autotuner times at most 16384 rows (enough row blocks for every SM)
+    return (int)(total < 16384 ? total : 16384);
 }
 
 bool tc_maps_for_rows(TcWs &t) {
