@@ -185,7 +185,7 @@ def _check_ray_samples(inst, X, ell, prec):
 
 @pytest.mark.parametrize("prec", [sb.PREC_BF16, sb.PREC_TF32])
 @pytest.mark.parametrize("d,K,n_rays,n_steps", [(64, 4, 64, 16), (300, 3, 32, 32), (200, 2, 130, 8),
-                                                (1024, 8, 32, 64), (7, 2, 16, 8), (1, 1, 4, 4)])
+                                                (1024, 8, 32, 64), (7, 2, 16, 8), (1, 1, 4, 4), (5, 2, 1, 8)])
 def test_discover_quadratic_ray_pass_against_oracle(prec, d, K, n_rays, n_steps):
     """Every ray sample (n_starts = n_rays x n_steps, so that discovery returns all of
     them) against the FP64 oracle's l at the returned point: ragged d (300, 200, 7, 1

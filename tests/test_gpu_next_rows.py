@@ -219,3 +219,42 @@ def test_ray_loglik_origins_matches_oracle(form, d, K, n_rays, n_steps):
     ref = np.array([oracle.loglik(inst, x) for x in X])
     prec = {2: sb.PREC_BF16, 3: sb.PREC_TF32}[form]
     tc_bound.check_ray_samples(inst, X, ell.reshape(-1) - ref, prec, O=Orep)
+
+
+@pytest.mark.parametrize("form", [2, 3])
+def test_ray_loglik_origins_edge_cases(form):
+    """Origins on the box surface and at a corner, axis-aligned directions (every other
+    coordinate of u zero), a ray leaving through the face it starts on (t_exit = 0, every
+    sample at the origin), one step per ray, one ray and 129 rays (a ragged 128-row
+    tile): t_exit against its definition bit for bit and l within the error model."""
+    d, K = 48, 3
+    inst = make_instance(d, K, 4848, s_range=(0.05, 0.5), mean_box=(-6, 6), sep=8.0)
+    rng = np.random.default_rng(4849)
+    n = 129
+    O = rng.uniform(inst.lo, inst.hi, (n, d))
+    U = rng.standard_normal((n, d))
+    O[0] = inst.hi                            # a corner
+    O[1, 5] = inst.lo[5]                      # on a face, leaving through it
+    U[1] = 0.0
+    U[1, 5] = -1.0
+    O[2, 7] = inst.hi[7]                      # on a face, entering the box
+    U[2] = 0.0
+    U[2, 7] = -1.0
+    U[3] = 0.0
+    U[3, 0] = 1.0                             # axis-aligned from inside
+    U /= np.linalg.norm(U, axis=1, keepdims=True)
+    prec = {2: sb.PREC_BF16, 3: sb.PREC_TF32}[form]
+    for rows, n_steps in ((n, 1), (1, 7), (n, 5)):
+        Or, Ur = O[:rows], U[:rows]
+        ell, te = sb.ray_loglik_origins(sb.Problem(inst), torch.as_tensor(Or), torch.as_tensor(Ur), n_steps,
+                                        form=form)
+        ell, te = ell.cpu().numpy(), te.cpu().numpy()
+        with np.errstate(divide="ignore", invalid="ignore"):
+            cand = np.where(Ur > 0, (inst.hi - Or) / Ur, np.where(Ur < 0, (inst.lo - Or) / Ur, np.inf))
+        np.testing.assert_array_equal(te, cand.min(1))
+        if rows > 1:
+            assert te[1] == 0.0 and te[2] > 0.0
+        tau = (np.arange(1, n_steps + 1) / n_steps)[None, :] * te[:, None]
+        X = (Or[:, None, :] + tau[:, :, None] * Ur[:, None, :]).reshape(-1, d)
+        ref = np.array([oracle.loglik(inst, x) for x in X])
+        tc_bound.check_ray_samples(inst, X, ell.reshape(-1) - ref, prec, O=np.repeat(Or, n_steps, axis=0))
