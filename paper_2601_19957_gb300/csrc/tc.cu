@@ -12,10 +12,10 @@
 //                 can still reach l, from per-walker bounds on |z_k| and on the
 //                 largest term (a skipped term is below FP32 resolution: exactly 0)
 //   k_tc_center   A1[k][n][:] = round(x_n - mu_k), formed in FP32 (walkers gathered
-//                 through the active list, or ray samples c + t u), bf16 or tf32
+//                 through the active list), bf16 or tf32
 //   k_tc_gemm ZW  z = A1 L_k (GEMM1) for the kept pairs: |z|^2 partials, and z
 //                 itself stored (bf16 / tf32) as Z[k][n][:] when the gradient is wanted
-//                 (ZR: the |z|^2 partials only, for l alone, e.g. at ray samples)
+//                 (ZR: the |z|^2 partials only, for l alone)
 //   k_tc_lse      l, r; flags of the (128-row block, component) pairs with r > 0,
 //                 marking those whose live rows all have r = 1 exactly
 //   k_tc_scale_z  Z[k][n][:] = round(r_nk z_nk) for the flagged pairs (the A
@@ -29,6 +29,12 @@
 // 128-byte swizzle, out-of-range rows/columns zero-filled), so the MMA
 // pipeline never waits on a gathered load. Centring before rounding keeps the
 // stationary point: at x = mu_k the A operand is exactly zero.
+//
+// Rays (x = o + tau u) take another route, the quadratic form in tau (Q below):
+//   k_tc_gemm Q   w = L_k^T u from split operands u_hi L_hi + u_lo L_hi + u_hi L_lo
+//                 (about FP32 accuracy) with q1 = z_k(o) . w and q2 = |w|^2 partials;
+//                 from per-ray origins a first pass stores z_k(o) = o L_k - mu_k L_k
+//   k_q_ell       l at every sample from q0 + 2 tau q1 + tau^2 q2 (FP64)
 //
 // Kernel anatomy (one persistent CTA per SM, 6 warps): warp 0 issues the TMA
 // loads of A and B for each 128-byte K chunk; warp 1 allocates TMEM and issues
