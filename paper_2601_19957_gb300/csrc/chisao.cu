@@ -562,14 +562,39 @@ __global__ void __launch_bounds__(256) k_cs_momentum_f32(int n, int d, const int
     const int smp = moving_list[e];
     const size_t base = (size_t)smp * d;
     float mv = 0.f;
-    for (int i = lane; i < d; i += 32) {
-        const float v = fmaf(m, V[base + i], alpha * GT[base + i]);
-        V[base + i] = v;
-        const float x0 = X[base + i];
-        const float x1 = fminf(fmaxf(x0 + v, (float)lo[i]), (float)hi[i]);
-        X[base + i] = x1;
+    auto step = [&](float vo, float g, float x0, double l, double h, float &vn, float &x1) {
+        vn = fmaf(m, vo, alpha * g);
+        x1 = fminf(fmaxf(x0 + vn, (float)l), (float)h);
         const float dx = x1 - x0;
         mv = fmaf(dx, dx, mv);
+    };
+    // 16-byte accesses: rows start at multiples of d floats; lo and hi (the caller's
+    // arrays) only when they are 16-byte aligned
+    if ((d & 3) == 0 && ((reinterpret_cast<uintptr_t>(lo) | reinterpret_cast<uintptr_t>(hi)) & 15) == 0) {
+        const float4 *G4 = reinterpret_cast<const float4 *>(GT + base);
+        float4 *V4 = reinterpret_cast<float4 *>(V + base);
+        float4 *X4 = reinterpret_cast<float4 *>(X + base);
+        for (int q = lane; q < d / 4; q += 32) {
+            const float4 g = G4[q], vo = V4[q], x0 = X4[q];
+            const double2 l01 = reinterpret_cast<const double2 *>(lo)[2 * q];
+            const double2 l23 = reinterpret_cast<const double2 *>(lo)[2 * q + 1];
+            const double2 h01 = reinterpret_cast<const double2 *>(hi)[2 * q];
+            const double2 h23 = reinterpret_cast<const double2 *>(hi)[2 * q + 1];
+            float4 vn, x1;
+            step(vo.x, g.x, x0.x, l01.x, h01.x, vn.x, x1.x);
+            step(vo.y, g.y, x0.y, l01.y, h01.y, vn.y, x1.y);
+            step(vo.z, g.z, x0.z, l23.x, h23.x, vn.z, x1.z);
+            step(vo.w, g.w, x0.w, l23.y, h23.y, vn.w, x1.w);
+            V4[q] = vn;
+            X4[q] = x1;
+        }
+    } else {
+        for (int i = lane; i < d; i += 32) {
+            float vn, x1;
+            step(V[base + i], GT[base + i], X[base + i], lo[i], hi[i], vn, x1);
+            V[base + i] = vn;
+            X[base + i] = x1;
+        }
     }
     mv = warp_sum(mv);
     if (lane == 0) dist[smp] = __fsqrt_ru(mv) * 1.0001f;

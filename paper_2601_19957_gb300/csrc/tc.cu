@@ -482,6 +482,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 uint32_t v[32];
+                // MODE_Q: this chunk's alpha (one 128-byte row piece per thread when the
+                // alphas are per row) is read before the accumulator, so that the two
+                // latencies overlap
+                float4 alv[8];
+                if (MODE == MODE_Q && a.qalpha) {
+                    const float4 *al4 = reinterpret_cast<const float4 *>(
+                        a.qalpha + (a.qalpha_rows ? ((size_t)n * K + ti.k) : (size_t)ti.k) * a.qald + ti.nt * BN + c0);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) alv[e] = al4[e];
+                }
                 SB_TMEM_LD32(taddr + c0, v);
                 const int col = ti.nt * BN + c0;
                 if (MODE == MODE_G) {
@@ -519,11 +529,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
                         const float z = __uint_as_float(v[e]);
                         q2 = fmaf(z, z, q2);
                     }
-                    if (MODE == MODE_Q && a.qalpha) {
-                        const float *al = a.qalpha + (a.qalpha_rows ? ((size_t)n * K + ti.k) : (size_t)ti.k) * a.qald +
-                                          col;  // zero past d
+                    if (MODE == MODE_Q && a.qalpha) {  // alv: zero past d
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) q1 = fmaf(al[e], __uint_as_float(v[e]), q1);
+                        for (int e = 0; e < 8; ++e) {
+                            q1 = fmaf(alv[e].x, __uint_as_float(v[4 * e]), q1);
+                            q1 = fmaf(alv[e].y, __uint_as_float(v[4 * e + 1]), q1);
+                            q1 = fmaf(alv[e].z, __uint_as_float(v[4 * e + 2]), q1);
+                            q1 = fmaf(alv[e].w, __uint_as_float(v[4 * e + 3]), q1);
+                        }
                     }
                     if (store_row && col < a.ldz) {
                         if (scaled)
